@@ -1,0 +1,194 @@
+"""Algorithm 2: robust non-rigid registration with Welsch's function and
+Anderson acceleration, in FP64.
+
+One *pass* is one execution of the repeat body of Algorithm 2: closest
+points and rotations at X^(k), the energy, the safeguard test, and (if the
+iterate is kept) the weights, the solve of Eq. (surr_solution) and the AA mix.
+
+Readings of Algorithm 2 used here:
+* The safeguard compares with E_prev, the energy of the last kept iterate in
+  the current stage, and rejects only if E > E_prev (ties are kept). After a
+  rejection, X^(k) becomes the last MM result G^(k-1) and that iterate is kept
+  unconditionally on its re-evaluation (MM descent holds in exact
+  arithmetic; the unconditional keep rules out an endless loop caused by
+  rounding). The AA history is kept across a rejection.
+* The stopping test max_i |v_hat_i^(k+1) - v_hat_i^(k)| < eps compares the
+  deformed source at the new iterate with the one at the kept iterate of
+  the pass; I_max counts solves in the stage.
+* Optional extra stopping test (off unless rel_energy_tol > 0): the stage
+  ends when two consecutive kept energies differ by less than
+  rel_energy_tol relative to the earlier one.
+* nu annealing: nu_a starts at the median initial closest-point distance of
+  the undeformed source, nu_r at 3 l-bar; after each stage nu_a is halved
+  (clamped at nu_a_min = l-bar / sqrt(3)) and nu_r is halved; the last stage
+  is the one run with nu_a == nu_a_min. alpha and beta follow Eq.
+  (WeightSettings) with the current nu values, |V| = P, |E_G| = undirected
+  edge count, |V_G| = N, unless given explicitly.
+* eps defaults to 1e-5 times the bbox diagonal of source and target (the
+  paper's 1e-5 on inputs scaled to unit diagonal).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import graph as graph_mod
+from . import model, surrogate
+from .anderson import Anderson
+
+
+@dataclass
+class Params:
+    radius: float = 0.0             # <= 0: 5 * l-bar (Sec. 4.1)
+    max_influence: int = 8
+    nu_a: float = 0.0               # <= 0: median initial NN distance
+    nu_r: float = 0.0               # <= 0: 3 l-bar
+    nu_a_min: float = 0.0           # <= 0: l-bar / sqrt(3)
+    anneal: bool = True
+    k_alpha: float = 100.0
+    k_beta: float = 1.0
+    alpha: float = -1.0             # >= 0 overrides k_alpha
+    beta: float = -1.0              # >= 0 overrides k_beta
+    aa_m: int = 5
+    max_iters_per_stage: int = 100  # I_max
+    max_total_passes: int = 100000
+    eps: float = 0.0                # <= 0: 1e-5 * bbox diagonal
+    rel_energy_tol: float = 0.0
+
+
+@dataclass
+class PassRecord:
+    E: float
+    E_align: float
+    E_reg: float
+    E_rot: float
+    kept: bool
+    nu_a: float
+    nu_r: float
+    stage: int
+    max_disp: float = float("nan")
+
+
+class Registration:
+    def __init__(self, src, tgt, params: Params | None = None, graph=None):
+        self.V = np.asarray(src, dtype=np.float64)
+        self.U = np.asarray(tgt, dtype=np.float64)
+        self.p = params or Params()
+        need_lbar = (self.p.radius <= 0 or self.p.nu_r <= 0
+                     or self.p.nu_a_min <= 0)
+        self.lbar = graph_mod.mean_spacing(self.V) if need_lbar else float("nan")
+        R = self.p.radius if self.p.radius > 0 else 5.0 * self.lbar
+        self.graph = graph if graph is not None else graph_mod.build_graph(
+            self.V, R, self.p.max_influence)
+        both = np.concatenate([self.V, self.U])
+        self.diag = float(np.linalg.norm(both.max(axis=0) - both.min(axis=0)))
+        self.eps = self.p.eps if self.p.eps > 0 else 1e-5 * self.diag
+        if self.p.nu_a > 0:
+            nu_a0 = self.p.nu_a
+        else:
+            _, d2 = model.closest_points(self.V, self.U)
+            nu_a0 = float(np.median(np.sqrt(d2)))
+        self.nu_a_min = self.p.nu_a_min if self.p.nu_a_min > 0 else self.lbar / math.sqrt(3.0)
+        self.nu_r = self.p.nu_r if self.p.nu_r > 0 else 3.0 * self.lbar
+        if not self.p.anneal:
+            self.nu_a_min = nu_a0
+        self.nu_a = max(nu_a0, self.nu_a_min)
+        self.X = model.identity_X(self.graph.N)
+        self.aa = Anderson(self.p.aa_m)
+        self.records: list[PassRecord] = []
+        self.stage = 0
+        self.done = False
+        self.n_solves_total = 0
+        self.n_rejected = 0
+        self._start_stage()
+
+    # -- parameters -------------------------------------------------------
+    def weights(self):
+        P, N, E = self.V.shape[0], self.graph.N, max(self.graph.n_edges, 1)
+        alpha = self.p.alpha if self.p.alpha >= 0 else (
+            self.p.k_alpha * P / E * self.nu_r ** 2 / self.nu_a ** 2)
+        beta = self.p.beta if self.p.beta >= 0 else (
+            self.p.k_beta * P / max(N, 1) / (2.0 * self.nu_a ** 2))
+        return alpha, beta
+
+    def _start_stage(self):
+        self.E_prev = math.inf
+        self.just_reverted = False
+        self.n_solves = 0
+        self.G_last = None
+        self.aa.reset()
+
+    def _end_stage(self):
+        if self.nu_a == self.nu_a_min:
+            self.done = True
+            return
+        self.nu_a = max(self.nu_a / 2.0, self.nu_a_min)
+        self.nu_r = self.nu_r / 2.0
+        self.stage += 1
+        self._start_stage()
+
+    # -- evaluation -------------------------------------------------------
+    def terms(self, X=None, rho=None):
+        return model.energy_terms(self.V, self.U, self.graph,
+                                  self.X if X is None else X,
+                                  self.nu_a, self.nu_r, rho=rho)
+
+    def energy(self, X=None):
+        t = self.terms(X)
+        a, b = self.weights()
+        return model.total_energy(t, a, b), t
+
+    def mm_map(self, terms):
+        """G(X^k): minimiser of the surrogate built at the state ``terms``."""
+        alpha, beta = self.weights()
+        K, B, _ = surrogate.normal_equations(self.V, self.U, self.graph, terms,
+                                             self.nu_a, self.nu_r, alpha, beta)
+        return surrogate.solve_normal_equations(K, B)
+
+    # -- one pass of Algorithm 2 -----------------------------------------
+    def step(self) -> PassRecord | None:
+        if self.done:
+            return None
+        alpha, beta = self.weights()
+        t = self.terms()
+        E = model.total_energy(t, alpha, beta)
+        rec = PassRecord(E, t["E_align"], t["E_reg"], t["E_rot"], True,
+                         self.nu_a, self.nu_r, self.stage)
+        if E > self.E_prev and not self.just_reverted:
+            rec.kept = False
+            self.records.append(rec)
+            self.n_rejected += 1
+            self.X = self.G_last.copy()
+            self.just_reverted = True
+            return rec
+        self.just_reverted = False
+        if (self.p.rel_energy_tol > 0 and math.isfinite(self.E_prev)
+                and abs(self.E_prev - E) < self.p.rel_energy_tol * abs(self.E_prev)):
+            self.records.append(rec)
+            self._end_stage()
+            return rec
+        self.E_prev = E
+        G = self.mm_map(t)
+        self.G_last = G.copy()
+        X_new = self.aa.mix(G, self.X)
+        self.n_solves += 1
+        self.n_solves_total += 1
+        vh_new = model.deform(self.V, self.graph.nidx, self.graph.w,
+                              self.graph.p, X_new)
+        disp = float(np.max(np.linalg.norm(vh_new - t["vhat"], axis=1)))
+        rec.max_disp = disp
+        self.records.append(rec)
+        self.X = X_new
+        if disp < self.eps or self.n_solves == self.p.max_iters_per_stage:
+            self._end_stage()
+        return rec
+
+    def solve(self, max_passes: int | None = None):
+        cap = self.p.max_total_passes if max_passes is None else max_passes
+        n = 0
+        while not self.done and n < cap:
+            self.step()
+            n += 1
+        return self.X

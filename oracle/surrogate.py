@@ -1,0 +1,141 @@
+"""Quadratic surrogate and its minimiser (Sec. 3.3.1 and 3.3.2) in FP64.
+
+The matrices are built exactly as the paper writes them:
+
+  E_align(X|X^k) = |W_a (F X - Q)|_F^2,   F_ij = w_ij [v_i^T - p_j^T, 1],
+                   Q_i = u_rho(i)^k - sum_j w_ij p_j,
+                   W_a = diag(sqrt(w^a_i)), w^a_i = exp(-d_i^2 / 2nu_a^2) / (2 nu_a^2)
+  E_reg(X|X^k)   = |W_r (H X - Y)|_F^2,   H row (i,j): r_ij [(p_i - p_j)^T, 1] at
+                   X_j and [0, 0, 0, -r_ij] at X_i;  Y row: r_ij (p_i - p_j)^T
+  E_rot(X|X^k)   = |J X - Z|_F^2,         J = diag(1,1,1,0, ...),
+                   Z block j = [proj_R(A_j^k)^T; 0]
+  K = F^T W_a^2 F + alpha H^T W_r^2 H + beta J^T J,
+  B = F^T W_a^2 Q + alpha H^T W_r^2 Y + beta J^T J Z,   K X = B  (Eq. surr_solution).
+
+The rotation surrogate is read with its square (|A - proj_R(A^k)|_F^2), the
+form the matrix expression |J X - Z|_F^2 states.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+def align_weights(d2: np.ndarray, nu_a: float) -> np.ndarray:
+    return np.exp(-np.asarray(d2) / (2.0 * nu_a * nu_a)) / (2.0 * nu_a * nu_a)
+
+
+def reg_weights(Dn2: np.ndarray, nu_r: float) -> np.ndarray:
+    return np.exp(-np.asarray(Dn2) / (2.0 * nu_r * nu_r)) / (2.0 * nu_r * nu_r)
+
+
+def build_F(V, graph) -> sp.csr_matrix:
+    V = np.asarray(V, dtype=np.float64)
+    P, K = graph.nidx.shape
+    rows, cols, vals = [], [], []
+    for s in range(K):
+        j = graph.nidx[:, s]
+        m = np.nonzero(j >= 0)[0]
+        jj = j[m]
+        wv = graph.w[m, s]
+        d = V[m] - graph.p[jj]
+        for c in range(3):
+            rows.append(m)
+            cols.append(4 * jj + c)
+            vals.append(wv * d[:, c])
+        rows.append(m)
+        cols.append(4 * jj + 3)
+        vals.append(wv)
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows),
+                          np.concatenate(cols))), shape=(P, 4 * graph.N))
+
+
+def build_Q(U_rho: np.ndarray, graph) -> np.ndarray:
+    Q = np.asarray(U_rho, dtype=np.float64).copy()
+    for s in range(graph.nidx.shape[1]):
+        j = graph.nidx[:, s]
+        m = j >= 0
+        Q[m] -= graph.w[m, s][:, None] * graph.p[j[m]]
+    return Q
+
+
+def build_H(graph):
+    """Returns (H [2|E|, 4N] sparse, Y [2|E|, 3])."""
+    E2 = len(graph.dpair)
+    if E2 == 0:
+        return sp.csr_matrix((0, 4 * graph.N)), np.zeros((0, 3))
+    i, j = graph.dpair[:, 0], graph.dpair[:, 1]
+    d = graph.p[i] - graph.p[j]
+    r = graph.r
+    e = np.arange(E2)
+    rows = [e, e, e, e, e]
+    cols = [4 * j + 0, 4 * j + 1, 4 * j + 2, 4 * j + 3, 4 * i + 3]
+    vals = [r * d[:, 0], r * d[:, 1], r * d[:, 2], r, -r]
+    H = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows),
+                      np.concatenate(cols))), shape=(E2, 4 * graph.N))
+    Y = r[:, None] * d
+    return H, Y
+
+
+def build_J(N: int) -> sp.csr_matrix:
+    diag = np.tile(np.array([1.0, 1.0, 1.0, 0.0]), N)
+    return sp.diags(diag, format="csr")
+
+
+def build_Z(Rm: np.ndarray) -> np.ndarray:
+    N = Rm.shape[0]
+    Z = np.zeros((N, 4, 3))
+    Z[:, :3, :] = np.transpose(Rm, (0, 2, 1))
+    return Z.reshape(4 * N, 3)
+
+
+def normal_equations(V, U, graph, terms, nu_a, nu_r, alpha, beta):
+    """K and B of Eq. (surr_solution) at the state whose energy terms are
+    ``terms`` (closest points, D_ij and rotations evaluated at X^k)."""
+    U = np.asarray(U, dtype=np.float64)
+    F = build_F(V, graph)
+    Q = build_Q(U[terms["rho"]], graph)
+    wa = align_weights(terms["d2"], nu_a)
+    H, Y = build_H(graph)
+    wr = reg_weights(np.sum(terms["D"] ** 2, axis=1), nu_r)
+    J = build_J(graph.N)
+    Z = build_Z(terms["R"])
+    Wa2 = sp.diags(wa)
+    Wr2 = sp.diags(wr)
+    K = (F.T @ Wa2 @ F + alpha * (H.T @ Wr2 @ H) + beta * (J.T @ J)).tocsr()
+    B = F.T @ (wa[:, None] * Q) + alpha * (H.T @ (wr[:, None] * Y)) + beta * (J.T @ (J @ Z))
+    return K, np.asarray(B), dict(F=F, Q=Q, wa=wa, H=H, Y=Y, wr=wr, J=J, Z=Z)
+
+
+def solve_normal_equations(K, B) -> np.ndarray:
+    """Direct solve of K X = B (dense Cholesky for small systems, sparse LU
+    otherwise). Returns X in [N,12] layout."""
+    n = K.shape[0]
+    if n <= 4000:
+        c = scipy.linalg.cho_factor(K.toarray(), lower=True)
+        X = scipy.linalg.cho_solve(c, B)
+    else:
+        X = spla.spsolve(K.tocsc(), B)
+    return np.asarray(X).reshape(n // 4, 4, 3).reshape(n // 4, 12)
+
+
+def surrogate_value(V, U, graph, terms_k, X, nu_a, nu_r, alpha, beta):
+    """The surrogate E(X | X^k) of Eq. (surrogate_func) summed term by term
+    (Eqs. ERegSurrogate, AlignQuadSurrogate and the rotation surrogate),
+    with the constants the paper drops restored so that it equals E at X^k."""
+    from . import model
+    U = np.asarray(U, dtype=np.float64)
+    vh = model.deform(V, graph.nidx, graph.w, graph.p, X)
+    u = U[terms_k["rho"]]
+    dk = np.sqrt(terms_k["d2"])
+    dx = np.sqrt(np.sum((vh - u) ** 2, axis=1))
+    s_align = np.sum(model.welsch_surrogate(dx, dk, nu_a))
+    D = model.reg_residuals(graph.p, graph.dpair, graph.r, X)
+    Dk = terms_k["D"]
+    s_reg = np.sum(model.welsch_surrogate(np.sqrt(np.sum(D * D, axis=1)),
+                                          np.sqrt(np.sum(Dk * Dk, axis=1)), nu_r))
+    A = model.A_of(X)
+    s_rot = np.sum((A - terms_k["R"]) ** 2)
+    return float(s_align + alpha * s_reg + beta * s_rot)

@@ -1,0 +1,324 @@
+"""Seeded synthetic inputs shaped like the registration workloads of
+Yao et al., "Fast and Robust Non-Rigid Registration Using Accelerated
+Majorization-Minimization" (Sec. 4: clean, noisy, partial and RGB-D pairs).
+
+This module is shared by the FP64 oracle, the tests and the benchmark. It
+holds only input generation (surfaces, a smooth ground-truth warp, noise,
+outliers, crops, a synthetic depth grid) and none of the registration
+method's arithmetic. Every array it returns is float32, the precision the
+library's entry points take; the oracle promotes them exactly to float64.
+
+Recipes (all seeded with numpy's PCG64 through ``default_rng``):
+
+* bumpy sphere: ``s(n) = (1 + sum_k a_k exp(-|n - c_k|^2 / (2 w^2))) n`` with
+  ``n`` uniform on the unit sphere, ``c_k`` uniform on the sphere and
+  ``a_k = +-amp`` with random sign; normals from the analytic gradient;
+* warp ``phi(x) = x + sum_{k<4} d_k exp(-|x - mu_k|^2 / (2 * 0.5^2))``,
+  rescaled so that ``max |phi(x) - x|`` over the warped points equals a cap;
+* dense noise: isotropic Gaussian, sigma = fraction x bbox diagonal;
+* outliers: uniform in the bounding box, appended after the surface points;
+* crop: a half-space with a random normal whose offset removes a fraction;
+* depth grid: a 640x480 pinhole view (fx = fy = 525, cx = 319.5,
+  cy = 239.5) of a height field ``z = 2 + h`` with 32 Gaussian bumps, with
+  disc-shaped hole patches until a fraction of pixels is invalid.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "Pair", "bumpy_sphere", "smooth_warp", "add_noise", "add_outliers",
+    "crop_halfspace", "depth_scene", "sphere_pair", "tiny_pair",
+    "workload", "WORKLOADS",
+]
+
+
+@dataclass
+class Pair:
+    """One registration problem: source/target points (+normals) and the
+    ground-truth position of every source point on the target surface."""
+    src: np.ndarray                      # [P,3] float32
+    src_nrm: np.ndarray                  # [P,3] float32
+    tgt: np.ndarray                      # [T,3] float32
+    tgt_nrm: np.ndarray                  # [T,3] float32
+    gt: np.ndarray                       # [P,3] float32, true match of src
+    params: dict = field(default_factory=dict)
+    name: str = ""
+
+    @property
+    def P(self) -> int:
+        return int(self.src.shape[0])
+
+    @property
+    def T(self) -> int:
+        return int(self.tgt.shape[0])
+
+
+def _unit_sphere(n: int, rng: np.random.Generator) -> np.ndarray:
+    g = rng.standard_normal((n, 3))
+    return g / np.linalg.norm(g, axis=1, keepdims=True)
+
+
+def bumpy_sphere(n: int, n_bumps: int, amp: float, width: float,
+                 rng: np.random.Generator, bumps=None):
+    """Samples ``n`` points of a radially bumped unit sphere.
+
+    Returns (xyz, normals, bumps) with bumps = (centres [K,3], amplitudes [K])
+    so that a second, independent sampling of the same surface can be drawn.
+    """
+    if bumps is None:
+        c = _unit_sphere(n_bumps, rng)
+        a = amp * np.where(rng.random(n_bumps) < 0.5, -1.0, 1.0)
+        bumps = (c, a)
+    c, a = bumps
+    nrm = _unit_sphere(n, rng)
+    diff = nrm[:, None, :] - c[None, :, :]                  # [n,K,3]
+    g = np.exp(-np.sum(diff * diff, axis=2) / (2.0 * width * width))
+    r = 1.0 + g @ a                                         # radius
+    # gradient of r(n) in R^3, projected on the tangent plane of the sphere
+    grad = -np.einsum("nk,nkd->nd", g * a[None, :], diff) / (width * width)
+    grad -= np.sum(grad * nrm, axis=1, keepdims=True) * nrm
+    xyz = r[:, None] * nrm
+    normal = r[:, None] * nrm - grad
+    normal /= np.linalg.norm(normal, axis=1, keepdims=True)
+    return xyz, normal, bumps
+
+
+def smooth_warp(x: np.ndarray, cap: float, rng: np.random.Generator,
+                lo=None, hi=None, n_rbf: int = 4, sigma: float = 0.5,
+                return_field: bool = False):
+    """Applies a smooth RBF displacement field whose largest displacement
+    over ``x`` is exactly ``cap``. ``lo``/``hi`` bound the RBF centres
+    (default: bbox of ``x``)."""
+    lo = x.min(axis=0) if lo is None else lo
+    hi = x.max(axis=0) if hi is None else hi
+    mu = lo + (hi - lo) * rng.random((n_rbf, 3))
+    d = _unit_sphere(n_rbf, rng)
+
+    def field_at(p):
+        diff = p[:, None, :] - mu[None, :, :]
+        g = np.exp(-np.sum(diff * diff, axis=2) / (2.0 * sigma * sigma))
+        return g @ d
+
+    disp = field_at(x)
+    scale = cap / max(float(np.linalg.norm(disp, axis=1).max()), 1e-300)
+    out = x + scale * disp
+    if return_field:
+        return out, (lambda p: p + scale * field_at(p))
+    return out
+
+
+def add_noise(x: np.ndarray, frac_of_diag: float, diag: float,
+              rng: np.random.Generator) -> np.ndarray:
+    return x + rng.standard_normal(x.shape) * (frac_of_diag * diag)
+
+
+def add_outliers(x: np.ndarray, nrm: np.ndarray, frac: float,
+                 rng: np.random.Generator):
+    """Appends ``round(frac * len(x))`` points uniform in the bbox of ``x``
+    (normals random unit vectors)."""
+    k = int(round(frac * x.shape[0]))
+    lo, hi = x.min(axis=0), x.max(axis=0)
+    o = lo + (hi - lo) * rng.random((k, 3))
+    on = _unit_sphere(k, rng)
+    return np.concatenate([x, o]), np.concatenate([nrm, on])
+
+
+def crop_halfspace(x: np.ndarray, frac: float, rng: np.random.Generator):
+    """Keeps the points on one side of a random plane chosen so that a
+    fraction ``frac`` of them is removed. Returns the boolean keep mask."""
+    if frac <= 0.0:
+        return np.ones(x.shape[0], dtype=bool)
+    n = _unit_sphere(1, rng)[0]
+    s = x @ n
+    thr = np.quantile(s, 1.0 - frac)
+    return s < thr
+
+
+def _bbox_diag(*arrs) -> float:
+    a = np.concatenate(arrs)
+    return float(np.linalg.norm(a.max(axis=0) - a.min(axis=0)))
+
+
+def _f32(*arrs):
+    return tuple(np.ascontiguousarray(a, dtype=np.float32) for a in arrs)
+
+
+def sphere_pair(P: int, T: int | None, n_bumps: int, amp: float, width: float,
+                warp_cap: float, noise: float, outliers: float, crop: float,
+                seed: int, same_samples: bool) -> Pair:
+    """Bumpy-sphere pair. With ``same_samples`` the target is the warped
+    source itself (before noise/outliers/crop); otherwise the target is an
+    independent sampling of the same surface of size ``T``."""
+    rng = np.random.default_rng(seed)
+    src, src_n, bumps = bumpy_sphere(P, n_bumps, amp, width, rng)
+    lo, hi = src.min(axis=0), src.max(axis=0)
+    if same_samples:
+        base, base_n = src, src_n
+    else:
+        base, base_n, _ = bumpy_sphere(T, n_bumps, amp, width, rng, bumps)
+    # one warp field, applied to the target samples and to the source (gt)
+    _, phi = smooth_warp(base, 1.0, rng, lo, hi, return_field=True)
+    # rescale the field so that the cap holds over the union of samples
+    both = np.concatenate([src, base])
+    disp = phi(both) - both
+    s = warp_cap / float(np.linalg.norm(disp, axis=1).max())
+    warp = lambda p: p + s * (phi(p) - p)
+    tgt = warp(base)
+    tgt_n = base_n
+    gt = warp(src)
+    diag = _bbox_diag(src, tgt)
+    keep = crop_halfspace(tgt, crop, rng)
+    tgt, tgt_n = tgt[keep], tgt_n[keep]
+    tgt = add_noise(tgt, noise, diag, rng) if noise > 0 else tgt
+    if outliers > 0:
+        tgt, tgt_n = add_outliers(tgt, tgt_n, outliers, rng)
+    src, src_n, tgt, tgt_n, gt = _f32(src, src_n, tgt, tgt_n, gt)
+    return Pair(src, src_n, tgt, tgt_n, gt)
+
+
+def depth_scene(P: int, seed: int, width_px: int = 640, height_px: int = 480,
+                hole_frac: float = 0.15, warp_frac: float = 0.10,
+                noise: float = 0.01, n_bumps: int = 32) -> Pair:
+    """Depth-map pair: target = valid pixels of a synthetic 640x480 depth
+    grid of a bumpy height field; source = ``P`` samples of the same surface
+    region under a smooth warp (cap = ``warp_frac`` x bbox diagonal) plus
+    Gaussian noise (``noise`` x bbox diagonal)."""
+    rng = np.random.default_rng(seed)
+    fx = fy = 525.0
+    cx, cy = (width_px - 1) / 2.0, (height_px - 1) / 2.0
+    bc = np.stack([rng.uniform(-1.3, 1.3, n_bumps),
+                   rng.uniform(-1.0, 1.0, n_bumps)], axis=1)
+    ba = rng.uniform(0.04, 0.12, n_bumps) * np.where(
+        rng.random(n_bumps) < 0.5, -1.0, 1.0)
+    bw = rng.uniform(0.12, 0.3, n_bumps)
+
+    def surf(a, b):
+        # point on the ray (a, b, 1) at depth z = 2 + h(2a, 2b)
+        x0, y0 = 2.0 * a, 2.0 * b
+        dx = x0[:, None] - bc[None, :, 0]
+        dy = y0[:, None] - bc[None, :, 1]
+        h = np.exp(-(dx * dx + dy * dy) / (2.0 * bw * bw)) @ ba
+        z = 2.0 + h
+        return np.stack([z * a, z * b, z], axis=1)
+
+    uu, vv = np.meshgrid(np.arange(width_px, dtype=np.float64),
+                         np.arange(height_px, dtype=np.float64))
+    A = ((uu - cx) / fx).ravel()
+    B = ((vv - cy) / fy).ravel()
+    grid = surf(A, B).reshape(height_px, width_px, 3)
+    # normals from grid cross products (central differences, clamped)
+    gx = np.gradient(grid, axis=1)
+    gy = np.gradient(grid, axis=0)
+    gn = np.cross(gx, gy)
+    gn /= np.linalg.norm(gn, axis=2, keepdims=True)
+    valid = np.ones((height_px, width_px), dtype=bool)
+    target_invalid = int(round(hole_frac * width_px * height_px))
+    while (~valid).sum() < target_invalid:
+        hx, hy = rng.uniform(0, width_px), rng.uniform(0, height_px)
+        r = rng.uniform(8.0, 40.0)
+        valid &= (uu - hx) ** 2 + (vv - hy) ** 2 >= r * r
+    tgt = grid[valid]
+    tgt_n = gn[valid]
+    # source: continuous samples of the same image region
+    a = (rng.uniform(0, width_px - 1, P) - cx) / fx
+    b = (rng.uniform(0, height_px - 1, P) - cy) / fy
+    base = surf(a, b)
+    eps = 1e-4
+    ta = surf(a + eps, b) - surf(a - eps, b)
+    tb = surf(a, b + eps) - surf(a, b - eps)
+    base_n = np.cross(ta, tb)
+    base_n /= np.linalg.norm(base_n, axis=1, keepdims=True)
+    diag = _bbox_diag(tgt)
+    warped, phi = smooth_warp(base, warp_frac * diag, rng, return_field=True)
+    src = add_noise(warped, noise, diag, rng)
+    gt = base                       # source point i truly sits at base[i]
+    src, src_n, tgt, tgt_n, gt = _f32(src, base_n, tgt, tgt_n, gt)
+    return Pair(src, src_n, tgt, tgt_n, gt)
+
+
+def tiny_pair(P: int, T: int, seed: int, noise: float = 0.0,
+              outliers: float = 0.0) -> Pair:
+    """Small bumpy-sphere pair for brute-force and unit tests."""
+    return sphere_pair(P, T, n_bumps=4, amp=0.1, width=0.4, warp_cap=0.05,
+                       noise=noise, outliers=outliers, crop=0.0, seed=seed,
+                       same_samples=False)
+
+
+# ---------------------------------------------------------------------------
+# Named workloads (sizes and parameters of the benchmark configurations)
+# ---------------------------------------------------------------------------
+
+def _sphere5k(seed: int = 0) -> Pair:
+    p = sphere_pair(5000, None, n_bumps=8, amp=0.1, width=0.3, warp_cap=0.15,
+                    noise=0.01, outliers=0.05, crop=0.0, seed=seed,
+                    same_samples=True)
+    p.params = dict(radius=0.15, k_alpha=100.0, k_beta=1.0, aa_m=5,
+                    iters=30, precision="fp64")
+    p.name = "sphere5k"
+    return p
+
+
+def _sphere50k_partial(seed: int = 1) -> Pair:
+    p = sphere_pair(50000, 60000, n_bumps=32, amp=0.1, width=0.3,
+                    warp_cap=0.15, noise=0.02, outliers=0.10, crop=0.30,
+                    seed=seed, same_samples=False)
+    p.params = dict(radius=0.055, k_alpha=100.0, k_beta=1.0, aa_m=5,
+                    iters=50, precision="mixed")
+    p.name = "sphere50k_partial"
+    return p
+
+
+def _depth100k(seed: int = 2) -> Pair:
+    p = depth_scene(100000, seed)
+    p.params = dict(radius=0.045, k_alpha=10.0, k_beta=1.0, aa_m=5,
+                    rel_energy_tol=1e-6, precision="mixed")
+    p.name = "depth100k"
+    return p
+
+
+def _grad20k(seed: int = 4) -> Pair:
+    p = sphere_pair(20000, 24000, n_bumps=32, amp=0.1, width=0.3,
+                    warp_cap=0.15, noise=0.02, outliers=0.10, crop=0.30,
+                    seed=seed, same_samples=False)
+    p.params = dict(radius=0.09, k_alpha=100.0, k_beta=1.0, aa_m=0,
+                    unroll=10, precision="mixed")
+    p.name = "grad20k"
+    return p
+
+
+def batch_pairs(n_pairs: int = 64, seed: int = 1000):
+    """Independent pairs with log-uniform point counts in [2000, 40000],
+    crop U[0, 0.3], outliers U[0, 0.1]; otherwise built like sphere5k."""
+    meta = np.random.default_rng(seed)
+    out = []
+    for i in range(n_pairs):
+        P = int(round(math.exp(meta.uniform(math.log(2000), math.log(40000)))))
+        crop = float(meta.uniform(0.0, 0.3))
+        outl = float(meta.uniform(0.0, 0.1))
+        n_nodes = int(meta.integers(100, 1001))
+        p = sphere_pair(P, None, n_bumps=8, amp=0.1, width=0.3,
+                        warp_cap=0.15, noise=0.01, outliers=outl, crop=crop,
+                        seed=seed + i + 1, same_samples=True)
+        # node count ~ surface area / R^2 on a near-unit sphere
+        p.params = dict(radius=float(2.2 / math.sqrt(n_nodes)), k_alpha=100.0,
+                        k_beta=1.0, aa_m=5, iters=30, precision="mixed")
+        p.name = f"batch{i}"
+        out.append(p)
+    return out
+
+
+WORKLOADS = {
+    "sphere5k": _sphere5k,
+    "sphere50k_partial": _sphere50k_partial,
+    "depth100k": _depth100k,
+    "grad20k": _grad20k,
+}
+
+
+def workload(name: str, seed: int | None = None) -> Pair:
+    fn = WORKLOADS[name]
+    return fn() if seed is None else fn(seed)

@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by
+mathematics: closed forms, invariants, special cases that reduce to library
+routines, brute force on tiny inputs, and a hand-worked example.
+
+Every check here is independent of the oracle's own formulas: a dropped
+term, a wrong sign or index, or a transposed operand in the oracle fails at
+least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.spatial
+
+import synth
+from oracle import anderson, graph as G, model as M, surrogate as S
+from oracle.solver import Params, Registration
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _rng(s=0):
+    return np.random.default_rng(s)
+
+
+def _near_identity_X(N, rng, scale=0.05):
+    X = M.identity_X(N).reshape(N, 4, 3)
+    X = X + scale * rng.standard_normal(X.shape)
+    return X.reshape(N, 12)
+
+
+@pytest.fixture(scope="module")
+def small():
+    pair = synth.tiny_pair(400, 450, seed=3, noise=0.002, outliers=0.05)
+    g = G.build_graph(pair.src.astype(np.float64), 0.35)
+    return pair, g
+
+
+# ---------------------------------------------------------------- Welsch ---
+
+def test_welsch_closed_forms():
+    """Eq. (Welsch_func): psi(0)=0, psi(nu)=1-e^{-1/2}, bounded by 1, and the
+    l0 limit as nu -> 0 (Sec. 3.2)."""
+    nu = 0.7
+    assert M.welsch(0.0, nu) == 0.0
+    assert abs(M.welsch(nu * nu, nu) - (1 - math.exp(-0.5))) < 1e-15
+    x = np.linspace(0, 50, 1001)
+    v = M.welsch(x * x, nu)
+    assert np.all(v <= 1.0) and np.all(v[x < 5] < 1.0) and np.all(np.diff(v) >= 0)
+    assert abs(M.welsch(1.0, 1e-3) - 1.0) < 1e-15
+
+
+def test_welsch_surrogate_majorizes_and_touches():
+    """Eq. (WelschSurrogateFunc) bounds psi from above and touches it at
+    x = y with equal slope (Sec. 3.3.1)."""
+    nu = 0.3
+    xs = np.linspace(0, 3, 301)
+    for y in np.linspace(0, 3, 61):
+        s = M.welsch_surrogate(xs, y, nu)
+        f = M.welsch(xs * xs, nu)
+        assert np.all(s >= f - 1e-15)
+        assert abs(M.welsch_surrogate(y, y, nu) - M.welsch(y * y, nu)) < 1e-15
+        h = 1e-6
+        ds = (M.welsch_surrogate(y + h, y, nu) - M.welsch_surrogate(y - h, y, nu)) / (2 * h)
+        df = (M.welsch((y + h) ** 2, nu) - M.welsch((y - h) ** 2, nu)) / (2 * h)
+        assert abs(ds - df) < 1e-7
+
+
+# ----------------------------------------------------------------- graph ---
+
+def test_graph_hand_worked_line():
+    """Algorithm 1 on 11 collinear points, worked by hand (golden file)."""
+    with open(os.path.join(HERE, "golden", "line_graph.json")) as f:
+        gold = json.load(f)
+    x = np.array(gold["points_x"])
+    V = np.stack([x, np.zeros_like(x), np.zeros_like(x)], axis=1)
+    g = G.build_graph(V, gold["radius"])
+    assert g.nodes.tolist() == gold["nodes"]
+    for i, inf in enumerate(gold["influence"]):
+        got = [int(j) for j in g.nidx[i] if j >= 0]
+        assert got == inf, (i, got, inf)
+    assert g.edges.tolist() == gold["edges"]
+    raw = np.array([(1 - 0.01 / 0.0625) ** 3, (1 - 0.04 / 0.0625) ** 3])
+    assert np.allclose(g.w[1, :2], raw / raw.sum(), rtol=0, atol=1e-15)
+
+
+def test_pca_axis_matches_svd():
+    V = _rng(1).standard_normal((300, 3)) * np.array([3.0, 1.0, 0.5])
+    a = G.pca_axis(V)
+    _, _, vt = np.linalg.svd(V - V.mean(0))
+    assert min(np.linalg.norm(a - vt[0]), np.linalg.norm(a + vt[0])) < 1e-10
+    assert a[np.argmax(np.abs(a))] > 0
+
+
+def test_graph_invariants_brute_force(small):
+    """Nodes are R-separated; every point has a non-empty influence set equal
+    to the brute-force set of nodes within R (cap 8 not binding here);
+    weights sum to one (Eq. weight_data); edges join co-influencing nodes;
+    mean r_ij over directed pairs is 1 and r_ij is proportional to 1/|p_i-p_j|."""
+    pair, g = small
+    V = pair.src.astype(np.float64)
+    R = g.radius
+    dn = scipy.spatial.distance.cdist(g.p, g.p)
+    np.fill_diagonal(dn, np.inf)
+    assert dn.min() >= R
+    dv = scipy.spatial.distance.cdist(V, g.p)
+    for i in range(V.shape[0]):
+        brute = sorted(np.nonzero(dv[i] < R)[0].tolist(), key=lambda j: (dv[i, j], j))
+        got = [int(j) for j in g.nidx[i] if j >= 0]
+        assert got == brute[:8] and len(got) >= 1
+    ws = g.w.sum(axis=1)
+    assert np.allclose(ws, 1.0, atol=1e-14)
+    expect = set()
+    for i in range(V.shape[0]):
+        ids = [int(j) for j in g.nidx[i] if j >= 0]
+        for a in ids:
+            for b in ids:
+                if a < b:
+                    expect.add((a, b))
+    assert set(map(tuple, g.edges.tolist())) == expect
+    assert abs(g.r.mean() - 1.0) < 1e-13
+    d = np.linalg.norm(g.p[g.dpair[:, 0]] - g.p[g.dpair[:, 1]], axis=1)
+    assert np.allclose(g.r * d, (g.r * d)[0], rtol=1e-12)
+
+
+def test_mean_spacing_matches_kdtree():
+    V = _rng(2).random((500, 3))
+    tree = scipy.spatial.cKDTree(V)
+    d, _ = tree.query(V, k=7)
+    assert abs(G.mean_spacing(V) - d[:, 1:].mean()) < 1e-13
+
+
+# ---------------------------------------------------------------- deform ---
+
+def test_deform_identity_translation_affine(small):
+    """Eq. (deformed_position) with the partition of unity: X = I gives v,
+    equal translations give v + t, and node-consistent affine maps give the
+    global map A v + t exactly."""
+    pair, g = small
+    V = pair.src.astype(np.float64)
+    N = g.N
+    assert np.allclose(M.deform(V, g.nidx, g.w, g.p, M.identity_X(N)), V, atol=1e-14)
+    t = np.array([0.3, -0.2, 0.1])
+    X = M.identity_X(N).reshape(N, 4, 3)
+    X[:, 3, :] = t
+    assert np.allclose(M.deform(V, g.nidx, g.w, g.p, X.reshape(N, 12)), V + t, atol=1e-14)
+    A = np.array([[1.1, 0.2, -0.1], [0.05, 0.9, 0.3], [-0.2, 0.1, 1.2]])
+    X = np.zeros((N, 4, 3))
+    X[:, :3, :] = A.T
+    X[:, 3, :] = t - g.p + g.p @ A.T          # t_j = t - p_j + A p_j
+    out = M.deform(V, g.nidx, g.w, g.p, X.reshape(N, 12))
+    assert np.allclose(out, V @ A.T + t, atol=1e-13)
+
+
+# ------------------------------------------------------------ closest pt ---
+
+def test_closest_points_match_kdtree_and_ties():
+    rng = _rng(4)
+    U = rng.random((700, 3))
+    Q = rng.random((300, 3))
+    rho, d2 = M.closest_points(Q, U)
+    d, idx = scipy.spatial.cKDTree(U).query(Q)
+    assert np.allclose(np.sqrt(d2), d, atol=1e-14)
+    # where the kd-tree's pick differs it must be an exact tie
+    assert np.all((rho == idx) | (np.abs(d2 - d * d) < 1e-15))
+    # exact duplicates: lowest index wins
+    U2 = np.concatenate([U, U])
+    rho2, _ = M.closest_points(Q, U2)
+    assert np.array_equal(rho2, rho)
+    rho3, _ = M.closest_points(Q, np.concatenate([U[:5], U]))
+    assert np.all(rho3 == np.where(rho < 5, rho, rho + 5))
+
+
+# ---------------------------------------------------------------- energy ---
+
+def test_energy_zero_for_identical_shapes():
+    """Source = target and X = I: closest points are the points themselves,
+    D_ij = 0 and A = I, so E = 0 (Eq. objective_func)."""
+    pair = synth.tiny_pair(300, 300, seed=5)
+    V = pair.src.astype(np.float64)
+    reg = Registration(V, V, Params(radius=0.4, nu_a=0.1, nu_r=0.1, nu_a_min=0.1))
+    E, t = reg.energy()
+    assert E == 0.0 and t["E_align"] == 0.0 and t["E_reg"] == 0.0 and t["E_rot"] == 0.0
+
+
+def test_rotation_projection_and_rot_energy():
+    """proj_R gives an orthonormal matrix with det +1; for A = R0 S with S
+    symmetric positive definite it returns R0 (polar decomposition); and
+    |A - proj_R(A)|_F^2 = sum (sigma_i - 1)^2 with sigma from eig(A^T A)."""
+    rng = _rng(6)
+    for _ in range(50):
+        q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+        if np.linalg.det(q) < 0:
+            q[:, 0] = -q[:, 0]
+        B = rng.standard_normal((3, 3))
+        Sm = B @ B.T + 0.5 * np.eye(3)
+        A = q @ Sm
+        Rm = M.proj_rotation(A)
+        assert np.allclose(Rm.T @ Rm, np.eye(3), atol=1e-13)
+        assert abs(np.linalg.det(Rm) - 1) < 1e-13
+        assert np.allclose(Rm, q, atol=1e-12)
+        sig = np.sqrt(np.linalg.eigvalsh(A.T @ A))
+        assert abs(np.sum((A - Rm) ** 2) - np.sum((sig - 1) ** 2)) < 1e-10
+    # reflection: det < 0 flips the smallest singular direction
+    A = np.diag([2.0, 1.0, -0.5])
+    assert np.allclose(M.proj_rotation(A), np.diag([1.0, 1.0, 1.0]))
+
+
+def test_reg_residual_zero_for_rigid_field(small):
+    """D_ij vanishes when all nodes carry the same affine map (Eq. reg_diff)."""
+    pair, g = small
+    A = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    t = np.array([0.1, 0.2, 0.3])
+    X = np.zeros((g.N, 4, 3))
+    X[:, :3, :] = A.T
+    X[:, 3, :] = t - g.p + g.p @ A.T
+    D = M.reg_residuals(g.p, g.dpair, g.r, X.reshape(g.N, 12))
+    assert np.abs(D).max() < 1e-13
+
+
+# ------------------------------------------------------------- surrogate ---
+
+def _state(pair, g, X, nu_a=0.05, nu_r=0.1):
+    V = pair.src.astype(np.float64)
+    U = pair.tgt.astype(np.float64)
+    t = M.energy_terms(V, U, g, X, nu_a, nu_r)
+    return V, U, t
+
+
+def test_matrix_form_equals_sums(small):
+    """|W_a(FX-Q)|^2, |W_r(HX-Y)|^2 and |JX-Z|^2 (Sec. 3.3.2) equal the
+    term-by-term surrogates of Eqs. (AlignQuadSurrogate), (ERegSurrogate) and
+    the rotation surrogate at an arbitrary X."""
+    pair, g = small
+    rng = _rng(7)
+    Xk = _near_identity_X(g.N, rng)
+    nu_a, nu_r = 0.05, 0.1
+    V, U, t = _state(pair, g, Xk, nu_a, nu_r)
+    _, _, parts = S.normal_equations(V, U, g, t, nu_a, nu_r, 1.0, 1.0)
+    X = _near_identity_X(g.N, rng).reshape(4 * g.N, 3)
+    vh = M.deform(V, g.nidx, g.w, g.p, X.reshape(g.N, 12))
+    wa = np.exp(-t["d2"] / (2 * nu_a ** 2)) / (2 * nu_a ** 2)
+    ref_a = np.sum(wa * np.sum((vh - U[t["rho"]]) ** 2, axis=1))
+    got_a = np.sum(parts["wa"][:, None] * (parts["F"] @ X - parts["Q"]) ** 2)
+    assert abs(got_a - ref_a) < 1e-10 * abs(ref_a)
+    D = M.reg_residuals(g.p, g.dpair, g.r, X.reshape(g.N, 12))
+    Dk = t["D"]
+    wr = np.exp(-np.sum(Dk ** 2, 1) / (2 * nu_r ** 2)) / (2 * nu_r ** 2)
+    ref_r = np.sum(wr * np.sum(D ** 2, axis=1))
+    got_r = np.sum(parts["wr"][:, None] * (parts["H"] @ X - parts["Y"]) ** 2)
+    assert abs(got_r - ref_r) < 1e-10 * abs(ref_r)
+    A = M.A_of(X.reshape(g.N, 12))
+    ref_o = np.sum((A - t["R"]) ** 2)
+    got_o = np.sum((parts["J"] @ X - parts["Z"]) ** 2)
+    assert abs(got_o - ref_o) < 1e-10 * abs(ref_o)
+
+
+def test_normal_equations_minimise_surrogate(small):
+    """The solution of K X = B zeroes the gradient of the term-by-term
+    surrogate (central differences) and the surrogate with the dropped
+    constants restored majorises E and touches it at X^k (Eq. MMConditions)."""
+    pair, g = small
+    rng = _rng(8)
+    Xk = _near_identity_X(g.N, rng, 0.02)
+    nu_a, nu_r, alpha, beta = 0.05, 0.1, 2.0, 0.5
+    V, U, t = _state(pair, g, Xk, nu_a, nu_r)
+    K, B, _ = S.normal_equations(V, U, g, t, nu_a, nu_r, alpha, beta)
+    Kd = K.toarray()
+    assert np.allclose(Kd, Kd.T, atol=1e-12)
+    assert np.linalg.eigvalsh(Kd).min() > 0
+    Xs = S.solve_normal_equations(K, B)
+    f = lambda X: S.surrogate_value(V, U, g, t, X, nu_a, nu_r, alpha, beta)
+    flat = Xs.ravel()
+    h = 1e-5
+    for idx in rng.choice(flat.size, 12, replace=False):
+        e = np.zeros_like(flat)
+        e[idx] = h
+        gd = (f((flat + e).reshape(Xs.shape)) - f((flat - e).reshape(Xs.shape))) / (2 * h)
+        assert abs(gd) < 1e-5 * (1 + abs(f(Xs))), (idx, gd)
+    # majorisation and touching
+    Ek = M.total_energy(t, alpha, beta)
+    assert abs(f(Xk) - Ek) < 1e-10 * abs(Ek)
+    for _ in range(10):
+        X = Xk + 0.01 * rng.standard_normal(Xk.shape)
+        tX = M.energy_terms(V, U, g, X, nu_a, nu_r)
+        assert f(X) >= M.total_energy(tX, alpha, beta) - 1e-10
+
+
+def test_known_affine_map_recovered_in_one_solve():
+    """Target = global affine image of the source with known correspondences
+    and beta = 0: one MM solve recovers the map on every node to 1e-10."""
+    pair = synth.tiny_pair(500, 500, seed=9)
+    V = pair.src.astype(np.float64)
+    A = np.array([[1.05, 0.1, 0.0], [-0.08, 0.97, 0.05], [0.02, -0.03, 1.1]])
+    t = np.array([0.02, -0.01, 0.03])
+    U = V @ A.T + t
+    g = G.build_graph(V, 0.35)
+    X0 = M.identity_X(g.N)
+    terms = M.energy_terms(V, U, g, X0, 0.2, 0.2, rho=np.arange(V.shape[0]))
+    K, B, _ = S.normal_equations(V, U, g, terms, 0.2, 0.2, 1.0, 0.0)
+    X = S.solve_normal_equations(K, B).reshape(g.N, 4, 3)
+    assert np.allclose(X[:, :3, :], np.broadcast_to(A.T, (g.N, 3, 3)), atol=1e-10)
+    assert np.allclose(X[:, 3, :], t - g.p + g.p @ A.T, atol=1e-10)
+
+
+# ----------------------------------------------------------- algorithm 2 ---
+
+def test_mm_monotone_and_aa_safeguard():
+    """Kept energies never increase within a stage (Sec. 3.3, monotone MM
+    plus the AA safeguard of Sec. 3.3.4)."""
+    pair = synth.tiny_pair(600, 650, seed=10, noise=0.003, outliers=0.05)
+    reg = Registration(pair.src, pair.tgt, Params(radius=0.35, aa_m=5,
+                                                  max_iters_per_stage=15))
+    reg.solve(max_passes=60)
+    by_stage = {}
+    for r in reg.records:
+        if r.kept:
+            by_stage.setdefault(r.stage, []).append(r.E)
+    assert by_stage
+    for es in by_stage.values():
+        assert all(b <= a * (1 + 1e-12) for a, b in zip(es, es[1:]))
+
+
+def test_aa_m0_is_plain_mm():
+    pair = synth.tiny_pair(300, 320, seed=11, noise=0.002)
+    p = Params(radius=0.4, aa_m=0, max_iters_per_stage=6)
+    a = Registration(pair.src, pair.tgt, p)
+    a.solve(max_passes=6)
+    b = Registration(pair.src, pair.tgt, p)
+    for _ in range(6):
+        if b.done:
+            break
+        t = b.terms()
+        G_ = b.mm_map(t)
+        b.step()
+        assert np.array_equal(b.X, G_) or b.done
+    assert np.array_equal(a.X, b.X)
+
+
+def test_anderson_linear_contraction():
+    """On an affine contraction G(x) = M x + b of dimension d, AA with
+    m >= d reaches the fixed point after d + 1 mixes (the textbook
+    equivalence with GMRES), up to the tiny ridge."""
+    rng = _rng(12)
+    d = 4
+    Q, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    Mx = Q @ np.diag([0.9, 0.5, -0.3, 0.7]) @ Q.T
+    b = rng.standard_normal(d)
+    xstar = np.linalg.solve(np.eye(d) - Mx, b)
+    aa = anderson.Anderson(m=d)
+    x = np.zeros(d)
+    for _ in range(d + 2):
+        x = aa.mix(Mx @ x + b, x)
+    assert np.linalg.norm(x - xstar) < 1e-6 * np.linalg.norm(xstar)
+    plain = np.zeros(d)
+    for _ in range(d + 2):
+        plain = Mx @ plain + b
+    assert np.linalg.norm(plain - xstar) > 1e-2
