@@ -1,0 +1,232 @@
+/*
+ * nrr.h - C ABI of the GB300 library for robust non-rigid registration with
+ * Welsch's function, majorization-minimization (MM) and Anderson acceleration
+ * (Yao, Deng, Xu, Zhang, "Fast and Robust Non-Rigid Registration Using
+ * Accelerated Majorization-Minimization", IEEE TPAMI 2023).
+ *
+ * Problem (Sec. 3): a source point set V = {v_i} (P points) is deformed by an
+ * embedded deformation graph with N nodes p_j subset of V; node j carries an
+ * affine map X_j = [A_j, t_j]. The library minimises
+ *     E(X) = E_align + alpha E_reg + beta E_rot                 (Eq. 2)
+ * with Welsch's function psi_nu (Eq. 4) on the closest-point distances to
+ * the target set U (T points) and on the regularisation residuals D_ij
+ * (Eq. 5), by MM with a convex quadratic surrogate solved as K X = B
+ * (Eq. surr_solution), accelerated by Anderson mixing with an
+ * energy-decrease safeguard (Sec. 3.3.4, Algorithm 2).
+ *
+ * Conventions shared by every call
+ *  - Transform layout: X is [N][12] row-major doubles; X[j] is the paper's
+ *    4x3 block of node j in the stacked X in R^{4N x 3}: X[j][0..8] = A_j^T
+ *    row-major (i.e. A_j column-major), X[j][9..11] = t_j.
+ *  - Point arrays are [n][3] row-major. Input and output buffers may live in
+ *    host or device memory (the library uses unified addressing to tell them
+ *    apart); they are caller-owned and only read/written during the call.
+ *    The library copies everything it keeps.
+ *  - Point indices are the caller's: index i of the arrays passed to
+ *    nrr_create. Internally points are reordered; outputs are permuted back.
+ *  - Every call runs on the CUDA stream given to nrr_create and returns when
+ *    its outputs are ready (calls that return host data synchronise it).
+ *  - Errors: every call returns an nrr_status; no exception crosses the ABI.
+ *    nrr_last_error() gives a message for the last failure of a context.
+ *    A context is not thread-safe; use one context per host thread.
+ *  - Determinism: identical inputs and parameters give bitwise identical
+ *    outputs (all reductions have a fixed order; no floating-point atomics).
+ */
+#ifndef NRR_H
+#define NRR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nrr_ctx nrr_ctx;
+
+typedef enum {
+    NRR_OK = 0,
+    NRR_E_INVALID = 1,        /* bad argument (null pointer, size, range)   */
+    NRR_E_CUDA = 2,           /* a CUDA runtime call failed                 */
+    NRR_E_OOM = 3,            /* device or host allocation failed           */
+    NRR_E_SINGULAR = 4,       /* the surrogate system could not be solved   */
+    NRR_E_TIMEOUT = 5,        /* a bounded device-side wait ran out         */
+    NRR_E_NOT_CONVERGED = 6,  /* informational: iteration cap reached       */
+    NRR_E_STATE = 7           /* call not valid in the current state        */
+} nrr_status;
+
+typedef enum {
+    NRR_FP64 = 0,   /* every step in double precision                        */
+    NRR_MIXED = 1   /* closest points, weights, assembly and PCG in float;
+                       energy sums, safeguard test and the Anderson
+                       least-squares problem in double                      */
+} nrr_precision;
+
+/* Solver parameters. nrr_params_default() fills the paper's defaults. */
+typedef struct {
+    double graph_radius;       /* R of Eq. (InfluenceNodes); <= 0: 5 * l-bar
+                                  (Sec. 4.1), l-bar = mean distance of a
+                                  source point to its 6 nearest neighbours  */
+    int    max_influence;      /* cap on |I(v_i)|, the nearest nodes kept;
+                                  1..8, default 8                           */
+    double nu_a;               /* initial nu_a; <= 0: median closest-point
+                                  distance of the undeformed source (Sec.
+                                  3.3.3)                                    */
+    double nu_r;               /* initial nu_r; <= 0: 3 * l-bar            */
+    double nu_a_min;           /* lower bound of nu_a; <= 0: l-bar/sqrt(3) */
+    int    anneal;             /* 1: halve nu_a, nu_r per stage (Algorithm
+                                  2); 0: a single stage at the initial nu   */
+    double k_alpha, k_beta;    /* Eq. (WeightSettings); defaults 100, 1     */
+    double alpha, beta;        /* >= 0 overrides the k_* rule; default -1  */
+    int    aa_m;               /* Anderson depth m, 0..8; 0 = plain MM;
+                                  default 5                                 */
+    int    max_iters_per_stage;/* I_max of Algorithm 2 (solves per stage),
+                                  default 100                               */
+    int    max_total_passes;   /* cap on passes of nrr_solve incl. rejected
+                                  ones; default 100000                      */
+    double eps;                /* stop when max_i |v_hat_i^(k+1) - v_hat_i^(k)|
+                                  < eps; <= 0: 1e-5 x bbox diagonal of
+                                  source and target (Sec. 4.1)              */
+    double rel_energy_tol;     /* > 0: a stage also ends when consecutive
+                                  kept energies differ by less than this
+                                  relative amount; default 0 (off)          */
+    int    precision;          /* nrr_precision; default NRR_MIXED          */
+    double pcg_tol;            /* relative residual of the PCG solve of
+                                  K X = B; <= 0: 1e-12 (FP64), 1e-6 (MIXED) */
+    int    pcg_max_iters;      /* PCG iteration cap; default 500            */
+} nrr_params;
+
+/* State after a pass (one execution of the repeat body of Algorithm 2). */
+typedef struct {
+    double E, E_align, E_reg, E_rot; /* energy terms at the evaluated iterate */
+    double nu_a, nu_r, alpha, beta;  /* parameters of the stage of that pass */
+    double max_disp;                 /* stop-test quantity of the last solve */
+    double pcg_rel_residual;         /* max over the 3 columns               */
+    int    kept;                     /* 1: iterate kept; 0: rejected (AA)   */
+    int    solved;                   /* 1: the pass ran the solve and mix   */
+    int    stage;                    /* 0-based annealing stage              */
+    int    done;                     /* 1: Algorithm 2 has returned          */
+    int    pcg_iters;
+    int    aa_mk;                    /* AA differences used in the mix      */
+    int    n_passes, n_solves, n_rejected;
+    int    status;                   /* nrr_status of device-side checks    */
+} nrr_step_info;
+
+void nrr_params_default(nrr_params* params);
+
+/* Creates a registration problem: builds the deformation graph (Sec. 3.1,
+ * Algorithm 1 with Euclidean distances), the target search structure and
+ * all device buffers, and sets X = identity (Algorithm 2).
+ *   src_xyz [P][3], tgt_xyz [T][3]: float32, host or device memory.
+ *   src_nrm, tgt_nrm: [P][3]/[T][3] normals or NULL. They are checked to be
+ *     finite; the paper's point-to-point energy does not use them.
+ *   cuda_stream: cudaStream_t to run on (NULL: the library creates its own
+ *     non-blocking stream).
+ * Returns NRR_E_INVALID for P < 1, T < 1, P >= 2^25, T >= 2^30, non-finite
+ * coordinates or invalid parameters. On success *out owns all resources.
+ * The caller's buffers are only read during the call. */
+nrr_status nrr_create(nrr_ctx** out,
+                      const float* src_xyz, const float* src_nrm, int64_t P,
+                      const float* tgt_xyz, const float* tgt_nrm, int64_t T,
+                      const nrr_params* params, void* cuda_stream);
+
+void nrr_destroy(nrr_ctx* ctx);
+
+/* One pass of Algorithm 2 at the current iterate X^(k): closest points
+ * (Sec. 3.2), rotation projections, energy (Eq. 2), the safeguard test
+ * (Sec. 3.3.4); if the iterate is kept: Welsch weights, assembly of K and B
+ * (Sec. 3.3.2), the PCG solve of K X = B, and the Anderson mix (Eq.
+ * AA_solution). The stopping test and the nu annealing of Algorithm 2 run
+ * at the start of the following pass. info (host, may be NULL) receives the
+ * pass summary. Returns NRR_E_STATE if the solve has already returned. */
+nrr_status nrr_step(nrr_ctx* ctx, nrr_step_info* info);
+
+/* Runs passes until Algorithm 2 returns or max_passes (<= 0: the
+ * max_total_passes parameter) passes have run. info (host, may be NULL)
+ * receives the final state; NRR_E_NOT_CONVERGED if the cap was hit. */
+nrr_status nrr_solve(nrr_ctx* ctx, int max_passes, nrr_step_info* info);
+
+/* Enqueues n passes (as nrr_step, without the host summary) on the
+ * context's stream and returns without waiting for them. Passes after
+ * Algorithm 2 has returned do nothing. For timing with events recorded on
+ * the same stream; read the outcome afterwards with nrr_get_info. */
+nrr_status nrr_enqueue_passes(nrr_ctx* ctx, int n);
+
+/* Runs n passes like nrr_enqueue_passes, launching the four kernels of a
+ * pass individually with CUDA events recorded around each on the context's
+ * stream, and adds their durations (milliseconds, summed over the n passes)
+ * to out_ms[0..3] = {deform + closest points, energy + weights + safeguard,
+ * assembly of K and B, PCG solve + Anderson mix}. Synchronises. For
+ * measuring kernel durations; the result of the passes is the same as with
+ * nrr_enqueue_passes. */
+nrr_status nrr_time_kernels(nrr_ctx* ctx, int n, double out_ms[4]);
+
+/* Restarts Algorithm 2 from the beginning: X = identity, first stage with
+ * the initial nu_a, nu_r, empty Anderson history, counters at zero. The
+ * graph and search structures are kept. */
+nrr_status nrr_reset(nrr_ctx* ctx);
+
+/* Energy terms of Eq. (2) at X (X [N][12] doubles, host or device; NULL =
+ * the current iterate) under the current stage's nu_a, nu_r, alpha, beta.
+ * out_terms (host) = {E, E_align, E_reg, E_rot}. Does not change the
+ * solver state. */
+nrr_status nrr_energy(nrr_ctx* ctx, const double* X, double out_terms[4]);
+
+/* Gradient of E (Eq. 2) at X (NULL = current iterate) with the closest
+ * points held fixed at their values at X (rho is piecewise constant):
+ *   grad_X   [N][12] doubles (d E / d X, same layout as X), may be NULL;
+ *   grad_src [P][3]  doubles (d E / d v_i through Eq. deformed_position,
+ *            with node positions p_j held constant), may be NULL.
+ * Host or device buffers. mode must be 0 (energy gradient). */
+nrr_status nrr_backward(nrr_ctx* ctx, int mode, const double* X,
+                        double* grad_X, double* grad_src);
+
+/* Sets the current iterate X^(k) (X [N][12] doubles) and restarts the
+ * current stage (E_prev = +inf, empty Anderson history). */
+nrr_status nrr_set_transforms(nrr_ctx* ctx, const double* X);
+
+/* Sets the annealing state: nu_a, nu_r of the current stage (alpha, beta
+ * follow Eq. WeightSettings unless fixed in the parameters) and restarts
+ * the stage. */
+nrr_status nrr_set_stage(nrr_ctx* ctx, double nu_a, double nu_r);
+
+nrr_status nrr_get_transforms(nrr_ctx* ctx, double* X);       /* [N][12]  */
+nrr_status nrr_get_deformed(nrr_ctx* ctx, double* v_hat);     /* [P][3] at
+                                                                 the last
+                                                                 evaluated X */
+/* Closest points of the last evaluated iterate: rho [P] (caller target
+ * index, ties to the lowest index) and squared distances d2 [P]. */
+nrr_status nrr_get_correspondence(nrr_ctx* ctx, int32_t* rho, double* d2);
+
+/* Sizes of the problem. Any pointer may be NULL. */
+nrr_status nrr_get_sizes(nrr_ctx* ctx, int64_t* P, int64_t* T, int64_t* N,
+                         int64_t* n_edges, int32_t* max_influence);
+
+/* The deformation graph (Algorithm 1): node_src [N] source index of each
+ * node; nidx [P][max_influence] node ids of I(v_i) nearest first, -1 padded;
+ * w [P][max_influence] weights of Eq. (weight_data); edges [n_edges][2]
+ * undirected j<k sorted; r [2 n_edges] r_ij over directed pairs sorted by
+ * (i, j) (Sec. 3.2); lbar (mean 6-NN spacing, or NaN if not needed).
+ * Host buffers; any pointer may be NULL. */
+nrr_status nrr_get_graph(nrr_ctx* ctx, int32_t* node_src, int32_t* nidx,
+                         double* w, int32_t* edges, double* r, double* lbar);
+
+/* The surrogate system of the last kept pass, in node order: Kdense
+ * [4N][4N] (row-major, only the graph's blocks are non-zero) and B [4N][3].
+ * Host buffers. For tests of the assembly; N <= 4096. */
+nrr_status nrr_get_system(nrr_ctx* ctx, double* Kdense, double* B);
+
+/* The G(X^(k)) of the last solve (the MM minimiser before mixing), [N][12]. */
+nrr_status nrr_get_mm_solution(nrr_ctx* ctx, double* G);
+
+/* State of the last pass without running one (host info). */
+nrr_status nrr_get_info(nrr_ctx* ctx, nrr_step_info* info);
+
+/* Message describing the last failure on ctx (or a global message if ctx is
+ * NULL). The string lives until the next call on ctx. */
+const char* nrr_last_error(const nrr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRR_H */

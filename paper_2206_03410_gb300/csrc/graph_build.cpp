@@ -1,0 +1,291 @@
+// Host construction of the embedded deformation graph (Sec. 3.1, Algorithm 1)
+// for point clouds, with Euclidean distances in place of geodesics, plus the
+// mean point spacing l-bar and Morton ordering used by the search structures.
+//
+// Built once per problem in nrr_create (setup, not part of the per-iteration
+// path). Compiled with -ffp-contract=off so that every squared distance is
+// evaluated as dx*dx + dy*dy + dz*dz with separate roundings on every host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "nrr_internal.h"
+
+namespace {
+
+struct Grid {
+    double lo[3];
+    double h;
+    int64_t dims[3];
+    std::unordered_map<int64_t, std::pair<int, int>> cells;  // key -> [start,count)
+    std::vector<int> items;
+
+    int64_t key(int64_t x, int64_t y, int64_t z) const {
+        return (x * dims[1] + y) * dims[2] + z;
+    }
+    void cell_of(const double* p, int64_t c[3]) const {
+        for (int d = 0; d < 3; ++d) {
+            int64_t v = (int64_t)std::floor((p[d] - lo[d]) / h);
+            c[d] = std::min<int64_t>(std::max<int64_t>(v, 0), dims[d] - 1);
+        }
+    }
+    void build(const double* V, int64_t n, double cell) {
+        double hi[3];
+        for (int d = 0; d < 3; ++d) { lo[d] = INFINITY; hi[d] = -INFINITY; }
+        for (int64_t i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], V[3 * i + d]);
+                hi[d] = std::max(hi[d], V[3 * i + d]);
+            }
+        h = cell > 0 ? cell : 1.0;
+        for (int d = 0; d < 3; ++d)
+            dims[d] = std::max<int64_t>(1, (int64_t)std::floor((hi[d] - lo[d]) / h) + 1);
+        std::vector<std::pair<int64_t, int>> kv((size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t c[3];
+            cell_of(V + 3 * i, c);
+            kv[(size_t)i] = {key(c[0], c[1], c[2]), (int)i};
+        }
+        std::sort(kv.begin(), kv.end());
+        items.resize((size_t)n);
+        for (size_t i = 0; i < kv.size(); ++i) {
+            items[i] = kv[i].second;
+            auto it = cells.find(kv[i].first);
+            if (it == cells.end()) cells.emplace(kv[i].first, std::make_pair((int)i, 1));
+            else it->second.second++;
+        }
+    }
+    template <class F>
+    void visit_cell(int64_t x, int64_t y, int64_t z, F&& f) const {
+        if (x < 0 || y < 0 || z < 0 || x >= dims[0] || y >= dims[1] || z >= dims[2]) return;
+        auto it = cells.find(key(x, y, z));
+        if (it == cells.end()) return;
+        for (int s = it->second.first, e = s + it->second.second; s < e; ++s) f(items[(size_t)s]);
+    }
+};
+
+inline double sqd(const double* a, const double* b) {
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (Golub & Van
+// Loan, Sec. 8.5): returns eigenvalues in ev and eigenvectors as columns of Q.
+void jacobi_eig3(const double Ain[9], double ev[3], double Q[9]) {
+    double A[9];
+    std::memcpy(A, Ain, sizeof(A));
+    for (int i = 0; i < 9; ++i) Q[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        if (off == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                double apq = A[3 * p + q];
+                if (apq == 0.0) continue;
+                double theta = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                // A <- J^T A J with J the rotation in the (p,q) plane
+                for (int k = 0; k < 3; ++k) {
+                    double akp = A[3 * k + p], akq = A[3 * k + q];
+                    A[3 * k + p] = c * akp - s * akq;
+                    A[3 * k + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double apk = A[3 * p + k], aqk = A[3 * q + k];
+                    A[3 * p + k] = c * apk - s * aqk;
+                    A[3 * q + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double qkp = Q[3 * k + p], qkq = Q[3 * k + q];
+                    Q[3 * k + p] = c * qkp - s * qkq;
+                    Q[3 * k + q] = s * qkp + c * qkq;
+                }
+            }
+    }
+    ev[0] = A[0]; ev[1] = A[4]; ev[2] = A[8];
+}
+
+}  // namespace
+
+double nrr_mean_spacing(const double* V, int64_t P, int k) {
+    if (P < 2) return 0.0;
+    int kk = (int)std::min<int64_t>(k, P - 1);
+    // cell size from the bbox and count: about 4 points per cell on a surface
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < P; ++i)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], V[3 * i + d]);
+            hi[d] = std::max(hi[d], V[3 * i + d]);
+        }
+    double diag = std::sqrt(sqd(lo, hi));
+    double cell = diag / std::sqrt((double)P) * 1.5;
+    if (!(cell > 0)) cell = 1.0;
+    Grid g;
+    g.build(V, P, cell);
+    double total = 0.0;
+    std::vector<double> best;
+    for (int64_t i = 0; i < P; ++i) {
+        const double* q = V + 3 * i;
+        int64_t c[3];
+        g.cell_of(q, c);
+        best.assign((size_t)kk, INFINITY);   // sorted ascending
+        for (int64_t s = 0;; ++s) {
+            for (int64_t x = c[0] - s; x <= c[0] + s; ++x)
+                for (int64_t y = c[1] - s; y <= c[1] + s; ++y)
+                    for (int64_t z = c[2] - s; z <= c[2] + s; ++z) {
+                        if (std::max({std::llabs(x - c[0]), std::llabs(y - c[1]), std::llabs(z - c[2])}) != s)
+                            continue;
+                        g.visit_cell(x, y, z, [&](int j) {
+                            if (j == (int)i) return;
+                            double d2 = sqd(q, V + 3 * (int64_t)j);
+                            if (d2 < best[(size_t)kk - 1]) {
+                                size_t pos = (size_t)kk - 1;
+                                while (pos > 0 && best[pos - 1] > d2) { best[pos] = best[pos - 1]; --pos; }
+                                best[pos] = d2;
+                            }
+                        });
+                    }
+            double reach = (double)s * g.h;
+            bool out_of_grid = s > std::max({g.dims[0], g.dims[1], g.dims[2]});
+            if (best[(size_t)kk - 1] <= reach * reach || out_of_grid) break;
+        }
+        for (int t = 0; t < kk; ++t) total += std::sqrt(best[(size_t)t]);
+    }
+    return total / ((double)P * kk);
+}
+
+void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) {
+    g.radius = R;
+    g.K = K;
+    const double R2 = R * R;
+    // PCA axis of the largest covariance eigenvalue
+    double mu[3] = {0, 0, 0};
+    for (int64_t i = 0; i < P; ++i)
+        for (int d = 0; d < 3; ++d) mu[d] += V[3 * i + d];
+    for (int d = 0; d < 3; ++d) mu[d] /= (double)P;
+    double C[9] = {0};
+    for (int64_t i = 0; i < P; ++i) {
+        double c[3] = {V[3 * i] - mu[0], V[3 * i + 1] - mu[1], V[3 * i + 2] - mu[2]};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) C[3 * a + b] += c[a] * c[b];
+    }
+    for (int i = 0; i < 9; ++i) C[i] /= (double)P;
+    double ev[3], Q[9];
+    jacobi_eig3(C, ev, Q);
+    int top = 0;
+    for (int i = 1; i < 3; ++i) if (ev[i] > ev[top]) top = i;
+    double ax[3] = {Q[0 * 3 + top], Q[1 * 3 + top], Q[2 * 3 + top]};
+    int big = 0;
+    for (int i = 1; i < 3; ++i) if (std::fabs(ax[i]) > std::fabs(ax[big])) big = i;
+    if (ax[big] < 0) for (double& a : ax) a = -a;
+    std::vector<double> proj((size_t)P);
+    for (int64_t i = 0; i < P; ++i)
+        proj[(size_t)i] = V[3 * i] * ax[0] + V[3 * i + 1] * ax[1] + V[3 * i + 2] * ax[2];
+    std::vector<int> order((size_t)P);
+    for (int64_t i = 0; i < P; ++i) order[(size_t)i] = (int)i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return proj[(size_t)a] < proj[(size_t)b] || (proj[(size_t)a] == proj[(size_t)b] && a < b);
+    });
+
+    // Greedy radius sampling: a point becomes a node if it has no influencing
+    // node yet; the new node influences every point strictly within R.
+    Grid grid;
+    grid.build(V, P, R);
+    std::vector<std::vector<std::pair<double, int>>> infl((size_t)P);
+    g.nodes.clear();
+    for (int i : order) {
+        if (!g.nodes.empty() && !infl[(size_t)i].empty()) continue;
+        int j = (int)g.nodes.size();
+        g.nodes.push_back(i);
+        const double* q = V + 3 * (int64_t)i;
+        int64_t c[3];
+        grid.cell_of(q, c);
+        for (int64_t x = c[0] - 1; x <= c[0] + 1; ++x)
+            for (int64_t y = c[1] - 1; y <= c[1] + 1; ++y)
+                for (int64_t z = c[2] - 1; z <= c[2] + 1; ++z)
+                    grid.visit_cell(x, y, z, [&](int pt) {
+                        double d2 = sqd(q, V + 3 * (int64_t)pt);
+                        if (d2 < R2) infl[(size_t)pt].push_back({d2, j});
+                    });
+    }
+    // Influence sets: the K nearest nodes, weights of Eq. (weight_data)
+    g.nidx.assign((size_t)P * K, -1);
+    g.w.assign((size_t)P * K, 0.0);
+    std::vector<std::pair<int, int>> edge_list;
+    for (int64_t i = 0; i < P; ++i) {
+        auto& L = infl[(size_t)i];
+        std::sort(L.begin(), L.end());
+        int n = (int)std::min<size_t>(L.size(), (size_t)K);
+        double raw[NRR_MAX_INFL];
+        double sum = 0.0;
+        for (int s = 0; s < n; ++s) {
+            double a = 1.0 - L[(size_t)s].first / R2;
+            raw[s] = std::pow(a, 3.0);
+        }
+        for (int s = 0; s < n; ++s) sum += raw[s];
+        for (int s = 0; s < n; ++s) {
+            g.nidx[(size_t)i * K + s] = L[(size_t)s].second;
+            g.w[(size_t)i * K + s] = raw[s] / sum;
+        }
+        for (int a = 0; a < n; ++a)
+            for (int b = a + 1; b < n; ++b) {
+                int u = L[(size_t)a].second, v = L[(size_t)b].second;
+                edge_list.push_back({std::min(u, v), std::max(u, v)});
+            }
+    }
+    std::sort(edge_list.begin(), edge_list.end());
+    edge_list.erase(std::unique(edge_list.begin(), edge_list.end()), edge_list.end());
+    g.edges.clear();
+    for (auto& e : edge_list) { g.edges.push_back(e.first); g.edges.push_back(e.second); }
+    std::vector<std::pair<int, int>> dp;
+    for (auto& e : edge_list) { dp.push_back(e); dp.push_back({e.second, e.first}); }
+    std::sort(dp.begin(), dp.end());
+    g.dpair.clear();
+    for (auto& e : dp) { g.dpair.push_back(e.first); g.dpair.push_back(e.second); }
+    // r_ij of Sec. 3.2
+    size_t E2 = dp.size();
+    std::vector<double> inv(E2);
+    double inv_sum = 0.0;
+    for (size_t e = 0; e < E2; ++e) {
+        const double* a = V + 3 * (int64_t)g.nodes[(size_t)dp[e].first];
+        const double* b = V + 3 * (int64_t)g.nodes[(size_t)dp[e].second];
+        inv[e] = 1.0 / std::sqrt(sqd(a, b));
+        inv_sum += inv[e];
+    }
+    g.r.resize(E2);
+    for (size_t e = 0; e < E2; ++e) g.r[e] = 2.0 * (double)edge_list.size() * inv[e] / inv_sum;
+}
+
+static inline uint64_t spread21(uint64_t v) {
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+
+void nrr_morton_order(const float* pts, int64_t n, const double lo[3], const double hi[3],
+                      std::vector<int>& order, std::vector<uint64_t>* codes_sorted) {
+    std::vector<std::pair<uint64_t, int>> kv((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t c[3];
+        for (int d = 0; d < 3; ++d) {
+            double ext = hi[d] - lo[d];
+            double f = ext > 0 ? ((double)pts[3 * i + d] - lo[d]) / ext : 0.0;
+            f = std::min(std::max(f, 0.0), 1.0);
+            c[d] = (uint64_t)std::llround(f * 2097151.0);
+        }
+        kv[(size_t)i] = {spread21(c[0]) | (spread21(c[1]) << 1) | (spread21(c[2]) << 2), (int)i};
+    }
+    std::sort(kv.begin(), kv.end());
+    order.resize((size_t)n);
+    if (codes_sorted) codes_sorted->resize((size_t)n);
+    for (size_t i = 0; i < kv.size(); ++i) {
+        order[i] = kv[i].second;
+        if (codes_sorted) (*codes_sorted)[i] = kv[i].first;
+    }
+}

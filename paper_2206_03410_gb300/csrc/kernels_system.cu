@@ -1,0 +1,385 @@
+// Energy (Eq. objective_func), Welsch weights of the surrogate (Sec. 3.3.1),
+// rotation projections, the safeguard test of Algorithm 2, and assembly of
+// the normal equations K X = B of Eq. (surr_solution) (Sec. 3.3.2).
+#include "nrr_device.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (Golub & Van
+// Loan, Sec. 8.5). A is destroyed; eigenvectors are the columns of Q.
+__device__ void jacobi3(double A[9], double Q[9]) {
+    for (int i = 0; i < 9; ++i) Q[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        const double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        const double dia = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+        if (off <= 1e-34 * dia || off == 0.0) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0;
+            const int q = pq == 0 ? 1 : 2;
+            const double apq = A[3 * p + q];
+            if (apq == 0.0) continue;
+            const double theta = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+            for (int k = 0; k < 3; ++k) {
+                const double akp = A[3 * k + p], akq = A[3 * k + q];
+                A[3 * k + p] = c * akp - s * akq;
+                A[3 * k + q] = s * akp + c * akq;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double apk = A[3 * p + k], aqk = A[3 * q + k];
+                A[3 * p + k] = c * apk - s * aqk;
+                A[3 * q + k] = s * apk + c * aqk;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double qkp = Q[3 * k + p], qkq = Q[3 * k + q];
+                Q[3 * k + p] = c * qkp - s * qkq;
+                Q[3 * k + q] = s * qkp + c * qkq;
+            }
+        }
+    }
+}
+
+// proj_R(A): the rotation closest to A in the Frobenius norm (Sec. 3.2).
+// With A^T A = V diag(l) V^T (l descending, det V = +1) and A = U S V^T,
+// the closest rotation is U diag(1, 1, det(U V^T)) V^T = [u1, u2, u1 x u2] V^T
+// where u1 = A v1 / |A v1|, u2 = the unit part of A v2 orthogonal to u1.
+// This form needs only the two largest singular values to be non-zero.
+__device__ void closest_rotation(const double A[9], double R[9]) {
+    double M[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            M[3 * a + b] = A[0 * 3 + a] * A[0 * 3 + b] + A[1 * 3 + a] * A[1 * 3 + b] +
+                           A[2 * 3 + a] * A[2 * 3 + b];
+    double V[9];
+    jacobi3(M, V);
+    double l[3] = {M[0], M[4], M[8]};
+    int o[3] = {0, 1, 2};
+    // sort eigenpairs by descending eigenvalue (stable 3-element sort)
+    if (l[o[1]] > l[o[0]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+    if (l[o[2]] > l[o[1]]) { int t = o[1]; o[1] = o[2]; o[2] = t; }
+    if (l[o[1]] > l[o[0]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+    double v1[3], v2[3], v3[3];
+    for (int k = 0; k < 3; ++k) { v1[k] = V[3 * k + o[0]]; v2[k] = V[3 * k + o[1]]; v3[k] = V[3 * k + o[2]]; }
+    const double det = v1[0] * (v2[1] * v3[2] - v2[2] * v3[1]) - v1[1] * (v2[0] * v3[2] - v2[2] * v3[0]) +
+                       v1[2] * (v2[0] * v3[1] - v2[1] * v3[0]);
+    if (det < 0) for (int k = 0; k < 3; ++k) v3[k] = -v3[k];
+    double a1[3], a2[3];
+    for (int k = 0; k < 3; ++k) {
+        a1[k] = A[3 * k + 0] * v1[0] + A[3 * k + 1] * v1[1] + A[3 * k + 2] * v1[2];
+        a2[k] = A[3 * k + 0] * v2[0] + A[3 * k + 1] * v2[1] + A[3 * k + 2] * v2[2];
+    }
+    double n1 = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+    if (!(n1 > 0)) {
+        for (int k = 0; k < 9; ++k) R[k] = (k % 4 == 0) ? 1.0 : 0.0;
+        return;
+    }
+    double u1[3] = {a1[0] / n1, a1[1] / n1, a1[2] / n1};
+    const double pr = u1[0] * a2[0] + u1[1] * a2[1] + u1[2] * a2[2];
+    double w2[3] = {a2[0] - pr * u1[0], a2[1] - pr * u1[1], a2[2] - pr * u1[2]};
+    double n2 = sqrt(w2[0] * w2[0] + w2[1] * w2[1] + w2[2] * w2[2]);
+    if (!(n2 > 1e-300)) {
+        // rank-one A: any unit vector orthogonal to u1
+        const int k = fabs(u1[0]) < 0.9 ? 0 : 1;
+        double e[3] = {0, 0, 0};
+        e[k] = 1.0;
+        const double pe = u1[k];
+        w2[0] = e[0] - pe * u1[0]; w2[1] = e[1] - pe * u1[1]; w2[2] = e[2] - pe * u1[2];
+        n2 = sqrt(w2[0] * w2[0] + w2[1] * w2[1] + w2[2] * w2[2]);
+    }
+    double u2[3] = {w2[0] / n2, w2[1] / n2, w2[2] / n2};
+    double u3[3] = {u1[1] * u2[2] - u1[2] * u2[1], u1[2] * u2[0] - u1[0] * u2[2], u1[0] * u2[1] - u1[1] * u2[0]};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) R[3 * a + b] = u1[a] * v1[b] + u2[a] * v2[b] + u3[a] * v3[b];
+}
+
+__device__ __forceinline__ double block_sum(double x, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = x;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+    return s;   // valid in thread 0
+}
+
+template <typename T>
+__device__ __forceinline__ T t_exp(T x);
+template <>
+__device__ __forceinline__ float t_exp<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double t_exp<double>(double x) { return exp(x); }
+template <typename T>
+__device__ __forceinline__ T t_expm1(T x);
+template <>
+__device__ __forceinline__ float t_expm1<float>(float x) { return expm1f(x); }
+template <>
+__device__ __forceinline__ double t_expm1<double>(double x) { return expm1(x); }
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
+    __shared__ double sh[kThreads / 32];
+    __shared__ int s_last, s_reject;
+    NrrState* st = d.st;
+    if (MODE == NRR_MODE_PASS && st->done) return;
+    const T* X = (MODE == NRR_MODE_EVAL) ? d.Xeval : d.X;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gstride = gridDim.x * blockDim.x;
+    const double nua = st->nu_a, nur = st->nu_r;
+    const T ia = (T)(1.0 / (2.0 * nua * nua));
+    const T ir = (T)(1.0 / (2.0 * nur * nur));
+    double ea = 0.0, er = 0.0, eo = 0.0;
+    // alignment term (Eq. AlignmentTerm) and its surrogate weights w^a_i
+    for (int i = gtid; i < d.P; i += gstride) {
+        const T x = d.d2[i] * ia;
+        ea += (double)(-t_expm1<T>(-x));
+        d.wa[i] = t_exp<T>(-x) * ia;
+    }
+    // regularisation term (Eq. RegTerm) over directed pairs, weights w^r_ij
+    for (int e = gtid; e < d.E2; e += gstride) {
+        const int a = d.e_i[e], b = d.e_j[e];
+        const T r = d.e_r[e];
+        const T* Xb = X + 12 * b;
+        const T* Xa = X + 12 * a;
+        const T dx = d.p[3 * a] - d.p[3 * b];
+        const T dy = d.p[3 * a + 1] - d.p[3 * b + 1];
+        const T dz = d.p[3 * a + 2] - d.p[3 * b + 2];
+        // D_ab = r (A_b (p_a - p_b) + p_b + t_b - p_a - t_a), with p_b - p_a = -(p_a - p_b)
+        const T Dx = r * ((Xb[0] * dx + Xb[3] * dy + Xb[6] * dz - dx) + (Xb[9] - Xa[9]));
+        const T Dy = r * ((Xb[1] * dx + Xb[4] * dy + Xb[7] * dz - dy) + (Xb[10] - Xa[10]));
+        const T Dz = r * ((Xb[2] * dx + Xb[5] * dy + Xb[8] * dz - dz) + (Xb[11] - Xa[11]));
+        const T n2 = (Dx * Dx + Dy * Dy + Dz * Dz) * ir;
+        er += (double)(-t_expm1<T>(-n2));
+        d.wr[e] = t_exp<T>(-n2) * ir;
+    }
+    // rotation term: |A_n - proj_R(A_n)|_F^2
+    // nodes are spread CTA-major so that the double-precision SVDs use every SM
+    for (int n = blockIdx.x + threadIdx.x * gridDim.x; n < d.N; n += gstride) {
+        const T* Xn = X + 12 * n;
+        double A[9], R[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) A[3 * a + b] = (double)Xn[3 * b + a];
+        closest_rotation(A, R);
+        double s = 0.0;
+        for (int k = 0; k < 9; ++k) {
+            const double df = A[k] - R[k];
+            s += df * df;
+            d.Rm[9 * n + k] = (T)R[k];
+        }
+        eo += s;
+    }
+    const double sa = block_sum(ea, sh);
+    const double sr = block_sum(er, sh);
+    const double so = block_sum(eo, sh);
+    if (threadIdx.x == 0) {
+        d.partials[blockIdx.x * NRR_PARTIAL_STRIDE + 0] = sa;
+        d.partials[blockIdx.x * NRR_PARTIAL_STRIDE + 1] = sr;
+        d.partials[blockIdx.x * NRR_PARTIAL_STRIDE + 2] = so;
+        __threadfence();
+        const unsigned t = atomicAdd(&st->cnt_energy, 1u);
+        s_last = (t == gridDim.x - 1);
+        s_reject = 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    {
+        // the last CTA adds all partials: thread-strided, then a fixed-order tree
+        double pa = 0.0, pr = 0.0, po = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+            pa += __ldcg(d.partials + b * NRR_PARTIAL_STRIDE + 0);
+            pr += __ldcg(d.partials + b * NRR_PARTIAL_STRIDE + 1);
+            po += __ldcg(d.partials + b * NRR_PARTIAL_STRIDE + 2);
+        }
+        const double ta = block_sum(pa, sh);
+        const double tr = block_sum(pr, sh);
+        const double to = block_sum(po, sh);
+        if (threadIdx.x == 0) { sh[0] = ta; sh[1] = tr; sh[2] = to; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double A = sh[0], Rg = sh[1], O = sh[2];
+        st->cnt_energy = 0;
+        const double E = A + st->alpha * Rg + st->beta * O;
+        if (MODE == NRR_MODE_EVAL) {
+            st->E_eval[0] = E; st->E_eval[1] = A; st->E_eval[2] = Rg; st->E_eval[3] = O;
+        } else {
+            st->E = E; st->E_align = A; st->E_reg = Rg; st->E_rot = O;
+            st->n_passes += 1;
+            st->solved = 0;
+            if (E > st->E_prev && !st->just_reverted) {
+                // Anderson iterate rejected: revert to the last MM result
+                st->kept = 0;
+                st->skip = 1;
+                st->just_reverted = 1;
+                st->n_rejected += 1;
+                s_reject = 1;
+            } else {
+                st->kept = 1;
+                st->just_reverted = 0;
+                st->vk = st->vlast;
+                st->have_vk = 1;
+                const double Ep = st->E_prev;
+                if (st->rel_tol > 0 && isfinite(Ep) && fabs(Ep - E) < st->rel_tol * fabs(Ep)) {
+                    st->skip = 1;
+                    nrr_end_stage(st);
+                } else {
+                    st->E_prev = E;
+                    st->skip = 0;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (MODE == NRR_MODE_PASS && s_reject) {
+        const int n12 = d.N * 12;
+        for (int k = threadIdx.x; k < n12; k += blockDim.x) d.X[k] = d.Gprev[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Assembly of K = F^T W_a F + alpha H^T W_r H + beta J^T J and
+// B = F^T W_a Q + alpha H^T W_r Y + beta J^T J Z (Sec. 3.3.2).
+// A group of 8 lanes owns one 4x4 block (row node n, column node k) and sums
+// the precomputed list of its point contributions in a fixed order, then adds
+// the regularisation and rotation parts: deterministic, no atomics.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) assemble_kernel(DevProblem<T> d) {
+    NrrState* st = d.st;
+    if (st->done || st->skip) return;
+    const int lane8 = threadIdx.x & 7;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int P = d.P;
+    const T alpha = (T)st->alpha, beta = (T)st->beta;
+    // the loop is warp-uniform so that the group shuffles see all 32 lanes
+    for (int b0 = gwarp * 4; b0 < d.nblk; b0 += nwarps * 4) {
+        const int b = min(b0 + ((threadIdx.x & 31) >> 3), d.nblk - 1);
+        const bool active = (b0 + ((threadIdx.x & 31) >> 3)) < d.nblk;
+        const int n = d.blk_row[b], k = d.bsr_col[b];
+        const bool diag = (n == k);
+        const T pnx = d.p[3 * n], pny = d.p[3 * n + 1], pnz = d.p[3 * n + 2];
+        const T pkx = d.p[3 * k], pky = d.p[3 * k + 1], pkz = d.p[3 * k + 2];
+        T acc[16];
+        T accB[12];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) acc[t] = 0;
+#pragma unroll
+        for (int t = 0; t < 12; ++t) accB[t] = 0;
+        const int e_end = active ? d.ent_ptr[b + 1] : 0;
+        for (int e = d.ent_ptr[b] + lane8; e < e_end; e += 8) {
+            const int i = d.ent[e] >> 6;
+            const T wn = d.ent_w[2 * e], wk = d.ent_w[2 * e + 1];
+            const T vx = d.v[i], vy = d.v[P + i], vz = d.v[2 * P + i];
+            const T wai = d.wa[i];
+            const T an[4] = {vx - pnx, vy - pny, vz - pnz, (T)1};
+            const T ak[4] = {vx - pkx, vy - pky, vz - pkz, (T)1};
+            const T c = wai * wn * wk;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const T cr = c * an[r];
+#pragma unroll
+                for (int s = 0; s < 4; ++s) acc[4 * r + s] += cr * ak[s];
+            }
+            if (diag) {
+                // Q_i = u_rho(i) - sum_j w_ij p_j
+                const T Qx = d.u[i] - d.pbar[i];
+                const T Qy = d.u[P + i] - d.pbar[P + i];
+                const T Qz = d.u[2 * P + i] - d.pbar[2 * P + i];
+                const T cb = wai * wn;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const T cr = cb * an[r];
+                    accB[3 * r + 0] += cr * Qx;
+                    accB[3 * r + 1] += cr * Qy;
+                    accB[3 * r + 2] += cr * Qz;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+#pragma unroll
+            for (int t = 0; t < 12; ++t) accB[t] += __shfl_xor_sync(0xffffffffu, accB[t], o);
+        }
+        if (lane8 != 0 || !active) continue;
+        if (diag) {
+            // edges (n, j): H row has [0,0,0,-r] at X_n -> r^2 on entry (3,3);
+            // B row 3 gets -r * y with y = r (p_n - p_j)
+            for (int e = d.adj_ptr[n]; e < d.adj_ptr[n + 1]; ++e) {
+                const int j = d.e_j[e];
+                const T r = d.e_r[e], w = alpha * d.wr[e];
+                acc[15] += w * r * r;
+                accB[9] -= w * r * r * (pnx - d.p[3 * j]);
+                accB[10] -= w * r * r * (pny - d.p[3 * j + 1]);
+                accB[11] -= w * r * r * (pnz - d.p[3 * j + 2]);
+                // reverse pair (j, n): h = r'[(p_j - p_n)^T, 1] at X_n
+                const int er = d.e_rev[e];
+                const T r2 = d.e_r[er], w2 = alpha * d.wr[er];
+                const T h[4] = {r2 * (d.p[3 * j] - pnx), r2 * (d.p[3 * j + 1] - pny),
+                                r2 * (d.p[3 * j + 2] - pnz), r2};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[4 * a + c] += w2 * h[a] * h[c];
+                    accB[3 * a + 0] += w2 * h[a] * h[0];
+                    accB[3 * a + 1] += w2 * h[a] * h[1];
+                    accB[3 * a + 2] += w2 * h[a] * h[2];
+                }
+            }
+            // rotation term: beta on A-rows, B rows 0..2 += beta R_n^T
+            acc[0] += beta; acc[5] += beta; acc[10] += beta;
+            const T* R = d.Rm + 9 * n;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) accB[3 * a + c] += beta * R[3 * c + a];
+#pragma unroll
+            for (int t = 0; t < 12; ++t) d.Bv[12 * n + t] = accB[t];
+        } else {
+            // pair (n, k): block (n, k) gets -r w h_k^T on row 3,
+            // h_k = r [(p_n - p_k)^T, 1]
+            const int e = d.bsr_edge[b];
+            const T r = d.e_r[e], w = alpha * d.wr[e];
+            const T hk[4] = {r * (pnx - pkx), r * (pny - pky), r * (pnz - pkz), r};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[12 + c] -= w * r * hk[c];
+            // pair (k, n): block (n, k) gets -r' w' h_n on column 3,
+            // h_n = r' [(p_k - p_n)^T, 1]
+            const int er = d.e_rev[e];
+            const T r2 = d.e_r[er], w2 = alpha * d.wr[er];
+            const T hn[4] = {r2 * (pkx - pnx), r2 * (pky - pny), r2 * (pkz - pnz), r2};
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[4 * a + 3] -= w2 * r2 * hn[a];
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) d.Kv[16 * b + t] = acc[t];
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t nrr_launch_energy(const DevProblem<T>& d, int mode, int grid, cudaStream_t s) {
+    if (mode == NRR_MODE_EVAL) energy_kernel<T, NRR_MODE_EVAL><<<grid, kThreads, 0, s>>>(d);
+    else energy_kernel<T, NRR_MODE_PASS><<<grid, kThreads, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t nrr_launch_assemble(const DevProblem<T>& d, int grid, cudaStream_t s) {
+    assemble_kernel<T><<<grid, kThreads, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+template cudaError_t nrr_launch_energy<float>(const DevProblem<float>&, int, int, cudaStream_t);
+template cudaError_t nrr_launch_energy<double>(const DevProblem<double>&, int, int, cudaStream_t);
+template cudaError_t nrr_launch_assemble<float>(const DevProblem<float>&, int, cudaStream_t);
+template cudaError_t nrr_launch_assemble<double>(const DevProblem<double>&, int, cudaStream_t);

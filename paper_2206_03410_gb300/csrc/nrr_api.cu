@@ -1,0 +1,918 @@
+// C ABI of the registration library (include/nrr.h): context creation,
+// per-pass launch sequence captured in a CUDA graph, and accessors.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "nrr_device.cuh"
+
+int nrr_solve_threads();
+template <typename T>
+int nrr_solve_max_blocks_per_sm();
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <typename T>
+struct Buffers {
+    DevProblem<T> d{};
+};
+
+}  // namespace
+
+struct nrr_ctx {
+    nrr_params prm{};
+    bool fp64 = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int64_t P = 0, T = 0;
+    int N = 0, E2 = 0, nblk = 0, n_leaves = 0, n_supers = 0;
+    HostGraph hg;
+    std::vector<int> src_order;   // internal -> caller
+    std::vector<int> src_rank;    // caller -> internal
+    std::vector<int> bsr_ptr, bsr_col;
+    std::vector<void*> allocs;
+    NrrState* d_state = nullptr;
+    NrrState* h_state = nullptr;
+    DevProblem<float> df{};
+    DevProblem<double> dd{};
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
+    bool coop = true;
+    int grid_energy = 0, grid_asm = 0, grid_solve = 0, num_sms = 0;
+    double diag = 0.0;
+    double nu_a0 = 0.0, nu_r0 = 0.0;   // first-stage parameters
+    bool failed = false;
+    std::string err;
+};
+
+namespace {
+
+nrr_status fail(nrr_ctx* c, nrr_status code, const std::string& msg) {
+    if (c) c->err = msg;
+    g_last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? NRR_E_OOM : NRR_E_CUDA,    \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(nrr_ctx* c, P** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(P));
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(q);
+    *p = (P*)q;
+    return cudaMemsetAsync(q, 0, count * sizeof(P), c->stream);
+}
+
+template <typename P>
+cudaError_t upload(nrr_ctx* c, P** p, const std::vector<P>& h) {
+    cudaError_t e = dalloc(c, p, h.size());
+    if (e != cudaSuccess || h.empty()) return e;
+    return cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(P), cudaMemcpyHostToDevice, c->stream);
+}
+
+bool finite3(const std::vector<float>& v) {
+    for (float x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+// Copies n floats from a host or device pointer to a host vector.
+cudaError_t fetch_floats(const float* src, size_t n, std::vector<float>& out, cudaStream_t s) {
+    out.resize(n);
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(out.data(), src, n * sizeof(float), cudaMemcpyDefault, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+void host_stage_weights(NrrState& st) {
+    st.alpha = st.alpha_fixed >= 0 ? st.alpha_fixed
+                                   : st.k_alpha * st.n_src / st.n_edges * (st.nu_r * st.nu_r) /
+                                         (st.nu_a * st.nu_a);
+    st.beta = st.beta_fixed >= 0 ? st.beta_fixed
+                                 : st.k_beta * st.n_src / st.n_nodes / (2.0 * st.nu_a * st.nu_a);
+}
+
+void host_restart_stage(NrrState& st) {
+    st.E_prev = std::numeric_limits<double>::infinity();
+    st.n_solves_stage = 0;
+    st.aa_count = 0;
+    st.aa_head = 0;
+    st.just_reverted = 0;
+    st.pending_stop = 0;
+    st.have_vk = 0;
+    st.skip = 0;
+    st.done = 0;
+}
+
+template <typename T>
+DevProblem<T>& prob(nrr_ctx* c);
+template <>
+DevProblem<float>& prob<float>(nrr_ctx* c) { return c->df; }
+template <>
+DevProblem<double>& prob<double>(nrr_ctx* c) { return c->dd; }
+
+nrr_status pull_state(nrr_ctx* c) {
+    CK(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(NrrState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRR_OK;
+}
+
+nrr_status push_state(nrr_ctx* c) {
+    CK(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(NrrState), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRR_OK;
+}
+
+template <typename T>
+cudaError_t launch_pass(nrr_ctx* c) {
+    DevProblem<T>& d = prob<T>(c);
+    cudaError_t e = nrr_launch_nn<T>(d, NRR_MODE_PASS, 0, c->stream);
+    if (e != cudaSuccess) return e;
+    e = nrr_launch_energy<T>(d, NRR_MODE_PASS, c->grid_energy, c->stream);
+    if (e != cudaSuccess) return e;
+    e = nrr_launch_assemble<T>(d, c->grid_asm, c->stream);
+    if (e != cudaSuccess) return e;
+    return nrr_launch_solve<T>(d, c->grid_solve, c->stream, c->coop);
+}
+
+cudaError_t launch_pass_any(nrr_ctx* c) { return c->fp64 ? launch_pass<double>(c) : launch_pass<float>(c); }
+
+nrr_status capture_graph(nrr_ctx* c) {
+    c->use_graph = false;
+    if (std::getenv("NRR_NO_GRAPH")) return NRR_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return NRR_OK;
+    }
+    cudaError_t le = launch_pass_any(c);
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (le != cudaSuccess || ee != cudaSuccess || g == nullptr) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return NRR_OK;   // direct launches instead
+    }
+    cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        c->gexec = nullptr;
+        return NRR_OK;
+    }
+    c->use_graph = true;
+    return NRR_OK;
+}
+
+nrr_status run_pass(nrr_ctx* c) {
+    if (c->use_graph) CK(cudaGraphLaunch(c->gexec, c->stream));
+    else CK(launch_pass_any(c));
+    return NRR_OK;
+}
+
+void fill_info(const NrrState& s, nrr_step_info* info) {
+    if (!info) return;
+    info->E = s.E; info->E_align = s.E_align; info->E_reg = s.E_reg; info->E_rot = s.E_rot;
+    info->nu_a = s.nu_a; info->nu_r = s.nu_r; info->alpha = s.alpha; info->beta = s.beta;
+    info->max_disp = s.max_disp;
+    info->pcg_rel_residual = s.pcg_res;
+    info->kept = s.kept; info->solved = s.solved; info->stage = s.stage; info->done = s.done;
+    info->pcg_iters = s.pcg_iters; info->aa_mk = s.aa_mk;
+    info->n_passes = s.n_passes; info->n_solves = s.n_solves; info->n_rejected = s.n_rejected;
+    info->status = s.status;
+}
+
+// ---------------------------------------------------------------------------
+// Creation
+// ---------------------------------------------------------------------------
+template <typename T>
+nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::vector<float>& tgt) {
+    DevProblem<T>& d = prob<T>(c);
+    const int64_t P = c->P, Tn = c->T;
+    const HostGraph& g = c->hg;
+    const int K = g.K, N = c->N;
+    // bbox of source and target together for the Morton codes
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < P; ++i)
+        for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], (double)src[3 * i + a]); hi[a] = std::max(hi[a], (double)src[3 * i + a]); }
+    for (int64_t i = 0; i < Tn; ++i)
+        for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], (double)tgt[3 * i + a]); hi[a] = std::max(hi[a], (double)tgt[3 * i + a]); }
+    {
+        double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        c->diag = std::sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    std::vector<uint64_t> src_codes, tgt_codes;
+    nrr_morton_order(src.data(), P, lo, hi, c->src_order, &src_codes);
+    std::vector<int> tgt_order;
+    nrr_morton_order(tgt.data(), Tn, lo, hi, tgt_order, &tgt_codes);
+    c->src_rank.assign((size_t)P, 0);
+    for (int64_t ii = 0; ii < P; ++ii) c->src_rank[(size_t)c->src_order[(size_t)ii]] = (int)ii;
+
+    // source SoA and influence CSR in internal order
+    std::vector<T> v((size_t)(3 * P));
+    std::vector<int> infl_ptr((size_t)P + 1, 0), infl_node;
+    std::vector<T> infl_w;
+    for (int64_t ii = 0; ii < P; ++ii) {
+        const int i = c->src_order[(size_t)ii];
+        for (int a = 0; a < 3; ++a) v[(size_t)(a * P + ii)] = (T)src[3 * (size_t)i + a];
+        for (int s = 0; s < K; ++s) {
+            const int j = g.nidx[(size_t)i * K + s];
+            if (j < 0) break;
+            infl_node.push_back(j);
+            infl_w.push_back((T)g.w[(size_t)i * K + s]);
+        }
+        infl_ptr[(size_t)ii + 1] = (int)infl_node.size();
+    }
+    std::vector<T> p((size_t)N * 3);
+    for (int j = 0; j < N; ++j)
+        for (int a = 0; a < 3; ++a) p[(size_t)3 * j + a] = (T)src[3 * (size_t)g.nodes[(size_t)j] + a];
+    // directed pairs (sorted by (i, j)), adjacency and reverse index
+    const int E2 = c->E2;
+    std::vector<int> e_i((size_t)E2), e_j((size_t)E2), adj_ptr((size_t)N + 1, 0), e_rev((size_t)E2);
+    std::vector<T> e_r((size_t)E2);
+    for (int e = 0; e < E2; ++e) {
+        e_i[(size_t)e] = g.dpair[2 * (size_t)e];
+        e_j[(size_t)e] = g.dpair[2 * (size_t)e + 1];
+        e_r[(size_t)e] = (T)g.r[(size_t)e];
+        adj_ptr[(size_t)e_i[(size_t)e] + 1]++;
+    }
+    for (int n = 0; n < N; ++n) adj_ptr[(size_t)n + 1] += adj_ptr[(size_t)n];
+    for (int e = 0; e < E2; ++e) {
+        const int a = e_i[(size_t)e], b = e_j[(size_t)e];
+        auto first = e_j.begin() + adj_ptr[(size_t)b], last = e_j.begin() + adj_ptr[(size_t)b + 1];
+        auto it = std::lower_bound(first, last, a);
+        e_rev[(size_t)e] = (int)(it - e_j.begin());
+    }
+    // BSR pattern: the diagonal plus the neighbours of each node
+    std::vector<int>& bp = c->bsr_ptr;
+    std::vector<int>& bc = c->bsr_col;
+    std::vector<int> be;
+    bp.assign((size_t)N + 1, 0);
+    bc.clear();
+    for (int n = 0; n < N; ++n) {
+        bool put_diag = false;
+        for (int e = adj_ptr[(size_t)n]; e < adj_ptr[(size_t)n + 1]; ++e) {
+            if (!put_diag && e_j[(size_t)e] > n) { bc.push_back(n); be.push_back(-1); put_diag = true; }
+            bc.push_back(e_j[(size_t)e]);
+            be.push_back(e);
+        }
+        if (!put_diag) { bc.push_back(n); be.push_back(-1); }
+        bp[(size_t)n + 1] = (int)bc.size();
+    }
+    c->nblk = (int)bc.size();
+    auto block_of = [&](int a, int b) {
+        auto first = bc.begin() + bp[(size_t)a], last = bc.begin() + bp[(size_t)a + 1];
+        return (int)(std::lower_bound(first, last, b) - bc.begin());
+    };
+    // per-block contribution lists (point, slot_row, slot_col), by point
+    std::vector<int> ent_cnt((size_t)c->nblk + 1, 0);
+    for (int64_t ii = 0; ii < P; ++ii)
+        for (int sa = infl_ptr[(size_t)ii]; sa < infl_ptr[(size_t)ii + 1]; ++sa)
+            for (int sb = infl_ptr[(size_t)ii]; sb < infl_ptr[(size_t)ii + 1]; ++sb)
+                ent_cnt[(size_t)block_of(infl_node[(size_t)sa], infl_node[(size_t)sb]) + 1]++;
+    for (int b = 0; b < c->nblk; ++b) ent_cnt[(size_t)b + 1] += ent_cnt[(size_t)b];
+    std::vector<int> ent((size_t)ent_cnt[(size_t)c->nblk]);
+    std::vector<int> fillp(ent_cnt.begin(), ent_cnt.end() - 1);
+    for (int64_t ii = 0; ii < P; ++ii) {
+        const int b0 = infl_ptr[(size_t)ii];
+        for (int sa = b0; sa < infl_ptr[(size_t)ii + 1]; ++sa)
+            for (int sb = b0; sb < infl_ptr[(size_t)ii + 1]; ++sb) {
+                const int blk = block_of(infl_node[(size_t)sa], infl_node[(size_t)sb]);
+                ent[(size_t)fillp[(size_t)blk]++] = (int)((ii << 6) | ((sa - b0) << 3) | (sb - b0));
+            }
+    }
+    std::vector<T> ent_w(ent.size() * 2);
+    for (size_t e = 0; e < ent.size(); ++e) {
+        const int ii = ent[e] >> 6, sa = (ent[e] >> 3) & 7, sb = ent[e] & 7;
+        ent_w[2 * e] = infl_w[(size_t)infl_ptr[(size_t)ii] + sa];
+        ent_w[2 * e + 1] = infl_w[(size_t)infl_ptr[(size_t)ii] + sb];
+    }
+    std::vector<int> blk_row((size_t)c->nblk);
+    for (int n = 0; n < N; ++n)
+        for (int b = bp[(size_t)n]; b < bp[(size_t)n + 1]; ++b) blk_row[(size_t)b] = n;
+    std::vector<T> pbar((size_t)(3 * P), (T)0);
+    for (int64_t ii = 0; ii < P; ++ii) {
+        double acc[3] = {0, 0, 0};
+        for (int s = infl_ptr[(size_t)ii]; s < infl_ptr[(size_t)ii + 1]; ++s) {
+            const int j = infl_node[(size_t)s];
+            for (int a = 0; a < 3; ++a)
+                acc[a] += (double)infl_w[(size_t)s] * (double)src[3 * (size_t)g.nodes[(size_t)j] + a];
+        }
+        for (int a = 0; a < 3; ++a) pbar[(size_t)(a * P + ii)] = (T)acc[a];
+    }
+    // target leaves (32 Morton-consecutive points) and super tiles
+    const int nl = (int)((Tn + NRR_LEAF - 1) / NRR_LEAF);
+    const int ns = (nl + 31) / 32;
+    c->n_leaves = nl;
+    c->n_supers = ns;
+    std::vector<TPoint<T>> tp((size_t)nl * NRR_LEAF);
+    std::vector<float> lbox((size_t)nl * 6), sbox((size_t)ns * 6);
+    for (size_t k = 0; k < tp.size(); ++k) {
+        if ((int64_t)k < Tn) {
+            const int t = tgt_order[k];
+            tp[k].x = (T)tgt[3 * (size_t)t]; tp[k].y = (T)tgt[3 * (size_t)t + 1]; tp[k].z = (T)tgt[3 * (size_t)t + 2];
+            tp[k].idx = t;
+        } else {
+            tp[k].x = tp[k].y = tp[k].z = std::numeric_limits<T>::infinity();
+            tp[k].idx = 0x7fffffff;
+        }
+    }
+    for (int L = 0; L < nl; ++L) {
+        float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int k = L * NRR_LEAF; k < std::min<int64_t>(Tn, (int64_t)(L + 1) * NRR_LEAF); ++k) {
+            const int t = tgt_order[(size_t)k];
+            for (int a = 0; a < 3; ++a) {
+                b[a] = std::min(b[a], tgt[3 * (size_t)t + a]);
+                b[3 + a] = std::max(b[3 + a], tgt[3 * (size_t)t + a]);
+            }
+        }
+        std::memcpy(&lbox[(size_t)L * 6], b, sizeof(b));
+    }
+    for (int S = 0; S < ns; ++S) {
+        float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int L = S * 32; L < std::min(nl, (S + 1) * 32); ++L)
+            for (int a = 0; a < 3; ++a) {
+                b[a] = std::min(b[a], lbox[(size_t)L * 6 + a]);
+                b[3 + a] = std::max(b[3 + a], lbox[(size_t)L * 6 + 3 + a]);
+            }
+        std::memcpy(&sbox[(size_t)S * 6], b, sizeof(b));
+    }
+    // initial correspondence guess: target point nearest in Morton order
+    std::vector<T> u0((size_t)(3 * P));
+    std::vector<int> rho0((size_t)P);
+    for (int64_t ii = 0; ii < P; ++ii) {
+        size_t pos = (size_t)(std::lower_bound(tgt_codes.begin(), tgt_codes.end(), src_codes[(size_t)ii]) - tgt_codes.begin());
+        if (pos >= (size_t)Tn) pos = (size_t)Tn - 1;
+        for (int a = 0; a < 3; ++a) u0[(size_t)(a * P + ii)] = a == 0 ? tp[pos].x : (a == 1 ? tp[pos].y : tp[pos].z);
+        rho0[(size_t)ii] = tp[pos].idx;
+    }
+    // identity transforms
+    std::vector<T> X0((size_t)N * 12, (T)0);
+    for (int j = 0; j < N; ++j) { X0[(size_t)12 * j + 0] = 1; X0[(size_t)12 * j + 4] = 1; X0[(size_t)12 * j + 8] = 1; }
+
+    d.P = (int)P; d.N = N; d.E2 = E2; d.n_leaves = nl; d.n_supers = ns; d.nblk = c->nblk;
+    d.aa_m = c->prm.aa_m;
+    d.pcg_max = c->prm.pcg_max_iters;
+    d.pcg_tol = (T)c->prm.pcg_tol;
+    T *pv_, *pw_, *pp_, *er_;
+    int *ip_, *in_, *ei_, *ej_, *ap_, *rv_, *bp_, *bc_, *be_, *ep_, *en_, *rho_;
+    TPoint<T>* tp_;
+    float *lb_, *sb_;
+    CK(upload(c, &pv_, v)); d.v = pv_;
+    CK(upload(c, &ip_, infl_ptr)); d.infl_ptr = ip_;
+    CK(upload(c, &in_, infl_node)); d.infl_node = in_;
+    CK(upload(c, &pw_, infl_w)); d.infl_w = pw_;
+    CK(upload(c, &pp_, p)); d.p = pp_;
+    CK(upload(c, &tp_, tp)); d.tpts = tp_;
+    CK(upload(c, &lb_, lbox)); d.leaf_box = lb_;
+    CK(upload(c, &sb_, sbox)); d.super_box = sb_;
+    CK(upload(c, &ei_, e_i)); d.e_i = ei_;
+    CK(upload(c, &ej_, e_j)); d.e_j = ej_;
+    CK(upload(c, &er_, e_r)); d.e_r = er_;
+    CK(upload(c, &ap_, adj_ptr)); d.adj_ptr = ap_;
+    CK(upload(c, &rv_, e_rev)); d.e_rev = rv_;
+    CK(upload(c, &bp_, bp)); d.bsr_ptr = bp_;
+    CK(upload(c, &bc_, bc)); d.bsr_col = bc_;
+    CK(upload(c, &be_, be)); d.bsr_edge = be_;
+    CK(upload(c, &ep_, ent_cnt)); d.ent_ptr = ep_;
+    CK(upload(c, &en_, ent)); d.ent = en_;
+    {
+        T *ew_, *pb_;
+        int* br_;
+        CK(upload(c, &ew_, ent_w)); d.ent_w = ew_;
+        CK(upload(c, &pb_, pbar)); d.pbar = pb_;
+        CK(upload(c, &br_, blk_row)); d.blk_row = br_;
+    }
+    CK(upload(c, &d.X, X0));
+    CK(dalloc(c, &d.Xeval, (size_t)N * 12));
+    CK(dalloc(c, &d.G, (size_t)N * 12));
+    CK(upload(c, &d.Gprev, X0));
+    CK(dalloc(c, &d.Fprev, (size_t)N * 12));
+    const int mm = std::max(1, c->prm.aa_m);
+    CK(dalloc(c, &d.dF, (size_t)mm * N * 12));
+    CK(dalloc(c, &d.dG, (size_t)mm * N * 12));
+    CK(dalloc(c, &d.vhat, (size_t)6 * P));
+    CK(upload(c, &d.u, u0));
+    CK(upload(c, &rho_, rho0)); d.rho = rho_;
+    CK(dalloc(c, &d.d2, (size_t)P));
+    CK(dalloc(c, &d.wa, (size_t)P));
+    CK(dalloc(c, &d.wr, (size_t)E2));
+    CK(dalloc(c, &d.Rm, (size_t)N * 9));
+    CK(dalloc(c, &d.Kv, (size_t)c->nblk * 16));
+    CK(dalloc(c, &d.Bv, (size_t)N * 12));
+    CK(dalloc(c, &d.r, (size_t)N * 12));
+    CK(dalloc(c, &d.z, (size_t)N * 12));
+    CK(dalloc(c, &d.pv, (size_t)N * 12));
+    CK(dalloc(c, &d.q, (size_t)N * 12));
+    CK(dalloc(c, &d.Minv, (size_t)N * 16));
+    const int max_ctas = std::max({c->grid_energy, c->grid_solve, 1});
+    CK(dalloc(c, &d.partials, (size_t)2 * max_ctas * NRR_PARTIAL_STRIDE));
+    d.st = c->d_state;
+    return NRR_OK;
+}
+
+template <typename T>
+nrr_status median_distance(nrr_ctx* c, double* out) {
+    DevProblem<T>& d = prob<T>(c);
+    CK(nrr_launch_nn<T>(d, NRR_MODE_RAW, 0, c->stream));
+    std::vector<T> d2((size_t)c->P);
+    CK(cudaMemcpyAsync(d2.data(), d.d2, sizeof(T) * (size_t)c->P, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<double> dist((size_t)c->P);
+    for (size_t i = 0; i < dist.size(); ++i) dist[i] = std::sqrt((double)d2[i]);
+    std::sort(dist.begin(), dist.end());
+    const size_t n = dist.size();
+    *out = (n % 2) ? dist[n / 2] : (dist[n / 2 - 1] + dist[n / 2]) / 2.0;
+    return NRR_OK;
+}
+
+template <typename T>
+nrr_status read_X(nrr_ctx* c, const T* src, double* X) {
+    std::vector<T> h((size_t)c->N * 12);
+    CK(cudaMemcpyAsync(h.data(), src, sizeof(T) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<double> o(h.begin(), h.end());
+    CK(cudaMemcpy(X, o.data(), sizeof(double) * o.size(), cudaMemcpyDefault));
+    return NRR_OK;
+}
+
+template <typename T>
+nrr_status write_X(nrr_ctx* c, T* dst, const double* X) {
+    std::vector<double> h((size_t)c->N * 12);
+    CK(cudaMemcpy(h.data(), X, sizeof(double) * h.size(), cudaMemcpyDefault));
+    for (double x : h)
+        if (!std::isfinite(x)) return fail(c, NRR_E_INVALID, "X has non-finite entries");
+    std::vector<T> t(h.begin(), h.end());
+    CK(cudaMemcpyAsync(dst, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void nrr_params_default(nrr_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->graph_radius = 0.0;
+    p->max_influence = 8;
+    p->nu_a = 0.0;
+    p->nu_r = 0.0;
+    p->nu_a_min = 0.0;
+    p->anneal = 1;
+    p->k_alpha = 100.0;
+    p->k_beta = 1.0;
+    p->alpha = -1.0;
+    p->beta = -1.0;
+    p->aa_m = 5;
+    p->max_iters_per_stage = 100;
+    p->max_total_passes = 100000;
+    p->eps = 0.0;
+    p->rel_energy_tol = 0.0;
+    p->precision = NRR_MIXED;
+    p->pcg_tol = 0.0;
+    p->pcg_max_iters = 500;
+}
+
+const char* nrr_last_error(const nrr_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+void nrr_destroy(nrr_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->d_state) cudaFree(c->d_state);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm, int64_t P,
+                      const float* tgt_xyz, const float* tgt_nrm, int64_t T,
+                      const nrr_params* params, void* cuda_stream) {
+    nrr_ctx* c = nullptr;
+    if (!out) return fail(nullptr, NRR_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!src_xyz || !tgt_xyz) return fail(nullptr, NRR_E_INVALID, "point arrays must not be NULL");
+    if (P < 1 || T < 1) return fail(nullptr, NRR_E_INVALID, "P and T must be >= 1");
+    if (P >= (1LL << 25) || T >= (1LL << 30)) return fail(nullptr, NRR_E_INVALID, "P must be < 2^25 and T < 2^30");
+    nrr_params prm;
+    if (params) prm = *params; else nrr_params_default(&prm);
+    if (prm.max_influence < 1 || prm.max_influence > NRR_MAX_INFL)
+        return fail(nullptr, NRR_E_INVALID, "max_influence must be in 1..8");
+    if (prm.aa_m < 0 || prm.aa_m > NRR_AA_MMAX) return fail(nullptr, NRR_E_INVALID, "aa_m must be in 0..8");
+    if (prm.precision != NRR_FP64 && prm.precision != NRR_MIXED)
+        return fail(nullptr, NRR_E_INVALID, "precision must be NRR_FP64 or NRR_MIXED");
+    if (prm.max_iters_per_stage < 1 || prm.pcg_max_iters < 1 || prm.max_total_passes < 1)
+        return fail(nullptr, NRR_E_INVALID, "iteration caps must be >= 1");
+    if (!(std::isfinite(prm.graph_radius) && std::isfinite(prm.nu_a) && std::isfinite(prm.nu_r) &&
+          std::isfinite(prm.nu_a_min) && std::isfinite(prm.eps) && std::isfinite(prm.k_alpha) &&
+          std::isfinite(prm.k_beta) && std::isfinite(prm.alpha) && std::isfinite(prm.beta)))
+        return fail(nullptr, NRR_E_INVALID, "parameters must be finite");
+    if (prm.pcg_tol <= 0) prm.pcg_tol = prm.precision == NRR_FP64 ? 1e-12 : 1e-6;
+
+    c = new (std::nothrow) nrr_ctx();
+    if (!c) return fail(nullptr, NRR_E_OOM, "host allocation failed");
+    std::unique_ptr<nrr_ctx, void (*)(nrr_ctx*)> guard(c, nrr_destroy);
+    c->prm = prm;
+    c->fp64 = prm.precision == NRR_FP64;
+    c->P = P;
+    c->T = T;
+    CK(cudaGetDevice(&c->device));
+    CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    std::vector<float> src, tgt, tmp;
+    CK(fetch_floats(src_xyz, (size_t)P * 3, src, c->stream));
+    CK(fetch_floats(tgt_xyz, (size_t)T * 3, tgt, c->stream));
+    if (!finite3(src) || !finite3(tgt)) return fail(nullptr, NRR_E_INVALID, "non-finite point coordinates");
+    if (src_nrm) {
+        CK(fetch_floats(src_nrm, (size_t)P * 3, tmp, c->stream));
+        if (!finite3(tmp)) return fail(nullptr, NRR_E_INVALID, "non-finite source normals");
+    }
+    if (tgt_nrm) {
+        CK(fetch_floats(tgt_nrm, (size_t)T * 3, tmp, c->stream));
+        if (!finite3(tmp)) return fail(nullptr, NRR_E_INVALID, "non-finite target normals");
+    }
+    // l-bar, radius and the deformation graph (Algorithm 1)
+    std::vector<double> V(src.begin(), src.end());
+    const bool need_lbar = prm.graph_radius <= 0 || prm.nu_r <= 0 || prm.nu_a_min <= 0;
+    c->hg.lbar = need_lbar ? nrr_mean_spacing(V.data(), P, 6) : std::nan("");
+    const double R = prm.graph_radius > 0 ? prm.graph_radius : 5.0 * c->hg.lbar;
+    if (!(R > 0)) return fail(nullptr, NRR_E_INVALID, "graph radius must be positive");
+    nrr_build_graph(V.data(), P, R, prm.max_influence, c->hg);
+    c->N = (int)c->hg.nodes.size();
+    c->E2 = (int)c->hg.r.size();
+    // launch geometry
+    c->grid_energy = 2 * c->num_sms;
+    c->grid_asm = std::max(1, std::min(8 * c->num_sms, (c->N + c->E2 + 31) / 32));
+    {
+        const int per_cta = nrr_solve_threads() / 3;   // (node, column) pairs per thread
+        int want = std::max(1, (c->N + per_cta - 1) / per_cta);
+        const int occ = c->fp64 ? nrr_solve_max_blocks_per_sm<double>() : nrr_solve_max_blocks_per_sm<float>();
+        c->grid_solve = std::max(1, std::min(want, c->num_sms * std::max(1, occ)));
+        c->grid_solve = std::min(c->grid_solve, c->num_sms);
+    }
+    // device state
+    CK(cudaMalloc(&c->d_state, sizeof(NrrState)));
+    CK(cudaMallocHost(&c->h_state, sizeof(NrrState)));
+    std::memset(c->h_state, 0, sizeof(NrrState));
+    nrr_status st = c->fp64 ? build_device<double>(c, src, tgt) : build_device<float>(c, src, tgt);
+    if (st != NRR_OK) return st;
+    NrrState& s = *c->h_state;
+    s.k_alpha = prm.k_alpha; s.k_beta = prm.k_beta;
+    s.alpha_fixed = prm.alpha; s.beta_fixed = prm.beta;
+    s.n_src = (double)P; s.n_edges = std::max(1.0, (double)c->hg.edges.size() / 2.0); s.n_nodes = std::max(1, c->N);
+    s.eps = prm.eps > 0 ? prm.eps : 1e-5 * c->diag;
+    s.rel_tol = prm.rel_energy_tol;
+    s.max_iters_stage = prm.max_iters_per_stage;
+    s.aa_m = prm.aa_m;
+    s.nu_a = 1.0; s.nu_r = 1.0;
+    CK(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(NrrState), cudaMemcpyHostToDevice, c->stream));
+    double nu_a0 = prm.nu_a;
+    if (nu_a0 <= 0) {
+        st = c->fp64 ? median_distance<double>(c, &nu_a0) : median_distance<float>(c, &nu_a0);
+        if (st != NRR_OK) return st;
+    }
+    double nu_min = prm.nu_a_min > 0 ? prm.nu_a_min : c->hg.lbar / std::sqrt(3.0);
+    if (!prm.anneal) nu_min = nu_a0;
+    s.nu_a_min = nu_min;
+    s.nu_a = std::max(nu_a0, nu_min);
+    s.nu_r = prm.nu_r > 0 ? prm.nu_r : 3.0 * c->hg.lbar;
+    if (!(s.nu_a > 0) || !(s.nu_r > 0)) return fail(nullptr, NRR_E_INVALID, "nu_a and nu_r must be positive");
+    host_stage_weights(s);
+    host_restart_stage(s);
+    c->nu_a0 = s.nu_a;
+    c->nu_r0 = s.nu_r;
+    st = push_state(c);
+    if (st != NRR_OK) return st;
+    st = capture_graph(c);
+    if (st != NRR_OK) return st;
+    guard.release();
+    *out = c;
+    return NRR_OK;
+}
+
+nrr_status nrr_step(nrr_ctx* c, nrr_step_info* info) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    if (c->h_state->done) return fail(c, NRR_E_STATE, "the solve has already returned");
+    nrr_status st = run_pass(c);
+    if (st != NRR_OK) { c->failed = true; return st; }
+    st = pull_state(c);
+    if (st != NRR_OK) { c->failed = true; return st; }
+    fill_info(*c->h_state, info);
+    if (c->h_state->status != 0) {
+        c->failed = true;
+        return fail(c, (nrr_status)c->h_state->status, "device-side wait timed out");
+    }
+    return NRR_OK;
+}
+
+nrr_status nrr_solve(nrr_ctx* c, int max_passes, nrr_step_info* info) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    const int cap = max_passes > 0 ? max_passes : c->prm.max_total_passes;
+    nrr_status st = pull_state(c);
+    if (st != NRR_OK) return st;
+    const int start = c->h_state->n_passes;
+    int launched = 0;
+    const int batch = 4;
+    while (!c->h_state->done && c->h_state->n_passes - start < cap) {
+        const int left = cap - (c->h_state->n_passes - start);
+        const int nb = std::min(batch, left);
+        for (int k = 0; k < nb; ++k) {
+            st = run_pass(c);
+            if (st != NRR_OK) { c->failed = true; return st; }
+        }
+        launched += nb;
+        st = pull_state(c);
+        if (st != NRR_OK) { c->failed = true; return st; }
+        if (c->h_state->status != 0) {
+            c->failed = true;
+            fill_info(*c->h_state, info);
+            return fail(c, (nrr_status)c->h_state->status, "device-side wait timed out");
+        }
+    }
+    fill_info(*c->h_state, info);
+    return c->h_state->done ? NRR_OK : NRR_E_NOT_CONVERGED;
+}
+
+nrr_status nrr_enqueue_passes(nrr_ctx* c, int n) {
+    if (!c || n < 0) return fail(c, NRR_E_INVALID, "bad argument");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    for (int k = 0; k < n; ++k) {
+        nrr_status st = run_pass(c);
+        if (st != NRR_OK) { c->failed = true; return st; }
+    }
+    return NRR_OK;
+}
+
+nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[4]) {
+    if (!c || n < 0 || !out_ms) return fail(c, NRR_E_INVALID, "bad argument");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    cudaEvent_t ev[5];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    nrr_status result = NRR_OK;
+    for (int k = 0; k < n && result == NRR_OK; ++k) {
+        cudaError_t e = cudaEventRecord(ev[0], c->stream);
+        for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
+            if (c->fp64) {
+                DevProblem<double>& d = c->dd;
+                e = s == 0 ? nrr_launch_nn<double>(d, NRR_MODE_PASS, 0, c->stream)
+                  : s == 1 ? nrr_launch_energy<double>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
+                  : s == 2 ? nrr_launch_assemble<double>(d, c->grid_asm, c->stream)
+                           : nrr_launch_solve<double>(d, c->grid_solve, c->stream, c->coop);
+            } else {
+                DevProblem<float>& d = c->df;
+                e = s == 0 ? nrr_launch_nn<float>(d, NRR_MODE_PASS, 0, c->stream)
+                  : s == 1 ? nrr_launch_energy<float>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
+                  : s == 2 ? nrr_launch_assemble<float>(d, c->grid_asm, c->stream)
+                           : nrr_launch_solve<float>(d, c->grid_solve, c->stream, c->coop);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev[s + 1], c->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+        for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+            out_ms[s] += ms;
+        }
+        if (e != cudaSuccess) {
+            c->failed = true;
+            result = fail(c, NRR_E_CUDA, std::string("nrr_time_kernels: ") + cudaGetErrorString(e));
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return result;
+}
+
+nrr_status nrr_reset(nrr_ctx* c) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    std::vector<double> I((size_t)c->N * 12, 0.0);
+    for (int j = 0; j < c->N; ++j) { I[(size_t)12 * j] = 1; I[(size_t)12 * j + 4] = 1; I[(size_t)12 * j + 8] = 1; }
+    nrr_status st = c->fp64 ? write_X<double>(c, c->dd.X, I.data()) : write_X<float>(c, c->df.X, I.data());
+    if (st != NRR_OK) return st;
+    st = pull_state(c);
+    if (st != NRR_OK) return st;
+    NrrState& s = *c->h_state;
+    s.nu_a = c->nu_a0;
+    s.nu_r = c->nu_r0;
+    s.stage = 0;
+    s.n_passes = s.n_solves = s.n_rejected = 0;
+    s.max_disp = 0;
+    s.kept = s.solved = 0;
+    host_stage_weights(s);
+    host_restart_stage(s);
+    return push_state(c);
+}
+
+nrr_status nrr_energy(nrr_ctx* c, const double* X, double out_terms[4]) {
+    if (!c || !out_terms) return fail(c, NRR_E_INVALID, "NULL argument");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    nrr_status st;
+    if (c->fp64) {
+        if (X) { st = write_X<double>(c, c->dd.Xeval, X); if (st != NRR_OK) return st; }
+        else CK(cudaMemcpyAsync(c->dd.Xeval, c->dd.X, sizeof(double) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
+        CK(nrr_launch_nn<double>(c->dd, NRR_MODE_EVAL, 0, c->stream));
+        CK(nrr_launch_energy<double>(c->dd, NRR_MODE_EVAL, c->grid_energy, c->stream));
+    } else {
+        if (X) { st = write_X<float>(c, c->df.Xeval, X); if (st != NRR_OK) return st; }
+        else CK(cudaMemcpyAsync(c->df.Xeval, c->df.X, sizeof(float) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
+        CK(nrr_launch_nn<float>(c->df, NRR_MODE_EVAL, 0, c->stream));
+        CK(nrr_launch_energy<float>(c->df, NRR_MODE_EVAL, c->grid_energy, c->stream));
+    }
+    st = pull_state(c);
+    if (st != NRR_OK) return st;
+    for (int k = 0; k < 4; ++k) out_terms[k] = c->h_state->E_eval[k];
+    // the evaluation wrote v_hat, rho and d2 of X into the non-kept buffers
+    c->h_state->vlast = c->h_state->vk ^ 1;
+    return push_state(c);
+}
+
+nrr_status nrr_set_transforms(nrr_ctx* c, const double* X) {
+    if (!c || !X) return fail(c, NRR_E_INVALID, "NULL argument");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    nrr_status st = c->fp64 ? write_X<double>(c, c->dd.X, X) : write_X<float>(c, c->df.X, X);
+    if (st != NRR_OK) return st;
+    st = pull_state(c);
+    if (st != NRR_OK) return st;
+    host_restart_stage(*c->h_state);
+    return push_state(c);
+}
+
+nrr_status nrr_set_stage(nrr_ctx* c, double nu_a, double nu_r) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (!(nu_a > 0) || !(nu_r > 0) || !std::isfinite(nu_a) || !std::isfinite(nu_r))
+        return fail(c, NRR_E_INVALID, "nu_a and nu_r must be positive and finite");
+    nrr_status st = pull_state(c);
+    if (st != NRR_OK) return st;
+    NrrState& s = *c->h_state;
+    s.nu_a = std::max(nu_a, s.nu_a_min);
+    s.nu_r = nu_r;
+    host_stage_weights(s);
+    host_restart_stage(s);
+    return push_state(c);
+}
+
+nrr_status nrr_get_transforms(nrr_ctx* c, double* X) {
+    if (!c || !X) return fail(c, NRR_E_INVALID, "NULL argument");
+    return c->fp64 ? read_X<double>(c, c->dd.X, X) : read_X<float>(c, c->df.X, X);
+}
+
+nrr_status nrr_get_mm_solution(nrr_ctx* c, double* G) {
+    if (!c || !G) return fail(c, NRR_E_INVALID, "NULL argument");
+    return c->fp64 ? read_X<double>(c, c->dd.Gprev, G) : read_X<float>(c, c->df.Gprev, G);
+}
+
+nrr_status nrr_get_info(nrr_ctx* c, nrr_step_info* info) {
+    if (!c || !info) return fail(c, NRR_E_INVALID, "NULL argument");
+    nrr_status st = pull_state(c);
+    if (st != NRR_OK) return st;
+    fill_info(*c->h_state, info);
+    return NRR_OK;
+}
+
+nrr_status nrr_get_sizes(nrr_ctx* c, int64_t* P, int64_t* T, int64_t* N, int64_t* n_edges,
+                         int32_t* max_influence) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (P) *P = c->P;
+    if (T) *T = c->T;
+    if (N) *N = c->N;
+    if (n_edges) *n_edges = (int64_t)c->hg.edges.size() / 2;
+    if (max_influence) *max_influence = c->hg.K;
+    return NRR_OK;
+}
+
+nrr_status nrr_get_graph(nrr_ctx* c, int32_t* node_src, int32_t* nidx, double* w, int32_t* edges,
+                         double* r, double* lbar) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    const HostGraph& g = c->hg;
+    if (node_src) std::copy(g.nodes.begin(), g.nodes.end(), node_src);
+    if (nidx) std::copy(g.nidx.begin(), g.nidx.end(), nidx);
+    if (w) std::copy(g.w.begin(), g.w.end(), w);
+    if (edges) std::copy(g.edges.begin(), g.edges.end(), edges);
+    if (r) std::copy(g.r.begin(), g.r.end(), r);
+    if (lbar) *lbar = g.lbar;
+    return NRR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+nrr_status get_points(nrr_ctx* c, const T* dev, int ncomp, double* out) {
+    const size_t P = (size_t)c->P;
+    std::vector<T> h(P * ncomp);
+    CK(cudaMemcpyAsync(h.data(), dev, sizeof(T) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<double> o(P * ncomp);
+    for (size_t ii = 0; ii < P; ++ii) {
+        const size_t i = (size_t)c->src_order[ii];
+        for (int a = 0; a < ncomp; ++a) o[i * ncomp + a] = (double)h[a * P + ii];
+    }
+    CK(cudaMemcpy(out, o.data(), sizeof(double) * o.size(), cudaMemcpyDefault));
+    return NRR_OK;
+}
+
+template <typename T>
+nrr_status get_system_t(nrr_ctx* c, double* Kd, double* B) {
+    DevProblem<T>& d = prob<T>(c);
+    const int N = c->N;
+    std::vector<T> kv((size_t)c->nblk * 16), bv((size_t)N * 12);
+    CK(cudaMemcpyAsync(kv.data(), d.Kv, sizeof(T) * kv.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(bv.data(), d.Bv, sizeof(T) * bv.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (Kd) {
+        const size_t n4 = (size_t)4 * N;
+        std::vector<double> K(n4 * n4, 0.0);
+        for (int n = 0; n < N; ++n)
+            for (int b = c->bsr_ptr[(size_t)n]; b < c->bsr_ptr[(size_t)n + 1]; ++b) {
+                const int k = c->bsr_col[(size_t)b];
+                for (int a = 0; a < 4; ++a)
+                    for (int t = 0; t < 4; ++t)
+                        K[(size_t)(4 * n + a) * n4 + 4 * k + t] = (double)kv[(size_t)16 * b + 4 * a + t];
+            }
+        CK(cudaMemcpy(Kd, K.data(), sizeof(double) * K.size(), cudaMemcpyDefault));
+    }
+    if (B) {
+        std::vector<double> o(bv.begin(), bv.end());
+        CK(cudaMemcpy(B, o.data(), sizeof(double) * o.size(), cudaMemcpyDefault));
+    }
+    return NRR_OK;
+}
+}  // namespace
+
+extern "C" {
+
+nrr_status nrr_get_deformed(nrr_ctx* c, double* v_hat) {
+    if (!c || !v_hat) return fail(c, NRR_E_INVALID, "NULL argument");
+    nrr_status st = pull_state(c);
+    if (st != NRR_OK) return st;
+    const int b = c->h_state->vlast;
+    const size_t off = (size_t)b * 3 * (size_t)c->P;
+    return c->fp64 ? get_points<double>(c, c->dd.vhat + off, 3, v_hat)
+                   : get_points<float>(c, c->df.vhat + off, 3, v_hat);
+}
+
+nrr_status nrr_get_correspondence(nrr_ctx* c, int32_t* rho, double* d2) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    const size_t P = (size_t)c->P;
+    if (rho) {
+        std::vector<int> h(P), o(P);
+        const int* src = c->fp64 ? c->dd.rho : c->df.rho;
+        CK(cudaMemcpyAsync(h.data(), src, sizeof(int) * P, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (size_t ii = 0; ii < P; ++ii) o[(size_t)c->src_order[ii]] = h[ii];
+        CK(cudaMemcpy(rho, o.data(), sizeof(int) * P, cudaMemcpyDefault));
+    }
+    if (d2) {
+        nrr_status st = c->fp64 ? get_points<double>(c, c->dd.d2, 1, d2) : get_points<float>(c, c->df.d2, 1, d2);
+        if (st != NRR_OK) return st;
+    }
+    return NRR_OK;
+}
+
+nrr_status nrr_get_system(nrr_ctx* c, double* Kdense, double* B) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (Kdense && c->N > 4096) return fail(c, NRR_E_INVALID, "dense K only for N <= 4096");
+    return c->fp64 ? get_system_t<double>(c, Kdense, B) : get_system_t<float>(c, Kdense, B);
+}
+
+nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, double* grad_src) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    (void)mode; (void)X; (void)grad_X; (void)grad_src;
+    return fail(c, NRR_E_INVALID, "nrr_backward: not available in this build");
+}
+
+}  // extern "C"

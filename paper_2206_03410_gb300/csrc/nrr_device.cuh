@@ -1,0 +1,135 @@
+// Device data layout and kernel entry points of one registration problem.
+//
+// HBM layout (T = float for the mixed path, double for the FP64 path):
+//   source, internal Morton order:  v [3][P] SoA; influence lists in CSR
+//     (infl_ptr [P+1], infl_node/infl_w [nnz]); per pass v_hat [2][3][P],
+//     closest target coordinates u [3][P], caller index rho [P], d2 [P],
+//     alignment weights wa [P].
+//   target, internal Morton order:  tpts [n_leaves*32] {x,y,z,caller idx},
+//     padded with +inf points; AABBs of 32-point leaves (float [6]) and of
+//     32-leaf super tiles (float [6]).
+//   graph: nodes p [N][3]; directed pairs (e_i, e_j, e_r) sorted by (i, j)
+//     with CSR adj_ptr [N+1] over e_i and e_rev [E2] (reverse pair);
+//     reg weights wr [E2]; rotations Rm [N][9].
+//   system: block-sparse K in BSR with 4x4 blocks on the node-graph pattern
+//     (bsr_ptr [N+1], bsr_col [nblk], bsr_edge [nblk] = directed pair (row,
+//     col) or -1 on the diagonal), Kv [nblk][16], B [N][12]; per block the
+//     list of (point, slot_row, slot_col) contributions (ent_ptr, ent).
+//   iterates: X, G, Gprev, Fprev [N][12]; Anderson rings dF, dG [m][N*12];
+//     PCG vectors r, z, p, q [N*12], block-Jacobi inverse Minv [N][16].
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "nrr_internal.h"
+
+template <typename T>
+struct __align__(16) TPoint {
+    T x, y, z;
+    int idx;
+};
+
+template <typename T>
+struct DevProblem {
+    int P, N, E2, n_leaves, n_supers, nblk;
+    int aa_m;
+    int pcg_max;
+    T pcg_tol;
+    // source
+    const T* v;
+    const int* infl_ptr;
+    const int* infl_node;
+    const T* infl_w;
+    const T* p;
+    // target
+    const TPoint<T>* tpts;
+    const float* leaf_box;
+    const float* super_box;
+    // iterates
+    T* X;
+    T* Xeval;
+    T* G;
+    T* Gprev;
+    T* Fprev;
+    T* dF;
+    T* dG;
+    // per point
+    T* vhat;        // [2][3][P]
+    T* u;           // [3][P]
+    int* rho;       // [P] caller target index
+    T* d2;          // [P]
+    T* wa;          // [P]
+    // graph edges
+    const int* e_i;
+    const int* e_j;
+    const T* e_r;
+    const int* adj_ptr;
+    const int* e_rev;
+    T* wr;
+    T* Rm;
+    // assembly
+    const int* bsr_ptr;
+    const int* bsr_col;
+    const int* bsr_edge;
+    const int* ent_ptr;
+    const int* ent;         // packed (point << 6 | slot_row << 3 | slot_col)
+    const T* ent_w;         // [n_ent][2] (w_row, w_col) of the entry's point
+    const int* blk_row;     // [nblk] row node of each block
+    const T* pbar;          // [3][P] sum_j w_ij p_j (constant part of Q_i)
+    T* Kv;
+    T* Bv;
+    // PCG
+    T* r;
+    T* z;
+    T* pv;
+    T* q;
+    T* Minv;
+    // reductions
+    double* partials;   // [max_ctas * NRR_PARTIAL_STRIDE]
+    NrrState* st;
+};
+
+#define NRR_PARTIAL_STRIDE 32
+
+enum NrrMode { NRR_MODE_PASS = 0, NRR_MODE_EVAL = 1, NRR_MODE_RAW = 2 };
+
+// Launch helpers (defined in the kernel translation units).
+template <typename T>
+cudaError_t nrr_launch_nn(const DevProblem<T>& d, int mode, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t nrr_launch_energy(const DevProblem<T>& d, int mode, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t nrr_launch_assemble(const DevProblem<T>& d, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t nrr_launch_solve(const DevProblem<T>& d, int grid, cudaStream_t s, bool cooperative);
+template <typename T>
+cudaError_t nrr_launch_gradient(const DevProblem<T>& d, double* grad_X, double* grad_v,
+                                int grid, cudaStream_t s);
+
+// Stage transition of Algorithm 2 (halve nu_a and nu_r, recompute alpha and
+// beta with Eq. WeightSettings, restart the stage). Single device thread.
+__device__ __forceinline__ void nrr_stage_weights(NrrState* st) {
+    st->alpha = st->alpha_fixed >= 0 ? st->alpha_fixed
+                                     : st->k_alpha * st->n_src / st->n_edges *
+                                           (st->nu_r * st->nu_r) / (st->nu_a * st->nu_a);
+    st->beta = st->beta_fixed >= 0 ? st->beta_fixed
+                                   : st->k_beta * st->n_src / st->n_nodes /
+                                         (2.0 * st->nu_a * st->nu_a);
+}
+
+__device__ __forceinline__ void nrr_end_stage(NrrState* st) {
+    if (st->nu_a == st->nu_a_min) {
+        st->done = 1;
+        return;
+    }
+    st->nu_a = fmax(st->nu_a * 0.5, st->nu_a_min);
+    st->nu_r = st->nu_r * 0.5;
+    st->stage += 1;
+    nrr_stage_weights(st);
+    st->E_prev = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    st->n_solves_stage = 0;
+    st->aa_count = 0;
+    st->aa_head = 0;
+    st->just_reverted = 0;
+    st->pending_stop = 0;
+}

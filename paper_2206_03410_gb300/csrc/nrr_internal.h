@@ -1,0 +1,74 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nrr.h"
+
+#define NRR_AA_MMAX 8       // largest Anderson depth m
+#define NRR_LEAF 32         // target points per leaf tile (one per lane)
+#define NRR_MAX_INFL 8      // largest |I(v_i)|
+
+// ---------------------------------------------------------------------------
+// Device-resident control block of one context. Written by the kernels of a
+// pass; the host reads it after a pass. Doubles first for alignment.
+// ---------------------------------------------------------------------------
+struct NrrState {
+    double nu_a, nu_r, nu_a_min, alpha, beta;   // current stage
+    double k_alpha, k_beta, alpha_fixed, beta_fixed;
+    double n_src, n_edges, n_nodes;             // |V|, |E_G|, |V_G|
+    double eps, rel_tol;
+    double E, E_align, E_reg, E_rot;            // of the last evaluated iterate
+    double E_prev;                              // last kept energy in stage
+    double max_disp;                            // of the last stop test
+    double pcg_res;                             // max relative residual
+    double gram[NRR_AA_MMAX * NRR_AA_MMAX];     // dF_a . dF_b by ring slot
+    double E_eval[4];                           // nrr_energy result
+    double theta[NRR_AA_MMAX];                  // last Anderson coefficients
+    unsigned long long disp_bits;               // running max of |dv|^2 bits
+    int stage;
+    int n_solves_stage, n_solves, n_passes, n_rejected;
+    int max_iters_stage;
+    int just_reverted;
+    int pending_stop;       // 1: the previous pass solved; test at next pass
+    int skip;               // 1: this pass stops after the energy
+    int kept, solved;       // flags of the last pass
+    int done;               // Algorithm 2 returned
+    int status;             // nrr_status from device-side checks
+    int aa_m, aa_count, aa_head, aa_mk;
+    int pcg_iters;
+    int vk;                 // which v_hat buffer holds the kept iterate
+    int vlast;              // which v_hat buffer was written last
+    int have_vk;            // v_hat of a kept iterate exists
+    unsigned int cnt_nn, cnt_energy;   // last-block-done counters
+    unsigned int bar_count, bar_gen;   // grid barrier of the solve kernel
+};
+
+// Host-side graph (Algorithm 1), all in caller point indices.
+struct HostGraph {
+    double radius = 0, lbar = 0;
+    int K = 8;                        // max influence
+    std::vector<int> nodes;           // source index of node j
+    std::vector<int> nidx;            // [P*K], -1 padded, nearest first
+    std::vector<double> w;            // [P*K]
+    std::vector<int> edges;           // [n_edges*2], j<k sorted
+    std::vector<int> dpair;           // [2*n_edges*2] directed (i,j) sorted
+    std::vector<double> r;            // [2*n_edges]
+};
+
+// graph_build.cpp
+double nrr_mean_spacing(const double* V, int64_t P, int k);
+void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g);
+void nrr_morton_order(const float* pts, int64_t n, const double lo[3],
+                      const double hi[3], std::vector<int>& order,
+                      std::vector<uint64_t>* codes_sorted);
+
+// Error helpers
+struct NrrError {
+    nrr_status code;
+    std::string msg;
+};

@@ -1,0 +1,409 @@
+"""ctypes binding of libnrr (include/nrr.h).
+
+Argument marshalling only: every computation of the registration runs in the
+library's CUDA kernels. The functions keep the C names (``nrr_create``,
+``nrr_step``, ``nrr_solve``, ``nrr_energy``, ``nrr_backward`` ...); the
+``Registration`` class is a thin owner of one context.
+
+Inputs may be numpy arrays (host) or torch tensors (host or CUDA); outputs
+are returned as numpy arrays. The library is loaded from the in-tree build
+(``_build/libnrr.so``); if it cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+NRR_OK = 0
+NRR_E_INVALID = 1
+NRR_E_CUDA = 2
+NRR_E_OOM = 3
+NRR_E_SINGULAR = 4
+NRR_E_TIMEOUT = 5
+NRR_E_NOT_CONVERGED = 6
+NRR_E_STATE = 7
+
+NRR_FP64 = 0
+NRR_MIXED = 1
+
+
+class NrrParams(ctypes.Structure):
+    _fields_ = [
+        ("graph_radius", ctypes.c_double),
+        ("max_influence", ctypes.c_int),
+        ("nu_a", ctypes.c_double),
+        ("nu_r", ctypes.c_double),
+        ("nu_a_min", ctypes.c_double),
+        ("anneal", ctypes.c_int),
+        ("k_alpha", ctypes.c_double),
+        ("k_beta", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("aa_m", ctypes.c_int),
+        ("max_iters_per_stage", ctypes.c_int),
+        ("max_total_passes", ctypes.c_int),
+        ("eps", ctypes.c_double),
+        ("rel_energy_tol", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("pcg_tol", ctypes.c_double),
+        ("pcg_max_iters", ctypes.c_int),
+    ]
+
+
+class NrrStepInfo(ctypes.Structure):
+    _fields_ = [
+        ("E", ctypes.c_double),
+        ("E_align", ctypes.c_double),
+        ("E_reg", ctypes.c_double),
+        ("E_rot", ctypes.c_double),
+        ("nu_a", ctypes.c_double),
+        ("nu_r", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("max_disp", ctypes.c_double),
+        ("pcg_rel_residual", ctypes.c_double),
+        ("kept", ctypes.c_int),
+        ("solved", ctypes.c_int),
+        ("stage", ctypes.c_int),
+        ("done", ctypes.c_int),
+        ("pcg_iters", ctypes.c_int),
+        ("aa_mk", ctypes.c_int),
+        ("n_passes", ctypes.c_int),
+        ("n_solves", ctypes.c_int),
+        ("n_rejected", ctypes.c_int),
+        ("status", ctypes.c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# (name, restype, argtypes) of every entry point declared in include/nrr.h
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = [
+    ("nrr_params_default", None, [ctypes.POINTER(NrrParams)]),
+    ("nrr_create", ctypes.c_int, [ctypes.POINTER(_VP), _VP, _VP, _I64, _VP, _VP, _I64,
+                                  ctypes.POINTER(NrrParams), _VP]),
+    ("nrr_destroy", None, [_VP]),
+    ("nrr_step", ctypes.c_int, [_VP, ctypes.POINTER(NrrStepInfo)]),
+    ("nrr_solve", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(NrrStepInfo)]),
+    ("nrr_enqueue_passes", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("nrr_reset", ctypes.c_int, [_VP]),
+    ("nrr_time_kernels", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    ("nrr_energy", ctypes.c_int, [_VP, _VP, _VP]),
+    ("nrr_backward", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    ("nrr_set_transforms", ctypes.c_int, [_VP, _VP]),
+    ("nrr_set_stage", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double]),
+    ("nrr_get_transforms", ctypes.c_int, [_VP, _VP]),
+    ("nrr_get_deformed", ctypes.c_int, [_VP, _VP]),
+    ("nrr_get_correspondence", ctypes.c_int, [_VP, _VP, _VP]),
+    ("nrr_get_sizes", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    ("nrr_get_graph", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("nrr_get_system", ctypes.c_int, [_VP, _VP, _VP]),
+    ("nrr_get_mm_solution", ctypes.c_int, [_VP, _VP]),
+    ("nrr_get_info", ctypes.c_int, [_VP, ctypes.POINTER(NrrStepInfo)]),
+    ("nrr_last_error", ctypes.c_char_p, [_VP]),
+]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libnrr.so (building it first if needed). Raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnrr.so not found at {path}")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class NrrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"nrr error {code}: {msg}")
+        self.code = code
+
+
+def _check(code: int, ctx=None, ok=(NRR_OK,)):
+    if code not in ok:
+        msg = load().nrr_last_error(ctx)
+        raise NrrError(code, msg.decode() if msg else "")
+    return code
+
+
+def _ptr(a):
+    """Device or host pointer of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def params_default() -> NrrParams:
+    p = NrrParams()
+    load().nrr_params_default(ctypes.byref(p))
+    return p
+
+
+def make_params(**kw) -> NrrParams:
+    p = params_default()
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = NRR_FP64 if v.lower() == "fp64" else NRR_MIXED
+        if k in ("radius",):
+            k = "graph_radius"
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+
+def nrr_create(src, tgt, params: NrrParams, src_nrm=None, tgt_nrm=None, stream=None):
+    lib = load()
+    ctx = _VP()
+    P = int(src.shape[0])
+    T = int(tgt.shape[0])
+    _check(lib.nrr_create(ctypes.byref(ctx), _ptr(src), _ptr(src_nrm), P, _ptr(tgt),
+                          _ptr(tgt_nrm), T, ctypes.byref(params), stream))
+    return ctx
+
+
+def nrr_destroy(ctx):
+    load().nrr_destroy(ctx)
+
+
+def nrr_step(ctx) -> NrrStepInfo:
+    info = NrrStepInfo()
+    _check(load().nrr_step(ctx, ctypes.byref(info)), ctx)
+    return info
+
+
+def nrr_solve(ctx, max_passes: int = 0) -> NrrStepInfo:
+    info = NrrStepInfo()
+    _check(load().nrr_solve(ctx, int(max_passes), ctypes.byref(info)), ctx,
+           ok=(NRR_OK, NRR_E_NOT_CONVERGED))
+    return info
+
+
+def nrr_enqueue_passes(ctx, n: int):
+    _check(load().nrr_enqueue_passes(ctx, int(n)), ctx)
+
+
+def nrr_reset(ctx):
+    _check(load().nrr_reset(ctx), ctx)
+
+
+KERNELS = ("nn_kernel", "energy_kernel", "assemble_kernel", "solve_kernel")
+
+
+def nrr_time_kernels(ctx, n: int = 1) -> np.ndarray:
+    """Milliseconds spent in each of the four kernels of a pass, summed over
+    n passes (event-timed on the context's stream)."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(load().nrr_time_kernels(ctx, int(n), _ptr(out)), ctx)
+    return out
+
+
+def nrr_energy(ctx, X=None) -> np.ndarray:
+    out = np.zeros(4, dtype=np.float64)
+    Xa = None if X is None else np.ascontiguousarray(X, dtype=np.float64)
+    _check(load().nrr_energy(ctx, _ptr(Xa), _ptr(out)), ctx)
+    return out
+
+
+def nrr_backward(ctx, X=None, mode: int = 0, want_src: bool = True):
+    P, _, N, _, _ = nrr_get_sizes(ctx)
+    gX = np.zeros((N, 12), dtype=np.float64)
+    gv = np.zeros((P, 3), dtype=np.float64) if want_src else None
+    Xa = None if X is None else np.ascontiguousarray(X, dtype=np.float64)
+    _check(load().nrr_backward(ctx, int(mode), _ptr(Xa), _ptr(gX), _ptr(gv)), ctx)
+    return gX, gv
+
+
+def nrr_set_transforms(ctx, X):
+    Xa = np.ascontiguousarray(X, dtype=np.float64)
+    _check(load().nrr_set_transforms(ctx, _ptr(Xa)), ctx)
+
+
+def nrr_set_stage(ctx, nu_a: float, nu_r: float):
+    _check(load().nrr_set_stage(ctx, float(nu_a), float(nu_r)), ctx)
+
+
+def nrr_get_sizes(ctx):
+    P, T, N, E = (ctypes.c_int64() for _ in range(4))
+    K = ctypes.c_int32()
+    _check(load().nrr_get_sizes(ctx, ctypes.byref(P), ctypes.byref(T), ctypes.byref(N),
+                                ctypes.byref(E), ctypes.byref(K)), ctx)
+    return P.value, T.value, N.value, E.value, K.value
+
+
+def nrr_get_transforms(ctx) -> np.ndarray:
+    _, _, N, _, _ = nrr_get_sizes(ctx)
+    X = np.zeros((N, 12), dtype=np.float64)
+    _check(load().nrr_get_transforms(ctx, _ptr(X)), ctx)
+    return X
+
+
+def nrr_get_mm_solution(ctx) -> np.ndarray:
+    _, _, N, _, _ = nrr_get_sizes(ctx)
+    X = np.zeros((N, 12), dtype=np.float64)
+    _check(load().nrr_get_mm_solution(ctx, _ptr(X)), ctx)
+    return X
+
+
+def nrr_get_deformed(ctx) -> np.ndarray:
+    P, _, _, _, _ = nrr_get_sizes(ctx)
+    v = np.zeros((P, 3), dtype=np.float64)
+    _check(load().nrr_get_deformed(ctx, _ptr(v)), ctx)
+    return v
+
+
+def nrr_get_correspondence(ctx):
+    P, _, _, _, _ = nrr_get_sizes(ctx)
+    rho = np.zeros(P, dtype=np.int32)
+    d2 = np.zeros(P, dtype=np.float64)
+    _check(load().nrr_get_correspondence(ctx, _ptr(rho), _ptr(d2)), ctx)
+    return rho, d2
+
+
+@dataclass
+class GraphView:
+    nodes: np.ndarray
+    nidx: np.ndarray
+    w: np.ndarray
+    edges: np.ndarray
+    r: np.ndarray
+    lbar: float
+
+
+def nrr_get_graph(ctx) -> GraphView:
+    P, _, N, E, K = nrr_get_sizes(ctx)
+    nodes = np.zeros(N, dtype=np.int32)
+    nidx = np.zeros((P, K), dtype=np.int32)
+    w = np.zeros((P, K), dtype=np.float64)
+    edges = np.zeros((E, 2), dtype=np.int32)
+    r = np.zeros(2 * E, dtype=np.float64)
+    lbar = ctypes.c_double()
+    _check(load().nrr_get_graph(ctx, _ptr(nodes), _ptr(nidx), _ptr(w), _ptr(edges), _ptr(r),
+                                ctypes.byref(lbar)), ctx)
+    return GraphView(nodes, nidx, w, edges, r, lbar.value)
+
+
+def nrr_get_system(ctx, dense: bool = True):
+    _, _, N, _, _ = nrr_get_sizes(ctx)
+    K = np.zeros((4 * N, 4 * N), dtype=np.float64) if dense else None
+    B = np.zeros((4 * N, 3), dtype=np.float64)
+    _check(load().nrr_get_system(ctx, _ptr(K), _ptr(B)), ctx)
+    return K, B
+
+
+def nrr_get_info(ctx) -> NrrStepInfo:
+    info = NrrStepInfo()
+    _check(load().nrr_get_info(ctx, ctypes.byref(info)), ctx)
+    return info
+
+
+class Registration:
+    """Owner of one nrr context.
+
+    >>> reg = Registration(src, tgt, precision="fp64", radius=0.15)
+    >>> info = reg.solve()
+    >>> X = reg.transforms()
+    """
+
+    def __init__(self, src, tgt, src_nrm=None, tgt_nrm=None, stream=None, **params):
+        self._p = make_params(**params)
+        self._keep = (src, tgt, src_nrm, tgt_nrm)
+        self.ctx = nrr_create(src, tgt, self._p, src_nrm, tgt_nrm, stream)
+        self.P, self.T, self.N, self.n_edges, self.K = nrr_get_sizes(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            nrr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self) -> NrrStepInfo:
+        return nrr_step(self.ctx)
+
+    def solve(self, max_passes: int = 0) -> NrrStepInfo:
+        return nrr_solve(self.ctx, max_passes)
+
+    def enqueue_passes(self, n: int):
+        nrr_enqueue_passes(self.ctx, n)
+
+    def reset(self):
+        nrr_reset(self.ctx)
+
+    def time_kernels(self, n: int = 1) -> np.ndarray:
+        return nrr_time_kernels(self.ctx, n)
+
+    def energy(self, X=None) -> np.ndarray:
+        return nrr_energy(self.ctx, X)
+
+    def backward(self, X=None, want_src: bool = True):
+        return nrr_backward(self.ctx, X, 0, want_src)
+
+    def set_transforms(self, X):
+        nrr_set_transforms(self.ctx, X)
+
+    def set_stage(self, nu_a, nu_r):
+        nrr_set_stage(self.ctx, nu_a, nu_r)
+
+    def transforms(self) -> np.ndarray:
+        return nrr_get_transforms(self.ctx)
+
+    def mm_solution(self) -> np.ndarray:
+        return nrr_get_mm_solution(self.ctx)
+
+    def deformed(self) -> np.ndarray:
+        return nrr_get_deformed(self.ctx)
+
+    def correspondence(self):
+        return nrr_get_correspondence(self.ctx)
+
+    def graph(self) -> GraphView:
+        return nrr_get_graph(self.ctx)
+
+    def system(self, dense: bool = True):
+        return nrr_get_system(self.ctx, dense)
+
+    def info(self) -> NrrStepInfo:
+        return nrr_get_info(self.ctx)

@@ -274,7 +274,7 @@ def _sphere50k_partial(seed: int = 1) -> Pair:
 
 def _depth100k(seed: int = 2) -> Pair:
     p = depth_scene(100000, seed)
-    p.params = dict(radius=0.045, k_alpha=10.0, k_beta=1.0, aa_m=5,
+    p.params = dict(radius=0.062, k_alpha=10.0, k_beta=1.0, aa_m=5,
                     rel_energy_tol=1e-6, precision="mixed")
     p.name = "depth100k"
     return p
@@ -309,6 +309,18 @@ def batch_pairs(n_pairs: int = 64, seed: int = 1000):
         p.name = f"batch{i}"
         out.append(p)
     return out
+
+
+def perturbed_transforms(N: int, seed: int, scale_a: float = 0.01,
+                         scale_t: float = 0.005) -> np.ndarray:
+    """Seeded node transforms near the identity, [N,12] float64 in the
+    library's layout (rows 0..2 of each 4x3 block = A^T, row 3 = t)."""
+    rng = np.random.default_rng(seed)
+    X = np.zeros((N, 4, 3))
+    X[:, 0, 0] = X[:, 1, 1] = X[:, 2, 2] = 1.0
+    X[:, :3, :] += scale_a * rng.standard_normal((N, 3, 3))
+    X[:, 3, :] += scale_t * rng.standard_normal((N, 3))
+    return X.reshape(N, 12)
 
 
 WORKLOADS = {
