@@ -221,6 +221,30 @@ nrr_status nrr_get_mm_solution(nrr_ctx* ctx, double* G);
 /* State of the last pass without running one (host info). */
 nrr_status nrr_get_info(nrr_ctx* ctx, nrr_step_info* info);
 
+/* Alignment term of Eq. (2) and the weights of its quadratic surrogate,
+ * computed from closest-point distances without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (a preallocated real-time tracking loop, a host
+ * framework whose allocator owns all device memory, work issued while a CUDA
+ * graph is being captured), who therefore cannot create an nrr context.
+ *   d2 [P]    float, device: squared closest-point distances |v_hat_i - u_rho(i)|^2
+ *   nu_a      Welsch parameter (> 0)
+ *   w_a [P]   float, device, output: exp(-d2_i / (2 nu_a^2)) / (2 nu_a^2)
+ *   E_align   one double, device, output: sum_i psi_nu_a(sqrt(d2_i)), summed
+ *             per CTA in double and then over CTAs in a fixed order
+ *   cuda_stream: stream to run on (NULL = legacy default stream)
+ * The call is asynchronous on the stream; it only enqueues work.
+ * Scratch: a fixed 64 KiB static device array inside the library (every GPU
+ * that loads the library holds it until the process exits), which bounds P
+ * to 1..33,423,360 (NRR_E_INVALID beyond, with a message in
+ * nrr_last_error(NULL)). The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture. All calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller. Allocates nothing, calls no cudaMalloc or
+ * cudaFree. */
+nrr_status nrr_align_energy_noalloc(const float* d2, int64_t P, double nu_a, float* w_a,
+                                    double* E_align, void* cuda_stream);
+
 /* Message describing the last failure on ctx (or a global message if ctx is
  * NULL). The string lives until the next call on ctx. */
 const char* nrr_last_error(const nrr_ctx* ctx);

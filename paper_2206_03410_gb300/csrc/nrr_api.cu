@@ -27,6 +27,11 @@ struct Buffers {
 
 }  // namespace
 
+nrr_status nrr_set_global_error(nrr_status code, const char* msg) {
+    g_last_error = msg;
+    return code;
+}
+
 struct nrr_ctx {
     nrr_params prm{};
     bool fp64 = false;

@@ -67,6 +67,9 @@ void nrr_morton_order(const float* pts, int64_t n, const double lo[3],
                       const double hi[3], std::vector<int>& order,
                       std::vector<uint64_t>* codes_sorted);
 
+// Records msg as the global last error (nrr_last_error(NULL)); returns code.
+nrr_status nrr_set_global_error(nrr_status code, const char* msg);
+
 // Error helpers
 struct NrrError {
     nrr_status code;

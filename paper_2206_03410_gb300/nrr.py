@@ -108,6 +108,7 @@ _SIGS = [
     ("nrr_get_system", ctypes.c_int, [_VP, _VP, _VP]),
     ("nrr_get_mm_solution", ctypes.c_int, [_VP, _VP]),
     ("nrr_get_info", ctypes.c_int, [_VP, ctypes.POINTER(NrrStepInfo)]),
+    ("nrr_align_energy_noalloc", ctypes.c_int, [_VP, _I64, ctypes.c_double, _VP, _VP, _VP]),
     ("nrr_last_error", ctypes.c_char_p, [_VP]),
 ]
 
@@ -244,6 +245,14 @@ def nrr_backward(ctx, X=None, mode: int = 0, want_src: bool = True):
     Xa = None if X is None else np.ascontiguousarray(X, dtype=np.float64)
     _check(load().nrr_backward(ctx, int(mode), _ptr(Xa), _ptr(gX), _ptr(gv)), ctx)
     return gX, gv
+
+
+def nrr_align_energy_noalloc(d2, nu_a: float, w_a, E_align, stream=None):
+    """Allocation-free alignment energy and surrogate weights. d2, w_a:
+    float32 CUDA tensors [P]; E_align: float64 CUDA tensor [1]. Enqueues on
+    ``stream`` (raw cudaStream_t, None = legacy default stream)."""
+    _check(load().nrr_align_energy_noalloc(_ptr(d2), int(d2.shape[0]), float(nu_a), _ptr(w_a),
+                                            _ptr(E_align), stream))
 
 
 def nrr_set_transforms(ctx, X):
