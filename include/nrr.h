@@ -218,6 +218,22 @@ nrr_status nrr_get_system(nrr_ctx* ctx, double* Kdense, double* B);
 /* The G(X^(k)) of the last solve (the MM minimiser before mixing), [N][12]. */
 nrr_status nrr_get_mm_solution(nrr_ctx* ctx, double* G);
 
+/* Per-warp counters of the last closest-point search, for profiling the
+ * search: recorded only if the context was created with the environment
+ * variable NRR_NN_STATS set (otherwise *n_warps = 0). out [max_warps][4]
+ * (host or device) = {SM cycles, super tiles visited, leaves staged, leaves
+ * scanned} per warp; *n_warps receives the number of warps of a search. */
+nrr_status nrr_get_search_stats(nrr_ctx* ctx, unsigned long long* out, int64_t max_warps,
+                                int64_t* n_warps);
+
+/* Phase timestamps (SM clock cycles) of the last cluster solve, recorded by
+ * its first CTA, for profiling: only if the context was created with the
+ * environment variable NRR_SOLVE_STATS set (otherwise zeros). out[63] holds
+ * the number of stamps: start, after setup, before/after the first
+ * reduction, before/after each reduction of the first 8 CG iterations,
+ * before and after the Anderson mix. */
+nrr_status nrr_get_solve_stats(nrr_ctx* ctx, long long out[64]);
+
 /* State of the last pass without running one (host info). */
 nrr_status nrr_get_info(nrr_ctx* ctx, nrr_step_info* info);
 

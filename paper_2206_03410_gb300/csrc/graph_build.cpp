@@ -1,6 +1,7 @@
 // Host construction of the embedded deformation graph (Sec. 3.1, Algorithm 1)
 // for point clouds, with Euclidean distances in place of geodesics, plus the
-// mean point spacing l-bar and Morton ordering used by the search structures.
+// mean point spacing l-bar and the space-filling-curve ordering used by the
+// search structures.
 //
 // Built once per problem in nrr_create (setup, not part of the per-iteration
 // path). Compiled with -ffp-contract=off so that every squared distance is
@@ -258,28 +259,52 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
     for (size_t e = 0; e < E2; ++e) g.r[e] = 2.0 * (double)edge_list.size() * inv[e] / inv_sum;
 }
 
-static inline uint64_t spread21(uint64_t v) {
-    v &= 0x1fffff;
-    v = (v | v << 32) & 0x1f00000000ffffULL;
-    v = (v | v << 16) & 0x1f0000ff0000ffULL;
-    v = (v | v << 8) & 0x100f00f00f00f00fULL;
-    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
-    v = (v | v << 2) & 0x1249249249249249ULL;
-    return v;
+// Hilbert index of a 3-D point with 21 bits per axis, after J. Skilling,
+// "Programming the Hilbert curve", AIP Conf. Proc. 707 (2004): the axes are
+// converted in place to the "transposed" Hilbert index, whose bits are then
+// interleaved most significant first.
+static uint64_t hilbert3(uint32_t x, uint32_t y, uint32_t z) {
+    const int bits = 21;
+    uint32_t X[3] = {x, y, z};
+    const uint32_t M = 1u << (bits - 1);
+    for (uint32_t Q = M; Q > 1; Q >>= 1) {
+        const uint32_t Pm = Q - 1;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= Pm;
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & Pm;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    for (int i = 1; i < 3; ++i) X[i] ^= X[i - 1];
+    uint32_t t = 0;
+    for (uint32_t Q = M; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    for (int i = 0; i < 3; ++i) X[i] ^= t;
+    uint64_t h = 0;
+    for (int b = bits - 1; b >= 0; --b)
+        for (int i = 0; i < 3; ++i) h = (h << 1) | ((X[i] >> b) & 1u);
+    return h;
 }
 
-void nrr_morton_order(const float* pts, int64_t n, const double lo[3], const double hi[3],
+void nrr_curve_order(const float* pts, int64_t n, const double lo[3], const double hi[3],
                       std::vector<int>& order, std::vector<uint64_t>* codes_sorted) {
+    // points ordered along a 3-D Hilbert curve over the common bounding box:
+    // consecutive points are always spatially adjacent (no jumps between
+    // distant regions), so runs of 32 points have compact bounding boxes
     std::vector<std::pair<uint64_t, int>> kv((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
-        uint64_t c[3];
+        uint32_t c[3];
         for (int d = 0; d < 3; ++d) {
             double ext = hi[d] - lo[d];
             double f = ext > 0 ? ((double)pts[3 * i + d] - lo[d]) / ext : 0.0;
             f = std::min(std::max(f, 0.0), 1.0);
-            c[d] = (uint64_t)std::llround(f * 2097151.0);
+            c[d] = (uint32_t)std::llround(f * 2097151.0);
         }
-        kv[(size_t)i] = {spread21(c[0]) | (spread21(c[1]) << 1) | (spread21(c[2]) << 2), (int)i};
+        kv[(size_t)i] = {hilbert3(c[0], c[1], c[2]), (int)i};
     }
     std::sort(kv.begin(), kv.end());
     order.resize((size_t)n);

@@ -2,9 +2,9 @@
 // search rho(i) = argmin_u |u - v_hat_i| of Sec. 3.2 (Algorithm 2, first step
 // of each pass), plus the stopping test of Algorithm 2.
 //
-// Design: one warp serves 32 Morton-consecutive source points (one per
-// lane). The target is Morton-sorted into 32-point leaves with AABBs, and
-// leaves into 32-leaf super tiles. Each lane starts from the distance to its
+// Design: one warp serves consecutive source points along a Hilbert
+// curve. The target is sorted along the same curve into 32-point leaves with
+// AABBs, and leaves into 32-leaf super tiles. Each lane starts from the distance to its
 // previous correspondence (an actual target point, so a valid upper bound),
 // the warp tests super-tile and leaf boxes against its query box and the
 // warp's largest bound, and every surviving leaf is staged in shared memory
@@ -20,6 +20,26 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
+// leaves staged per batch (independent asynchronous copies); 32 KiB of
+// shared memory per CTA for float points, 32 KiB for double points
+template <typename T>
+struct Batch { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
+
+// 16-byte global->shared asynchronous copy (cp.async, L1-allocating) and
+// the wait for all of a thread's outstanding copies.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void stage_point(TPoint<float>* dst, const TPoint<float>* src) {
+    cp_async16(dst, src);
+}
+__device__ __forceinline__ void stage_point(TPoint<double>* dst, const TPoint<double>* src) {
+    cp_async16(dst, src);
+    cp_async16(reinterpret_cast<char*>(dst) + 16, reinterpret_cast<const char*>(src) + 16);
+}
 
 __device__ __forceinline__ float lo_f(double x) { return __double2float_rd(x); }
 __device__ __forceinline__ float hi_f(double x) { return __double2float_ru(x); }
@@ -41,32 +61,60 @@ __device__ __forceinline__ float box_gap2(float alox, float aloy, float aloz, fl
 __device__ __forceinline__ float ub_f(float b) { return __fmul_ru(b, 1.000002f); }
 __device__ __forceinline__ float ub_f(double b) { return __fmul_ru(__double2float_ru(b), 1.000002f); }
 
-__device__ __forceinline__ float warp_max(float x) {
-    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
-    return x;
-}
-__device__ __forceinline__ float warp_min(float x) {
-    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
-    return x;
-}
-
 template <typename T>
 __device__ __forceinline__ T sqdist(T ax, T ay, T az, T bx, T by, T bz) {
     T dx = ax - bx, dy = ay - by, dz = az - bz;
     return dx * dx + dy * dy + dz * dz;
 }
 
-template <typename T, int MODE>
+// Group arg-min over the LPQ lanes that share a query: smallest distance,
+// ties to the lowest caller index.
+template <typename T, int LPQ>
+__device__ __forceinline__ void group_argmin(T& best, int& bidx, T& bx, T& by, T& bz) {
+#pragma unroll
+    for (int o = LPQ / 2; o > 0; o >>= 1) {
+        const T od = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        const T ox = __shfl_xor_sync(0xffffffffu, bx, o);
+        const T oy = __shfl_xor_sync(0xffffffffu, by, o);
+        const T oz = __shfl_xor_sync(0xffffffffu, bz, o);
+        if (od < best || (od == best && oi < bidx)) { best = od; bidx = oi; bx = ox; by = oy; bz = oz; }
+    }
+}
+
+template <typename T, int LPQ>
+__device__ __forceinline__ T group_min(T v) {
+#pragma unroll
+    for (int o = LPQ / 2; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        v = ov < v ? ov : v;
+    }
+    return v;
+}
+
+// LPQ lanes serve one query: a warp serves 32 / LPQ curve-consecutive source
+// points, and each lane scans 32 / LPQ of the 32 points of every leaf that
+// its query needs. Splitting a query over several lanes shortens the serial
+// work of the slowest warps (queries far from the target, e.g. over holes),
+// and fewer queries per warp keep the warp's candidate set tight.
+template <typename T, int MODE, int LPQ>
 __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
-    __shared__ TPoint<T> tile[kWarps][32];
+    constexpr int QPW = 32 / LPQ;   // queries per warp
+    constexpr int PPL = 32 / LPQ;   // points of a leaf per lane
+    constexpr int kBatch = Batch<T>::value;
+    __shared__ TPoint<T> tile[kWarps][kBatch][32];
+    __shared__ float s_gb[kWarps][4][8];
     __shared__ double s_disp[kWarps];
     __shared__ int s_last;
     NrrState* st = d.st;
     if (MODE == NRR_MODE_PASS && st->done) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane % LPQ;
     const int P = d.P;
-    const int i = (blockIdx.x * kWarps + warp) * 32 + lane;
+    const int i = (blockIdx.x * kWarps + warp) * QPW + lane / LPQ;
     const bool valid = i < P;
+    const long long t_start = clock64();
+    unsigned n_super = 0, n_staged = 0, n_scanned = 0;
 
     // ---- query point: v_hat_i (Eq. deformed_position) or v_i -------------
     T qx = 0, qy = 0, qz = 0;
@@ -98,75 +146,127 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
         bidx = d.rho[i];
         best = sqdist(qx, qy, qz, bx, by, bz);
     }
+    T gbest = best;   // best over the lanes of the query (pruning bound)
     // lane query box (float, rounded outwards) and the warp's query box
     const float lx = valid ? lo_f(qx) : INFINITY, ly = valid ? lo_f(qy) : INFINITY,
                 lz = valid ? lo_f(qz) : INFINITY;
     const float hx = valid ? hi_f(qx) : -INFINITY, hy = valid ? hi_f(qy) : -INFINITY,
                 hz = valid ? hi_f(qz) : -INFINITY;
-    const float wlx = warp_min(lx), wly = warp_min(ly), wlz = warp_min(lz);
-    const float whx = warp_max(hx), why = warp_max(hy), whz = warp_max(hz);
+    // boxes of the four 8-lane groups of the warp and their largest bounds,
+    // kept in shared memory: a super tile or leaf is a candidate if it comes
+    // within the bound of any group's box
+    {
+        float g[6] = {lx, ly, lz, hx, hy, hz};
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) g[k] = fminf(g[k], __shfl_xor_sync(0xffffffffu, g[k], o));
+#pragma unroll
+            for (int k = 3; k < 6; ++k) g[k] = fmaxf(g[k], __shfl_xor_sync(0xffffffffu, g[k], o));
+        }
+        if ((lane & 7) == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s_gb[warp][lane >> 3][k] = g[k];
+        }
+    }
     const bool any_valid = __ballot_sync(0xffffffffu, valid) != 0;
-    float UB = warp_max(valid ? ub_f(best) : 0.f);
+    auto refresh_bounds = [&]() {
+        float u = valid ? ub_f(gbest) : 0.f;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) u = fmaxf(u, __shfl_xor_sync(0xffffffffu, u, o));
+        if ((lane & 7) == 0) s_gb[warp][lane >> 3][6] = u;
+        __syncwarp();
+    };
+    auto candidate = [&](const float* box) {
+        bool c = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float* gk = s_gb[warp][k];
+            c = c || box_gap2(gk[0], gk[1], gk[2], gk[3], gk[4], gk[5], box) <= gk[6];
+        }
+        return c;
+    };
+    refresh_bounds();
 
     if (any_valid) {
         for (int s0 = 0; s0 < d.n_supers; s0 += 32) {
             const int s = s0 + lane;
-            bool sc = s < d.n_supers &&
-                      box_gap2(wlx, wly, wlz, whx, why, whz, d.super_box + 6 * s) <= UB;
+            bool sc = s < d.n_supers && candidate(d.super_box + 6 * s);
             unsigned smask = __ballot_sync(0xffffffffu, sc);
             while (smask) {
                 const int sb = __ffs(smask) - 1;
                 smask &= smask - 1;
                 const int base = (s0 + sb) * 32;
+                ++n_super;
                 // lane l holds the box of leaf base + l
                 float bl[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
                 bool lc = false;
                 if (base + lane < d.n_leaves) {
 #pragma unroll
                     for (int k = 0; k < 6; ++k) bl[k] = d.leaf_box[6 * (base + lane) + k];
-                    lc = box_gap2(wlx, wly, wlz, whx, why, whz, bl) <= UB;
+                    lc = candidate(bl);
                 }
                 unsigned lmask = __ballot_sync(0xffffffffu, lc);
-                int lb = lmask ? __ffs(lmask) - 1 : -1;
-                TPoint<T> cur;
-                if (lb >= 0) cur = d.tpts[(size_t)(base + lb) * 32 + lane];
-                while (lb >= 0) {
-                    lmask &= lmask - 1;
-                    const int nb = lmask ? __ffs(lmask) - 1 : -1;
-                    TPoint<T> nxt;
-                    if (nb >= 0) nxt = d.tpts[(size_t)(base + nb) * 32 + lane];   // prefetch
-                    float b6[6];
+                while (lmask) {
+                    // up to kBatch leaves that some query of the warp needs
+                    int ids[kBatch];
+                    int cnt = 0;
+                    while (lmask && cnt < kBatch) {
+                        const int lb = __ffs(lmask) - 1;
+                        lmask &= lmask - 1;
+                        float b6[6];
 #pragma unroll
-                    for (int k = 0; k < 6; ++k) b6[k] = __shfl_sync(0xffffffffu, bl[k], lb);
-                    const bool need = valid && box_gap2(lx, ly, lz, hx, hy, hz, b6) <= ub_f(best);
-                    if (__ballot_sync(0xffffffffu, need)) {
-                        tile[warp][lane] = cur;
-                        __syncwarp();
-                        if (need) {
-#pragma unroll 8
-                            for (int j = 0; j < 32; ++j) {
-                                const TPoint<T> c = tile[warp][j];
-                                const T dd = sqdist(qx, qy, qz, c.x, c.y, c.z);
-                                if (dd < best || (dd == best && c.idx < bidx)) {
-                                    best = dd; bidx = c.idx;
-                                    bx = c.x; by = c.y; bz = c.z;
+                        for (int k = 0; k < 6; ++k) b6[k] = __shfl_sync(0xffffffffu, bl[k], lb);
+                        const bool need = valid && box_gap2(lx, ly, lz, hx, hy, hz, b6) <= ub_f(gbest);
+                        if (__ballot_sync(0xffffffffu, need)) ids[cnt++] = lb;
+                    }
+                    // stage them with independent asynchronous copies
+                    n_staged += cnt;
+#pragma unroll
+                    for (int k = 0; k < kBatch; ++k)
+                        if (k < cnt) stage_point(&tile[warp][k][lane], d.tpts + (size_t)(base + ids[k]) * 32 + lane);
+                    cp_async_wait_all();
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < kBatch; ++k) {
+                        if (k >= cnt) break;
+                        float b6[6];
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) b6[q] = __shfl_sync(0xffffffffu, bl[q], ids[k]);
+                        const bool need = valid && box_gap2(lx, ly, lz, hx, hy, hz, b6) <= ub_f(gbest);
+                        if (__ballot_sync(0xffffffffu, need)) {
+                            ++n_scanned;
+                            if (need) {
+#pragma unroll
+                                for (int j = 0; j < PPL; ++j) {
+                                    const TPoint<T> c = tile[warp][k][sub + j * LPQ];
+                                    const T dd = sqdist(qx, qy, qz, c.x, c.y, c.z);
+                                    if (dd < best || (dd == best && c.idx < bidx)) {
+                                        best = dd; bidx = c.idx;
+                                        bx = c.x; by = c.y; bz = c.z;
+                                    }
                                 }
                             }
+                            gbest = group_min<T, LPQ>(best);
                         }
-                        __syncwarp();
                     }
-                    cur = nxt;
-                    lb = nb;
+                    __syncwarp();
                 }
-                UB = warp_max(valid ? ub_f(best) : 0.f);
+                refresh_bounds();
             }
         }
+    }
+    group_argmin<T, LPQ>(best, bidx, bx, by, bz);
+    if (d.nn_stats != nullptr && lane == 0) {
+        unsigned long long* o = d.nn_stats + 4 * (size_t)(blockIdx.x * kWarps + warp);
+        o[0] = (unsigned long long)(clock64() - t_start);
+        o[1] = n_super; o[2] = n_staged; o[3] = n_scanned;
     }
 
     // ---- outputs ------------------------------------------------------------
     const int wb = (MODE == NRR_MODE_RAW) ? 0 : (st->vk ^ 1);
     double dv2 = 0.0;
-    if (valid) {
+    if (valid && sub == 0) {
         d.rho[i] = bidx;
         d.d2[i] = best;
         d.u[i] = bx; d.u[P + i] = by; d.u[2 * P + i] = bz;
@@ -175,10 +275,10 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
             vh[i] = qx; vh[P + i] = qy; vh[2 * P + i] = qz;
             if (MODE == NRR_MODE_PASS && st->pending_stop && st->have_vk) {
                 const T* vk = d.vhat + (size_t)(wb ^ 1) * 3 * P;
-                const double ex = (double)qx - (double)vk[i];
-                const double ey = (double)qy - (double)vk[P + i];
-                const double ez = (double)qz - (double)vk[2 * P + i];
-                dv2 = ex * ex + ey * ey + ez * ez;
+                const double dx = (double)qx - (double)vk[i];
+                const double dy = (double)qy - (double)vk[P + i];
+                const double dz = (double)qz - (double)vk[2 * P + i];
+                dv2 = dx * dx + dy * dy + dz * dz;
             }
         }
     }
@@ -213,17 +313,28 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
 
 }  // namespace
 
-template <typename T>
-cudaError_t nrr_launch_nn(const DevProblem<T>& d, int mode, int grid, cudaStream_t s) {
-    (void)grid;
-    const int g = (d.P + kThreads - 1) / kThreads;
+template <typename T, int LPQ>
+cudaError_t launch_nn_lpq(const DevProblem<T>& d, int mode, cudaStream_t s) {
+    const int per_cta = kWarps * (32 / LPQ);
+    const int g = (d.P + per_cta - 1) / per_cta;
     if (g == 0) return cudaSuccess;
     switch (mode) {
-        case NRR_MODE_PASS: nn_kernel<T, NRR_MODE_PASS><<<g, kThreads, 0, s>>>(d); break;
-        case NRR_MODE_EVAL: nn_kernel<T, NRR_MODE_EVAL><<<g, kThreads, 0, s>>>(d); break;
-        default: nn_kernel<T, NRR_MODE_RAW><<<g, kThreads, 0, s>>>(d); break;
+        case NRR_MODE_PASS: nn_kernel<T, NRR_MODE_PASS, LPQ><<<g, kThreads, 0, s>>>(d); break;
+        case NRR_MODE_EVAL: nn_kernel<T, NRR_MODE_EVAL, LPQ><<<g, kThreads, 0, s>>>(d); break;
+        default: nn_kernel<T, NRR_MODE_RAW, LPQ><<<g, kThreads, 0, s>>>(d); break;
     }
     return cudaGetLastError();
+}
+
+// lanes per query: the launch tuning parameter of the search (1, 2, 4 or 8)
+template <typename T>
+cudaError_t nrr_launch_nn(const DevProblem<T>& d, int mode, int lanes_per_query, cudaStream_t s) {
+    switch (lanes_per_query) {
+        case 1: return launch_nn_lpq<T, 1>(d, mode, s);
+        case 8: return launch_nn_lpq<T, 8>(d, mode, s);
+        case 2: return launch_nn_lpq<T, 2>(d, mode, s);
+        default: return launch_nn_lpq<T, 4>(d, mode, s);
+    }
 }
 
 template cudaError_t nrr_launch_nn<float>(const DevProblem<float>&, int, int, cudaStream_t);

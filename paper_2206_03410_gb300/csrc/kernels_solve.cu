@@ -12,7 +12,13 @@
 // partial sums, and after the barrier every CTA adds all partials in the same
 // fixed order. The barrier is bounded: after about two seconds of waiting it
 // records NRR_E_TIMEOUT in the state and the kernel returns.
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
 #include "nrr_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -68,15 +74,15 @@ struct Red {
     // Sums K per-thread values over the whole grid; out[] valid in all threads.
     // Every CTA adds the partials of all CTAs in the same fixed order, so the
     // result is identical everywhere and deterministic.
-    template <int K>
-    __device__ bool run(Barrier& bar, const double (&v)[K], double* s_tmp, double (&out)[K]) {
+    template <int K, typename A>
+    __device__ bool run(Barrier& bar, const A (&v)[K], double* s_tmp, double (&out)[K]) {
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            double x = v[j];
+            A x = v[j];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) s_tmp[w * kMaxRed + j] = x;
+            if (lane == 0) s_tmp[w * kMaxRed + j] = (double)x;
         }
         __syncthreads();
         if (threadIdx.x < K) {
@@ -114,36 +120,48 @@ struct Red {
     }
 };
 
-// 4x4 SPD inverse by Cholesky, in double. Returns false if not positive definite.
-__device__ bool spd_inverse4(const double A[16], double Inv[16]) {
-    double L[16] = {0};
+// 4x4 SPD inverse by Cholesky in type F. Returns false if not positive definite.
+template <typename F>
+__device__ bool spd_inverse4(const F A[16], F Inv[16]) {
+    F L[16] = {0};
     for (int j = 0; j < 4; ++j) {
-        double s = A[4 * j + j];
+        F s = A[4 * j + j];
         for (int k = 0; k < j; ++k) s -= L[4 * j + k] * L[4 * j + k];
-        if (!(s > 0)) return false;
+        if (!(s > F(0))) return false;
         L[4 * j + j] = sqrt(s);
         for (int i = j + 1; i < 4; ++i) {
-            double t = A[4 * i + j];
+            F t = A[4 * i + j];
             for (int k = 0; k < j; ++k) t -= L[4 * i + k] * L[4 * j + k];
             L[4 * i + j] = t / L[4 * j + j];
         }
     }
     // columns of inv(L), then Inv = inv(L)^T inv(L)
-    double Li[16] = {0};
+    F Li[16] = {0};
     for (int c = 0; c < 4; ++c) {
         for (int i = 0; i < 4; ++i) {
-            double t = (i == c) ? 1.0 : 0.0;
+            F t = (i == c) ? F(1) : F(0);
             for (int k = 0; k < i; ++k) t -= L[4 * i + k] * Li[4 * k + c];
             Li[4 * i + c] = t / L[4 * i + i];
         }
     }
     for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) {
-            double s = 0.0;
+            F s = 0;
             for (int k = 0; k < 4; ++k) s += Li[4 * k + i] * Li[4 * k + j];
             Inv[4 * i + j] = s;
         }
     return true;
+}
+
+// four consecutive values from shared memory with vector loads
+__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
 
 // y[a] = sum over blocks of row n of K[b][a][t] * vec[col(b)][t][c], a = 0..3
@@ -163,11 +181,171 @@ __device__ __forceinline__ void spmv_pair(const DevProblem<T>& d, const T* vec, 
     }
 }
 
+// Anderson mix of Sec. 3.3.4 (Eq. AA_solution) after the solve, shared by
+// both solve kernels: G = d.G holds the MM minimiser G(X^(k)) and d.X holds
+// X^(k) for the pairs of nodes [n0, n1) of this CTA. Updates the difference
+// rings, the Gram matrix (double), solves for theta (every CTA identically),
+// writes X^(k+1) and the bookkeeping of the state (CTA 0).
+template <typename T, class Reducer>
+__device__ __noinline__ bool aa_mix_and_finish(const DevProblem<T>& d, Reducer& red, int n0, int n1,
+                                  int first_solve, int aa_count, int aa_head, int it, double rel,
+                                  double* s_theta) {
+    NrrState* st = d.st;
+    const int N = d.N;
+    const int aa_m = d.aa_m;
+    const int npairs = (n1 - n0) * 3;
+    long long* ts = (d.solve_stats != nullptr && blockIdx.x == 0 && threadIdx.x == 0) ? d.solve_stats + 48 : nullptr;
+    int tsn = 0;
+    auto stamp = [&]() { if (ts && tsn < 12) ts[tsn++] = clock64(); };
+    stamp();
+    const bool insert = !first_solve && aa_m > 0;
+    const int slot = aa_head;
+    const int mk = insert ? min(aa_count + 1, aa_m) : 0;
+    const size_t n12 = (size_t)N * 12;
+    // the stored Gram entries, prefetched in parallel for thread 0's solve
+    __shared__ double s_gram[NRR_AA_MMAX * NRR_AA_MMAX];
+    for (int k = threadIdx.x; k < NRR_AA_MMAX * NRR_AA_MMAX; k += blockDim.x) s_gram[k] = st->gram[k];
+    __syncthreads();
+    if (mk > 0) {
+        // products and per-warp sums in T, sums over warps and CTAs in double
+        T aa[kMaxRed];
+        double sa[kMaxRed];
+#pragma unroll
+        for (int j = 0; j < kMaxRed; ++j) aa[j] = 0;
+        for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
+            const int n = n0 + idx / 3, c = idx % 3;
+            // all loads of the four elements first (they are independent)
+            T g[4], xk[4], fp[4], gp[4], dfo[4][NRR_AA_MMAX];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int e = 12 * n + 3 * a + c;
+                g[a] = d.G[e]; xk[a] = d.X[e]; fp[a] = d.Fprev[e]; gp[a] = d.Gprev[e];
+#pragma unroll
+                for (int b = 0; b < NRR_AA_MMAX; ++b) dfo[a][b] = (b < mk && b != slot) ? d.dF[b * n12 + e] : T(0);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int e = 12 * n + 3 * a + c;
+                const T f = g[a] - xk[a];
+                const T dfn = f - fp[a];
+                d.dF[slot * n12 + e] = dfn;
+                d.dG[slot * n12 + e] = g[a] - gp[a];
+#pragma unroll
+                for (int b = 0; b < NRR_AA_MMAX; ++b) {
+                    const T dfb = (b == slot) ? dfn : dfo[a][b];
+                    aa[b] += dfb * dfn;                 // Gram row of the new slot
+                    aa[NRR_AA_MMAX + b] += dfb * f;     // right-hand side
+                }
+            }
+        }
+        stamp();
+        if (!red.template run<kMaxRed, T>(aa, sa)) return false;
+        stamp();
+        if (threadIdx.x == 0) {
+            double Gm[NRR_AA_MMAX * NRR_AA_MMAX], rhs[NRR_AA_MMAX], th[NRR_AA_MMAX];
+            double tr = 0.0;
+            for (int a = 0; a < mk; ++a) {
+                for (int b = 0; b < mk; ++b) {
+                    double v;
+                    if (a == slot) v = sa[b];
+                    else if (b == slot) v = sa[a];
+                    else v = s_gram[a * NRR_AA_MMAX + b];
+                    Gm[a * NRR_AA_MMAX + b] = v;
+                }
+                rhs[a] = sa[NRR_AA_MMAX + a];
+                tr += Gm[a * NRR_AA_MMAX + a];
+            }
+            const double lam = 1e-10 * tr / mk;
+            for (int a = 0; a < mk; ++a) Gm[a * NRR_AA_MMAX + a] += lam;
+            // Cholesky solve in place
+            bool ok = true;
+            for (int j = 0; j < mk && ok; ++j) {
+                double s = Gm[j * NRR_AA_MMAX + j];
+                for (int k = 0; k < j; ++k) s -= Gm[j * NRR_AA_MMAX + k] * Gm[j * NRR_AA_MMAX + k];
+                if (!(s > 0)) { ok = false; break; }
+                const double l = sqrt(s);
+                Gm[j * NRR_AA_MMAX + j] = l;
+                for (int i = j + 1; i < mk; ++i) {
+                    double t = Gm[i * NRR_AA_MMAX + j];
+                    for (int k = 0; k < j; ++k) t -= Gm[i * NRR_AA_MMAX + k] * Gm[j * NRR_AA_MMAX + k];
+                    Gm[i * NRR_AA_MMAX + j] = t / l;
+                }
+            }
+            double nrm = 0.0;
+            if (ok) {
+                for (int i = 0; i < mk; ++i) {
+                    double t = rhs[i];
+                    for (int k = 0; k < i; ++k) t -= Gm[i * NRR_AA_MMAX + k] * th[k];
+                    th[i] = t / Gm[i * NRR_AA_MMAX + i];
+                }
+                for (int i = mk - 1; i >= 0; --i) {
+                    double t = th[i];
+                    for (int k = i + 1; k < mk; ++k) t -= Gm[k * NRR_AA_MMAX + i] * th[k];
+                    th[i] = t / Gm[i * NRR_AA_MMAX + i];
+                }
+                for (int i = 0; i < mk; ++i) nrm += th[i] * th[i];
+                ok = isfinite(nrm) && sqrt(nrm) <= 1e4;
+            }
+            for (int i = 0; i < NRR_AA_MMAX; ++i) s_theta[i] = (ok && i < mk) ? th[i] : 0.0;
+            stamp();
+            if (blockIdx.x == 0) {
+                for (int b = 0; b < mk; ++b) {
+                    st->gram[slot * NRR_AA_MMAX + b] = sa[b];
+                    st->gram[b * NRR_AA_MMAX + slot] = sa[b];
+                }
+                st->aa_mk = ok ? mk : 0;
+                for (int i = 0; i < NRR_AA_MMAX; ++i) st->theta[i] = s_theta[i];
+            }
+        }
+        __syncthreads();
+    } else if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->aa_mk = 0;
+    }
+    stamp();
+    // X^(k+1) = G - sum theta_b dG_b; keep F and G for the next differences
+    for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
+        const int n = n0 + idx / 3, c = idx % 3;
+        for (int a = 0; a < 4; ++a) {
+            const int e = 12 * n + 3 * a + c;
+            const T g = d.G[e];
+            const T f = g - d.X[e];
+            T xn = g;
+            for (int b = 0; b < mk; ++b) xn -= (T)s_theta[b] * d.dG[b * n12 + e];
+            d.X[e] = xn;
+            d.Fprev[e] = f;
+            d.Gprev[e] = g;
+        }
+    }
+    stamp();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->aa_count = mk;
+        st->aa_head = insert ? (aa_head + 1) % aa_m : aa_head;
+        st->n_solves_stage += 1;
+        st->n_solves += 1;
+        st->pending_stop = 1;
+        st->solved = 1;
+        st->pcg_iters = it;
+        st->pcg_res = rel;
+    }
+    return true;
+}
+
+struct GridReducer {
+    Barrier& bar;
+    Red& red;
+    double* s_tmp;
+    template <int K, typename A>
+    __device__ bool run(const A (&v)[K], double (&out)[K]) {
+        return red.run<K, A>(bar, v, s_tmp, out);
+    }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
     __shared__ double s_tmp[(kThreads / 32) * kMaxRed];
     __shared__ int s_flag;
     __shared__ double s_theta[NRR_AA_MMAX];
+    __shared__ double s_scal[12];
     NrrState* st = d.st;
     if (st->done || st->skip) return;
     const int N = d.N;
@@ -222,11 +400,17 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
             acc[3 + c] += (double)rr[a] * (double)rr[a];
         }
     }
-    if (!red.run<9>(bar, acc, s_tmp, sums)) return;
+    if (!red.run<9, double>(bar, acc, s_tmp, sums)) return;
+    // CG scalars: thread 0 computes them (double), shared memory broadcasts
     double rz[3] = {sums[0], sums[1], sums[2]};
     double bb[3] = {sums[6], sums[7], sums[8]};
-    double rel = 0.0;
-    for (int c = 0; c < 3; ++c) rel = fmax(rel, sqrt(sums[3 + c] / fmax(bb[c], 1e-300)));
+    if (threadIdx.x == 0) {
+        double rel0 = 0.0;
+        for (int c = 0; c < 3; ++c) rel0 = fmax(rel0, sqrt(sums[3 + c] / fmax(bb[c], 1e-300)));
+        s_scal[4] = rel0;
+    }
+    __syncthreads();
+    double rel = s_scal[4];
     int it = 0;
     double beta_c[3] = {0, 0, 0};
     while (rel > tol && it < d.pcg_max) {
@@ -247,9 +431,10 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
                 a3[c] += (double)pn * (double)qn;
             }
         }
-        if (!red.run<3>(bar, a3, s_tmp, s3)) return;
-        double al[3];
-        for (int c = 0; c < 3; ++c) al[c] = s3[c] != 0.0 ? rz[c] / s3[c] : 0.0;
+        if (!red.run<3, double>(bar, a3, s_tmp, s3)) return;
+        if (threadIdx.x < 3) s_scal[threadIdx.x] = s3[threadIdx.x] != 0.0 ? rz[threadIdx.x] / s3[threadIdx.x] : 0.0;
+        __syncthreads();
+        const double al[3] = {s_scal[0], s_scal[1], s_scal[2]};
         double a6[6] = {0, 0, 0, 0, 0, 0}, s6[6];
         for (int idx = threadIdx.x; idx < npairs; idx += kThreads) {
             const int n = n0 + idx / 3, c = idx % 3;
@@ -269,125 +454,321 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
                 a6[3 + c] += (double)rr[a] * (double)rr[a];
             }
         }
-        if (!red.run<6>(bar, a6, s_tmp, s6)) return;
+        if (!red.run<6, double>(bar, a6, s_tmp, s6)) return;
         ++it;
-        rel = 0.0;
-        for (int c = 0; c < 3; ++c) {
-            beta_c[c] = rz[c] != 0.0 ? s6[c] / rz[c] : 0.0;
-            rz[c] = s6[c];
-            rel = fmax(rel, sqrt(s6[3 + c] / fmax(bb[c], 1e-300)));
-        }
-    }
-
-    // ---- Anderson acceleration (Eq. AA_solution) ---------------------------
-    const bool insert = !first_solve && aa_m > 0;
-    const int slot = aa_head;
-    const int mk = insert ? min(aa_count + 1, aa_m) : 0;
-    const size_t n12 = (size_t)N * 12;
-    if (mk > 0) {
-        double aa[kMaxRed], sa[kMaxRed];
-#pragma unroll
-        for (int j = 0; j < kMaxRed; ++j) aa[j] = 0.0;
-        for (int idx = threadIdx.x; idx < npairs; idx += kThreads) {
-            const int n = n0 + idx / 3, c = idx % 3;
-            for (int a = 0; a < 4; ++a) {
-                const int e = 12 * n + 3 * a + c;
-                const T g = d.G[e];
-                const T f = g - d.X[e];
-                const T dfn = f - d.Fprev[e];
-                d.dF[slot * n12 + e] = dfn;
-                d.dG[slot * n12 + e] = g - d.Gprev[e];
-                for (int b = 0; b < mk; ++b) {
-                    const T dfb = (b == slot) ? dfn : d.dF[b * n12 + e];
-                    aa[b] += (double)dfb * (double)dfn;                 // Gram row of the new slot
-                    aa[NRR_AA_MMAX + b] += (double)dfb * (double)f;     // right-hand side
-                }
-            }
-        }
-        if (!red.run<kMaxRed>(bar, aa, s_tmp, sa)) return;
+        if (threadIdx.x < 3) s_scal[8 + threadIdx.x] = rz[threadIdx.x] != 0.0 ? s6[threadIdx.x] / rz[threadIdx.x] : 0.0;
         if (threadIdx.x == 0) {
-            double Gm[NRR_AA_MMAX * NRR_AA_MMAX], rhs[NRR_AA_MMAX], th[NRR_AA_MMAX];
-            double tr = 0.0;
-            for (int a = 0; a < mk; ++a) {
-                for (int b = 0; b < mk; ++b) {
-                    double v;
-                    if (a == slot) v = sa[b];
-                    else if (b == slot) v = sa[a];
-                    else v = st->gram[a * NRR_AA_MMAX + b];
-                    Gm[a * NRR_AA_MMAX + b] = v;
-                }
-                rhs[a] = sa[NRR_AA_MMAX + a];
-                tr += Gm[a * NRR_AA_MMAX + a];
-            }
-            const double lam = 1e-10 * tr / mk;
-            for (int a = 0; a < mk; ++a) Gm[a * NRR_AA_MMAX + a] += lam;
-            // Cholesky solve in place
-            bool ok = true;
-            for (int j = 0; j < mk && ok; ++j) {
-                double s = Gm[j * NRR_AA_MMAX + j];
-                for (int k = 0; k < j; ++k) s -= Gm[j * NRR_AA_MMAX + k] * Gm[j * NRR_AA_MMAX + k];
-                if (!(s > 0)) { ok = false; break; }
-                const double l = sqrt(s);
-                Gm[j * NRR_AA_MMAX + j] = l;
-                for (int i = j + 1; i < mk; ++i) {
-                    double t = Gm[i * NRR_AA_MMAX + j];
-                    for (int k = 0; k < j; ++k) t -= Gm[i * NRR_AA_MMAX + k] * Gm[j * NRR_AA_MMAX + k];
-                    Gm[i * NRR_AA_MMAX + j] = t / l;
-                }
-            }
-            double nrm = 0.0;
-            if (ok) {
-                for (int i = 0; i < mk; ++i) {
-                    double t = rhs[i];
-                    for (int k = 0; k < i; ++k) t -= Gm[i * NRR_AA_MMAX + k] * th[k];
-                    th[i] = t / Gm[i * NRR_AA_MMAX + i];
-                }
-                for (int i = mk - 1; i >= 0; --i) {
-                    double t = th[i];
-                    for (int k = i + 1; k < mk; ++k) t -= Gm[k * NRR_AA_MMAX + i] * th[k];
-                    th[i] = t / Gm[i * NRR_AA_MMAX + i];
-                }
-                for (int i = 0; i < mk; ++i) nrm += th[i] * th[i];
-                ok = isfinite(nrm) && sqrt(nrm) <= 1e4;
-            }
-            for (int i = 0; i < NRR_AA_MMAX; ++i) s_theta[i] = (ok && i < mk) ? th[i] : 0.0;
-            if (blockIdx.x == 0) {
-                for (int b = 0; b < mk; ++b) {
-                    st->gram[slot * NRR_AA_MMAX + b] = sa[b];
-                    st->gram[b * NRR_AA_MMAX + slot] = sa[b];
-                }
-                st->aa_mk = ok ? mk : 0;
-                for (int i = 0; i < NRR_AA_MMAX; ++i) st->theta[i] = s_theta[i];
-            }
+            double rel0 = 0.0;
+            for (int c = 0; c < 3; ++c) rel0 = fmax(rel0, sqrt(s6[3 + c] / fmax(bb[c], 1e-300)));
+            s_scal[4] = rel0;
         }
         __syncthreads();
-    } else if (threadIdx.x == 0 && blockIdx.x == 0) {
-        st->aa_mk = 0;
+        for (int c = 0; c < 3; ++c) { beta_c[c] = s_scal[8 + c]; rz[c] = s6[c]; }
+        rel = s_scal[4];
+        __syncthreads();
     }
-    // X^(k+1) = G - sum theta_b dG_b; keep F and G for the next differences
-    for (int idx = threadIdx.x; idx < npairs; idx += kThreads) {
-        const int n = n0 + idx / 3, c = idx % 3;
-        for (int a = 0; a < 4; ++a) {
-            const int e = 12 * n + 3 * a + c;
-            const T g = d.G[e];
-            const T f = g - d.X[e];
-            T xn = g;
-            for (int b = 0; b < mk; ++b) xn -= (T)s_theta[b] * d.dG[b * n12 + e];
-            d.X[e] = xn;
-            d.Fprev[e] = f;
-            d.Gprev[e] = g;
+
+    GridReducer gr{bar, red, s_tmp};
+    aa_mix_and_finish<T>(d, gr, n0, n1, first_solve, aa_count, aa_head, it, rel, s_theta);
+}
+
+
+// ---------------------------------------------------------------------------
+// Cluster variant: one thread-block cluster of C CTAs (C <= 16) solves the
+// system. Each CTA keeps the K rows of its nodes, their block-Jacobi
+// inverses and its slice of z in shared memory; the SpMV reads neighbouring
+// z values through distributed shared memory, and reductions and barriers
+// use the hardware cluster barrier, so an iteration touches no global
+// memory. Used when the node count and the K rows fit (chosen at creation).
+// ---------------------------------------------------------------------------
+constexpr int kClusterThreads = 768;
+constexpr int kSpmvChunk = 4;
+constexpr int kClusterWarps = kClusterThreads / 32;
+
+// Cluster-wide sum of K values per thread. Per-thread values (type W) are
+// reduced within each warp by a shuffle tree in W, then in R: over the warps
+// of a CTA (warp 0), and over the CTAs of the cluster. The cross-CTA step is
+// push-based: warp 0 of every CTA stores its CTA's sums into a slot of every
+// CTA's shared memory before the cluster barrier, so after the barrier each
+// warp reads local shared memory only. All trees have a fixed shape and
+// floating-point addition is commutative, so every thread of every CTA gets
+// bitwise the same sums on every run.
+constexpr int kClusterMaxCtas = 16;
+
+template <typename R>
+struct ClusterSum {
+    R* s_red;   // [2][kClusterMaxCtas][kMaxRed], written by every CTA
+    R* s_tmp;   // [kClusterWarps][kMaxRed]
+    int buf;
+    template <int K, typename W>
+    __device__ void run(const W (&v)[K], R (&out)[K]) {
+        cg::cluster_group cl = cg::this_cluster();
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        W x[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) x[j] = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) x[j] += __shfl_xor_sync(0xffffffffu, x[j], o);
         }
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) s_tmp[w * kMaxRed + j] = (R)x[j];
+        }
+        __syncthreads();
+        const int nr = (int)cl.num_blocks();
+        if (w == 0) {
+            const int nw = (int)(blockDim.x >> 5);
+            R y[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) y[j] = lane < nw ? s_tmp[lane * kMaxRed + j] : R(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) y[j] += __shfl_xor_sync(0xffffffffu, y[j], o);
+            }
+            if (lane < nr) {
+                R* dst = cl.map_shared_rank(s_red, lane) + (buf * kClusterMaxCtas + (int)cl.block_rank()) * kMaxRed;
+#pragma unroll
+                for (int j = 0; j < K; ++j) dst[j] = y[j];
+            }
+        }
+        cl.sync();   // release/acquire: every CTA's slot is written
+        if (sizeof(R) == 4 || w == 0) {
+            // float: every warp adds the slots itself (no further barrier);
+            // double: warp 0 only (double adds are slow), then a broadcast
+            R z[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) z[j] = lane < nr ? s_red[(buf * kClusterMaxCtas + lane) * kMaxRed + j] : R(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) z[j] += __shfl_xor_sync(0xffffffffu, z[j], o);
+            }
+#pragma unroll
+            for (int j = 0; j < K; ++j) out[j] = z[j];
+            if (sizeof(R) != 4 && lane == 0) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) s_tmp[j] = z[j];
+            }
+        }
+        if (sizeof(R) != 4) {
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < K; ++j) out[j] = s_tmp[j];
+            __syncthreads();
+        }
+        buf ^= 1;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->aa_count = mk;
-        st->aa_head = insert ? (aa_head + 1) % aa_m : aa_head;
-        st->n_solves_stage += 1;
-        st->n_solves += 1;
-        st->pending_stop = 1;
-        st->solved = 1;
-        st->pcg_iters = it;
-        st->pcg_res = rel;
+};
+
+// Adapter with the interface aa_mix_and_finish expects (double results).
+struct ClusterReducer {
+    ClusterSum<double> sum;
+    template <int K, typename A>
+    __device__ bool run(const A (&v)[K], double (&out)[K]) {
+        sum.template run<K, A>(v, out);
+        return true;
     }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevProblem<T> d, int cap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ T t_red[2 * kClusterMaxCtas * kMaxRed];
+    __shared__ T t_tmp[kClusterWarps * kMaxRed];
+    __shared__ double d_red[2 * kClusterMaxCtas * kMaxRed];
+    __shared__ double d_tmp[kClusterWarps * kMaxRed];
+    __shared__ double s_theta[NRR_AA_MMAX];
+    NrrState* st = d.st;
+    if (st->done || st->skip) return;   // the same decision in every CTA
+    cg::cluster_group cl = cg::this_cluster();
+    long long* ts = (d.solve_stats != nullptr && blockIdx.x == 0 && threadIdx.x == 0) ? d.solve_stats : nullptr;
+    int tsn = 0;
+    auto stamp = [&]() { if (ts && tsn < 64) ts[tsn++] = clock64(); };
+    stamp();
+    const int C = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int N = d.N;
+    const int per = (N + C - 1) / C;
+    const int n0 = min(N, rank * per), n1 = min(N, n0 + per);
+    const int b0 = d.bsr_ptr[n0];
+    const int nbl = d.bsr_ptr[n1] - b0;
+    // shared layout (identical offsets in every CTA): K rows, z slice,
+    // preconditioner blocks, packed column (owner rank, local node)
+    T* Kloc = reinterpret_cast<T*>(smem);
+    T* zloc = Kloc + (size_t)cap * 16;
+    T* Mloc = zloc + (size_t)per * 12;
+    unsigned short* colloc = reinterpret_cast<unsigned short*>(Mloc + (size_t)per * 16);
+    const int tid = threadIdx.x, bd = blockDim.x;
+    {
+        // the K rows of this CTA's nodes, as 16-byte vectors
+        using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        const int nv = nbl * 16 * (int)sizeof(T) / 16;
+        const V4* src = reinterpret_cast<const V4*>(d.Kv + (size_t)b0 * 16);
+        V4* dst = reinterpret_cast<V4*>(Kloc);
+#pragma unroll 4
+        for (int k = tid; k < nv; k += bd) dst[k] = __ldg(src + k);
+    }
+    for (int k = tid; k < nbl; k += bd) {
+        const int col = d.bsr_col[b0 + k];
+        const int owner = col / per;
+        colloc[k] = (unsigned short)((owner << 12) | (col - owner * per));
+    }
+    __syncthreads();
+    for (int n = n0 + tid; n < n1; n += bd) {
+        int bdg = d.bsr_ptr[n] - b0;
+        while ((int)d.bsr_col[b0 + bdg] != n) ++bdg;
+        // the preconditioner only steers CG: its inverse is formed in T
+        T A[16], I[16];
+        for (int t = 0; t < 16; ++t) A[t] = Kloc[16 * bdg + t];
+        if (!spd_inverse4(A, I)) {
+            for (int t = 0; t < 16; ++t) I[t] = 0;
+            for (int t = 0; t < 4; ++t) I[5 * t] = A[5 * t] > T(0) ? T(1) / A[5 * t] : T(1);
+        }
+        for (int t = 0; t < 16; ++t) Mloc[16 * (n - n0) + t] = I[t];
+    }
+    __syncthreads();
+
+    stamp();
+    ClusterSum<T> red{t_red, t_tmp, 0};
+    const int first_solve = st->n_solves_stage == 0;
+    const int aa_count = st->aa_count, aa_head = st->aa_head;
+    const T tol = d.pcg_tol;
+    const bool has = tid < (n1 - n0) * 3;
+    const int ln = has ? tid / 3 : 0;
+    const int n = n0 + ln, c = tid % 3;
+    const int rb0 = has ? d.bsr_ptr[n] - b0 : 0, rb1 = has ? d.bsr_ptr[n + 1] - b0 : 0;
+    T x[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, q[4] = {0, 0, 0, 0};
+    const T* Mi = Mloc + 16 * ln;
+
+    // r = B - K X^(k), z = M^-1 r; per-thread values go to the slot of its column
+    T acc9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, s9[9];
+    if (has) {
+        T y[4] = {0, 0, 0, 0};
+        for (int b = rb0; b < rb1; ++b) {
+            const int k = d.bsr_col[b0 + b];
+            const T* Kb = Kloc + 16 * b;
+            T v[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) v[t] = d.X[12 * k + 3 * t + c];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                y[a] += Kb[4 * a] * v[0] + Kb[4 * a + 1] * v[1] + Kb[4 * a + 2] * v[2] + Kb[4 * a + 3] * v[3];
+        }
+        T bb = 0, rz = 0, rr = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const T bv = d.Bv[12 * n + 3 * a + c];
+            x[a] = d.X[12 * n + 3 * a + c];
+            r[a] = bv - y[a];
+            bb += bv * bv;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const T zz = Mi[4 * a] * r[0] + Mi[4 * a + 1] * r[1] + Mi[4 * a + 2] * r[2] + Mi[4 * a + 3] * r[3];
+            zloc[12 * ln + 3 * a + c] = zz;
+            rz += r[a] * zz;
+            rr += r[a] * r[a];
+        }
+        acc9[c] = rz; acc9[3 + c] = rr; acc9[6 + c] = bb;
+    }
+    stamp();
+    red.template run<9, T>(acc9, s9);
+    stamp();
+    // CG scalars: every thread holds the same reduced values
+    T rzc[3] = {s9[0], s9[1], s9[2]};
+    const T bbc[3] = {s9[6] > T(0) ? s9[6] : T(1e-30), s9[7] > T(0) ? s9[7] : T(1e-30),
+                      s9[8] > T(0) ? s9[8] : T(1e-30)};
+    const T tol2 = tol * tol;
+    // converged when every column has |r|^2 <= tol^2 |B|^2
+    bool done = s9[3] <= tol2 * bbc[0] && s9[4] <= tol2 * bbc[1] && s9[5] <= tol2 * bbc[2];
+    T relmax2 = fmax(fmax(s9[3] / bbc[0], s9[4] / bbc[1]), s9[5] / bbc[2]);
+    int it = 0;
+    T beta_t = 0;
+    while (!done && it < d.pcg_max) {
+        T a3[3] = {0, 0, 0}, s3[3];
+        if (has) {
+            T w[4] = {0, 0, 0, 0};
+            // blocks in chunks: all remote (DSMEM) loads of a chunk are issued
+            // before any of them is used
+            for (int b = rb0; b < rb1; b += kSpmvChunk) {
+                T v[kSpmvChunk][4];
+#pragma unroll
+                for (int u = 0; u < kSpmvChunk; ++u) {
+                    if (b + u < rb1) {
+                        const unsigned cw = colloc[b + u];
+                        const T* zr = cl.map_shared_rank(zloc, (int)(cw >> 12)) + 12 * (cw & 0xfff);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) v[u][t] = zr[3 * t + c];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kSpmvChunk; ++u) {
+                    if (b + u < rb1) {
+                        const T* Kb = Kloc + 16 * (b + u);
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            T k4[4];
+                            load4(Kb + 4 * a, k4);
+                            w[a] += k4[0] * v[u][0] + k4[1] * v[u][1] + k4[2] * v[u][2] + k4[3] * v[u][3];
+                        }
+                    }
+                }
+            }
+            T pq = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const T zz = zloc[12 * ln + 3 * a + c];
+                p[a] = (it == 0) ? zz : zz + beta_t * p[a];
+                q[a] = (it == 0) ? w[a] : w[a] + beta_t * q[a];
+                pq += p[a] * q[a];
+            }
+            a3[c] = pq;
+        }
+        if (it < 8) stamp();
+        red.template run<3, T>(a3, s3);   // also: every CTA finished reading z
+        if (it < 8) stamp();
+        const T alpha_t = s3[c] != T(0) ? rzc[c] / s3[c] : T(0);
+        T a6[6] = {0, 0, 0, 0, 0, 0}, s6[6];
+        if (has) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                x[a] += alpha_t * p[a];
+                r[a] -= alpha_t * q[a];
+            }
+            T rz = 0, rr = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const T zz = Mi[4 * a] * r[0] + Mi[4 * a + 1] * r[1] + Mi[4 * a + 2] * r[2] + Mi[4 * a + 3] * r[3];
+                zloc[12 * ln + 3 * a + c] = zz;
+                rz += r[a] * zz;
+                rr += r[a] * r[a];
+            }
+            a6[c] = rz; a6[3 + c] = rr;
+        }
+        if (it < 8) stamp();
+        red.template run<6, T>(a6, s6);   // also: the new z is visible to the cluster
+        if (it < 8) stamp();
+        ++it;
+        beta_t = rzc[c] != T(0) ? s6[c] / rzc[c] : T(0);
+        rzc[0] = s6[0]; rzc[1] = s6[1]; rzc[2] = s6[2];
+        done = s6[3] <= tol2 * bbc[0] && s6[4] <= tol2 * bbc[1] && s6[5] <= tol2 * bbc[2];
+        relmax2 = fmax(fmax(s6[3] / bbc[0], s6[4] / bbc[1]), s6[5] / bbc[2]);
+    }
+    if (has) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) d.G[12 * n + 3 * a + c] = x[a];
+    }
+    stamp();
+    ClusterReducer dred{ClusterSum<double>{d_red, d_tmp, 0}};
+    aa_mix_and_finish<T>(d, dred, n0, n1, first_solve, aa_count, aa_head, it, sqrt((double)relmax2),
+                         s_theta);
+    stamp();
+    if (ts) ts[63] = tsn;
+    // no CTA may leave while another can still read its shared memory
+    cl.sync();
 }
 
 }  // namespace
@@ -420,3 +801,60 @@ template cudaError_t nrr_launch_solve<float>(const DevProblem<float>&, int, cuda
 template cudaError_t nrr_launch_solve<double>(const DevProblem<double>&, int, cudaStream_t, bool);
 template int nrr_solve_max_blocks_per_sm<float>();
 template int nrr_solve_max_blocks_per_sm<double>();
+
+template <typename T>
+size_t nrr_solve_cluster_smem(int cap, int per) {
+    return (size_t)cap * 16 * sizeof(T) + (size_t)per * 12 * sizeof(T) + (size_t)per * 16 * sizeof(T) +
+           (size_t)cap * sizeof(unsigned short) + 16;
+}
+
+// Prepares the cluster kernel for C CTAs with the given shared memory;
+// returns the number of clusters that can be co-resident (0: not usable).
+template <typename T>
+int nrr_solve_cluster_setup(int C, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(solve_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && C > 8)
+        e = cudaFuncSetAttribute(solve_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    e = cudaOccupancyMaxActiveClusters(&nc, solve_cluster_kernel<T>, &cfg);
+    if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+    return nc;
+}
+
+template <typename T>
+cudaError_t nrr_launch_solve_cluster(const DevProblem<T>& d, int C, int cap, size_t smem, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, solve_cluster_kernel<T>, d, cap);
+}
+
+int nrr_solve_cluster_threads() { return kClusterThreads; }
+
+template size_t nrr_solve_cluster_smem<float>(int, int);
+template size_t nrr_solve_cluster_smem<double>(int, int);
+template int nrr_solve_cluster_setup<float>(int, size_t);
+template int nrr_solve_cluster_setup<double>(int, size_t);
+template cudaError_t nrr_launch_solve_cluster<float>(const DevProblem<float>&, int, int, size_t, cudaStream_t);
+template cudaError_t nrr_launch_solve_cluster<double>(const DevProblem<double>&, int, int, size_t, cudaStream_t);

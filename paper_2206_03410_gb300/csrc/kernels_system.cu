@@ -96,6 +96,44 @@ __device__ void closest_rotation(const double A[9], double R[9]) {
         for (int b = 0; b < 3; ++b) R[3 * a + b] = u1[a] * v1[b] + u2[a] * v2[b] + u3[a] * v3[b];
 }
 
+// Closest rotation for det(A) > 0: the orthogonal polar factor of A, by
+// Newton's iteration X <- (X + X^{-T}) / 2 (Higham, "Computing the polar
+// decomposition - with applications", SIAM J. Sci. Stat. Comput. 1986),
+// with X^{-T} = cof(X) / det(X). Quadratic convergence; near-orthogonal A
+// (the usual case) takes 4-6 steps. Returns false if it did not converge,
+// in which case the SVD route is used.
+__device__ bool polar_rotation(const double A[9], double R[9]) {
+    double X[9];
+    for (int k = 0; k < 9; ++k) X[k] = A[k];
+    for (int iter = 0; iter < 30; ++iter) {
+        const double c0 = X[4] * X[8] - X[5] * X[7];
+        const double c1 = X[5] * X[6] - X[3] * X[8];
+        const double c2 = X[3] * X[7] - X[4] * X[6];
+        const double det = X[0] * c0 + X[1] * c1 + X[2] * c2;
+        if (!(det > 0)) return false;
+        const double id = 1.0 / det;
+        double C[9];
+        C[0] = c0; C[1] = c1; C[2] = c2;
+        C[3] = X[2] * X[7] - X[1] * X[8];
+        C[4] = X[0] * X[8] - X[2] * X[6];
+        C[5] = X[1] * X[6] - X[0] * X[7];
+        C[6] = X[1] * X[5] - X[2] * X[4];
+        C[7] = X[2] * X[3] - X[0] * X[5];
+        C[8] = X[0] * X[4] - X[1] * X[3];
+        double diff = 0.0;
+        for (int k = 0; k < 9; ++k) {
+            const double nx = 0.5 * (X[k] + C[k] * id);
+            diff += (nx - X[k]) * (nx - X[k]);
+            X[k] = nx;
+        }
+        if (diff < 1e-30) {
+            for (int k = 0; k < 9; ++k) R[k] = X[k];
+            return true;
+        }
+    }
+    return false;
+}
+
 __device__ __forceinline__ double block_sum(double x, double* sh) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -164,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
         double A[9], R[9];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) A[3 * a + b] = (double)Xn[3 * b + a];
-        closest_rotation(A, R);
+        if (!polar_rotation(A, R)) closest_rotation(A, R);
         double s = 0.0;
         for (int k = 0; k < 9; ++k) {
             const double df = A[k] - R[k];

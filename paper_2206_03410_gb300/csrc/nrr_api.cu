@@ -15,6 +15,13 @@
 int nrr_solve_threads();
 template <typename T>
 int nrr_solve_max_blocks_per_sm();
+int nrr_solve_cluster_threads();
+template <typename T>
+size_t nrr_solve_cluster_smem(int cap, int per);
+template <typename T>
+int nrr_solve_cluster_setup(int C, size_t smem);
+template <typename T>
+cudaError_t nrr_launch_solve_cluster(const DevProblem<T>& d, int C, int cap, size_t smem, cudaStream_t s);
 
 namespace {
 
@@ -53,6 +60,10 @@ struct nrr_ctx {
     bool use_graph = true;
     bool coop = true;
     int grid_energy = 0, grid_asm = 0, grid_solve = 0, num_sms = 0;
+    int nn_lpq = 4;                    // closest points: lanes per query (1, 2, 4, 8)
+    size_t nn_stats_n = 0;             // per-warp search counters (debug, opt-in)
+    int cl_C = 0, cl_cap = 0;          // cluster solve: CTAs per cluster, K blocks per CTA
+    size_t cl_smem = 0;
     double diag = 0.0;
     double nu_a0 = 0.0, nu_r0 = 0.0;   // first-stage parameters
     bool failed = false;
@@ -149,15 +160,52 @@ nrr_status push_state(nrr_ctx* c) {
 }
 
 template <typename T>
+cudaError_t launch_solve(nrr_ctx* c) {
+    if (c->cl_C > 0) return nrr_launch_solve_cluster<T>(prob<T>(c), c->cl_C, c->cl_cap, c->cl_smem, c->stream);
+    return nrr_launch_solve<T>(prob<T>(c), c->grid_solve, c->stream, c->coop);
+}
+
+// Chooses the cluster solve when one cluster of 16 (or 8) CTAs can hold the
+// K rows of its nodes in shared memory; otherwise the grid-wide solve.
+template <typename T>
+void choose_solver(nrr_ctx* c) {
+    c->cl_C = 0;
+    if (std::getenv("NRR_NO_CLUSTER")) return;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const int N = c->N;
+    for (int C : {16, 8}) {
+        const int per = (N + C - 1) / C;
+        if (per * 3 > nrr_solve_cluster_threads() || per >= 4096) continue;
+        int cap = 0;
+        for (int r = 0; r < C; ++r) {
+            const int n0 = std::min(N, r * per), n1 = std::min(N, n0 + per);
+            cap = std::max(cap, c->bsr_ptr[(size_t)n1] - c->bsr_ptr[(size_t)n0]);
+        }
+        const size_t smem = nrr_solve_cluster_smem<T>(cap, per);
+        if (smem + 8192 > (size_t)optin) continue;
+        if (nrr_solve_cluster_setup<T>(C, smem) >= 1) {
+            c->cl_C = C;
+            c->cl_cap = cap;
+            c->cl_smem = smem;
+            return;
+        }
+    }
+}
+
+template <typename T>
 cudaError_t launch_pass(nrr_ctx* c) {
     DevProblem<T>& d = prob<T>(c);
-    cudaError_t e = nrr_launch_nn<T>(d, NRR_MODE_PASS, 0, c->stream);
+    cudaError_t e = nrr_launch_nn<T>(d, NRR_MODE_PASS, c->nn_lpq, c->stream);
     if (e != cudaSuccess) return e;
     e = nrr_launch_energy<T>(d, NRR_MODE_PASS, c->grid_energy, c->stream);
     if (e != cudaSuccess) return e;
     e = nrr_launch_assemble<T>(d, c->grid_asm, c->stream);
     if (e != cudaSuccess) return e;
-    return nrr_launch_solve<T>(d, c->grid_solve, c->stream, c->coop);
+    return launch_solve<T>(c);
 }
 
 cudaError_t launch_pass_any(nrr_ctx* c) { return c->fp64 ? launch_pass<double>(c) : launch_pass<float>(c); }
@@ -215,7 +263,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     const int64_t P = c->P, Tn = c->T;
     const HostGraph& g = c->hg;
     const int K = g.K, N = c->N;
-    // bbox of source and target together for the Morton codes
+    // bbox of source and target together for the Hilbert codes
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t i = 0; i < P; ++i)
         for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], (double)src[3 * i + a]); hi[a] = std::max(hi[a], (double)src[3 * i + a]); }
@@ -226,9 +274,9 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         c->diag = std::sqrt(dx * dx + dy * dy + dz * dz);
     }
     std::vector<uint64_t> src_codes, tgt_codes;
-    nrr_morton_order(src.data(), P, lo, hi, c->src_order, &src_codes);
+    nrr_curve_order(src.data(), P, lo, hi, c->src_order, &src_codes);
     std::vector<int> tgt_order;
-    nrr_morton_order(tgt.data(), Tn, lo, hi, tgt_order, &tgt_codes);
+    nrr_curve_order(tgt.data(), Tn, lo, hi, tgt_order, &tgt_codes);
     c->src_rank.assign((size_t)P, 0);
     for (int64_t ii = 0; ii < P; ++ii) c->src_rank[(size_t)c->src_order[(size_t)ii]] = (int)ii;
 
@@ -324,7 +372,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         }
         for (int a = 0; a < 3; ++a) pbar[(size_t)(a * P + ii)] = (T)acc[a];
     }
-    // target leaves (32 Morton-consecutive points) and super tiles
+    // target leaves (32 curve-consecutive points) and super tiles
     const int nl = (int)((Tn + NRR_LEAF - 1) / NRR_LEAF);
     const int ns = (nl + 31) / 32;
     c->n_leaves = nl;
@@ -361,7 +409,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
             }
         std::memcpy(&sbox[(size_t)S * 6], b, sizeof(b));
     }
-    // initial correspondence guess: target point nearest in Morton order
+    // initial correspondence guess: the target point next along the curve
     std::vector<T> u0((size_t)(3 * P));
     std::vector<int> rho0((size_t)P);
     for (int64_t ii = 0; ii < P; ++ii) {
@@ -432,13 +480,27 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     const int max_ctas = std::max({c->grid_energy, c->grid_solve, 1});
     CK(dalloc(c, &d.partials, (size_t)2 * max_ctas * NRR_PARTIAL_STRIDE));
     d.st = c->d_state;
+    d.nn_stats = nullptr;
+    d.solve_stats = nullptr;
+    if (std::getenv("NRR_SOLVE_STATS")) {
+        long long* ss = nullptr;
+        CK(dalloc(c, &ss, 64));
+        d.solve_stats = ss;
+    }
+    if (std::getenv("NRR_NN_STATS")) {
+        const size_t warps = (size_t)(P + 7) / 8 + 64;   // enough for any lanes-per-query
+        unsigned long long* ns = nullptr;
+        CK(dalloc(c, &ns, warps * 4));
+        d.nn_stats = ns;
+        c->nn_stats_n = warps;
+    }
     return NRR_OK;
 }
 
 template <typename T>
 nrr_status median_distance(nrr_ctx* c, double* out) {
     DevProblem<T>& d = prob<T>(c);
-    CK(nrr_launch_nn<T>(d, NRR_MODE_RAW, 0, c->stream));
+    CK(nrr_launch_nn<T>(d, NRR_MODE_RAW, c->nn_lpq, c->stream));
     std::vector<T> d2((size_t)c->P);
     CK(cudaMemcpyAsync(d2.data(), d.d2, sizeof(T) * (size_t)c->P, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -578,6 +640,10 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     c->N = (int)c->hg.nodes.size();
     c->E2 = (int)c->hg.r.size();
     // launch geometry
+    if (const char* e = std::getenv("NRR_NN_LPQ")) {
+        const int v = std::atoi(e);
+        if (v == 1 || v == 2 || v == 4 || v == 8) c->nn_lpq = v;
+    }
     c->grid_energy = 2 * c->num_sms;
     c->grid_asm = std::max(1, std::min(8 * c->num_sms, (c->N + c->E2 + 31) / 32));
     {
@@ -593,6 +659,7 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     std::memset(c->h_state, 0, sizeof(NrrState));
     nrr_status st = c->fp64 ? build_device<double>(c, src, tgt) : build_device<float>(c, src, tgt);
     if (st != NRR_OK) return st;
+    if (c->fp64) choose_solver<double>(c); else choose_solver<float>(c);
     NrrState& s = *c->h_state;
     s.k_alpha = prm.k_alpha; s.k_beta = prm.k_beta;
     s.alpha_fixed = prm.alpha; s.beta_fixed = prm.beta;
@@ -693,16 +760,16 @@ nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[4]) {
         for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
             if (c->fp64) {
                 DevProblem<double>& d = c->dd;
-                e = s == 0 ? nrr_launch_nn<double>(d, NRR_MODE_PASS, 0, c->stream)
+                e = s == 0 ? nrr_launch_nn<double>(d, NRR_MODE_PASS, c->nn_lpq, c->stream)
                   : s == 1 ? nrr_launch_energy<double>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
                   : s == 2 ? nrr_launch_assemble<double>(d, c->grid_asm, c->stream)
-                           : nrr_launch_solve<double>(d, c->grid_solve, c->stream, c->coop);
+                           : launch_solve<double>(c);
             } else {
                 DevProblem<float>& d = c->df;
-                e = s == 0 ? nrr_launch_nn<float>(d, NRR_MODE_PASS, 0, c->stream)
+                e = s == 0 ? nrr_launch_nn<float>(d, NRR_MODE_PASS, c->nn_lpq, c->stream)
                   : s == 1 ? nrr_launch_energy<float>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
                   : s == 2 ? nrr_launch_assemble<float>(d, c->grid_asm, c->stream)
-                           : nrr_launch_solve<float>(d, c->grid_solve, c->stream, c->coop);
+                           : launch_solve<float>(c);
             }
             if (e == cudaSuccess) e = cudaEventRecord(ev[s + 1], c->stream);
         }
@@ -749,12 +816,12 @@ nrr_status nrr_energy(nrr_ctx* c, const double* X, double out_terms[4]) {
     if (c->fp64) {
         if (X) { st = write_X<double>(c, c->dd.Xeval, X); if (st != NRR_OK) return st; }
         else CK(cudaMemcpyAsync(c->dd.Xeval, c->dd.X, sizeof(double) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
-        CK(nrr_launch_nn<double>(c->dd, NRR_MODE_EVAL, 0, c->stream));
+        CK(nrr_launch_nn<double>(c->dd, NRR_MODE_EVAL, c->nn_lpq, c->stream));
         CK(nrr_launch_energy<double>(c->dd, NRR_MODE_EVAL, c->grid_energy, c->stream));
     } else {
         if (X) { st = write_X<float>(c, c->df.Xeval, X); if (st != NRR_OK) return st; }
         else CK(cudaMemcpyAsync(c->df.Xeval, c->df.X, sizeof(float) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
-        CK(nrr_launch_nn<float>(c->df, NRR_MODE_EVAL, 0, c->stream));
+        CK(nrr_launch_nn<float>(c->df, NRR_MODE_EVAL, c->nn_lpq, c->stream));
         CK(nrr_launch_energy<float>(c->df, NRR_MODE_EVAL, c->grid_energy, c->stream));
     }
     st = pull_state(c);
@@ -798,6 +865,28 @@ nrr_status nrr_get_transforms(nrr_ctx* c, double* X) {
 nrr_status nrr_get_mm_solution(nrr_ctx* c, double* G) {
     if (!c || !G) return fail(c, NRR_E_INVALID, "NULL argument");
     return c->fp64 ? read_X<double>(c, c->dd.Gprev, G) : read_X<float>(c, c->df.Gprev, G);
+}
+
+nrr_status nrr_get_search_stats(nrr_ctx* c, unsigned long long* out, int64_t max_warps, int64_t* n_warps) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    const unsigned long long* src = c->fp64 ? c->dd.nn_stats : c->df.nn_stats;
+    const int per_warp = 32 / c->nn_lpq;
+    const int64_t nw = (c->P + per_warp - 1) / per_warp;
+    if (n_warps) *n_warps = src ? nw : 0;
+    if (!src || !out) return NRR_OK;
+    const int64_t n = std::min<int64_t>(nw, max_warps);
+    CK(cudaMemcpyAsync(out, src, sizeof(unsigned long long) * 4 * (size_t)n, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRR_OK;
+}
+
+nrr_status nrr_get_solve_stats(nrr_ctx* c, long long out[64]) {
+    if (!c || !out) return fail(c, NRR_E_INVALID, "NULL argument");
+    const long long* src = c->fp64 ? c->dd.solve_stats : c->df.solve_stats;
+    if (!src) { std::memset(out, 0, 64 * sizeof(long long)); return NRR_OK; }
+    CK(cudaMemcpyAsync(out, src, 64 * sizeof(long long), cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRR_OK;
 }
 
 nrr_status nrr_get_info(nrr_ctx* c, nrr_step_info* info) {

@@ -1,11 +1,11 @@
 // Device data layout and kernel entry points of one registration problem.
 //
 // HBM layout (T = float for the mixed path, double for the FP64 path):
-//   source, internal Morton order:  v [3][P] SoA; influence lists in CSR
+//   source, internal Hilbert-curve order:  v [3][P] SoA; influence lists in CSR
 //     (infl_ptr [P+1], infl_node/infl_w [nnz]); per pass v_hat [2][3][P],
 //     closest target coordinates u [3][P], caller index rho [P], d2 [P],
 //     alignment weights wa [P].
-//   target, internal Morton order:  tpts [n_leaves*32] {x,y,z,caller idx},
+//   target, internal Hilbert-curve order:  tpts [n_leaves*32] {x,y,z,caller idx},
 //     padded with +inf points; AABBs of 32-point leaves (float [6]) and of
 //     32-leaf super tiles (float [6]).
 //   graph: nodes p [N][3]; directed pairs (e_i, e_j, e_r) sorted by (i, j)
@@ -87,6 +87,11 @@ struct DevProblem {
     // reductions
     double* partials;   // [max_ctas * NRR_PARTIAL_STRIDE]
     NrrState* st;
+    // optional per-warp counters of the closest-point search (NULL: off):
+    // [warps][4] = {cycles, super tiles visited, leaves staged, leaves scanned}
+    unsigned long long* nn_stats;
+    // optional phase timestamps of the cluster solve (CTA 0, thread 0; NULL: off)
+    long long* solve_stats;
 };
 
 #define NRR_PARTIAL_STRIDE 32
@@ -95,7 +100,7 @@ enum NrrMode { NRR_MODE_PASS = 0, NRR_MODE_EVAL = 1, NRR_MODE_RAW = 2 };
 
 // Launch helpers (defined in the kernel translation units).
 template <typename T>
-cudaError_t nrr_launch_nn(const DevProblem<T>& d, int mode, int grid, cudaStream_t s);
+cudaError_t nrr_launch_nn(const DevProblem<T>& d, int mode, int lanes_per_query, cudaStream_t s);
 template <typename T>
 cudaError_t nrr_launch_energy(const DevProblem<T>& d, int mode, int grid, cudaStream_t s);
 template <typename T>

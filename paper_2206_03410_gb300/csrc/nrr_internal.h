@@ -63,7 +63,7 @@ struct HostGraph {
 // graph_build.cpp
 double nrr_mean_spacing(const double* V, int64_t P, int k);
 void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g);
-void nrr_morton_order(const float* pts, int64_t n, const double lo[3],
+void nrr_curve_order(const float* pts, int64_t n, const double lo[3],
                       const double hi[3], std::vector<int>& order,
                       std::vector<uint64_t>* codes_sorted);
 

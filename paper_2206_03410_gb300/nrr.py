@@ -108,6 +108,8 @@ _SIGS = [
     ("nrr_get_system", ctypes.c_int, [_VP, _VP, _VP]),
     ("nrr_get_mm_solution", ctypes.c_int, [_VP, _VP]),
     ("nrr_get_info", ctypes.c_int, [_VP, ctypes.POINTER(NrrStepInfo)]),
+    ("nrr_get_search_stats", ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    ("nrr_get_solve_stats", ctypes.c_int, [_VP, _VP]),
     ("nrr_align_energy_noalloc", ctypes.c_int, [_VP, _I64, ctypes.c_double, _VP, _VP, _VP]),
     ("nrr_last_error", ctypes.c_char_p, [_VP]),
 ]
@@ -330,6 +332,24 @@ def nrr_get_system(ctx, dense: bool = True):
     B = np.zeros((4 * N, 3), dtype=np.float64)
     _check(load().nrr_get_system(ctx, _ptr(K), _ptr(B)), ctx)
     return K, B
+
+
+def nrr_get_search_stats(ctx):
+    """Per-warp counters of the last closest-point search ([warps, 4]:
+    cycles, super tiles, leaves staged, leaves scanned) or None."""
+    n = ctypes.c_int64()
+    _check(load().nrr_get_search_stats(ctx, None, 0, ctypes.byref(n)), ctx)
+    if n.value == 0:
+        return None
+    out = np.zeros((n.value, 4), dtype=np.uint64)
+    _check(load().nrr_get_search_stats(ctx, _ptr(out), n.value, ctypes.byref(n)), ctx)
+    return out
+
+
+def nrr_get_solve_stats(ctx) -> np.ndarray:
+    out = np.zeros(64, dtype=np.int64)
+    _check(load().nrr_get_solve_stats(ctx, _ptr(out)), ctx)
+    return out
 
 
 def nrr_get_info(ctx) -> NrrStepInfo:
