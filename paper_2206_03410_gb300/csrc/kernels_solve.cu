@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
 // memory. Used when the node count and the K rows fit (chosen at creation).
 // ---------------------------------------------------------------------------
 constexpr int kClusterThreads = 768;
-constexpr int kSpmvChunk = 4;
+constexpr int kSpmvChunk = 1;   // blocks per thread whose z rows are in flight together
 constexpr int kClusterWarps = kClusterThreads / 32;
 
 // Cluster-wide sum of K values per thread. Per-thread values (type W) are
@@ -500,6 +500,7 @@ struct ClusterSum {
     R* s_red;   // [2][kClusterMaxCtas][kMaxRed], written by every CTA
     R* s_tmp;   // [kClusterWarps][kMaxRed]
     int buf;
+    int active_warps;   // warps whose threads may hold non-zero values
     template <int K, typename W>
     __device__ void run(const W (&v)[K], R (&out)[K]) {
         cg::cluster_group cl = cg::this_cluster();
@@ -507,19 +508,21 @@ struct ClusterSum {
         W x[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) x[j] = v[j];
+        if (w < active_warps) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int j = 0; j < K; ++j) x[j] += __shfl_xor_sync(0xffffffffu, x[j], o);
-        }
-        if (lane == 0) {
+                for (int j = 0; j < K; ++j) x[j] += __shfl_xor_sync(0xffffffffu, x[j], o);
+            }
+            if (lane == 0) {
 #pragma unroll
-            for (int j = 0; j < K; ++j) s_tmp[w * kMaxRed + j] = (R)x[j];
+                for (int j = 0; j < K; ++j) s_tmp[w * kMaxRed + j] = (R)x[j];
+            }
         }
         __syncthreads();
         const int nr = (int)cl.num_blocks();
         if (w == 0) {
-            const int nw = (int)(blockDim.x >> 5);
+            const int nw = active_warps;
             R y[K];
 #pragma unroll
             for (int j = 0; j < K; ++j) y[j] = lane < nw ? s_tmp[lane * kMaxRed + j] : R(0);
@@ -632,14 +635,21 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     __syncthreads();
 
     stamp();
-    ClusterSum<T> red{t_red, t_tmp, 0};
+    // warps that hold work: four threads per node in the SpMV and the updates
+    const int active_warps = min((int)(bd >> 5), ((n1 - n0) * 4 + 31) / 32);
+    ClusterSum<T> red{t_red, t_tmp, 0, max(active_warps, 1)};
     const int first_solve = st->n_solves_stage == 0;
     const int aa_count = st->aa_count, aa_head = st->aa_head;
     const T tol = d.pcg_tol;
-    const bool has = tid < (n1 - n0) * 3;
-    const int ln = has ? tid / 3 : 0;
-    const int n = n0 + ln, c = tid % 3;
-    const int rb0 = has ? d.bsr_ptr[n] - b0 : 0, rb1 = has ? d.bsr_ptr[n + 1] - b0 : 0;
+    // four threads per node: in the SpMV each takes every fourth block of
+    // the node's row for all three columns; in the CG updates thread s < 3
+    // owns column c = s of the node
+    const int s4 = tid & 3;
+    const bool node_ok = (tid >> 2) < (n1 - n0);
+    const bool has = node_ok && s4 < 3;
+    const int ln = node_ok ? tid >> 2 : 0;
+    const int n = n0 + ln, c = s4 < 3 ? s4 : 0;
+    const int rb0 = node_ok ? d.bsr_ptr[n] - b0 : 0, rb1 = node_ok ? d.bsr_ptr[n + 1] - b0 : 0;
     T x[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, q[4] = {0, 0, 0, 0};
     const T* Mi = Mloc + 16 * ln;
 
@@ -689,34 +699,53 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     T beta_t = 0;
     while (!done && it < d.pcg_max) {
         T a3[3] = {0, 0, 0}, s3[3];
-        if (has) {
-            T w[4] = {0, 0, 0, 0};
-            // blocks in chunks: all remote (DSMEM) loads of a chunk are issued
-            // before any of them is used
-            for (int b = rb0; b < rb1; b += kSpmvChunk) {
-                T v[kSpmvChunk][4];
+        // w = K z for the node: this thread's share of the row's blocks, all
+        // three columns, with 16-byte loads of K rows (local) and z rows
+        // (local or another CTA's shared memory)
+        T wv[12];
 #pragma unroll
-                for (int u = 0; u < kSpmvChunk; ++u) {
-                    if (b + u < rb1) {
-                        const unsigned cw = colloc[b + u];
-                        const T* zr = cl.map_shared_rank(zloc, (int)(cw >> 12)) + 12 * (cw & 0xfff);
+        for (int k = 0; k < 12; ++k) wv[k] = 0;
+        for (int b = rb0 + s4; b < rb1; b += 4 * kSpmvChunk) {
+            T zr[kSpmvChunk][12];
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) v[u][t] = zr[3 * t + c];
-                    }
-                }
+            for (int u = 0; u < kSpmvChunk; ++u) {
+                if (b + 4 * u < rb1) {
+                    const unsigned cw = colloc[b + 4 * u];
+                    const T* zp = cl.map_shared_rank(zloc, (int)(cw >> 12)) + 12 * (cw & 0xfff);
 #pragma unroll
-                for (int u = 0; u < kSpmvChunk; ++u) {
-                    if (b + u < rb1) {
-                        const T* Kb = Kloc + 16 * (b + u);
-#pragma unroll
-                        for (int a = 0; a < 4; ++a) {
-                            T k4[4];
-                            load4(Kb + 4 * a, k4);
-                            w[a] += k4[0] * v[u][0] + k4[1] * v[u][1] + k4[2] * v[u][2] + k4[3] * v[u][3];
-                        }
+                    for (int k = 0; k < 12; k += 4) {
+                        T t4[4];
+                        load4(zp + k, t4);
+                        zr[u][k] = t4[0]; zr[u][k + 1] = t4[1]; zr[u][k + 2] = t4[2]; zr[u][k + 3] = t4[3];
                     }
                 }
             }
+#pragma unroll
+            for (int u = 0; u < kSpmvChunk; ++u) {
+                if (b + 4 * u < rb1) {
+                    const T* Kb = Kloc + 16 * (b + 4 * u);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        T k4[4];
+                        load4(Kb + 4 * a, k4);
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc)
+                            wv[3 * a + cc] += k4[0] * zr[u][cc] + k4[1] * zr[u][3 + cc] + k4[2] * zr[u][6 + cc] +
+                                              k4[3] * zr[u][9 + cc];
+                    }
+                }
+            }
+        }
+        // the node's four partial results (lanes 4k .. 4k+3 of a warp)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            wv[k] += __shfl_xor_sync(0xffffffffu, wv[k], 1);
+            wv[k] += __shfl_xor_sync(0xffffffffu, wv[k], 2);
+        }
+        if (has) {
+            T w[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) w[a] = wv[3 * a + c];
             T pq = 0;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
@@ -762,7 +791,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
         for (int a = 0; a < 4; ++a) d.G[12 * n + 3 * a + c] = x[a];
     }
     stamp();
-    ClusterReducer dred{ClusterSum<double>{d_red, d_tmp, 0}};
+    ClusterReducer dred{ClusterSum<double>{d_red, d_tmp, 0, (int)(bd >> 5)}};
     aa_mix_and_finish<T>(d, dred, n0, n1, first_solve, aa_count, aa_head, it, sqrt((double)relmax2),
                          s_theta);
     stamp();

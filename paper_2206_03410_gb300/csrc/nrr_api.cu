@@ -179,7 +179,7 @@ void choose_solver(nrr_ctx* c) {
     const int N = c->N;
     for (int C : {16, 8}) {
         const int per = (N + C - 1) / C;
-        if (per * 3 > nrr_solve_cluster_threads() || per >= 4096) continue;
+        if (per * 4 > nrr_solve_cluster_threads() || per >= 4096) continue;
         int cap = 0;
         for (int r = 0; r < C; ++r) {
             const int n0 = std::min(N, r * per), n1 = std::min(N, n0 + per);
