@@ -128,3 +128,51 @@ def energy_terms(V, U, graph, X, nu_a, nu_r, rho=None):
 
 def total_energy(terms: dict, alpha: float, beta: float) -> float:
     return terms["E_align"] + alpha * terms["E_reg"] + beta * terms["E_rot"]
+
+
+def energy_gradient(V, U, graph, X, nu_a, nu_r, alpha, beta, rho=None):
+    """Gradient of E (Eq. objective_func) with the closest points held at
+    their values at X (rho is piecewise constant in X), the node positions
+    p_j and the weights w_ij held constant.
+
+    d psi_nu(x) / d(x^2) = exp(-x^2 / 2nu^2) / (2nu^2) = w (the surrogate's
+    weight), so with r_i = v_hat_i - u_rho(i):
+      dE/dX_j  = sum_i 2 w^a_i w_ij [v_i - p_j; 1] r_i^T
+               + alpha sum_(i,j) 2 w^r_ij (h_j D_ij^T at X_j, h_i D_ij^T at X_i)
+               + beta 2 [(A_j - proj_R(A_j))^T; 0]
+      dE/dv_i  = 2 w^a_i (sum_j w_ij A_j)^T r_i
+    (the rotation term's derivative is 2 (A - proj_R(A)) because proj_R(A)
+    minimises the distance to the rotation group).
+    Returns (grad_X [N,12], grad_v [P,3])."""
+    V = np.asarray(V, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64)
+    t = energy_terms(V, U, graph, X, nu_a, nu_r, rho=rho)
+    r = t["vhat"] - U[t["rho"]]
+    wa = np.exp(-t["d2"] / (2 * nu_a * nu_a)) / (2 * nu_a * nu_a)
+    N = graph.N
+    gX = np.zeros((N, 4, 3))
+    gv = np.zeros_like(V)
+    A = A_of(X)
+    for s in range(graph.nidx.shape[1]):
+        j = graph.nidx[:, s]
+        m = np.nonzero(j >= 0)[0]
+        jj = j[m]
+        wij = graph.w[m, s]
+        a = np.concatenate([V[m] - graph.p[jj], np.ones((len(m), 1))], axis=1)   # [n,4]
+        contrib = 2.0 * (wa[m] * wij)[:, None, None] * a[:, :, None] * r[m][:, None, :]
+        np.add.at(gX, jj, contrib)
+        gv[m] += 2.0 * wa[m, None] * wij[:, None] * np.einsum("nab,na->nb", A[jj], r[m])
+    if len(graph.dpair):
+        D = t["D"]
+        wr = np.exp(-np.sum(D * D, axis=1) / (2 * nu_r * nu_r)) / (2 * nu_r * nu_r)
+        i, j = graph.dpair[:, 0], graph.dpair[:, 1]
+        rr = graph.r
+        hj = np.concatenate([rr[:, None] * (graph.p[i] - graph.p[j]), rr[:, None]], axis=1)
+        hi = np.zeros((len(i), 4))
+        hi[:, 3] = -rr
+        cj = 2.0 * alpha * wr[:, None, None] * hj[:, :, None] * D[:, None, :]
+        ci = 2.0 * alpha * wr[:, None, None] * hi[:, :, None] * D[:, None, :]
+        np.add.at(gX, j, cj)
+        np.add.at(gX, i, ci)
+    gX[:, :3, :] += 2.0 * beta * np.transpose(A - t["R"], (0, 2, 1))
+    return gX.reshape(N, 12), gv

@@ -402,6 +402,124 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(DevProblem<T> d) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Gradient of E (Eq. objective_func) at the evaluated iterate (Xeval), with
+// the closest points fixed at their values there (piecewise-constant rho):
+//   dE/dX_n = sum_i 2 w^a_i w_in [v_i - p_n; 1] (v_hat_i - u_i)^T
+//           + 2 alpha sum_{pairs with n} w^r h D^T + 2 beta [(A_n - R_n)^T; 0]
+// (the surrogate of Sec. 3.3.1 touches E with the same gradient). A group of
+// 8 lanes owns one node and sums the contribution list of its diagonal
+// block in a fixed order; deterministic.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) gradient_kernel(DevProblem<T> d, double* __restrict__ gX) {
+    NrrState* st = d.st;
+    const int lane8 = threadIdx.x & 7;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int P = d.P;
+    const T alpha = (T)st->alpha, beta = (T)st->beta;
+    const T* vh = d.vhat + (size_t)(st->vk ^ 1) * 3 * P;   // written by the evaluation
+    const T* X = d.Xeval;
+    for (int n0 = gwarp * 4; n0 < d.N; n0 += nwarps * 4) {
+        const int n = min(n0 + ((threadIdx.x & 31) >> 3), d.N - 1);
+        const bool active = (n0 + ((threadIdx.x & 31) >> 3)) < d.N;
+        int bdg = d.bsr_ptr[n];
+        while (d.bsr_col[bdg] != n) ++bdg;
+        const T pnx = d.p[3 * n], pny = d.p[3 * n + 1], pnz = d.p[3 * n + 2];
+        T g[12];
+#pragma unroll
+        for (int t = 0; t < 12; ++t) g[t] = 0;
+        const int e_end = active ? d.ent_ptr[bdg + 1] : 0;
+        for (int e = d.ent_ptr[bdg] + lane8; e < e_end; e += 8) {
+            const int i = d.ent[e] >> 6;
+            const T wn = d.ent_w[2 * e];
+            const T c = (T)2 * d.wa[i] * wn;
+            const T an[4] = {d.v[i] - pnx, d.v[P + i] - pny, d.v[2 * P + i] - pnz, (T)1};
+            const T rx = vh[i] - d.u[i], ry = vh[P + i] - d.u[P + i], rz = vh[2 * P + i] - d.u[2 * P + i];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const T ca = c * an[a];
+                g[3 * a + 0] += ca * rx;
+                g[3 * a + 1] += ca * ry;
+                g[3 * a + 2] += ca * rz;
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+#pragma unroll
+            for (int t = 0; t < 12; ++t) g[t] += __shfl_xor_sync(0xffffffffu, g[t], o);
+        }
+        if (lane8 != 0 || !active) continue;
+        // regularisation: pairs (n, j) with h_i = [0,0,0,-r] at X_n, and the
+        // reverse pairs (j, n) with h_j = r [(p_j - p_n)^T, 1] at X_n
+        const T* Xn = X + 12 * n;
+        for (int e = d.adj_ptr[n]; e < d.adj_ptr[n + 1]; ++e) {
+            for (int side = 0; side < 2; ++side) {
+                const int ee = side == 0 ? e : d.e_rev[e];
+                const int a_ = d.e_i[ee], b_ = d.e_j[ee];   // D_ab: a = first node, b = second
+                const T r = d.e_r[ee];
+                const T* Xa = X + 12 * a_;
+                const T* Xb = X + 12 * b_;
+                const T dx = d.p[3 * a_] - d.p[3 * b_];
+                const T dy = d.p[3 * a_ + 1] - d.p[3 * b_ + 1];
+                const T dz = d.p[3 * a_ + 2] - d.p[3 * b_ + 2];
+                const T D[3] = {r * ((Xb[0] * dx + Xb[3] * dy + Xb[6] * dz - dx) + (Xb[9] - Xa[9])),
+                                r * ((Xb[1] * dx + Xb[4] * dy + Xb[7] * dz - dy) + (Xb[10] - Xa[10])),
+                                r * ((Xb[2] * dx + Xb[5] * dy + Xb[8] * dz - dz) + (Xb[11] - Xa[11]))};
+                const T w2 = (T)2 * alpha * d.wr[ee];
+                if (side == 0) {
+                    // n is the first node of the pair: h at X_n = [0,0,0,-r]
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) g[9 + cc] -= w2 * r * D[cc];
+                } else {
+                    // n is the second node: h at X_n = r [(p_a - p_n)^T, 1]
+                    const T h[4] = {r * dx, r * dy, r * dz, r};
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) g[3 * a + cc] += w2 * h[a] * D[cc];
+                }
+            }
+        }
+        // rotation term: 2 beta (A_n - R_n)^T in rows 0..2
+        const T* R = d.Rm + 9 * n;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) g[3 * a + cc] += (T)2 * beta * (Xn[3 * a + cc] - R[3 * cc + a]);
+#pragma unroll
+        for (int t = 0; t < 12; ++t) gX[12 * n + t] = (double)g[t];
+    }
+}
+
+// dE/dv_i = 2 w^a_i (sum_j w_ij A_j)^T (v_hat_i - u_i), written in the
+// caller's point order (order[internal] = caller index).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) src_gradient_kernel(DevProblem<T> d, const int* __restrict__ order,
+                                                                double* __restrict__ gv) {
+    NrrState* st = d.st;
+    const int P = d.P;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const T* vh = d.vhat + (size_t)(st->vk ^ 1) * 3 * P;
+    const T rx = vh[i] - d.u[i], ry = vh[P + i] - d.u[P + i], rz = vh[2 * P + i] - d.u[2 * P + i];
+    const T c = (T)2 * d.wa[i];
+    T o[3] = {0, 0, 0};
+    for (int s = d.infl_ptr[i]; s < d.infl_ptr[i + 1]; ++s) {
+        const T* Xj = d.Xeval + 12 * d.infl_node[s];
+        const T w = d.infl_w[s];
+        // (A_j^T r): A_j[b][a] = Xj[3a + b], so (A^T r)_a = sum_b Xj[3a + b] r_b
+#pragma unroll
+        for (int a = 0; a < 3; ++a) o[a] += w * (Xj[3 * a] * rx + Xj[3 * a + 1] * ry + Xj[3 * a + 2] * rz);
+    }
+    const int ci = order[i];
+    gv[3 * ci + 0] = (double)(c * o[0]);
+    gv[3 * ci + 1] = (double)(c * o[1]);
+    gv[3 * ci + 2] = (double)(c * o[2]);
+}
+
 }  // namespace
 
 template <typename T>
@@ -421,3 +539,14 @@ template cudaError_t nrr_launch_energy<float>(const DevProblem<float>&, int, int
 template cudaError_t nrr_launch_energy<double>(const DevProblem<double>&, int, int, cudaStream_t);
 template cudaError_t nrr_launch_assemble<float>(const DevProblem<float>&, int, cudaStream_t);
 template cudaError_t nrr_launch_assemble<double>(const DevProblem<double>&, int, cudaStream_t);
+
+template <typename T>
+cudaError_t nrr_launch_gradient(const DevProblem<T>& d, double* grad_X, double* grad_v, const int* order,
+                                int grid, cudaStream_t s) {
+    if (grad_X) gradient_kernel<T><<<grid, kThreads, 0, s>>>(d, grad_X);
+    if (grad_v) src_gradient_kernel<T><<<(d.P + kThreads - 1) / kThreads, kThreads, 0, s>>>(d, order, grad_v);
+    return cudaGetLastError();
+}
+
+template cudaError_t nrr_launch_gradient<float>(const DevProblem<float>&, double*, double*, const int*, int, cudaStream_t);
+template cudaError_t nrr_launch_gradient<double>(const DevProblem<double>&, double*, double*, const int*, int, cudaStream_t);

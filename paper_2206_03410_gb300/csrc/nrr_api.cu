@@ -61,6 +61,8 @@ struct nrr_ctx {
     bool coop = true;
     int grid_energy = 0, grid_asm = 0, grid_solve = 0, num_sms = 0;
     int nn_lpq = 4;                    // closest points: lanes per query (1, 2, 4, 8)
+    int* d_order = nullptr;            // internal -> caller source index (gradients)
+    double* d_grad = nullptr;          // gradient staging [N*12 + P*3]
     size_t nn_stats_n = 0;             // per-warp search counters (debug, opt-in)
     int cl_C = 0, cl_cap = 0;          // cluster solve: CTAs per cluster, K blocks per CTA
     size_t cl_smem = 0;
@@ -573,6 +575,8 @@ void nrr_destroy(nrr_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (void* p : c->allocs) cudaFree(p);
+    if (c->d_order) cudaFree(c->d_order);
+    if (c->d_grad) cudaFree(c->d_grad);
     if (c->d_state) cudaFree(c->d_state);
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1005,8 +1009,29 @@ nrr_status nrr_get_system(nrr_ctx* c, double* Kdense, double* B) {
 
 nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, double* grad_src) {
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
-    (void)mode; (void)X; (void)grad_X; (void)grad_src;
-    return fail(c, NRR_E_INVALID, "nrr_backward: not available in this build");
+    if (mode != 0) return fail(c, NRR_E_INVALID, "nrr_backward: only mode 0 (energy gradient) is available");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    // evaluate closest points, weights and rotations at X (as nrr_energy)
+    double terms[4];
+    nrr_status st = nrr_energy(c, X, terms);
+    if (st != NRR_OK) return st;
+    if (!c->d_order) {
+        CK(cudaMalloc(&c->d_order, sizeof(int) * (size_t)c->P));
+        CK(cudaMemcpyAsync(c->d_order, c->src_order.data(), sizeof(int) * (size_t)c->P, cudaMemcpyHostToDevice,
+                           c->stream));
+    }
+    if (!c->d_grad) {
+        CK(cudaMalloc(&c->d_grad, sizeof(double) * ((size_t)c->N * 12 + (size_t)c->P * 3)));
+    }
+    double* gX = c->d_grad;
+    double* gv = c->d_grad + (size_t)c->N * 12;
+    const int grid = std::max(1, (c->N + 31) / 32);
+    if (c->fp64) CK(nrr_launch_gradient<double>(c->dd, grad_X ? gX : nullptr, grad_src ? gv : nullptr, c->d_order, grid, c->stream));
+    else CK(nrr_launch_gradient<float>(c->df, grad_X ? gX : nullptr, grad_src ? gv : nullptr, c->d_order, grid, c->stream));
+    if (grad_X) CK(cudaMemcpyAsync(grad_X, gX, sizeof(double) * (size_t)c->N * 12, cudaMemcpyDefault, c->stream));
+    if (grad_src) CK(cudaMemcpyAsync(grad_src, gv, sizeof(double) * (size_t)c->P * 3, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRR_OK;
 }
 
 }  // extern "C"

@@ -436,3 +436,31 @@ class Registration:
 
     def info(self) -> NrrStepInfo:
         return nrr_get_info(self.ctx)
+
+
+def energy_function():
+    """torch.autograd.Function computing E(X) of a registration with the
+    hand-written gradient kernel as its backward (closest points held at X).
+
+    Usage: E = energy_function().apply(X, reg) with X a float64 tensor
+    [N, 12] (requires_grad) and reg a Registration; E.backward() fills
+    X.grad with dE/dX from nrr_backward. Imported lazily so that the binding
+    itself does not need torch."""
+    import torch
+
+    class NrrEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X, reg):
+            Xh = X.detach().cpu().numpy().astype(np.float64)
+            ctx.reg = reg
+            ctx.Xh = Xh
+            e = reg.energy(Xh)
+            return torch.tensor(e[0], dtype=X.dtype, device=X.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            gX, _ = ctx.reg.backward(ctx.Xh, want_src=False)
+            g = torch.from_numpy(gX).to(device=grad_out.device, dtype=grad_out.dtype)
+            return grad_out * g, None
+
+    return NrrEnergy

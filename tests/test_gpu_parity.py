@@ -265,3 +265,32 @@ def test_step_after_return_is_rejected():
     info = reg.step()
     assert info.n_passes == 1
     reg.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_energy_gradient_matches_oracle(s5k, prec):
+    """nrr_backward (mode 0): dE/dX and dE/dv with the closest points held
+    at X, against the oracle's analytic gradient (itself pinned by central
+    differences). Nodes influenced by a point whose closest target differs
+    (a near tie, mixed path only) are excluded."""
+    pair, ora = s5k
+    reg = _gpu(pair, prec)
+    X = synth.perturbed_transforms(reg.N, seed=17)
+    if prec == "mixed":
+        X = X.astype(np.float32).astype(np.float64)
+    gX, gv = reg.backward(X)
+    info = reg.info()
+    rho, _ = reg.correspondence()
+    ogX, ogv = M.energy_gradient(ora.V, ora.U, ora.graph, X, info.nu_a, info.nu_r,
+                                 info.alpha, info.beta)
+    t = ora.terms(X)
+    bad_pts = np.nonzero(rho != t["rho"])[0]
+    if prec == "fp64":
+        assert len(bad_pts) == 0
+    bad_nodes = np.unique(ora.graph.nidx[bad_pts][ora.graph.nidx[bad_pts] >= 0])
+    keep = np.setdiff1d(np.arange(reg.N), bad_nodes)
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    assert relmax(gX[keep], ogX[keep]) < tol, relmax(gX[keep], ogX[keep])
+    keep_pts = np.setdiff1d(np.arange(reg.P), bad_pts)
+    assert relmax(gv[keep_pts], ogv[keep_pts]) < tol, relmax(gv[keep_pts], ogv[keep_pts])
+    reg.close()

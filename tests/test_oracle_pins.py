@@ -358,3 +358,38 @@ def test_anderson_linear_contraction():
     for _ in range(d + 2):
         plain = Mx @ plain + b
     assert np.linalg.norm(plain - xstar) > 1e-2
+
+
+def test_energy_gradient_matches_central_differences(small):
+    """The analytic gradient of E with the closest points held fixed equals
+    FP64 central differences (h = 1e-6) of E at points where no closest point
+    changes within +-h (checked), for X and for the source positions."""
+    pair, g = small
+    rng = _rng(13)
+    X = _near_identity_X(g.N, rng, 0.02)
+    V = pair.src.astype(np.float64)
+    U = pair.tgt.astype(np.float64)
+    nu_a, nu_r, alpha, beta = 0.05, 0.1, 3.0, 0.7
+    t0 = M.energy_terms(V, U, g, X, nu_a, nu_r)
+    gX, gv = M.energy_gradient(V, U, g, X, nu_a, nu_r, alpha, beta)
+
+    def E(Xv, Vv):
+        t = M.energy_terms(Vv, U, g, Xv, nu_a, nu_r)
+        assert np.array_equal(t["rho"], t0["rho"])     # no flip within the step
+        return M.total_energy(t, alpha, beta)
+
+    h = 1e-6
+    flat = X.ravel()
+    for idx in rng.choice(flat.size, 10, replace=False):
+        e = np.zeros_like(flat)
+        e[idx] = h
+        fd = (E((flat + e).reshape(X.shape), V) - E((flat - e).reshape(X.shape), V)) / (2 * h)
+        assert abs(fd - gX.ravel()[idx]) < 1e-6 * max(1.0, abs(fd)), (idx, fd, gX.ravel()[idx])
+    for i in rng.choice(V.shape[0], 6, replace=False):
+        for c in range(3):
+            Vp, Vm = V.copy(), V.copy()
+            Vp[i, c] += h
+            Vm[i, c] -= h
+            # node positions p_j are held constant: only v_i moves
+            fd = (E(X, Vp) - E(X, Vm)) / (2 * h)
+            assert abs(fd - gv[i, c]) < 1e-6 * max(1.0, abs(fd)), (i, c, fd, gv[i, c])
