@@ -93,6 +93,11 @@ typedef struct {
     double pcg_tol;            /* relative residual of the PCG solve of
                                   K X = B; <= 0: 1e-12 (FP64), 1e-6 (MIXED) */
     int    pcg_max_iters;      /* PCG iteration cap; default 500            */
+    int    solve_ctas;         /* CTAs of the cluster solve: 0 = the largest
+                                  cluster that holds the system (lowest
+                                  latency for one pair), -1 = the smallest
+                                  (batches; leaves SMs to other pairs),
+                                  1..16 = that size if it fits              */
 } nrr_params;
 
 /* State after a pass (one execution of the repeat body of Algorithm 2). */
@@ -260,6 +265,36 @@ nrr_status nrr_get_info(nrr_ctx* ctx, nrr_step_info* info);
  * cudaFree. */
 nrr_status nrr_align_energy_noalloc(const float* d2, int64_t P, double nu_a, float* w_a,
                                     double* E_align, void* cuda_stream);
+
+/* Batches of independent registration problems (pairs). Each pair gets its
+ * own context (its own graph, parameters and stream); one CUDA graph runs a
+ * pass of every pair as parallel branches, so a batch advances all pairs in
+ * one launch. Pairs that have returned do nothing in later passes.
+ *   src_xyz[i], tgt_xyz[i]: float32 [P[i]][3], [T[i]][3], host or device.
+ *   params: NULL (defaults), one nrr_params for all pairs
+ *     (params_per_pair = 0) or an array of n_pairs (params_per_pair = 1).
+ *   cuda_stream: the stream the batch graph runs on (NULL: own stream).
+ * Errors of pair i are reported with its index in nrr_last_error(NULL). */
+typedef struct nrr_batch nrr_batch;
+
+nrr_status nrr_batch_create(nrr_batch** out, int n_pairs, const float* const* src_xyz,
+                            const int64_t* P, const float* const* tgt_xyz, const int64_t* T,
+                            const nrr_params* params, int params_per_pair, void* cuda_stream);
+
+/* Runs batch passes until every pair's Algorithm 2 has returned or
+ * max_passes (<= 0: the largest max_total_passes) passes ran. infos (host,
+ * may be NULL) receives n_pairs summaries. NRR_E_NOT_CONVERGED if the cap
+ * was hit. */
+nrr_status nrr_batch_solve(nrr_batch* b, int max_passes, nrr_step_info* infos);
+
+/* Restarts every pair (nrr_reset). */
+nrr_status nrr_batch_reset(nrr_batch* b);
+
+/* The context of pair i (owned by the batch; valid until nrr_batch_destroy),
+ * for the per-pair getters. */
+nrr_status nrr_batch_get_context(nrr_batch* b, int i, nrr_ctx** out);
+
+void nrr_batch_destroy(nrr_batch* b);
 
 /* Message describing the last failure on ctx (or a global message if ctx is
  * NULL). The string lives until the next call on ctx. */

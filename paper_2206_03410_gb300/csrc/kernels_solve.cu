@@ -840,9 +840,23 @@ size_t nrr_solve_cluster_smem(int cap, int per) {
 // Prepares the cluster kernel for C CTAs with the given shared memory;
 // returns the number of clusters that can be co-resident (0: not usable).
 template <typename T>
-int nrr_solve_cluster_setup(int C, size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(solve_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess && C > 8)
+size_t nrr_solve_cluster_static_smem() {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, solve_cluster_kernel<T>) != cudaSuccess) {
+        cudaGetLastError();
+        return (size_t)1 << 30;
+    }
+    return fa.sharedSizeBytes;
+}
+
+// The dynamic shared-memory limit of the kernel is set to the largest value
+// the device allows (a permission, identical for every context), so contexts
+// with different needs can coexist; the amount used is given per launch.
+template <typename T>
+int nrr_solve_cluster_setup(int C, size_t smem, size_t optin) {
+    const size_t max_dyn = optin - nrr_solve_cluster_static_smem<T>();
+    cudaError_t e = cudaFuncSetAttribute(solve_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dyn);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(solve_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) { cudaGetLastError(); return 0; }
     cudaLaunchConfig_t cfg = {};
@@ -883,7 +897,9 @@ int nrr_solve_cluster_threads() { return kClusterThreads; }
 
 template size_t nrr_solve_cluster_smem<float>(int, int);
 template size_t nrr_solve_cluster_smem<double>(int, int);
-template int nrr_solve_cluster_setup<float>(int, size_t);
-template int nrr_solve_cluster_setup<double>(int, size_t);
+template int nrr_solve_cluster_setup<float>(int, size_t, size_t);
+template int nrr_solve_cluster_setup<double>(int, size_t, size_t);
+template size_t nrr_solve_cluster_static_smem<float>();
+template size_t nrr_solve_cluster_static_smem<double>();
 template cudaError_t nrr_launch_solve_cluster<float>(const DevProblem<float>&, int, int, size_t, cudaStream_t);
 template cudaError_t nrr_launch_solve_cluster<double>(const DevProblem<double>&, int, int, size_t, cudaStream_t);

@@ -19,7 +19,9 @@ int nrr_solve_cluster_threads();
 template <typename T>
 size_t nrr_solve_cluster_smem(int cap, int per);
 template <typename T>
-int nrr_solve_cluster_setup(int C, size_t smem);
+int nrr_solve_cluster_setup(int C, size_t smem, size_t optin);
+template <typename T>
+size_t nrr_solve_cluster_static_smem();
 template <typename T>
 cudaError_t nrr_launch_solve_cluster(const DevProblem<T>& d, int C, int cap, size_t smem, cudaStream_t s);
 
@@ -179,7 +181,15 @@ void choose_solver(nrr_ctx* c) {
         return;
     }
     const int N = c->N;
-    for (int C : {16, 8}) {
+    // a cluster whose CTAs hold their K rows: by default the largest (more
+    // SMs for one pair), with solve_ctas = -1 the smallest (cheaper barriers,
+    // SMs left free for the other pairs of a batch)
+    int forced = c->prm.solve_ctas > 0 ? c->prm.solve_ctas : 0;
+    if (const char* e = std::getenv("NRR_CLUSTER_CTAS")) forced = std::atoi(e);
+    const bool smallest = c->prm.solve_ctas < 0;
+    const int order_small[5] = {1, 2, 4, 8, 16}, order_large[5] = {16, 8, 4, 2, 1};
+    for (int C : (smallest ? order_small : order_large)) {
+        if (forced > 0 && C != forced) continue;
         const int per = (N + C - 1) / C;
         if (per * 4 > nrr_solve_cluster_threads() || per >= 4096) continue;
         int cap = 0;
@@ -188,8 +198,8 @@ void choose_solver(nrr_ctx* c) {
             cap = std::max(cap, c->bsr_ptr[(size_t)n1] - c->bsr_ptr[(size_t)n0]);
         }
         const size_t smem = nrr_solve_cluster_smem<T>(cap, per);
-        if (smem + 8192 > (size_t)optin) continue;
-        if (nrr_solve_cluster_setup<T>(C, smem) >= 1) {
+        if (smem + nrr_solve_cluster_static_smem<T>() > (size_t)optin) continue;
+        if (nrr_solve_cluster_setup<T>(C, smem, (size_t)optin) >= 1) {
             c->cl_C = C;
             c->cl_cap = cap;
             c->cl_smem = smem;
@@ -564,6 +574,7 @@ void nrr_params_default(nrr_params* p) {
     p->precision = NRR_MIXED;
     p->pcg_tol = 0.0;
     p->pcg_max_iters = 500;
+    p->solve_ctas = 0;
 }
 
 const char* nrr_last_error(const nrr_ctx* ctx) {
@@ -601,6 +612,8 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         return fail(nullptr, NRR_E_INVALID, "precision must be NRR_FP64 or NRR_MIXED");
     if (prm.max_iters_per_stage < 1 || prm.pcg_max_iters < 1 || prm.max_total_passes < 1)
         return fail(nullptr, NRR_E_INVALID, "iteration caps must be >= 1");
+    if (prm.solve_ctas < -1 || prm.solve_ctas > 16)
+        return fail(nullptr, NRR_E_INVALID, "solve_ctas must be in -1..16");
     if (!(std::isfinite(prm.graph_radius) && std::isfinite(prm.nu_a) && std::isfinite(prm.nu_r) &&
           std::isfinite(prm.nu_a_min) && std::isfinite(prm.eps) && std::isfinite(prm.k_alpha) &&
           std::isfinite(prm.k_beta) && std::isfinite(prm.alpha) && std::isfinite(prm.beta)))
@@ -1031,6 +1044,179 @@ nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, d
     if (grad_X) CK(cudaMemcpyAsync(grad_X, gX, sizeof(double) * (size_t)c->N * 12, cudaMemcpyDefault, c->stream));
     if (grad_src) CK(cudaMemcpyAsync(grad_src, gv, sizeof(double) * (size_t)c->P * 3, cudaMemcpyDefault, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return NRR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent pairs: one context per pair; one CUDA graph runs one
+// pass of every pair as parallel branches, then gathers every pair's flags
+// so that a single small read tells the host which pairs have returned.
+// ---------------------------------------------------------------------------
+struct nrr_batch {
+    std::vector<nrr_ctx*> ctx;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    cudaGraphExec_t gexec = nullptr;
+    NrrState** d_states = nullptr;
+    int* d_flags = nullptr;
+    int* h_flags = nullptr;
+    std::string err;
+};
+
+namespace {
+
+__global__ void gather_flags(NrrState* const* st, int n, int* flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        flags[4 * i + 0] = st[i]->done;
+        flags[4 * i + 1] = st[i]->status;
+        flags[4 * i + 2] = st[i]->n_passes;
+        flags[4 * i + 3] = st[i]->n_solves;
+    }
+}
+
+nrr_status batch_fail(nrr_batch* b, nrr_status code, const std::string& msg) {
+    if (b) b->err = msg;
+    g_last_error = msg;
+    return code;
+}
+
+#define BK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return batch_fail(b, e_ == cudaErrorMemoryAllocation ? NRR_E_OOM : NRR_E_CUDA, \
+                              std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+void nrr_batch_destroy(nrr_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (nrr_ctx* c : b->ctx) nrr_destroy(c);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    if (b->d_states) cudaFree(b->d_states);
+    if (b->d_flags) cudaFree(b->d_flags);
+    if (b->h_flags) cudaFreeHost(b->h_flags);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+nrr_status nrr_batch_create(nrr_batch** out, int n_pairs, const float* const* src_xyz, const int64_t* P,
+                            const float* const* tgt_xyz, const int64_t* T, const nrr_params* params,
+                            int params_per_pair, void* cuda_stream) {
+    nrr_batch* b = nullptr;
+    if (!out || n_pairs < 1 || !src_xyz || !P || !tgt_xyz || !T)
+        return batch_fail(nullptr, NRR_E_INVALID, "nrr_batch_create: bad arguments");
+    *out = nullptr;
+    b = new (std::nothrow) nrr_batch();
+    if (!b) return batch_fail(nullptr, NRR_E_OOM, "host allocation failed");
+    std::unique_ptr<nrr_batch, void (*)(nrr_batch*)> guard(b, nrr_batch_destroy);
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        BK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    for (int i = 0; i < n_pairs; ++i) {
+        nrr_ctx* c = nullptr;
+        const nrr_params* pp = params ? (params_per_pair ? &params[i] : params) : nullptr;
+        nrr_params q;
+        if (pp) q = *pp; else nrr_params_default(&q);
+        if (q.solve_ctas == 0) q.solve_ctas = -1;   // smallest cluster inside a batch
+        nrr_status st = nrr_create(&c, src_xyz[i], nullptr, P[i], tgt_xyz[i], nullptr, T[i], &q, nullptr);
+        if (st != NRR_OK) return batch_fail(b, st, "pair " + std::to_string(i) + ": " + g_last_error);
+        b->ctx.push_back(c);
+    }
+    const int n = n_pairs;
+    std::vector<NrrState*> sts((size_t)n);
+    for (int i = 0; i < n; ++i) sts[(size_t)i] = b->ctx[(size_t)i]->d_state;
+    BK(cudaMalloc(&b->d_states, sizeof(NrrState*) * (size_t)n));
+    BK(cudaMemcpy(b->d_states, sts.data(), sizeof(NrrState*) * (size_t)n, cudaMemcpyHostToDevice));
+    BK(cudaMalloc(&b->d_flags, sizeof(int) * 4 * (size_t)n));
+    BK(cudaMallocHost(&b->h_flags, sizeof(int) * 4 * (size_t)n));
+    // capture: fork every pair's pass onto its own stream, join, gather
+    b->events.resize((size_t)n + 1);
+    for (auto& e : b->events) BK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaEventRecord(b->events[(size_t)n], b->stream);
+    for (int i = 0; i < n && ce == cudaSuccess; ++i) {
+        nrr_ctx* c = b->ctx[(size_t)i];
+        ce = cudaStreamWaitEvent(c->stream, b->events[(size_t)n], 0);
+        if (ce == cudaSuccess) ce = launch_pass_any(c);
+        if (ce == cudaSuccess) ce = cudaEventRecord(b->events[(size_t)i], c->stream);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, b->events[(size_t)i], 0);
+    }
+    if (ce == cudaSuccess) {
+        gather_flags<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_states, n, b->d_flags);
+        ce = cudaGetLastError();
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    if (ce != cudaSuccess || ee != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return batch_fail(b, NRR_E_CUDA, std::string("batch graph capture failed: ") +
+                                             cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    BK(ie);
+    guard.release();
+    *out = b;
+    return NRR_OK;
+}
+
+nrr_status nrr_batch_solve(nrr_batch* b, int max_passes, nrr_step_info* infos) {
+    if (!b) return batch_fail(nullptr, NRR_E_INVALID, "batch is NULL");
+    const int n = (int)b->ctx.size();
+    int cap = max_passes;
+    if (cap <= 0) {
+        cap = 0;
+        for (nrr_ctx* c : b->ctx) cap = std::max(cap, c->prm.max_total_passes);
+    }
+    int launched = 0;
+    bool all_done = false;
+    while (!all_done && launched < cap) {
+        const int nb = std::min(4, cap - launched);
+        for (int k = 0; k < nb; ++k) BK(cudaGraphLaunch(b->gexec, b->stream));
+        launched += nb;
+        BK(cudaMemcpyAsync(b->h_flags, b->d_flags, sizeof(int) * 4 * (size_t)n, cudaMemcpyDeviceToHost, b->stream));
+        BK(cudaStreamSynchronize(b->stream));
+        all_done = true;
+        for (int i = 0; i < n; ++i) {
+            if (b->h_flags[4 * i + 1] != 0)
+                return batch_fail(b, (nrr_status)b->h_flags[4 * i + 1],
+                                  "pair " + std::to_string(i) + ": device-side wait timed out");
+            all_done = all_done && b->h_flags[4 * i] != 0;
+        }
+    }
+    if (infos)
+        for (int i = 0; i < n; ++i) {
+            nrr_status st = nrr_get_info(b->ctx[(size_t)i], &infos[i]);
+            if (st != NRR_OK) return st;
+        }
+    return all_done ? NRR_OK : NRR_E_NOT_CONVERGED;
+}
+
+nrr_status nrr_batch_reset(nrr_batch* b) {
+    if (!b) return batch_fail(nullptr, NRR_E_INVALID, "batch is NULL");
+    for (nrr_ctx* c : b->ctx) {
+        nrr_status st = nrr_reset(c);
+        if (st != NRR_OK) return st;
+    }
+    return NRR_OK;
+}
+
+nrr_status nrr_batch_get_context(nrr_batch* b, int i, nrr_ctx** out) {
+    if (!b || !out || i < 0 || i >= (int)b->ctx.size()) return batch_fail(b, NRR_E_INVALID, "bad pair index");
+    *out = b->ctx[(size_t)i];
     return NRR_OK;
 }
 

@@ -52,6 +52,7 @@ class NrrParams(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("pcg_tol", ctypes.c_double),
         ("pcg_max_iters", ctypes.c_int),
+        ("solve_ctas", ctypes.c_int),
     ]
 
 
@@ -111,6 +112,12 @@ _SIGS = [
     ("nrr_get_search_stats", ctypes.c_int, [_VP, _VP, _I64, _VP]),
     ("nrr_get_solve_stats", ctypes.c_int, [_VP, _VP]),
     ("nrr_align_energy_noalloc", ctypes.c_int, [_VP, _I64, ctypes.c_double, _VP, _VP, _VP]),
+    ("nrr_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _VP, _VP, _VP, _VP, _VP,
+                                        ctypes.c_int, _VP]),
+    ("nrr_batch_solve", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    ("nrr_batch_reset", ctypes.c_int, [_VP]),
+    ("nrr_batch_get_context", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("nrr_batch_destroy", None, [_VP]),
     ("nrr_last_error", ctypes.c_char_p, [_VP]),
 ]
 
@@ -464,3 +471,56 @@ def energy_function():
             return grad_out * g, None
 
     return NrrEnergy
+
+
+class BatchRegistration:
+    """Independent pairs advanced together by one CUDA-graph launch per pass
+    (nrr_batch_*). ``pairs`` is a list of (src, tgt) arrays; ``params`` a
+    dict applied to every pair or a list of dicts, one per pair."""
+
+    def __init__(self, pairs, params=None, stream=None):
+        lib = load()
+        n = len(pairs)
+        self._keep = [(np.ascontiguousarray(s, dtype=np.float32) if isinstance(s, np.ndarray) else s,
+                       np.ascontiguousarray(t, dtype=np.float32) if isinstance(t, np.ndarray) else t)
+                      for s, t in pairs]
+        srcp = (_VP * n)(*[_ptr(s) for s, _ in self._keep])
+        tgtp = (_VP * n)(*[_ptr(t) for _, t in self._keep])
+        P = (ctypes.c_int64 * n)(*[int(s.shape[0]) for s, _ in self._keep])
+        T = (ctypes.c_int64 * n)(*[int(t.shape[0]) for _, t in self._keep])
+        if params is None:
+            pp, per = None, 0
+        elif isinstance(params, dict):
+            pp, per = ctypes.byref(make_params(**params)), 0
+        else:
+            arr = (NrrParams * n)(*[make_params(**p) for p in params])
+            pp, per = arr, 1
+            self._params = arr
+        self.b = _VP()
+        _check(lib.nrr_batch_create(ctypes.byref(self.b), n, srcp, P, tgtp, T, pp, per, stream))
+        self.n = n
+
+    def solve(self, max_passes: int = 0):
+        infos = (NrrStepInfo * self.n)()
+        _check(load().nrr_batch_solve(self.b, int(max_passes), infos), None,
+               ok=(NRR_OK, NRR_E_NOT_CONVERGED))
+        return list(infos)
+
+    def reset(self):
+        _check(load().nrr_batch_reset(self.b))
+
+    def context(self, i: int):
+        c = _VP()
+        _check(load().nrr_batch_get_context(self.b, int(i), ctypes.byref(c)))
+        return c
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().nrr_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

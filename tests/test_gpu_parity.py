@@ -294,3 +294,24 @@ def test_energy_gradient_matches_oracle(s5k, prec):
     keep_pts = np.setdiff1d(np.arange(reg.P), bad_pts)
     assert relmax(gv[keep_pts], ogv[keep_pts]) < tol, relmax(gv[keep_pts], ogv[keep_pts])
     reg.close()
+
+
+def test_batch_matches_single_pairs():
+    """A batch of uneven pairs (one graph launch per pass) gives bitwise the
+    same transforms as solving each pair alone with the same launch shape."""
+    nrr = _nrr()
+    pairs = [synth.tiny_pair(P, T, seed=50 + k, noise=0.002, outliers=0.03)
+             for k, (P, T) in enumerate([(700, 800), (1500, 1400), (300, 350), (2100, 2300)])]
+    kw = dict(radius=0.3, aa_m=5, precision="mixed", max_iters_per_stage=20)
+    batch = nrr.BatchRegistration([(p.src, p.tgt) for p in pairs], params=kw)
+    infos = batch.solve(3000)
+    assert all(i.done == 1 and i.status == 0 for i in infos)
+    for k, p in enumerate(pairs):
+        # inside a batch a pair uses the smallest cluster that holds its system
+        single = nrr.Registration(p.src, p.tgt, solve_ctas=-1, **kw)
+        si = single.solve(3000)
+        assert si.n_passes == infos[k].n_passes and si.n_solves == infos[k].n_solves
+        Xb = nrr.nrr_get_transforms(batch.context(k))
+        assert np.array_equal(Xb, single.transforms())
+        single.close()
+    batch.close()
