@@ -331,9 +331,9 @@ template <typename T>
 cudaError_t nrr_launch_nn(const DevProblem<T>& d, int mode, int lanes_per_query, cudaStream_t s) {
     switch (lanes_per_query) {
         case 1: return launch_nn_lpq<T, 1>(d, mode, s);
-        case 8: return launch_nn_lpq<T, 8>(d, mode, s);
         case 2: return launch_nn_lpq<T, 2>(d, mode, s);
-        default: return launch_nn_lpq<T, 4>(d, mode, s);
+        case 4: return launch_nn_lpq<T, 4>(d, mode, s);
+        default: return launch_nn_lpq<T, 8>(d, mode, s);
     }
 }
 

@@ -62,7 +62,7 @@ struct nrr_ctx {
     bool use_graph = true;
     bool coop = true;
     int grid_energy = 0, grid_asm = 0, grid_solve = 0, num_sms = 0;
-    int nn_lpq = 4;                    // closest points: lanes per query (1, 2, 4, 8)
+    int nn_lpq = 8;                    // closest points: lanes per query (1, 2, 4, 8)
     int* d_order = nullptr;            // internal -> caller source index (gradients)
     double* d_grad = nullptr;          // gradient staging [N*12 + P*3]
     size_t nn_stats_n = 0;             // per-warp search counters (debug, opt-in)
