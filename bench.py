@@ -171,6 +171,20 @@ def algorithmic_bytes(P, T, N, nblk, nnz_infl, pcg_iters, n_ent, esz=4):
     return {"nn_kernel": nn, "energy_kernel": energy, "assemble_kernel": assemble, "solve_kernel": solve}
 
 
+def reduce_over_ranks(total_ms: float, iters: float, device) -> tuple[float, float]:
+    """Whole-job numbers over the ranks of a replica run: the slowest rank's
+    timed milliseconds and the sum of every rank's iterations."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), float(iters)
+    tmax = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    tsum = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0])
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -218,14 +232,7 @@ def run_ours(args):
     i1 = reg.info()
     iters = i1.n_solves - i0.n_solves
     passes = i1.n_passes - i0.n_passes
-    t = torch.tensor([total_ms, float(iters)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms_all, iters_all = float(tmax[0]), float(t[1])
-    else:
-        total_ms_all, iters_all = total_ms, float(iters)
+    total_ms_all, iters_all = reduce_over_ranks(total_ms, iters, "cuda")
     value = iters_all / (total_ms_all / 1e3)
 
     # ---- per-kernel durations (events on the library's stream) ----------
