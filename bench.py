@@ -159,7 +159,7 @@ def oracle_pass_seconds(pair, kw, n_sample: int = 1000, seed: int = 0) -> dict:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(P, T, N, nblk, nnz_infl, pcg_iters, n_ent, esz=4):
+def algorithmic_bytes(P, T, N, nblk, nnz_infl, pcg_iters, n_ent, esz=4, aa_m=5):
     """Algorithmic HBM bytes per launch of each kernel of a pass (mixed path,
     esz = 4): data each kernel must read or write at least once."""
     nn = P * (3 * esz + 4 + 3 * esz) + nnz_infl * (4 + esz) + T * 16 + \
@@ -168,7 +168,11 @@ def algorithmic_bytes(P, T, N, nblk, nnz_infl, pcg_iters, n_ent, esz=4):
     assemble = n_ent * 4 + P * (3 * esz + esz + 3 * esz) + nnz_infl * (4 + esz) + nblk * 16 * esz + N * 12 * esz
     # per PCG iteration: K once, z gathered, p, q, r, x, z own rows read+written
     solve = max(pcg_iters, 1) * (nblk * 16 * esz + 12 * N * esz * 8) + nblk * 16 * esz
-    return {"nn_kernel": nn, "energy_kernel": energy, "assemble_kernel": assemble, "solve_kernel": solve}
+    # Anderson: differences and dots (G, X, F_prev, G_prev and m-1 stored dF
+    # read; dF, dG written), then the mix (G, X and m dG read; X, F, G written)
+    aa = 12 * N * esz * ((4 + aa_m - 1 + 2) + (2 + aa_m + 3))
+    return {"nn_kernel": nn, "energy_kernel": energy, "assemble_kernel": assemble, "solve_kernel": solve,
+            "aa_kernels": aa}
 
 
 def reduce_over_ranks(total_ms: float, iters: float, device) -> tuple[float, float]:
@@ -239,7 +243,7 @@ def run_ours(args):
     reg.reset()
     reg.enqueue_passes(args.warmup)
     torch.cuda.synchronize()
-    ms = np.zeros(4)
+    ms = np.zeros(len(nrr.KERNELS))
     ks0 = reg.info()
     for k in range(args.steps):
         with torch.cuda.stream(stream):

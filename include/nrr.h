@@ -156,14 +156,14 @@ nrr_status nrr_solve(nrr_ctx* ctx, int max_passes, nrr_step_info* info);
  * the same stream; read the outcome afterwards with nrr_get_info. */
 nrr_status nrr_enqueue_passes(nrr_ctx* ctx, int n);
 
-/* Runs n passes like nrr_enqueue_passes, launching the four kernels of a
- * pass individually with CUDA events recorded around each on the context's
+/* Runs n passes like nrr_enqueue_passes, launching the steps of a pass
+ * individually with CUDA events recorded around each on the context's
  * stream, and adds their durations (milliseconds, summed over the n passes)
- * to out_ms[0..3] = {deform + closest points, energy + weights + safeguard,
- * assembly of K and B, PCG solve + Anderson mix}. Synchronises. For
- * measuring kernel durations; the result of the passes is the same as with
- * nrr_enqueue_passes. */
-nrr_status nrr_time_kernels(nrr_ctx* ctx, int n, double out_ms[4]);
+ * to out_ms[0..4] = {deform + closest points, energy + weights + safeguard,
+ * assembly of K and B, PCG solve, Anderson mix (two kernels)}. Synchronises.
+ * For measuring kernel durations; the result of the passes is the same as
+ * with nrr_enqueue_passes. */
+nrr_status nrr_time_kernels(nrr_ctx* ctx, int n, double out_ms[5]);
 
 /* Restarts Algorithm 2 from the beginning: X = identity, first stage with
  * the initial nu_a, nu_r, empty Anderson history, counters at zero. The

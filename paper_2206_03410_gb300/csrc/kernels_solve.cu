@@ -1,6 +1,7 @@
 // Solve of the surrogate normal equations K X = B (Eq. surr_solution) by
-// block-Jacobi preconditioned conjugate gradients, followed by the Anderson
-// mix of Sec. 3.3.4 (Eq. AA_solution), in one persistent kernel.
+// block-Jacobi preconditioned conjugate gradients, warm-started at X^(k), in
+// one persistent kernel that leaves G(X^(k)) in d.G (the Anderson mix that
+// follows is in kernels_aa.cu).
 //
 // K is the same 4N x 4N matrix for the three columns of X, so the kernel
 // runs three CG recurrences (one per column) that share every SpMV and every
@@ -23,7 +24,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kMaxRed = 2 * NRR_AA_MMAX;   // values per reduction
+constexpr int kMaxRed = 9;   // values per reduction (at most)
 constexpr long long kSpinLimit = 4000000000LL;   // clock64 cycles
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -164,6 +165,28 @@ __device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
     o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
 
+// a[c] for a runtime c in 0..2 without indexing (keeps a[] in registers)
+template <typename T>
+__device__ __forceinline__ T pick3(const T* a, int c) {
+    return c == 0 ? a[0] : (c == 1 ? a[1] : a[2]);
+}
+
+// Row a of block blk of the K rows a cluster CTA keeps in shared memory.
+// Layout, vector-major: block blk's 16-byte vectors v = 0 .. 16*sizeof(T)/16-1
+// (row a = vectors a*sizeof(T)/4 ..) sit at vector index v * cap + blk, so the
+// lanes of a warp that read the same row of consecutive blocks read
+// consecutive 16-byte words (no bank conflicts between them).
+__device__ __forceinline__ void krow(const float* K, int cap, int blk, int a, float (&o)[4]) {
+    const float4 v = reinterpret_cast<const float4*>(K)[(size_t)a * cap + blk];
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void krow(const double* K, int cap, int blk, int a, double (&o)[4]) {
+    const double2* K2 = reinterpret_cast<const double2*>(K);
+    const double2 x = K2[(size_t)(2 * a) * cap + blk];
+    const double2 y = K2[(size_t)(2 * a + 1) * cap + blk];
+    o[0] = x.x; o[1] = x.y; o[2] = y.x; o[3] = y.y;
+}
+
 // y[a] = sum over blocks of row n of K[b][a][t] * vec[col(b)][t][c], a = 0..3
 template <typename T, bool CG_LOAD>
 __device__ __forceinline__ void spmv_pair(const DevProblem<T>& d, const T* vec, int n, int c, T y[4]) {
@@ -181,170 +204,10 @@ __device__ __forceinline__ void spmv_pair(const DevProblem<T>& d, const T* vec, 
     }
 }
 
-// Anderson mix of Sec. 3.3.4 (Eq. AA_solution) after the solve, shared by
-// both solve kernels: G = d.G holds the MM minimiser G(X^(k)) and d.X holds
-// X^(k) for the pairs of nodes [n0, n1) of this CTA. Updates the difference
-// rings, the Gram matrix (double), solves for theta (every CTA identically),
-// writes X^(k+1) and the bookkeeping of the state (CTA 0).
-template <typename T, class Reducer>
-__device__ __noinline__ bool aa_mix_and_finish(const DevProblem<T>& d, Reducer& red, int n0, int n1,
-                                  int first_solve, int aa_count, int aa_head, int it, double rel,
-                                  double* s_theta) {
-    NrrState* st = d.st;
-    const int N = d.N;
-    const int aa_m = d.aa_m;
-    const int npairs = (n1 - n0) * 3;
-    long long* ts = (d.solve_stats != nullptr && blockIdx.x == 0 && threadIdx.x == 0) ? d.solve_stats + 48 : nullptr;
-    int tsn = 0;
-    auto stamp = [&]() { if (ts && tsn < 12) ts[tsn++] = clock64(); };
-    stamp();
-    const bool insert = !first_solve && aa_m > 0;
-    const int slot = aa_head;
-    const int mk = insert ? min(aa_count + 1, aa_m) : 0;
-    const size_t n12 = (size_t)N * 12;
-    // the stored Gram entries, prefetched in parallel for thread 0's solve
-    __shared__ double s_gram[NRR_AA_MMAX * NRR_AA_MMAX];
-    for (int k = threadIdx.x; k < NRR_AA_MMAX * NRR_AA_MMAX; k += blockDim.x) s_gram[k] = st->gram[k];
-    __syncthreads();
-    if (mk > 0) {
-        // products and per-warp sums in T, sums over warps and CTAs in double
-        T aa[kMaxRed];
-        double sa[kMaxRed];
-#pragma unroll
-        for (int j = 0; j < kMaxRed; ++j) aa[j] = 0;
-        for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
-            const int n = n0 + idx / 3, c = idx % 3;
-            // all loads of the four elements first (they are independent)
-            T g[4], xk[4], fp[4], gp[4], dfo[4][NRR_AA_MMAX];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int e = 12 * n + 3 * a + c;
-                g[a] = d.G[e]; xk[a] = d.X[e]; fp[a] = d.Fprev[e]; gp[a] = d.Gprev[e];
-#pragma unroll
-                for (int b = 0; b < NRR_AA_MMAX; ++b) dfo[a][b] = (b < mk && b != slot) ? d.dF[b * n12 + e] : T(0);
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int e = 12 * n + 3 * a + c;
-                const T f = g[a] - xk[a];
-                const T dfn = f - fp[a];
-                d.dF[slot * n12 + e] = dfn;
-                d.dG[slot * n12 + e] = g[a] - gp[a];
-#pragma unroll
-                for (int b = 0; b < NRR_AA_MMAX; ++b) {
-                    const T dfb = (b == slot) ? dfn : dfo[a][b];
-                    aa[b] += dfb * dfn;                 // Gram row of the new slot
-                    aa[NRR_AA_MMAX + b] += dfb * f;     // right-hand side
-                }
-            }
-        }
-        stamp();
-        if (!red.template run<kMaxRed, T>(aa, sa)) return false;
-        stamp();
-        if (threadIdx.x == 0) {
-            double Gm[NRR_AA_MMAX * NRR_AA_MMAX], rhs[NRR_AA_MMAX], th[NRR_AA_MMAX];
-            double tr = 0.0;
-            for (int a = 0; a < mk; ++a) {
-                for (int b = 0; b < mk; ++b) {
-                    double v;
-                    if (a == slot) v = sa[b];
-                    else if (b == slot) v = sa[a];
-                    else v = s_gram[a * NRR_AA_MMAX + b];
-                    Gm[a * NRR_AA_MMAX + b] = v;
-                }
-                rhs[a] = sa[NRR_AA_MMAX + a];
-                tr += Gm[a * NRR_AA_MMAX + a];
-            }
-            const double lam = 1e-10 * tr / mk;
-            for (int a = 0; a < mk; ++a) Gm[a * NRR_AA_MMAX + a] += lam;
-            // Cholesky solve in place
-            bool ok = true;
-            for (int j = 0; j < mk && ok; ++j) {
-                double s = Gm[j * NRR_AA_MMAX + j];
-                for (int k = 0; k < j; ++k) s -= Gm[j * NRR_AA_MMAX + k] * Gm[j * NRR_AA_MMAX + k];
-                if (!(s > 0)) { ok = false; break; }
-                const double l = sqrt(s);
-                Gm[j * NRR_AA_MMAX + j] = l;
-                for (int i = j + 1; i < mk; ++i) {
-                    double t = Gm[i * NRR_AA_MMAX + j];
-                    for (int k = 0; k < j; ++k) t -= Gm[i * NRR_AA_MMAX + k] * Gm[j * NRR_AA_MMAX + k];
-                    Gm[i * NRR_AA_MMAX + j] = t / l;
-                }
-            }
-            double nrm = 0.0;
-            if (ok) {
-                for (int i = 0; i < mk; ++i) {
-                    double t = rhs[i];
-                    for (int k = 0; k < i; ++k) t -= Gm[i * NRR_AA_MMAX + k] * th[k];
-                    th[i] = t / Gm[i * NRR_AA_MMAX + i];
-                }
-                for (int i = mk - 1; i >= 0; --i) {
-                    double t = th[i];
-                    for (int k = i + 1; k < mk; ++k) t -= Gm[k * NRR_AA_MMAX + i] * th[k];
-                    th[i] = t / Gm[i * NRR_AA_MMAX + i];
-                }
-                for (int i = 0; i < mk; ++i) nrm += th[i] * th[i];
-                ok = isfinite(nrm) && sqrt(nrm) <= 1e4;
-            }
-            for (int i = 0; i < NRR_AA_MMAX; ++i) s_theta[i] = (ok && i < mk) ? th[i] : 0.0;
-            stamp();
-            if (blockIdx.x == 0) {
-                for (int b = 0; b < mk; ++b) {
-                    st->gram[slot * NRR_AA_MMAX + b] = sa[b];
-                    st->gram[b * NRR_AA_MMAX + slot] = sa[b];
-                }
-                st->aa_mk = ok ? mk : 0;
-                for (int i = 0; i < NRR_AA_MMAX; ++i) st->theta[i] = s_theta[i];
-            }
-        }
-        __syncthreads();
-    } else if (threadIdx.x == 0 && blockIdx.x == 0) {
-        st->aa_mk = 0;
-    }
-    stamp();
-    // X^(k+1) = G - sum theta_b dG_b; keep F and G for the next differences
-    for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
-        const int n = n0 + idx / 3, c = idx % 3;
-        for (int a = 0; a < 4; ++a) {
-            const int e = 12 * n + 3 * a + c;
-            const T g = d.G[e];
-            const T f = g - d.X[e];
-            T xn = g;
-            for (int b = 0; b < mk; ++b) xn -= (T)s_theta[b] * d.dG[b * n12 + e];
-            d.X[e] = xn;
-            d.Fprev[e] = f;
-            d.Gprev[e] = g;
-        }
-    }
-    stamp();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->aa_count = mk;
-        st->aa_head = insert ? (aa_head + 1) % aa_m : aa_head;
-        st->n_solves_stage += 1;
-        st->n_solves += 1;
-        st->pending_stop = 1;
-        st->solved = 1;
-        st->pcg_iters = it;
-        st->pcg_res = rel;
-    }
-    return true;
-}
-
-struct GridReducer {
-    Barrier& bar;
-    Red& red;
-    double* s_tmp;
-    template <int K, typename A>
-    __device__ bool run(const A (&v)[K], double (&out)[K]) {
-        return red.run<K, A>(bar, v, s_tmp, out);
-    }
-};
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
     __shared__ double s_tmp[(kThreads / 32) * kMaxRed];
     __shared__ int s_flag;
-    __shared__ double s_theta[NRR_AA_MMAX];
     __shared__ double s_scal[12];
     NrrState* st = d.st;
     if (st->done || st->skip) return;
@@ -355,9 +218,6 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
     const int npairs = (n1 - n0) * 3;
     Barrier bar{st, *(volatile unsigned*)&st->bar_gen, (unsigned)G, &s_flag};
     Red red{d.partials, 0};
-    const int first_solve = st->n_solves_stage == 0;
-    const int aa_m = d.aa_m;
-    const int aa_count = st->aa_count, aa_head = st->aa_head;
     const double tol = (double)d.pcg_tol;
 
     // block-Jacobi preconditioner: inverse of each node's diagonal block
@@ -468,8 +328,10 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
         __syncthreads();
     }
 
-    GridReducer gr{bar, red, s_tmp};
-    aa_mix_and_finish<T>(d, gr, n0, n1, first_solve, aa_count, aa_head, it, rel, s_theta);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->pcg_iters = it;
+        st->pcg_res = rel;
+    }
 }
 
 
@@ -494,6 +356,9 @@ constexpr int kClusterWarps = kClusterThreads / 32;
 // floating-point addition is commutative, so every thread of every CTA gets
 // bitwise the same sums on every run.
 constexpr int kClusterMaxCtas = 16;
+// row stride (elements of T) of the preconditioner blocks in shared memory:
+// 20 rather than 16 puts the rows of 8 consecutive nodes in distinct banks
+constexpr int kMStride = 20;
 
 template <typename R>
 struct ClusterSum {
@@ -566,24 +431,11 @@ struct ClusterSum {
     }
 };
 
-// Adapter with the interface aa_mix_and_finish expects (double results).
-struct ClusterReducer {
-    ClusterSum<double> sum;
-    template <int K, typename A>
-    __device__ bool run(const A (&v)[K], double (&out)[K]) {
-        sum.template run<K, A>(v, out);
-        return true;
-    }
-};
-
 template <typename T>
 __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevProblem<T> d, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ T t_red[2 * kClusterMaxCtas * kMaxRed];
     __shared__ T t_tmp[kClusterWarps * kMaxRed];
-    __shared__ double d_red[2 * kClusterMaxCtas * kMaxRed];
-    __shared__ double d_tmp[kClusterWarps * kMaxRed];
-    __shared__ double s_theta[NRR_AA_MMAX];
     NrrState* st = d.st;
     if (st->done || st->skip) return;   // the same decision in every CTA
     cg::cluster_group cl = cg::this_cluster();
@@ -603,16 +455,17 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     T* Kloc = reinterpret_cast<T*>(smem);
     T* zloc = Kloc + (size_t)cap * 16;
     T* Mloc = zloc + (size_t)per * 12;
-    unsigned short* colloc = reinterpret_cast<unsigned short*>(Mloc + (size_t)per * 16);
+    unsigned short* colloc = reinterpret_cast<unsigned short*>(Mloc + (size_t)per * kMStride);
     const int tid = threadIdx.x, bd = blockDim.x;
     {
-        // the K rows of this CTA's nodes, as 16-byte vectors
+        // the K rows of this CTA's nodes, as 16-byte vectors, vector-major
         using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-        const int nv = nbl * 16 * (int)sizeof(T) / 16;
+        constexpr int kVpb = (int)sizeof(T);   // 16-byte vectors per 4x4 block
+        const int nv = nbl * kVpb;
         const V4* src = reinterpret_cast<const V4*>(d.Kv + (size_t)b0 * 16);
         V4* dst = reinterpret_cast<V4*>(Kloc);
 #pragma unroll 4
-        for (int k = tid; k < nv; k += bd) dst[k] = __ldg(src + k);
+        for (int k = tid; k < nv; k += bd) dst[(size_t)(k % kVpb) * cap + k / kVpb] = __ldg(src + k);
     }
     for (int k = tid; k < nbl; k += bd) {
         const int col = d.bsr_col[b0 + k];
@@ -625,12 +478,16 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
         while ((int)d.bsr_col[b0 + bdg] != n) ++bdg;
         // the preconditioner only steers CG: its inverse is formed in T
         T A[16], I[16];
-        for (int t = 0; t < 16; ++t) A[t] = Kloc[16 * bdg + t];
+        for (int a = 0; a < 4; ++a) {
+            T k4[4];
+            krow(Kloc, cap, bdg, a, k4);
+            for (int t = 0; t < 4; ++t) A[4 * a + t] = k4[t];
+        }
         if (!spd_inverse4(A, I)) {
             for (int t = 0; t < 16; ++t) I[t] = 0;
             for (int t = 0; t < 4; ++t) I[5 * t] = A[5 * t] > T(0) ? T(1) / A[5 * t] : T(1);
         }
-        for (int t = 0; t < 16; ++t) Mloc[16 * (n - n0) + t] = I[t];
+        for (int t = 0; t < 16; ++t) Mloc[kMStride * (n - n0) + t] = I[t];
     }
     __syncthreads();
 
@@ -638,8 +495,6 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     // warps that hold work: four threads per node in the SpMV and the updates
     const int active_warps = min((int)(bd >> 5), ((n1 - n0) * 4 + 31) / 32);
     ClusterSum<T> red{t_red, t_tmp, 0, max(active_warps, 1)};
-    const int first_solve = st->n_solves_stage == 0;
-    const int aa_count = st->aa_count, aa_head = st->aa_head;
     const T tol = d.pcg_tol;
     // four threads per node: in the SpMV each takes every fourth block of
     // the node's row for all three columns; in the CG updates thread s < 3
@@ -651,7 +506,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     const int n = n0 + ln, c = s4 < 3 ? s4 : 0;
     const int rb0 = node_ok ? d.bsr_ptr[n] - b0 : 0, rb1 = node_ok ? d.bsr_ptr[n + 1] - b0 : 0;
     T x[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, q[4] = {0, 0, 0, 0};
-    const T* Mi = Mloc + 16 * ln;
+    const T* Mi = Mloc + kMStride * ln;
 
     // r = B - K X^(k), z = M^-1 r; per-thread values go to the slot of its column
     T acc9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, s9[9];
@@ -659,13 +514,15 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
         T y[4] = {0, 0, 0, 0};
         for (int b = rb0; b < rb1; ++b) {
             const int k = d.bsr_col[b0 + b];
-            const T* Kb = Kloc + 16 * b;
             T v[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) v[t] = d.X[12 * k + 3 * t + c];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-                y[a] += Kb[4 * a] * v[0] + Kb[4 * a + 1] * v[1] + Kb[4 * a + 2] * v[2] + Kb[4 * a + 3] * v[3];
+            for (int a = 0; a < 4; ++a) {
+                T k4[4];
+                krow(Kloc, cap, b, a, k4);
+                y[a] += k4[0] * v[0] + k4[1] * v[1] + k4[2] * v[2] + k4[3] * v[3];
+            }
         }
         T bb = 0, rz = 0, rr = 0;
 #pragma unroll
@@ -682,7 +539,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
             rz += r[a] * zz;
             rr += r[a] * r[a];
         }
-        acc9[c] = rz; acc9[3 + c] = rr; acc9[6 + c] = bb;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            acc9[cc] = cc == c ? rz : T(0);
+            acc9[3 + cc] = cc == c ? rr : T(0);
+            acc9[6 + cc] = cc == c ? bb : T(0);
+        }
     }
     stamp();
     red.template run<9, T>(acc9, s9);
@@ -723,11 +585,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
 #pragma unroll
             for (int u = 0; u < kSpmvChunk; ++u) {
                 if (b + 4 * u < rb1) {
-                    const T* Kb = Kloc + 16 * (b + 4 * u);
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         T k4[4];
-                        load4(Kb + 4 * a, k4);
+                        krow(Kloc, cap, b + 4 * u, a, k4);
 #pragma unroll
                         for (int cc = 0; cc < 3; ++cc)
                             wv[3 * a + cc] += k4[0] * zr[u][cc] + k4[1] * zr[u][3 + cc] + k4[2] * zr[u][6 + cc] +
@@ -754,12 +615,14 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
                 q[a] = (it == 0) ? w[a] : w[a] + beta_t * q[a];
                 pq += p[a] * q[a];
             }
-            a3[c] = pq;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) a3[cc] = cc == c ? pq : T(0);
         }
         if (it < 8) stamp();
         red.template run<3, T>(a3, s3);   // also: every CTA finished reading z
         if (it < 8) stamp();
-        const T alpha_t = s3[c] != T(0) ? rzc[c] / s3[c] : T(0);
+        const T s3c = pick3(s3, c), rzcc = pick3(rzc, c);
+        const T alpha_t = s3c != T(0) ? rzcc / s3c : T(0);
         T a6[6] = {0, 0, 0, 0, 0, 0}, s6[6];
         if (has) {
 #pragma unroll
@@ -775,13 +638,17 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
                 rz += r[a] * zz;
                 rr += r[a] * r[a];
             }
-            a6[c] = rz; a6[3 + c] = rr;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                a6[cc] = cc == c ? rz : T(0);
+                a6[3 + cc] = cc == c ? rr : T(0);
+            }
         }
         if (it < 8) stamp();
         red.template run<6, T>(a6, s6);   // also: the new z is visible to the cluster
         if (it < 8) stamp();
         ++it;
-        beta_t = rzc[c] != T(0) ? s6[c] / rzc[c] : T(0);
+        beta_t = rzcc != T(0) ? pick3(s6, c) / rzcc : T(0);
         rzc[0] = s6[0]; rzc[1] = s6[1]; rzc[2] = s6[2];
         done = s6[3] <= tol2 * bbc[0] && s6[4] <= tol2 * bbc[1] && s6[5] <= tol2 * bbc[2];
         relmax2 = fmax(fmax(s6[3] / bbc[0], s6[4] / bbc[1]), s6[5] / bbc[2]);
@@ -790,10 +657,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
 #pragma unroll
         for (int a = 0; a < 4; ++a) d.G[12 * n + 3 * a + c] = x[a];
     }
-    stamp();
-    ClusterReducer dred{ClusterSum<double>{d_red, d_tmp, 0, (int)(bd >> 5)}};
-    aa_mix_and_finish<T>(d, dred, n0, n1, first_solve, aa_count, aa_head, it, sqrt((double)relmax2),
-                         s_theta);
+    if (rank == 0 && tid == 0) {
+        st->pcg_iters = it;
+        st->pcg_res = sqrt((double)relmax2);
+    }
     stamp();
     if (ts) ts[63] = tsn;
     // no CTA may leave while another can still read its shared memory
@@ -833,7 +700,7 @@ template int nrr_solve_max_blocks_per_sm<double>();
 
 template <typename T>
 size_t nrr_solve_cluster_smem(int cap, int per) {
-    return (size_t)cap * 16 * sizeof(T) + (size_t)per * 12 * sizeof(T) + (size_t)per * 16 * sizeof(T) +
+    return (size_t)cap * 16 * sizeof(T) + (size_t)per * 12 * sizeof(T) + (size_t)per * kMStride * sizeof(T) +
            (size_t)cap * sizeof(unsigned short) + 16;
 }
 

@@ -61,7 +61,7 @@ struct nrr_ctx {
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
     bool coop = true;
-    int grid_energy = 0, grid_asm = 0, grid_solve = 0, num_sms = 0;
+    int grid_energy = 0, grid_asm = 0, grid_solve = 0, grid_aa = 0, num_sms = 0;
     int nn_lpq = 8;                    // closest points: lanes per query (1, 2, 4, 8)
     int* d_order = nullptr;            // internal -> caller source index (gradients)
     double* d_grad = nullptr;          // gradient staging [N*12 + P*3]
@@ -217,7 +217,9 @@ cudaError_t launch_pass(nrr_ctx* c) {
     if (e != cudaSuccess) return e;
     e = nrr_launch_assemble<T>(d, c->grid_asm, c->stream);
     if (e != cudaSuccess) return e;
-    return launch_solve<T>(c);
+    e = launch_solve<T>(c);
+    if (e != cudaSuccess) return e;
+    return nrr_launch_aa<T>(d, c->grid_aa, c->stream);
 }
 
 cudaError_t launch_pass_any(nrr_ctx* c) { return c->fp64 ? launch_pass<double>(c) : launch_pass<float>(c); }
@@ -663,6 +665,9 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     }
     c->grid_energy = 2 * c->num_sms;
     c->grid_asm = std::max(1, std::min(8 * c->num_sms, (c->N + c->E2 + 31) / 32));
+    // Anderson kernels: one element of X per thread up to grid_energy CTAs
+    // (the partials buffer is sized for grid_energy)
+    c->grid_aa = std::max(1, std::min(c->grid_energy, (c->N * 12 + 255) / 256));
     {
         const int per_cta = nrr_solve_threads() / 3;   // (node, column) pairs per thread
         int want = std::max(1, (c->N + per_cta - 1) / per_cta);
@@ -766,32 +771,35 @@ nrr_status nrr_enqueue_passes(nrr_ctx* c, int n) {
     return NRR_OK;
 }
 
-nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[4]) {
+nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[5]) {
     if (!c || n < 0 || !out_ms) return fail(c, NRR_E_INVALID, "bad argument");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
-    cudaEvent_t ev[5];
+    constexpr int kSteps = 5;
+    cudaEvent_t ev[kSteps + 1];
     for (auto& e : ev) CK(cudaEventCreate(&e));
     nrr_status result = NRR_OK;
     for (int k = 0; k < n && result == NRR_OK; ++k) {
         cudaError_t e = cudaEventRecord(ev[0], c->stream);
-        for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
+        for (int s = 0; s < kSteps && e == cudaSuccess; ++s) {
             if (c->fp64) {
                 DevProblem<double>& d = c->dd;
                 e = s == 0 ? nrr_launch_nn<double>(d, NRR_MODE_PASS, c->nn_lpq, c->stream)
                   : s == 1 ? nrr_launch_energy<double>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
                   : s == 2 ? nrr_launch_assemble<double>(d, c->grid_asm, c->stream)
-                           : launch_solve<double>(c);
+                  : s == 3 ? launch_solve<double>(c)
+                           : nrr_launch_aa<double>(d, c->grid_aa, c->stream);
             } else {
                 DevProblem<float>& d = c->df;
                 e = s == 0 ? nrr_launch_nn<float>(d, NRR_MODE_PASS, c->nn_lpq, c->stream)
                   : s == 1 ? nrr_launch_energy<float>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
                   : s == 2 ? nrr_launch_assemble<float>(d, c->grid_asm, c->stream)
-                           : launch_solve<float>(c);
+                  : s == 3 ? launch_solve<float>(c)
+                           : nrr_launch_aa<float>(d, c->grid_aa, c->stream);
             }
             if (e == cudaSuccess) e = cudaEventRecord(ev[s + 1], c->stream);
         }
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
-        for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[kSteps]);
+        for (int s = 0; s < kSteps && e == cudaSuccess; ++s) {
             float ms = 0.f;
             e = cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
             out_ms[s] += ms;

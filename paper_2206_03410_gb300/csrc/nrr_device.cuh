@@ -108,6 +108,8 @@ cudaError_t nrr_launch_assemble(const DevProblem<T>& d, int grid, cudaStream_t s
 template <typename T>
 cudaError_t nrr_launch_solve(const DevProblem<T>& d, int grid, cudaStream_t s, bool cooperative);
 template <typename T>
+cudaError_t nrr_launch_aa(const DevProblem<T>& d, int grid, cudaStream_t s);
+template <typename T>
 cudaError_t nrr_launch_gradient(const DevProblem<T>& d, double* grad_X, double* grad_v, const int* order,
                                 int grid, cudaStream_t s);
 

@@ -229,13 +229,15 @@ def nrr_reset(ctx):
     _check(load().nrr_reset(ctx), ctx)
 
 
-KERNELS = ("nn_kernel", "energy_kernel", "assemble_kernel", "solve_kernel")
+# the steps of a pass in launch order; the last is two kernels
+# (aa_dots_kernel, aa_mix_kernel)
+KERNELS = ("nn_kernel", "energy_kernel", "assemble_kernel", "solve_kernel", "aa_kernels")
 
 
 def nrr_time_kernels(ctx, n: int = 1) -> np.ndarray:
-    """Milliseconds spent in each of the four kernels of a pass, summed over
-    n passes (event-timed on the context's stream)."""
-    out = np.zeros(4, dtype=np.float64)
+    """Milliseconds spent in each step of a pass (KERNELS), summed over n
+    passes (event-timed on the context's stream)."""
+    out = np.zeros(len(KERNELS), dtype=np.float64)
     _check(load().nrr_time_kernels(ctx, int(n), _ptr(out)), ctx)
     return out
 
