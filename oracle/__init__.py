@@ -21,8 +21,10 @@ Modules:
              normal equations K X = B.
   anderson   Sec. 3.3.4 Anderson acceleration least squares and mix.
   solver     Algorithm 2 (stage loop, MM + AA passes, safeguard).
+  unrolled   K plain MM steps at fixed nu and their reverse-mode derivative
+             w.r.t. the initial transforms and the source positions.
 
 Parity pins: every function is pinned by the tests in tests/test_oracle_*.py
 against closed forms, invariants, brute force and library routines.
 """
-from . import graph, model, surrogate, anderson, solver  # noqa: F401
+from . import graph, model, surrogate, anderson, solver, unrolled  # noqa: F401

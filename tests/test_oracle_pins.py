@@ -393,3 +393,75 @@ def test_energy_gradient_matches_central_differences(small):
             # node positions p_j are held constant: only v_i moves
             fd = (E(X, Vp) - E(X, Vm)) / (2 * h)
             assert abs(fd - gv[i, c]) < 1e-6 * max(1.0, abs(fd)), (i, c, fd, gv[i, c])
+
+
+# ------------------------------------------------- unrolled MM derivative ---
+
+def test_proj_rotation_vjp_matches_central_differences():
+    """The reverse-mode derivative of proj_R equals FP64 central differences
+    of <Rbar, proj_R(A)>, for det A > 0 (polar factor) and det A < 0 (the
+    reflected singular vector), on random matrices."""
+    from oracle import unrolled as UR
+    rng = _rng(31)
+    for flip in (False, True):
+        for _ in range(4):
+            A = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+            if flip:
+                A[:, 0] = -A[:, 0]
+            if (np.linalg.det(A) < 0) != flip:
+                continue
+            Rbar = rng.standard_normal((3, 3))
+            Abar = UR.proj_rotation_vjp(A, Rbar)
+            h = 1e-6
+            for a in range(3):
+                for b in range(3):
+                    Ap, Am = A.copy(), A.copy()
+                    Ap[a, b] += h
+                    Am[a, b] -= h
+                    fd = (np.sum(Rbar * M.proj_rotation(Ap)) - np.sum(Rbar * M.proj_rotation(Am))) / (2 * h)
+                    assert abs(fd - Abar[a, b]) < 1e-7 * max(1.0, abs(fd)), (flip, a, b, fd, Abar[a, b])
+
+
+@pytest.fixture(scope="module")
+def unroll_case():
+    pair = synth.tiny_pair(300, 330, seed=8, noise=0.002, outliers=0.03)
+    g = G.build_graph(pair.src.astype(np.float64), 0.4)
+    X0 = _near_identity_X(g.N, _rng(5), 0.01)
+    return pair.src.astype(np.float64), pair.tgt.astype(np.float64), g, X0
+
+
+@pytest.mark.parametrize("loss", ["energy", "cotangent"])
+def test_unrolled_backward_matches_central_differences(unroll_case, loss):
+    """dL/dX^(0) and dL/dV of K = 3 unrolled MM steps (fixed nu, no AA)
+    equal FP64 central differences (h = 1e-6) of the oracle's forward map, at
+    points where no closest point of any step changes within +-h (checked);
+    node positions and skinning weights are held constant."""
+    from oracle import unrolled as UR
+    V, U, g, X0 = unroll_case
+    nu_a, nu_r, alpha, beta, K = 0.04, 0.12, 2.0, 0.5, 3
+    C = _rng(6).standard_normal((g.N, 12)) if loss == "cotangent" else None
+    Xs = UR.unrolled_forward(V, U, g, X0, nu_a, nu_r, alpha, beta, K)
+    gX, gV = UR.unrolled_backward(V, U, g, Xs, nu_a, nu_r, alpha, beta, cotangent=C)
+    _, rho0 = UR.unrolled_loss(V, U, g, X0, nu_a, nu_r, alpha, beta, K, C)
+
+    def L(Xv, Vv):
+        val, rhos = UR.unrolled_loss(Vv, U, g, Xv, nu_a, nu_r, alpha, beta, K, C)
+        for a, b in zip(rhos, rho0):
+            assert np.array_equal(a, b)           # no flip within the step
+        return val
+
+    rng = _rng(7)
+    h = 1e-6
+    flat = X0.ravel()
+    for idx in rng.choice(flat.size, 12, replace=False):
+        e = np.zeros_like(flat)
+        e[idx] = h
+        fd = (L((flat + e).reshape(X0.shape), V) - L((flat - e).reshape(X0.shape), V)) / (2 * h)
+        assert abs(fd - gX.ravel()[idx]) < 1e-6 * max(1.0, abs(fd)), (idx, fd, gX.ravel()[idx])
+    for i in rng.choice(V.shape[0], 5, replace=False):
+        for c in range(3):
+            Vp, Vm = V.copy(), V.copy()
+            Vp[i, c] += h
+            Vm[i, c] -= h
+            fd = (L(X0, Vp) - L(X0, Vm)) / (2 * h)
+            assert abs(fd - gV[i, c]) < 1e-6 * max(1.0, abs(fd)), (i, c, fd, gV[i, c])
