@@ -176,14 +176,41 @@ nrr_status nrr_reset(nrr_ctx* ctx);
  * solver state. */
 nrr_status nrr_energy(nrr_ctx* ctx, const double* X, double out_terms[4]);
 
-/* Gradient of E (Eq. 2) at X (NULL = current iterate) with the closest
- * points held fixed at their values at X (rho is piecewise constant):
+/* Derivatives (the paper does not differentiate its solver; the readings
+ * below are this library's).
+ *
+ * mode 0 - gradient of E (Eq. 2) at X (NULL = current iterate) with the
+ * closest points held fixed at their values at X (rho is piecewise
+ * constant):
  *   grad_X   [N][12] doubles (d E / d X, same layout as X), may be NULL;
  *   grad_src [P][3]  doubles (d E / d v_i through Eq. deformed_position,
  *            with node positions p_j held constant), may be NULL.
- * Host or device buffers. mode must be 0 (energy gradient). */
+ *
+ * mode 1 - gradient of a loss L(X^(K)) of the last nrr_unroll w.r.t. its
+ * X^(0) and the source positions. X is then the cotangent dL/dX^(K)
+ * ([N][12] doubles), or NULL for L = E(X^(K)) (closest points held at
+ * X^(K)). Each step is differentiated implicitly: with lambda solving
+ * K lambda = dL/dX^(k+1) (the same PCG), dL/dB = lambda and dL/dK =
+ * -lambda X^(k+1)^T, propagated through the Welsch weights, the rotation
+ * targets proj_R(A_j) and the rows of F; closest points, node positions,
+ * skinning weights and r_ij are held constant; no gradient flows through
+ * the argmin. Closest points, weights and K are recomputed from the
+ * checkpoints X^(k). grad_X receives dL/dX^(0) [N][12], grad_src dL/dv
+ * [P][3] (caller order); either may be NULL.
+ * NRR_E_STATE for mode 1 without a previous nrr_unroll or after the stage
+ * parameters changed. Host or device buffers. */
 nrr_status nrr_backward(nrr_ctx* ctx, int mode, const double* X,
                         double* grad_X, double* grad_src);
+
+/* K plain MM steps from X0 (Sec. 3.3.1-3.3.2): X^(k+1) = K(X^(k))^-1
+ * B(X^(k)) of Eq. (surr_solution) at the current stage's nu_a, nu_r, alpha,
+ * beta, without the Anderson mix and the safeguard (the accept/reject
+ * branch of Algorithm 2 is not differentiable). Keeps X^(0..K) in the
+ * context as checkpoints for nrr_backward mode 1 (12 N values per step in
+ * the context's precision). X0 [N][12] doubles; XK (may be NULL) receives
+ * X^(K). Host or device buffers. The solver state (iterate, stage, Anderson
+ * history) is left as it was. K in 0..1024. */
+nrr_status nrr_unroll(nrr_ctx* ctx, int K, const double* X0, double* XK);
 
 /* Sets the current iterate X^(k) (X [N][12] doubles) and restarts the
  * current stage (E_prev = +inf, empty Anderson history). */

@@ -17,9 +17,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnrr.so")
 
-CU_SOURCES = ["kernels_nn.cu", "kernels_system.cu", "kernels_solve.cu", "kernels_aa.cu", "nrr_api.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels_nn.cu", "kernels_system.cu", "kernels_solve.cu", "kernels_aa.cu", "kernels_unroll.cu",
+              "nrr_api.cu", "noalloc.cu"]
 CPP_SOURCES = ["graph_build.cpp"]
-HEADERS = ["nrr_internal.h", "nrr_device.cuh"]
+HEADERS = ["nrr_internal.h", "nrr_device.cuh", "nrr_rotation.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",

@@ -65,6 +65,13 @@ struct nrr_ctx {
     int nn_lpq = 8;                    // closest points: lanes per query (1, 2, 4, 8)
     int* d_order = nullptr;            // internal -> caller source index (gradients)
     double* d_grad = nullptr;          // gradient staging [N*12 + P*3]
+    // unrolled MM steps (nrr_unroll / nrr_backward mode 1)
+    int unroll_K = -1;                 // steps of the last nrr_unroll (-1: none)
+    double unroll_prm[4] = {0, 0, 0, 0};   // nu_a, nu_r, alpha, beta of that run
+    void* d_ck = nullptr;              // checkpoints X^(0..K) [K+1][N][12] in T
+    int ck_cap = 0;                    // checkpoints the buffer holds
+    void* d_adj = nullptr;             // zero, lambda, g_bar [N][12] and e [3][P] in T
+    double* d_adjd = nullptr;          // g_bar [N][12] and dL/dv [P][3] in double
     size_t nn_stats_n = 0;             // per-warp search counters (debug, opt-in)
     int cl_C = 0, cl_cap = 0;          // cluster solve: CTAs per cluster, K blocks per CTA
     size_t cl_smem = 0;
@@ -164,10 +171,13 @@ nrr_status push_state(nrr_ctx* c) {
 }
 
 template <typename T>
-cudaError_t launch_solve(nrr_ctx* c) {
-    if (c->cl_C > 0) return nrr_launch_solve_cluster<T>(prob<T>(c), c->cl_C, c->cl_cap, c->cl_smem, c->stream);
-    return nrr_launch_solve<T>(prob<T>(c), c->grid_solve, c->stream, c->coop);
+cudaError_t launch_solve_on(nrr_ctx* c, const DevProblem<T>& d) {
+    if (c->cl_C > 0) return nrr_launch_solve_cluster<T>(d, c->cl_C, c->cl_cap, c->cl_smem, c->stream);
+    return nrr_launch_solve<T>(d, c->grid_solve, c->stream, c->coop);
 }
+
+template <typename T>
+cudaError_t launch_solve(nrr_ctx* c) { return launch_solve_on<T>(c, prob<T>(c)); }
 
 // Chooses the cluster solve when one cluster of 16 (or 8) CTAs can hold the
 // K rows of its nodes in shared memory; otherwise the grid-wide solve.
@@ -548,6 +558,160 @@ nrr_status write_X(nrr_ctx* c, T* dst, const double* X) {
     return NRR_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Unrolled MM steps: K plain MM steps (no Anderson mix, no safeguard) at the
+// current stage's nu_a, nu_r, alpha, beta, with X^(0..K) kept as checkpoints;
+// the backward recomputes closest points, weights and K at each checkpoint
+// and solves the adjoint system with the same PCG.
+// ---------------------------------------------------------------------------
+
+// Runs the off-trajectory work of nrr_unroll / nrr_backward with the pass
+// flags cleared, then puts the solver state back (the evaluations wrote
+// v_hat into the non-kept buffer, as nrr_energy does).
+struct StateGuard {
+    nrr_ctx* c;
+    NrrState saved{};
+    nrr_status open() {
+        nrr_status st = pull_state(c);
+        if (st != NRR_OK) return st;
+        saved = *c->h_state;
+        c->h_state->done = 0;
+        c->h_state->skip = 0;
+        return push_state(c);
+    }
+    nrr_status close() {
+        *c->h_state = saved;
+        c->h_state->vlast = saved.vk ^ 1;
+        return push_state(c);
+    }
+};
+
+template <typename T>
+nrr_status unroll_buffers(nrr_ctx* c, int K) {
+    const size_t n12 = (size_t)c->N * 12, P = (size_t)c->P;
+    if (c->ck_cap < K + 1) {
+        if (c->d_ck) { CK(cudaFree(c->d_ck)); c->d_ck = nullptr; c->ck_cap = 0; }
+        const int cap = std::max(K + 1, 11);
+        CK(cudaMalloc(&c->d_ck, sizeof(T) * n12 * (size_t)cap));
+        c->ck_cap = cap;
+    }
+    if (!c->d_adj) {
+        CK(cudaMalloc(&c->d_adj, sizeof(T) * (3 * n12 + 3 * P)));
+        CK(cudaMemsetAsync(c->d_adj, 0, sizeof(T) * n12, c->stream));   // the zero warm start
+    }
+    if (!c->d_adjd) CK(cudaMalloc(&c->d_adjd, sizeof(double) * (n12 + 3 * P)));
+    if (!c->d_order) {
+        CK(cudaMalloc(&c->d_order, sizeof(int) * P));
+        CK(cudaMemcpyAsync(c->d_order, c->src_order.data(), sizeof(int) * P, cudaMemcpyHostToDevice, c->stream));
+    }
+    return NRR_OK;
+}
+
+// Closest points, Welsch weights, rotations and K, B at the checkpoint Xk.
+template <typename T>
+nrr_status unroll_system_at(nrr_ctx* c, const T* Xk) {
+    DevProblem<T>& d = prob<T>(c);
+    CK(cudaMemcpyAsync(d.Xeval, Xk, sizeof(T) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
+    CK(nrr_launch_nn<T>(d, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+    CK(nrr_launch_energy<T>(d, NRR_MODE_EVAL, c->grid_energy, c->stream));
+    CK(nrr_launch_assemble<T>(d, c->grid_asm, c->stream));
+    return NRR_OK;
+}
+
+template <typename T>
+nrr_status unroll_t(nrr_ctx* c, int K, const double* X0, double* XK) {
+    nrr_status st = unroll_buffers<T>(c, K);
+    if (st != NRR_OK) return st;
+    const size_t n12 = (size_t)c->N * 12;
+    T* ck = (T*)c->d_ck;
+    st = write_X<T>(c, ck, X0);
+    if (st != NRR_OK) return st;
+    StateGuard guard{c};
+    st = guard.open();
+    if (st != NRR_OK) return st;
+    c->unroll_prm[0] = c->h_state->nu_a;
+    c->unroll_prm[1] = c->h_state->nu_r;
+    c->unroll_prm[2] = c->h_state->alpha;
+    c->unroll_prm[3] = c->h_state->beta;
+    for (int k = 0; k < K; ++k) {
+        st = unroll_system_at<T>(c, ck + (size_t)k * n12);
+        if (st != NRR_OK) return st;
+        DevProblem<T> ds = prob<T>(c);
+        ds.X = ck + (size_t)k * n12;          // warm start X^(k)
+        ds.G = ck + (size_t)(k + 1) * n12;    // X^(k+1) = K^-1 B
+        CK(launch_solve_on<T>(c, ds));
+    }
+    st = pull_state(c);
+    if (st != NRR_OK) return st;
+    const int dev_status = c->h_state->status;
+    st = guard.close();
+    if (st != NRR_OK) return st;
+    if (dev_status != 0) return fail(c, (nrr_status)dev_status, "nrr_unroll: device-side check failed");
+    c->unroll_K = K;
+    if (XK) return read_X<T>(c, ck + (size_t)K * n12, XK);
+    return NRR_OK;
+}
+
+template <typename T>
+nrr_status unroll_backward_t(nrr_ctx* c, const double* C, double* grad_X, double* grad_src) {
+    const int K = c->unroll_K;
+    const size_t n12 = (size_t)c->N * 12, P = (size_t)c->P;
+    T* ck = (T*)c->d_ck;
+    T* zero = (T*)c->d_adj;
+    T* lam = zero + n12;
+    T* gt = lam + n12;
+    T* ebuf = gt + n12;
+    double* gd = c->d_adjd;
+    double* gv = gd + n12;
+    DevProblem<T>& d = prob<T>(c);
+    StateGuard guard{c};
+    nrr_status st = guard.open();
+    if (st != NRR_OK) return st;
+    const NrrState& h = *c->h_state;
+    if (h.nu_a != c->unroll_prm[0] || h.nu_r != c->unroll_prm[1] || h.alpha != c->unroll_prm[2] ||
+        h.beta != c->unroll_prm[3]) {
+        guard.close();
+        return fail(c, NRR_E_STATE, "nrr_backward mode 1: the stage changed since nrr_unroll");
+    }
+    CK(cudaMemsetAsync(gv, 0, sizeof(double) * 3 * P, c->stream));
+    if (C == nullptr) {
+        // L = E(X^(K)): closest points held at X^(K)
+        CK(cudaMemcpyAsync(d.Xeval, ck + (size_t)K * n12, sizeof(T) * n12, cudaMemcpyDeviceToDevice, c->stream));
+        CK(nrr_launch_nn<T>(d, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+        CK(nrr_launch_energy<T>(d, NRR_MODE_EVAL, c->grid_energy, c->stream));
+        const int grid = std::max(1, (c->N + 31) / 32);
+        CK(nrr_launch_gradient<T>(d, gd, gv, c->d_order, grid, c->stream));
+    } else {
+        std::vector<double> hC(n12);
+        CK(cudaMemcpy(hC.data(), C, sizeof(double) * n12, cudaMemcpyDefault));
+        for (double x : hC)
+            if (!std::isfinite(x)) { guard.close(); return fail(c, NRR_E_INVALID, "cotangent has non-finite entries"); }
+        CK(cudaMemcpyAsync(gd, hC.data(), sizeof(double) * n12, cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(nrr_launch_to_t<T>(gd, gt, (int)n12, c->stream));
+    for (int k = K - 1; k >= 0; --k) {
+        st = unroll_system_at<T>(c, ck + (size_t)k * n12);
+        if (st != NRR_OK) return st;
+        DevProblem<T> ds = d;
+        ds.X = zero;     // warm start 0
+        ds.Bv = gt;      // K lambda = g_bar
+        ds.G = lam;
+        CK(launch_solve_on<T>(c, ds));
+        CK(nrr_launch_adjoint<T>(d, lam, ck + (size_t)(k + 1) * n12, c->d_order, ebuf, gv, gd, gt, c->stream));
+    }
+    if (grad_X) CK(cudaMemcpyAsync(grad_X, gd, sizeof(double) * n12, cudaMemcpyDefault, c->stream));
+    if (grad_src) CK(cudaMemcpyAsync(grad_src, gv, sizeof(double) * 3 * P, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    st = pull_state(c);
+    if (st != NRR_OK) return st;
+    const int dev_status = c->h_state->status;
+    st = guard.close();
+    if (st != NRR_OK) return st;
+    if (dev_status != 0) return fail(c, (nrr_status)dev_status, "nrr_backward: device-side check failed");
+    return NRR_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -590,6 +754,9 @@ void nrr_destroy(nrr_ctx* c) {
     for (void* p : c->allocs) cudaFree(p);
     if (c->d_order) cudaFree(c->d_order);
     if (c->d_grad) cudaFree(c->d_grad);
+    if (c->d_ck) cudaFree(c->d_ck);
+    if (c->d_adj) cudaFree(c->d_adj);
+    if (c->d_adjd) cudaFree(c->d_adjd);
     if (c->d_state) cudaFree(c->d_state);
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1030,8 +1197,13 @@ nrr_status nrr_get_system(nrr_ctx* c, double* Kdense, double* B) {
 
 nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, double* grad_src) {
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
-    if (mode != 0) return fail(c, NRR_E_INVALID, "nrr_backward: only mode 0 (energy gradient) is available");
+    if (mode != 0 && mode != 1) return fail(c, NRR_E_INVALID, "nrr_backward: mode must be 0 or 1");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    if (mode == 1) {
+        if (c->unroll_K < 0) return fail(c, NRR_E_STATE, "nrr_backward mode 1 needs a previous nrr_unroll");
+        return c->fp64 ? unroll_backward_t<double>(c, X, grad_X, grad_src)
+                       : unroll_backward_t<float>(c, X, grad_X, grad_src);
+    }
     // evaluate closest points, weights and rotations at X (as nrr_energy)
     double terms[4];
     nrr_status st = nrr_energy(c, X, terms);
@@ -1053,6 +1225,15 @@ nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, d
     if (grad_src) CK(cudaMemcpyAsync(grad_src, gv, sizeof(double) * (size_t)c->P * 3, cudaMemcpyDefault, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return NRR_OK;
+}
+
+nrr_status nrr_unroll(nrr_ctx* c, int K, const double* X0, double* XK) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (!X0) return fail(c, NRR_E_INVALID, "nrr_unroll: X0 is NULL");
+    if (K < 0 || K > 1024) return fail(c, NRR_E_INVALID, "nrr_unroll: K must be in 0..1024");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    c->unroll_K = -1;
+    return c->fp64 ? unroll_t<double>(c, K, X0, XK) : unroll_t<float>(c, K, X0, XK);
 }
 
 }  // extern "C"

@@ -112,6 +112,14 @@ cudaError_t nrr_launch_aa(const DevProblem<T>& d, int grid, cudaStream_t s);
 template <typename T>
 cudaError_t nrr_launch_gradient(const DevProblem<T>& d, double* grad_X, double* grad_v, const int* order,
                                 int grid, cudaStream_t s);
+// Unrolled backward (kernels_unroll.cu): per-point and per-node adjoint
+// contributions of one MM step given lambda = K^-1 g_bar and X' = X^(k+1);
+// adds dL/dv to gv (caller order) and writes the new g_bar to gd and gt.
+template <typename T>
+cudaError_t nrr_launch_adjoint(const DevProblem<T>& d, const T* lam, const T* Xn, const int* order, T* ebuf,
+                               double* gv, double* gd, T* gt, cudaStream_t s);
+template <typename T>
+cudaError_t nrr_launch_to_t(const double* in, T* out, int n, cudaStream_t s);
 
 // Stage transition of Algorithm 2 (halve nu_a and nu_r, recompute alpha and
 // beta with Eq. WeightSettings, restart the stage). Single device thread.

@@ -99,6 +99,7 @@ _SIGS = [
     ("nrr_time_kernels", ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     ("nrr_energy", ctypes.c_int, [_VP, _VP, _VP]),
     ("nrr_backward", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    ("nrr_unroll", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     ("nrr_set_transforms", ctypes.c_int, [_VP, _VP]),
     ("nrr_set_stage", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double]),
     ("nrr_get_transforms", ctypes.c_int, [_VP, _VP]),
@@ -256,6 +257,16 @@ def nrr_backward(ctx, X=None, mode: int = 0, want_src: bool = True):
     Xa = None if X is None else np.ascontiguousarray(X, dtype=np.float64)
     _check(load().nrr_backward(ctx, int(mode), _ptr(Xa), _ptr(gX), _ptr(gv)), ctx)
     return gX, gv
+
+
+def nrr_unroll(ctx, K: int, X0):
+    """K plain MM steps from X0 (checkpoints kept for nrr_backward mode 1);
+    returns X^(K) [N, 12] float64."""
+    _, _, N, _, _ = nrr_get_sizes(ctx)
+    X0a = np.ascontiguousarray(X0, dtype=np.float64)
+    XK = np.zeros((N, 12), dtype=np.float64)
+    _check(load().nrr_unroll(ctx, int(K), _ptr(X0a), _ptr(XK)), ctx)
+    return XK
 
 
 def nrr_align_energy_noalloc(d2, nu_a: float, w_a, E_align, stream=None):
@@ -419,6 +430,14 @@ class Registration:
     def backward(self, X=None, want_src: bool = True):
         return nrr_backward(self.ctx, X, 0, want_src)
 
+    def unroll(self, K: int, X0) -> np.ndarray:
+        return nrr_unroll(self.ctx, K, X0)
+
+    def unrolled_backward(self, cotangent=None, want_src: bool = True):
+        """dL/dX^(0), dL/dv of the last unroll; cotangent = dL/dX^(K) or
+        None for L = E(X^(K))."""
+        return nrr_backward(self.ctx, cotangent, 1, want_src)
+
     def set_transforms(self, X):
         nrr_set_transforms(self.ctx, X)
 
@@ -473,6 +492,35 @@ def energy_function():
             return grad_out * g, None
 
     return NrrEnergy
+
+
+def unrolled_function():
+    """torch.autograd.Function for K unrolled MM steps: XK = fn.apply(X0, src,
+    reg, K) runs nrr_unroll from X0 [N, 12] (float64 tensor) and returns
+    X^(K); its backward calls nrr_backward mode 1 with the incoming gradient
+    as the cotangent and returns dL/dX0 and dL/dsrc. ``src`` [P, 3] must be
+    the source the registration was created from (it carries the source
+    gradient; the library uses its own copy). Imported lazily so that the
+    binding itself does not need torch."""
+    import torch
+
+    class NrrUnrolled(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X0, src, reg, K):
+            ctx.reg = reg
+            ctx.src_meta = (src.dtype, src.device)
+            XK = reg.unroll(int(K), X0.detach().cpu().numpy().astype(np.float64))
+            return torch.from_numpy(XK).to(device=X0.device, dtype=X0.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            C = grad_out.detach().cpu().numpy().astype(np.float64)
+            gX, gv = ctx.reg.unrolled_backward(np.ascontiguousarray(C))
+            dt, dev = ctx.src_meta
+            return (torch.from_numpy(gX).to(device=grad_out.device, dtype=grad_out.dtype),
+                    torch.from_numpy(gv).to(device=dev, dtype=dt), None, None)
+
+    return NrrUnrolled
 
 
 class BatchRegistration:

@@ -284,8 +284,8 @@ def _grad20k(seed: int = 4) -> Pair:
     p = sphere_pair(20000, 24000, n_bumps=32, amp=0.1, width=0.3,
                     warp_cap=0.15, noise=0.02, outliers=0.10, crop=0.30,
                     seed=seed, same_samples=False)
-    p.params = dict(radius=0.09, k_alpha=100.0, k_beta=1.0, aa_m=0,
-                    unroll=10, precision="mixed")
+    p.params = dict(radius=0.14, k_alpha=100.0, k_beta=1.0, aa_m=0,
+                    unroll=10, precision="fp64")
     p.name = "grad20k"
     return p
 

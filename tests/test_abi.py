@@ -79,3 +79,11 @@ def test_create_rejects_bad_arguments_without_gpu():
     assert lib.nrr_step(None, None) == nrr.NRR_E_INVALID
     assert lib.nrr_solve(None, 0, None) == nrr.NRR_E_INVALID
     assert lib.nrr_energy(None, None, None) == nrr.NRR_E_INVALID
+
+
+def test_unrolled_entry_points_reject_bad_arguments_without_gpu():
+    lib = nrr.load()
+    X = (ctypes.c_double * 12)()
+    assert lib.nrr_unroll(None, 3, X, None) == nrr.NRR_E_INVALID
+    assert lib.nrr_backward(None, 1, None, None, None) == nrr.NRR_E_INVALID
+    assert lib.nrr_last_error(None)
