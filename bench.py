@@ -42,6 +42,32 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 METRIC = "MM iters/s and time-to-converge at 100k pts, mixed vs FP64 GPU, same energy"
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the kernels of a pass from one ncu capture of this benchmark's workload,
+# with the SHA-256 prefix of the kernel's source file at capture time; a
+# figure whose source has changed since is reported as null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_depth100k.txt")
+KERNEL_SOURCES = {"nn_kernel": "kernels_nn.cu", "energy_kernel": "kernels_system.cu",
+                  "assemble_kernel": "kernels_system.cu", "solve_kernel": "kernels_solve.cu",
+                  "aa_kernels": "kernels_aa.cu"}
+
+
+def measured_traffic(kernel: str):
+    """Per-launch DRAM bytes of ``kernel`` from the committed ncu summary, or
+    None if there is none or the kernel's source changed after the capture."""
+    import hashlib
+    try:
+        lines = open(TRAFFIC_FILE).read().splitlines()
+    except OSError:
+        return None
+    src = os.path.join(ROOT, "paper_2206_03410_gb300", "csrc", KERNEL_SOURCES[kernel])
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) >= 3 and parts[0] == kernel and not ln.startswith("#"):
+            return int(float(parts[1])) if parts[2] == digest else None
+    return None
 UNIT = "MM iters/s"
 FLUSH_BYTES = 256 << 20
 
@@ -281,7 +307,7 @@ def run_ours(args):
         achieved = ab[top_name] / (per_launch_ms[top] / 1e3) / 1e9
         roofline = {"kernel": top_name, "bound": "hbm", "achieved": round(achieved, 2),
                     "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 5),
-                    "traffic": None,
+                    "traffic": measured_traffic(top_name),
                     "peak_source": "measured" if peaks else "fallback",
                     "algorithmic_bytes_per_launch": int(ab[top_name]),
                     "avg_launch_ms": round(float(per_launch_ms[top]), 4),
@@ -373,6 +399,11 @@ def cpu_baseline(pair, kw):
             "wall_s": round(time.perf_counter() - t0, 1)}
 
 
+def nrr_launches_per_pass() -> int:
+    from paper_2206_03410_gb300 import nrr
+    return nrr.LAUNCHES_PER_PASS
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -396,7 +427,7 @@ def main():
                    "iters_timed": res["iters"], "passes_timed": res["passes"]},
         "roofline": res["roofline"],
         "clocks": res["clocks"],
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": nrr_launches_per_pass() * args.steps,
         "e2e": res.get("e2e"),
         "ttc": res.get("ttc"),
         "batch": res.get("batch"),
