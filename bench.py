@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--no-ttc", action="store_true", help="skip time-to-converge runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair batch run")
+    ap.add_argument("--ttc-seeds", type=int, default=3,
+                    help="extra seeds of the workload for the mixed-vs-FP64 energy comparison")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
 
@@ -201,6 +204,47 @@ def algorithmic_bytes(P, T, N, nblk, nnz_infl, pcg_iters, n_ent, esz=4, aa_m=5):
             "aa_kernels": aa}
 
 
+def tuned(cfg) -> dict:
+    """Launch shapes chosen by the library's autotuner."""
+    return {"nn_lanes_per_query": cfg.nn_lanes_per_query, "solve_ctas": cfg.solve_ctas,
+            **({"nn_ms": round(cfg.nn_ms, 4), "solve_ms": round(cfg.solve_ms, 4)} if cfg.nn_ms else {}),
+            **({"pass_ms": round(cfg.pass_ms, 4)} if cfg.pass_ms else {})}
+
+
+def ttc_pair(nrr, pair, kw, stream, args) -> dict:
+    """Time-to-converge of the mixed and FP64 paths on one pair and the
+    signed relative gap of their final energies (both in FP64 at the FP64
+    run's final nu)."""
+    import torch
+    src = torch.from_numpy(pair.src).cuda()
+    tgt = torch.from_numpy(pair.tgt).cuda()
+    out = {}
+    finals = {}
+    regs = {}
+    for prec in ("mixed", "fp64"):
+        r = nrr.Registration(src, tgt, stream=stream.cuda_stream, precision=prec, **kw)
+        if not args.no_tune:
+            r.tune()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = r.solve(20000)
+        torch.cuda.synchronize()
+        out[prec + "_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+        out[prec + "_iters"] = info.n_solves
+        finals[prec] = (r.transforms(), info)
+        regs[prec] = r
+    r64 = regs["fp64"]
+    i64 = finals["fp64"][1]
+    r64.set_stage(i64.nu_a, i64.nu_r)
+    e64 = r64.energy(finals["fp64"][0])[0]
+    e32 = r64.energy(finals["mixed"][0])[0]
+    for r in regs.values():
+        r.close()
+    out["gap"] = float((e32 - e64) / abs(e64))
+    out["speedup"] = round(out["fp64_ms"] / out["mixed_ms"], 2)
+    return out
+
+
 def reduce_over_ranks(total_ms: float, iters: float, device) -> tuple[float, float]:
     """Whole-job numbers over the ranks of a replica run: the slowest rank's
     timed milliseconds and the sum of every rank's iterations."""
@@ -233,6 +277,9 @@ def run_ours(args):
     src = torch.from_numpy(pair.src).cuda()
     tgt = torch.from_numpy(pair.tgt).cuda()
     reg = nrr.Registration(src, tgt, stream=stream.cuda_stream, precision="mixed", **kw)
+    launch = {}
+    if not args.no_tune:
+        launch["mixed"] = tuned(reg.tune())
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -314,13 +361,15 @@ def run_ours(args):
                     "launch_ms": {n: round(float(v), 4) for n, v in zip(names, per_launch_ms)},
                     "share": {n: round(float(v / ms.sum()), 4) for n, v in zip(names, ms)}}
         result.update(dict(roofline=roofline, P=reg.P, T=reg.T, N=reg.N, n_edges=reg.n_edges,
-                           last_pcg_iters=avg_pcg, clocks=clk))
+                           last_pcg_iters=avg_pcg, clocks=clk, launch=launch))
 
         # ---- time-to-converge: mixed vs FP64, same energy -----------------
         if not args.no_ttc:
             ttc = {}
             finals = {}
             reg64 = nrr.Registration(src, tgt, stream=stream.cuda_stream, precision="fp64", **kw)
+            if not args.no_tune:
+                launch["fp64"] = tuned(reg64.tune())
             for name, r in (("mixed", reg), ("fp64", reg64)):
                 r.reset()
                 torch.cuda.synchronize()
@@ -339,8 +388,19 @@ def run_ours(args):
             ttc["energy_rel_gap"] = float(abs(e32 - e64) / abs(e64))
             ttc["E_fp64"] = float(e64)
             ttc["E_mixed_in_fp64"] = float(e32)
-            result["ttc"] = ttc
             reg64.close()
+            # the same comparison on further seeds of the workload: signed
+            # relative gap (E_mixed - E_fp64) / E_fp64 at the FP64 run's final nu
+            seeds = []
+            for sd in range(args.ttc_seeds):
+                seeds.append(ttc_pair(nrr, synth.workload(args.workload, seed=100 + sd), kw, stream, args))
+            if seeds:
+                ttc["seeds"] = seeds
+                gaps = [x["gap"] for x in seeds] + [float((e32 - e64) / abs(e64))]
+                ttc["signed_gaps_all"] = gaps
+                ttc["mixed_not_worse"] = int(sum(g <= 1e-5 for g in gaps))
+                ttc["runs"] = len(gaps)
+            result["ttc"] = ttc
 
         # ---- batched pairs (64 independent pairs, one graph launch per pass) ----
         if not args.no_batch:
@@ -351,6 +411,8 @@ def run_ours(args):
             bt = nrr.BatchRegistration([(p.src, p.tgt) for p in pairs], params=prm,
                                        stream=stream.cuda_stream)
             t_create = time.perf_counter() - t0
+            if not args.no_tune:
+                launch["batch"] = tuned(bt.tune())
             runs = []
             for _ in range(2):
                 bt.reset()
@@ -431,6 +493,7 @@ def main():
         "e2e": res.get("e2e"),
         "ttc": res.get("ttc"),
         "batch": res.get("batch"),
+        "launch": res.get("launch"),
     }
     if ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(pair, kw)

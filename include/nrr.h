@@ -323,6 +323,52 @@ nrr_status nrr_batch_get_context(nrr_batch* b, int i, nrr_ctx** out);
 
 void nrr_batch_destroy(nrr_batch* b);
 
+/* Launch shapes of the two kernels whose best shape depends on the problem
+ * (the paper has no counterpart; it runs on a CPU). */
+typedef struct {
+    int    nn_lanes_per_query; /* lanes that share one closest-point query:
+                                  1, 2, 4 or 8 (more lanes shorten the
+                                  serial search of the slowest warps)       */
+    int    solve_ctas;         /* PCG solve: CTAs of the cluster that keeps
+                                  K in shared memory (1..16), or 0 for the
+                                  grid-wide solve. For a batch: -1 = each
+                                  pair's smallest fitting cluster, 0 = its
+                                  largest                                   */
+    double nn_ms, solve_ms;    /* measured mean kernel durations of the
+                                  chosen shapes (nrr_tune; 0 otherwise)     */
+    double pass_ms;            /* measured mean batch pass (nrr_batch_tune) */
+} nrr_launch_config;
+
+/* Current launch shapes of a context (ms fields 0). */
+nrr_status nrr_get_launch_config(nrr_ctx* ctx, nrr_launch_config* out);
+
+/* Sets the launch shapes (NRR_E_INVALID for lanes not in {1,2,4,8} or a
+ * cluster that does not fit this problem or device) and recaptures the
+ * pass graph. Results stay within the tolerances of every shape; the
+ * floating-point summation order, hence the last bits, depend on it. */
+nrr_status nrr_set_launch_config(nrr_ctx* ctx, const nrr_launch_config* cfg);
+
+/* Autotuner: picks the launch shapes by timing them on this context's own
+ * problem. It runs the first pass of Algorithm 2 from X = identity, then
+ * times reps (<= 0: 5) launches of the closest-point kernel for every
+ * lanes-per-query value and of the PCG solve of that pass's system (from the
+ * pass's own warm start) for every cluster size that fits (and the
+ * grid-wide solve), with CUDA events on the
+ * context's stream, keeps the fastest of each and restarts the solve (as
+ * nrr_reset). table_path (may be NULL): a text file of earlier results,
+ * keyed by precision and the half-octave buckets of P, T and N; a usable
+ * entry is applied without timing, a new result is appended. out (host, may
+ * be NULL) receives the choice and its timings. */
+nrr_status nrr_tune(nrr_ctx* ctx, const char* table_path, int reps, nrr_launch_config* out);
+
+/* Autotuner for a batch: for lanes per query in {4, 8, 2} and each pair's
+ * smallest or largest fitting cluster, times reps (<= 0: 3) batch passes
+ * from the start (after one untimed pass), keeps the fastest policy for all
+ * pairs and restarts every pair. Table as for nrr_tune (keyed by precision,
+ * pair count, total points and total nodes). out->pass_ms receives the mean
+ * batch pass of the choice. */
+nrr_status nrr_batch_tune(nrr_batch* b, const char* table_path, int reps, nrr_launch_config* out);
+
 /* Message describing the last failure on ctx (or a global message if ctx is
  * NULL). The string lives until the next call on ctx. */
 const char* nrr_last_error(const nrr_ctx* ctx);

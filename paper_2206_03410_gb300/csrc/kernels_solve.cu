@@ -439,6 +439,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     NrrState* st = d.st;
     if (st->done || st->skip) return;   // the same decision in every CTA
     cg::cluster_group cl = cg::this_cluster();
+    // no CTA touches another's shared memory before every CTA of the cluster
+    // runs: arrive now, wait after the local setup
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
     long long* ts = (d.solve_stats != nullptr && blockIdx.x == 0 && threadIdx.x == 0) ? d.solve_stats : nullptr;
     int tsn = 0;
     auto stamp = [&]() { if (ts && tsn < 64) ts[tsn++] = clock64(); };
@@ -491,6 +494,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     }
     __syncthreads();
 
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     stamp();
     // warps that hold work: four threads per node in the SpMV and the updates
     const int active_warps = min((int)(bd >> 5), ((n1 - n0) * 4 + 31) / 32);

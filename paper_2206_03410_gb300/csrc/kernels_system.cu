@@ -157,78 +157,88 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
 // ---------------------------------------------------------------------------
 // Assembly of K = F^T W_a F + alpha H^T W_r H + beta J^T J and
 // B = F^T W_a Q + alpha H^T W_r Y + beta J^T J Z (Sec. 3.3.2).
-// A group of 8 lanes owns one 4x4 block (row node n, column node k) and sums
-// the precomputed list of its point contributions in a fixed order, then adds
-// the regularisation and rotation parts: deterministic, no atomics.
+// Every 4x4 block sums its precomputed list of point contributions in a
+// fixed order, then adds its regularisation and rotation parts:
+// deterministic, no atomics. A diagonal block (node n, n) collects every
+// point that n influences (about |I|-times more than an off-diagonal block)
+// and the node's row of B: a whole warp owns it and accumulates the 10
+// entries of its symmetric upper triangle. Off-diagonal blocks go four to a
+// warp, 8 lanes each. Warps with diagonal blocks come first.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) assemble_kernel(DevProblem<T> d) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) assemble_kernel(DevProblem<T> d) {
     NrrState* st = d.st;
     if (st->done || st->skip) return;
-    const int lane8 = threadIdx.x & 7;
+    const int lane = threadIdx.x & 31;
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int P = d.P;
+    const int N = d.N;
+    const int n_off = d.nblk - N;
+    const int n_work = N + (n_off + 3) / 4;
     const T alpha = (T)st->alpha, beta = (T)st->beta;
-    // the loop is warp-uniform so that the group shuffles see all 32 lanes
-    for (int b0 = gwarp * 4; b0 < d.nblk; b0 += nwarps * 4) {
-        const int b = min(b0 + ((threadIdx.x & 31) >> 3), d.nblk - 1);
-        const bool active = (b0 + ((threadIdx.x & 31) >> 3)) < d.nblk;
-        const int n = d.blk_row[b], k = d.bsr_col[b];
-        const bool diag = (n == k);
-        const T pnx = d.p[3 * n], pny = d.p[3 * n + 1], pnz = d.p[3 * n + 2];
-        const T pkx = d.p[3 * k], pky = d.p[3 * k + 1], pkz = d.p[3 * k + 2];
-        T acc[16];
-        T accB[12];
+    // the loop is warp-uniform so that the shuffles see all 32 lanes
+    for (int wk = gwarp; wk < n_work; wk += nwarps) {
+        if (wk < N) {
+            // ---- diagonal block of node n and row n of B: one warp ----
+            const int n = wk;
+            const int b = d.diag_blk[n];
+            const T pnx = d.p[3 * n], pny = d.p[3 * n + 1], pnz = d.p[3 * n + 2];
+            T acc[10];
+            T accB[12];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) acc[t] = 0;
+            for (int t = 0; t < 10; ++t) acc[t] = 0;
 #pragma unroll
-        for (int t = 0; t < 12; ++t) accB[t] = 0;
-        const int e_end = active ? d.ent_ptr[b + 1] : 0;
-        for (int e = d.ent_ptr[b] + lane8; e < e_end; e += 8) {
-            const int i = d.ent[e] >> 6;
-            const T wn = d.ent_w[2 * e], wk = d.ent_w[2 * e + 1];
-            const T vx = d.v[i], vy = d.v[P + i], vz = d.v[2 * P + i];
-            const T wai = d.wa[i];
-            const T an[4] = {vx - pnx, vy - pny, vz - pnz, (T)1};
-            const T ak[4] = {vx - pkx, vy - pky, vz - pkz, (T)1};
-            const T c = wai * wn * wk;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const T cr = c * an[r];
-#pragma unroll
-                for (int s = 0; s < 4; ++s) acc[4 * r + s] += cr * ak[s];
-            }
-            if (diag) {
+            for (int t = 0; t < 12; ++t) accB[t] = 0;
+            for (int e = d.ent_ptr[b] + lane, e_end = d.ent_ptr[b + 1]; e < e_end; e += 32) {
+                const int i = d.ent[e] >> 6;
+                const T wn = d.ent_w[2 * e];
+                const T wai = d.wa[i];
+                const T an[4] = {d.v[i] - pnx, d.v[P + i] - pny, d.v[2 * P + i] - pnz, (T)1};
                 // Q_i = u_rho(i) - sum_j w_ij p_j
                 const T Qx = d.u[i] - d.pbar[i];
                 const T Qy = d.u[P + i] - d.pbar[P + i];
                 const T Qz = d.u[2 * P + i] - d.pbar[2 * P + i];
                 const T cb = wai * wn;
+                const T c = cb * wn;
+                int t = 0;
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    const T cr = cb * an[r];
-                    accB[3 * r + 0] += cr * Qx;
-                    accB[3 * r + 1] += cr * Qy;
-                    accB[3 * r + 2] += cr * Qz;
+                    const T cr = c * an[r];
+#pragma unroll
+                    for (int s2 = r; s2 < 4; ++s2) acc[t++] += cr * an[s2];
+                    const T br = cb * an[r];
+                    accB[3 * r + 0] += br * Qx;
+                    accB[3 * r + 1] += br * Qy;
+                    accB[3 * r + 2] += br * Qz;
                 }
             }
-        }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
+            for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int t = 0; t < 16; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+                for (int t = 0; t < 10; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
 #pragma unroll
-            for (int t = 0; t < 12; ++t) accB[t] += __shfl_xor_sync(0xffffffffu, accB[t], o);
-        }
-        if (lane8 != 0 || !active) continue;
-        if (diag) {
+                for (int t = 0; t < 12; ++t) accB[t] += __shfl_xor_sync(0xffffffffu, accB[t], o);
+            }
+            if (lane != 0) continue;
+            T K16[16];
+            {
+                int t = 0;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int s2 = r; s2 < 4; ++s2) {
+                        K16[4 * r + s2] = acc[t];
+                        K16[4 * s2 + r] = acc[t];
+                        ++t;
+                    }
+            }
             // edges (n, j): H row has [0,0,0,-r] at X_n -> r^2 on entry (3,3);
             // B row 3 gets -r * y with y = r (p_n - p_j)
             for (int e = d.adj_ptr[n]; e < d.adj_ptr[n + 1]; ++e) {
                 const int j = d.e_j[e];
                 const T r = d.e_r[e], w = alpha * d.wr[e];
-                acc[15] += w * r * r;
+                K16[15] += w * r * r;
                 accB[9] -= w * r * r * (pnx - d.p[3 * j]);
                 accB[10] -= w * r * r * (pny - d.p[3 * j + 1]);
                 accB[11] -= w * r * r * (pnz - d.p[3 * j + 2]);
@@ -240,29 +250,63 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(DevProblem<T> d) {
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[4 * a + c] += w2 * h[a] * h[c];
+                    for (int cc = 0; cc < 4; ++cc) K16[4 * a + cc] += w2 * h[a] * h[cc];
                     accB[3 * a + 0] += w2 * h[a] * h[0];
                     accB[3 * a + 1] += w2 * h[a] * h[1];
                     accB[3 * a + 2] += w2 * h[a] * h[2];
                 }
             }
             // rotation term: beta on A-rows, B rows 0..2 += beta R_n^T
-            acc[0] += beta; acc[5] += beta; acc[10] += beta;
+            K16[0] += beta; K16[5] += beta; K16[10] += beta;
             const T* R = d.Rm + 9 * n;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) accB[3 * a + c] += beta * R[3 * c + a];
+                for (int cc = 0; cc < 3; ++cc) accB[3 * a + cc] += beta * R[3 * cc + a];
 #pragma unroll
             for (int t = 0; t < 12; ++t) d.Bv[12 * n + t] = accB[t];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) d.Kv[16 * b + t] = K16[t];
         } else {
+            // ---- four off-diagonal blocks, 8 lanes each ----
+            const int q = (wk - N) * 4 + (lane >> 3);
+            const bool active = q < n_off;
+            const int lane8 = lane & 7;
+            const int b = d.offd_blk[active ? q : n_off - 1];
+            const int n = d.blk_row[b], k = d.bsr_col[b];
+            const T pnx = d.p[3 * n], pny = d.p[3 * n + 1], pnz = d.p[3 * n + 2];
+            const T pkx = d.p[3 * k], pky = d.p[3 * k + 1], pkz = d.p[3 * k + 2];
+            T acc[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) acc[t] = 0;
+            const int e_end = active ? d.ent_ptr[b + 1] : 0;
+            for (int e = d.ent_ptr[b] + lane8; e < e_end; e += 8) {
+                const int i = d.ent[e] >> 6;
+                const T wn = d.ent_w[2 * e], wk2 = d.ent_w[2 * e + 1];
+                const T vx = d.v[i], vy = d.v[P + i], vz = d.v[2 * P + i];
+                const T an[4] = {vx - pnx, vy - pny, vz - pnz, (T)1};
+                const T ak[4] = {vx - pkx, vy - pky, vz - pkz, (T)1};
+                const T c = d.wa[i] * wn * wk2;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const T cr = c * an[r];
+#pragma unroll
+                    for (int s2 = 0; s2 < 4; ++s2) acc[4 * r + s2] += cr * ak[s2];
+                }
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+            }
+            if (lane8 != 0 || !active) continue;
             // pair (n, k): block (n, k) gets -r w h_k^T on row 3,
             // h_k = r [(p_n - p_k)^T, 1]
             const int e = d.bsr_edge[b];
             const T r = d.e_r[e], w = alpha * d.wr[e];
             const T hk[4] = {r * (pnx - pkx), r * (pny - pky), r * (pnz - pkz), r};
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[12 + c] -= w * r * hk[c];
+            for (int cc = 0; cc < 4; ++cc) acc[12 + cc] -= w * r * hk[cc];
             // pair (k, n): block (n, k) gets -r' w' h_n on column 3,
             // h_n = r' [(p_k - p_n)^T, 1]
             const int er = d.e_rev[e];
@@ -270,9 +314,9 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(DevProblem<T> d) {
             const T hn[4] = {r2 * (pkx - pnx), r2 * (pky - pny), r2 * (pkz - pnz), r2};
 #pragma unroll
             for (int a = 0; a < 4; ++a) acc[4 * a + 3] -= w2 * r2 * hn[a];
-        }
 #pragma unroll
-        for (int t = 0; t < 16; ++t) d.Kv[16 * b + t] = acc[t];
+            for (int t = 0; t < 16; ++t) d.Kv[16 * b + t] = acc[t];
+        }
     }
 }
 

@@ -65,6 +65,7 @@ struct nrr_ctx {
     int nn_lpq = 8;                    // closest points: lanes per query (1, 2, 4, 8)
     int* d_order = nullptr;            // internal -> caller source index (gradients)
     double* d_grad = nullptr;          // gradient staging [N*12 + P*3]
+    void* d_tune = nullptr;            // autotuner scratch: warm start and output of a solve, [2][N][12] in T
     // unrolled MM steps (nrr_unroll / nrr_backward mode 1)
     int unroll_K = -1;                 // steps of the last nrr_unroll (-1: none)
     double unroll_prm[4] = {0, 0, 0, 0};   // nu_a, nu_r, alpha, beta of that run
@@ -179,18 +180,56 @@ cudaError_t launch_solve_on(nrr_ctx* c, const DevProblem<T>& d) {
 template <typename T>
 cudaError_t launch_solve(nrr_ctx* c) { return launch_solve_on<T>(c, prob<T>(c)); }
 
-// Chooses the cluster solve when one cluster of 16 (or 8) CTAs can hold the
+// Whether the cluster solve with C CTAs can run: every CTA's K rows fit in
+// shared memory and one such cluster can be resident. Fills the launch
+// parameters (K blocks per CTA, dynamic shared memory).
+template <typename T>
+bool cluster_fits(nrr_ctx* c, int C, int* cap_out, size_t* smem_out) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int N = c->N;
+    if (C < 1 || C > 16) return false;
+    const int per = (N + C - 1) / C;
+    if (per * 4 > nrr_solve_cluster_threads() || per >= 4096) return false;
+    int cap = 0;
+    for (int r = 0; r < C; ++r) {
+        const int n0 = std::min(N, r * per), n1 = std::min(N, n0 + per);
+        cap = std::max(cap, c->bsr_ptr[(size_t)n1] - c->bsr_ptr[(size_t)n0]);
+    }
+    const size_t smem = nrr_solve_cluster_smem<T>(cap, per);
+    if (smem + nrr_solve_cluster_static_smem<T>() > (size_t)optin) return false;
+    if (nrr_solve_cluster_setup<T>(C, smem, (size_t)optin) < 1) return false;
+    *cap_out = cap;
+    *smem_out = smem;
+    return true;
+}
+
+// Sets the solve to the cluster of C CTAs (C >= 1, must fit) or to the
+// grid-wide solve (C = 0).
+template <typename T>
+bool set_solver(nrr_ctx* c, int C) {
+    if (C == 0) {
+        c->cl_C = 0;
+        return true;
+    }
+    int cap = 0;
+    size_t smem = 0;
+    if (!cluster_fits<T>(c, C, &cap, &smem)) return false;
+    c->cl_C = C;
+    c->cl_cap = cap;
+    c->cl_smem = smem;
+    return true;
+}
+
+// Chooses the cluster solve when one cluster of up to 16 CTAs can hold the
 // K rows of its nodes in shared memory; otherwise the grid-wide solve.
 template <typename T>
 void choose_solver(nrr_ctx* c) {
     c->cl_C = 0;
     if (std::getenv("NRR_NO_CLUSTER")) return;
-    int optin = 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
-    const int N = c->N;
     // a cluster whose CTAs hold their K rows: by default the largest (more
     // SMs for one pair), with solve_ctas = -1 the smallest (cheaper barriers,
     // SMs left free for the other pairs of a batch)
@@ -200,21 +239,7 @@ void choose_solver(nrr_ctx* c) {
     const int order_small[5] = {1, 2, 4, 8, 16}, order_large[5] = {16, 8, 4, 2, 1};
     for (int C : (smallest ? order_small : order_large)) {
         if (forced > 0 && C != forced) continue;
-        const int per = (N + C - 1) / C;
-        if (per * 4 > nrr_solve_cluster_threads() || per >= 4096) continue;
-        int cap = 0;
-        for (int r = 0; r < C; ++r) {
-            const int n0 = std::min(N, r * per), n1 = std::min(N, n0 + per);
-            cap = std::max(cap, c->bsr_ptr[(size_t)n1] - c->bsr_ptr[(size_t)n0]);
-        }
-        const size_t smem = nrr_solve_cluster_smem<T>(cap, per);
-        if (smem + nrr_solve_cluster_static_smem<T>() > (size_t)optin) continue;
-        if (nrr_solve_cluster_setup<T>(C, smem, (size_t)optin) >= 1) {
-            c->cl_C = C;
-            c->cl_cap = cap;
-            c->cl_smem = smem;
-            return;
-        }
+        if (set_solver<T>(c, C)) return;
     }
 }
 
@@ -236,6 +261,10 @@ cudaError_t launch_pass_any(nrr_ctx* c) { return c->fp64 ? launch_pass<double>(c
 
 nrr_status capture_graph(nrr_ctx* c) {
     c->use_graph = false;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
     if (std::getenv("NRR_NO_GRAPH")) return NRR_OK;
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -478,6 +507,15 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         CK(upload(c, &ew_, ent_w)); d.ent_w = ew_;
         CK(upload(c, &pb_, pbar)); d.pbar = pb_;
         CK(upload(c, &br_, blk_row)); d.blk_row = br_;
+        std::vector<int> diag_blk((size_t)N), offd_blk;
+        for (int n = 0; n < N; ++n)
+            for (int b = bp[(size_t)n]; b < bp[(size_t)n + 1]; ++b) {
+                if (bc[(size_t)b] == n) diag_blk[(size_t)n] = b;
+                else offd_blk.push_back(b);
+            }
+        int *db_, *ob_;
+        CK(upload(c, &db_, diag_blk)); d.diag_blk = db_;
+        CK(upload(c, &ob_, offd_blk)); d.offd_blk = ob_;
     }
     CK(upload(c, &d.X, X0));
     CK(dalloc(c, &d.Xeval, (size_t)N * 12));
@@ -712,6 +750,131 @@ nrr_status unroll_backward_t(nrr_ctx* c, const double* C, double* grad_X, double
     return NRR_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Autotuner: the launch shapes of the two kernels whose best shape depends on
+// the problem - lanes per closest-point query and the CTAs of the cluster
+// solve (or the grid-wide solve) - are timed on the context's own data and
+// the fastest is kept. Results can be cached in a text table keyed by the
+// precision and the half-octave buckets of P, T and N.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+    int fp64, bP, bT, bN;
+};
+
+int half_octave(int64_t x) { return (int)std::floor(2.0 * std::log2((double)std::max<int64_t>(x, 1))); }
+
+TuneKey tune_key(const nrr_ctx* c) { return {c->fp64 ? 1 : 0, half_octave(c->P), half_octave(c->T), half_octave(c->N)}; }
+
+// Last line of the table that matches key: "nrr-tune <fp64> <bP> <bT> <bN> <lpq> <ctas>".
+bool table_lookup(const char* path, const TuneKey& k, int* lpq, int* ctas) {
+    FILE* f = path ? std::fopen(path, "r") : nullptr;
+    if (!f) return false;
+    char line[256];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        int a[6];
+        if (std::sscanf(line, "nrr-tune %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5]) == 6 &&
+            a[0] == k.fp64 && a[1] == k.bP && a[2] == k.bT && a[3] == k.bN) {
+            *lpq = a[4];
+            *ctas = a[5];
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void table_append(const char* path, const TuneKey& k, int lpq, int ctas) {
+    FILE* f = path ? std::fopen(path, "a") : nullptr;
+    if (!f) return;
+    std::fprintf(f, "nrr-tune %d %d %d %d %d %d\n", k.fp64, k.bP, k.bT, k.bN, lpq, ctas);
+    std::fclose(f);
+}
+
+// Mean device milliseconds of reps launches of f() on the context's stream,
+// after one untimed launch.
+template <typename F>
+nrr_status time_launches(nrr_ctx* c, int reps, F&& f, double* ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    cudaError_t e = f();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = f();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(e);
+    *ms = (double)t / reps;
+    return NRR_OK;
+}
+
+bool valid_lpq(int v) { return v == 1 || v == 2 || v == 4 || v == 8; }
+
+// Applies a launch configuration (validated) and recaptures the pass graph.
+template <typename T>
+nrr_status apply_config(nrr_ctx* c, int lpq, int ctas) {
+    if (!valid_lpq(lpq)) return fail(c, NRR_E_INVALID, "lanes per query must be 1, 2, 4 or 8");
+    if (ctas < 0 || ctas > 16 || !set_solver<T>(c, ctas))
+        return fail(c, NRR_E_INVALID, "the cluster solve with " + std::to_string(ctas) + " CTAs does not fit");
+    c->nn_lpq = lpq;
+    return capture_graph(c);
+}
+
+template <typename T>
+nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, double* nn_ms, double* solve_ms) {
+    DevProblem<T>& d = prob<T>(c);
+    const size_t n12 = (size_t)c->N * 12;
+    if (!c->d_tune) CK(cudaMalloc(&c->d_tune, 2 * sizeof(T) * n12));
+    T* x0 = (T*)c->d_tune;
+    // a surrogate system to time the solve on: the first pass from the
+    // start; the solve is then timed from that pass's own warm start X^(0)
+    // (the pass's mix already holds its solution)
+    nrr_status st = nrr_reset(c);
+    if (st != NRR_OK) return st;
+    CK(cudaMemcpyAsync(x0, d.X, sizeof(T) * n12, cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_pass_any(c));
+    CK(cudaMemcpyAsync(d.Xeval, d.X, sizeof(T) * n12, cudaMemcpyDeviceToDevice, c->stream));
+    // closest points at the current iterate, per lanes-per-query
+    *nn_ms = INFINITY;
+    for (int lpq : {1, 2, 4, 8}) {
+        double ms = 0;
+        st = time_launches(c, reps, [&]() { return nrr_launch_nn<T>(d, NRR_MODE_EVAL, lpq, c->stream); }, &ms);
+        if (st != NRR_OK) return st;
+        if (ms < *nn_ms) { *nn_ms = ms; *best_lpq = lpq; }
+    }
+    // the solve of that system, per cluster size (0: grid-wide); the
+    // solution goes to scratch, the pass state is not touched
+    DevProblem<T> ds = d;
+    ds.X = x0;
+    ds.G = x0 + n12;
+    *solve_ms = INFINITY;
+    const int keep_C = c->cl_C;
+    for (int C : {16, 8, 4, 2, 1, 0}) {
+        if (!set_solver<T>(c, C)) continue;
+        if (C == 0 && !c->coop) continue;
+        double ms = 0;
+        st = time_launches(c, reps, [&]() { return launch_solve_on<T>(c, ds); }, &ms);
+        if (st != NRR_OK) return st;
+        if (ms < *solve_ms) { *solve_ms = ms; *best_ctas = C; }
+    }
+    if (!std::isfinite(*solve_ms)) *best_ctas = keep_C;
+    st = pull_state(c);
+    if (st != NRR_OK) return st;
+    if (c->h_state->status != 0) return fail(c, (nrr_status)c->h_state->status, "nrr_tune: device-side check failed");
+    // the evaluations wrote v_hat into the non-kept buffer
+    c->h_state->vlast = c->h_state->vk ^ 1;
+    st = push_state(c);
+    if (st != NRR_OK) return st;
+    st = apply_config<T>(c, *best_lpq, *best_ctas);
+    if (st != NRR_OK) return st;
+    return nrr_reset(c);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -754,6 +917,7 @@ void nrr_destroy(nrr_ctx* c) {
     for (void* p : c->allocs) cudaFree(p);
     if (c->d_order) cudaFree(c->d_order);
     if (c->d_grad) cudaFree(c->d_grad);
+    if (c->d_tune) cudaFree(c->d_tune);
     if (c->d_ck) cudaFree(c->d_ck);
     if (c->d_adj) cudaFree(c->d_adj);
     if (c->d_adjd) cudaFree(c->d_adjd);
@@ -831,7 +995,8 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         if (v == 1 || v == 2 || v == 4 || v == 8) c->nn_lpq = v;
     }
     c->grid_energy = 2 * c->num_sms;
-    c->grid_asm = std::max(1, std::min(8 * c->num_sms, (c->N + c->E2 + 31) / 32));
+    // assembly: one warp per diagonal block, one per four off-diagonal blocks
+    c->grid_asm = std::max(1, std::min(16 * c->num_sms, (c->N + (c->E2 + 3) / 4 + 7) / 8));
     // Anderson kernels: one element of X per thread up to grid_energy CTAs
     // (the partials buffer is sized for grid_energy)
     c->grid_aa = std::max(1, std::min(c->grid_energy, (c->N * 12 + 255) / 256));
@@ -1195,6 +1360,52 @@ nrr_status nrr_get_system(nrr_ctx* c, double* Kdense, double* B) {
     return c->fp64 ? get_system_t<double>(c, Kdense, B) : get_system_t<float>(c, Kdense, B);
 }
 
+nrr_status nrr_get_launch_config(nrr_ctx* c, nrr_launch_config* out) {
+    if (!c || !out) return fail(c, NRR_E_INVALID, "NULL argument");
+    out->nn_lanes_per_query = c->nn_lpq;
+    out->solve_ctas = c->cl_C;
+    out->nn_ms = 0.0;
+    out->solve_ms = 0.0;
+    out->pass_ms = 0.0;
+    return NRR_OK;
+}
+
+nrr_status nrr_set_launch_config(nrr_ctx* c, const nrr_launch_config* cfg) {
+    if (!c || !cfg) return fail(c, NRR_E_INVALID, "NULL argument");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    return c->fp64 ? apply_config<double>(c, cfg->nn_lanes_per_query, cfg->solve_ctas)
+                   : apply_config<float>(c, cfg->nn_lanes_per_query, cfg->solve_ctas);
+}
+
+nrr_status nrr_tune(nrr_ctx* c, const char* table_path, int reps, nrr_launch_config* out) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    if (reps <= 0) reps = 5;
+    if (reps > 1000) return fail(c, NRR_E_INVALID, "nrr_tune: reps must be at most 1000");
+    const TuneKey key = tune_key(c);
+    int lpq = 0, ctas = 0;
+    double nn_ms = 0.0, solve_ms = 0.0;
+    nrr_status st = NRR_E_INVALID;
+    if (table_lookup(table_path, key, &lpq, &ctas)) {
+        st = c->fp64 ? apply_config<double>(c, lpq, ctas) : apply_config<float>(c, lpq, ctas);
+        if (st == NRR_OK) st = nrr_reset(c);
+    }
+    if (st != NRR_OK) {   // no usable entry: measure
+        st = c->fp64 ? tune_t<double>(c, reps, &lpq, &ctas, &nn_ms, &solve_ms)
+                     : tune_t<float>(c, reps, &lpq, &ctas, &nn_ms, &solve_ms);
+        if (st != NRR_OK) return st;
+        table_append(table_path, key, lpq, ctas);
+    }
+    if (out) {
+        out->nn_lanes_per_query = lpq;
+        out->solve_ctas = ctas;
+        out->nn_ms = nn_ms;
+        out->solve_ms = solve_ms;
+        out->pass_ms = 0.0;
+    }
+    return NRR_OK;
+}
+
 nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, double* grad_src) {
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
     if (mode != 0 && mode != 1) return fail(c, NRR_E_INVALID, "nrr_backward: mode must be 0 or 1");
@@ -1273,6 +1484,8 @@ nrr_status batch_fail(nrr_batch* b, nrr_status code, const std::string& msg) {
     return code;
 }
 
+nrr_status batch_capture(nrr_batch* b);
+
 #define BK(call)                                                                           \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
@@ -1283,7 +1496,116 @@ nrr_status batch_fail(nrr_batch* b, nrr_status code, const std::string& msg) {
 
 }  // namespace
 
+
+namespace {
+
+// Captures the batch graph: fork every pair's pass onto its own stream,
+// join, gather the flags.
+nrr_status batch_capture(nrr_batch* b) {
+    const int n = (int)b->ctx.size();
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaEventRecord(b->events[(size_t)n], b->stream);
+    for (int i = 0; i < n && ce == cudaSuccess; ++i) {
+        nrr_ctx* c = b->ctx[(size_t)i];
+        ce = cudaStreamWaitEvent(c->stream, b->events[(size_t)n], 0);
+        if (ce == cudaSuccess) ce = launch_pass_any(c);
+        if (ce == cudaSuccess) ce = cudaEventRecord(b->events[(size_t)i], c->stream);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, b->events[(size_t)i], 0);
+    }
+    if (ce == cudaSuccess) {
+        gather_flags<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_states, n, b->d_flags);
+        ce = cudaGetLastError();
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    if (ce != cudaSuccess || ee != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return batch_fail(b, NRR_E_CUDA, std::string("batch graph capture failed: ") +
+                                             cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    BK(ie);
+    return NRR_OK;
+}
+
+// Applies one launch policy to every pair of a batch: lanes per query and
+// each pair's smallest (policy -1) or largest (policy 0) fitting cluster.
+nrr_status batch_apply(nrr_batch* b, int lpq, int policy) {
+    for (nrr_ctx* c : b->ctx) {
+        c->nn_lpq = lpq;
+        c->prm.solve_ctas = policy;
+        if (c->fp64) choose_solver<double>(c); else choose_solver<float>(c);
+        nrr_status st = capture_graph(c);
+        if (st != NRR_OK) return st;
+    }
+    return batch_capture(b);
+}
+
+}  // namespace
+
 extern "C" {
+
+nrr_status nrr_batch_tune(nrr_batch* b, const char* table_path, int reps, nrr_launch_config* out) {
+    if (!b) return batch_fail(nullptr, NRR_E_INVALID, "batch is NULL");
+    if (reps <= 0) reps = 3;
+    if (reps > 1000) return batch_fail(b, NRR_E_INVALID, "nrr_batch_tune: reps must be at most 1000");
+    int64_t sumP = 0, sumN = 0;
+    for (nrr_ctx* c : b->ctx) { sumP += c->P; sumN += c->N; }
+    // key: precision, pair count, total points and nodes (half octaves)
+    const TuneKey key = {b->ctx[0]->fp64 ? 3 : 2, half_octave((int64_t)b->ctx.size()), half_octave(sumP),
+                         half_octave(sumN)};
+    int lpq = 0, policy = 0;
+    double best_ms = 0.0;
+    nrr_status st = NRR_E_INVALID;
+    if (table_lookup(table_path, key, &lpq, &policy) && valid_lpq(lpq) && (policy == -1 || policy == 0)) {
+        st = batch_apply(b, lpq, policy);
+    }
+    if (st != NRR_OK) {
+        best_ms = INFINITY;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        BK(cudaEventCreate(&e0));
+        BK(cudaEventCreate(&e1));
+        for (int cl : {4, 8, 2})
+            for (int pol : {-1, 0}) {
+                st = batch_apply(b, cl, pol);
+                if (st == NRR_OK) st = nrr_batch_reset(b);
+                if (st != NRR_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+                cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);   // untimed first pass
+                if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(b->gexec, b->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float t = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                if (e != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    BK(e);
+                }
+                if (t / reps < best_ms) { best_ms = t / reps; lpq = cl; policy = pol; }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        st = batch_apply(b, lpq, policy);
+        if (st != NRR_OK) return st;
+        table_append(table_path, key, lpq, policy);
+    }
+    st = nrr_batch_reset(b);
+    if (st != NRR_OK) return st;
+    if (out) {
+        out->nn_lanes_per_query = lpq;
+        out->solve_ctas = policy;
+        out->nn_ms = 0.0;
+        out->solve_ms = 0.0;
+        out->pass_ms = best_ms;
+    }
+    return NRR_OK;
+}
 
 void nrr_batch_destroy(nrr_batch* b) {
     if (!b) return;
@@ -1331,32 +1653,10 @@ nrr_status nrr_batch_create(nrr_batch** out, int n_pairs, const float* const* sr
     BK(cudaMemcpy(b->d_states, sts.data(), sizeof(NrrState*) * (size_t)n, cudaMemcpyHostToDevice));
     BK(cudaMalloc(&b->d_flags, sizeof(int) * 4 * (size_t)n));
     BK(cudaMallocHost(&b->h_flags, sizeof(int) * 4 * (size_t)n));
-    // capture: fork every pair's pass onto its own stream, join, gather
     b->events.resize((size_t)n + 1);
     for (auto& e : b->events) BK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaEventRecord(b->events[(size_t)n], b->stream);
-    for (int i = 0; i < n && ce == cudaSuccess; ++i) {
-        nrr_ctx* c = b->ctx[(size_t)i];
-        ce = cudaStreamWaitEvent(c->stream, b->events[(size_t)n], 0);
-        if (ce == cudaSuccess) ce = launch_pass_any(c);
-        if (ce == cudaSuccess) ce = cudaEventRecord(b->events[(size_t)i], c->stream);
-        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, b->events[(size_t)i], 0);
-    }
-    if (ce == cudaSuccess) {
-        gather_flags<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_states, n, b->d_flags);
-        ce = cudaGetLastError();
-    }
-    cudaGraph_t g = nullptr;
-    cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
-    if (ce != cudaSuccess || ee != cudaSuccess || !g) {
-        if (g) cudaGraphDestroy(g);
-        return batch_fail(b, NRR_E_CUDA, std::string("batch graph capture failed: ") +
-                                             cudaGetErrorString(ce != cudaSuccess ? ce : ee));
-    }
-    cudaError_t ie = cudaGraphInstantiate(&b->gexec, g, 0);
-    cudaGraphDestroy(g);
-    BK(ie);
+    nrr_status cst = batch_capture(b);
+    if (cst != NRR_OK) return cst;
     guard.release();
     *out = b;
     return NRR_OK;

@@ -75,6 +75,8 @@ struct DevProblem {
     const int* ent;         // packed (point << 6 | slot_row << 3 | slot_col)
     const T* ent_w;         // [n_ent][2] (w_row, w_col) of the entry's point
     const int* blk_row;     // [nblk] row node of each block
+    const int* diag_blk;    // [N] block (n, n) of each node
+    const int* offd_blk;    // [nblk - N] the off-diagonal blocks, in BSR order
     const T* pbar;          // [3][P] sum_j w_ij p_j (constant part of Q_i)
     T* Kv;
     T* Bv;

@@ -56,6 +56,19 @@ class NrrParams(ctypes.Structure):
     ]
 
 
+class NrrLaunchConfig(ctypes.Structure):
+    _fields_ = [
+        ("nn_lanes_per_query", ctypes.c_int),
+        ("solve_ctas", ctypes.c_int),
+        ("nn_ms", ctypes.c_double),
+        ("solve_ms", ctypes.c_double),
+        ("pass_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class NrrStepInfo(ctypes.Structure):
     _fields_ = [
         ("E", ctypes.c_double),
@@ -119,6 +132,10 @@ _SIGS = [
     ("nrr_batch_reset", ctypes.c_int, [_VP]),
     ("nrr_batch_get_context", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
     ("nrr_batch_destroy", None, [_VP]),
+    ("nrr_get_launch_config", ctypes.c_int, [_VP, ctypes.POINTER(NrrLaunchConfig)]),
+    ("nrr_set_launch_config", ctypes.c_int, [_VP, ctypes.POINTER(NrrLaunchConfig)]),
+    ("nrr_tune", ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(NrrLaunchConfig)]),
+    ("nrr_batch_tune", ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(NrrLaunchConfig)]),
     ("nrr_last_error", ctypes.c_char_p, [_VP]),
 ]
 
@@ -270,6 +287,31 @@ def nrr_unroll(ctx, K: int, X0):
     XK = np.zeros((N, 12), dtype=np.float64)
     _check(load().nrr_unroll(ctx, int(K), _ptr(X0a), _ptr(XK)), ctx)
     return XK
+
+
+def nrr_get_launch_config(ctx) -> NrrLaunchConfig:
+    out = NrrLaunchConfig()
+    _check(load().nrr_get_launch_config(ctx, ctypes.byref(out)), ctx)
+    return out
+
+
+def nrr_set_launch_config(ctx, nn_lanes_per_query: int, solve_ctas: int):
+    cfg = NrrLaunchConfig(nn_lanes_per_query=int(nn_lanes_per_query), solve_ctas=int(solve_ctas))
+    _check(load().nrr_set_launch_config(ctx, ctypes.byref(cfg)), ctx)
+
+
+def nrr_tune(ctx, table: str | None = None, reps: int = 0) -> NrrLaunchConfig:
+    out = NrrLaunchConfig()
+    path = table.encode() if table else None
+    _check(load().nrr_tune(ctx, path, int(reps), ctypes.byref(out)), ctx)
+    return out
+
+
+def nrr_batch_tune(batch, table: str | None = None, reps: int = 0) -> NrrLaunchConfig:
+    out = NrrLaunchConfig()
+    path = table.encode() if table else None
+    _check(load().nrr_batch_tune(batch, path, int(reps), ctypes.byref(out)))
+    return out
 
 
 def nrr_align_energy_noalloc(d2, nu_a: float, w_a, E_align, stream=None):
@@ -433,6 +475,16 @@ class Registration:
     def backward(self, X=None, want_src: bool = True):
         return nrr_backward(self.ctx, X, 0, want_src)
 
+    def tune(self, table: str | None = None, reps: int = 0) -> NrrLaunchConfig:
+        """Autotunes the launch shapes on this problem (restarts the solve)."""
+        return nrr_tune(self.ctx, table, reps)
+
+    def launch_config(self) -> NrrLaunchConfig:
+        return nrr_get_launch_config(self.ctx)
+
+    def set_launch_config(self, nn_lanes_per_query: int, solve_ctas: int):
+        nrr_set_launch_config(self.ctx, nn_lanes_per_query, solve_ctas)
+
     def unroll(self, K: int, X0) -> np.ndarray:
         return nrr_unroll(self.ctx, K, X0)
 
@@ -561,6 +613,10 @@ class BatchRegistration:
 
     def reset(self):
         _check(load().nrr_batch_reset(self.b))
+
+    def tune(self, table: str | None = None, reps: int = 0) -> NrrLaunchConfig:
+        """Autotunes the batch's launch policy (restarts every pair)."""
+        return nrr_batch_tune(self.b, table, reps)
 
     def context(self, i: int):
         c = _VP()

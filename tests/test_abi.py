@@ -87,3 +87,12 @@ def test_unrolled_entry_points_reject_bad_arguments_without_gpu():
     assert lib.nrr_unroll(None, 3, X, None) == nrr.NRR_E_INVALID
     assert lib.nrr_backward(None, 1, None, None, None) == nrr.NRR_E_INVALID
     assert lib.nrr_last_error(None)
+
+
+def test_tuner_entry_points_reject_bad_arguments_without_gpu():
+    lib = nrr.load()
+    cfg = nrr.NrrLaunchConfig()
+    assert lib.nrr_tune(None, None, 0, ctypes.byref(cfg)) == nrr.NRR_E_INVALID
+    assert lib.nrr_batch_tune(None, None, 0, ctypes.byref(cfg)) == nrr.NRR_E_INVALID
+    assert lib.nrr_get_launch_config(None, ctypes.byref(cfg)) == nrr.NRR_E_INVALID
+    assert lib.nrr_set_launch_config(None, ctypes.byref(cfg)) == nrr.NRR_E_INVALID
