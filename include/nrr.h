@@ -157,13 +157,15 @@ nrr_status nrr_solve(nrr_ctx* ctx, int max_passes, nrr_step_info* info);
 nrr_status nrr_enqueue_passes(nrr_ctx* ctx, int n);
 
 /* Runs n passes like nrr_enqueue_passes, launching the steps of a pass
- * individually with CUDA events recorded around each on the context's
- * stream, and adds their durations (milliseconds, summed over the n passes)
- * to out_ms[0..4] = {deform + closest points, energy + weights + safeguard,
- * assembly of K and B, PCG solve, Anderson mix (two kernels)}. Synchronises.
- * For measuring kernel durations; the result of the passes is the same as
- * with nrr_enqueue_passes. */
-nrr_status nrr_time_kernels(nrr_ctx* ctx, int n, double out_ms[5]);
+ * one after the other with CUDA events recorded around each on the
+ * context's stream, and adds their durations (milliseconds, summed over the
+ * n passes) to out_ms[0..5] = {deform + closest points, regularisation and
+ * rotation terms, alignment energy + weights + safeguard, assembly of K and
+ * B, PCG solve, Anderson mix (two kernels)}. Synchronises. (In the pass
+ * graph the second step runs beside the first.) For measuring kernel
+ * durations; the result of the passes is the same as with
+ * nrr_enqueue_passes. */
+nrr_status nrr_time_kernels(nrr_ctx* ctx, int n, double out_ms[6]);
 
 /* Restarts Algorithm 2 from the beginning: X = identity, first stage with
  * the initial nu_a, nu_r, empty Anderson history, counters at zero. The

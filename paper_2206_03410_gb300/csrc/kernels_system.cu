@@ -33,25 +33,23 @@ __device__ __forceinline__ float t_expm1<float>(float x) { return expm1f(x); }
 template <>
 __device__ __forceinline__ double t_expm1<double>(double x) { return expm1(x); }
 
+// Terms of Eq. (objective_func) that depend on X only, not on the closest
+// points: the regularisation term (Eq. RegTerm) with its surrogate weights
+// w^r_ij, and the rotation term with the projections proj_R(A_n). A pass
+// runs this kernel on a parallel branch of its graph, beside the
+// closest-point search. Each CTA writes its two partial sums to
+// d.xpartials; energy_kernel adds them.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
+__global__ void __launch_bounds__(kThreads) xterm_kernel(DevProblem<T> d) {
     __shared__ double sh[kThreads / 32];
-    __shared__ int s_last, s_reject;
     NrrState* st = d.st;
     if (MODE == NRR_MODE_PASS && st->done) return;
     const T* X = (MODE == NRR_MODE_EVAL) ? d.Xeval : d.X;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gstride = gridDim.x * blockDim.x;
-    const double nua = st->nu_a, nur = st->nu_r;
-    const T ia = (T)(1.0 / (2.0 * nua * nua));
+    const double nur = st->nu_r;
     const T ir = (T)(1.0 / (2.0 * nur * nur));
-    double ea = 0.0, er = 0.0, eo = 0.0;
-    // alignment term (Eq. AlignmentTerm) and its surrogate weights w^a_i
-    for (int i = gtid; i < d.P; i += gstride) {
-        const T x = d.d2[i] * ia;
-        ea += (double)(-t_expm1<T>(-x));
-        d.wa[i] = t_exp<T>(-x) * ia;
-    }
+    double er = 0.0, eo = 0.0;
     // regularisation term (Eq. RegTerm) over directed pairs, weights w^r_ij
     for (int e = gtid; e < d.E2; e += gstride) {
         const int a = d.e_i[e], b = d.e_j[e];
@@ -85,13 +83,38 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
         }
         eo += s;
     }
-    const double sa = block_sum(ea, sh);
     const double sr = block_sum(er, sh);
     const double so = block_sum(eo, sh);
     if (threadIdx.x == 0) {
+        d.xpartials[2 * blockIdx.x + 0] = sr;
+        d.xpartials[2 * blockIdx.x + 1] = so;
+    }
+}
+
+// The alignment term (Eq. AlignmentTerm) and its surrogate weights w^a_i
+// from the closest-point distances, the sum of all terms (FP64, fixed
+// order: the last CTA adds every CTA's partial sums and xterm_kernel's), and
+// in a pass the safeguard test of Algorithm 2.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
+    __shared__ double sh[kThreads / 32];
+    __shared__ int s_last, s_reject;
+    NrrState* st = d.st;
+    if (MODE == NRR_MODE_PASS && st->done) return;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gstride = gridDim.x * blockDim.x;
+    const double nua = st->nu_a;
+    const T ia = (T)(1.0 / (2.0 * nua * nua));
+    double ea = 0.0;
+    // alignment term (Eq. AlignmentTerm) and its surrogate weights w^a_i
+    for (int i = gtid; i < d.P; i += gstride) {
+        const T x = d.d2[i] * ia;
+        ea += (double)(-t_expm1<T>(-x));
+        d.wa[i] = t_exp<T>(-x) * ia;
+    }
+    const double sa = block_sum(ea, sh);
+    if (threadIdx.x == 0) {
         d.partials[blockIdx.x * NRR_PARTIAL_STRIDE + 0] = sa;
-        d.partials[blockIdx.x * NRR_PARTIAL_STRIDE + 1] = sr;
-        d.partials[blockIdx.x * NRR_PARTIAL_STRIDE + 2] = so;
         __threadfence();
         const unsigned t = atomicAdd(&st->cnt_energy, 1u);
         s_last = (t == gridDim.x - 1);
@@ -103,10 +126,11 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
     {
         // the last CTA adds all partials: thread-strided, then a fixed-order tree
         double pa = 0.0, pr = 0.0, po = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
             pa += __ldcg(d.partials + b * NRR_PARTIAL_STRIDE + 0);
-            pr += __ldcg(d.partials + b * NRR_PARTIAL_STRIDE + 1);
-            po += __ldcg(d.partials + b * NRR_PARTIAL_STRIDE + 2);
+        for (int b = threadIdx.x; b < d.n_xpart; b += blockDim.x) {
+            pr += __ldcg(d.xpartials + 2 * b + 0);
+            po += __ldcg(d.xpartials + 2 * b + 1);
         }
         const double ta = block_sum(pa, sh);
         const double tr = block_sum(pr, sh);
@@ -446,6 +470,16 @@ cudaError_t nrr_launch_energy(const DevProblem<T>& d, int mode, int grid, cudaSt
     else energy_kernel<T, NRR_MODE_PASS><<<grid, kThreads, 0, s>>>(d);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t nrr_launch_xterm(const DevProblem<T>& d, int mode, cudaStream_t s) {
+    if (mode == NRR_MODE_EVAL) xterm_kernel<T, NRR_MODE_EVAL><<<d.n_xpart, kThreads, 0, s>>>(d);
+    else xterm_kernel<T, NRR_MODE_PASS><<<d.n_xpart, kThreads, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+template cudaError_t nrr_launch_xterm<float>(const DevProblem<float>&, int, cudaStream_t);
+template cudaError_t nrr_launch_xterm<double>(const DevProblem<double>&, int, cudaStream_t);
 
 template <typename T>
 cudaError_t nrr_launch_assemble(const DevProblem<T>& d, int grid, cudaStream_t s) {

@@ -46,6 +46,8 @@ struct nrr_ctx {
     bool fp64 = false;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t aux = nullptr;                 // parallel branch of a pass
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     int64_t P = 0, T = 0;
     int N = 0, E2 = 0, nblk = 0, n_leaves = 0, n_supers = 0;
@@ -243,10 +245,20 @@ void choose_solver(nrr_ctx* c) {
     }
 }
 
+// One pass. The regularisation and rotation terms depend on X only: they run
+// on the auxiliary stream (a parallel branch of the captured graph) beside
+// the closest-point search, and the energy kernel waits for both.
 template <typename T>
 cudaError_t launch_pass(nrr_ctx* c) {
     DevProblem<T>& d = prob<T>(c);
-    cudaError_t e = nrr_launch_nn<T>(d, NRR_MODE_PASS, c->nn_lpq, c->stream);
+    cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+    if (e == cudaSuccess) e = nrr_launch_xterm<T>(d, NRR_MODE_PASS, c->aux);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->aux);
+    if (e != cudaSuccess) return e;
+    e = nrr_launch_nn<T>(d, NRR_MODE_PASS, c->nn_lpq, c->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
     if (e != cudaSuccess) return e;
     e = nrr_launch_energy<T>(d, NRR_MODE_PASS, c->grid_energy, c->stream);
     if (e != cudaSuccess) return e;
@@ -541,6 +553,10 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     CK(dalloc(c, &d.Minv, (size_t)N * 16));
     const int max_ctas = std::max({c->grid_energy, c->grid_solve, 1});
     CK(dalloc(c, &d.partials, (size_t)2 * max_ctas * NRR_PARTIAL_STRIDE));
+    // few CTAs: the kernel runs beside the closest-point search and should
+    // take few of its SM slots
+    d.n_xpart = std::max(1, std::min(std::max(1, c->num_sms / 4), (c->E2 + c->N + 255) / 256));
+    CK(dalloc(c, &d.xpartials, (size_t)2 * d.n_xpart));
     d.st = c->d_state;
     d.nn_stats = nullptr;
     d.solve_stats = nullptr;
@@ -652,6 +668,7 @@ nrr_status unroll_system_at(nrr_ctx* c, const T* Xk) {
     DevProblem<T>& d = prob<T>(c);
     CK(cudaMemcpyAsync(d.Xeval, Xk, sizeof(T) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
     CK(nrr_launch_nn<T>(d, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+    CK(nrr_launch_xterm<T>(d, NRR_MODE_EVAL, c->stream));
     CK(nrr_launch_energy<T>(d, NRR_MODE_EVAL, c->grid_energy, c->stream));
     CK(nrr_launch_assemble<T>(d, c->grid_asm, c->stream));
     return NRR_OK;
@@ -717,6 +734,7 @@ nrr_status unroll_backward_t(nrr_ctx* c, const double* C, double* grad_X, double
         // L = E(X^(K)): closest points held at X^(K)
         CK(cudaMemcpyAsync(d.Xeval, ck + (size_t)K * n12, sizeof(T) * n12, cudaMemcpyDeviceToDevice, c->stream));
         CK(nrr_launch_nn<T>(d, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+        CK(nrr_launch_xterm<T>(d, NRR_MODE_EVAL, c->stream));
         CK(nrr_launch_energy<T>(d, NRR_MODE_EVAL, c->grid_energy, c->stream));
         const int grid = std::max(1, (c->N + 31) / 32);
         CK(nrr_launch_gradient<T>(d, gd, gv, c->d_order, grid, c->stream));
@@ -923,6 +941,9 @@ void nrr_destroy(nrr_ctx* c) {
     if (c->d_adjd) cudaFree(c->d_adjd);
     if (c->d_state) cudaFree(c->d_state);
     if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -968,6 +989,9 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
+    CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     std::vector<float> src, tgt, tmp;
     CK(fetch_floats(src_xyz, (size_t)P * 3, src, c->stream));
     CK(fetch_floats(tgt_xyz, (size_t)T * 3, tgt, c->stream));
@@ -1103,10 +1127,10 @@ nrr_status nrr_enqueue_passes(nrr_ctx* c, int n) {
     return NRR_OK;
 }
 
-nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[5]) {
+nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[6]) {
     if (!c || n < 0 || !out_ms) return fail(c, NRR_E_INVALID, "bad argument");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
-    constexpr int kSteps = 5;
+    constexpr int kSteps = 6;
     cudaEvent_t ev[kSteps + 1];
     for (auto& e : ev) CK(cudaEventCreate(&e));
     nrr_status result = NRR_OK;
@@ -1116,16 +1140,18 @@ nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[5]) {
             if (c->fp64) {
                 DevProblem<double>& d = c->dd;
                 e = s == 0 ? nrr_launch_nn<double>(d, NRR_MODE_PASS, c->nn_lpq, c->stream)
-                  : s == 1 ? nrr_launch_energy<double>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
-                  : s == 2 ? nrr_launch_assemble<double>(d, c->grid_asm, c->stream)
-                  : s == 3 ? launch_solve<double>(c)
+                  : s == 1 ? nrr_launch_xterm<double>(d, NRR_MODE_PASS, c->stream)
+                  : s == 2 ? nrr_launch_energy<double>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
+                  : s == 3 ? nrr_launch_assemble<double>(d, c->grid_asm, c->stream)
+                  : s == 4 ? launch_solve<double>(c)
                            : nrr_launch_aa<double>(d, c->grid_aa, c->stream);
             } else {
                 DevProblem<float>& d = c->df;
                 e = s == 0 ? nrr_launch_nn<float>(d, NRR_MODE_PASS, c->nn_lpq, c->stream)
-                  : s == 1 ? nrr_launch_energy<float>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
-                  : s == 2 ? nrr_launch_assemble<float>(d, c->grid_asm, c->stream)
-                  : s == 3 ? launch_solve<float>(c)
+                  : s == 1 ? nrr_launch_xterm<float>(d, NRR_MODE_PASS, c->stream)
+                  : s == 2 ? nrr_launch_energy<float>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
+                  : s == 3 ? nrr_launch_assemble<float>(d, c->grid_asm, c->stream)
+                  : s == 4 ? launch_solve<float>(c)
                            : nrr_launch_aa<float>(d, c->grid_aa, c->stream);
             }
             if (e == cudaSuccess) e = cudaEventRecord(ev[s + 1], c->stream);
@@ -1174,11 +1200,13 @@ nrr_status nrr_energy(nrr_ctx* c, const double* X, double out_terms[4]) {
         if (X) { st = write_X<double>(c, c->dd.Xeval, X); if (st != NRR_OK) return st; }
         else CK(cudaMemcpyAsync(c->dd.Xeval, c->dd.X, sizeof(double) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
         CK(nrr_launch_nn<double>(c->dd, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+        CK(nrr_launch_xterm<double>(c->dd, NRR_MODE_EVAL, c->stream));
         CK(nrr_launch_energy<double>(c->dd, NRR_MODE_EVAL, c->grid_energy, c->stream));
     } else {
         if (X) { st = write_X<float>(c, c->df.Xeval, X); if (st != NRR_OK) return st; }
         else CK(cudaMemcpyAsync(c->df.Xeval, c->df.X, sizeof(float) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
         CK(nrr_launch_nn<float>(c->df, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+        CK(nrr_launch_xterm<float>(c->df, NRR_MODE_EVAL, c->stream));
         CK(nrr_launch_energy<float>(c->df, NRR_MODE_EVAL, c->grid_energy, c->stream));
     }
     st = pull_state(c);

@@ -88,6 +88,8 @@ struct DevProblem {
     T* Minv;
     // reductions
     double* partials;   // [max_ctas * NRR_PARTIAL_STRIDE]
+    double* xpartials;  // [n_xpart][2] E_reg, E_rot partial sums of xterm_kernel's CTAs
+    int n_xpart;        // CTAs of xterm_kernel
     NrrState* st;
     // optional per-warp counters of the closest-point search (NULL: off):
     // [warps][4] = {cycles, super tiles visited, leaves staged, leaves scanned}
@@ -107,6 +109,9 @@ template <typename T>
 cudaError_t nrr_launch_energy(const DevProblem<T>& d, int mode, int grid, cudaStream_t s);
 template <typename T>
 cudaError_t nrr_launch_assemble(const DevProblem<T>& d, int grid, cudaStream_t s);
+// Regularisation and rotation terms (X only; d.n_xpart CTAs).
+template <typename T>
+cudaError_t nrr_launch_xterm(const DevProblem<T>& d, int mode, cudaStream_t s);
 template <typename T>
 cudaError_t nrr_launch_solve(const DevProblem<T>& d, int grid, cudaStream_t s, bool cooperative);
 template <typename T>
