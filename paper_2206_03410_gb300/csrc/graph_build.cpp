@@ -9,11 +9,68 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <thread>
 #include <unordered_map>
 
 #include "nrr_internal.h"
 
 namespace {
+
+// Number of host threads for setup work on n items, at least `grain` items
+// per thread.
+int64_t setup_threads(int64_t n, int64_t grain = 4096) {
+    const int64_t hw = (int64_t)std::max(1u, std::thread::hardware_concurrency());
+    return std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw, 64), n / grain));
+}
+
+// Runs f(chunk, begin, end) over [0, n) split into nt contiguous chunks on
+// the host's cores (setup work; each chunk writes only its own outputs, so
+// results do not depend on the number of threads).
+template <class F>
+void parallel_chunks_idx(int64_t n, int64_t nt, F&& f) {
+    if (nt <= 1) { f((int64_t)0, (int64_t)0, n); return; }
+    std::vector<std::thread> th;
+    const int64_t per = (n + nt - 1) / nt;
+    for (int64_t t = 0; t < nt; ++t) {
+        const int64_t b = std::min(n, t * per), e = std::min(n, b + per);
+        th.emplace_back([&f, t, b, e]() { f(t, b, e); });
+    }
+    for (auto& x : th) x.join();
+}
+
+template <class F>
+void parallel_chunks(int64_t n, F&& f, int64_t grain = 4096) {
+    parallel_chunks_idx(n, setup_threads(n, grain), [&f](int64_t, int64_t b, int64_t e) { f(b, e); });
+}
+
+// Sorts v (whose elements are all distinct) with chunks sorted in parallel
+// and merged pairwise in parallel; the result is the unique sorted order.
+template <class E>
+void parallel_sort(std::vector<E>& v) {
+    const int64_t n = (int64_t)v.size();
+    int64_t nt = setup_threads(n);
+    if (nt <= 1) { std::sort(v.begin(), v.end()); return; }
+    const int64_t per = (n + nt - 1) / nt;
+    std::vector<int64_t> bounds;
+    for (int64_t t = 0; t <= nt; ++t) bounds.push_back(std::min(n, t * per));
+    parallel_chunks_idx(n, nt, [&](int64_t t, int64_t, int64_t) {
+        std::sort(v.begin() + bounds[(size_t)t], v.begin() + bounds[(size_t)t + 1]);
+    });
+    while (bounds.size() > 2) {
+        std::vector<int64_t> next;
+        std::vector<std::thread> th;
+        for (size_t k = 0; k + 2 < bounds.size(); k += 2) {
+            const int64_t a = bounds[k], m = bounds[k + 1], b = bounds[k + 2];
+            th.emplace_back([&v, a, m, b]() { std::inplace_merge(v.begin() + a, v.begin() + m, v.begin() + b); });
+            next.push_back(a);
+        }
+        if (bounds.size() % 2 == 0) next.push_back(bounds[bounds.size() - 2]);
+        next.push_back(bounds.back());
+        for (auto& x : th) x.join();
+        bounds.swap(next);
+    }
+}
 
 struct Grid {
     double lo[3];
@@ -43,12 +100,14 @@ struct Grid {
         for (int d = 0; d < 3; ++d)
             dims[d] = std::max<int64_t>(1, (int64_t)std::floor((hi[d] - lo[d]) / h) + 1);
         std::vector<std::pair<int64_t, int>> kv((size_t)n);
-        for (int64_t i = 0; i < n; ++i) {
-            int64_t c[3];
-            cell_of(V + 3 * i, c);
-            kv[(size_t)i] = {key(c[0], c[1], c[2]), (int)i};
-        }
-        std::sort(kv.begin(), kv.end());
+        parallel_chunks(n, [&](int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i) {
+                int64_t c[3];
+                cell_of(V + 3 * i, c);
+                kv[(size_t)i] = {key(c[0], c[1], c[2]), (int)i};
+            }
+        });
+        parallel_sort(kv);   // (cell, index) pairs are distinct
         items.resize((size_t)n);
         for (size_t i = 0; i < kv.size(); ++i) {
             items[i] = kv[i].second;
@@ -110,24 +169,43 @@ void jacobi_eig3(const double Ain[9], double ev[3], double Q[9]) {
 
 }  // namespace
 
+void nrr_parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f) { parallel_chunks(n, f); }
+
 double nrr_mean_spacing(const double* V, int64_t P, int k) {
     if (P < 2) return 0.0;
-    int kk = (int)std::min<int64_t>(k, P - 1);
-    // cell size from the bbox and count: about 4 points per cell on a surface
+    const int kk = (int)std::min<int64_t>(k, P - 1);
+    // cells of about three point spacings (from the bbox and the count); the
+    // points of each cell scan the candidates of its 27 neighbouring cells,
+    // gathered once per cell, and fall back to a growing shell search when
+    // their kk-th neighbour is not certified within that block
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t i = 0; i < P; ++i)
         for (int d = 0; d < 3; ++d) {
             lo[d] = std::min(lo[d], V[3 * i + d]);
             hi[d] = std::max(hi[d], V[3 * i + d]);
         }
-    double diag = std::sqrt(sqd(lo, hi));
-    double cell = diag / std::sqrt((double)P) * 1.5;
+    const double diag = std::sqrt(sqd(lo, hi));
+    double cell = diag / std::sqrt((double)P) * 3.0;
     if (!(cell > 0)) cell = 1.0;
     Grid g;
     g.build(V, P, cell);
-    double total = 0.0;
-    std::vector<double> best;
-    for (int64_t i = 0; i < P; ++i) {
+    // cells as runs of g.items (sorted by cell key)
+    std::vector<int64_t> run_start;
+    {
+        int64_t prev_key = -1;
+        for (int64_t s = 0; s < P; ++s) {
+            int64_t c[3];
+            g.cell_of(V + 3 * (int64_t)g.items[(size_t)s], c);
+            const int64_t key = g.key(c[0], c[1], c[2]);
+            if (s == 0 || key != prev_key) run_start.push_back(s);
+            prev_key = key;
+        }
+        run_start.push_back(P);
+    }
+    const int64_t n_cells = (int64_t)run_start.size() - 1;
+    // per point: the sum of its kk nearest distances, then a sum in point order
+    std::vector<double> per_point((size_t)P, 0.0);
+    auto shell_search = [&](int64_t i, std::vector<double>& best) {
         const double* q = V + 3 * i;
         int64_t c[3];
         g.cell_of(q, c);
@@ -148,12 +226,50 @@ double nrr_mean_spacing(const double* V, int64_t P, int k) {
                             }
                         });
                     }
-            double reach = (double)s * g.h;
-            bool out_of_grid = s > std::max({g.dims[0], g.dims[1], g.dims[2]});
+            const double reach = (double)s * g.h;
+            const bool out_of_grid = s > std::max({g.dims[0], g.dims[1], g.dims[2]});
             if (best[(size_t)kk - 1] <= reach * reach || out_of_grid) break;
         }
-        for (int t = 0; t < kk; ++t) total += std::sqrt(best[(size_t)t]);
-    }
+    };
+    parallel_chunks(n_cells, [&](int64_t c0, int64_t c1) {
+        std::vector<double> best;
+        std::vector<int> cand;
+        std::vector<double> cpos;   // candidate coordinates, contiguous
+        for (int64_t cidx = c0; cidx < c1; ++cidx) {
+            const int64_t s0 = run_start[(size_t)cidx], s1 = run_start[(size_t)cidx + 1];
+            int64_t c[3];
+            g.cell_of(V + 3 * (int64_t)g.items[(size_t)s0], c);
+            cand.clear();
+            for (int64_t x = c[0] - 1; x <= c[0] + 1; ++x)
+                for (int64_t y = c[1] - 1; y <= c[1] + 1; ++y)
+                    for (int64_t z = c[2] - 1; z <= c[2] + 1; ++z)
+                        g.visit_cell(x, y, z, [&](int j) { cand.push_back(j); });
+            cpos.resize(cand.size() * 3);
+            for (size_t t = 0; t < cand.size(); ++t)
+                for (int d = 0; d < 3; ++d) cpos[3 * t + d] = V[3 * (int64_t)cand[t] + d];
+            for (int64_t sidx = s0; sidx < s1; ++sidx) {
+                const int64_t i = g.items[(size_t)sidx];
+                const double* q = V + 3 * i;
+                best.assign((size_t)kk, INFINITY);
+                for (size_t t = 0; t < cand.size(); ++t) {
+                    if (cand[t] == (int)i) continue;
+                    const double d2 = sqd(q, cpos.data() + 3 * t);
+                    if (d2 < best[(size_t)kk - 1]) {
+                        size_t pos = (size_t)kk - 1;
+                        while (pos > 0 && best[pos - 1] > d2) { best[pos] = best[pos - 1]; --pos; }
+                        best[pos] = d2;
+                    }
+                }
+                // every point outside the 27 cells is at least one cell width away
+                if (!(best[(size_t)kk - 1] <= g.h * g.h)) shell_search(i, best);
+                double sp = 0.0;
+                for (int t = 0; t < kk; ++t) sp += std::sqrt(best[(size_t)t]);
+                per_point[(size_t)i] = sp;
+            }
+        }
+    }, 64);
+    double total = 0.0;
+    for (int64_t i = 0; i < P; ++i) total += per_point[(size_t)i];
     return total / ((double)P * kk);
 }
 
@@ -184,20 +300,26 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
     std::vector<double> proj((size_t)P);
     for (int64_t i = 0; i < P; ++i)
         proj[(size_t)i] = V[3 * i] * ax[0] + V[3 * i + 1] * ax[1] + V[3 * i + 2] * ax[2];
+    // ascending projection, ties to the lower index: (projection, index)
+    // pairs are distinct
+    std::vector<std::pair<double, int>> pk((size_t)P);
+    for (int64_t i = 0; i < P; ++i) pk[(size_t)i] = {proj[(size_t)i], (int)i};
+    parallel_sort(pk);
     std::vector<int> order((size_t)P);
-    for (int64_t i = 0; i < P; ++i) order[(size_t)i] = (int)i;
-    std::sort(order.begin(), order.end(), [&](int a, int b) {
-        return proj[(size_t)a] < proj[(size_t)b] || (proj[(size_t)a] == proj[(size_t)b] && a < b);
-    });
+    for (int64_t i = 0; i < P; ++i) order[(size_t)i] = pk[(size_t)i].second;
 
     // Greedy radius sampling: a point becomes a node if it has no influencing
     // node yet; the new node influences every point strictly within R.
     Grid grid;
     grid.build(V, P, R);
-    std::vector<std::vector<std::pair<double, int>>> infl((size_t)P);
+    // (point, squared distance, node) of every influence, appended in node
+    // order; a point is covered once some node influences it
+    struct Infl { int pt; int node; double d2; };
+    std::vector<Infl> trip;
+    std::vector<unsigned char> covered((size_t)P, 0);
     g.nodes.clear();
     for (int i : order) {
-        if (!g.nodes.empty() && !infl[(size_t)i].empty()) continue;
+        if (!g.nodes.empty() && covered[(size_t)i]) continue;
         int j = (int)g.nodes.size();
         g.nodes.push_back(i);
         const double* q = V + 3 * (int64_t)i;
@@ -208,17 +330,34 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
                 for (int64_t z = c[2] - 1; z <= c[2] + 1; ++z)
                     grid.visit_cell(x, y, z, [&](int pt) {
                         double d2 = sqd(q, V + 3 * (int64_t)pt);
-                        if (d2 < R2) infl[(size_t)pt].push_back({d2, j});
+                        if (d2 < R2) {
+                            trip.push_back({pt, j, d2});
+                            covered[(size_t)pt] = 1;
+                        }
                     });
     }
-    // Influence sets: the K nearest nodes, weights of Eq. (weight_data)
+    // grouped by point (counting sort, node order kept within a point)
+    std::vector<int64_t> iptr((size_t)P + 1, 0);
+    for (const Infl& t : trip) iptr[(size_t)t.pt + 1]++;
+    for (int64_t i = 0; i < P; ++i) iptr[(size_t)i + 1] += iptr[(size_t)i];
+    std::vector<std::pair<double, int>> iv(trip.size());
+    {
+        std::vector<int64_t> fill(iptr.begin(), iptr.end() - 1);
+        for (const Infl& t : trip) iv[(size_t)fill[(size_t)t.pt]++] = {t.d2, t.node};
+    }
+    // Influence sets: the K nearest nodes, weights of Eq. (weight_data);
+    // point chunks in parallel, each with its own list of node pairs
     g.nidx.assign((size_t)P * K, -1);
     g.w.assign((size_t)P * K, 0.0);
-    std::vector<std::pair<int, int>> edge_list;
-    for (int64_t i = 0; i < P; ++i) {
-        auto& L = infl[(size_t)i];
-        std::sort(L.begin(), L.end());
-        int n = (int)std::min<size_t>(L.size(), (size_t)K);
+    const int64_t nt = setup_threads(P);
+    std::vector<std::vector<std::pair<int, int>>> chunk_edges((size_t)nt);
+    parallel_chunks_idx(P, nt, [&](int64_t t, int64_t i0, int64_t i1) {
+    std::vector<std::pair<int, int>>& edge_list = chunk_edges[(size_t)t];
+    for (int64_t i = i0; i < i1; ++i) {
+        std::pair<double, int>* L = iv.data() + iptr[(size_t)i];
+        const size_t nl = (size_t)(iptr[(size_t)i + 1] - iptr[(size_t)i]);
+        std::sort(L, L + nl);
+        int n = (int)std::min<size_t>(nl, (size_t)K);
         double raw[NRR_MAX_INFL];
         double sum = 0.0;
         for (int s = 0; s < n; ++s) {
@@ -236,6 +375,11 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
                 edge_list.push_back({std::min(u, v), std::max(u, v)});
             }
     }
+    std::sort(edge_list.begin(), edge_list.end());
+    edge_list.erase(std::unique(edge_list.begin(), edge_list.end()), edge_list.end());
+    });
+    std::vector<std::pair<int, int>> edge_list;
+    for (auto& ce : chunk_edges) edge_list.insert(edge_list.end(), ce.begin(), ce.end());
     std::sort(edge_list.begin(), edge_list.end());
     edge_list.erase(std::unique(edge_list.begin(), edge_list.end()), edge_list.end());
     g.edges.clear();
@@ -296,17 +440,19 @@ void nrr_curve_order(const float* pts, int64_t n, const double lo[3], const doub
     // consecutive points are always spatially adjacent (no jumps between
     // distant regions), so runs of 32 points have compact bounding boxes
     std::vector<std::pair<uint64_t, int>> kv((size_t)n);
-    for (int64_t i = 0; i < n; ++i) {
-        uint32_t c[3];
-        for (int d = 0; d < 3; ++d) {
-            double ext = hi[d] - lo[d];
-            double f = ext > 0 ? ((double)pts[3 * i + d] - lo[d]) / ext : 0.0;
-            f = std::min(std::max(f, 0.0), 1.0);
-            c[d] = (uint32_t)std::llround(f * 2097151.0);
+    parallel_chunks(n, [&](int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i) {
+            uint32_t c[3];
+            for (int d = 0; d < 3; ++d) {
+                double ext = hi[d] - lo[d];
+                double f = ext > 0 ? ((double)pts[3 * i + d] - lo[d]) / ext : 0.0;
+                f = std::min(std::max(f, 0.0), 1.0);
+                c[d] = (uint32_t)std::llround(f * 2097151.0);
+            }
+            kv[(size_t)i] = {hilbert3(c[0], c[1], c[2]), (int)i};
         }
-        kv[(size_t)i] = {hilbert3(c[0], c[1], c[2]), (int)i};
-    }
-    std::sort(kv.begin(), kv.end());
+    });
+    parallel_sort(kv);   // (code, index) pairs are distinct
     order.resize((size_t)n);
     if (codes_sorted) codes_sorted->resize((size_t)n);
     for (size_t i = 0; i < kv.size(); ++i) {

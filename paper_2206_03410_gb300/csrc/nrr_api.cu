@@ -1,6 +1,7 @@
 // C ABI of the registration library (include/nrr.h): context creation,
 // per-pass launch sequence captured in a CUDA graph, and accessors.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -8,6 +9,7 @@
 #include <limits>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "nrr_device.cuh"
@@ -85,6 +87,20 @@ struct nrr_ctx {
 };
 
 namespace {
+
+// Wall-clock phases of nrr_create, printed to stderr when the environment
+// variable NRR_SETUP_TIMES is set (profiling of the host setup).
+struct SetupTimer {
+    bool on = std::getenv("NRR_SETUP_TIMES") != nullptr;
+    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+    void lap(const char* what) {
+        if (!on) return;
+        const auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "nrr_create %-22s %8.2f ms\n", what,
+                     std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
 
 nrr_status fail(nrr_ctx* c, nrr_status code, const std::string& msg) {
     if (c) c->err = msg;
@@ -323,7 +339,7 @@ void fill_info(const NrrState& s, nrr_step_info* info) {
 // Creation
 // ---------------------------------------------------------------------------
 template <typename T>
-nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::vector<float>& tgt) {
+nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::vector<float>& tgt, SetupTimer& tm) {
     DevProblem<T>& d = prob<T>(c);
     const int64_t P = c->P, Tn = c->T;
     const HostGraph& g = c->hg;
@@ -339,11 +355,16 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         c->diag = std::sqrt(dx * dx + dy * dy + dz * dz);
     }
     std::vector<uint64_t> src_codes, tgt_codes;
-    nrr_curve_order(src.data(), P, lo, hi, c->src_order, &src_codes);
     std::vector<int> tgt_order;
-    nrr_curve_order(tgt.data(), Tn, lo, hi, tgt_order, &tgt_codes);
+    {
+        // the two orders are independent: the target's on a second thread
+        std::thread tt([&]() { nrr_curve_order(tgt.data(), Tn, lo, hi, tgt_order, &tgt_codes); });
+        nrr_curve_order(src.data(), P, lo, hi, c->src_order, &src_codes);
+        tt.join();
+    }
     c->src_rank.assign((size_t)P, 0);
     for (int64_t ii = 0; ii < P; ++ii) c->src_rank[(size_t)c->src_order[(size_t)ii]] = (int)ii;
+    tm.lap("curve orders");
 
     // source SoA and influence CSR in internal order
     std::vector<T> v((size_t)(3 * P));
@@ -401,23 +422,38 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         auto first = bc.begin() + bp[(size_t)a], last = bc.begin() + bp[(size_t)a + 1];
         return (int)(std::lower_bound(first, last, b) - bc.begin());
     };
-    // per-block contribution lists (point, slot_row, slot_col), by point
+    // per-block contribution lists (point, slot_row, slot_col), by point:
+    // the block of every (point, slot, slot) in parallel, then a counting
+    // sort by block that keeps point order
+    std::vector<int64_t> pent((size_t)P + 1, 0);
+    for (int64_t ii = 0; ii < P; ++ii) {
+        const int64_t k = infl_ptr[(size_t)ii + 1] - infl_ptr[(size_t)ii];
+        pent[(size_t)ii + 1] = pent[(size_t)ii] + k * k;
+    }
+    std::vector<int> eblk((size_t)pent[(size_t)P]);
+    nrr_parallel_for(P, [&](int64_t i0, int64_t i1) {
+        for (int64_t ii = i0; ii < i1; ++ii) {
+            int64_t o = pent[(size_t)ii];
+            for (int sa = infl_ptr[(size_t)ii]; sa < infl_ptr[(size_t)ii + 1]; ++sa)
+                for (int sb = infl_ptr[(size_t)ii]; sb < infl_ptr[(size_t)ii + 1]; ++sb)
+                    eblk[(size_t)o++] = block_of(infl_node[(size_t)sa], infl_node[(size_t)sb]);
+        }
+    });
     std::vector<int> ent_cnt((size_t)c->nblk + 1, 0);
-    for (int64_t ii = 0; ii < P; ++ii)
-        for (int sa = infl_ptr[(size_t)ii]; sa < infl_ptr[(size_t)ii + 1]; ++sa)
-            for (int sb = infl_ptr[(size_t)ii]; sb < infl_ptr[(size_t)ii + 1]; ++sb)
-                ent_cnt[(size_t)block_of(infl_node[(size_t)sa], infl_node[(size_t)sb]) + 1]++;
+    for (int b : eblk) ent_cnt[(size_t)b + 1]++;
     for (int b = 0; b < c->nblk; ++b) ent_cnt[(size_t)b + 1] += ent_cnt[(size_t)b];
     std::vector<int> ent((size_t)ent_cnt[(size_t)c->nblk]);
     std::vector<int> fillp(ent_cnt.begin(), ent_cnt.end() - 1);
     for (int64_t ii = 0; ii < P; ++ii) {
         const int b0 = infl_ptr[(size_t)ii];
+        int64_t o = pent[(size_t)ii];
         for (int sa = b0; sa < infl_ptr[(size_t)ii + 1]; ++sa)
             for (int sb = b0; sb < infl_ptr[(size_t)ii + 1]; ++sb) {
-                const int blk = block_of(infl_node[(size_t)sa], infl_node[(size_t)sb]);
+                const int blk = eblk[(size_t)o++];
                 ent[(size_t)fillp[(size_t)blk]++] = (int)((ii << 6) | ((sa - b0) << 3) | (sb - b0));
             }
     }
+    tm.lap("BSR + contribution lists");
     std::vector<T> ent_w(ent.size() * 2);
     for (size_t e = 0; e < ent.size(); ++e) {
         const int ii = ent[e] >> 6, sa = (ent[e] >> 3) & 7, sb = ent[e] & 7;
@@ -487,6 +523,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     std::vector<T> X0((size_t)N * 12, (T)0);
     for (int j = 0; j < N; ++j) { X0[(size_t)12 * j + 0] = 1; X0[(size_t)12 * j + 4] = 1; X0[(size_t)12 * j + 8] = 1; }
 
+    tm.lap("leaves + initial bound");
     d.P = (int)P; d.N = N; d.E2 = E2; d.n_leaves = nl; d.n_supers = ns; d.nblk = c->nblk;
     d.aa_m = c->prm.aa_m;
     d.pcg_max = c->prm.pcg_max_iters;
@@ -565,6 +602,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         CK(dalloc(c, &ss, 64));
         d.solve_stats = ss;
     }
+    tm.lap("uploads");
     if (std::getenv("NRR_NN_STATS")) {
         const size_t warps = (size_t)(P + 7) / 8 + 64;   // enough for any lanes-per-query
         unsigned long long* ns = nullptr;
@@ -992,6 +1030,7 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    SetupTimer tm;
     std::vector<float> src, tgt, tmp;
     CK(fetch_floats(src_xyz, (size_t)P * 3, src, c->stream));
     CK(fetch_floats(tgt_xyz, (size_t)T * 3, tgt, c->stream));
@@ -1004,13 +1043,16 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         CK(fetch_floats(tgt_nrm, (size_t)T * 3, tmp, c->stream));
         if (!finite3(tmp)) return fail(nullptr, NRR_E_INVALID, "non-finite target normals");
     }
+    tm.lap("inputs");
     // l-bar, radius and the deformation graph (Algorithm 1)
     std::vector<double> V(src.begin(), src.end());
     const bool need_lbar = prm.graph_radius <= 0 || prm.nu_r <= 0 || prm.nu_a_min <= 0;
     c->hg.lbar = need_lbar ? nrr_mean_spacing(V.data(), P, 6) : std::nan("");
+    tm.lap("l-bar");
     const double R = prm.graph_radius > 0 ? prm.graph_radius : 5.0 * c->hg.lbar;
     if (!(R > 0)) return fail(nullptr, NRR_E_INVALID, "graph radius must be positive");
     nrr_build_graph(V.data(), P, R, prm.max_influence, c->hg);
+    tm.lap("graph (Algorithm 1)");
     c->N = (int)c->hg.nodes.size();
     c->E2 = (int)c->hg.r.size();
     // launch geometry
@@ -1035,9 +1077,10 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     CK(cudaMalloc(&c->d_state, sizeof(NrrState)));
     CK(cudaMallocHost(&c->h_state, sizeof(NrrState)));
     std::memset(c->h_state, 0, sizeof(NrrState));
-    nrr_status st = c->fp64 ? build_device<double>(c, src, tgt) : build_device<float>(c, src, tgt);
+    nrr_status st = c->fp64 ? build_device<double>(c, src, tgt, tm) : build_device<float>(c, src, tgt, tm);
     if (st != NRR_OK) return st;
     if (c->fp64) choose_solver<double>(c); else choose_solver<float>(c);
+    tm.lap("solver choice");
     NrrState& s = *c->h_state;
     s.k_alpha = prm.k_alpha; s.k_beta = prm.k_beta;
     s.alpha_fixed = prm.alpha; s.beta_fixed = prm.beta;
@@ -1053,6 +1096,7 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         st = c->fp64 ? median_distance<double>(c, &nu_a0) : median_distance<float>(c, &nu_a0);
         if (st != NRR_OK) return st;
     }
+    tm.lap("median distance");
     double nu_min = prm.nu_a_min > 0 ? prm.nu_a_min : c->hg.lbar / std::sqrt(3.0);
     if (!prm.anneal) nu_min = nu_a0;
     s.nu_a_min = nu_min;
@@ -1067,6 +1111,7 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     if (st != NRR_OK) return st;
     st = capture_graph(c);
     if (st != NRR_OK) return st;
+    tm.lap("state + graph capture");
     guard.release();
     *out = c;
     return NRR_OK;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -61,6 +62,9 @@ struct HostGraph {
 };
 
 // graph_build.cpp
+// Runs f(begin, end) over [0, n) in contiguous chunks on the host's cores
+// (setup work; f writes only the outputs of its own range).
+void nrr_parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f);
 double nrr_mean_spacing(const double* V, int64_t P, int k);
 void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g);
 void nrr_curve_order(const float* pts, int64_t n, const double lo[3],
