@@ -71,6 +71,53 @@ def welsch(x2: np.ndarray, nu: float) -> np.ndarray:
     return 1.0 - np.exp(-np.asarray(x2, dtype=np.float64) / (2.0 * nu * nu))
 
 
+# Robust functions of the alignment and regularisation terms. The paper's
+# method uses Welsch's function; Sec. 4.2 compares it with two variants that
+# replace it by the squared l2 norm, with all alignment weights 1 ("l2") or
+# with an alignment weight 0 once a distance reaches 3 nu_a ("l2r"). The
+# l2r weights are the MM weights of the truncated quadratic min(d^2, 9 nu_a^2),
+# which is the energy read here for that variant; the regularisation term of
+# both variants is sum |D_ij|^2.
+ROBUST = ("welsch", "l2", "l2r")
+
+
+def align_psi(d2: np.ndarray, nu_a: float, robust: str = "welsch") -> np.ndarray:
+    """Per-point alignment energy as a function of the squared distance."""
+    d2 = np.asarray(d2, dtype=np.float64)
+    if robust == "welsch":
+        return welsch(d2, nu_a)
+    if robust == "l2":
+        return d2.copy()
+    if robust == "l2r":
+        return np.minimum(d2, 9.0 * nu_a * nu_a)
+    raise ValueError(robust)
+
+
+def align_weight(d2: np.ndarray, nu_a: float, robust: str = "welsch") -> np.ndarray:
+    """Derivative of align_psi w.r.t. the squared distance: the weight of the
+    quadratic surrogate (Eq. AlignQuadSurrogate for Welsch's function)."""
+    d2 = np.asarray(d2, dtype=np.float64)
+    if robust == "welsch":
+        return np.exp(-d2 / (2.0 * nu_a * nu_a)) / (2.0 * nu_a * nu_a)
+    if robust == "l2":
+        return np.ones_like(d2)
+    if robust == "l2r":
+        return (d2 < 9.0 * nu_a * nu_a).astype(np.float64)
+    raise ValueError(robust)
+
+
+def reg_psi(Dn2: np.ndarray, nu_r: float, robust: str = "welsch") -> np.ndarray:
+    Dn2 = np.asarray(Dn2, dtype=np.float64)
+    return welsch(Dn2, nu_r) if robust == "welsch" else Dn2.copy()
+
+
+def reg_weight(Dn2: np.ndarray, nu_r: float, robust: str = "welsch") -> np.ndarray:
+    Dn2 = np.asarray(Dn2, dtype=np.float64)
+    if robust == "welsch":
+        return np.exp(-Dn2 / (2.0 * nu_r * nu_r)) / (2.0 * nu_r * nu_r)
+    return np.ones_like(Dn2)
+
+
 def welsch_surrogate(x: np.ndarray, y: np.ndarray, nu: float) -> np.ndarray:
     """Eq. (WelschSurrogateFunc): psi(y) + (1 - psi(y)) / (2 nu^2) (x^2 - y^2)."""
     py = welsch(np.asarray(y) ** 2, nu)
@@ -103,11 +150,12 @@ def proj_rotation(A: np.ndarray) -> np.ndarray:
     return U @ (D[..., :, None] * Vt)
 
 
-def energy_terms(V, U, graph, X, nu_a, nu_r, rho=None):
+def energy_terms(V, U, graph, X, nu_a, nu_r, rho=None, robust="welsch"):
     """Eq. (objective_func) terms at X. Returns dict with E_align, E_reg,
     E_rot, the closest points (rho, d2), v_hat, D and the rotations R.
     ``rho`` replaces the closest-point search (used only by tests that
-    supply known correspondences)."""
+    supply known correspondences); ``robust`` selects the variant of Sec.
+    4.2 (see ROBUST)."""
     vh = deform(V, graph.nidx, graph.w, graph.p, X)
     U64 = np.asarray(U, dtype=np.float64)
     if rho is None:
@@ -115,10 +163,10 @@ def energy_terms(V, U, graph, X, nu_a, nu_r, rho=None):
     else:
         diff = vh - U64[rho]
         d2 = diff[:, 0] ** 2 + diff[:, 1] ** 2 + diff[:, 2] ** 2
-    e_align = float(np.sum(welsch(d2, nu_a)))
+    e_align = float(np.sum(align_psi(d2, nu_a, robust)))
     D = reg_residuals(graph.p, graph.dpair, graph.r, X)
     Dn2 = np.sum(D * D, axis=1)
-    e_reg = float(np.sum(welsch(Dn2, nu_r)))
+    e_reg = float(np.sum(reg_psi(Dn2, nu_r, robust)))
     A = A_of(X)
     Rm = proj_rotation(A) if len(A) else A
     e_rot = float(np.sum((A - Rm) ** 2))
@@ -130,7 +178,7 @@ def total_energy(terms: dict, alpha: float, beta: float) -> float:
     return terms["E_align"] + alpha * terms["E_reg"] + beta * terms["E_rot"]
 
 
-def energy_gradient(V, U, graph, X, nu_a, nu_r, alpha, beta, rho=None):
+def energy_gradient(V, U, graph, X, nu_a, nu_r, alpha, beta, rho=None, robust="welsch"):
     """Gradient of E (Eq. objective_func) with the closest points held at
     their values at X (rho is piecewise constant in X), the node positions
     p_j and the weights w_ij held constant.
@@ -146,9 +194,9 @@ def energy_gradient(V, U, graph, X, nu_a, nu_r, alpha, beta, rho=None):
     Returns (grad_X [N,12], grad_v [P,3])."""
     V = np.asarray(V, dtype=np.float64)
     U = np.asarray(U, dtype=np.float64)
-    t = energy_terms(V, U, graph, X, nu_a, nu_r, rho=rho)
+    t = energy_terms(V, U, graph, X, nu_a, nu_r, rho=rho, robust=robust)
     r = t["vhat"] - U[t["rho"]]
-    wa = np.exp(-t["d2"] / (2 * nu_a * nu_a)) / (2 * nu_a * nu_a)
+    wa = align_weight(t["d2"], nu_a, robust)
     N = graph.N
     gX = np.zeros((N, 4, 3))
     gv = np.zeros_like(V)
@@ -164,7 +212,7 @@ def energy_gradient(V, U, graph, X, nu_a, nu_r, alpha, beta, rho=None):
         gv[m] += 2.0 * wa[m, None] * wij[:, None] * np.einsum("nab,na->nb", A[jj], r[m])
     if len(graph.dpair):
         D = t["D"]
-        wr = np.exp(-np.sum(D * D, axis=1) / (2 * nu_r * nu_r)) / (2 * nu_r * nu_r)
+        wr = reg_weight(np.sum(D * D, axis=1), nu_r, robust)
         i, j = graph.dpair[:, 0], graph.dpair[:, 1]
         rr = graph.r
         hj = np.concatenate([rr[:, None] * (graph.p[i] - graph.p[j]), rr[:, None]], axis=1)

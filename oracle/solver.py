@@ -26,6 +26,17 @@ Readings of Algorithm 2 used here:
   edge count, |V_G| = N, unless given explicitly.
 * eps defaults to 1e-5 times the bbox diagonal of source and target (the
   paper's 1e-5 on inputs scaled to unit diagonal).
+* Variants of Sec. 4.2 (Params.robust, Params.nu_fixed): "l2" replaces both
+  Welsch functions by squared norms (all weights 1) and runs one stage (its
+  energy has no nu); "l2r" keeps the nu_a schedule and gives an alignment
+  weight 0 once a distance reaches 3 nu_a (the MM weights of the truncated
+  quadratic min(d^2, 9 nu_a^2)). For both, alpha = k_alpha |V| / |E_G| and
+  beta = k_beta |V| / |V_G|: the factors nu_r^2/nu_a^2 and 1/(2 nu_a^2) of
+  Eq. (WeightSettings) scale Welsch's curvature at 0 (psi_nu(x) ~ x^2 /
+  (2 nu^2)), which the squared norms do not have. nu_fixed = "max" / "min" /
+  "med" runs one stage at the first stage's (nu_a, nu_r), at the last
+  stage's, or at their means, the stages being those the annealing would
+  run.
 """
 from __future__ import annotations
 
@@ -56,6 +67,8 @@ class Params:
     max_total_passes: int = 100000
     eps: float = 0.0                # <= 0: 1e-5 * bbox diagonal
     rel_energy_tol: float = 0.0
+    robust: str = "welsch"          # "welsch" | "l2" | "l2r" (Sec. 4.2 variants)
+    nu_fixed: str = ""              # "" (anneal per `anneal`) | "max" | "min" | "med"
 
 
 @dataclass
@@ -95,6 +108,19 @@ class Registration:
         if not self.p.anneal:
             self.nu_a_min = nu_a0
         self.nu_a = max(nu_a0, self.nu_a_min)
+        if self.p.nu_fixed:
+            # the stages the annealing would run: nu_a halves (clamped at
+            # nu_a_min) and nu_r halves until nu_a == nu_a_min
+            na, nr = self.nu_a, self.nu_r
+            while na != self.nu_a_min:
+                na = max(na / 2.0, self.nu_a_min)
+                nr = nr / 2.0
+            pick = {"max": (self.nu_a, self.nu_r), "min": (na, nr),
+                    "med": ((self.nu_a + na) / 2.0, (self.nu_r + nr) / 2.0)}[self.p.nu_fixed]
+            self.nu_a, self.nu_r = pick
+            self.nu_a_min = self.nu_a
+        if self.p.robust == "l2":
+            self.nu_a_min = self.nu_a
         self.X = model.identity_X(self.graph.N)
         self.aa = Anderson(self.p.aa_m)
         self.records: list[PassRecord] = []
@@ -107,10 +133,16 @@ class Registration:
     # -- parameters -------------------------------------------------------
     def weights(self):
         P, N, E = self.V.shape[0], self.graph.N, max(self.graph.n_edges, 1)
-        alpha = self.p.alpha if self.p.alpha >= 0 else (
-            self.p.k_alpha * P / E * self.nu_r ** 2 / self.nu_a ** 2)
-        beta = self.p.beta if self.p.beta >= 0 else (
-            self.p.k_beta * P / max(N, 1) / (2.0 * self.nu_a ** 2))
+        if self.p.robust == "welsch":
+            alpha = self.p.k_alpha * P / E * self.nu_r ** 2 / self.nu_a ** 2
+            beta = self.p.k_beta * P / max(N, 1) / (2.0 * self.nu_a ** 2)
+        else:
+            alpha = self.p.k_alpha * P / E
+            beta = self.p.k_beta * P / max(N, 1)
+        if self.p.alpha >= 0:
+            alpha = self.p.alpha
+        if self.p.beta >= 0:
+            beta = self.p.beta
         return alpha, beta
 
     def _start_stage(self):
@@ -133,7 +165,7 @@ class Registration:
     def terms(self, X=None, rho=None):
         return model.energy_terms(self.V, self.U, self.graph,
                                   self.X if X is None else X,
-                                  self.nu_a, self.nu_r, rho=rho)
+                                  self.nu_a, self.nu_r, rho=rho, robust=self.p.robust)
 
     def energy(self, X=None):
         t = self.terms(X)
@@ -144,7 +176,8 @@ class Registration:
         """G(X^k): minimiser of the surrogate built at the state ``terms``."""
         alpha, beta = self.weights()
         K, B, _ = surrogate.normal_equations(self.V, self.U, self.graph, terms,
-                                             self.nu_a, self.nu_r, alpha, beta)
+                                             self.nu_a, self.nu_r, alpha, beta,
+                                             robust=self.p.robust)
         return surrogate.solve_normal_equations(K, B)
 
     # -- one pass of Algorithm 2 -----------------------------------------

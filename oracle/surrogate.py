@@ -23,14 +23,6 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 
-def align_weights(d2: np.ndarray, nu_a: float) -> np.ndarray:
-    return np.exp(-np.asarray(d2) / (2.0 * nu_a * nu_a)) / (2.0 * nu_a * nu_a)
-
-
-def reg_weights(Dn2: np.ndarray, nu_r: float) -> np.ndarray:
-    return np.exp(-np.asarray(Dn2) / (2.0 * nu_r * nu_r)) / (2.0 * nu_r * nu_r)
-
-
 def build_F(V, graph) -> sp.csr_matrix:
     V = np.asarray(V, dtype=np.float64)
     P, K = graph.nidx.shape
@@ -91,15 +83,17 @@ def build_Z(Rm: np.ndarray) -> np.ndarray:
     return Z.reshape(4 * N, 3)
 
 
-def normal_equations(V, U, graph, terms, nu_a, nu_r, alpha, beta):
+def normal_equations(V, U, graph, terms, nu_a, nu_r, alpha, beta, robust="welsch"):
     """K and B of Eq. (surr_solution) at the state whose energy terms are
-    ``terms`` (closest points, D_ij and rotations evaluated at X^k)."""
+    ``terms`` (closest points, D_ij and rotations evaluated at X^k); the
+    weights are those of the robust function ``robust`` (model.ROBUST)."""
+    from . import model
     U = np.asarray(U, dtype=np.float64)
     F = build_F(V, graph)
     Q = build_Q(U[terms["rho"]], graph)
-    wa = align_weights(terms["d2"], nu_a)
+    wa = model.align_weight(terms["d2"], nu_a, robust)
     H, Y = build_H(graph)
-    wr = reg_weights(np.sum(terms["D"] ** 2, axis=1), nu_r)
+    wr = model.reg_weight(np.sum(terms["D"] ** 2, axis=1), nu_r, robust)
     J = build_J(graph.N)
     Z = build_Z(terms["R"])
     Wa2 = sp.diags(wa)

@@ -67,19 +67,19 @@ def proj_rotation_vjp(A: np.ndarray, Rbar: np.ndarray) -> np.ndarray:
 
 # ------------------------------------------------------------- forward -----
 
-def mm_step(V, U, graph, X, nu_a, nu_r, alpha, beta):
+def mm_step(V, U, graph, X, nu_a, nu_r, alpha, beta, robust="welsch"):
     """One plain MM step: the minimiser of the surrogate built at X."""
-    t = model.energy_terms(V, U, graph, X, nu_a, nu_r)
-    K, B, parts = surrogate.normal_equations(V, U, graph, t, nu_a, nu_r, alpha, beta)
+    t = model.energy_terms(V, U, graph, X, nu_a, nu_r, robust=robust)
+    K, B, parts = surrogate.normal_equations(V, U, graph, t, nu_a, nu_r, alpha, beta, robust=robust)
     Xn = np.asarray(scipy.linalg.cho_solve(scipy.linalg.cho_factor(K.toarray(), lower=True), B))
     return Xn.reshape(graph.N, 12), t, K, parts
 
 
-def unrolled_forward(V, U, graph, X0, nu_a, nu_r, alpha, beta, n_steps):
+def unrolled_forward(V, U, graph, X0, nu_a, nu_r, alpha, beta, n_steps, robust="welsch"):
     """X^(0..K) of K plain MM steps from X0 (the checkpoints of the backward)."""
     Xs = [np.asarray(X0, dtype=np.float64).reshape(graph.N, 12).copy()]
     for _ in range(n_steps):
-        Xn, _, _, _ = mm_step(V, U, graph, Xs[-1], nu_a, nu_r, alpha, beta)
+        Xn, _, _, _ = mm_step(V, U, graph, Xs[-1], nu_a, nu_r, alpha, beta, robust)
         Xs.append(Xn)
     return Xs
 
@@ -91,7 +91,14 @@ def _rows4(M):
     return np.asarray(M).reshape(-1, 3)
 
 
-def step_vjp(V, U, graph, Xk, Xn, gbar, nu_a, nu_r, alpha, beta):
+def weight_slope(w, nu, robust):
+    """d w / d(x^2) of a surrogate weight as a function of the squared
+    residual: -w / (2 nu^2) for Welsch's function; 0 for the squared norm
+    (and almost everywhere for its truncation)."""
+    return -w / (2.0 * nu * nu) if robust == "welsch" else np.zeros_like(w)
+
+
+def step_vjp(V, U, graph, Xk, Xn, gbar, nu_a, nu_r, alpha, beta, robust="welsch"):
     """Reverse-mode derivative of one MM step X' = Phi(X^k, V) at X^k with
     X' = Xn given: returns (dL/dX^k [N,12], dL/dV [P,3]) for dL/dX' = gbar.
     Every product below is a matrix-calculus identity on the matrices of
@@ -99,8 +106,8 @@ def step_vjp(V, U, graph, Xk, Xn, gbar, nu_a, nu_r, alpha, beta):
     V = np.asarray(V, dtype=np.float64)
     U = np.asarray(U, dtype=np.float64)
     N = graph.N
-    t = model.energy_terms(V, U, graph, Xk, nu_a, nu_r)
-    K, B, parts = surrogate.normal_equations(V, U, graph, t, nu_a, nu_r, alpha, beta)
+    t = model.energy_terms(V, U, graph, Xk, nu_a, nu_r, robust=robust)
+    K, B, parts = surrogate.normal_equations(V, U, graph, t, nu_a, nu_r, alpha, beta, robust=robust)
     F, Q, wa, H, Y, wr, Z = (parts[k] for k in ("F", "Q", "wa", "H", "Y", "wr", "Z"))
     Xp = _rows4(Xn)                                    # X' in [4N, 3]
     lam = scipy.linalg.cho_solve(scipy.linalg.cho_factor(K.toarray(), lower=True),
@@ -135,8 +142,8 @@ def step_vjp(V, U, graph, Xk, Xn, gbar, nu_a, nu_r, alpha, beta):
                                   + np.einsum("nac,nc->na", lam_b[jj], Q[m]))
         gV[m] += graph.w[m, s][:, None] * Fbar_blk[:, :3]
 
-    # chain through w^a_i = exp(-d_i^2 / 2 nu_a^2) / (2 nu_a^2), d_i^2 = |v_hat_i - u_i|^2
-    d2_bar = -wa_bar * wa / (2.0 * nu_a * nu_a)
+    # chain through w^a_i(d_i^2) (slope: weight_slope), d_i^2 = |v_hat_i - u_i|^2
+    d2_bar = wa_bar * weight_slope(wa, nu_a, robust)
     vh_bar = 2.0 * d2_bar[:, None] * (t["vhat"] - U[t["rho"]])
     # v_hat = F X^k + sum_j w_ij p_j: dL/dX^k += F^T vh_bar
     gX = np.asarray(F.T @ vh_bar)
@@ -146,10 +153,10 @@ def step_vjp(V, U, graph, Xk, Xn, gbar, nu_a, nu_r, alpha, beta):
         j = graph.nidx[:, s]
         m = np.nonzero(j >= 0)[0]
         gV[m] += graph.w[m, s][:, None] * np.einsum("nab,na->nb", A[j[m]], vh_bar[m])
-    # chain through w^r = exp(-|D|^2 / 2 nu_r^2) / (2 nu_r^2), D = H X^k - Y
+    # chain through w^r(|D|^2) (slope: weight_slope), D = H X^k - Y
     if H.shape[0]:
         Dk = t["D"]
-        Dn2_bar = -wr_bar * wr / (2.0 * nu_r * nu_r)
+        Dn2_bar = wr_bar * weight_slope(wr, nu_r, robust)
         gX += np.asarray(H.T @ (2.0 * Dn2_bar[:, None] * Dk))
     # chain through Z_j rows 0..2 = proj_R(A_j)^T
     Rbar = np.transpose(Z_bar.reshape(N, 4, 3)[:, :3, :], (0, 2, 1))
@@ -159,7 +166,7 @@ def step_vjp(V, U, graph, Xk, Xn, gbar, nu_a, nu_r, alpha, beta):
     return gXb.reshape(N, 12), gV
 
 
-def unrolled_backward(V, U, graph, Xs, nu_a, nu_r, alpha, beta, cotangent=None):
+def unrolled_backward(V, U, graph, Xs, nu_a, nu_r, alpha, beta, cotangent=None, robust="welsch"):
     """Gradient of L(X^(K)) w.r.t. X^(0) and V through the K steps whose
     iterates are Xs = [X^(0), ..., X^(K)]. cotangent: dL/dX^(K) [N,12], or
     None for L = E(X^(K)) (Eq. objective_func with the closest points held
@@ -167,26 +174,26 @@ def unrolled_backward(V, U, graph, Xs, nu_a, nu_r, alpha, beta, cotangent=None):
     Returns (dL/dX^(0) [N,12], dL/dV [P,3])."""
     V = np.asarray(V, dtype=np.float64)
     if cotangent is None:
-        g, gV = model.energy_gradient(V, U, graph, Xs[-1], nu_a, nu_r, alpha, beta)
+        g, gV = model.energy_gradient(V, U, graph, Xs[-1], nu_a, nu_r, alpha, beta, robust=robust)
     else:
         g = np.asarray(cotangent, dtype=np.float64).reshape(graph.N, 12).copy()
         gV = np.zeros_like(V)
     for k in range(len(Xs) - 2, -1, -1):
-        g, gv_k = step_vjp(V, U, graph, Xs[k], Xs[k + 1], g, nu_a, nu_r, alpha, beta)
+        g, gv_k = step_vjp(V, U, graph, Xs[k], Xs[k + 1], g, nu_a, nu_r, alpha, beta, robust)
         gV += gv_k
     return g, gV
 
 
-def unrolled_loss(V, U, graph, X0, nu_a, nu_r, alpha, beta, n_steps, cotangent=None):
+def unrolled_loss(V, U, graph, X0, nu_a, nu_r, alpha, beta, n_steps, cotangent=None, robust="welsch"):
     """L(X^(K)) of the unrolled map (for finite-difference checks); also the
     closest points of every step (to detect flips)."""
     Xs = [np.asarray(X0, dtype=np.float64).reshape(graph.N, 12)]
     rhos = []
     for _ in range(n_steps):
-        Xn, t, _, _ = mm_step(V, U, graph, Xs[-1], nu_a, nu_r, alpha, beta)
+        Xn, t, _, _ = mm_step(V, U, graph, Xs[-1], nu_a, nu_r, alpha, beta, robust)
         rhos.append(t["rho"])
         Xs.append(Xn)
-    tK = model.energy_terms(V, U, graph, Xs[-1], nu_a, nu_r)
+    tK = model.energy_terms(V, U, graph, Xs[-1], nu_a, nu_r, robust=robust)
     rhos.append(tK["rho"])
     if cotangent is None:
         L = model.total_energy(tK, alpha, beta)

@@ -307,11 +307,13 @@ def test_known_affine_map_recovered_in_one_solve():
 
 # ----------------------------------------------------------- algorithm 2 ---
 
-def test_mm_monotone_and_aa_safeguard():
+@pytest.mark.parametrize("robust,aa_m", [("welsch", 5), ("l2", 5), ("l2r", 0), ("l2r", 5)])
+def test_mm_monotone_and_aa_safeguard(robust, aa_m):
     """Kept energies never increase within a stage (Sec. 3.3, monotone MM
-    plus the AA safeguard of Sec. 3.3.4)."""
+    plus the AA safeguard of Sec. 3.3.4), for Welsch's function and for the
+    variants of Sec. 4.2 (plain MM on the truncated quadratic included)."""
     pair = synth.tiny_pair(600, 650, seed=10, noise=0.003, outliers=0.05)
-    reg = Registration(pair.src, pair.tgt, Params(radius=0.35, aa_m=5,
+    reg = Registration(pair.src, pair.tgt, Params(radius=0.35, aa_m=aa_m, robust=robust,
                                                   max_iters_per_stage=15))
     reg.solve(max_passes=60)
     by_stage = {}
@@ -465,3 +467,100 @@ def test_unrolled_backward_matches_central_differences(unroll_case, loss):
             Vm[i, c] -= h
             fd = (L(X0, Vp) - L(X0, Vm)) / (2 * h)
             assert abs(fd - gV[i, c]) < 1e-6 * max(1.0, abs(fd)), (i, c, fd, gV[i, c])
+
+
+# ------------------------------------------------- robust-norm variants ---
+
+def test_variant_functions_closed_forms():
+    """Sec. 4.2 variants: the squared l2 norm (weights 1) and the truncation
+    at 3 nu_a (weight 1 strictly below, 0 from 3 nu_a on), against values
+    worked by hand; Welsch's function unchanged."""
+    nu = 0.5
+    d2 = np.array([0.0, 0.25, 2.25, 4.0])      # d = 0, 0.5, 1.5 (= 3 nu), 2
+    assert np.allclose(M.align_psi(d2, nu, "l2"), [0.0, 0.25, 2.25, 4.0])
+    assert np.allclose(M.align_weight(d2, nu, "l2"), [1, 1, 1, 1])
+    assert np.allclose(M.align_psi(d2, nu, "l2r"), [0.0, 0.25, 2.25, 2.25])
+    assert np.array_equal(M.align_weight(d2, nu, "l2r"), [1.0, 1.0, 0.0, 0.0])
+    assert np.allclose(M.reg_psi(d2, nu, "l2r"), d2) and np.allclose(M.reg_weight(d2, nu, "l2"), 1)
+    assert np.allclose(M.align_psi(d2, nu, "welsch"), 1 - np.exp(-d2 / 0.5))
+    # the truncated weight is the derivative of the truncated quadratic a.e.
+    h = 1e-7
+    for x2 in (0.3, 1.0, 3.0):
+        fd = (M.align_psi(x2 + h, nu, "l2r") - M.align_psi(x2 - h, nu, "l2r")) / (2 * h)
+        assert abs(fd - M.align_weight(x2, nu, "l2r")) < 1e-6
+
+
+@pytest.mark.parametrize("robust", ["l2", "l2r"])
+def test_variant_energy_gradient_matches_central_differences(small, robust):
+    pair, g = small
+    rng = _rng(23)
+    X = _near_identity_X(g.N, rng, 0.02)
+    V = pair.src.astype(np.float64)
+    U = pair.tgt.astype(np.float64)
+    nu_a, nu_r, alpha, beta = 0.05, 0.1, 3.0, 0.7
+    t0 = M.energy_terms(V, U, g, X, nu_a, nu_r, robust=robust)
+    gX, gv = M.energy_gradient(V, U, g, X, nu_a, nu_r, alpha, beta, robust=robust)
+
+    def E(Xv):
+        t = M.energy_terms(V, U, g, Xv, nu_a, nu_r, robust=robust)
+        assert np.array_equal(t["rho"], t0["rho"])
+        # no distance crosses the truncation within the step
+        assert np.array_equal(t["d2"] < 9 * nu_a ** 2, t0["d2"] < 9 * nu_a ** 2)
+        return M.total_energy(t, alpha, beta)
+
+    h = 1e-6
+    flat = X.ravel()
+    for idx in rng.choice(flat.size, 10, replace=False):
+        e = np.zeros_like(flat)
+        e[idx] = h
+        fd = (E((flat + e).reshape(X.shape)) - E((flat - e).reshape(X.shape))) / (2 * h)
+        assert abs(fd - gX.ravel()[idx]) < 1e-6 * max(1.0, abs(fd)), (idx, fd, gX.ravel()[idx])
+
+
+def test_l2_step_minimises_the_l2_energy_for_fixed_correspondences(small):
+    """For the squared l2 norm the surrogate is the energy itself once the
+    closest points are fixed: the MM step's solution G is the minimiser of
+    E_l2(.; rho) (convex quadratic), so E_l2 rises in every direction from G
+    and its central-difference gradient at G vanishes."""
+    pair, g = small
+    V = pair.src.astype(np.float64)
+    U = pair.tgt.astype(np.float64)
+    X = _near_identity_X(g.N, _rng(24), 0.01)
+    nu_a, nu_r, alpha, beta = 0.05, 0.1, 3.0, 0.7
+    t = M.energy_terms(V, U, g, X, nu_a, nu_r, robust="l2")
+    K, B, _ = S.normal_equations(V, U, g, t, nu_a, nu_r, alpha, beta, robust="l2")
+    Gs = S.solve_normal_equations(K, B)
+    rho = t["rho"]
+
+    def E(Xv):
+        tt = M.energy_terms(V, U, g, Xv, nu_a, nu_r, rho=rho, robust="l2")
+        # E_rot of the surrogate: |A - R(A^k)|^2 with R held at X
+        A = M.A_of(Xv)
+        return tt["E_align"] + alpha * tt["E_reg"] + beta * float(np.sum((A - t["R"]) ** 2))
+
+    e0 = E(Gs)
+    rng = _rng(25)
+    for _ in range(5):
+        D = rng.standard_normal(Gs.shape)
+        assert E(Gs + 1e-3 * D) > e0
+        fd = (E(Gs + 1e-6 * D) - E(Gs - 1e-6 * D)) / 2e-6
+        assert abs(fd) < 1e-6 * max(1.0, e0)
+
+
+def test_nu_fixed_variants_follow_the_annealing_schedule():
+    """Welsch-fmax / fmin / fmed (Sec. 4.2) run one stage at the first
+    stage's nu, at the last stage's, and at their means, the stages being
+    those the annealed run actually visits."""
+    pair = synth.tiny_pair(300, 330, seed=9, noise=0.002, outliers=0.03)
+    base = dict(radius=0.35, nu_a=0.2, nu_r=0.4, nu_a_min=0.03, aa_m=0, max_iters_per_stage=3)
+    ann = Registration(pair.src, pair.tgt, Params(**base))
+    ann.solve()
+    stages = sorted({(r.stage, r.nu_a, r.nu_r) for r in ann.records})
+    first, last = stages[0][1:], stages[-1][1:]
+    assert len(stages) == 4 and last[0] == 0.03          # 0.2 -> 0.1 -> 0.05 -> 0.03
+    for which, want in [("max", first), ("min", last),
+                        ("med", ((first[0] + last[0]) / 2, (first[1] + last[1]) / 2))]:
+        r = Registration(pair.src, pair.tgt, Params(nu_fixed=which, **base))
+        assert (r.nu_a, r.nu_r) == want
+        r.solve()
+        assert {rec.stage for rec in r.records} == {0}
