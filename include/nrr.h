@@ -54,6 +54,30 @@ typedef enum {
     NRR_E_STATE = 7           /* call not valid in the current state        */
 } nrr_status;
 
+/* Robust function of the alignment and regularisation terms. The paper's
+ * method uses Welsch's function (Eq. 4); Sec. 4.2 compares it with the
+ * squared l2 norm (all weights 1) and with l2 whose alignment weight is 0
+ * once a distance reaches 3 nu_a (read as the MM weights of the truncated
+ * quadratic min(d^2, 9 nu_a^2), the energy the library then reports). For
+ * both l2 variants the regularisation term is sum |D_ij|^2 and Eq.
+ * (WeightSettings) drops the factors that scale Welsch's curvature at zero:
+ * alpha = k_alpha |V|/|E_G|, beta = k_beta |V|/|V_G|; NRR_L2 runs one stage. */
+typedef enum {
+    NRR_WELSCH = 0,
+    NRR_L2 = 1,
+    NRR_L2_TRUNCATED = 2
+} nrr_robust;
+
+/* Fixed nu instead of the annealing (Sec. 4.2, "Welsch-fmax/fmin/fmed"):
+ * one stage at the first stage's (nu_a, nu_r), at the last stage's, or at
+ * their means, the stages being those the annealing would run. */
+typedef enum {
+    NRR_NU_ANNEAL = 0,
+    NRR_NU_FIXED_MAX = 1,
+    NRR_NU_FIXED_MIN = 2,
+    NRR_NU_FIXED_MED = 3
+} nrr_nu_schedule;
+
 typedef enum {
     NRR_FP64 = 0,   /* every step in double precision                        */
     NRR_MIXED = 1   /* closest points, weights, assembly and PCG in float;
@@ -98,6 +122,9 @@ typedef struct {
                                   latency for one pair), -1 = the smallest
                                   (batches; leaves SMs to other pairs),
                                   1..16 = that size if it fits              */
+    int    robust;             /* nrr_robust; default NRR_WELSCH            */
+    int    nu_schedule;        /* nrr_nu_schedule; default NRR_NU_ANNEAL
+                                  (then `anneal` applies)                   */
 } nrr_params;
 
 /* State after a pass (one execution of the repeat body of Algorithm 2). */

@@ -63,9 +63,16 @@ __global__ void __launch_bounds__(kThreads) xterm_kernel(DevProblem<T> d) {
         const T Dx = r * ((Xb[0] * dx + Xb[3] * dy + Xb[6] * dz - dx) + (Xb[9] - Xa[9]));
         const T Dy = r * ((Xb[1] * dx + Xb[4] * dy + Xb[7] * dz - dy) + (Xb[10] - Xa[10]));
         const T Dz = r * ((Xb[2] * dx + Xb[5] * dy + Xb[8] * dz - dz) + (Xb[11] - Xa[11]));
-        const T n2 = (Dx * Dx + Dy * Dy + Dz * Dz) * ir;
-        er += (double)(-t_expm1<T>(-n2));
-        d.wr[e] = t_exp<T>(-n2) * ir;
+        const T D2 = Dx * Dx + Dy * Dy + Dz * Dz;
+        if (d.robust == NRR_WELSCH) {
+            const T n2 = D2 * ir;
+            er += (double)(-t_expm1<T>(-n2));
+            d.wr[e] = t_exp<T>(-n2) * ir;
+        } else {
+            // squared norm: energy |D|^2, weight 1
+            er += (double)D2;
+            d.wr[e] = (T)1;
+        }
     }
     // rotation term: |A_n - proj_R(A_n)|_F^2
     // nodes are spread CTA-major so that the double-precision SVDs use every SM
@@ -106,11 +113,24 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
     const double nua = st->nu_a;
     const T ia = (T)(1.0 / (2.0 * nua * nua));
     double ea = 0.0;
-    // alignment term (Eq. AlignmentTerm) and its surrogate weights w^a_i
-    for (int i = gtid; i < d.P; i += gstride) {
-        const T x = d.d2[i] * ia;
-        ea += (double)(-t_expm1<T>(-x));
-        d.wa[i] = t_exp<T>(-x) * ia;
+    // alignment term (Eq. AlignmentTerm) and its surrogate weights w^a_i;
+    // the l2 variants: d^2 with weight 1, or min(d^2, 9 nu_a^2) with weight
+    // 1 below 3 nu_a and 0 from there on
+    if (d.robust == NRR_WELSCH) {
+        for (int i = gtid; i < d.P; i += gstride) {
+            const T x = d.d2[i] * ia;
+            ea += (double)(-t_expm1<T>(-x));
+            d.wa[i] = t_exp<T>(-x) * ia;
+        }
+    } else {
+        const T cut = (T)(9.0 * nua * nua);
+        const bool trunc = d.robust == NRR_L2_TRUNCATED;
+        for (int i = gtid; i < d.P; i += gstride) {
+            const T d2 = d.d2[i];
+            const bool in = !trunc || d2 < cut;
+            ea += (double)(in ? d2 : cut);
+            d.wa[i] = in ? (T)1 : (T)0;
+        }
     }
     const double sa = block_sum(ea, sh);
     if (threadIdx.x == 0) {

@@ -11,15 +11,17 @@
 // Per point i (adj_point_kernel), with a_i = lambda^T f_i, v'_i the deformed
 // point under X', u_i the closest target point:
 //   dL/dw^a_i = a_i . (u_i - v'_i)
-//   e_i       = dL/dv_hat_i = 2 (dL/dw^a_i) (-w^a_i / 2nu_a^2) (v_hat_i - u_i)
+//   e_i       = dL/dv_hat_i = 2 (dL/dw^a_i) w'(d_i^2) (v_hat_i - u_i)
 //   dL/dv_i  += w^a_i sum_j w_ij (Lambda_j (u_i - v'_i) - A'_j^T a_i)
 //             + sum_j w_ij A_j^T e_i
 // (Lambda_j: rows 0..2 of lambda's block j, in the layout of X).
 // Per node n (adj_node_kernel), the new cotangent dL/dX^k_n collects
 //   sum_i w_in [v_i - p_n; 1] e_i^T                       (alignment weights)
-//   h D_ij(X^k)^T scaled by 2 (dL/dw^r_ij)(-w^r_ij / 2nu_r^2),
+//   h D_ij(X^k)^T scaled by 2 (dL/dw^r_ij) w'(|D_ij|^2),
 //     dL/dw^r_ij = -alpha (h^T lambda) . D_ij(X')         (regularisation weights)
 //   the derivative of proj_R at A_n applied to beta Lambda_n^T (rotation targets).
+// The slope w' of a weight is -w / (2 nu^2) for Welsch's function and 0 for
+// the squared norm and its truncation (almost everywhere).
 // The derivative of proj_R: with R = proj_R(A) and S = R^T A (symmetric),
 // A = R S gives R^T dR = Omega with Omega S + S Omega = R^T dA - dA^T R; in
 // the eigenbasis of S the adjoint is Gamma_kl = skew(R^T Rbar)_kl /
@@ -65,7 +67,8 @@ __global__ void __launch_bounds__(kThreads)
     const T wai = d.wa[i];
     const T ia = (T)(1.0 / (2.0 * st->nu_a * st->nu_a));
     const T wbar = a[0] * rq[0] + a[1] * rq[1] + a[2] * rq[2];
-    const T c2 = (T)-2 * wbar * wai * ia;
+    // dw/d(d^2): -w / (2 nu_a^2) for Welsch's function, 0 for the l2 variants
+    const T c2 = d.robust == NRR_WELSCH ? (T)-2 * wbar * wai * ia : (T)0;
     const T e[3] = {c2 * (vh[i] - ux), c2 * (vh[P + i] - uy), c2 * (vh[2 * P + i] - uz)};
     ebuf[i] = e[0];
     ebuf[P + i] = e[1];
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(kThreads)
                     wbar -= hl * Dn;
                 }
                 wbar *= alpha;
-                const T coef = (T)-2 * wbar * d.wr[ee] * ir;
+                const T coef = d.robust == NRR_WELSCH ? (T)-2 * wbar * d.wr[ee] * ir : (T)0;
                 if (side == 0) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) g[9 + c] -= coef * r * Dk[c];

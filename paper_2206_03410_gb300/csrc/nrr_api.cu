@@ -150,12 +150,15 @@ cudaError_t fetch_floats(const float* src, size_t n, std::vector<float>& out, cu
     return cudaStreamSynchronize(s);
 }
 
+// Eq. (WeightSettings); for the l2 variants without the factors that scale
+// Welsch's curvature at zero.
 void host_stage_weights(NrrState& st) {
+    const bool w = st.robust == NRR_WELSCH;
     st.alpha = st.alpha_fixed >= 0 ? st.alpha_fixed
-                                   : st.k_alpha * st.n_src / st.n_edges * (st.nu_r * st.nu_r) /
-                                         (st.nu_a * st.nu_a);
+                                   : st.k_alpha * st.n_src / st.n_edges *
+                                         (w ? (st.nu_r * st.nu_r) / (st.nu_a * st.nu_a) : 1.0);
     st.beta = st.beta_fixed >= 0 ? st.beta_fixed
-                                 : st.k_beta * st.n_src / st.n_nodes / (2.0 * st.nu_a * st.nu_a);
+                                 : st.k_beta * st.n_src / st.n_nodes / (w ? 2.0 * st.nu_a * st.nu_a : 1.0);
 }
 
 void host_restart_stage(NrrState& st) {
@@ -526,6 +529,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     tm.lap("leaves + initial bound");
     d.P = (int)P; d.N = N; d.E2 = E2; d.n_leaves = nl; d.n_supers = ns; d.nblk = c->nblk;
     d.aa_m = c->prm.aa_m;
+    d.robust = c->prm.robust;
     d.pcg_max = c->prm.pcg_max_iters;
     d.pcg_tol = (T)c->prm.pcg_tol;
     T *pv_, *pw_, *pp_, *er_;
@@ -960,6 +964,8 @@ void nrr_params_default(nrr_params* p) {
     p->pcg_tol = 0.0;
     p->pcg_max_iters = 500;
     p->solve_ctas = 0;
+    p->robust = NRR_WELSCH;
+    p->nu_schedule = NRR_NU_ANNEAL;
 }
 
 const char* nrr_last_error(const nrr_ctx* ctx) {
@@ -1006,6 +1012,10 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         return fail(nullptr, NRR_E_INVALID, "iteration caps must be >= 1");
     if (prm.solve_ctas < -1 || prm.solve_ctas > 16)
         return fail(nullptr, NRR_E_INVALID, "solve_ctas must be in -1..16");
+    if (prm.robust < NRR_WELSCH || prm.robust > NRR_L2_TRUNCATED)
+        return fail(nullptr, NRR_E_INVALID, "robust must be NRR_WELSCH, NRR_L2 or NRR_L2_TRUNCATED");
+    if (prm.nu_schedule < NRR_NU_ANNEAL || prm.nu_schedule > NRR_NU_FIXED_MED)
+        return fail(nullptr, NRR_E_INVALID, "nu_schedule must be one of nrr_nu_schedule");
     if (!(std::isfinite(prm.graph_radius) && std::isfinite(prm.nu_a) && std::isfinite(prm.nu_r) &&
           std::isfinite(prm.nu_a_min) && std::isfinite(prm.eps) && std::isfinite(prm.k_alpha) &&
           std::isfinite(prm.k_beta) && std::isfinite(prm.alpha) && std::isfinite(prm.beta)))
@@ -1089,6 +1099,7 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     s.rel_tol = prm.rel_energy_tol;
     s.max_iters_stage = prm.max_iters_per_stage;
     s.aa_m = prm.aa_m;
+    s.robust = prm.robust;
     s.nu_a = 1.0; s.nu_r = 1.0;
     CK(cudaMemcpyAsync(c->d_state, c->h_state, sizeof(NrrState), cudaMemcpyHostToDevice, c->stream));
     double nu_a0 = prm.nu_a;
@@ -1103,6 +1114,19 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     s.nu_a = std::max(nu_a0, nu_min);
     s.nu_r = prm.nu_r > 0 ? prm.nu_r : 3.0 * c->hg.lbar;
     if (!(s.nu_a > 0) || !(s.nu_r > 0)) return fail(nullptr, NRR_E_INVALID, "nu_a and nu_r must be positive");
+    if (prm.nu_schedule != NRR_NU_ANNEAL) {
+        // the stages the annealing would run: nu_a halves (clamped at
+        // nu_a_min), nu_r halves, until nu_a == nu_a_min
+        double na = s.nu_a, nr = s.nu_r;
+        while (na != s.nu_a_min) {
+            na = std::max(na * 0.5, s.nu_a_min);
+            nr = nr * 0.5;
+        }
+        if (prm.nu_schedule == NRR_NU_FIXED_MIN) { s.nu_a = na; s.nu_r = nr; }
+        else if (prm.nu_schedule == NRR_NU_FIXED_MED) { s.nu_a = (s.nu_a + na) / 2.0; s.nu_r = (s.nu_r + nr) / 2.0; }
+        s.nu_a_min = s.nu_a;
+    }
+    if (prm.robust == NRR_L2) s.nu_a_min = s.nu_a;   // no nu in the energy: one stage
     host_stage_weights(s);
     host_restart_stage(s);
     c->nu_a0 = s.nu_a;

@@ -33,6 +33,7 @@ template <typename T>
 struct DevProblem {
     int P, N, E2, n_leaves, n_supers, nblk;
     int aa_m;
+    int robust;         // nrr_robust: Welsch's function or an l2 variant
     int pcg_max;
     T pcg_tol;
     // source
@@ -131,12 +132,13 @@ cudaError_t nrr_launch_to_t(const double* in, T* out, int n, cudaStream_t s);
 // Stage transition of Algorithm 2 (halve nu_a and nu_r, recompute alpha and
 // beta with Eq. WeightSettings, restart the stage). Single device thread.
 __device__ __forceinline__ void nrr_stage_weights(NrrState* st) {
+    const bool w = st->robust == NRR_WELSCH;
     st->alpha = st->alpha_fixed >= 0 ? st->alpha_fixed
                                      : st->k_alpha * st->n_src / st->n_edges *
-                                           (st->nu_r * st->nu_r) / (st->nu_a * st->nu_a);
+                                           (w ? (st->nu_r * st->nu_r) / (st->nu_a * st->nu_a) : 1.0);
     st->beta = st->beta_fixed >= 0 ? st->beta_fixed
                                    : st->k_beta * st->n_src / st->n_nodes /
-                                         (2.0 * st->nu_a * st->nu_a);
+                                         (w ? 2.0 * st->nu_a * st->nu_a : 1.0);
 }
 
 __device__ __forceinline__ void nrr_end_stage(NrrState* st) {

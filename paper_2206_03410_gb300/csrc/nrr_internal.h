@@ -41,6 +41,7 @@ struct NrrState {
     int done;               // Algorithm 2 returned
     int status;             // nrr_status from device-side checks
     int aa_m, aa_count, aa_head, aa_mk;
+    int robust;             // nrr_robust (alpha, beta rule of the stages)
     int pcg_iters;
     int vk;                 // which v_hat buffer holds the kept iterate
     int vlast;              // which v_hat buffer was written last

@@ -30,6 +30,8 @@ NRR_E_STATE = 7
 
 NRR_FP64 = 0
 NRR_MIXED = 1
+ROBUST = {"welsch": 0, "l2": 1, "l2r": 2}
+NU_SCHEDULE = {"": 0, "anneal": 0, "max": 1, "min": 2, "med": 3}
 
 
 class NrrParams(ctypes.Structure):
@@ -53,6 +55,8 @@ class NrrParams(ctypes.Structure):
         ("pcg_tol", ctypes.c_double),
         ("pcg_max_iters", ctypes.c_int),
         ("solve_ctas", ctypes.c_int),
+        ("robust", ctypes.c_int),
+        ("nu_schedule", ctypes.c_int),
     ]
 
 
@@ -200,6 +204,12 @@ def make_params(**kw) -> NrrParams:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = NRR_FP64 if v.lower() == "fp64" else NRR_MIXED
+        if k == "robust" and isinstance(v, str):
+            v = ROBUST[v]
+        if k in ("nu_fixed", "nu_schedule"):
+            k = "nu_schedule"
+            if isinstance(v, str):
+                v = NU_SCHEDULE[v]
         if k in ("radius",):
             k = "graph_radius"
         if not hasattr(p, k):
