@@ -86,6 +86,7 @@ def parse():
     ap.add_argument("--ttc-seeds", type=int, default=3,
                     help="extra seeds of the workload for the mixed-vs-FP64 energy comparison")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-variants", action="store_true", help="skip the robust-norm variants run")
     return ap.parse_args()
 
 
@@ -244,6 +245,40 @@ def ttc_pair(nrr, pair, kw, stream, args) -> dict:
         r.close()
     out["gap"] = float((e32 - e64) / abs(e64))
     out["speedup"] = round(out["fp64_ms"] / out["mixed_ms"], 2)
+    return out
+
+
+VARIANTS = [("welsch", {}), ("l2", dict(robust="l2")), ("l2r", dict(robust="l2r")),
+            ("welsch_fmax", dict(nu_fixed="max")), ("welsch_fmin", dict(nu_fixed="min")),
+            ("welsch_fmed", dict(nu_fixed="med"))]
+
+
+def run_variants(nrr, stream) -> dict:
+    """Sec. 4.2's comparison on the partial-overlap workload (50,000 source
+    points, 30 % of the target cropped, 2 % noise, 10 % outliers), mixed
+    precision: wall time of nrr_solve to convergence and the RMSE of the
+    deformed source against the generator's ground truth (Eq. gt_metric)."""
+    import torch
+    pair = synth.workload("sphere50k_partial")
+    kw = {k: v for k, v in pair.params.items() if k not in ("precision", "iters", "unroll")}
+    kw["rel_energy_tol"] = 1e-6
+    src = torch.from_numpy(pair.src).cuda()
+    tgt = torch.from_numpy(pair.tgt).cuda()
+    gt = pair.gt.astype(np.float64)
+    out = {"workload": "sphere50k_partial: P=%d, T=%d, 30 %% crop, 2 %% noise, 10 %% outliers, mixed, "
+                       "stages end at relative dE < 1e-6" % (pair.P, pair.T)}
+    for name, extra in VARIANTS:
+        r = nrr.Registration(src, tgt, stream=stream.cuda_stream, precision="mixed", **kw, **extra)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = r.solve(20000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        vh = r.deformed()
+        rmse = float(np.sqrt(np.mean(np.sum((vh - gt) ** 2, axis=1))))
+        out[name] = {"ms": round(dt * 1e3, 2), "iters": info.n_solves, "stages": info.stage + 1,
+                     "rmse": rmse, "done": info.done}
+        r.close()
     return out
 
 
@@ -434,6 +469,10 @@ def run_ours(args):
                                "all_done": all(i.done for i in infos), "create_s": round(t_create, 2)}
             bt.close()
 
+        # ---- robust-norm variants (Sec. 4.2) on the partial-overlap workload ----
+        if not args.no_variants:
+            result["variants"] = run_variants(nrr, stream)
+
         # ---- end to end through the public API from pinned host buffers ----
         hs = torch.from_numpy(pair.src).pin_memory()
         ht = torch.from_numpy(pair.tgt).pin_memory()
@@ -498,6 +537,7 @@ def main():
         "ttc": res.get("ttc"),
         "batch": res.get("batch"),
         "launch": res.get("launch"),
+        "variants": res.get("variants"),
     }
     if ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(pair, kw)
