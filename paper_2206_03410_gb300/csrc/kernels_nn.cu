@@ -82,6 +82,25 @@ __device__ __forceinline__ void group_argmin(T& best, int& bidx, T& bx, T& by, T
     }
 }
 
+// Float path: a candidate is the 64-bit key (bits of d^2 << 32 | caller
+// index); for d^2 >= 0 the bits of a float order like its value, so the
+// smallest key is the smallest distance with ties to the lowest index. The
+// winner's coordinates are fetched once at the end from its slot in the
+// target array (slot -1: the initial candidate, whose coordinates are known).
+__device__ __forceinline__ unsigned long long cand_key(float dd, int idx) {
+    return ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned)idx;
+}
+
+template <int LPQ>
+__device__ __forceinline__ void group_argmin_key(unsigned long long& key, int& pos) {
+#pragma unroll
+    for (int o = LPQ / 2; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+        const int op = __shfl_xor_sync(0xffffffffu, pos, o);
+        if (ok < key) { key = ok; pos = op; }
+    }
+}
+
 template <typename T, int LPQ>
 __device__ __forceinline__ T group_min(T v) {
 #pragma unroll
@@ -146,6 +165,9 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
         bidx = d.rho[i];
         best = sqdist(qx, qy, qz, bx, by, bz);
     }
+    // float path: packed key and slot of the best candidate
+    unsigned long long bkey = sizeof(T) == 4 && valid ? cand_key((float)best, bidx) : 0ull;
+    int bpos = -1;
     T gbest = best;   // best over the lanes of the query (pruning bound)
     // lane query box (float, rounded outwards) and the warp's query box
     const float lx = valid ? lo_f(qx) : INFINITY, ly = valid ? lo_f(qy) : INFINITY,
@@ -241,12 +263,21 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
                                 for (int j = 0; j < PPL; ++j) {
                                     const TPoint<T> c = tile[warp][k][sub + j * LPQ];
                                     const T dd = sqdist(qx, qy, qz, c.x, c.y, c.z);
-                                    if (dd < best || (dd == best && c.idx < bidx)) {
-                                        best = dd; bidx = c.idx;
-                                        bx = c.x; by = c.y; bz = c.z;
+                                    if constexpr (sizeof(T) == 4) {
+                                        const unsigned long long key = cand_key((float)dd, c.idx);
+                                        if (key < bkey) {
+                                            bkey = key;
+                                            bpos = (base + ids[k]) * 32 + sub + j * LPQ;
+                                        }
+                                    } else {
+                                        if (dd < best || (dd == best && c.idx < bidx)) {
+                                            best = dd; bidx = c.idx;
+                                            bx = c.x; by = c.y; bz = c.z;
+                                        }
                                     }
                                 }
                             }
+                            if constexpr (sizeof(T) == 4) best = (T)__uint_as_float((unsigned)(bkey >> 32));
                             gbest = group_min<T, LPQ>(best);
                         }
                     }
@@ -256,7 +287,17 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
             }
         }
     }
-    group_argmin<T, LPQ>(best, bidx, bx, by, bz);
+    if constexpr (sizeof(T) == 4) {
+        group_argmin_key<LPQ>(bkey, bpos);
+        best = (T)__uint_as_float((unsigned)(bkey >> 32));
+        bidx = (int)(unsigned)(bkey & 0xffffffffull);
+        if (valid && bpos >= 0) {
+            const TPoint<T> c = d.tpts[bpos];
+            bx = c.x; by = c.y; bz = c.z;
+        }
+    } else {
+        group_argmin<T, LPQ>(best, bidx, bx, by, bz);
+    }
     if (d.nn_stats != nullptr && lane == 0) {
         unsigned long long* o = d.nn_stats + 4 * (size_t)(blockIdx.x * kWarps + warp);
         o[0] = (unsigned long long)(clock64() - t_start);
