@@ -38,6 +38,7 @@ struct Barrier {
     unsigned gen;
     unsigned nblocks;
     int* s_flag;
+    int skip_arrival;   // failure-detection test: this CTA does not arrive once
 
     // Returns false if the wait timed out or another CTA reported a failure.
     __device__ bool sync() {
@@ -45,8 +46,10 @@ struct Barrier {
         if (threadIdx.x == 0) {
             int fail = 0;
             __threadfence();
-            const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-            if (arrived == nblocks - 1) {
+            const bool skipped = skip_arrival != 0;
+            const unsigned arrived = skipped ? 0u : atomicAdd(&st->bar_count, 1u);
+            skip_arrival = 0;
+            if (!skipped && arrived == nblocks - 1) {
                 atomicExch(&st->bar_count, 0u);
                 __threadfence();
                 atomicExch(&st->bar_gen, gen + 1);
@@ -216,7 +219,10 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
     const int per = (N + G - 1) / G;
     const int n0 = min(N, (int)blockIdx.x * per), n1 = min(N, n0 + per);
     const int npairs = (n1 - n0) * 3;
-    Barrier bar{st, *(volatile unsigned*)&st->bar_gen, (unsigned)G, &s_flag};
+    // d.fault_barrier (a host-side test knob): CTA 0 skips its first arrival,
+    // so every CTA's bounded wait runs out and records NRR_E_TIMEOUT
+    Barrier bar{st, *(volatile unsigned*)&st->bar_gen, (unsigned)G, &s_flag,
+                (d.fault_barrier && blockIdx.x == 0 && G > 1) ? 1 : 0};
     Red red{d.partials, 0};
     const double tol = (double)d.pcg_tol;
 

@@ -601,6 +601,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     d.st = c->d_state;
     d.nn_stats = nullptr;
     d.solve_stats = nullptr;
+    d.fault_barrier = std::getenv("NRR_FAULT_BARRIER") ? 1 : 0;
     if (std::getenv("NRR_SOLVE_STATS")) {
         long long* ss = nullptr;
         CK(dalloc(c, &ss, 64));
@@ -668,18 +669,25 @@ nrr_status write_X(nrr_ctx* c, T* dst, const double* X) {
 struct StateGuard {
     nrr_ctx* c;
     NrrState saved{};
+    bool is_open = false;
     nrr_status open() {
         nrr_status st = pull_state(c);
         if (st != NRR_OK) return st;
         saved = *c->h_state;
+        is_open = true;
         c->h_state->done = 0;
         c->h_state->skip = 0;
         return push_state(c);
     }
     nrr_status close() {
+        is_open = false;
         *c->h_state = saved;
         c->h_state->vlast = saved.vk ^ 1;
         return push_state(c);
+    }
+    // an early return (an error) still puts the state back
+    ~StateGuard() {
+        if (is_open) close();
     }
 };
 
@@ -907,6 +915,7 @@ nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, double* n
         if (st != NRR_OK) return st;
         if (ms < *nn_ms) { *nn_ms = ms; *best_lpq = lpq; }
     }
+    if (!std::isfinite(*nn_ms)) *best_lpq = c->nn_lpq;
     // the solve of that system, per cluster size (0: grid-wide); the
     // solution goes to scratch, the pass state is not touched
     DevProblem<T> ds = d;
@@ -919,7 +928,12 @@ nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, double* n
         if (C == 0 && !c->coop) continue;
         double ms = 0;
         st = time_launches(c, reps, [&]() { return launch_solve_on<T>(c, ds); }, &ms);
-        if (st != NRR_OK) return st;
+        if (st != NRR_OK) {
+            // a shape the device cannot launch (resources): not a candidate
+            cudaGetLastError();
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) return st;
+            continue;
+        }
         if (ms < *solve_ms) { *solve_ms = ms; *best_ctas = C; }
     }
     if (!std::isfinite(*solve_ms)) *best_ctas = keep_C;

@@ -97,6 +97,9 @@ struct DevProblem {
     unsigned long long* nn_stats;
     // optional phase timestamps of the cluster solve (CTA 0, thread 0; NULL: off)
     long long* solve_stats;
+    // failure-detection test knob (NRR_FAULT_BARRIER, read on the host at
+    // creation): the grid-wide solve's CTA 0 skips its first barrier arrival
+    int fault_barrier;
 };
 
 #define NRR_PARTIAL_STRIDE 32

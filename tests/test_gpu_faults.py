@@ -1,0 +1,44 @@
+"""Failure detection without a GPU fault: the grid-wide solve's barrier wait
+is bounded. With the host-side test knob NRR_FAULT_BARRIER (read when a
+context is created), one CTA skips its first arrival; every CTA's wait then
+runs out after about two seconds, the kernel records NRR_E_TIMEOUT in the
+context's device state and returns, and the host reports the code. The
+device stays usable: a new context solves normally afterwards."""
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def test_bounded_barrier_wait_reports_timeout(monkeypatch):
+    from paper_2206_03410_gb300 import nrr
+    nrr.load()
+    pair = synth.tiny_pair(3000, 3200, seed=81, noise=0.002, outliers=0.05)
+    kw = dict(radius=0.2, aa_m=5, precision="mixed")
+    monkeypatch.setenv("NRR_FAULT_BARRIER", "1")
+    reg = nrr.Registration(pair.src, pair.tgt, **kw)
+    monkeypatch.delenv("NRR_FAULT_BARRIER")
+    reg.set_launch_config(8, 0)            # the grid-wide solve (software barrier)
+    with pytest.raises(nrr.NrrError) as e:
+        reg.step()
+    assert e.value.code == nrr.NRR_E_TIMEOUT
+    with pytest.raises(nrr.NrrError) as e2:
+        reg.step()                          # the context is marked failed
+    assert e2.value.code == nrr.NRR_E_STATE
+    reg.close()
+    torch.cuda.synchronize()
+    ok = nrr.Registration(pair.src, pair.tgt, **kw)
+    ok.set_launch_config(8, 0)
+    info = ok.solve(3000)
+    assert info.done == 1 and info.status == 0
+    ok.close()
