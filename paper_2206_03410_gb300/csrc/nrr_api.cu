@@ -1575,6 +1575,7 @@ struct nrr_batch {
     NrrState** d_states = nullptr;
     int* d_flags = nullptr;
     int* h_flags = nullptr;
+    std::vector<int> captured;   // pairs whose pass the batch graph holds
     std::string err;
 };
 
@@ -1595,7 +1596,7 @@ nrr_status batch_fail(nrr_batch* b, nrr_status code, const std::string& msg) {
     return code;
 }
 
-nrr_status batch_capture(nrr_batch* b);
+nrr_status batch_capture(nrr_batch* b, const std::vector<int>& members);
 
 #define BK(call)                                                                           \
     do {                                                                                   \
@@ -1610,17 +1611,19 @@ nrr_status batch_capture(nrr_batch* b);
 
 namespace {
 
-// Captures the batch graph: fork every pair's pass onto its own stream,
-// join, gather the flags.
-nrr_status batch_capture(nrr_batch* b) {
+// Captures the batch graph: fork the pass of every member pair onto its own
+// stream, join, gather the flags of all pairs.
+nrr_status batch_capture(nrr_batch* b, const std::vector<int>& members) {
     const int n = (int)b->ctx.size();
     if (b->gexec) {
         cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;
     }
+    b->captured = members;
     BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaEventRecord(b->events[(size_t)n], b->stream);
-    for (int i = 0; i < n && ce == cudaSuccess; ++i) {
+    for (int i : members) {
+        if (ce != cudaSuccess) break;
         nrr_ctx* c = b->ctx[(size_t)i];
         ce = cudaStreamWaitEvent(c->stream, b->events[(size_t)n], 0);
         if (ce == cudaSuccess) ce = launch_pass_any(c);
@@ -1644,6 +1647,12 @@ nrr_status batch_capture(nrr_batch* b) {
     return NRR_OK;
 }
 
+std::vector<int> all_pairs(const nrr_batch* b) {
+    std::vector<int> v(b->ctx.size());
+    for (size_t i = 0; i < v.size(); ++i) v[i] = (int)i;
+    return v;
+}
+
 // Applies one launch policy to every pair of a batch: lanes per query and
 // each pair's smallest (policy -1) or largest (policy 0) fitting cluster.
 nrr_status batch_apply(nrr_batch* b, int lpq, int policy) {
@@ -1654,7 +1663,7 @@ nrr_status batch_apply(nrr_batch* b, int lpq, int policy) {
         nrr_status st = capture_graph(c);
         if (st != NRR_OK) return st;
     }
-    return batch_capture(b);
+    return batch_capture(b, all_pairs(b));
 }
 
 }  // namespace
@@ -1766,7 +1775,7 @@ nrr_status nrr_batch_create(nrr_batch** out, int n_pairs, const float* const* sr
     BK(cudaMallocHost(&b->h_flags, sizeof(int) * 4 * (size_t)n));
     b->events.resize((size_t)n + 1);
     for (auto& e : b->events) BK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    nrr_status cst = batch_capture(b);
+    nrr_status cst = batch_capture(b, all_pairs(b));
     if (cst != NRR_OK) return cst;
     guard.release();
     *out = b;
@@ -1783,6 +1792,13 @@ nrr_status nrr_batch_solve(nrr_batch* b, int max_passes, nrr_step_info* infos) {
     }
     int launched = 0;
     bool all_done = false;
+    // the graph holds every pair at the start; when half of its pairs have
+    // returned it is recaptured with the pairs still running (passes of
+    // returned pairs do nothing, but their launches still cost)
+    if ((int)b->captured.size() != n) {
+        nrr_status cst = batch_capture(b, all_pairs(b));
+        if (cst != NRR_OK) return cst;
+    }
     while (!all_done && launched < cap) {
         const int nb = std::min(4, cap - launched);
         for (int k = 0; k < nb; ++k) BK(cudaGraphLaunch(b->gexec, b->stream));
@@ -1790,11 +1806,17 @@ nrr_status nrr_batch_solve(nrr_batch* b, int max_passes, nrr_step_info* infos) {
         BK(cudaMemcpyAsync(b->h_flags, b->d_flags, sizeof(int) * 4 * (size_t)n, cudaMemcpyDeviceToHost, b->stream));
         BK(cudaStreamSynchronize(b->stream));
         all_done = true;
+        std::vector<int> running;
         for (int i = 0; i < n; ++i) {
             if (b->h_flags[4 * i + 1] != 0)
                 return batch_fail(b, (nrr_status)b->h_flags[4 * i + 1],
                                   "pair " + std::to_string(i) + ": device-side wait timed out");
-            all_done = all_done && b->h_flags[4 * i] != 0;
+            if (b->h_flags[4 * i] == 0) running.push_back(i);
+        }
+        all_done = running.empty();
+        if (!all_done && 2 * running.size() <= b->captured.size()) {
+            nrr_status cst = batch_capture(b, running);
+            if (cst != NRR_OK) return cst;
         }
     }
     if (infos)
