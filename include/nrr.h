@@ -35,6 +35,7 @@
 #ifndef NRR_H
 #define NRR_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -240,6 +241,20 @@ nrr_status nrr_backward(nrr_ctx* ctx, int mode, const double* X,
  * X^(K). Host or device buffers. The solver state (iterate, stage, Anderson
  * history) is left as it was. K in 0..1024. */
 nrr_status nrr_unroll(nrr_ctx* ctx, int K, const double* X0, double* XK);
+
+/* Checkpoint and resume of a solve (the paper has no counterpart). The
+ * state is what later passes read and do not rebuild: the stage and
+ * safeguard scalars, the iterate X, the last MM results, the Anderson
+ * history and the deformed source of the last kept iterate, in the
+ * context's precision, behind a header naming the problem's sizes and
+ * precision. nrr_get_state_size gives its size in bytes; nrr_save_state
+ * writes it to buf (host or device, at least that size); nrr_load_state
+ * reads it into a context created from the same inputs and parameters, after
+ * which the solve continues exactly (bitwise) as the saved one would have.
+ * NRR_E_INVALID for a short buffer or a state saved from another problem. */
+nrr_status nrr_get_state_size(nrr_ctx* ctx, size_t* bytes);
+nrr_status nrr_save_state(nrr_ctx* ctx, void* buf, size_t bytes);
+nrr_status nrr_load_state(nrr_ctx* ctx, const void* buf, size_t bytes);
 
 /* Sets the current iterate X^(k) (X [N][12] doubles) and restarts the
  * current stage (E_prev = +inf, empty Anderson history). */

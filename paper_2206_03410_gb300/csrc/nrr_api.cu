@@ -949,6 +949,50 @@ nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, double* n
     return nrr_reset(c);
 }
 
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: the solver state that a pass reads and that later
+// passes do not rebuild - the device control block, the iterate X, the MM
+// results G, G_prev, F_prev, the Anderson rings dF, dG and both deformed-
+// source buffers (the stop test compares with the kept one). Layout: a
+// header {magic, version, precision, P, N, m}, then NrrState, then the
+// arrays in that order, in the context's precision.
+// ---------------------------------------------------------------------------
+struct CkptHeader {
+    uint64_t magic;      // "nrr-ckpt"
+    uint32_t version, fp64;
+    int64_t P, N, m;
+};
+constexpr uint64_t kCkptMagic = 0x74706b632d72726eull;
+
+size_t ckpt_bytes(const nrr_ctx* c) {
+    const size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
+    const size_t m = (size_t)std::max(1, c->prm.aa_m);
+    const size_t n12 = (size_t)c->N * 12;
+    return sizeof(CkptHeader) + sizeof(NrrState) + esz * (4 * n12 + 2 * m * n12 + 6 * (size_t)c->P);
+}
+
+template <typename T>
+nrr_status ckpt_copy(nrr_ctx* c, unsigned char* host, bool save) {
+    DevProblem<T>& d = prob<T>(c);
+    const size_t m = (size_t)std::max(1, c->prm.aa_m);
+    const size_t n12 = (size_t)c->N * 12;
+    T* arrays[6] = {d.X, d.G, d.Gprev, d.Fprev, d.dF, d.dG};
+    const size_t counts[6] = {n12, n12, n12, n12, m * n12, m * n12};
+    unsigned char* p = host;
+    for (int k = 0; k < 6; ++k) {
+        const size_t nb = sizeof(T) * counts[k];
+        if (save) CK(cudaMemcpyAsync(p, arrays[k], nb, cudaMemcpyDeviceToHost, c->stream));
+        else CK(cudaMemcpyAsync(arrays[k], p, nb, cudaMemcpyHostToDevice, c->stream));
+        p += nb;
+    }
+    const size_t nv = sizeof(T) * 6 * (size_t)c->P;
+    if (save) CK(cudaMemcpyAsync(p, d.vhat, nv, cudaMemcpyDeviceToHost, c->stream));
+    else CK(cudaMemcpyAsync(d.vhat, p, nv, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRR_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1515,6 +1559,52 @@ nrr_status nrr_tune(nrr_ctx* c, const char* table_path, int reps, nrr_launch_con
         out->pass_ms = 0.0;
     }
     return NRR_OK;
+}
+
+nrr_status nrr_get_state_size(nrr_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(c, NRR_E_INVALID, "NULL argument");
+    *bytes = ckpt_bytes(c);
+    return NRR_OK;
+}
+
+nrr_status nrr_save_state(nrr_ctx* c, void* buf, size_t bytes) {
+    if (!c || !buf) return fail(c, NRR_E_INVALID, "NULL argument");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    if (bytes < ckpt_bytes(c)) return fail(c, NRR_E_INVALID, "nrr_save_state: buffer smaller than nrr_get_state_size");
+    nrr_status st = pull_state(c);
+    if (st != NRR_OK) return st;
+    std::vector<unsigned char> h(ckpt_bytes(c));
+    CkptHeader hd{kCkptMagic, 1u, c->fp64 ? 1u : 0u, c->P, (int64_t)c->N, (int64_t)std::max(1, c->prm.aa_m)};
+    std::memcpy(h.data(), &hd, sizeof hd);
+    std::memcpy(h.data() + sizeof hd, c->h_state, sizeof(NrrState));
+    unsigned char* arrays = h.data() + sizeof hd + sizeof(NrrState);
+    st = c->fp64 ? ckpt_copy<double>(c, arrays, true) : ckpt_copy<float>(c, arrays, true);
+    if (st != NRR_OK) return st;
+    CK(cudaMemcpy(buf, h.data(), h.size(), cudaMemcpyDefault));
+    return NRR_OK;
+}
+
+nrr_status nrr_load_state(nrr_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf) return fail(c, NRR_E_INVALID, "NULL argument");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    if (bytes < ckpt_bytes(c)) return fail(c, NRR_E_INVALID, "nrr_load_state: buffer smaller than nrr_get_state_size");
+    std::vector<unsigned char> h(ckpt_bytes(c));
+    CK(cudaMemcpy(h.data(), buf, h.size(), cudaMemcpyDefault));
+    CkptHeader hd;
+    std::memcpy(&hd, h.data(), sizeof hd);
+    if (hd.magic != kCkptMagic || hd.version != 1u || hd.fp64 != (c->fp64 ? 1u : 0u) || hd.P != c->P ||
+        hd.N != (int64_t)c->N || hd.m != (int64_t)std::max(1, c->prm.aa_m))
+        return fail(c, NRR_E_INVALID, "nrr_load_state: the state was saved from a different problem or precision");
+    NrrState s;
+    std::memcpy(&s, h.data() + sizeof hd, sizeof s);
+    // counters of the last-block and barrier protocols start from zero
+    s.cnt_nn = 0; s.cnt_energy = 0; s.bar_count = 0; s.disp_bits = 0ull;
+    const unsigned char* arrays = h.data() + sizeof hd + sizeof(NrrState);
+    nrr_status st = c->fp64 ? ckpt_copy<double>(c, const_cast<unsigned char*>(arrays), false)
+                            : ckpt_copy<float>(c, const_cast<unsigned char*>(arrays), false);
+    if (st != NRR_OK) return st;
+    *c->h_state = s;
+    return push_state(c);
 }
 
 nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, double* grad_src) {

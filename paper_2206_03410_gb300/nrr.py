@@ -117,6 +117,9 @@ _SIGS = [
     ("nrr_energy", ctypes.c_int, [_VP, _VP, _VP]),
     ("nrr_backward", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     ("nrr_unroll", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    ("nrr_get_state_size", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    ("nrr_save_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    ("nrr_load_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("nrr_set_transforms", ctypes.c_int, [_VP, _VP]),
     ("nrr_set_stage", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double]),
     ("nrr_get_transforms", ctypes.c_int, [_VP, _VP]),
@@ -298,6 +301,20 @@ def nrr_unroll(ctx, K: int, X0):
     XK = np.zeros((N, 12), dtype=np.float64)
     _check(load().nrr_unroll(ctx, int(K), _ptr(X0a), _ptr(XK)), ctx)
     return XK
+
+
+def nrr_save_state(ctx) -> bytes:
+    """Checkpoint of the solve (see nrr_save_state in nrr.h)."""
+    n = ctypes.c_size_t()
+    _check(load().nrr_get_state_size(ctx, ctypes.byref(n)), ctx)
+    buf = (ctypes.c_ubyte * n.value)()
+    _check(load().nrr_save_state(ctx, ctypes.cast(buf, _VP), n), ctx)
+    return bytes(buf)
+
+
+def nrr_load_state(ctx, state: bytes):
+    buf = (ctypes.c_ubyte * len(state)).from_buffer_copy(state)
+    _check(load().nrr_load_state(ctx, ctypes.cast(buf, _VP), len(state)), ctx)
 
 
 def nrr_get_launch_config(ctx) -> NrrLaunchConfig:
@@ -485,6 +502,12 @@ class Registration:
 
     def backward(self, X=None, want_src: bool = True):
         return nrr_backward(self.ctx, X, 0, want_src)
+
+    def save_state(self) -> bytes:
+        return nrr_save_state(self.ctx)
+
+    def load_state(self, state: bytes):
+        nrr_load_state(self.ctx, state)
 
     def tune(self, table: str | None = None, reps: int = 0) -> NrrLaunchConfig:
         """Autotunes the launch shapes on this problem (restarts the solve)."""
