@@ -341,33 +341,42 @@ void fill_info(const NrrState& s, nrr_step_info* info) {
 // ---------------------------------------------------------------------------
 // Creation
 // ---------------------------------------------------------------------------
+// Hilbert orders of source and target over their common bounding box; they
+// depend on the inputs only, so nrr_create computes them on a second host
+// thread while it builds the deformation graph.
+struct CurveOrders {
+    double diag = 0.0;
+    std::vector<int> src_order, tgt_order;
+    std::vector<uint64_t> src_codes, tgt_codes;
+    void compute(const std::vector<float>& src, int64_t P, const std::vector<float>& tgt, int64_t Tn) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t i = 0; i < P; ++i)
+            for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], (double)src[3 * i + a]); hi[a] = std::max(hi[a], (double)src[3 * i + a]); }
+        for (int64_t i = 0; i < Tn; ++i)
+            for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], (double)tgt[3 * i + a]); hi[a] = std::max(hi[a], (double)tgt[3 * i + a]); }
+        const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        diag = std::sqrt(dx * dx + dy * dy + dz * dz);
+        // the two orders are independent: the target's on a further thread
+        std::thread tt([&]() { nrr_curve_order(tgt.data(), Tn, lo, hi, tgt_order, &tgt_codes); });
+        nrr_curve_order(src.data(), P, lo, hi, src_order, &src_codes);
+        tt.join();
+    }
+};
+
 template <typename T>
-nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::vector<float>& tgt, SetupTimer& tm) {
+nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::vector<float>& tgt, CurveOrders& co,
+                        SetupTimer& tm) {
     DevProblem<T>& d = prob<T>(c);
     const int64_t P = c->P, Tn = c->T;
     const HostGraph& g = c->hg;
     const int K = g.K, N = c->N;
-    // bbox of source and target together for the Hilbert codes
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = 0; i < P; ++i)
-        for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], (double)src[3 * i + a]); hi[a] = std::max(hi[a], (double)src[3 * i + a]); }
-    for (int64_t i = 0; i < Tn; ++i)
-        for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], (double)tgt[3 * i + a]); hi[a] = std::max(hi[a], (double)tgt[3 * i + a]); }
-    {
-        double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
-        c->diag = std::sqrt(dx * dx + dy * dy + dz * dz);
-    }
-    std::vector<uint64_t> src_codes, tgt_codes;
-    std::vector<int> tgt_order;
-    {
-        // the two orders are independent: the target's on a second thread
-        std::thread tt([&]() { nrr_curve_order(tgt.data(), Tn, lo, hi, tgt_order, &tgt_codes); });
-        nrr_curve_order(src.data(), P, lo, hi, c->src_order, &src_codes);
-        tt.join();
-    }
+    c->diag = co.diag;
+    c->src_order.swap(co.src_order);
+    std::vector<uint64_t>& src_codes = co.src_codes;
+    std::vector<uint64_t>& tgt_codes = co.tgt_codes;
+    std::vector<int>& tgt_order = co.tgt_order;
     c->src_rank.assign((size_t)P, 0);
     for (int64_t ii = 0; ii < P; ++ii) c->src_rank[(size_t)c->src_order[(size_t)ii]] = (int)ii;
-    tm.lap("curve orders");
 
     // source SoA and influence CSR in internal order
     std::vector<T> v((size_t)(3 * P));
@@ -1112,6 +1121,12 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         if (!finite3(tmp)) return fail(nullptr, NRR_E_INVALID, "non-finite target normals");
     }
     tm.lap("inputs");
+    // the curve orders on a second thread, beside l-bar and Algorithm 1
+    CurveOrders co;
+    struct Joiner {
+        std::thread t;
+        ~Joiner() { if (t.joinable()) t.join(); }
+    } orders_thread{std::thread([&]() { co.compute(src, P, tgt, T); })};
     // l-bar, radius and the deformation graph (Algorithm 1)
     std::vector<double> V(src.begin(), src.end());
     const bool need_lbar = prm.graph_radius <= 0 || prm.nu_r <= 0 || prm.nu_a_min <= 0;
@@ -1145,7 +1160,9 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     CK(cudaMalloc(&c->d_state, sizeof(NrrState)));
     CK(cudaMallocHost(&c->h_state, sizeof(NrrState)));
     std::memset(c->h_state, 0, sizeof(NrrState));
-    nrr_status st = c->fp64 ? build_device<double>(c, src, tgt, tm) : build_device<float>(c, src, tgt, tm);
+    orders_thread.t.join();
+    tm.lap("curve orders (joined)");
+    nrr_status st = c->fp64 ? build_device<double>(c, src, tgt, co, tm) : build_device<float>(c, src, tgt, co, tm);
     if (st != NRR_OK) return st;
     if (c->fp64) choose_solver<double>(c); else choose_solver<float>(c);
     tm.lap("solver choice");
