@@ -400,7 +400,8 @@ def run_ours(args):
                     "launch_ms_note": "steps timed one after the other; in the pass graph xterm_kernel "
                                       "runs beside nn_kernel"}
         result.update(dict(roofline=roofline, P=reg.P, T=reg.T, N=reg.N, n_edges=reg.n_edges,
-                           last_pcg_iters=avg_pcg, clocks=clk, launch=launch))
+                           last_pcg_iters=avg_pcg, clocks=clk, launch=launch,
+                           launches_per_pass=reg.launch_config().launches_per_pass))
 
         # ---- time-to-converge: mixed vs FP64, same energy -----------------
         if not args.no_ttc:
@@ -504,9 +505,6 @@ def cpu_baseline(pair, kw):
             "wall_s": round(time.perf_counter() - t0, 1)}
 
 
-def nrr_launches_per_pass() -> int:
-    from paper_2206_03410_gb300 import nrr
-    return nrr.LAUNCHES_PER_PASS
 
 
 def main():
@@ -532,7 +530,7 @@ def main():
                    "iters_timed": res["iters"], "passes_timed": res["passes"]},
         "roofline": res["roofline"],
         "clocks": res["clocks"],
-        "gpu_launches": nrr_launches_per_pass() * args.steps,
+        "gpu_launches": res["launches_per_pass"] * args.steps,
         "e2e": res.get("e2e"),
         "ttc": res.get("ttc"),
         "batch": res.get("batch"),

@@ -381,6 +381,7 @@ typedef struct {
     double nn_ms, solve_ms;    /* measured mean kernel durations of the
                                   chosen shapes (nrr_tune; 0 otherwise)     */
     double pass_ms;            /* measured mean batch pass (nrr_batch_tune) */
+    int    launches_per_pass;  /* kernels one pass launches                 */
 } nrr_launch_config;
 
 /* Current launch shapes of a context (ms fields 0). */

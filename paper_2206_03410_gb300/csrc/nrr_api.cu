@@ -1539,6 +1539,7 @@ nrr_status nrr_get_launch_config(nrr_ctx* c, nrr_launch_config* out) {
     out->nn_ms = 0.0;
     out->solve_ms = 0.0;
     out->pass_ms = 0.0;
+    out->launches_per_pass = kNrrLaunchesPerPass;
     return NRR_OK;
 }
 
@@ -1574,6 +1575,7 @@ nrr_status nrr_tune(nrr_ctx* c, const char* table_path, int reps, nrr_launch_con
         out->nn_ms = nn_ms;
         out->solve_ms = solve_ms;
         out->pass_ms = 0.0;
+        out->launches_per_pass = kNrrLaunchesPerPass;
     }
     return NRR_OK;
 }
@@ -1830,6 +1832,7 @@ nrr_status nrr_batch_tune(nrr_batch* b, const char* table_path, int reps, nrr_la
         out->nn_ms = 0.0;
         out->solve_ms = 0.0;
         out->pass_ms = best_ms;
+        out->launches_per_pass = 0;
     }
     return NRR_OK;
 }

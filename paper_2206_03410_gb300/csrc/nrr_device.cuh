@@ -120,6 +120,9 @@ template <typename T>
 cudaError_t nrr_launch_solve(const DevProblem<T>& d, int grid, cudaStream_t s, bool cooperative);
 template <typename T>
 cudaError_t nrr_launch_aa(const DevProblem<T>& d, int grid, cudaStream_t s);
+// kernels one pass launches: closest points, X-only terms, energy, assembly,
+// solve, Anderson differences/Gram solve, Anderson mix
+constexpr int kNrrLaunchesPerPass = 7;
 template <typename T>
 cudaError_t nrr_launch_gradient(const DevProblem<T>& d, double* grad_X, double* grad_v, const int* order,
                                 int grid, cudaStream_t s);

@@ -67,6 +67,7 @@ class NrrLaunchConfig(ctypes.Structure):
         ("nn_ms", ctypes.c_double),
         ("solve_ms", ctypes.c_double),
         ("pass_ms", ctypes.c_double),
+        ("launches_per_pass", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -263,10 +264,6 @@ def nrr_reset(ctx):
 # the steps of a pass in launch order; the last is two kernels
 # (aa_dots_kernel, aa_mix_kernel)
 KERNELS = ("nn_kernel", "xterm_kernel", "energy_kernel", "assemble_kernel", "solve_kernel", "aa_kernels")
-# kernel launches of one pass: closest points, regularisation and rotation
-# terms (beside the closest points in the pass graph), energy, assembly,
-# solve and the two Anderson kernels (aa_dots, aa_mix)
-LAUNCHES_PER_PASS = 7
 
 
 def nrr_time_kernels(ctx, n: int = 1) -> np.ndarray:

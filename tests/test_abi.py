@@ -38,8 +38,9 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layout_matches_header():
     src = ('#include <stdio.h>\n#include <stddef.h>\n#include "nrr.h"\n'
-           'int main(){printf("%zu %zu %zu %zu\\n", sizeof(nrr_params), sizeof(nrr_step_info),'
-           ' offsetof(nrr_params, pcg_max_iters), offsetof(nrr_step_info, status));}\n')
+           'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(nrr_params), sizeof(nrr_step_info),'
+           ' offsetof(nrr_params, pcg_max_iters), offsetof(nrr_step_info, status),'
+           ' sizeof(nrr_launch_config), offsetof(nrr_params, nu_schedule));}\n')
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "p.c")
         exe = os.path.join(d, "p")
@@ -51,6 +52,8 @@ def test_struct_layout_matches_header():
     assert vals[1] == ctypes.sizeof(nrr.NrrStepInfo)
     assert vals[2] == nrr.NrrParams.pcg_max_iters.offset
     assert vals[3] == nrr.NrrStepInfo.status.offset
+    assert vals[4] == ctypes.sizeof(nrr.NrrLaunchConfig)
+    assert vals[5] == nrr.NrrParams.nu_schedule.offset
 
 
 def test_params_default_values():
