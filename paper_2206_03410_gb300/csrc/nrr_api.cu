@@ -12,6 +12,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nrr_device.cuh"
 
 int nrr_solve_threads();
@@ -88,12 +90,22 @@ struct nrr_ctx {
 
 namespace {
 
+// NVTX range around a host call (visible in Nsight Systems / Compute
+// timelines; a no-op without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Wall-clock phases of nrr_create, printed to stderr when the environment
 // variable NRR_SETUP_TIMES is set (profiling of the host setup).
 struct SetupTimer {
     bool on = std::getenv("NRR_SETUP_TIMES") != nullptr;
     std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
     void lap(const char* what) {
+        nvtxMarkA(what);
         if (!on) return;
         const auto now = std::chrono::steady_clock::now();
         std::fprintf(stderr, "nrr_create %-22s %8.2f ms\n", what,
@@ -1062,6 +1074,7 @@ void nrr_destroy(nrr_ctx* c) {
 nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm, int64_t P,
                       const float* tgt_xyz, const float* tgt_nrm, int64_t T,
                       const nrr_params* params, void* cuda_stream) {
+    NvtxRange nvtx_range("nrr_create");
     nrr_ctx* c = nullptr;
     if (!out) return fail(nullptr, NRR_E_INVALID, "out is NULL");
     *out = nullptr;
@@ -1217,6 +1230,7 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
 }
 
 nrr_status nrr_step(nrr_ctx* c, nrr_step_info* info) {
+    NvtxRange nvtx_range("nrr_step");
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
     if (c->h_state->done) return fail(c, NRR_E_STATE, "the solve has already returned");
@@ -1233,6 +1247,7 @@ nrr_status nrr_step(nrr_ctx* c, nrr_step_info* info) {
 }
 
 nrr_status nrr_solve(nrr_ctx* c, int max_passes, nrr_step_info* info) {
+    NvtxRange nvtx_range("nrr_solve");
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
     const int cap = max_passes > 0 ? max_passes : c->prm.max_total_passes;
@@ -1337,6 +1352,7 @@ nrr_status nrr_reset(nrr_ctx* c) {
 }
 
 nrr_status nrr_energy(nrr_ctx* c, const double* X, double out_terms[4]) {
+    NvtxRange nvtx_range("nrr_energy");
     if (!c || !out_terms) return fail(c, NRR_E_INVALID, "NULL argument");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
     nrr_status st;
@@ -1551,6 +1567,7 @@ nrr_status nrr_set_launch_config(nrr_ctx* c, const nrr_launch_config* cfg) {
 }
 
 nrr_status nrr_tune(nrr_ctx* c, const char* table_path, int reps, nrr_launch_config* out) {
+    NvtxRange nvtx_range("nrr_tune");
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
     if (reps <= 0) reps = 5;
@@ -1587,6 +1604,7 @@ nrr_status nrr_get_state_size(nrr_ctx* c, size_t* bytes) {
 }
 
 nrr_status nrr_save_state(nrr_ctx* c, void* buf, size_t bytes) {
+    NvtxRange nvtx_range("nrr_save_state");
     if (!c || !buf) return fail(c, NRR_E_INVALID, "NULL argument");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
     if (bytes < ckpt_bytes(c)) return fail(c, NRR_E_INVALID, "nrr_save_state: buffer smaller than nrr_get_state_size");
@@ -1604,6 +1622,7 @@ nrr_status nrr_save_state(nrr_ctx* c, void* buf, size_t bytes) {
 }
 
 nrr_status nrr_load_state(nrr_ctx* c, const void* buf, size_t bytes) {
+    NvtxRange nvtx_range("nrr_load_state");
     if (!c || !buf) return fail(c, NRR_E_INVALID, "NULL argument");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
     if (bytes < ckpt_bytes(c)) return fail(c, NRR_E_INVALID, "nrr_load_state: buffer smaller than nrr_get_state_size");
@@ -1627,6 +1646,7 @@ nrr_status nrr_load_state(nrr_ctx* c, const void* buf, size_t bytes) {
 }
 
 nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, double* grad_src) {
+    NvtxRange nvtx_range("nrr_backward");
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
     if (mode != 0 && mode != 1) return fail(c, NRR_E_INVALID, "nrr_backward: mode must be 0 or 1");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
@@ -1659,6 +1679,7 @@ nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, d
 }
 
 nrr_status nrr_unroll(nrr_ctx* c, int K, const double* X0, double* XK) {
+    NvtxRange nvtx_range("nrr_unroll");
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
     if (!X0) return fail(c, NRR_E_INVALID, "nrr_unroll: X0 is NULL");
     if (K < 0 || K > 1024) return fail(c, NRR_E_INVALID, "nrr_unroll: K must be in 0..1024");
@@ -1780,6 +1801,7 @@ nrr_status batch_apply(nrr_batch* b, int lpq, int policy) {
 extern "C" {
 
 nrr_status nrr_batch_tune(nrr_batch* b, const char* table_path, int reps, nrr_launch_config* out) {
+    NvtxRange nvtx_range("nrr_batch_tune");
     if (!b) return batch_fail(nullptr, NRR_E_INVALID, "batch is NULL");
     if (reps <= 0) reps = 3;
     if (reps > 1000) return batch_fail(b, NRR_E_INVALID, "nrr_batch_tune: reps must be at most 1000");
@@ -1893,6 +1915,7 @@ nrr_status nrr_batch_create(nrr_batch** out, int n_pairs, const float* const* sr
 }
 
 nrr_status nrr_batch_solve(nrr_batch* b, int max_passes, nrr_step_info* infos) {
+    NvtxRange nvtx_range("nrr_batch_solve");
     if (!b) return batch_fail(nullptr, NRR_E_INVALID, "batch is NULL");
     const int n = (int)b->ctx.size();
     int cap = max_passes;
