@@ -266,7 +266,7 @@ def _sphere50k_partial(seed: int = 1) -> Pair:
     p = sphere_pair(50000, 60000, n_bumps=32, amp=0.1, width=0.3,
                     warp_cap=0.15, noise=0.02, outliers=0.10, crop=0.30,
                     seed=seed, same_samples=False)
-    p.params = dict(radius=0.055, k_alpha=100.0, k_beta=1.0, aa_m=5,
+    p.params = dict(radius=0.085, k_alpha=100.0, k_beta=1.0, aa_m=5,
                     iters=50, precision="mixed")
     p.name = "sphere50k_partial"
     return p
