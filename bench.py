@@ -224,28 +224,38 @@ def ttc_pair(nrr, pair, kw, stream, args) -> dict:
     out = {}
     finals = {}
     regs = {}
-    for prec in ("mixed", "fp64"):
-        r = nrr.Registration(src, tgt, stream=stream.cuda_stream, precision=prec, **kw)
+    for name, prec, extra in ARMS:
+        r = nrr.Registration(src, tgt, stream=stream.cuda_stream, precision=prec, **kw, **extra)
         if not args.no_tune:
             r.tune()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         info = r.solve(20000)
         torch.cuda.synchronize()
-        out[prec + "_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
-        out[prec + "_iters"] = info.n_solves
-        finals[prec] = (r.transforms(), info)
-        regs[prec] = r
+        out[name + "_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+        out[name + "_iters"] = info.n_solves
+        finals[name] = (r.transforms(), info)
+        regs[name] = r
     r64 = regs["fp64"]
     i64 = finals["fp64"][1]
     r64.set_stage(i64.nu_a, i64.nu_r)
     e64 = r64.energy(finals["fp64"][0])[0]
     e32 = r64.energy(finals["mixed"][0])[0]
+    ec = r64.energy(finals[CONTROL][0])[0]
     for r in regs.values():
         r.close()
     out["gap"] = float((e32 - e64) / abs(e64))
+    out["gap_" + CONTROL] = float((ec - e64) / abs(e64))
     out["speedup"] = round(out["fp64_ms"] / out["mixed_ms"], 2)
     return out
+
+
+# time-to-converge arms: the mixed path, the FP64 path (PCG to 1e-12), and a
+# control in FP64 arithmetic with the mixed path's PCG tolerance (1e-6): the
+# gap of the control to the FP64 arm is what the solve tolerance alone does
+# to the end point of the trajectory
+CONTROL = "fp64_pcg1e-6"
+ARMS = (("mixed", "mixed", {}), ("fp64", "fp64", {}), (CONTROL, "fp64", dict(pcg_tol=1e-6)))
 
 
 VARIANTS = [("welsch", {}), ("l2", dict(robust="l2")), ("l2r", dict(robust="l2r")),
@@ -440,6 +450,11 @@ def run_ours(args):
                 ttc["signed_gaps_all"] = gaps
                 ttc["mixed_not_worse"] = int(sum(g <= 1e-5 for g in gaps))
                 ttc["runs"] = len(gaps)
+                ctl = [x["gap_" + CONTROL] for x in seeds]
+                ttc["control"] = {"arm": CONTROL + ": FP64 arithmetic, PCG to relative residual 1e-6",
+                                  "signed_gaps": ctl,
+                                  "mean_abs_gap": float(np.mean(np.abs(ctl))),
+                                  "mixed_mean_abs_gap": float(np.mean(np.abs([x["gap"] for x in seeds])))}
             result["ttc"] = ttc
 
         # ---- batched pairs (64 independent pairs, one graph launch per pass) ----

@@ -111,9 +111,11 @@ typedef struct {
     double eps;                /* stop when max_i |v_hat_i^(k+1) - v_hat_i^(k)|
                                   < eps; <= 0: 1e-5 x bbox diagonal of
                                   source and target (Sec. 4.1)              */
-    double rel_energy_tol;     /* > 0: a stage also ends when consecutive
-                                  kept energies differ by less than this
-                                  relative amount; default 0 (off)          */
+    double rel_energy_tol;     /* > 0: a stage ends when consecutive kept
+                                  energies differ by less than this
+                                  relative amount (or at I_max), and the
+                                  eps test is not applied; default 0 (off:
+                                  the eps test)                             */
     int    precision;          /* nrr_precision; default NRR_MIXED          */
     double pcg_tol;            /* relative residual of the PCG solve of
                                   K X = B; <= 0: 1e-12 (FP64), 1e-6 (MIXED) */

@@ -15,9 +15,11 @@ Readings of Algorithm 2 used here:
 * The stopping test max_i |v_hat_i^(k+1) - v_hat_i^(k)| < eps compares the
   deformed source at the new iterate with the one at the kept iterate of
   the pass; I_max counts solves in the stage.
-* Optional extra stopping test (off unless rel_energy_tol > 0): the stage
+* Optional energy stopping test (off unless rel_energy_tol > 0): the stage
   ends when two consecutive kept energies differ by less than
-  rel_energy_tol relative to the earlier one.
+  rel_energy_tol relative to the earlier one. It replaces the displacement
+  test (a stage then ends on the energy test or I_max only): the
+  depth-scale workload is run to a relative energy change below 1e-6.
 * nu annealing: nu_a starts at the median initial closest-point distance of
   the undeformed source, nu_r at 3 l-bar; after each stage nu_a is halved
   (clamped at nu_a_min = l-bar / sqrt(3)) and nu_r is halved; the last stage
@@ -214,7 +216,8 @@ class Registration:
         rec.max_disp = disp
         self.records.append(rec)
         self.X = X_new
-        if disp < self.eps or self.n_solves == self.p.max_iters_per_stage:
+        disp_stop = self.p.rel_energy_tol <= 0 and disp < self.eps
+        if disp_stop or self.n_solves == self.p.max_iters_per_stage:
             self._end_stage()
         return rec
 

@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
         const double disp = sqrt(__longlong_as_double((long long)atomicAdd(&st->disp_bits, 0ull)));
         st->max_disp = disp;
         st->pending_stop = 0;
-        if (disp < st->eps || st->n_solves_stage >= st->max_iters_stage) nrr_end_stage(st);
+        // with an energy test the stage ends on it (or I_max) only
+        if ((st->rel_tol <= 0 && disp < st->eps) || st->n_solves_stage >= st->max_iters_stage) nrr_end_stage(st);
     }
     st->disp_bits = 0ull;
     }

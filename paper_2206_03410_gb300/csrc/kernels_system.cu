@@ -33,12 +33,39 @@ __device__ __forceinline__ float t_expm1<float>(float x) { return expm1f(x); }
 template <>
 __device__ __forceinline__ double t_expm1<double>(double x) { return expm1(x); }
 
+// |D_ab|^2 of the regularisation residual of directed edge e (Eq. RegTerm):
+// D_ab = r_ab (A_b (p_a - p_b) + p_b + t_b - p_a - t_a). One definition for
+// both kernels that form the weights, so that they agree bit for bit.
+template <typename T>
+__device__ __forceinline__ T reg_d2(const DevProblem<T>& d, const T* X, int e) {
+    const int a = d.e_i[e], b = d.e_j[e];
+    const T r = d.e_r[e];
+    const T* Xb = X + 12 * b;
+    const T* Xa = X + 12 * a;
+    const T dx = d.p[3 * a] - d.p[3 * b];
+    const T dy = d.p[3 * a + 1] - d.p[3 * b + 1];
+    const T dz = d.p[3 * a + 2] - d.p[3 * b + 2];
+    // p_b - p_a = -(p_a - p_b)
+    const T Dx = r * ((Xb[0] * dx + Xb[3] * dy + Xb[6] * dz - dx) + (Xb[9] - Xa[9]));
+    const T Dy = r * ((Xb[1] * dx + Xb[4] * dy + Xb[7] * dz - dy) + (Xb[10] - Xa[10]));
+    const T Dz = r * ((Xb[2] * dx + Xb[5] * dy + Xb[8] * dz - dz) + (Xb[11] - Xa[11]));
+    return Dx * Dx + Dy * Dy + Dz * Dz;
+}
+
+// 1 / (2 nu^2) in T, the scale of the Welsch weights and energy terms
+template <typename T>
+__device__ __forceinline__ T welsch_scale(double nu) { return (T)(1.0 / (2.0 * nu * nu)); }
+
 // Terms of Eq. (objective_func) that depend on X only, not on the closest
 // points: the regularisation term (Eq. RegTerm) with its surrogate weights
 // w^r_ij, and the rotation term with the projections proj_R(A_n). A pass
 // runs this kernel on a parallel branch of its graph, beside the
-// closest-point search. Each CTA writes its two partial sums to
-// d.xpartials; energy_kernel adds them.
+// closest-point search, whose last CTA may end the stage (Algorithm 2) and
+// halve nu_r while this kernel runs. So each CTA records the nu_r it read
+// and sums the regularisation term at that nu_r and at half of it;
+// energy_kernel, which runs after both, takes the sum at the stage's nu_r
+// and re-forms the weights if a CTA read the previous stage's value.
+// Per CTA: d.xpartials[4 b ..] = {E_reg at nu, E_reg at nu / 2, E_rot, nu}.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) xterm_kernel(DevProblem<T> d) {
     __shared__ double sh[kThreads / 32];
@@ -47,30 +74,23 @@ __global__ void __launch_bounds__(kThreads) xterm_kernel(DevProblem<T> d) {
     const T* X = (MODE == NRR_MODE_EVAL) ? d.Xeval : d.X;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gstride = gridDim.x * blockDim.x;
-    const double nur = st->nu_r;
-    const T ir = (T)(1.0 / (2.0 * nur * nur));
-    double er = 0.0, eo = 0.0;
+    __shared__ double s_nu;
+    if (threadIdx.x == 0) s_nu = *reinterpret_cast<volatile const double*>(&st->nu_r);
+    __syncthreads();
+    const double nur = s_nu;
+    const T ir = welsch_scale<T>(nur), irh = welsch_scale<T>(0.5 * nur);
+    double er = 0.0, erh = 0.0, eo = 0.0;
     // regularisation term (Eq. RegTerm) over directed pairs, weights w^r_ij
     for (int e = gtid; e < d.E2; e += gstride) {
-        const int a = d.e_i[e], b = d.e_j[e];
-        const T r = d.e_r[e];
-        const T* Xb = X + 12 * b;
-        const T* Xa = X + 12 * a;
-        const T dx = d.p[3 * a] - d.p[3 * b];
-        const T dy = d.p[3 * a + 1] - d.p[3 * b + 1];
-        const T dz = d.p[3 * a + 2] - d.p[3 * b + 2];
-        // D_ab = r (A_b (p_a - p_b) + p_b + t_b - p_a - t_a), with p_b - p_a = -(p_a - p_b)
-        const T Dx = r * ((Xb[0] * dx + Xb[3] * dy + Xb[6] * dz - dx) + (Xb[9] - Xa[9]));
-        const T Dy = r * ((Xb[1] * dx + Xb[4] * dy + Xb[7] * dz - dy) + (Xb[10] - Xa[10]));
-        const T Dz = r * ((Xb[2] * dx + Xb[5] * dy + Xb[8] * dz - dz) + (Xb[11] - Xa[11]));
-        const T D2 = Dx * Dx + Dy * Dy + Dz * Dz;
+        const T D2 = reg_d2(d, X, e);
         if (d.robust == NRR_WELSCH) {
-            const T n2 = D2 * ir;
-            er += (double)(-t_expm1<T>(-n2));
-            d.wr[e] = t_exp<T>(-n2) * ir;
+            er += (double)(-t_expm1<T>(-D2 * ir));
+            erh += (double)(-t_expm1<T>(-D2 * irh));
+            d.wr[e] = t_exp<T>(-D2 * ir) * ir;
         } else {
             // squared norm: energy |D|^2, weight 1
             er += (double)D2;
+            erh += (double)D2;
             d.wr[e] = (T)1;
         }
     }
@@ -91,10 +111,13 @@ __global__ void __launch_bounds__(kThreads) xterm_kernel(DevProblem<T> d) {
         eo += s;
     }
     const double sr = block_sum(er, sh);
+    const double srh = block_sum(erh, sh);
     const double so = block_sum(eo, sh);
     if (threadIdx.x == 0) {
-        d.xpartials[2 * blockIdx.x + 0] = sr;
-        d.xpartials[2 * blockIdx.x + 1] = so;
+        d.xpartials[4 * blockIdx.x + 0] = sr;
+        d.xpartials[4 * blockIdx.x + 1] = srh;
+        d.xpartials[4 * blockIdx.x + 2] = so;
+        d.xpartials[4 * blockIdx.x + 3] = nur;
     }
 }
 
@@ -111,8 +134,20 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gstride = gridDim.x * blockDim.x;
     const double nua = st->nu_a;
-    const T ia = (T)(1.0 / (2.0 * nua * nua));
+    const T ia = welsch_scale<T>(nua);
     double ea = 0.0;
+    // did a CTA of xterm_kernel read the nu_r of the previous stage (the
+    // closest-point search ended the stage while it ran)? Then the weights
+    // w^r are formed again here at the stage's nu_r.
+    const double nur = st->nu_r;
+    int mine = 0;
+    for (int b = threadIdx.x; b < d.n_xpart; b += blockDim.x) mine |= __ldcg(d.xpartials + 4 * b + 3) != nur;
+    const int stale = __syncthreads_or(mine);
+    if (stale && d.robust == NRR_WELSCH) {
+        const T* X = (MODE == NRR_MODE_EVAL) ? d.Xeval : d.X;
+        const T ir = welsch_scale<T>(nur);
+        for (int e = gtid; e < d.E2; e += gstride) d.wr[e] = t_exp<T>(-reg_d2(d, X, e) * ir) * ir;
+    }
     // alignment term (Eq. AlignmentTerm) and its surrogate weights w^a_i;
     // the l2 variants: d^2 with weight 1, or min(d^2, 9 nu_a^2) with weight
     // 1 below 3 nu_a and 0 from there on
@@ -149,8 +184,11 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
         for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
             pa += __ldcg(d.partials + b * NRR_PARTIAL_STRIDE + 0);
         for (int b = threadIdx.x; b < d.n_xpart; b += blockDim.x) {
-            pr += __ldcg(d.xpartials + 2 * b + 0);
-            po += __ldcg(d.xpartials + 2 * b + 1);
+            // a CTA that read the previous stage's nu_r (twice the current
+            // one, exactly) summed the term at the current nu_r second
+            const bool same = __ldcg(d.xpartials + 4 * b + 3) == nur;
+            pr += __ldcg(d.xpartials + 4 * b + (same ? 0 : 1));
+            po += __ldcg(d.xpartials + 4 * b + 2);
         }
         const double ta = block_sum(pa, sh);
         const double tr = block_sum(pr, sh);

@@ -618,7 +618,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     // few CTAs: the kernel runs beside the closest-point search and should
     // take few of its SM slots
     d.n_xpart = std::max(1, std::min(std::max(1, c->num_sms / 4), (c->E2 + c->N + 255) / 256));
-    CK(dalloc(c, &d.xpartials, (size_t)2 * d.n_xpart));
+    CK(dalloc(c, &d.xpartials, (size_t)4 * d.n_xpart));
     d.st = c->d_state;
     d.nn_stats = nullptr;
     d.solve_stats = nullptr;

@@ -89,7 +89,7 @@ struct DevProblem {
     T* Minv;
     // reductions
     double* partials;   // [max_ctas * NRR_PARTIAL_STRIDE]
-    double* xpartials;  // [n_xpart][2] E_reg, E_rot partial sums of xterm_kernel's CTAs
+    double* xpartials;  // [n_xpart][4] E_reg at nu_r and nu_r / 2, E_rot, the nu_r read (xterm_kernel's CTAs)
     int n_xpart;        // CTAs of xterm_kernel
     NrrState* st;
     // optional per-warp counters of the closest-point search (NULL: off):

@@ -163,6 +163,34 @@ def test_fp64_trajectory_matches_oracle():
     reg.close()
 
 
+@pytest.mark.parametrize("stop", [dict(eps=1e9), dict(eps=1e9, rel_energy_tol=1e-300),
+                                  dict(eps=1e9, rel_energy_tol=1.0), dict(rel_energy_tol=1e-3)])
+def test_stop_rules_match_oracle(stop):
+    """Stage ends on the displacement test, or, with an energy tolerance, on
+    the relative energy change between kept passes (Algorithm 2 and the
+    depth-scale workload's convergence rule): the same passes, stages and
+    energies as the oracle, pass by pass, to the end of the run."""
+    pair = synth.tiny_pair(300, 330, seed=9, noise=0.002, outliers=0.03)
+    kw = dict(radius=0.35, nu_a=0.2, nu_r=0.4, nu_a_min=0.03, aa_m=0, max_iters_per_stage=3, **stop)
+    ora = OReg(pair.src, pair.tgt, Params(**kw))
+    reg = _gpu(pair, "fp64", **kw)
+    k = 0
+    while not ora.done:
+        rec = ora.step()
+        info = reg.step()
+        # the energy of a pass is taken at its stage's nu: equal energies
+        # mean equal stages
+        assert info.kept == int(rec.kept), (k, stop)
+        assert abs(info.E - rec.E) < 1e-9 * abs(rec.E), (k, stop)
+        k += 1
+    # a displacement or I_max stop is detected at the start of the next pass
+    info = reg.step() if not info.done else info
+    assert info.done == 1 and info.stage == ora.stage, stop
+    assert (info.n_passes, info.n_solves) == (len(ora.records), ora.n_solves_total), stop
+    assert relmax(reg.transforms(), ora.X) < 1e-6
+    reg.close()
+
+
 def test_solve_converges_and_mixed_matches_fp64_energy():
     pair = synth.tiny_pair(2000, 2200, seed=32, noise=0.002, outliers=0.05)
     kw = dict(radius=0.25, aa_m=5, rel_energy_tol=1e-6)

@@ -564,3 +564,37 @@ def test_nu_fixed_variants_follow_the_annealing_schedule():
         assert (r.nu_a, r.nu_r) == want
         r.solve()
         assert {rec.stage for rec in r.records} == {0}
+
+
+def _solves_per_stage(reg):
+    """Solves of each stage: the passes that reached the solve carry the
+    displacement of their new iterate."""
+    out = {}
+    for r in reg.records:
+        if not math.isnan(r.max_disp):
+            out[r.stage] = out.get(r.stage, 0) + 1
+    return [out.get(k, 0) for k in range(max(out) + 1)]
+
+
+def test_stop_rules_displacement_or_energy():
+    """Algorithm 2 ends a stage when the deformed source moves less than eps
+    (or after I_max solves); with an energy tolerance, the rule the
+    depth-scale workload is run to, a stage ends when two consecutive kept
+    energies differ by less than that tolerance (or at I_max) and the
+    displacement test is off."""
+    pair = synth.tiny_pair(300, 330, seed=9, noise=0.002, outliers=0.03)
+    base = dict(radius=0.35, nu_a=0.2, nu_r=0.4, nu_a_min=0.03, aa_m=0, max_iters_per_stage=3)
+    # eps above any displacement: every stage ends after its first solve
+    r = Registration(pair.src, pair.tgt, Params(eps=1e9, **base))
+    r.solve()
+    assert r.done and _solves_per_stage(r) == [1, 1, 1, 1]
+    # an energy tolerance that never holds: I_max solves per stage, eps unused
+    r = Registration(pair.src, pair.tgt, Params(eps=1e9, rel_energy_tol=1e-300, **base))
+    r.solve()
+    assert r.done and _solves_per_stage(r) == [3, 3, 3, 3]
+    # a tolerance that always holds: the second kept pass of a stage ends it
+    # without a solve
+    r = Registration(pair.src, pair.tgt, Params(eps=1e9, rel_energy_tol=1.0, **base))
+    r.solve()
+    assert r.done and _solves_per_stage(r) == [1, 1, 1, 1]
+    assert [math.isnan(x.max_disp) for x in r.records] == [False, True] * 4
