@@ -353,14 +353,20 @@ constexpr int kClusterThreads = 768;
 constexpr int kSpmvChunk = 1;   // blocks per thread whose z rows are in flight together
 constexpr int kClusterWarps = kClusterThreads / 32;
 
-// Cluster-wide sum of K values per thread. Per-thread values (type W) are
-// reduced within each warp by a shuffle tree in W, then in R: over the warps
-// of a CTA (warp 0), and over the CTAs of the cluster. The cross-CTA step is
-// push-based: warp 0 of every CTA stores its CTA's sums into a slot of every
-// CTA's shared memory before the cluster barrier, so after the barrier each
-// warp reads local shared memory only. All trees have a fixed shape and
-// floating-point addition is commutative, so every thread of every CTA gets
-// bitwise the same sums on every run.
+// Cluster-wide sums of K3 values per node and column: value j of column c
+// is total 3 j + c. The thread of node ln and column c (four threads per
+// node, the fourth without values) adds its values in three steps, each a
+// fixed-shape tree, so every thread of every CTA gets bitwise the same sums
+// on every run:
+//  1. within the warp over its 8 nodes (shuffles across lanes 4k + c): lane
+//     c < 3 then holds the warp's sums for column c and stores them;
+//  2. over the warps of the CTA, one warp per total (K warps), which pushes
+//     the CTA's sum into a slot of every CTA's shared memory before the
+//     cluster barrier (push-based: after it each CTA reads local memory);
+//  3. over the CTAs, again one warp per total, then a CTA barrier, after
+//     which every thread reads the totals.
+// One warp per total keeps the shuffle count of a reduction at about
+// (3 K3 x warps + 10 K): the shuffle unit is shared by the CTA's 24 warps.
 constexpr int kClusterMaxCtas = 16;
 // row stride (elements of T) of the preconditioner blocks in shared memory:
 // 20 rather than 16 puts the rows of 8 consecutive nodes in distinct banks
@@ -369,70 +375,49 @@ constexpr int kMStride = 20;
 template <typename R>
 struct ClusterSum {
     R* s_red;   // [2][kClusterMaxCtas][kMaxRed], written by every CTA
-    R* s_tmp;   // [kClusterWarps][kMaxRed]
+    R* s_tmp;   // [kClusterWarps][kMaxRed]: per-warp sums
+    R* s_tot;   // [kMaxRed]: cluster totals
     int buf;
     int active_warps;   // warps whose threads may hold non-zero values
-    template <int K, typename W>
-    __device__ void run(const W (&v)[K], R (&out)[K]) {
+    template <int K3>
+    __device__ void run(bool has, int c, const R (&v)[K3], R (&out)[3 * K3]) {
+        constexpr int K = 3 * K3;
+        static_assert(K <= kMaxRed && K <= kClusterWarps, "reduction size");
         cg::cluster_group cl = cg::this_cluster();
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        W x[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) x[j] = v[j];
         if (w < active_warps) {
+            R x[K3];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int j = 0; j < K3; ++j) x[j] = has ? v[j] : R(0);
 #pragma unroll
-                for (int j = 0; j < K; ++j) x[j] += __shfl_xor_sync(0xffffffffu, x[j], o);
+            for (int o = 4; o < 32; o <<= 1) {
+#pragma unroll
+                for (int j = 0; j < K3; ++j) x[j] += __shfl_xor_sync(0xffffffffu, x[j], o);
             }
-            if (lane == 0) {
+            if (lane < 3) {
 #pragma unroll
-                for (int j = 0; j < K; ++j) s_tmp[w * kMaxRed + j] = (R)x[j];
+                for (int j = 0; j < K3; ++j) s_tmp[w * kMaxRed + 3 * j + lane] = x[j];
             }
         }
         __syncthreads();
         const int nr = (int)cl.num_blocks();
-        if (w == 0) {
-            const int nw = active_warps;
-            R y[K];
+        if (w < K) {
+            R y = lane < active_warps ? s_tmp[lane * kMaxRed + w] : R(0);
 #pragma unroll
-            for (int j = 0; j < K; ++j) y[j] = lane < nw ? s_tmp[lane * kMaxRed + j] : R(0);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                for (int j = 0; j < K; ++j) y[j] += __shfl_xor_sync(0xffffffffu, y[j], o);
-            }
-            if (lane < nr) {
-                R* dst = cl.map_shared_rank(s_red, lane) + (buf * kClusterMaxCtas + (int)cl.block_rank()) * kMaxRed;
-#pragma unroll
-                for (int j = 0; j < K; ++j) dst[j] = y[j];
-            }
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            if (lane < nr)
+                cl.map_shared_rank(s_red, lane)[(buf * kClusterMaxCtas + (int)cl.block_rank()) * kMaxRed + w] = y;
         }
         cl.sync();   // release/acquire: every CTA's slot is written
-        if (sizeof(R) == 4 || w == 0) {
-            // float: every warp adds the slots itself (no further barrier);
-            // double: warp 0 only (double adds are slow), then a broadcast
-            R z[K];
+        if (w < K) {
+            R z = lane < nr ? s_red[(buf * kClusterMaxCtas + lane) * kMaxRed + w] : R(0);
 #pragma unroll
-            for (int j = 0; j < K; ++j) z[j] = lane < nr ? s_red[(buf * kClusterMaxCtas + lane) * kMaxRed + j] : R(0);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                for (int j = 0; j < K; ++j) z[j] += __shfl_xor_sync(0xffffffffu, z[j], o);
-            }
-#pragma unroll
-            for (int j = 0; j < K; ++j) out[j] = z[j];
-            if (sizeof(R) != 4 && lane == 0) {
-#pragma unroll
-                for (int j = 0; j < K; ++j) s_tmp[j] = z[j];
-            }
+            for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+            if (lane == 0) s_tot[w] = z;
         }
-        if (sizeof(R) != 4) {
-            __syncthreads();
+        __syncthreads();
 #pragma unroll
-            for (int j = 0; j < K; ++j) out[j] = s_tmp[j];
-            __syncthreads();
-        }
+        for (int j = 0; j < K; ++j) out[j] = s_tot[j];
         buf ^= 1;
     }
 };
@@ -442,6 +427,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ T t_red[2 * kClusterMaxCtas * kMaxRed];
     __shared__ T t_tmp[kClusterWarps * kMaxRed];
+    __shared__ T t_tot[kMaxRed];
     NrrState* st = d.st;
     if (st->done || st->skip) return;   // the same decision in every CTA
     cg::cluster_group cl = cg::this_cluster();
@@ -504,7 +490,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     stamp();
     // warps that hold work: four threads per node in the SpMV and the updates
     const int active_warps = min((int)(bd >> 5), ((n1 - n0) * 4 + 31) / 32);
-    ClusterSum<T> red{t_red, t_tmp, 0, max(active_warps, 1)};
+    ClusterSum<T> red{t_red, t_tmp, t_tot, 0, max(active_warps, 1)};
     const T tol = d.pcg_tol;
     // four threads per node: in the SpMV each takes every fourth block of
     // the node's row for all three columns; in the CG updates thread s < 3
@@ -518,8 +504,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     T x[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, q[4] = {0, 0, 0, 0};
     const T* Mi = Mloc + kMStride * ln;
 
-    // r = B - K X^(k), z = M^-1 r; per-thread values go to the slot of its column
-    T acc9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, s9[9];
+    // r = B - K X^(k), z = M^-1 r; per-thread values of its column:
+    // r.z, r.r, B.B
+    T acc3[3] = {0, 0, 0}, s9[9];
     if (has) {
         T y[4] = {0, 0, 0, 0};
         for (int b = rb0; b < rb1; ++b) {
@@ -549,15 +536,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
             rz += r[a] * zz;
             rr += r[a] * r[a];
         }
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-            acc9[cc] = cc == c ? rz : T(0);
-            acc9[3 + cc] = cc == c ? rr : T(0);
-            acc9[6 + cc] = cc == c ? bb : T(0);
-        }
+        acc3[0] = rz;
+        acc3[1] = rr;
+        acc3[2] = bb;
     }
     stamp();
-    red.template run<9, T>(acc9, s9);
+    red.template run<3>(has, c, acc3, s9);
     stamp();
     // CG scalars: every thread holds the same reduced values
     T rzc[3] = {s9[0], s9[1], s9[2]};
@@ -570,7 +554,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     int it = 0;
     T beta_t = 0;
     while (!done && it < d.pcg_max) {
-        T a3[3] = {0, 0, 0}, s3[3];
+        T a1[1] = {0}, s3[3];
         // w = K z for the node: this thread's share of the row's blocks, all
         // three columns, with 16-byte loads of K rows (local) and z rows
         // (local or another CTA's shared memory)
@@ -625,15 +609,14 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
                 q[a] = (it == 0) ? w[a] : w[a] + beta_t * q[a];
                 pq += p[a] * q[a];
             }
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) a3[cc] = cc == c ? pq : T(0);
+            a1[0] = pq;
         }
         if (it < 8) stamp();
-        red.template run<3, T>(a3, s3);   // also: every CTA finished reading z
+        red.template run<1>(has, c, a1, s3);   // also: every CTA finished reading z
         if (it < 8) stamp();
         const T s3c = pick3(s3, c), rzcc = pick3(rzc, c);
         const T alpha_t = s3c != T(0) ? rzcc / s3c : T(0);
-        T a6[6] = {0, 0, 0, 0, 0, 0}, s6[6];
+        T a2[2] = {0, 0}, s6[6];
         if (has) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
@@ -648,14 +631,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
                 rz += r[a] * zz;
                 rr += r[a] * r[a];
             }
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                a6[cc] = cc == c ? rz : T(0);
-                a6[3 + cc] = cc == c ? rr : T(0);
-            }
+            a2[0] = rz;
+            a2[1] = rr;
         }
         if (it < 8) stamp();
-        red.template run<6, T>(a6, s6);   // also: the new z is visible to the cluster
+        red.template run<2>(has, c, a2, s6);   // also: the new z is visible to the cluster
         if (it < 8) stamp();
         ++it;
         beta_t = rzcc != T(0) ? pick3(s6, c) / rzcc : T(0);
