@@ -630,7 +630,9 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     }
     tm.lap("uploads");
     if (std::getenv("NRR_NN_STATS")) {
-        const size_t warps = (size_t)(P + 7) / 8 + 64;   // enough for any lanes-per-query
+        // the most warps a search launches: 8 lanes per query, 4 queries
+        // per warp, whole CTAs of 8 warps
+        const size_t warps = ((size_t)P + 31) / 32 * 8;
         unsigned long long* ns = nullptr;
         CK(dalloc(c, &ns, warps * 4));
         d.nn_stats = ns;
@@ -1419,7 +1421,7 @@ nrr_status nrr_get_search_stats(nrr_ctx* c, unsigned long long* out, int64_t max
     const int64_t nw = (c->P + per_warp - 1) / per_warp;
     if (n_warps) *n_warps = src ? nw : 0;
     if (!src || !out) return NRR_OK;
-    const int64_t n = std::min<int64_t>(nw, max_warps);
+    const int64_t n = std::min<int64_t>(std::min<int64_t>(nw, max_warps), (int64_t)c->nn_stats_n);
     CK(cudaMemcpyAsync(out, src, sizeof(unsigned long long) * 4 * (size_t)n, cudaMemcpyDefault, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return NRR_OK;
