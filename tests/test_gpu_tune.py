@@ -101,3 +101,33 @@ def test_batch_tune():
     infos = batch.solve(3000)
     assert all(i.done == 1 and i.status == 0 for i in infos)
     batch.close()
+
+
+@pytest.mark.parametrize("lpq", [8, 4, 1])
+def test_search_and_solve_counters(pair, lpq, monkeypatch):
+    """The opt-in per-warp search counters and the solve's phase stamps
+    cover every warp a search launches, for any lanes-per-query setting,
+    and leave the results unchanged."""
+    nrr = _nrr()
+    ref = nrr.Registration(pair.src, pair.tgt, **KW)
+    ref.set_launch_config(lpq, ref.launch_config().solve_ctas)
+    monkeypatch.setenv("NRR_NN_STATS", "1")
+    monkeypatch.setenv("NRR_SOLVE_STATS", "1")
+    reg = nrr.Registration(pair.src, pair.tgt, **KW)
+    reg.set_launch_config(lpq, reg.launch_config().solve_ctas)
+    for _ in range(3):
+        reg.step()
+        ref.step()
+    assert np.array_equal(reg.transforms(), ref.transforms())
+    s = nrr.nrr_get_search_stats(reg.ctx)
+    per_warp = 32 // lpq
+    assert s.shape == (-(-pair.P // per_warp), 4)
+    assert np.all(s[:, 0] > 0)                      # every warp ran and stamped its cycles
+    assert np.all(s[:, 2] >= s[:, 3])               # scanned leaves were staged first
+    assert s[:, 3].sum() > 0
+    if reg.launch_config().solve_ctas > 0:          # the cluster solve stamps its phases
+        t = nrr.nrr_get_solve_stats(reg.ctx)
+        n = int(t[63])
+        assert 2 <= n < 64 and np.all(np.diff(t[:n]) >= 0)
+    reg.close()
+    ref.close()
