@@ -350,7 +350,6 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
 // memory. Used when the node count and the K rows fit (chosen at creation).
 // ---------------------------------------------------------------------------
 constexpr int kClusterThreads = 768;
-constexpr int kSpmvChunk = 1;   // blocks per thread whose z rows are in flight together
 constexpr int kClusterWarps = kClusterThreads / 32;
 
 // Cluster-wide sums of K3 values per node and column: value j of column c
@@ -367,10 +366,59 @@ constexpr int kClusterWarps = kClusterThreads / 32;
 //     which every thread reads the totals.
 // One warp per total keeps the shuffle count of a reduction at about
 // (3 K3 x warps + 10 K): the shuffle unit is shared by the CTA's 24 warps.
-constexpr int kClusterMaxCtas = 16;
-// row stride (elements of T) of the preconditioner blocks in shared memory:
-// 20 rather than 16 puts the rows of 8 consecutive nodes in distinct banks
-constexpr int kMStride = 20;
+constexpr int kClusterMaxCtas = kNrrClusterMaxCtas;
+// the block-Jacobi inverses are symmetric: their upper triangles (10 values)
+// at a stride of 12 elements of T per node, which puts the float rows of 8
+// consecutive nodes in distinct banks
+constexpr int kMStride = 12;
+__host__ __device__ constexpr int sym4u(int a, int t) { return a == 0 ? t : a == 1 ? 3 + t : a == 2 ? 5 + t : 9; }
+// index of entry (a, t) of a symmetric 4x4 matrix in its packed upper triangle
+__host__ __device__ constexpr int sym4(int a, int t) {
+    return a > t ? sym4u(t, a) : sym4u(a, t);
+}
+
+// mbarrier and bulk-copy primitives (PTX) for the halo exchange
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ unsigned cluster_addr(const void* p, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+// bulk copy of `bytes` (a multiple of 16, 16-byte aligned ends) from this
+// CTA's shared memory to another CTA's, completing on that CTA's mbarrier
+__device__ __forceinline__ void bulk_push(unsigned dst, unsigned src, unsigned bytes, unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "r"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+// the halo copies of a CTA, precomputed: {destination, source, bytes,
+// destination mbarrier} towards CTA r-1, then the same towards CTA r+1
+// (bytes 0: no copy). The generic-proxy writes of the rows are made visible
+// to the bulk copies first.
+__device__ __forceinline__ void issue_halo(const unsigned* sp) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (sp[2]) bulk_push(sp[0], sp[1], sp[2], sp[3]);
+    if (sp[6]) bulk_push(sp[4], sp[5], sp[6], sp[7]);
+}
 
 template <typename R>
 struct ClusterSum {
@@ -379,8 +427,12 @@ struct ClusterSum {
     R* s_tot;   // [kMaxRed]: cluster totals
     int buf;
     int active_warps;   // warps whose threads may hold non-zero values
+    const unsigned* s_push;   // halo copies to issue (see issue_halo)
+    // push: lane 0 of the CTA's last warp (no part in the later steps) issues
+    // the halo copies right after the CTA barrier of step 1, when every
+    // thread's earlier shared-memory writes are complete
     template <int K3>
-    __device__ void run(bool has, int c, const R (&v)[K3], R (&out)[3 * K3]) {
+    __device__ __forceinline__ void run(bool has, int c, const R (&v)[K3], R (&out)[3 * K3], bool push = false) {
         constexpr int K = 3 * K3;
         static_assert(K <= kMaxRed && K <= kClusterWarps, "reduction size");
         cg::cluster_group cl = cg::this_cluster();
@@ -400,6 +452,7 @@ struct ClusterSum {
             }
         }
         __syncthreads();
+        if (push && threadIdx.x == blockDim.x - 32) issue_halo(s_push);
         const int nr = (int)cl.num_blocks();
         if (w < K) {
             R y = lane < active_warps ? s_tmp[lane * kMaxRed + w] : R(0);
@@ -422,15 +475,44 @@ struct ClusterSum {
     }
 };
 
+// Waits (every thread) for phase `parity` of the halo mbarrier, whose
+// arrival thread 0 arms with the bytes the CTA receives. Bounded: a missing
+// arrival is recorded in the state, not waited for forever (after a first
+// miss, later waits give up quickly).
+__device__ __forceinline__ void halo_wait(unsigned long long* bar, unsigned parity, unsigned bytes, int* bad,
+                                          NrrState* st) {
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, bytes);
+    if (mbar_try_wait(bar, parity)) return;
+    const long long limit = *(volatile int*)bad ? 100000LL : kSpinLimit;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit) {
+            atomicExch(&st->status, (int)NRR_E_TIMEOUT);
+            *(volatile int*)bad = 1;
+            return;
+        }
+    }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevProblem<T> d, int cap) {
+__global__ void __launch_bounds__(kClusterThreads, 1)
+    solve_cluster_kernel(DevProblem<T> d, int cap, NrrHaloWin win) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ T t_red[2 * kClusterMaxCtas * kMaxRed];
     __shared__ T t_tmp[kClusterWarps * kMaxRed];
     __shared__ T t_tot[kMaxRed];
+    __shared__ __align__(8) unsigned long long s_bar;   // halo arrivals
+    __shared__ int s_halo_bad;
+    __shared__ unsigned s_push[8];
     NrrState* st = d.st;
     if (st->done || st->skip) return;   // the same decision in every CTA
     cg::cluster_group cl = cg::this_cluster();
+    const int tid = threadIdx.x, bd = blockDim.x;
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        s_halo_bad = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     // no CTA touches another's shared memory before every CTA of the cluster
     // runs: arrive now, wait after the local setup
     asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
@@ -443,15 +525,27 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     const int N = d.N;
     const int per = (N + C - 1) / C;
     const int n0 = min(N, rank * per), n1 = min(N, n0 + per);
+    const int cnt = n1 - n0;
     const int b0 = d.bsr_ptr[n0];
     const int nbl = d.bsr_ptr[n1] - b0;
-    // shared layout (identical offsets in every CTA): K rows, z slice,
-    // preconditioner blocks, packed column (owner rank, local node)
+    const int hmax = win.hmax;
+    // this CTA's window, and the rows it pushes to CTA r-1 and CTA r+1
+    int hlo = 0, hhi = 0, h_dn = 0, h_up = 0;
+#pragma unroll
+    for (int k = 0; k < kClusterMaxCtas; ++k) {
+        if (k == rank) { hlo = win.lo[k]; hhi = win.hi[k]; }
+        if (k == rank - 1) h_dn = win.hi[k];
+        if (k == rank + 1) h_up = win.lo[k];
+    }
+    // shared layout (identical offsets in every CTA): K rows; the z window
+    // (hmax halo rows, the CTA's own rows, hmax halo rows); preconditioner
+    // blocks; per K block the window row of its column, or the owner rank
+    // and local node of a column outside the window (bit 15 set)
     T* Kloc = reinterpret_cast<T*>(smem);
-    T* zloc = Kloc + (size_t)cap * 16;
-    T* Mloc = zloc + (size_t)per * 12;
+    T* zwin = Kloc + (size_t)cap * 16;
+    T* zloc = zwin + (size_t)12 * hmax;
+    T* Mloc = zwin + (size_t)12 * (2 * hmax + per);
     unsigned short* colloc = reinterpret_cast<unsigned short*>(Mloc + (size_t)per * kMStride);
-    const int tid = threadIdx.x, bd = blockDim.x;
     {
         // the K rows of this CTA's nodes, as 16-byte vectors, vector-major
         using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
@@ -464,8 +558,14 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     }
     for (int k = tid; k < nbl; k += bd) {
         const int col = d.bsr_col[b0 + k];
-        const int owner = col / per;
-        colloc[k] = (unsigned short)((owner << 12) | (col - owner * per));
+        unsigned short code;
+        if (col >= n0 - hlo && col < n1 + hhi) {
+            code = (unsigned short)(hmax + col - n0);
+        } else {
+            const int owner = col / per;
+            code = (unsigned short)(0x8000u | ((unsigned)owner << 8) | (unsigned)(col - owner * per));
+        }
+        colloc[k] = code;
     }
     __syncthreads();
     for (int n = n0 + tid; n < n1; n += bd) {
@@ -482,28 +582,54 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
             for (int t = 0; t < 16; ++t) I[t] = 0;
             for (int t = 0; t < 4; ++t) I[5 * t] = A[5 * t] > T(0) ? T(1) / A[5 * t] : T(1);
         }
-        for (int t = 0; t < 16; ++t) Mloc[kMStride * (n - n0) + t] = I[t];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int t = a; t < 4; ++t) Mloc[kMStride * (n - n0) + sym4(a, t)] = I[4 * a + t];
     }
     __syncthreads();
 
     asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     stamp();
+    // halo exchange: after the CTA's new z rows are written (thread 0, after
+    // a CTA barrier) push the first hi[r-1] rows to CTA r-1 and the last
+    // lo[r+1] rows to CTA r+1; before each SpMV wait for the rows this CTA
+    // receives (phase k of its mbarrier carries the halo of the k-th z)
+    const unsigned row_bytes = 12u * (unsigned)sizeof(T);
+    const unsigned in_bytes = (unsigned)(hlo + hhi) * row_bytes;
+    const int cnt_prev = rank > 0 ? min(N, rank * per) - min(N, (rank - 1) * per) : 0;
+    unsigned long long* bar = &s_bar;
+    if (tid == 0) {
+        s_push[2] = s_push[6] = 0;
+        if (h_dn > 0) {
+            s_push[0] = cluster_addr(zwin + (size_t)12 * (hmax + cnt_prev), rank - 1);
+            s_push[1] = smem_u32(zloc);
+            s_push[2] = (unsigned)h_dn * row_bytes;
+            s_push[3] = cluster_addr(bar, rank - 1);
+        }
+        if (h_up > 0) {
+            s_push[4] = cluster_addr(zwin + (size_t)12 * (hmax - h_up), rank + 1);
+            s_push[5] = smem_u32(zloc + (size_t)12 * (cnt - h_up));
+            s_push[6] = (unsigned)h_up * row_bytes;
+            s_push[7] = cluster_addr(bar, rank + 1);
+        }
+    }
+    unsigned hphase = 0;
     // warps that hold work: four threads per node in the SpMV and the updates
-    const int active_warps = min((int)(bd >> 5), ((n1 - n0) * 4 + 31) / 32);
-    ClusterSum<T> red{t_red, t_tmp, t_tot, 0, max(active_warps, 1)};
+    const int active_warps = min((int)(bd >> 5), (cnt * 4 + 31) / 32);
+    ClusterSum<T> red{t_red, t_tmp, t_tot, 0, max(active_warps, 1), s_push};
     const T tol = d.pcg_tol;
     // four threads per node: in the SpMV each takes every fourth block of
     // the node's row for all three columns; in the CG updates thread s < 3
     // owns column c = s of the node
     const int s4 = tid & 3;
-    const bool node_ok = (tid >> 2) < (n1 - n0);
+    const bool node_ok = (tid >> 2) < cnt;
     const bool has = node_ok && s4 < 3;
     const int ln = node_ok ? tid >> 2 : 0;
     const int n = n0 + ln, c = s4 < 3 ? s4 : 0;
     const int rb0 = node_ok ? d.bsr_ptr[n] - b0 : 0, rb1 = node_ok ? d.bsr_ptr[n + 1] - b0 : 0;
     T x[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, q[4] = {0, 0, 0, 0};
     const T* Mi = Mloc + kMStride * ln;
-
     // r = B - K X^(k), z = M^-1 r; per-thread values of its column:
     // r.z, r.r, B.B
     T acc3[3] = {0, 0, 0}, s9[9];
@@ -521,7 +647,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
                 y[a] += k4[0] * v[0] + k4[1] * v[1] + k4[2] * v[2] + k4[3] * v[3];
             }
         }
-        T bb = 0, rz = 0, rr = 0;
+        T bb = 0;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const T bv = d.Bv[12 * n + 3 * a + c];
@@ -529,9 +655,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
             r[a] = bv - y[a];
             bb += bv * bv;
         }
+        T rz = 0, rr = 0;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const T zz = Mi[4 * a] * r[0] + Mi[4 * a + 1] * r[1] + Mi[4 * a + 2] * r[2] + Mi[4 * a + 3] * r[3];
+            // z = M^-1 r for the node's column, into the CTA's window rows
+            const T zz = Mi[sym4(a, 0)] * r[0] + Mi[sym4(a, 1)] * r[1] + Mi[sym4(a, 2)] * r[2] +
+                         Mi[sym4(a, 3)] * r[3];
             zloc[12 * ln + 3 * a + c] = zz;
             rz += r[a] * zz;
             rr += r[a] * r[a];
@@ -541,7 +670,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
         acc3[2] = bb;
     }
     stamp();
-    red.template run<3>(has, c, acc3, s9);
+    red.template run<3>(has, c, acc3, s9, true);   // pushes the halo of the first z
     stamp();
     // CG scalars: every thread holds the same reduced values
     T rzc[3] = {s9[0], s9[1], s9[2]};
@@ -555,40 +684,32 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
     T beta_t = 0;
     while (!done && it < d.pcg_max) {
         T a1[1] = {0}, s3[3];
+        halo_wait(bar, hphase & 1u, in_bytes, &s_halo_bad, st);
+        ++hphase;
         // w = K z for the node: this thread's share of the row's blocks, all
-        // three columns, with 16-byte loads of K rows (local) and z rows
-        // (local or another CTA's shared memory)
+        // three columns, with 16-byte loads of K rows and z rows (from the
+        // window in this CTA's shared memory, or from the owner's)
         T wv[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) wv[k] = 0;
-        for (int b = rb0 + s4; b < rb1; b += 4 * kSpmvChunk) {
-            T zr[kSpmvChunk][12];
+        for (int b = rb0 + s4; b < rb1; b += 4) {
+            const unsigned cw = colloc[b];
+            const T* zp = (cw & 0x8000u) ? cl.map_shared_rank(zloc, (int)((cw >> 8) & 15u)) + 12 * (cw & 0xffu)
+                                         : zwin + 12 * cw;
+            T zr[12];
 #pragma unroll
-            for (int u = 0; u < kSpmvChunk; ++u) {
-                if (b + 4 * u < rb1) {
-                    const unsigned cw = colloc[b + 4 * u];
-                    const T* zp = cl.map_shared_rank(zloc, (int)(cw >> 12)) + 12 * (cw & 0xfff);
-#pragma unroll
-                    for (int k = 0; k < 12; k += 4) {
-                        T t4[4];
-                        load4(zp + k, t4);
-                        zr[u][k] = t4[0]; zr[u][k + 1] = t4[1]; zr[u][k + 2] = t4[2]; zr[u][k + 3] = t4[3];
-                    }
-                }
+            for (int k = 0; k < 12; k += 4) {
+                T t4[4];
+                load4(zp + k, t4);
+                zr[k] = t4[0]; zr[k + 1] = t4[1]; zr[k + 2] = t4[2]; zr[k + 3] = t4[3];
             }
 #pragma unroll
-            for (int u = 0; u < kSpmvChunk; ++u) {
-                if (b + 4 * u < rb1) {
+            for (int a = 0; a < 4; ++a) {
+                T k4[4];
+                krow(Kloc, cap, b, a, k4);
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        T k4[4];
-                        krow(Kloc, cap, b + 4 * u, a, k4);
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc)
-                            wv[3 * a + cc] += k4[0] * zr[u][cc] + k4[1] * zr[u][3 + cc] + k4[2] * zr[u][6 + cc] +
-                                              k4[3] * zr[u][9 + cc];
-                    }
-                }
+                for (int cc = 0; cc < 3; ++cc)
+                    wv[3 * a + cc] += k4[0] * zr[cc] + k4[1] * zr[3 + cc] + k4[2] * zr[6 + cc] + k4[3] * zr[9 + cc];
             }
         }
         // the node's four partial results (lanes 4k .. 4k+3 of a warp)
@@ -624,9 +745,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
                 r[a] -= alpha_t * q[a];
             }
             T rz = 0, rr = 0;
-#pragma unroll
+    #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const T zz = Mi[4 * a] * r[0] + Mi[4 * a + 1] * r[1] + Mi[4 * a + 2] * r[2] + Mi[4 * a + 3] * r[3];
+                // z = M^-1 r for the node's column, into the CTA's window rows
+                const T zz = Mi[sym4(a, 0)] * r[0] + Mi[sym4(a, 1)] * r[1] + Mi[sym4(a, 2)] * r[2] +
+                             Mi[sym4(a, 3)] * r[3];
                 zloc[12 * ln + 3 * a + c] = zz;
                 rz += r[a] * zz;
                 rr += r[a] * r[a];
@@ -635,7 +758,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
             a2[1] = rr;
         }
         if (it < 8) stamp();
-        red.template run<2>(has, c, a2, s6);   // also: the new z is visible to the cluster
+        // also: the new z is visible to the cluster; its halo is pushed
+        red.template run<2>(has, c, a2, s6, true);
         if (it < 8) stamp();
         ++it;
         beta_t = rzcc != T(0) ? pick3(s6, c) / rzcc : T(0);
@@ -643,6 +767,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) solve_cluster_kernel(DevPr
         done = s6[3] <= tol2 * bbc[0] && s6[4] <= tol2 * bbc[1] && s6[5] <= tol2 * bbc[2];
         relmax2 = fmax(fmax(s6[3] / bbc[0], s6[4] / bbc[1]), s6[5] / bbc[2]);
     }
+    // the halo of the last z is in flight: receive it before any CTA leaves
+    halo_wait(bar, hphase & 1u, in_bytes, &s_halo_bad, st);
     if (has) {
 #pragma unroll
         for (int a = 0; a < 4; ++a) d.G[12 * n + 3 * a + c] = x[a];
@@ -689,9 +815,9 @@ template int nrr_solve_max_blocks_per_sm<float>();
 template int nrr_solve_max_blocks_per_sm<double>();
 
 template <typename T>
-size_t nrr_solve_cluster_smem(int cap, int per) {
-    return (size_t)cap * 16 * sizeof(T) + (size_t)per * 12 * sizeof(T) + (size_t)per * kMStride * sizeof(T) +
-           (size_t)cap * sizeof(unsigned short) + 16;
+size_t nrr_solve_cluster_smem(int cap, int per, int hmax) {
+    return (size_t)cap * 16 * sizeof(T) + (size_t)(per + 2 * hmax) * 12 * sizeof(T) +
+           (size_t)per * kMStride * sizeof(T) + (size_t)cap * sizeof(unsigned short) + 16;
 }
 
 // Prepares the cluster kernel for C CTAs with the given shared memory;
@@ -734,7 +860,8 @@ int nrr_solve_cluster_setup(int C, size_t smem, size_t optin) {
 }
 
 template <typename T>
-cudaError_t nrr_launch_solve_cluster(const DevProblem<T>& d, int C, int cap, size_t smem, cudaStream_t s) {
+cudaError_t nrr_launch_solve_cluster(const DevProblem<T>& d, int C, int cap, const NrrHaloWin& win, size_t smem,
+                                     cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(kClusterThreads);
@@ -747,16 +874,18 @@ cudaError_t nrr_launch_solve_cluster(const DevProblem<T>& d, int C, int cap, siz
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, solve_cluster_kernel<T>, d, cap);
+    return cudaLaunchKernelEx(&cfg, solve_cluster_kernel<T>, d, cap, win);
 }
 
 int nrr_solve_cluster_threads() { return kClusterThreads; }
 
-template size_t nrr_solve_cluster_smem<float>(int, int);
-template size_t nrr_solve_cluster_smem<double>(int, int);
+template size_t nrr_solve_cluster_smem<float>(int, int, int);
+template size_t nrr_solve_cluster_smem<double>(int, int, int);
 template int nrr_solve_cluster_setup<float>(int, size_t, size_t);
 template int nrr_solve_cluster_setup<double>(int, size_t, size_t);
 template size_t nrr_solve_cluster_static_smem<float>();
 template size_t nrr_solve_cluster_static_smem<double>();
-template cudaError_t nrr_launch_solve_cluster<float>(const DevProblem<float>&, int, int, size_t, cudaStream_t);
-template cudaError_t nrr_launch_solve_cluster<double>(const DevProblem<double>&, int, int, size_t, cudaStream_t);
+template cudaError_t nrr_launch_solve_cluster<float>(const DevProblem<float>&, int, int, const NrrHaloWin&, size_t,
+                                                     cudaStream_t);
+template cudaError_t nrr_launch_solve_cluster<double>(const DevProblem<double>&, int, int, const NrrHaloWin&, size_t,
+                                                      cudaStream_t);

@@ -21,13 +21,14 @@ template <typename T>
 int nrr_solve_max_blocks_per_sm();
 int nrr_solve_cluster_threads();
 template <typename T>
-size_t nrr_solve_cluster_smem(int cap, int per);
+size_t nrr_solve_cluster_smem(int cap, int per, int hmax);
 template <typename T>
 int nrr_solve_cluster_setup(int C, size_t smem, size_t optin);
 template <typename T>
 size_t nrr_solve_cluster_static_smem();
 template <typename T>
-cudaError_t nrr_launch_solve_cluster(const DevProblem<T>& d, int C, int cap, size_t smem, cudaStream_t s);
+cudaError_t nrr_launch_solve_cluster(const DevProblem<T>& d, int C, int cap, const NrrHaloWin& win, size_t smem,
+                                     cudaStream_t s);
 
 namespace {
 
@@ -82,6 +83,7 @@ struct nrr_ctx {
     size_t nn_stats_n = 0;             // per-warp search counters (debug, opt-in)
     int cl_C = 0, cl_cap = 0;          // cluster solve: CTAs per cluster, K blocks per CTA
     size_t cl_smem = 0;
+    NrrHaloWin cl_win{};               // cluster solve: halo windows
     double diag = 0.0;
     double nu_a0 = 0.0, nu_r0 = 0.0;   // first-stage parameters
     bool failed = false;
@@ -206,7 +208,7 @@ nrr_status push_state(nrr_ctx* c) {
 
 template <typename T>
 cudaError_t launch_solve_on(nrr_ctx* c, const DevProblem<T>& d) {
-    if (c->cl_C > 0) return nrr_launch_solve_cluster<T>(d, c->cl_C, c->cl_cap, c->cl_smem, c->stream);
+    if (c->cl_C > 0) return nrr_launch_solve_cluster<T>(d, c->cl_C, c->cl_cap, c->cl_win, c->cl_smem, c->stream);
     return nrr_launch_solve<T>(d, c->grid_solve, c->stream, c->coop);
 }
 
@@ -215,9 +217,12 @@ cudaError_t launch_solve(nrr_ctx* c) { return launch_solve_on<T>(c, prob<T>(c));
 
 // Whether the cluster solve with C CTAs can run: every CTA's K rows fit in
 // shared memory and one such cluster can be resident. Fills the launch
-// parameters (K blocks per CTA, dynamic shared memory).
+// parameters (K blocks per CTA, halo windows, dynamic shared memory). The
+// halo window of CTA r reaches from its lowest to its highest column
+// (clamped to the neighbouring CTAs' nodes and to what shared memory holds
+// beside the K rows); columns outside it are read from the owner CTA.
 template <typename T>
-bool cluster_fits(nrr_ctx* c, int C, int* cap_out, size_t* smem_out) {
+bool cluster_fits(nrr_ctx* c, int C, int* cap_out, NrrHaloWin* win_out, size_t* smem_out) {
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) {
         cudaGetLastError();
@@ -232,10 +237,41 @@ bool cluster_fits(nrr_ctx* c, int C, int* cap_out, size_t* smem_out) {
         const int n0 = std::min(N, r * per), n1 = std::min(N, n0 + per);
         cap = std::max(cap, c->bsr_ptr[(size_t)n1] - c->bsr_ptr[(size_t)n0]);
     }
-    const size_t smem = nrr_solve_cluster_smem<T>(cap, per);
-    if (smem + nrr_solve_cluster_static_smem<T>() > (size_t)optin) return false;
+    const size_t base = nrr_solve_cluster_smem<T>(cap, per, 0);
+    const size_t stat = nrr_solve_cluster_static_smem<T>();
+    if (base + stat > (size_t)optin) return false;
+    NrrHaloWin win{};
+    int want = 0;
+    for (int r = 0; r < C; ++r) {
+        const int n0 = std::min(N, r * per), n1 = std::min(N, n0 + per);
+        int lo = 0, hi = 0;
+        if (n1 > n0) {
+            const int* col = c->bsr_col.data();
+            const int cmin = *std::min_element(col + c->bsr_ptr[(size_t)n0], col + c->bsr_ptr[(size_t)n1]);
+            const int cmax = *std::max_element(col + c->bsr_ptr[(size_t)n0], col + c->bsr_ptr[(size_t)n1]);
+            const int prev = n0 - std::min(N, std::max(0, r - 1) * per);   // nodes of CTA r-1
+            const int next = std::min(N, n1 + per) - n1;                   // nodes of CTA r+1
+            lo = std::min(std::max(0, n0 - cmin), prev);
+            hi = std::min(std::max(0, cmax + 1 - n1), next);
+        }
+        win.lo[r] = (short)lo;
+        win.hi[r] = (short)hi;
+        want = std::max(want, std::max(lo, hi));
+    }
+    const size_t row2 = 2 * 12 * sizeof(T);   // one halo row on each side
+    const int room = (int)std::min<size_t>(((size_t)optin - base - stat) / row2, 4096);
+    win.hmax = std::min(want, room);
+    for (int r = 0; r < C; ++r) {
+        win.lo[r] = (short)std::min<int>(win.lo[r], win.hmax);
+        win.hi[r] = (short)std::min<int>(win.hi[r], win.hmax);
+    }
+    if (std::getenv("NRR_NO_HALO")) {
+        win = NrrHaloWin{};
+    }
+    const size_t smem = nrr_solve_cluster_smem<T>(cap, per, win.hmax);
     if (nrr_solve_cluster_setup<T>(C, smem, (size_t)optin) < 1) return false;
     *cap_out = cap;
+    *win_out = win;
     *smem_out = smem;
     return true;
 }
@@ -250,9 +286,11 @@ bool set_solver(nrr_ctx* c, int C) {
     }
     int cap = 0;
     size_t smem = 0;
-    if (!cluster_fits<T>(c, C, &cap, &smem)) return false;
+    NrrHaloWin win{};
+    if (!cluster_fits<T>(c, C, &cap, &win, &smem)) return false;
     c->cl_C = C;
     c->cl_cap = cap;
+    c->cl_win = win;
     c->cl_smem = smem;
     return true;
 }

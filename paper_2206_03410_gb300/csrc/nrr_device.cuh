@@ -23,6 +23,19 @@
 
 #include "nrr_internal.h"
 
+// Halo windows of the cluster solve (at most 16 CTAs): CTA r keeps, beside
+// its own z rows, copies of the z rows of the last lo[r] nodes of CTA r-1
+// and of the first hi[r] nodes of CTA r+1 (the nodes its K rows reference
+// there, at most hmax on each side), which those CTAs push to it with bulk
+// asynchronous copies each CG iteration. Columns outside the window are read
+// from the owner's shared memory.
+constexpr int kNrrClusterMaxCtas = 16;
+struct NrrHaloWin {
+    int hmax;
+    short lo[kNrrClusterMaxCtas];
+    short hi[kNrrClusterMaxCtas];
+};
+
 template <typename T>
 struct __align__(16) TPoint {
     T x, y, z;

@@ -131,3 +131,25 @@ def test_search_and_solve_counters(pair, lpq, monkeypatch):
         assert 2 <= n < 64 and np.all(np.diff(t[:n]) >= 0)
     reg.close()
     ref.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_cluster_halo_matches_remote_reads(prec, monkeypatch):
+    """The cluster solve reads neighbouring CTAs' z rows from halo copies
+    pushed into its own shared memory; with the halo off (every such row
+    read from the owner CTA) the products are summed in the same order, so
+    the two runs agree bit for bit."""
+    nrr = _nrr()
+    pair = synth.workload("sphere5k")
+    kw = dict(radius=0.15, aa_m=5, precision=prec)
+    out = []
+    for off in (False, True):
+        if off:
+            monkeypatch.setenv("NRR_NO_HALO", "1")
+        reg = nrr.Registration(pair.src, pair.tgt, **kw)
+        assert reg.launch_config().solve_ctas > 1
+        infos = [reg.step() for _ in range(4)]
+        out.append((reg.transforms(), [i.pcg_iters for i in infos]))
+        reg.close()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
