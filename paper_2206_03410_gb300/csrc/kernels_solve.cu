@@ -24,7 +24,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kMaxRed = 9;   // values per reduction (at most)
+constexpr int kMaxRed = 12;  // values per reduction (at most)
 constexpr long long kSpinLimit = 4000000000LL;   // clock64 cycles
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -628,71 +628,54 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     const int ln = node_ok ? tid >> 2 : 0;
     const int n = n0 + ln, c = s4 < 3 ? s4 : 0;
     const int rb0 = node_ok ? d.bsr_ptr[n] - b0 : 0, rb1 = node_ok ? d.bsr_ptr[n + 1] - b0 : 0;
-    T x[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, q[4] = {0, 0, 0, 0};
     const T* Mi = Mloc + kMStride * ln;
-    // r = B - K X^(k), z = M^-1 r; per-thread values of its column:
-    // r.z, r.r, B.B
-    T acc3[3] = {0, 0, 0}, s9[9];
-    if (has) {
-        T y[4] = {0, 0, 0, 0};
-        for (int b = rb0; b < rb1; ++b) {
-            const int k = d.bsr_col[b0 + b];
-            T v[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) v[t] = d.X[12 * k + 3 * t + c];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                T k4[4];
-                krow(Kloc, cap, b, a, k4);
-                y[a] += k4[0] * v[0] + k4[1] * v[1] + k4[2] * v[2] + k4[3] * v[3];
-            }
-        }
-        T bb = 0;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const T bv = d.Bv[12 * n + 3 * a + c];
-            x[a] = d.X[12 * n + 3 * a + c];
-            r[a] = bv - y[a];
-            bb += bv * bv;
-        }
-        T rz = 0, rr = 0;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            // z = M^-1 r for the node's column, into the CTA's window rows
-            const T zz = Mi[sym4(a, 0)] * r[0] + Mi[sym4(a, 1)] * r[1] + Mi[sym4(a, 2)] * r[2] +
-                         Mi[sym4(a, 3)] * r[3];
-            zloc[12 * ln + 3 * a + c] = zz;
-            rz += r[a] * zz;
-            rr += r[a] * r[a];
-        }
-        acc3[0] = rz;
-        acc3[1] = rr;
-        acc3[2] = bb;
+    // window rows of this CTA's own nodes
+    const unsigned own_lo = (unsigned)hmax, own_hi = (unsigned)(hmax + cnt);
+
+    // Preconditioned CG in the form of Chronopoulos and Gear (J. Comput.
+    // Appl. Math. 25, 1989), which has the iterates of PCG in exact
+    // arithmetic: with u = M^-1 r and w = K u,
+    //   gamma = r.u, delta = w.u, beta = gamma / gamma_old,
+    //   alpha = gamma / (delta - beta gamma / alpha_old),
+    //   p = u + beta p, s = w + beta s (= K p), x += alpha p, r -= alpha s.
+    // One cluster-wide reduction per iteration (gamma, delta, r.r of the
+    // three columns, after the SpMV). u reaches the neighbours by the halo
+    // copies, pushed as soon as it is written; the SpMV takes the columns of
+    // the CTA's own nodes first and waits for the halo before the others.
+    // Without full windows (some column read from its owner CTA) a cluster
+    // barrier publishes u before the SpMV.
+    T x[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, sv[4] = {0, 0, 0, 0};
+    T u[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
+    const bool full = win.full != 0;
+    const unsigned in_bytes_c = in_bytes;
+    // u = M^-1 r for the node's column, into the CTA's window rows; then the
+    // halo push and the SpMV w = K u (this thread's share of the row's
+    // blocks, all three columns, 16-byte loads of K and u rows; the node's
+    // four partial results added by shuffles)
+#define NRR_CG_PRECONDITION()                                                                               \
+    if (has) {                                                                                              \
+        _Pragma("unroll") for (int a = 0; a < 4; ++a) {                                                     \
+            u[a] = Mi[sym4(a, 0)] * r[0] + Mi[sym4(a, 1)] * r[1] + Mi[sym4(a, 2)] * r[2] + Mi[sym4(a, 3)] * r[3]; \
+            zloc[12 * ln + 3 * a + c] = u[a];                                                               \
+        }                                                                                                   \
     }
-    stamp();
-    red.template run<3>(has, c, acc3, s9, true);   // pushes the halo of the first z
-    stamp();
-    // CG scalars: every thread holds the same reduced values
-    T rzc[3] = {s9[0], s9[1], s9[2]};
-    const T bbc[3] = {s9[6] > T(0) ? s9[6] : T(1e-30), s9[7] > T(0) ? s9[7] : T(1e-30),
-                      s9[8] > T(0) ? s9[8] : T(1e-30)};
-    const T tol2 = tol * tol;
-    // converged when every column has |r|^2 <= tol^2 |B|^2
-    bool done = s9[3] <= tol2 * bbc[0] && s9[4] <= tol2 * bbc[1] && s9[5] <= tol2 * bbc[2];
-    T relmax2 = fmax(fmax(s9[3] / bbc[0], s9[4] / bbc[1]), s9[5] / bbc[2]);
-    int it = 0;
-    T beta_t = 0;
-    while (!done && it < d.pcg_max) {
-        T a1[1] = {0}, s3[3];
-        halo_wait(bar, hphase & 1u, in_bytes, &s_halo_bad, st);
-        ++hphase;
-        // w = K z for the node: this thread's share of the row's blocks, all
-        // three columns, with 16-byte loads of K rows and z rows (from the
-        // window in this CTA's shared memory, or from the owner's)
-        T wv[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) wv[k] = 0;
-        for (int b = rb0 + s4; b < rb1; b += 4) {
+    // the row's blocks are sorted by column: those of the CTA's own nodes
+    // form one range [ob0, ob1) of it
+    int ob0 = rb0, ob1 = rb0;
+    {
+        int b = rb0;
+        while (b < rb1 && !(colloc[b] >= own_lo && colloc[b] < own_hi)) ++b;
+        ob0 = b;
+        while (b < rb1 && colloc[b] >= own_lo && colloc[b] < own_hi) ++b;
+        ob1 = b;
+    }
+    // this thread's blocks (every fourth from rb0 + s4) in [from, to)
+    auto first_at = [&](int from) {
+        const int b = rb0 + s4;
+        return b >= from ? b : b + ((from - b + 3) >> 2) * 4;
+    };
+    auto spmv_range = [&](int from, int to, T (&wv)[12]) {
+        for (int b = first_at(from); b < to; b += 4) {
             const unsigned cw = colloc[b];
             const T* zp = (cw & 0x8000u) ? cl.map_shared_rank(zloc, (int)((cw >> 8) & 15u)) + 12 * (cw & 0xffu)
                                          : zwin + 12 * cw;
@@ -712,63 +695,115 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                     wv[3 * a + cc] += k4[0] * zr[cc] + k4[1] * zr[3 + cc] + k4[2] * zr[6 + cc] + k4[3] * zr[9 + cc];
             }
         }
-        // the node's four partial results (lanes 4k .. 4k+3 of a warp)
+    };
+#define NRR_CG_SPMV()                                                                  \
+    {                                                                                  \
+        __syncthreads(); /* every thread's u rows are written */                     \
+        if (tid == bd - 32) issue_halo(s_push);                                        \
+        if (!full) cl.sync(); /* u rows read from their owners */                      \
+        T wv[12];                                                                      \
+        _Pragma("unroll") for (int k = 0; k < 12; ++k) wv[k] = 0;                    \
+        spmv_range(ob0, ob1, wv);                                                      \
+        halo_wait(bar, hphase & 1u, in_bytes_c, &s_halo_bad, st);                      \
+        ++hphase;                                                                      \
+        spmv_range(rb0, ob0, wv);                                                      \
+        spmv_range(ob1, rb1, wv);                                                      \
+        _Pragma("unroll") for (int k = 0; k < 12; ++k) {                               \
+            wv[k] += __shfl_xor_sync(0xffffffffu, wv[k], 1);                           \
+            wv[k] += __shfl_xor_sync(0xffffffffu, wv[k], 2);                           \
+        }                                                                              \
+        _Pragma("unroll") for (int a = 0; a < 4; ++a) w[a] = wv[3 * a + c];            \
+    }
+
+    // start: r = B - K X^(k), u = M^-1 r, w = K u
+    T bb = 0;
+    if (has) {
+        T y[4] = {0, 0, 0, 0};
+        for (int b = rb0; b < rb1; ++b) {
+            const int k = d.bsr_col[b0 + b];
+            T v[4];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            wv[k] += __shfl_xor_sync(0xffffffffu, wv[k], 1);
-            wv[k] += __shfl_xor_sync(0xffffffffu, wv[k], 2);
+            for (int t = 0; t < 4; ++t) v[t] = d.X[12 * k + 3 * t + c];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                T k4[4];
+                krow(Kloc, cap, b, a, k4);
+                y[a] += k4[0] * v[0] + k4[1] * v[1] + k4[2] * v[2] + k4[3] * v[3];
+            }
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const T bv = d.Bv[12 * n + 3 * a + c];
+            x[a] = d.X[12 * n + 3 * a + c];
+            r[a] = bv - y[a];
+            bb += bv * bv;
+        }
+    }
+    NRR_CG_PRECONDITION()
+    stamp();
+    NRR_CG_SPMV()
+    // per column: r.u, w.u, r.r, B.B
+    T acc4[4] = {0, 0, 0, 0}, s12[12];
+    if (has) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            acc4[0] += r[a] * u[a];
+            acc4[1] += w[a] * u[a];
+            acc4[2] += r[a] * r[a];
+        }
+        acc4[3] = bb;
+    }
+    stamp();
+    red.template run<4>(has, c, acc4, s12);
+    stamp();
+    const T bbc[3] = {s12[9] > T(0) ? s12[9] : T(1e-30), s12[10] > T(0) ? s12[10] : T(1e-30),
+                      s12[11] > T(0) ? s12[11] : T(1e-30)};
+    const T tol2 = tol * tol;
+    // converged when every column has |r|^2 <= tol^2 |B|^2
+    bool done = s12[6] <= tol2 * bbc[0] && s12[7] <= tol2 * bbc[1] && s12[8] <= tol2 * bbc[2];
+    T relmax2 = fmax(fmax(s12[6] / bbc[0], s12[7] / bbc[1]), s12[8] / bbc[2]);
+    // this thread's column: gamma, alpha, beta
+    T gam = pick3(s12, c);
+    T dl0 = pick3(s12 + 3, c);
+    T alph = dl0 != T(0) ? gam / dl0 : T(0), beta = 0;
+    int it = 0;
+    while (!done && it < d.pcg_max) {
         if (has) {
-            T w[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) w[a] = wv[3 * a + c];
-            T pq = 0;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const T zz = zloc[12 * ln + 3 * a + c];
-                p[a] = (it == 0) ? zz : zz + beta_t * p[a];
-                q[a] = (it == 0) ? w[a] : w[a] + beta_t * q[a];
-                pq += p[a] * q[a];
+                p[a] = u[a] + beta * p[a];
+                sv[a] = w[a] + beta * sv[a];
+                x[a] += alph * p[a];
+                r[a] -= alph * sv[a];
             }
-            a1[0] = pq;
         }
+        NRR_CG_PRECONDITION()
         if (it < 8) stamp();
-        red.template run<1>(has, c, a1, s3);   // also: every CTA finished reading z
-        if (it < 8) stamp();
-        const T s3c = pick3(s3, c), rzcc = pick3(rzc, c);
-        const T alpha_t = s3c != T(0) ? rzcc / s3c : T(0);
-        T a2[2] = {0, 0}, s6[6];
+        NRR_CG_SPMV()
+        T a3[3] = {0, 0, 0}, s9[9];
         if (has) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                x[a] += alpha_t * p[a];
-                r[a] -= alpha_t * q[a];
+                a3[0] += r[a] * u[a];
+                a3[1] += w[a] * u[a];
+                a3[2] += r[a] * r[a];
             }
-            T rz = 0, rr = 0;
-    #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                // z = M^-1 r for the node's column, into the CTA's window rows
-                const T zz = Mi[sym4(a, 0)] * r[0] + Mi[sym4(a, 1)] * r[1] + Mi[sym4(a, 2)] * r[2] +
-                             Mi[sym4(a, 3)] * r[3];
-                zloc[12 * ln + 3 * a + c] = zz;
-                rz += r[a] * zz;
-                rr += r[a] * r[a];
-            }
-            a2[0] = rz;
-            a2[1] = rr;
         }
         if (it < 8) stamp();
-        // also: the new z is visible to the cluster; its halo is pushed
-        red.template run<2>(has, c, a2, s6, true);
+        red.template run<3>(has, c, a3, s9);   // also: every CTA finished its SpMV
         if (it < 8) stamp();
         ++it;
-        beta_t = rzcc != T(0) ? pick3(s6, c) / rzcc : T(0);
-        rzc[0] = s6[0]; rzc[1] = s6[1]; rzc[2] = s6[2];
-        done = s6[3] <= tol2 * bbc[0] && s6[4] <= tol2 * bbc[1] && s6[5] <= tol2 * bbc[2];
-        relmax2 = fmax(fmax(s6[3] / bbc[0], s6[4] / bbc[1]), s6[5] / bbc[2]);
+        done = s9[6] <= tol2 * bbc[0] && s9[7] <= tol2 * bbc[1] && s9[8] <= tol2 * bbc[2];
+        relmax2 = fmax(fmax(s9[6] / bbc[0], s9[7] / bbc[1]), s9[8] / bbc[2]);
+        const T gn = pick3(s9, c), dn = pick3(s9 + 3, c);
+        const T be = gam != T(0) ? gn / gam : T(0);
+        const T den = dn - (alph != T(0) ? be * gn / alph : T(0));
+        beta = be;
+        alph = den > T(0) ? gn / den : T(0);
+        gam = gn;
     }
-    // the halo of the last z is in flight: receive it before any CTA leaves
-    halo_wait(bar, hphase & 1u, in_bytes, &s_halo_bad, st);
+#undef NRR_CG_SPMV
+#undef NRR_CG_PRECONDITION
     if (has) {
 #pragma unroll
         for (int a = 0; a < 4; ++a) d.G[12 * n + 3 * a + c] = x[a];

@@ -261,6 +261,16 @@ bool cluster_fits(nrr_ctx* c, int C, int* cap_out, NrrHaloWin* win_out, size_t* 
     const size_t row2 = 2 * 12 * sizeof(T);   // one halo row on each side
     const int room = (int)std::min<size_t>(((size_t)optin - base - stat) / row2, 4096);
     win.hmax = std::min(want, room);
+    // full: no CTA reads a column outside its window (the windows reach
+    // every referenced column and no column lies beyond a neighbour)
+    win.full = want <= room ? 1 : 0;
+    for (int r = 0; r < C && win.full; ++r) {
+        const int n0 = std::min(N, r * per), n1 = std::min(N, n0 + per);
+        for (int b = c->bsr_ptr[(size_t)n0]; b < c->bsr_ptr[(size_t)n1]; ++b) {
+            const int col = c->bsr_col[(size_t)b];
+            if (col < n0 - win.lo[r] || col >= n1 + win.hi[r]) { win.full = 0; break; }
+        }
+    }
     for (int r = 0; r < C; ++r) {
         win.lo[r] = (short)std::min<int>(win.lo[r], win.hmax);
         win.hi[r] = (short)std::min<int>(win.hi[r], win.hmax);

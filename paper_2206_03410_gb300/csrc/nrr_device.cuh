@@ -32,6 +32,7 @@
 constexpr int kNrrClusterMaxCtas = 16;
 struct NrrHaloWin {
     int hmax;
+    int full;   // 1: every column of every CTA lies in its window
     short lo[kNrrClusterMaxCtas];
     short hi[kNrrClusterMaxCtas];
 };
