@@ -344,10 +344,12 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
 // ---------------------------------------------------------------------------
 // Cluster variant: one thread-block cluster of C CTAs (C <= 16) solves the
 // system. Each CTA keeps the K rows of its nodes, their block-Jacobi
-// inverses and its slice of z in shared memory; the SpMV reads neighbouring
-// z values through distributed shared memory, and reductions and barriers
-// use the hardware cluster barrier, so an iteration touches no global
-// memory. Used when the node count and the K rows fit (chosen at creation).
+// inverses and a window of the preconditioned residual (its own rows and
+// copies of the neighbouring CTAs' rows its K rows reference, pushed by bulk
+// asynchronous copies) in shared memory; the single reduction of each
+// iteration uses the hardware cluster barrier, so an iteration touches no
+// global memory. Used when the node count and the K rows fit (chosen at
+// creation).
 // ---------------------------------------------------------------------------
 constexpr int kClusterThreads = 768;
 constexpr int kClusterWarps = kClusterThreads / 32;
