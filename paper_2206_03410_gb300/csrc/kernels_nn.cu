@@ -25,11 +25,12 @@ constexpr int kThreads = kWarps * 32;
 template <typename T>
 struct Batch { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
 
-// 16-byte global->shared asynchronous copy (cp.async, L1-allocating) and
-// the wait for all of a thread's outstanding copies.
+// 16-byte global->shared asynchronous copy (cp.async, cached in L2 only:
+// a staged point is read once, from shared memory, and L1 is kept for the
+// tile and leaf boxes) and the wait for all of a thread's outstanding copies.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
