@@ -430,6 +430,7 @@ struct ClusterSum {
     int buf;
     int active_warps;   // warps whose threads may hold non-zero values
     const unsigned* s_push;   // halo copies to issue (see issue_halo)
+    const int* s_bad;         // set: this CTA failed; total 0 becomes NaN
     // push: lane 0 of the CTA's last warp (no part in the later steps) issues
     // the halo copies right after the CTA barrier of step 1, when every
     // thread's earlier shared-memory writes are complete
@@ -458,6 +459,7 @@ struct ClusterSum {
         const int nr = (int)cl.num_blocks();
         if (w < K) {
             R y = lane < active_warps ? s_tmp[lane * kMaxRed + w] : R(0);
+            if (w == 0 && s_bad != nullptr && *(volatile const int*)s_bad) y = (R)__int_as_float(0x7fc00000);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
             if (lane < nr)
@@ -478,22 +480,26 @@ struct ClusterSum {
 };
 
 // Waits (every thread) for phase `parity` of the halo mbarrier, whose
-// arrival thread 0 arms with the bytes the CTA receives. Bounded: a missing
-// arrival is recorded in the state, not waited for forever (after a first
-// miss, later waits give up quickly).
-__device__ __forceinline__ void halo_wait(unsigned long long* bar, unsigned parity, unsigned bytes, int* bad,
+// arrival thread 0 arms with the bytes the CTA receives. Bounded: if the
+// rows have not all arrived after about two seconds, the thread records
+// NRR_E_TIMEOUT in the state and marks the CTA failed (*bad); the next
+// cluster reduction then carries NaN, so every CTA leaves the solve at the
+// same point (the failed CTA arms and waits on the mbarrier no more: the
+// solve ends at that reduction, before the next wait). Returns whether the
+// rows arrived.
+__device__ __forceinline__ bool halo_wait(unsigned long long* bar, unsigned parity, unsigned bytes, int* bad,
                                           NrrState* st) {
     if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, bytes);
-    if (mbar_try_wait(bar, parity)) return;
-    const long long limit = *(volatile int*)bad ? 100000LL : kSpinLimit;
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > limit) {
+        if (clock64() - t0 > kSpinLimit) {
             atomicExch(&st->status, (int)NRR_E_TIMEOUT);
             *(volatile int*)bad = 1;
-            return;
+            return false;
         }
     }
+    return true;
 }
 
 template <typename T>
@@ -619,7 +625,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     unsigned hphase = 0;
     // warps that hold work: four threads per node in the SpMV and the updates
     const int active_warps = min((int)(bd >> 5), (cnt * 4 + 31) / 32);
-    ClusterSum<T> red{t_red, t_tmp, t_tot, 0, max(active_warps, 1), s_push};
+    ClusterSum<T> red{t_red, t_tmp, t_tot, 0, max(active_warps, 1), s_push, &s_halo_bad};
     const T tol = d.pcg_tol;
     // four threads per node: in the SpMV each takes every fourth block of
     // the node's row for all three columns; in the CG updates thread s < 3
@@ -649,6 +655,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     T x[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, sv[4] = {0, 0, 0, 0};
     T u[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
     const bool full = win.full != 0;
+    // failure-detection test knob (host side): CTA 1 does not push the halo
+    // of the first u, so its neighbours' bounded waits run out
+    const bool skip_push = d.fault_halo != 0 && rank == 1;
+
     const unsigned in_bytes_c = in_bytes;
     // u = M^-1 r for the node's column, into the CTA's window rows; then the
     // halo push and the SpMV w = K u (this thread's share of the row's
@@ -701,7 +711,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
 #define NRR_CG_SPMV()                                                                  \
     {                                                                                  \
         __syncthreads(); /* every thread's u rows are written */                     \
-        if (tid == bd - 32) issue_halo(s_push);                                        \
+        if (tid == bd - 32 && !(skip_push && hphase == 0)) issue_halo(s_push);         \
         if (!full) cl.sync(); /* u rows read from their owners */                      \
         T wv[12];                                                                      \
         _Pragma("unroll") for (int k = 0; k < 12; ++k) wv[k] = 0;                    \
@@ -762,7 +772,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                       s12[11] > T(0) ? s12[11] : T(1e-30)};
     const T tol2 = tol * tol;
     // converged when every column has |r|^2 <= tol^2 |B|^2
-    bool done = s12[6] <= tol2 * bbc[0] && s12[7] <= tol2 * bbc[1] && s12[8] <= tol2 * bbc[2];
+    // a failed CTA (NaN in the sum of column 0) ends the solve everywhere
+    const bool failed0 = s12[0] != s12[0];
+    bool done = failed0 || (s12[6] <= tol2 * bbc[0] && s12[7] <= tol2 * bbc[1] && s12[8] <= tol2 * bbc[2]);
     T relmax2 = fmax(fmax(s12[6] / bbc[0], s12[7] / bbc[1]), s12[8] / bbc[2]);
     // this thread's column: gamma, alpha, beta
     T gam = pick3(s12, c);
@@ -795,6 +807,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         red.template run<3>(has, c, a3, s9);   // also: every CTA finished its SpMV
         if (it < 8) stamp();
         ++it;
+        if (s9[0] != s9[0]) break;   // a CTA failed (or the recurrence broke down)
         done = s9[6] <= tol2 * bbc[0] && s9[7] <= tol2 * bbc[1] && s9[8] <= tol2 * bbc[2];
         relmax2 = fmax(fmax(s9[6] / bbc[0], s9[7] / bbc[1]), s9[8] / bbc[2]);
         const T gn = pick3(s9, c), dn = pick3(s9 + 3, c);
@@ -806,6 +819,13 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     }
 #undef NRR_CG_SPMV
 #undef NRR_CG_PRECONDITION
+    if (s_halo_bad) {
+        // rows pushed to this CTA may still be in flight: let them land (a
+        // bounded pause) before the cluster's CTAs leave
+        const long long t0 = clock64();
+        while (clock64() - t0 < 200000LL) {
+        }
+    }
     if (has) {
 #pragma unroll
         for (int a = 0; a < 4; ++a) d.G[12 * n + 3 * a + c] = x[a];

@@ -671,6 +671,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     d.nn_stats = nullptr;
     d.solve_stats = nullptr;
     d.fault_barrier = std::getenv("NRR_FAULT_BARRIER") ? 1 : 0;
+    d.fault_halo = std::getenv("NRR_FAULT_HALO") ? 1 : 0;
     if (std::getenv("NRR_SOLVE_STATS")) {
         long long* ss = nullptr;
         CK(dalloc(c, &ss, 64));

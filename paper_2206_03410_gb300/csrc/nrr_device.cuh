@@ -114,6 +114,7 @@ struct DevProblem {
     // failure-detection test knob (NRR_FAULT_BARRIER, read on the host at
     // creation): the grid-wide solve's CTA 0 skips its first barrier arrival
     int fault_barrier;
+    int fault_halo;      // test knob: CTA 1 of the cluster solve skips its first halo push
 };
 
 #define NRR_PARTIAL_STRIDE 32

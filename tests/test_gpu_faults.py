@@ -42,3 +42,29 @@ def test_bounded_barrier_wait_reports_timeout(monkeypatch):
     info = ok.solve(3000)
     assert info.done == 1 and info.status == 0
     ok.close()
+
+
+def test_bounded_halo_wait_reports_timeout(monkeypatch):
+    """The cluster solve's halo wait is bounded too. With the host-side knob
+    NRR_FAULT_HALO (read when a context is created), CTA 1 of the cluster
+    does not push the halo rows of the first preconditioned residual; its
+    neighbours' mbarrier waits run out after about two seconds, they record
+    NRR_E_TIMEOUT and add NaN to the next cluster reduction, so every CTA
+    leaves the solve at the same point and the kernel returns."""
+    from paper_2206_03410_gb300 import nrr
+    nrr.load()
+    pair = synth.workload("sphere5k")
+    kw = dict(radius=0.15, aa_m=5, precision="mixed")
+    monkeypatch.setenv("NRR_FAULT_HALO", "1")
+    reg = nrr.Registration(pair.src, pair.tgt, **kw)
+    monkeypatch.delenv("NRR_FAULT_HALO")
+    assert reg.launch_config().solve_ctas > 2      # CTA 1 has neighbours to push to
+    with pytest.raises(nrr.NrrError) as e:
+        reg.step()
+    assert e.value.code == nrr.NRR_E_TIMEOUT
+    reg.close()
+    torch.cuda.synchronize()
+    ok = nrr.Registration(pair.src, pair.tgt, **kw)
+    info = ok.solve(3000)
+    assert info.done == 1 and info.status == 0
+    ok.close()
