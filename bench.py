@@ -365,10 +365,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms = np.zeros(len(nrr.KERNELS))
     ks0 = reg.info()
+    pcg_sum = 0   # CG iterations of the timed solve launches (0 for a pass that did not solve)
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(float(k))
         ms += reg.time_kernels(1)
+        inf = reg.info()
+        if inf.solved:
+            pcg_sum += int(inf.pcg_iters)
     ks1 = reg.info()
     kt_passes = max(ks1.n_passes - ks0.n_passes, 1)
     solves_k = max(ks1.n_solves - ks0.n_solves, 1)
@@ -386,10 +390,9 @@ def run_ours(args):
         # contributions per block list: sum over points of |I(v_i)|^2
         k_i = (g.nidx >= 0).sum(axis=1)
         n_ent = int(np.sum(k_i * k_i))
-        avg_pcg = None
-        pcg_hist = []
-        info_now = reg.info()
-        avg_pcg = info_now.pcg_iters
+        # CG iterations per solve launch, over the launches whose durations
+        # make per_launch_ms (the algorithmic bytes scale with them)
+        avg_pcg = pcg_sum / max(args.steps, 1)
         ab = algorithmic_bytes(reg.P, reg.T, reg.N, nblk, nnz, avg_pcg, n_ent)
         peaks = {}
         try:
@@ -409,8 +412,16 @@ def run_ours(args):
                     "share": {n: round(float(v / ms.sum()), 4) for n, v in zip(names, ms)},
                     "launch_ms_note": "steps timed one after the other; in the pass graph xterm_kernel "
                                       "runs beside nn_kernel"}
+        # the solve is latency-bound: time per CG iteration and the
+        # cluster-wide synchronisations each iteration needs
+        cl_ctas = reg.launch_config().solve_ctas
+        solve_ms = float(per_launch_ms[names.index("solve_kernel")])
+        pcg = {"cg_iters_per_launch": round(avg_pcg, 2),
+               "us_per_cg_iter": round(solve_ms * 1e3 / avg_pcg, 3) if avg_pcg > 0 else None,
+               "syncs_per_cg_iter": 1 if cl_ctas > 0 else 2,
+               "solver": f"cluster of {cl_ctas} CTAs" if cl_ctas > 0 else "grid-wide"}
         result.update(dict(roofline=roofline, P=reg.P, T=reg.T, N=reg.N, n_edges=reg.n_edges,
-                           last_pcg_iters=avg_pcg, clocks=clk, launch=launch,
+                           pcg=pcg, clocks=clk, launch=launch,
                            launches_per_pass=reg.launch_config().launches_per_pass))
 
         # ---- time-to-converge: mixed vs FP64, same energy -----------------
@@ -544,6 +555,7 @@ def main():
                    "l2": "flushed before every timed pass (256 MiB write); inputs L2-resident otherwise",
                    "iters_timed": res["iters"], "passes_timed": res["passes"]},
         "roofline": res["roofline"],
+        "pcg": res["pcg"],
         "clocks": res["clocks"],
         "gpu_launches": res["launches_per_pass"] * args.steps,
         "e2e": res.get("e2e"),
