@@ -429,13 +429,9 @@ struct ClusterSum {
     R* s_tot;   // [kMaxRed]: cluster totals
     int buf;
     int active_warps;   // warps whose threads may hold non-zero values
-    const unsigned* s_push;   // halo copies to issue (see issue_halo)
-    const int* s_bad;         // set: this CTA failed; total 0 becomes NaN
-    // push: lane 0 of the CTA's last warp (no part in the later steps) issues
-    // the halo copies right after the CTA barrier of step 1, when every
-    // thread's earlier shared-memory writes are complete
+    const int* s_bad;   // set: this CTA failed; total 0 becomes NaN
     template <int K3>
-    __device__ __forceinline__ void run(bool has, int c, const R (&v)[K3], R (&out)[3 * K3], bool push = false) {
+    __device__ __forceinline__ void run(bool has, int c, const R (&v)[K3], R (&out)[3 * K3]) {
         constexpr int K = 3 * K3;
         static_assert(K <= kMaxRed && K <= kClusterWarps, "reduction size");
         cg::cluster_group cl = cg::this_cluster();
@@ -455,7 +451,6 @@ struct ClusterSum {
             }
         }
         __syncthreads();
-        if (push && threadIdx.x == blockDim.x - 32) issue_halo(s_push);
         const int nr = (int)cl.num_blocks();
         if (w < K) {
             R y = lane < active_warps ? s_tmp[lane * kMaxRed + w] : R(0);
@@ -625,7 +620,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     unsigned hphase = 0;
     // warps that hold work: four threads per node in the SpMV and the updates
     const int active_warps = min((int)(bd >> 5), (cnt * 4 + 31) / 32);
-    ClusterSum<T> red{t_red, t_tmp, t_tot, 0, max(active_warps, 1), s_push, &s_halo_bad};
+    ClusterSum<T> red{t_red, t_tmp, t_tot, 0, max(active_warps, 1), &s_halo_bad};
     const T tol = d.pcg_tol;
     // four threads per node: in the SpMV each takes every fourth block of
     // the node's row for all three columns; in the CG updates thread s < 3
@@ -659,7 +654,6 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     // of the first u, so its neighbours' bounded waits run out
     const bool skip_push = d.fault_halo != 0 && rank == 1;
 
-    const unsigned in_bytes_c = in_bytes;
     // u = M^-1 r for the node's column, into the CTA's window rows; then the
     // halo push and the SpMV w = K u (this thread's share of the row's
     // blocks, all three columns, 16-byte loads of K and u rows; the node's
@@ -716,7 +710,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         T wv[12];                                                                      \
         _Pragma("unroll") for (int k = 0; k < 12; ++k) wv[k] = 0;                    \
         spmv_range(ob0, ob1, wv);                                                      \
-        halo_wait(bar, hphase & 1u, in_bytes_c, &s_halo_bad, st);                      \
+        halo_wait(bar, hphase & 1u, in_bytes, &s_halo_bad, st);                        \
         ++hphase;                                                                      \
         spmv_range(rb0, ob0, wv);                                                      \
         spmv_range(ob1, rb1, wv);                                                      \
