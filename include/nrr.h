@@ -288,6 +288,26 @@ nrr_status nrr_get_sizes(nrr_ctx* ctx, int64_t* P, int64_t* T, int64_t* N,
 nrr_status nrr_get_graph(nrr_ctx* ctx, int32_t* node_src, int32_t* nidx,
                          double* w, int32_t* edges, double* r, double* lbar);
 
+/* The deformation graph alone, built on the host without a GPU: the same
+ * construction nrr_create performs (Algorithm 1 with Euclidean distances,
+ * Sec. 3.1; the weights of Eq. (weight_data) and r_ij of Sec. 3.2).
+ * nrr_graph_build: src_xyz [P][3] host float32 source points (copied),
+ * radius R (> 0; <= 0: 5 lbar with lbar the mean distance of each point to
+ * its 6 nearest others), max_influence 1..8 (<= 0: 8). Errors:
+ * NRR_E_INVALID (NULL pointer, P < 1, non-finite coordinate or radius,
+ * max_influence > 8), NRR_E_OOM. nrr_graph_sizes: N, n_edges (undirected),
+ * max_influence and the radius used. nrr_graph_get: the arrays of
+ * nrr_get_graph (same layouts; host buffers, any pointer may be NULL; lbar
+ * is always computed here). nrr_graph_destroy accepts NULL. */
+typedef struct nrr_graph nrr_graph;
+nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, double radius,
+                           int max_influence);
+nrr_status nrr_graph_sizes(const nrr_graph* g, int64_t* N, int64_t* n_edges, int32_t* max_influence,
+                           double* radius);
+nrr_status nrr_graph_get(const nrr_graph* g, int32_t* node_src, int32_t* nidx, double* w,
+                         int32_t* edges, double* r, double* lbar);
+void nrr_graph_destroy(nrr_graph* g);
+
 /* The surrogate system of the last kept pass, in node order: Kdense
  * [4N][4N] (row-major, only the graph's blocks are non-zero) and B [4N][3].
  * Host buffers. For tests of the assembly; N <= 4096. */

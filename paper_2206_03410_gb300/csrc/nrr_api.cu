@@ -1504,6 +1504,59 @@ nrr_status nrr_get_sizes(nrr_ctx* c, int64_t* P, int64_t* T, int64_t* N, int64_t
     return NRR_OK;
 }
 
+struct nrr_graph {
+    HostGraph g;
+};
+
+nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, double radius, int max_influence) {
+    if (!out || !src_xyz) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build: NULL argument");
+    *out = nullptr;
+    if (P < 1) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build: P < 1");
+    if (!std::isfinite(radius)) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build: radius not finite");
+    const int K = max_influence <= 0 ? 8 : max_influence;
+    if (K > 8) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build: max_influence > 8");
+    try {
+        std::vector<double> V((size_t)P * 3);
+        for (size_t k = 0; k < V.size(); ++k) {
+            V[k] = (double)src_xyz[k];
+            if (!std::isfinite(V[k])) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build: non-finite point");
+        }
+        std::unique_ptr<nrr_graph> g(new nrr_graph);
+        g->g.lbar = nrr_mean_spacing(V.data(), P, 6);
+        const double R = radius > 0 ? radius : 5.0 * g->g.lbar;
+        nrr_build_graph(V.data(), P, R, K, g->g);
+        *out = g.release();
+        return NRR_OK;
+    } catch (const std::bad_alloc&) {
+        return nrr_set_global_error(NRR_E_OOM, "nrr_graph_build: out of host memory");
+    }
+}
+
+nrr_status nrr_graph_sizes(const nrr_graph* g, int64_t* N, int64_t* n_edges, int32_t* max_influence,
+                           double* radius) {
+    if (!g) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_sizes: graph is NULL");
+    if (N) *N = (int64_t)g->g.nodes.size();
+    if (n_edges) *n_edges = (int64_t)(g->g.edges.size() / 2);
+    if (max_influence) *max_influence = g->g.K;
+    if (radius) *radius = g->g.radius;
+    return NRR_OK;
+}
+
+nrr_status nrr_graph_get(const nrr_graph* gh, int32_t* node_src, int32_t* nidx, double* w, int32_t* edges,
+                         double* r, double* lbar) {
+    if (!gh) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_get: graph is NULL");
+    const HostGraph& g = gh->g;
+    if (node_src) std::copy(g.nodes.begin(), g.nodes.end(), node_src);
+    if (nidx) std::copy(g.nidx.begin(), g.nidx.end(), nidx);
+    if (w) std::copy(g.w.begin(), g.w.end(), w);
+    if (edges) std::copy(g.edges.begin(), g.edges.end(), edges);
+    if (r) std::copy(g.r.begin(), g.r.end(), r);
+    if (lbar) *lbar = g.lbar;
+    return NRR_OK;
+}
+
+void nrr_graph_destroy(nrr_graph* g) { delete g; }
+
 nrr_status nrr_get_graph(nrr_ctx* c, int32_t* node_src, int32_t* nidx, double* w, int32_t* edges,
                          double* r, double* lbar) {
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");

@@ -128,6 +128,10 @@ _SIGS = [
     ("nrr_get_correspondence", ctypes.c_int, [_VP, _VP, _VP]),
     ("nrr_get_sizes", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     ("nrr_get_graph", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("nrr_graph_build", ctypes.c_int, [ctypes.POINTER(_VP), _VP, _I64, ctypes.c_double, ctypes.c_int]),
+    ("nrr_graph_sizes", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    ("nrr_graph_get", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("nrr_graph_destroy", None, [_VP]),
     ("nrr_get_system", ctypes.c_int, [_VP, _VP, _VP]),
     ("nrr_get_mm_solution", ctypes.c_int, [_VP, _VP]),
     ("nrr_get_info", ctypes.c_int, [_VP, ctypes.POINTER(NrrStepInfo)]),
@@ -413,6 +417,34 @@ def nrr_get_graph(ctx) -> GraphView:
     lbar = ctypes.c_double()
     _check(load().nrr_get_graph(ctx, _ptr(nodes), _ptr(nidx), _ptr(w), _ptr(edges), _ptr(r),
                                 ctypes.byref(lbar)), ctx)
+    return GraphView(nodes, nidx, w, edges, r, lbar.value)
+
+
+def build_graph(src, radius: float = 0.0, max_influence: int = 0) -> GraphView:
+    """The deformation graph of the source points src [P,3] (Algorithm 1,
+    Sec. 3.1-3.2), built on the host by the library without a GPU: the graph
+    nrr_create would build with the same radius (<= 0: 5 lbar) and influence
+    cap (<= 0: 8)."""
+    v = np.ascontiguousarray(np.asarray(src, dtype=np.float32))
+    if v.ndim != 2 or v.shape[1] != 3:
+        raise ValueError("src must be [P, 3]")
+    lib = load()
+    g = _VP()
+    _check(lib.nrr_graph_build(ctypes.byref(g), _ptr(v), v.shape[0], float(radius), int(max_influence)))
+    try:
+        N, E, K = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        R = ctypes.c_double()
+        _check(lib.nrr_graph_sizes(g, ctypes.byref(N), ctypes.byref(E), ctypes.byref(K), ctypes.byref(R)))
+        P = v.shape[0]
+        nodes = np.zeros(N.value, dtype=np.int32)
+        nidx = np.zeros((P, K.value), dtype=np.int32)
+        w = np.zeros((P, K.value), dtype=np.float64)
+        edges = np.zeros((E.value, 2), dtype=np.int32)
+        r = np.zeros(2 * E.value, dtype=np.float64)
+        lbar = ctypes.c_double()
+        _check(lib.nrr_graph_get(g, _ptr(nodes), _ptr(nidx), _ptr(w), _ptr(edges), _ptr(r), ctypes.byref(lbar)))
+    finally:
+        lib.nrr_graph_destroy(g)
     return GraphView(nodes, nidx, w, edges, r, lbar.value)
 
 
