@@ -10,8 +10,8 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <iterator>
 #include <thread>
-#include <unordered_map>
 
 #include "nrr_internal.h"
 
@@ -72,12 +72,19 @@ void parallel_sort(std::vector<E>& v) {
     }
 }
 
+// Uniform grid over a point set: the point indices sorted by (cell key,
+// index) and, per occupied cell, its run of them. Cells are found through a
+// dense table of the occupied cells' ranks when the grid has few cells for
+// the points (the common case), else by binary search of the sorted keys.
 struct Grid {
     double lo[3];
     double h;
     int64_t dims[3];
-    std::unordered_map<int64_t, std::pair<int, int>> cells;  // key -> [start,count)
-    std::vector<int> items;
+    std::vector<int> items;          // point indices by (cell key, index)
+    std::vector<double> pxyz;        // their coordinates, in the same order [n][3]
+    std::vector<int64_t> ukeys;      // occupied cells' keys, ascending
+    std::vector<int> ustart;         // their runs in items (ukeys.size() + 1)
+    std::vector<int> dense;          // key -> rank in ukeys, or -1 (if used)
 
     int64_t key(int64_t x, int64_t y, int64_t z) const {
         return (x * dims[1] + y) * dims[2] + z;
@@ -109,19 +116,51 @@ struct Grid {
         });
         parallel_sort(kv);   // (cell, index) pairs are distinct
         items.resize((size_t)n);
+        ukeys.clear();
+        ustart.clear();
         for (size_t i = 0; i < kv.size(); ++i) {
             items[i] = kv[i].second;
-            auto it = cells.find(kv[i].first);
-            if (it == cells.end()) cells.emplace(kv[i].first, std::make_pair((int)i, 1));
-            else it->second.second++;
+            if (i == 0 || kv[i].first != kv[i - 1].first) {
+                ukeys.push_back(kv[i].first);
+                ustart.push_back((int)i);
+            }
         }
+        ustart.push_back((int)n);
+        pxyz.resize((size_t)n * 3);
+        parallel_chunks(n, [&](int64_t s0, int64_t s1) {
+            for (int64_t s = s0; s < s1; ++s)
+                for (int d = 0; d < 3; ++d) pxyz[(size_t)(3 * s + d)] = V[3 * (int64_t)items[(size_t)s] + d];
+        });
+        // dims[d] <= extent / h + 1 each; the product can overflow only for
+        // absurd extents, which take the sparse path
+        const double total = (double)dims[0] * (double)dims[1] * (double)dims[2];
+        dense.clear();
+        if (total <= 4.0 * (double)n + 1048576.0) {
+            dense.assign((size_t)total, -1);
+            for (size_t u = 0; u < ukeys.size(); ++u) dense[(size_t)ukeys[u]] = (int)u;
+        }
+    }
+    // rank of cell (x, y, z) among the occupied cells, or -1
+    int find(int64_t x, int64_t y, int64_t z) const {
+        if (x < 0 || y < 0 || z < 0 || x >= dims[0] || y >= dims[1] || z >= dims[2]) return -1;
+        const int64_t k = key(x, y, z);
+        if (!dense.empty()) return dense[(size_t)k];
+        auto it = std::lower_bound(ukeys.begin(), ukeys.end(), k);
+        return (it != ukeys.end() && *it == k) ? (int)(it - ukeys.begin()) : -1;
     }
     template <class F>
     void visit_cell(int64_t x, int64_t y, int64_t z, F&& f) const {
-        if (x < 0 || y < 0 || z < 0 || x >= dims[0] || y >= dims[1] || z >= dims[2]) return;
-        auto it = cells.find(key(x, y, z));
-        if (it == cells.end()) return;
-        for (int s = it->second.first, e = s + it->second.second; s < e; ++s) f(items[(size_t)s]);
+        const int u = find(x, y, z);
+        if (u < 0) return;
+        for (int s = ustart[(size_t)u], e = ustart[(size_t)u + 1]; s < e; ++s) f(items[(size_t)s]);
+    }
+    // f(point index, its coordinates) for the points of cell (x, y, z)
+    template <class F>
+    void visit_cell_xyz(int64_t x, int64_t y, int64_t z, F&& f) const {
+        const int u = find(x, y, z);
+        if (u < 0) return;
+        for (int s = ustart[(size_t)u], e = ustart[(size_t)u + 1]; s < e; ++s)
+            f(items[(size_t)s], pxyz.data() + 3 * (size_t)s);
     }
 };
 
@@ -190,18 +229,7 @@ double nrr_mean_spacing(const double* V, int64_t P, int k) {
     Grid g;
     g.build(V, P, cell);
     // cells as runs of g.items (sorted by cell key)
-    std::vector<int64_t> run_start;
-    {
-        int64_t prev_key = -1;
-        for (int64_t s = 0; s < P; ++s) {
-            int64_t c[3];
-            g.cell_of(V + 3 * (int64_t)g.items[(size_t)s], c);
-            const int64_t key = g.key(c[0], c[1], c[2]);
-            if (s == 0 || key != prev_key) run_start.push_back(s);
-            prev_key = key;
-        }
-        run_start.push_back(P);
-    }
+    const std::vector<int>& run_start = g.ustart;
     const int64_t n_cells = (int64_t)run_start.size() - 1;
     // per point: the sum of its kk nearest distances, then a sum in point order
     std::vector<double> per_point((size_t)P, 0.0);
@@ -234,30 +262,38 @@ double nrr_mean_spacing(const double* V, int64_t P, int k) {
     parallel_chunks(n_cells, [&](int64_t c0, int64_t c1) {
         std::vector<double> best;
         std::vector<int> cand;
-        std::vector<double> cpos;   // candidate coordinates, contiguous
+        std::vector<double> cx, cy, cz, d2v;   // candidate coordinates (SoA), distances
         for (int64_t cidx = c0; cidx < c1; ++cidx) {
             const int64_t s0 = run_start[(size_t)cidx], s1 = run_start[(size_t)cidx + 1];
             int64_t c[3];
             g.cell_of(V + 3 * (int64_t)g.items[(size_t)s0], c);
-            cand.clear();
+            cand.clear(); cx.clear(); cy.clear(); cz.clear();
             for (int64_t x = c[0] - 1; x <= c[0] + 1; ++x)
                 for (int64_t y = c[1] - 1; y <= c[1] + 1; ++y)
                     for (int64_t z = c[2] - 1; z <= c[2] + 1; ++z)
-                        g.visit_cell(x, y, z, [&](int j) { cand.push_back(j); });
-            cpos.resize(cand.size() * 3);
-            for (size_t t = 0; t < cand.size(); ++t)
-                for (int d = 0; d < 3; ++d) cpos[3 * t + d] = V[3 * (int64_t)cand[t] + d];
+                        g.visit_cell_xyz(x, y, z, [&](int j, const double* p) {
+                            cand.push_back(j);
+                            cx.push_back(p[0]); cy.push_back(p[1]); cz.push_back(p[2]);
+                        });
+            const size_t nc = cand.size();
+            d2v.resize(nc);
             for (int64_t sidx = s0; sidx < s1; ++sidx) {
                 const int64_t i = g.items[(size_t)sidx];
-                const double* q = V + 3 * i;
+                const double qx = V[3 * i], qy = V[3 * i + 1], qz = V[3 * i + 2];
+                // the same arithmetic as sqd(q, p), for all candidates
+                for (size_t t = 0; t < nc; ++t) {
+                    const double dx = qx - cx[t], dy = qy - cy[t], dz = qz - cz[t];
+                    d2v[t] = dx * dx + dy * dy + dz * dz;
+                }
                 best.assign((size_t)kk, INFINITY);
-                for (size_t t = 0; t < cand.size(); ++t) {
-                    if (cand[t] == (int)i) continue;
-                    const double d2 = sqd(q, cpos.data() + 3 * t);
-                    if (d2 < best[(size_t)kk - 1]) {
+                double worst = INFINITY;
+                for (size_t t = 0; t < nc; ++t) {
+                    const double d2 = d2v[t];
+                    if (d2 < worst && cand[t] != (int)i) {
                         size_t pos = (size_t)kk - 1;
                         while (pos > 0 && best[pos - 1] > d2) { best[pos] = best[pos - 1]; --pos; }
                         best[pos] = d2;
+                        worst = best[(size_t)kk - 1];
                     }
                 }
                 // every point outside the 27 cells is at least one cell width away
@@ -316,6 +352,7 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
     // order; a point is covered once some node influences it
     struct Infl { int pt; int node; double d2; };
     std::vector<Infl> trip;
+    trip.reserve((size_t)P * 4);
     std::vector<unsigned char> covered((size_t)P, 0);
     g.nodes.clear();
     for (int i : order) {
@@ -328,8 +365,8 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
         for (int64_t x = c[0] - 1; x <= c[0] + 1; ++x)
             for (int64_t y = c[1] - 1; y <= c[1] + 1; ++y)
                 for (int64_t z = c[2] - 1; z <= c[2] + 1; ++z)
-                    grid.visit_cell(x, y, z, [&](int pt) {
-                        double d2 = sqd(q, V + 3 * (int64_t)pt);
+                    grid.visit_cell_xyz(x, y, z, [&](int pt, const double* pp) {
+                        const double d2 = sqd(q, pp);
                         if (d2 < R2) {
                             trip.push_back({pt, j, d2});
                             covered[(size_t)pt] = 1;
@@ -378,10 +415,21 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
     std::sort(edge_list.begin(), edge_list.end());
     edge_list.erase(std::unique(edge_list.begin(), edge_list.end()), edge_list.end());
     });
+    // the chunks' lists are sorted and unique: merge them pairwise
+    while (chunk_edges.size() > 1) {
+        std::vector<std::vector<std::pair<int, int>>> next;
+        for (size_t k = 0; k + 1 < chunk_edges.size(); k += 2) {
+            std::vector<std::pair<int, int>> m;
+            m.reserve(chunk_edges[k].size() + chunk_edges[k + 1].size());
+            std::set_union(chunk_edges[k].begin(), chunk_edges[k].end(), chunk_edges[k + 1].begin(),
+                           chunk_edges[k + 1].end(), std::back_inserter(m));
+            next.push_back(std::move(m));
+        }
+        if (chunk_edges.size() % 2) next.push_back(std::move(chunk_edges.back()));
+        chunk_edges.swap(next);
+    }
     std::vector<std::pair<int, int>> edge_list;
-    for (auto& ce : chunk_edges) edge_list.insert(edge_list.end(), ce.begin(), ce.end());
-    std::sort(edge_list.begin(), edge_list.end());
-    edge_list.erase(std::unique(edge_list.begin(), edge_list.end()), edge_list.end());
+    if (!chunk_edges.empty()) edge_list.swap(chunk_edges[0]);
     g.edges.clear();
     for (auto& e : edge_list) { g.edges.push_back(e.first); g.edges.push_back(e.second); }
     std::vector<std::pair<int, int>> dp;
