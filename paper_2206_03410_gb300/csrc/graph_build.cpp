@@ -72,6 +72,23 @@ void parallel_sort(std::vector<E>& v) {
     }
 }
 
+// Sorts pairs (u, v) with 0 <= u, v < n lexicographically and removes
+// duplicates: two stable counting passes (by v, then by u).
+void sort_unique_pairs(std::vector<std::pair<int, int>>& e, int n) {
+    if (e.size() < 2) return;
+    std::vector<std::pair<int, int>> tmp(e.size());
+    std::vector<int> cnt((size_t)n + 1);
+    auto pass = [&](std::vector<std::pair<int, int>>& from, std::vector<std::pair<int, int>>& to, bool by_u) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (const auto& x : from) cnt[(size_t)(by_u ? x.first : x.second) + 1]++;
+        for (int k = 0; k < n; ++k) cnt[(size_t)k + 1] += cnt[(size_t)k];
+        for (const auto& x : from) to[(size_t)cnt[(size_t)(by_u ? x.first : x.second)]++] = x;
+    };
+    pass(e, tmp, false);
+    pass(tmp, e, true);
+    e.erase(std::unique(e.begin(), e.end()), e.end());
+}
+
 // Uniform grid over a point set: the point indices sorted by (cell key,
 // index) and, per occupied cell, its run of them. Cells are found through a
 // dense table of the occupied cells' ranks when the grid has few cells for
@@ -233,12 +250,13 @@ double nrr_mean_spacing(const double* V, int64_t P, int k) {
     const int64_t n_cells = (int64_t)run_start.size() - 1;
     // per point: the sum of its kk nearest distances, then a sum in point order
     std::vector<double> per_point((size_t)P, 0.0);
+    // continues the search of point i over the shells of cells s >= 2 around
+    // its cell (best: the kk nearest among shells 0 and 1, ascending)
     auto shell_search = [&](int64_t i, std::vector<double>& best) {
         const double* q = V + 3 * i;
         int64_t c[3];
         g.cell_of(q, c);
-        best.assign((size_t)kk, INFINITY);   // sorted ascending
-        for (int64_t s = 0;; ++s) {
+        for (int64_t s = 2;; ++s) {
             for (int64_t x = c[0] - s; x <= c[0] + s; ++x)
                 for (int64_t y = c[1] - s; y <= c[1] + s; ++y)
                     for (int64_t z = c[2] - s; z <= c[2] + s; ++z) {
@@ -373,14 +391,40 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
                         }
                     });
     }
-    // grouped by point (counting sort, node order kept within a point)
+    // grouped by point (counting sort, node order kept within a point): per
+    // chunk of the triples a histogram over the points, then every chunk
+    // scatters its triples after those of the earlier chunks
     std::vector<int64_t> iptr((size_t)P + 1, 0);
-    for (const Infl& t : trip) iptr[(size_t)t.pt + 1]++;
-    for (int64_t i = 0; i < P; ++i) iptr[(size_t)i + 1] += iptr[(size_t)i];
     std::vector<std::pair<double, int>> iv(trip.size());
     {
-        std::vector<int64_t> fill(iptr.begin(), iptr.end() - 1);
-        for (const Infl& t : trip) iv[(size_t)fill[(size_t)t.pt]++] = {t.d2, t.node};
+        const int64_t nT = (int64_t)trip.size();
+        const int64_t nc = setup_threads(nT, 16384);
+        std::vector<std::vector<int>> cnt((size_t)nc);
+        parallel_chunks_idx(nT, nc, [&](int64_t t, int64_t a, int64_t b) {
+            std::vector<int>& h = cnt[(size_t)t];
+            h.assign((size_t)P, 0);
+            for (int64_t e = a; e < b; ++e) h[(size_t)trip[(size_t)e].pt]++;
+        });
+        // per point: its total, and each chunk's first slot relative to it
+        parallel_chunks(P, [&](int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i) {
+                int run = 0;
+                for (int64_t t = 0; t < nc; ++t) {
+                    const int c = cnt[(size_t)t][(size_t)i];
+                    cnt[(size_t)t][(size_t)i] = run;
+                    run += c;
+                }
+                iptr[(size_t)i + 1] = run;
+            }
+        });
+        for (int64_t i = 0; i < P; ++i) iptr[(size_t)i + 1] += iptr[(size_t)i];
+        parallel_chunks_idx(nT, nc, [&](int64_t t, int64_t a, int64_t b) {
+            std::vector<int>& h = cnt[(size_t)t];
+            for (int64_t e = a; e < b; ++e) {
+                const Infl& x = trip[(size_t)e];
+                iv[(size_t)(iptr[(size_t)x.pt] + h[(size_t)x.pt]++)] = {x.d2, x.node};
+            }
+        });
     }
     // Influence sets: the K nearest nodes, weights of Eq. (weight_data);
     // point chunks in parallel, each with its own list of node pairs
@@ -412,8 +456,7 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
                 edge_list.push_back({std::min(u, v), std::max(u, v)});
             }
     }
-    std::sort(edge_list.begin(), edge_list.end());
-    edge_list.erase(std::unique(edge_list.begin(), edge_list.end()), edge_list.end());
+    sort_unique_pairs(edge_list, (int)g.nodes.size());
     });
     // the chunks' lists are sorted and unique: merge them pairwise
     while (chunk_edges.size() > 1) {
