@@ -540,8 +540,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         if (k == rank - 1) h_dn = win.hi[k];
         if (k == rank + 1) h_up = win.lo[k];
     }
-    // shared layout (identical offsets in every CTA): K rows; the z window
-    // (hmax halo rows, the CTA's own rows, hmax halo rows); preconditioner
+    // shared layout (identical offsets in every CTA): K rows; the window of
+    // u = M^-1 r (hmax halo rows, the CTA's own rows, hmax halo rows); preconditioner
     // blocks; per K block the window row of its column, or the owner rank
     // and local node of a column outside the window (bit 15 set)
     T* Kloc = reinterpret_cast<T*>(smem);
@@ -594,10 +594,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
 
     asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     stamp();
-    // halo exchange: after the CTA's new z rows are written (thread 0, after
-    // a CTA barrier) push the first hi[r-1] rows to CTA r-1 and the last
-    // lo[r+1] rows to CTA r+1; before each SpMV wait for the rows this CTA
-    // receives (phase k of its mbarrier carries the halo of the k-th z)
+    // halo exchange: once the CTA's new rows of u are written (after a CTA
+    // barrier, lane 0 of the last warp) push the first hi[r-1] rows to CTA
+    // r-1 and the last lo[r+1] rows to CTA r+1, with the copy descriptors
+    // precomputed here; before the halo columns of each SpMV wait for the
+    // rows this CTA receives (phase k of its mbarrier carries the halo of the
+    // k-th u)
     const unsigned row_bytes = 12u * (unsigned)sizeof(T);
     const unsigned in_bytes = (unsigned)(hlo + hhi) * row_bytes;
     const int cnt_prev = rank > 0 ? min(N, rank * per) - min(N, (rank - 1) * per) : 0;
