@@ -295,7 +295,8 @@ nrr_status nrr_get_graph(nrr_ctx* ctx, int32_t* node_src, int32_t* nidx,
  * radius R (> 0; <= 0: 5 lbar with lbar the mean distance of each point to
  * its 6 nearest others), max_influence 1..8 (<= 0: 8). Errors:
  * NRR_E_INVALID (NULL pointer, P < 1, non-finite coordinate or radius,
- * max_influence > 8), NRR_E_OOM. nrr_graph_sizes: N, n_edges (undirected),
+ * max_influence > 8, a default radius 5 lbar that is 0, e.g. for identical
+ * points), NRR_E_OOM. nrr_graph_sizes: N, n_edges (undirected),
  * max_influence and the radius used. nrr_graph_get: the arrays of
  * nrr_get_graph (same layouts; host buffers, any pointer may be NULL; lbar
  * is always computed here). nrr_graph_destroy accepts NULL. */

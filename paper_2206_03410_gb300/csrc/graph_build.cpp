@@ -494,6 +494,28 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
     for (size_t e = 0; e < E2; ++e) g.r[e] = 2.0 * (double)edge_list.size() * inv[e] / inv_sum;
 }
 
+bool nrr_graph_and_spacing(const double* V, int64_t P, double radius, int K, bool need_lbar, HostGraph& g) {
+    double lbar = std::nan("");
+    if (radius > 0) {
+        // the graph does not need l-bar: its search runs on other threads
+        // while Algorithm 1's greedy pass (sequential) holds one
+        std::thread t;
+        if (need_lbar) t = std::thread([&]() { lbar = nrr_mean_spacing(V, P, 6); });
+        struct Join {
+            std::thread& t;
+            ~Join() { if (t.joinable()) t.join(); }
+        } join{t};
+        nrr_build_graph(V, P, radius, K, g);
+    } else {
+        lbar = nrr_mean_spacing(V, P, 6);
+        const double R = 5.0 * lbar;
+        if (!(R > 0)) return false;   // e.g. all points identical
+        nrr_build_graph(V, P, R, K, g);
+    }
+    g.lbar = lbar;
+    return true;
+}
+
 // Hilbert index of a 3-D point with 21 bits per axis, after J. Skilling,
 // "Programming the Hilbert curve", AIP Conf. Proc. 707 (2004): the axes are
 // converted in place to the "transposed" Hilbert index, whose bits are then

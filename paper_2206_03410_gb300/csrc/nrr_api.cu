@@ -1194,12 +1194,9 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     // l-bar, radius and the deformation graph (Algorithm 1)
     std::vector<double> V(src.begin(), src.end());
     const bool need_lbar = prm.graph_radius <= 0 || prm.nu_r <= 0 || prm.nu_a_min <= 0;
-    c->hg.lbar = need_lbar ? nrr_mean_spacing(V.data(), P, 6) : std::nan("");
-    tm.lap("l-bar");
-    const double R = prm.graph_radius > 0 ? prm.graph_radius : 5.0 * c->hg.lbar;
-    if (!(R > 0)) return fail(nullptr, NRR_E_INVALID, "graph radius must be positive");
-    nrr_build_graph(V.data(), P, R, prm.max_influence, c->hg);
-    tm.lap("graph (Algorithm 1)");
+    if (!nrr_graph_and_spacing(V.data(), P, prm.graph_radius, prm.max_influence, need_lbar, c->hg))
+        return fail(nullptr, NRR_E_INVALID, "graph radius must be positive");
+    tm.lap("l-bar + graph (Algorithm 1)");
     c->N = (int)c->hg.nodes.size();
     c->E2 = (int)c->hg.r.size();
     // launch geometry
@@ -1522,9 +1519,8 @@ nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, dou
             if (!std::isfinite(V[k])) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build: non-finite point");
         }
         std::unique_ptr<nrr_graph> g(new nrr_graph);
-        g->g.lbar = nrr_mean_spacing(V.data(), P, 6);
-        const double R = radius > 0 ? radius : 5.0 * g->g.lbar;
-        nrr_build_graph(V.data(), P, R, K, g->g);
+        if (!nrr_graph_and_spacing(V.data(), P, radius, K, true, g->g))
+            return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build: radius 5 l-bar is not positive");
         *out = g.release();
         return NRR_OK;
     } catch (const std::bad_alloc&) {

@@ -68,6 +68,11 @@ struct HostGraph {
 void nrr_parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f);
 double nrr_mean_spacing(const double* V, int64_t P, int k);
 void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g);
+// Algorithm 1 with radius R (> 0), or with 5 l-bar (radius <= 0), and l-bar
+// (the mean 6-NN spacing) into g.lbar if need_lbar or radius <= 0 (else
+// NaN); with a given radius the two run concurrently. Returns false (and
+// builds nothing) if the radius would be 5 l-bar = 0.
+bool nrr_graph_and_spacing(const double* V, int64_t P, double radius, int K, bool need_lbar, HostGraph& g);
 void nrr_curve_order(const float* pts, int64_t n, const double lo[3],
                       const double hi[3], std::vector<int>& order,
                       std::vector<uint64_t>* codes_sorted);

@@ -58,3 +58,14 @@ def test_host_graph_rejects_bad_arguments():
     with pytest.raises(nrr.NrrError) as e:
         nrr.build_graph(pts, radius=0.1, max_influence=9)
     assert e.value.code == nrr.NRR_E_INVALID
+
+
+def test_host_graph_default_radius_needs_spread_points():
+    """With the default radius 5 lbar, identical points give lbar = 0 and no
+    valid radius: the call fails instead of building a degenerate graph."""
+    pts = np.repeat(np.array([[0.1, 0.2, 0.3]], np.float32), 20, axis=0)
+    with pytest.raises(nrr.NrrError) as e:
+        nrr.build_graph(pts, radius=0.0)
+    assert e.value.code == nrr.NRR_E_INVALID
+    g = nrr.build_graph(pts, radius=0.1)      # an explicit radius works
+    assert len(g.nodes) == 1 and g.lbar == 0.0
