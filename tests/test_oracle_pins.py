@@ -598,3 +598,32 @@ def test_stop_rules_displacement_or_energy():
     r.solve()
     assert r.done and _solves_per_stage(r) == [1, 1, 1, 1]
     assert [math.isnan(x.max_disp) for x in r.records] == [False, True] * 4
+
+
+def test_small_rigid_motion_recovered_by_algorithm_2():
+    """Target = a small rigid motion of the source (no noise, no outliers;
+    the largest displacement a fifth of the smallest distance between two
+    source points, so every point's closest target is its own image):
+    Algorithm 2 with its own closest points (no correspondence hook),
+    Anderson mixing and annealing, run with a tight stopping threshold,
+    reaches the motion (E = 0 at the exact map): every deformed point lies
+    on its image to 1e-10 of the bounding-box diagonal."""
+    pair = synth.tiny_pair(400, 400, seed=12)
+    V = pair.src.astype(np.float64)
+    d2 = np.sum((V[:, None, :] - V[None, :, :]) ** 2, axis=2)
+    np.fill_diagonal(d2, np.inf)
+    dmin = float(np.sqrt(d2.min()))
+    ang = 0.1 * dmin / np.linalg.norm(V - V.mean(axis=0), axis=1).max()
+    c, s = np.cos(ang), np.sin(ang)
+    Rz = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    center = V.mean(axis=0)
+    t = np.array([0.6, -0.4, 0.2]) * 0.1 * dmin
+    U = (V - center) @ Rz.T + center + t
+    assert np.linalg.norm(U - V, axis=1).max() <= 0.2 * dmin
+    assert np.array_equal(M.closest_points(V, U)[0], np.arange(len(V)))
+    diag = np.linalg.norm(np.maximum(V.max(0), U.max(0)) - np.minimum(V.min(0), U.min(0)))
+    reg = Registration(V, U, Params(radius=0.35, aa_m=5, eps=1e-12 * diag))
+    reg.solve()
+    assert reg.done
+    vh = M.deform(V, reg.graph.nidx, reg.graph.w, reg.graph.p, reg.X)
+    assert np.abs(vh - U).max() < 1e-10 * diag
