@@ -271,6 +271,16 @@ def test_normal_equations_minimise_surrogate(small):
     assert np.allclose(Kd, Kd.T, atol=1e-12)
     assert np.linalg.eigvalsh(Kd).min() > 0
     Xs = S.solve_normal_equations(K, B)
+    # the dense Cholesky the oracle uses for small systems and the sparse LU
+    # it uses for large ones agree, and both leave a residual at rounding
+    Bm = np.asarray(B).reshape(-1, 3)
+    Xlu = np.asarray(S.spla.spsolve(K.tocsc(), Bm)).reshape(Xs.shape)
+    assert np.abs(Xlu - Xs).max() <= 1e-10 * np.abs(Xs).max()
+    knorm = np.linalg.norm(Kd, 2)
+    for Xsol in (Xs, Xlu):
+        # backward error of a backward-stable direct solve
+        res = Kd @ Xsol.reshape(-1, 3) - Bm
+        assert np.linalg.norm(res) <= 1e-13 * knorm * np.linalg.norm(Xsol)
     f = lambda X: S.surrogate_value(V, U, g, t, X, nu_a, nu_r, alpha, beta)
     flat = Xs.ravel()
     h = 1e-5
