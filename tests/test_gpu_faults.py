@@ -68,3 +68,24 @@ def test_bounded_halo_wait_reports_timeout(monkeypatch):
     info = ok.solve(3000)
     assert info.done == 1 and info.status == 0
     ok.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_pcg_iteration_cap_is_reported_not_fatal(prec):
+    """Injected PCG non-convergence: with pcg_max_iters = 2 the solve stops
+    after two CG iterations, far above its tolerance; the pass reports the
+    iteration count and the residual reached, the MM step is taken from
+    that inexact solve, and the run continues without an error status (the
+    energy safeguard of Algorithm 2 still decides every kept iterate)."""
+    from paper_2206_03410_gb300 import nrr
+    nrr.load()
+    pair = synth.tiny_pair(3000, 3200, seed=83, noise=0.002, outliers=0.05)
+    reg = nrr.Registration(pair.src, pair.tgt, radius=0.2, aa_m=5, precision=prec, pcg_max_iters=2)
+    info = reg.step()
+    assert info.solved == 1 and info.status == 0
+    assert info.pcg_iters == 2
+    assert info.pcg_rel_residual > 1e-6
+    for _ in range(4):
+        info = reg.step()
+        assert info.status == 0 and info.E == info.E   # finite, no NaN
+    reg.close()
