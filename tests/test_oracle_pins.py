@@ -617,7 +617,8 @@ def test_small_rigid_motion_recovered_by_algorithm_2():
     Algorithm 2 with its own closest points (no correspondence hook),
     Anderson mixing and annealing, run with a tight stopping threshold,
     reaches the motion (E = 0 at the exact map): every deformed point lies
-    on its image to 1e-10 of the bounding-box diagonal."""
+    on its image to 1e-10 of the bounding-box diagonal, and the limit is a
+    fixed point of the MM map."""
     pair = synth.tiny_pair(400, 400, seed=12)
     V = pair.src.astype(np.float64)
     d2 = np.sum((V[:, None, :] - V[None, :, :]) ** 2, axis=2)
@@ -637,3 +638,7 @@ def test_small_rigid_motion_recovered_by_algorithm_2():
     assert reg.done
     vh = M.deform(V, reg.graph.nidx, reg.graph.w, reg.graph.p, reg.X)
     assert np.abs(vh - U).max() < 1e-10 * diag
+    # the limit is a fixed point of the MM map G (Sec. 3.3.4): one more
+    # surrogate minimisation from it stays there
+    G_ = reg.mm_map(reg.terms())
+    assert np.abs(G_ - reg.X).max() < 1e-9 * np.abs(reg.X).max()
