@@ -249,11 +249,13 @@ nrr_status nrr_unroll(nrr_ctx* ctx, int K, const double* X0, double* XK);
  * safeguard scalars, the iterate X, the last MM results, the Anderson
  * history and the deformed source of the last kept iterate, in the
  * context's precision, behind a header naming the problem's sizes and
- * precision. nrr_get_state_size gives its size in bytes; nrr_save_state
+ * precision and a 64-bit hash of its inputs (source and target points),
+ * deformation graph and parameters. nrr_get_state_size gives its size in bytes; nrr_save_state
  * writes it to buf (host or device, at least that size); nrr_load_state
  * reads it into a context created from the same inputs and parameters, after
  * which the solve continues exactly (bitwise) as the saved one would have.
- * NRR_E_INVALID for a short buffer or a state saved from another problem. */
+ * NRR_E_INVALID for a short buffer or a state saved from another problem
+ * (other sizes, precision, inputs, graph or parameters). */
 nrr_status nrr_get_state_size(nrr_ctx* ctx, size_t* bytes);
 nrr_status nrr_save_state(nrr_ctx* ctx, void* buf, size_t bytes);
 nrr_status nrr_load_state(nrr_ctx* ctx, const void* buf, size_t bytes);
@@ -336,8 +338,9 @@ nrr_status nrr_get_solve_stats(nrr_ctx* ctx, long long out[64]);
 /* State of the last pass without running one (host info). */
 nrr_status nrr_get_info(nrr_ctx* ctx, nrr_step_info* info);
 
-/* Alignment term of Eq. (2) and the weights of its quadratic surrogate,
- * computed from closest-point distances without allocating any memory.
+/* The alignment term of the energy (the sum of Welsch's function psi_nu_a
+ * over the closest-point distances) and the weights of its quadratic
+ * surrogate, computed from those distances without allocating any memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc (a preallocated real-time tracking loop, a host
  * framework whose allocator owns all device memory, work issued while a CUDA

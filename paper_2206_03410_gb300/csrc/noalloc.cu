@@ -55,7 +55,7 @@ align_energy_kernel(const float* __restrict__ d2, int64_t P, float ia, float* __
         const int64_t i = base + (int64_t)k * kThreads + threadIdx.x;
         if (i < P) {
             const float x = d2[i] * ia;
-            e += (double)(-expm1f(-x));        // Welsch psi_nu_a (Eq. Welsch_func)
+            e += (double)(-expm1f(-x));        // Welsch's function psi_nu_a (Sec. 3.2)
             wa[i] = expf(-x) * ia;             // weight of the quadratic surrogate
         }
     }

@@ -86,6 +86,7 @@ struct nrr_ctx {
     NrrHaloWin cl_win{};               // cluster solve: halo windows
     double diag = 0.0;
     double nu_a0 = 0.0, nu_r0 = 0.0;   // first-stage parameters
+    uint64_t problem_hash = 0;         // inputs, graph and parameters (checkpoints)
     bool failed = false;
     std::string err;
 };
@@ -401,6 +402,52 @@ void fill_info(const NrrState& s, nrr_step_info* info) {
 // ---------------------------------------------------------------------------
 // Creation
 // ---------------------------------------------------------------------------
+// 64-bit hash of the bytes of a problem (source, target, graph, parameters),
+// stored in checkpoints so that a state saved from another problem of the
+// same sizes is refused. Word-wise multiply-xorshift mixing; not
+// cryptographic.
+struct ProblemHash {
+    uint64_t h = 0x9e3779b97f4a7c15ull;
+    void word(uint64_t w) {
+        h ^= w + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+        h *= 0xff51afd7ed558ccdull;
+        h ^= h >> 33;
+    }
+    void bytes(const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        size_t k = 0;
+        for (; k + 8 <= n; k += 8) {
+            uint64_t w;
+            std::memcpy(&w, b + k, 8);
+            word(w);
+        }
+        uint64_t t = 0;
+        for (size_t j = 0; k + j < n; ++j) t |= (uint64_t)b[k + j] << (8 * j);
+        word(t ^ ((uint64_t)n << 56));
+    }
+    template <typename V>
+    void vec(const std::vector<V>& v) { bytes(v.data(), v.size() * sizeof(V)); }
+};
+
+uint64_t problem_hash(const std::vector<float>& src, const std::vector<float>& tgt, const HostGraph& g,
+                      const nrr_params& prm) {
+    ProblemHash ph;
+    ph.vec(src);
+    ph.vec(tgt);
+    ph.vec(g.nodes);
+    ph.vec(g.nidx);
+    ph.vec(g.w);
+    ph.vec(g.edges);
+    ph.vec(g.r);
+    const double dp[] = {prm.graph_radius, prm.nu_a, prm.nu_r, prm.nu_a_min, prm.k_alpha, prm.k_beta, prm.alpha,
+                         prm.beta, prm.eps, prm.rel_energy_tol, prm.pcg_tol};
+    const int ip[] = {prm.max_influence, prm.anneal, prm.aa_m, prm.max_iters_per_stage, prm.precision,
+                      prm.pcg_max_iters, prm.robust, prm.nu_schedule};
+    ph.bytes(dp, sizeof dp);
+    ph.bytes(ip, sizeof ip);
+    return ph.h;
+}
+
 // Hilbert orders of source and target over their common bounding box; they
 // depend on the inputs only, so nrr_create computes them on a second host
 // thread while it builds the deformation graph.
@@ -1027,14 +1074,16 @@ nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, double* n
 // passes do not rebuild - the device control block, the iterate X, the MM
 // results G, G_prev, F_prev, the Anderson rings dF, dG and both deformed-
 // source buffers (the stop test compares with the kept one). Layout: a
-// header {magic, version, precision, P, N, m}, then NrrState, then the
+// header {magic, version, precision, P, N, m, problem hash}, then NrrState, then the
 // arrays in that order, in the context's precision.
 // ---------------------------------------------------------------------------
 struct CkptHeader {
     uint64_t magic;      // "nrr-ckpt"
     uint32_t version, fp64;
     int64_t P, N, m;
+    uint64_t problem;    // hash of the inputs, the graph and the parameters
 };
+constexpr uint32_t kCkptVersion = 2u;
 constexpr uint64_t kCkptMagic = 0x74706b632d72726eull;
 
 size_t ckpt_bytes(const nrr_ctx* c) {
@@ -1199,6 +1248,7 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     tm.lap("l-bar + graph (Algorithm 1)");
     c->N = (int)c->hg.nodes.size();
     c->E2 = (int)c->hg.r.size();
+    c->problem_hash = problem_hash(src, tgt, c->hg, prm);
     // launch geometry
     if (const char* e = std::getenv("NRR_NN_LPQ")) {
         const int v = std::atoi(e);
@@ -1711,7 +1761,8 @@ nrr_status nrr_save_state(nrr_ctx* c, void* buf, size_t bytes) {
     nrr_status st = pull_state(c);
     if (st != NRR_OK) return st;
     std::vector<unsigned char> h(ckpt_bytes(c));
-    CkptHeader hd{kCkptMagic, 1u, c->fp64 ? 1u : 0u, c->P, (int64_t)c->N, (int64_t)std::max(1, c->prm.aa_m)};
+    CkptHeader hd{kCkptMagic, kCkptVersion, c->fp64 ? 1u : 0u, c->P, (int64_t)c->N,
+                  (int64_t)std::max(1, c->prm.aa_m), c->problem_hash};
     std::memcpy(h.data(), &hd, sizeof hd);
     std::memcpy(h.data() + sizeof hd, c->h_state, sizeof(NrrState));
     unsigned char* arrays = h.data() + sizeof hd + sizeof(NrrState);
@@ -1730,8 +1781,8 @@ nrr_status nrr_load_state(nrr_ctx* c, const void* buf, size_t bytes) {
     CK(cudaMemcpy(h.data(), buf, h.size(), cudaMemcpyDefault));
     CkptHeader hd;
     std::memcpy(&hd, h.data(), sizeof hd);
-    if (hd.magic != kCkptMagic || hd.version != 1u || hd.fp64 != (c->fp64 ? 1u : 0u) || hd.P != c->P ||
-        hd.N != (int64_t)c->N || hd.m != (int64_t)std::max(1, c->prm.aa_m))
+    if (hd.magic != kCkptMagic || hd.version != kCkptVersion || hd.fp64 != (c->fp64 ? 1u : 0u) || hd.P != c->P ||
+        hd.N != (int64_t)c->N || hd.m != (int64_t)std::max(1, c->prm.aa_m) || hd.problem != c->problem_hash)
         return fail(c, NRR_E_INVALID, "nrr_load_state: the state was saved from a different problem or precision");
     NrrState s;
     std::memcpy(&s, h.data() + sizeof hd, sizeof s);

@@ -345,10 +345,36 @@ def nrr_batch_tune(batch, table: str | None = None, reps: int = 0) -> NrrLaunchC
 
 def nrr_align_energy_noalloc(d2, nu_a: float, w_a, E_align, stream=None):
     """Allocation-free alignment energy and surrogate weights. d2, w_a:
-    float32 CUDA tensors [P]; E_align: float64 CUDA tensor [1]. Enqueues on
-    ``stream`` (raw cudaStream_t, None = legacy default stream)."""
-    _check(load().nrr_align_energy_noalloc(_ptr(d2), int(d2.shape[0]), float(nu_a), _ptr(w_a),
-                                            _ptr(E_align), stream))
+    float32 CUDA tensors [P] (w_a at least P elements); E_align: float64
+    CUDA tensor with at least one element; all three contiguous and on the
+    same device. Enqueues on ``stream`` (raw cudaStream_t, None = legacy
+    default stream). Buffers of the wrong kind raise ValueError before
+    anything is launched: the library reads and writes them as raw device
+    pointers."""
+    import torch
+    bufs = {"d2": d2, "w_a": w_a, "E_align": E_align}
+    for name, t in bufs.items():
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if d2.dtype != torch.float32 or w_a.dtype != torch.float32:
+        raise ValueError("d2 and w_a must be float32")
+    if E_align.dtype != torch.float64:
+        raise ValueError("E_align must be float64")
+    if d2.dim() != 1 or d2.numel() < 1:
+        raise ValueError("d2 must be a non-empty 1-D tensor [P]")
+    P = int(d2.numel())
+    if w_a.numel() < P:
+        raise ValueError(f"w_a holds {w_a.numel()} elements, fewer than P = {P}")
+    if E_align.numel() < 1:
+        raise ValueError("E_align must hold one element")
+    for name, t in bufs.items():
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+    if not (d2.device == w_a.device == E_align.device):
+        raise ValueError("d2, w_a and E_align must be on the same device")
+    _check(load().nrr_align_energy_noalloc(_ptr(d2), P, float(nu_a), _ptr(w_a), _ptr(E_align), stream))
 
 
 def nrr_set_transforms(ctx, X):

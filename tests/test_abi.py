@@ -99,3 +99,26 @@ def test_tuner_entry_points_reject_bad_arguments_without_gpu():
     assert lib.nrr_batch_tune(None, None, 0, ctypes.byref(cfg)) == nrr.NRR_E_INVALID
     assert lib.nrr_get_launch_config(None, ctypes.byref(cfg)) == nrr.NRR_E_INVALID
     assert lib.nrr_set_launch_config(None, ctypes.byref(cfg)) == nrr.NRR_E_INVALID
+
+
+def test_noalloc_wrapper_rejects_wrong_buffers_before_launch():
+    """The binding of nrr_align_energy_noalloc passes raw device pointers, so
+    it checks the buffers first: wrong dtype, too few elements or host
+    memory raise ValueError and nothing reaches the library."""
+    torch = pytest.importorskip("torch")
+    f32 = torch.zeros(16, dtype=torch.float32)
+    f64 = torch.zeros(1, dtype=torch.float64)
+    cases = [
+        (f32.double(), f32, f64, "float32"),            # d2 float64
+        (f32, f32.double(), f64, "float32"),            # w_a float64
+        (f32, f32, f64.float(), "float64"),             # E_align float32
+        (f32, torch.zeros(15, dtype=torch.float32), f64, "fewer"),
+        (f32, f32, torch.zeros(0, dtype=torch.float64), "one element"),
+        (torch.zeros(0, dtype=torch.float32), f32, f64, "non-empty"),
+        (torch.zeros(16, 2, dtype=torch.float32)[:, 0], f32, f64, "contiguous"),
+        (f32, f32, f64, "CUDA"),                        # host tensors
+        (f32.numpy(), f32, f64, "torch tensor"),
+    ]
+    for d2, w, E, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            nrr.nrr_align_energy_noalloc(d2, 0.1, w, E)

@@ -1,6 +1,7 @@
 """Checkpoint / resume through the C ABI: a solve saved after some passes
 and resumed in a fresh context of the same problem ends bitwise where the
-uninterrupted solve ends; a state from another problem is rejected."""
+uninterrupted solve ends; a state from another problem (other sizes, or
+the same sizes with another target or other parameters) is rejected."""
 import numpy as np
 import pytest
 
@@ -46,5 +47,18 @@ def test_resume_is_bitwise_identical(prec):
     with pytest.raises(nrr.NrrError) as e:
         b.load_state(state[: len(state) // 2])   # short buffer
     assert e.value.code == nrr.NRR_E_INVALID
-    for r in (a, b, c):
+    # the same sizes but another problem: a different target, or the same
+    # pair with other parameters (the header's hash differs)
+    tgt2 = pair.tgt.copy()
+    tgt2[:, 0] += 0.01
+    d = nrr.Registration(pair.src, tgt2, **kw)
+    assert (d.P, d.N) == (a.P, a.N)
+    with pytest.raises(nrr.NrrError) as e:
+        d.load_state(state)
+    assert e.value.code == nrr.NRR_E_INVALID
+    e2 = nrr.Registration(pair.src, pair.tgt, **dict(kw, k_alpha=50.0))
+    with pytest.raises(nrr.NrrError) as e:
+        e2.load_state(state)
+    assert e.value.code == nrr.NRR_E_INVALID
+    for r in (a, b, c, d, e2):
         r.close()

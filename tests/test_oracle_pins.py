@@ -642,3 +642,45 @@ def test_small_rigid_motion_recovered_by_algorithm_2():
     # surrogate minimisation from it stays there
     G_ = reg.mm_map(reg.terms())
     assert np.abs(G_ - reg.X).max() < 1e-9 * np.abs(reg.X).max()
+
+
+def test_revert_target_is_the_last_mm_result():
+    """After the safeguard rejects an Anderson iterate (Algorithm 2), the
+    next iterate is G^(k-1), the minimiser of the surrogate built at the last
+    kept iterate X^(k-1): every directional derivative of that surrogate
+    (summed term by term: Eqs. AlignQuadSurrogate and ERegSurrogate and the
+    rotation surrogate; a quadratic in X, so central differences are exact
+    up to rounding) vanishes at the new iterate, and not at X^(k-1) nor at
+    the rejected iterate. The re-evaluated iterate is then kept, and by MM
+    descent (Sec. 3.3.1: E(G) <= surrogate(G) <= surrogate(X^(k-1)) =
+    E(X^(k-1))) its energy is at most the last kept energy."""
+    pair = synth.tiny_pair(1200, 1320, seed=31, noise=0.002, outliers=0.05)
+    reg = Registration(pair.src, pair.tgt, Params(radius=0.25, aa_m=5))
+    evaluated = []
+    rej = None
+    for k in range(12):
+        evaluated.append(reg.X.copy())
+        rec = reg.step()
+        if not rec.kept:
+            rej = k
+            break
+    assert rej is not None and rej >= 2
+    prev = reg.records[rej - 1]
+    assert prev.kept and prev.stage == reg.records[rej].stage == reg.stage
+    X_k1, X_rej, X_rev = evaluated[rej - 1], evaluated[rej], reg.X.copy()
+    terms_k1 = reg.terms(X_k1)
+    a, b = reg.weights()
+
+    def ddir(X, D, h=1e-3):
+        f = lambda Y: S.surrogate_value(reg.V, reg.U, reg.graph, terms_k1, Y, reg.nu_a, reg.nu_r, a, b)
+        return (f(X + h * D) - f(X - h * D)) / (2 * h)
+
+    rng = _rng(5)
+    for _ in range(4):
+        D = rng.standard_normal(X_rev.shape)
+        g_rev, g_k1, g_rej = ddir(X_rev, D), ddir(X_k1, D), ddir(X_rej, D)
+        assert abs(g_rev) < 1e-6 * abs(g_k1), (g_rev, g_k1)
+        assert abs(g_rev) < 1e-6 * abs(g_rej), (g_rev, g_rej)
+    nxt = reg.step()
+    assert nxt.kept
+    assert nxt.E <= prev.E * (1 + 1e-12), (nxt.E, prev.E)
