@@ -144,6 +144,16 @@ typedef struct {
     int    aa_mk;                    /* AA differences used in the mix      */
     int    n_passes, n_solves, n_rejected;
     int    status;                   /* nrr_status of device-side checks    */
+    int    warning;                  /* NRR_E_SINGULAR if the last solve's K
+                                        was singular (see n_singular), else
+                                        NRR_OK; the pass itself succeeded   */
+    int    n_singular;               /* connected components of the
+                                        deformation graph on which no point
+                                        had alignment weight in the last
+                                        solve: K does not fix their common
+                                        translation, and G keeps the
+                                        component's summed translation of
+                                        X^(k) (the paper is silent)         */
 } nrr_step_info;
 
 void nrr_params_default(nrr_params* params);

@@ -28,6 +28,13 @@ Readings of Algorithm 2 used here:
   edge count, |V_G| = N, unless given explicitly.
 * eps defaults to 1e-5 times the bbox diagonal of source and target (the
   paper's 1e-5 on inputs scaled to unit diagonal).
+* Singular K (the paper is silent): when no point with a non-zero alignment
+  weight is influenced by a connected component of the deformation graph
+  (far from the target at a small nu_a, the Welsch weights underflow to 0),
+  the surrogate does not depend on that component's common translation. G
+  then keeps the component's summed translation of X^(k) (the minimiser
+  whose update has no component along the null space), and the pass
+  records the count of such components (PassRecord.n_singular).
 * Variants of Sec. 4.2 (Params.robust, Params.nu_fixed): "l2" replaces both
   Welsch functions by squared norms (all weights 1) and runs one stage (its
   energy has no nu); "l2r" keeps the nu_a schedule and gives an alignment
@@ -84,6 +91,7 @@ class PassRecord:
     nu_r: float
     stage: int
     max_disp: float = float("nan")
+    n_singular: int = 0             # free components of the pass's solve
 
 
 class Registration:
@@ -174,13 +182,19 @@ class Registration:
         a, b = self.weights()
         return model.total_energy(t, a, b), t
 
-    def mm_map(self, terms):
-        """G(X^k): minimiser of the surrogate built at the state ``terms``."""
+    def mm_map(self, terms, X=None):
+        """G(X^k): minimiser of the surrogate built at the state ``terms``
+        (evaluated at X^k = ``X``, default the current iterate). Components
+        of the graph without alignment weight keep their summed translation
+        of X^k (surrogate.free_components); their count is left in
+        ``self.last_free``."""
         alpha, beta = self.weights()
-        K, B, _ = surrogate.normal_equations(self.V, self.U, self.graph, terms,
-                                             self.nu_a, self.nu_r, alpha, beta,
-                                             robust=self.p.robust)
-        return surrogate.solve_normal_equations(K, B)
+        K, B, parts = surrogate.normal_equations(self.V, self.U, self.graph, terms,
+                                                 self.nu_a, self.nu_r, alpha, beta,
+                                                 robust=self.p.robust)
+        free = surrogate.free_components(self.graph, parts["wa"])
+        self.last_free = len(free)
+        return surrogate.solve_normal_equations(K, B, self.X if X is None else X, free)
 
     # -- one pass of Algorithm 2 -----------------------------------------
     def step(self) -> PassRecord | None:
@@ -206,6 +220,7 @@ class Registration:
             return rec
         self.E_prev = E
         G = self.mm_map(t)
+        rec.n_singular = self.last_free
         self.G_last = G.copy()
         X_new = self.aa.mix(G, self.X)
         self.n_solves += 1

@@ -20,6 +20,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg
 import scipy.sparse as sp
+import scipy.sparse.csgraph  # noqa: F401  (sp.csgraph)
 import scipy.sparse.linalg as spla
 
 
@@ -103,16 +104,67 @@ def normal_equations(V, U, graph, terms, nu_a, nu_r, alpha, beta, robust="welsch
     return K, np.asarray(B), dict(F=F, Q=Q, wa=wa, H=H, Y=Y, wr=wr, J=J, Z=Z)
 
 
-def solve_normal_equations(K, B) -> np.ndarray:
-    """Direct solve of K X = B (dense Cholesky for small systems, sparse LU
-    otherwise). Returns X in [N,12] layout."""
-    n = K.shape[0]
-    if n <= 4000:
-        c = scipy.linalg.cho_factor(K.toarray(), lower=True)
-        X = scipy.linalg.cho_solve(c, B)
+def free_components(graph, wa) -> list[np.ndarray]:
+    """Connected components of the deformation graph on which the alignment
+    term has no weight: every node j of the component has
+    a_j = sum_i w^a_i w_ij^2 = 0 exactly (the (t_j, t_j) entry of
+    F^T W_a F), which happens when the Welsch weights of all points the
+    component influences underflow to 0. The surrogate then does not depend
+    on the component's common translation (H annihilates it: D_ij does not
+    change when t_i and t_j move together), so K is singular. Returns the
+    node index arrays of those components (empty if K is regular in this
+    respect)."""
+    N = graph.N
+    a = np.zeros(N)
+    for s in range(graph.nidx.shape[1]):
+        j = graph.nidx[:, s]
+        m = j >= 0
+        np.add.at(a, j[m], np.asarray(wa, dtype=np.float64)[m] * graph.w[m, s] ** 2)
+    if len(graph.edges):
+        e = np.asarray(graph.edges)
+        adj = sp.coo_matrix((np.ones(len(e)), (e[:, 0], e[:, 1])), shape=(N, N))
     else:
-        X = spla.spsolve(K.tocsc(), B)
-    return np.asarray(X).reshape(n // 4, 4, 3).reshape(n // 4, 12)
+        adj = sp.coo_matrix((N, N))
+    n_comp, label = sp.csgraph.connected_components(adj, directed=False)
+    out = []
+    for c in range(n_comp):
+        nodes = np.nonzero(label == c)[0]
+        if np.all(a[nodes] == 0.0):
+            out.append(nodes)
+    return out
+
+
+def solve_normal_equations(K, B, X_prev=None, free=()) -> np.ndarray:
+    """Direct solve of K X = B (dense Cholesky for small systems, sparse LU
+    otherwise). Returns X in [N,12] layout.
+
+    ``free`` lists components whose common translation K does not determine
+    (free_components); for each, the solution keeps the component's summed
+    translation of ``X_prev`` ([N,12], the iterate the surrogate was built
+    at): the constraint sum_{j in C} t_j = sum_{j in C} t_j(X_prev) is
+    added with a Lagrange multiplier, per column of X, and the augmented
+    system [[K, N], [N^T, 0]] is solved directly."""
+    n = K.shape[0]
+    if len(free) == 0:
+        if n <= 4000:
+            c = scipy.linalg.cho_factor(K.toarray(), lower=True)
+            X = scipy.linalg.cho_solve(c, B)
+        else:
+            X = spla.spsolve(K.tocsc(), B)
+        return np.asarray(X).reshape(n // 4, 4, 3).reshape(n // 4, 12)
+    nc = len(free)
+    rows = np.concatenate([4 * np.asarray(C) + 3 for C in free])
+    cols = np.concatenate([np.full(len(C), k) for k, C in enumerate(free)])
+    Nm = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, nc))
+    Xp = np.asarray(X_prev, dtype=np.float64).reshape(n // 4, 4, 3).reshape(n, 3)
+    A = sp.bmat([[K, Nm], [Nm.T, None]], format="csc")
+    rhs = np.concatenate([np.asarray(B), Nm.T @ Xp])
+    if n <= 4000:
+        sol = scipy.linalg.solve(A.toarray(), rhs)
+    else:
+        sol = spla.spsolve(A, rhs)
+    X = np.asarray(sol)[:n]
+    return X.reshape(n // 4, 4, 3).reshape(n // 4, 12)
 
 
 def surrogate_value(V, U, graph, terms_k, X, nu_a, nu_r, alpha, beta):

@@ -836,7 +836,65 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     cl.sync();
 }
 
+// ---------------------------------------------------------------------------
+// Singular K (the paper is silent on it): a connected component of the node
+// graph on which no point has alignment weight (every node's alignment part
+// of its (t, t) entry of K, sum_i w^a_i w_ij^2, is exactly 0: the Welsch
+// weights of all the points it influences underflowed) leaves the
+// surrogate independent of the component's common translation, since
+// D_ij does not change when t_i and t_j move together. K is then singular
+// along that translation and the PCG solve leaves it (nearly) where the
+// warm start X^(k) had it. This kernel fixes it exactly: G keeps the
+// component's summed translation of X^(k),
+//     t_j(G) -= (1/|C|) sum_{k in C} (t_k(G) - t_k(X^(k)))   for j in C,
+// the minimiser of the surrogate whose update has no part along the null
+// space. One warp per component; fixed-order sums; counts the components.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) free_translation_kernel(DevProblem<T> d) {
+    NrrState* st = d.st;
+    if (st->done || st->skip || st->status != 0) return;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int comp = gwarp; comp < d.n_comp; comp += nwarps) {
+        const int c0 = d.comp_ptr[comp], c1 = d.comp_ptr[comp + 1];
+        bool weighted = false;
+        for (int k = c0 + lane; k < c1; k += 32) weighted = weighted || d.anode[d.comp_nodes[k]] != T(0);
+        if (__any_sync(0xffffffffu, weighted)) continue;
+        double sh[3] = {0.0, 0.0, 0.0};
+        for (int k = c0 + lane; k < c1; k += 32) {
+            const int j = d.comp_nodes[k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sh[a] += (double)d.G[12 * j + 9 + a] - (double)d.X[12 * j + 9 + a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sh[a] += __shfl_xor_sync(0xffffffffu, sh[a], o);
+            sh[a] /= (double)(c1 - c0);
+        }
+        for (int k = c0 + lane; k < c1; k += 32) {
+            const int j = d.comp_nodes[k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) d.G[12 * j + 9 + a] = (T)((double)d.G[12 * j + 9 + a] - sh[a]);
+        }
+        if (lane == 0) atomicAdd(&st->n_singular, 1);
+    }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t nrr_launch_free_translation(const DevProblem<T>& d, cudaStream_t s) {
+    if (d.n_comp < 1) return cudaSuccess;
+    const int grid = (d.n_comp + 7) / 8;
+    free_translation_kernel<T><<<grid, 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+template cudaError_t nrr_launch_free_translation<float>(const DevProblem<float>&, cudaStream_t);
+template cudaError_t nrr_launch_free_translation<double>(const DevProblem<double>&, cudaStream_t);
 
 template <typename T>
 cudaError_t nrr_launch_solve(const DevProblem<T>& d, int grid, cudaStream_t s, bool cooperative) {

@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
             st->E = E; st->E_align = A; st->E_reg = Rg; st->E_rot = O;
             st->n_passes += 1;
             st->solved = 0;
+            st->n_singular = 0;
             if (E > st->E_prev && !st->just_reverted) {
                 // Anderson iterate rejected: revert to the last MM result
                 st->kept = 0;
@@ -303,6 +304,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) assemble_ker
                 for (int t = 0; t < 12; ++t) accB[t] += __shfl_xor_sync(0xffffffffu, accB[t], o);
             }
             if (lane != 0) continue;
+            // alignment part of the (t, t) entry: 0 when no point that node n
+            // influences has alignment weight (singular K, kernels_solve.cu)
+            d.anode[n] = acc[9];
             T K16[16];
             {
                 int t = 0;

@@ -216,6 +216,15 @@ cudaError_t launch_solve_on(nrr_ctx* c, const DevProblem<T>& d) {
 template <typename T>
 cudaError_t launch_solve(nrr_ctx* c) { return launch_solve_on<T>(c, prob<T>(c)); }
 
+// The solve step of a pass: PCG, then the free-translation fix of singular
+// components.
+template <typename T>
+cudaError_t launch_solve_step(nrr_ctx* c) {
+    cudaError_t e = launch_solve<T>(c);
+    if (e != cudaSuccess) return e;
+    return nrr_launch_free_translation<T>(prob<T>(c), c->stream);
+}
+
 // Whether the cluster solve with C CTAs can run: every CTA's K rows fit in
 // shared memory and one such cluster can be resident. Fills the launch
 // parameters (K blocks per CTA, halo windows, dynamic shared memory). The
@@ -346,6 +355,8 @@ cudaError_t launch_pass(nrr_ctx* c) {
     if (e != cudaSuccess) return e;
     e = launch_solve<T>(c);
     if (e != cudaSuccess) return e;
+    e = nrr_launch_free_translation<T>(d, c->stream);
+    if (e != cudaSuccess) return e;
     return nrr_launch_aa<T>(d, c->grid_aa, c->stream);
 }
 
@@ -397,6 +408,8 @@ void fill_info(const NrrState& s, nrr_step_info* info) {
     info->pcg_iters = s.pcg_iters; info->aa_mk = s.aa_mk;
     info->n_passes = s.n_passes; info->n_solves = s.n_solves; info->n_rejected = s.n_rejected;
     info->status = s.status;
+    info->n_singular = s.n_singular;
+    info->warning = s.n_singular > 0 ? NRR_E_SINGULAR : NRR_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -573,6 +586,36 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
             }
     }
     tm.lap("BSR + contribution lists");
+    // connected components of the node graph (union-find over the edges),
+    // nodes listed by component in increasing order
+    std::vector<int> comp_ptr, comp_nodes;
+    {
+        std::vector<int> parent((size_t)N);
+        for (int j = 0; j < N; ++j) parent[(size_t)j] = j;
+        auto root = [&](int x) {
+            while (parent[(size_t)x] != x) {
+                parent[(size_t)x] = parent[(size_t)parent[(size_t)x]];
+                x = parent[(size_t)x];
+            }
+            return x;
+        };
+        for (size_t e = 0; e + 1 < g.edges.size(); e += 2) {
+            const int a = root(g.edges[e]), b = root(g.edges[e + 1]);
+            if (a != b) parent[(size_t)std::max(a, b)] = std::min(a, b);
+        }
+        std::vector<int> label((size_t)N, -1), count;
+        for (int j = 0; j < N; ++j) {
+            const int r = root(j);
+            if (label[(size_t)r] < 0) { label[(size_t)r] = (int)count.size(); count.push_back(0); }
+            label[(size_t)j] = label[(size_t)r];
+            count[(size_t)label[(size_t)j]]++;
+        }
+        comp_ptr.assign(count.size() + 1, 0);
+        for (size_t k = 0; k < count.size(); ++k) comp_ptr[k + 1] = comp_ptr[k] + count[k];
+        comp_nodes.assign((size_t)N, 0);
+        std::vector<int> fill(comp_ptr.begin(), comp_ptr.end() - 1);
+        for (int j = 0; j < N; ++j) comp_nodes[(size_t)fill[(size_t)label[(size_t)j]]++] = j;
+    }
     std::vector<T> ent_w(ent.size() * 2);
     for (size_t e = 0; e < ent.size(); ++e) {
         const int ii = ent[e] >> 6, sa = (ent[e] >> 3) & 7, sb = ent[e] & 7;
@@ -702,6 +745,13 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     CK(dalloc(c, &d.wr, (size_t)E2));
     CK(dalloc(c, &d.Rm, (size_t)N * 9));
     CK(dalloc(c, &d.Kv, (size_t)c->nblk * 16));
+    CK(dalloc(c, &d.anode, (size_t)N));
+    {
+        int *cp_, *cn_;
+        CK(upload(c, &cp_, comp_ptr)); d.comp_ptr = cp_;
+        CK(upload(c, &cn_, comp_nodes)); d.comp_nodes = cn_;
+        d.n_comp = (int)comp_ptr.size() - 1;
+    }
     CK(dalloc(c, &d.Bv, (size_t)N * 12));
     CK(dalloc(c, &d.r, (size_t)N * 12));
     CK(dalloc(c, &d.z, (size_t)N * 12));
@@ -1400,7 +1450,7 @@ nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[6]) {
                   : s == 1 ? nrr_launch_xterm<double>(d, NRR_MODE_PASS, c->stream)
                   : s == 2 ? nrr_launch_energy<double>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
                   : s == 3 ? nrr_launch_assemble<double>(d, c->grid_asm, c->stream)
-                  : s == 4 ? launch_solve<double>(c)
+                  : s == 4 ? launch_solve_step<double>(c)
                            : nrr_launch_aa<double>(d, c->grid_aa, c->stream);
             } else {
                 DevProblem<float>& d = c->df;
@@ -1408,7 +1458,7 @@ nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[6]) {
                   : s == 1 ? nrr_launch_xterm<float>(d, NRR_MODE_PASS, c->stream)
                   : s == 2 ? nrr_launch_energy<float>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
                   : s == 3 ? nrr_launch_assemble<float>(d, c->grid_asm, c->stream)
-                  : s == 4 ? launch_solve<float>(c)
+                  : s == 4 ? launch_solve_step<float>(c)
                            : nrr_launch_aa<float>(d, c->grid_aa, c->stream);
             }
             if (e == cudaSuccess) e = cudaEventRecord(ev[s + 1], c->stream);

@@ -95,6 +95,12 @@ struct DevProblem {
     const T* pbar;          // [3][P] sum_j w_ij p_j (constant part of Q_i)
     T* Kv;
     T* Bv;
+    T* anode;               // [N] alignment part of each node's (t, t) entry of K
+    // connected components of the node graph: nodes of component c are
+    // comp_nodes[comp_ptr[c] .. comp_ptr[c+1])
+    int n_comp;
+    const int* comp_ptr;
+    const int* comp_nodes;
     // PCG
     T* r;
     T* z;
@@ -135,9 +141,14 @@ template <typename T>
 cudaError_t nrr_launch_solve(const DevProblem<T>& d, int grid, cudaStream_t s, bool cooperative);
 template <typename T>
 cudaError_t nrr_launch_aa(const DevProblem<T>& d, int grid, cudaStream_t s);
+// Components of the node graph without alignment weight (K singular along
+// their common translation): G keeps the component's summed translation of
+// X (one warp per component; kernels_solve.cu).
+template <typename T>
+cudaError_t nrr_launch_free_translation(const DevProblem<T>& d, cudaStream_t s);
 // kernels one pass launches: closest points, X-only terms, energy, assembly,
-// solve, Anderson differences/Gram solve, Anderson mix
-constexpr int kNrrLaunchesPerPass = 7;
+// solve, free translations, Anderson differences/Gram solve, Anderson mix
+constexpr int kNrrLaunchesPerPass = 8;
 template <typename T>
 cudaError_t nrr_launch_gradient(const DevProblem<T>& d, double* grad_X, double* grad_v, const int* order,
                                 int grid, cudaStream_t s);

@@ -43,6 +43,7 @@ struct NrrState {
     int aa_m, aa_count, aa_head, aa_mk;
     int robust;             // nrr_robust (alpha, beta rule of the stages)
     int pcg_iters;
+    int n_singular;         // free components of the last solve (translation kept)
     int vk;                 // which v_hat buffer holds the kept iterate
     int vlast;              // which v_hat buffer was written last
     int have_vk;            // v_hat of a kept iterate exists

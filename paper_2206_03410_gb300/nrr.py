@@ -96,6 +96,8 @@ class NrrStepInfo(ctypes.Structure):
         ("n_solves", ctypes.c_int),
         ("n_rejected", ctypes.c_int),
         ("status", ctypes.c_int),
+        ("warning", ctypes.c_int),
+        ("n_singular", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -265,7 +267,8 @@ def nrr_reset(ctx):
     _check(load().nrr_reset(ctx), ctx)
 
 
-# the steps of a pass in launch order; the last is two kernels
+# the steps of a pass in launch order; "solve_kernel" is the PCG solve and
+# the free-translation kernel after it, the last is two kernels
 # (aa_dots_kernel, aa_mix_kernel)
 KERNELS = ("nn_kernel", "xterm_kernel", "energy_kernel", "assemble_kernel", "solve_kernel", "aa_kernels")
 

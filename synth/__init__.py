@@ -31,7 +31,7 @@ import numpy as np
 
 __all__ = [
     "Pair", "bumpy_sphere", "smooth_warp", "add_noise", "add_outliers",
-    "crop_halfspace", "depth_scene", "sphere_pair", "tiny_pair",
+    "crop_halfspace", "depth_scene", "sphere_pair", "tiny_pair", "island_pair",
     "workload", "WORKLOADS",
 ]
 
@@ -246,6 +246,27 @@ def tiny_pair(P: int, T: int, seed: int, noise: float = 0.0,
     return sphere_pair(P, T, n_bumps=4, amp=0.1, width=0.4, warp_cap=0.05,
                        noise=noise, outliers=outliers, crop=0.0, seed=seed,
                        same_samples=False)
+
+
+def island_pair(P: int, T: int, seed: int, n_island: int = 60,
+                offset: float = 2.5) -> Pair:
+    """A tiny pair whose source also holds an island: ``n_island`` source
+    points (a patch of the sphere around its +x pole) shifted by ``offset``
+    along +x, far from every target point. The island's points are appended
+    after the ``P`` surface points; its ground truth is the unshifted patch."""
+    base = tiny_pair(P, T, seed=seed, noise=0.002, outliers=0.0)
+    rng = np.random.default_rng(seed + 7919)
+    src = base.src.astype(np.float64)
+    pole = src[np.argmax(src[:, 0])]
+    d = np.linalg.norm(src - pole, axis=1)
+    patch = np.argsort(d)[:n_island]
+    island = src[patch] + np.array([offset, 0.0, 0.0])
+    island += 1e-4 * rng.standard_normal(island.shape)
+    src2 = np.concatenate([src, island])
+    nrm2 = np.concatenate([base.src_nrm, base.src_nrm[patch]])
+    gt2 = np.concatenate([base.gt, base.gt[patch]])
+    s32, n32, g32 = _f32(src2, nrm2, gt2)
+    return Pair(s32, n32, base.tgt, base.tgt_nrm, g32, name="island")
 
 
 # ---------------------------------------------------------------------------

@@ -27,7 +27,10 @@ def test_reference_arm_json_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
-    assert line["config"]["workload"] == "depth100k"
+    assert line["config"]["workload"].startswith("depth100k: P=100000 source, T=261104 target")
+    # ms_per_step is time actually spent; the value is an estimate from the sample
+    assert line["value_is_estimate"] is True and line["ms_per_step"] > 0
+    assert line["estimated_seconds_per_pass"] > line["ms_per_step"] / 1e3
 
 
 def test_traffic_is_null_once_the_kernel_source_changes(tmp_path, monkeypatch):

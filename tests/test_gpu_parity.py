@@ -272,6 +272,46 @@ def test_mixed_revert_keeps_last_mm_result(revert_run):
     reg.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_singular_system_keeps_free_translation(prec):
+    """An island of source points far from every target point at a small
+    nu_a: the Welsch weights of its points underflow to 0 (in double and in
+    float), its component of the deformation graph has no alignment weight
+    and K is singular along the component's common translation. Both the
+    oracle and the GPU keep the island's summed translation of X^(k) in G,
+    report the component (NRR_E_SINGULAR as a warning, n_singular = 1) and
+    go on. FP64: five passes against the oracle's trajectory (E, X 1e-9);
+    mixed: each pass's G against the oracle's minimiser from the GPU's own
+    iterate and closest points (1e-4)."""
+    nrr = _nrr()
+    pair = synth.island_pair(1200, 1300, seed=5)
+    kw = dict(radius=0.3, aa_m=5, nu_a=0.03, nu_r=0.2, nu_a_min=0.03)
+    ora = OReg(pair.src, pair.tgt, Params(**kw))
+    reg = _gpu(pair, prec, **kw)
+    island = np.nonzero(ora.graph.p[:, 0] > 2.0)[0]
+    for k in range(5):
+        X_eval = reg.transforms()
+        info = reg.step()
+        assert info.status == 0 and info.kept == 1 and info.solved == 1, k
+        assert info.n_singular == 1 and info.warning == nrr.NRR_E_SINGULAR, k
+        G = reg.mm_solution()
+        tG = G.reshape(-1, 4, 3)[island, 3, :].sum(axis=0)
+        tX = X_eval.reshape(-1, 4, 3)[island, 3, :].sum(axis=0)
+        assert np.abs(tG - tX).max() < (1e-12 if prec == "fp64" else 1e-5), k
+        if prec == "fp64":
+            rec = ora.step()
+            assert rec.kept and rec.n_singular == 1, k
+            assert abs(info.E - rec.E) < 1e-9 * rec.E, (k, info.E, rec.E)
+            assert relmax(reg.transforms(), ora.X) < 1e-9, (k, relmax(reg.transforms(), ora.X))
+        else:
+            rho, _ = reg.correspondence()
+            t = ora.terms(X_eval, rho=rho.astype(np.int64))
+            Go = ora.mm_map(t, X_eval)
+            assert ora.last_free == 1
+            assert relmax(G, Go) < TOL["mixed"]["X"], (k, relmax(G, Go))
+    reg.close()
+
+
 @pytest.mark.parametrize("stop", [dict(eps=1e9), dict(eps=1e9, rel_energy_tol=1e-300),
                                   dict(eps=1e9, rel_energy_tol=1.0), dict(rel_energy_tol=1e-3)])
 def test_stop_rules_match_oracle(stop):

@@ -684,3 +684,57 @@ def test_revert_target_is_the_last_mm_result():
     nxt = reg.step()
     assert nxt.kept
     assert nxt.E <= prev.E * (1 + 1e-12), (nxt.E, prev.E)
+
+
+def test_singular_system_keeps_free_translation():
+    """Singular K (the paper is silent): an island of source points far from
+    every target point at a small nu_a gets Welsch weights that underflow to
+    0, so the island's component of the deformation graph has no alignment
+    weight and K is singular along the component's common translation (an
+    exact null vector: the indicator of the component's t rows). The
+    oracle's minimiser then keeps the island's summed translation of X^k:
+    it equals the minimum-norm update X^k + K^+ (B - K X^k) from an SVD
+    least-squares solve, and every directional derivative of the surrogate
+    (summed term by term) vanishes at it. The same pair with the island on
+    the target has no free component."""
+    pair = synth.island_pair(1200, 1300, seed=5)
+    kw = dict(radius=0.3, aa_m=5, nu_a=0.03, nu_r=0.2, nu_a_min=0.03)
+    reg = Registration(pair.src, pair.tgt, Params(**kw))
+    g = reg.graph
+    island_nodes = np.nonzero(g.p[:, 0] > 2.0)[0]
+    assert len(island_nodes) >= 2
+    X = _near_identity_X(g.N, _rng(3), scale=0.01)
+    t = reg.terms(X)
+    a, b = reg.weights()
+    K, B, parts = S.normal_equations(reg.V, reg.U, g, t, reg.nu_a, reg.nu_r, a, b)
+    free = S.free_components(g, parts["wa"])
+    assert len(free) == 1 and np.array_equal(np.sort(free[0]), island_nodes)
+    n = K.shape[0]
+    null = np.zeros(n)
+    null[4 * island_nodes + 3] = 1.0
+    Kd = K.toarray()
+    assert np.abs(Kd @ null).max() < 1e-12 * np.abs(Kd).max()
+    G = S.solve_normal_equations(K, B, X, free)
+    Xp = X.reshape(-1, 4, 3).reshape(n, 3)
+    upd, *_ = np.linalg.lstsq(Kd, np.asarray(B) - Kd @ Xp, rcond=1e-10)
+    G_min = (Xp + upd).reshape(-1, 4, 3).reshape(-1, 12)
+    assert np.abs(G - G_min).max() < 1e-10 * np.abs(G_min).max()
+    tG = G.reshape(-1, 4, 3)[island_nodes, 3, :].sum(axis=0)
+    tX = X.reshape(-1, 4, 3)[island_nodes, 3, :].sum(axis=0)
+    assert np.abs(tG - tX).max() < 1e-12
+    f = lambda Y: S.surrogate_value(reg.V, reg.U, g, t, Y, reg.nu_a, reg.nu_r, a, b)
+    rng = _rng(9)
+    for _ in range(3):
+        D = rng.standard_normal(G.shape)
+        gG = (f(G + 1e-3 * D) - f(G - 1e-3 * D)) / 2e-3
+        gX = (f(X + 1e-3 * D) - f(X - 1e-3 * D)) / 2e-3
+        assert abs(gG) < 1e-6 * abs(gX), (gG, gX)
+    # a pass of Algorithm 2 records the free component
+    rec = reg.step()
+    assert rec.kept and rec.n_singular == 1
+    # the island on the target: no free component, the plain solve
+    near = synth.island_pair(1200, 1300, seed=5, offset=0.0)
+    reg2 = Registration(near.src, near.tgt, Params(**kw))
+    t2 = reg2.terms()
+    _, _, parts2 = S.normal_equations(reg2.V, reg2.U, reg2.graph, t2, reg2.nu_a, reg2.nu_r, a, b)
+    assert S.free_components(reg2.graph, parts2["wa"]) == []
