@@ -333,7 +333,10 @@ nrr_status nrr_get_mm_solution(nrr_ctx* ctx, double* G);
  * search: recorded only if the context was created with the environment
  * variable NRR_NN_STATS set (otherwise *n_warps = 0). out [max_warps][4]
  * (host or device) = {SM cycles, super tiles visited, leaves staged, leaves
- * scanned} per warp; *n_warps receives the number of warps of a search. */
+ * scanned} per warp; *n_warps receives the number of warps of a search.
+ * With the tensor-core search the rows are per CTA of 128 queries: {SM
+ * cycles, candidate leaves, chunks of 128 candidates (MMAs), queries searched
+ * exactly because their window exceeded the kept candidates}. */
 nrr_status nrr_get_search_stats(nrr_ctx* ctx, unsigned long long* out, int64_t max_warps,
                                 int64_t* n_warps);
 
@@ -418,21 +421,30 @@ typedef struct {
                                   chosen shapes (nrr_tune; 0 otherwise)     */
     double pass_ms;            /* measured mean batch pass (nrr_batch_tune) */
     int    launches_per_pass;  /* kernels one pass launches                 */
+    int    nn_tensor_cores;    /* 1: closest points by the tensor-core
+                                  candidate search (mixed path only): BF16
+                                  split-precision distance tiles on the
+                                  tensor cores choose each query's
+                                  candidates, an exact float re-rank picks
+                                  the winner; the results are bitwise those
+                                  of the exact search (nn_lanes_per_query is
+                                  then unused). 0: the exact pruned search   */
 } nrr_launch_config;
 
 /* Current launch shapes of a context (ms fields 0). */
 nrr_status nrr_get_launch_config(nrr_ctx* ctx, nrr_launch_config* out);
 
-/* Sets the launch shapes (NRR_E_INVALID for lanes not in {1,2,4,8} or a
- * cluster that does not fit this problem or device) and recaptures the
- * pass graph. Results stay within the tolerances of every shape; the
+/* Sets the launch shapes (NRR_E_INVALID for lanes not in {1,2,4,8}, a
+ * cluster that does not fit this problem or device, or nn_tensor_cores on
+ * an FP64 context) and recaptures the pass graph. Results stay within the tolerances of every shape; the
  * floating-point summation order, hence the last bits, depend on it. */
 nrr_status nrr_set_launch_config(nrr_ctx* ctx, const nrr_launch_config* cfg);
 
 /* Autotuner: picks the launch shapes by timing them on this context's own
  * problem. It runs the first pass of Algorithm 2 from X = identity, then
  * times reps (<= 0: 5) launches of the closest-point kernel for every
- * lanes-per-query value and of the PCG solve of that pass's system (from the
+ * lanes-per-query value and of the tensor-core candidate search (mixed path)
+ * and of the PCG solve of that pass's system (from the
  * pass's own warm start) for every cluster size that fits (and the
  * grid-wide solve), with CUDA events on the
  * context's stream, keeps the fastest of each and restarts the solve (as

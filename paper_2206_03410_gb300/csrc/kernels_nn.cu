@@ -14,6 +14,8 @@
 // that could win or tie; the distance itself is evaluated in T. Ties go to
 // the lowest caller index. Work per query is a few hundred distance
 // evaluations instead of T; the kernel is bound by issue slots.
+#include <cuda_bf16.h>
+
 #include "nrr_device.cuh"
 
 namespace {
@@ -112,6 +114,95 @@ __device__ __forceinline__ T group_min(T v) {
     return v;
 }
 
+// The query of source point i: v_hat_i of Eq. (deformed_position) at the
+// pass's iterate (or at Xeval), or v_i itself (MODE_RAW). One definition
+// for both closest-point kernels, so that they see the same query bits.
+template <typename T, int MODE>
+__device__ __forceinline__ void query_point(const DevProblem<T>& d, int i, T& qx, T& qy, T& qz) {
+    const int P = d.P;
+    const T vx = d.v[i], vy = d.v[P + i], vz = d.v[2 * P + i];
+    if (MODE == NRR_MODE_RAW) {
+        qx = vx; qy = vy; qz = vz;
+        return;
+    }
+    qx = 0; qy = 0; qz = 0;
+    const T* X = (MODE == NRR_MODE_EVAL) ? d.Xeval : d.X;
+    for (int s = d.infl_ptr[i], e = d.infl_ptr[i + 1]; s < e; ++s) {
+        const int j = d.infl_node[s];
+        const T w = d.infl_w[s];
+        const T* Xj = X + 12 * j;
+        const T px = d.p[3 * j], py = d.p[3 * j + 1], pz = d.p[3 * j + 2];
+        const T dx = vx - px, dy = vy - py, dz = vz - pz;
+        // rows 0..2 of the block hold A_j^T, row 3 holds t_j
+        const T ox = Xj[0] * dx + Xj[3] * dy + Xj[6] * dz + px + Xj[9];
+        const T oy = Xj[1] * dx + Xj[4] * dy + Xj[7] * dz + py + Xj[10];
+        const T oz = Xj[2] * dx + Xj[5] * dy + Xj[8] * dz + pz + Xj[11];
+        qx += w * ox; qy += w * oy; qz += w * oz;
+    }
+}
+
+// Outputs of a closest-point search (rho, d^2, the closest coordinates u and
+// v_hat in the non-kept buffer) for the thread that owns query i (``write``),
+// and in a pass the stopping test of Algorithm 2: the largest displacement
+// of v_hat from the kept iterate's, reduced over the grid (the CTA's kWarps
+// warps, then a 64-bit atomic max of the bits of non-negative doubles); the
+// last CTA to finish ends the stage when the displacement is below eps or
+// the stage has run I_max solves. Shared by both closest-point kernels (256
+// threads per CTA).
+template <typename T, int MODE>
+__device__ __forceinline__ void search_outputs(const DevProblem<T>& d, int i, bool write, int bidx, T best, T bx,
+                                               T by, T bz, T qx, T qy, T qz, double* s_disp, int* s_last) {
+    NrrState* st = d.st;
+    const int P = d.P;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wb = (MODE == NRR_MODE_RAW) ? 0 : (st->vk ^ 1);
+    double dv2 = 0.0;
+    if (write) {
+        d.rho[i] = bidx;
+        d.d2[i] = best;
+        d.u[i] = bx; d.u[P + i] = by; d.u[2 * P + i] = bz;
+        if (MODE != NRR_MODE_RAW) {
+            T* vh = d.vhat + (size_t)wb * 3 * P;
+            vh[i] = qx; vh[P + i] = qy; vh[2 * P + i] = qz;
+            if (MODE == NRR_MODE_PASS && st->pending_stop && st->have_vk) {
+                const T* vk = d.vhat + (size_t)(wb ^ 1) * 3 * P;
+                const double dx = (double)qx - (double)vk[i];
+                const double dy = (double)qy - (double)vk[P + i];
+                const double dz = (double)qz - (double)vk[2 * P + i];
+                dv2 = dx * dx + dy * dy + dz * dz;
+            }
+        }
+    }
+    if constexpr (MODE == NRR_MODE_PASS) {
+        for (int o = 16; o > 0; o >>= 1) dv2 = fmax(dv2, __shfl_xor_sync(0xffffffffu, dv2, o));
+        if (lane == 0) s_disp[warp] = dv2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = s_disp[0];
+            for (int w = 1; w < kWarps; ++w) m = fmax(m, s_disp[w]);
+            // non-negative doubles order like their bit patterns
+            atomicMax(&st->disp_bits, (unsigned long long)__double_as_longlong(m));
+            __threadfence();
+            const unsigned t = atomicAdd(&st->cnt_nn, 1u);
+            *s_last = (t == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (!*s_last || threadIdx.x != 0) return;
+        __threadfence();
+        st->cnt_nn = 0;
+        st->vlast = wb;
+        if (st->pending_stop) {
+            const double disp = sqrt(__longlong_as_double((long long)atomicAdd(&st->disp_bits, 0ull)));
+            st->max_disp = disp;
+            st->pending_stop = 0;
+            // with an energy test the stage ends on it (or I_max) only
+            if ((st->rel_tol <= 0 && disp < st->eps) || st->n_solves_stage >= st->max_iters_stage)
+                nrr_end_stage(st);
+        }
+        st->disp_bits = 0ull;
+    }
+}
+
 // LPQ lanes serve one query: a warp serves 32 / LPQ curve-consecutive source
 // points, and each lane scans 32 / LPQ of the 32 points of every leaf that
 // its query needs. Splitting a query over several lanes shortens the serial
@@ -138,26 +229,7 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
 
     // ---- query point: v_hat_i (Eq. deformed_position) or v_i -------------
     T qx = 0, qy = 0, qz = 0;
-    if (valid) {
-        T vx = d.v[i], vy = d.v[P + i], vz = d.v[2 * P + i];
-        if (MODE == NRR_MODE_RAW) {
-            qx = vx; qy = vy; qz = vz;
-        } else {
-            const T* X = (MODE == NRR_MODE_EVAL) ? d.Xeval : d.X;
-            for (int s = d.infl_ptr[i], e = d.infl_ptr[i + 1]; s < e; ++s) {
-                const int j = d.infl_node[s];
-                const T w = d.infl_w[s];
-                const T* Xj = X + 12 * j;
-                const T px = d.p[3 * j], py = d.p[3 * j + 1], pz = d.p[3 * j + 2];
-                const T dx = vx - px, dy = vy - py, dz = vz - pz;
-                // rows 0..2 of the block hold A_j^T, row 3 holds t_j
-                const T ox = Xj[0] * dx + Xj[3] * dy + Xj[6] * dz + px + Xj[9];
-                const T oy = Xj[1] * dx + Xj[4] * dy + Xj[7] * dz + py + Xj[10];
-                const T oz = Xj[2] * dx + Xj[5] * dy + Xj[8] * dz + pz + Xj[11];
-                qx += w * ox; qy += w * oy; qz += w * oz;
-            }
-        }
-    }
+    if (valid) query_point<T, MODE>(d, i, qx, qy, qz);
     // ---- initial candidate: the previous correspondence --------------------
     T bx = 0, by = 0, bz = 0, best = 0;
     int bidx = 0x7fffffff;
@@ -305,53 +377,474 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
         o[1] = n_super; o[2] = n_staged; o[3] = n_scanned;
     }
 
-    // ---- outputs ------------------------------------------------------------
-    const int wb = (MODE == NRR_MODE_RAW) ? 0 : (st->vk ^ 1);
-    double dv2 = 0.0;
-    if (valid && sub == 0) {
-        d.rho[i] = bidx;
-        d.d2[i] = best;
-        d.u[i] = bx; d.u[P + i] = by; d.u[2 * P + i] = bz;
-        if (MODE != NRR_MODE_RAW) {
-            T* vh = d.vhat + (size_t)wb * 3 * P;
-            vh[i] = qx; vh[P + i] = qy; vh[2 * P + i] = qz;
-            if (MODE == NRR_MODE_PASS && st->pending_stop && st->have_vk) {
-                const T* vk = d.vhat + (size_t)(wb ^ 1) * 3 * P;
-                const double dx = (double)qx - (double)vk[i];
-                const double dy = (double)qy - (double)vk[P + i];
-                const double dz = (double)qz - (double)vk[2 * P + i];
-                dv2 = dx * dx + dy * dy + dz * dz;
+    // ---- outputs and the stopping test ----------------------------------------
+    search_outputs<T, MODE>(d, i, valid && sub == 0, bidx, best, bx, by, bz, qx, qy, qz, s_disp, &s_last);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core candidate search (float path). The same outputs as nn_kernel,
+// bit for bit: the closest point rho(i) (ties to the lowest caller index),
+// its float squared distance and coordinates, v_hat and the stopping test.
+//
+// A CTA serves 128 curve-consecutive source points (the M = 128 rows of a
+// tcgen05.mma). Its candidate target points are the union of the leaves
+// that any of its eight 16-query boxes may need under the queries' current
+// bounds (the distance to the previous correspondence), in chunks of four
+// leaves (N = 128 columns). For every chunk one MMA (kind::f16, BF16 inputs,
+// FP32 accumulator in tensor memory) forms all 128 x 128 approximate squared
+// distances at once, as one dot product of K = 16:
+//   query row     [-2 x_hi, -2 x_hi, -2 x_lo, 1, 1, |x|^2_hi, |x|^2_lo, 0...]
+//   candidate row [ y_hi,    y_lo,    y_hi, |y|^2_hi, |y|^2_lo, 1, 1, 0...]
+// with x, y the float coordinates minus the CTA's centre and every value
+// split into two BF16 parts (hi + lo), so that the product carries about 16
+// significant bits: |x - y|^2 = |x|^2 + |y|^2 - 2 x.y up to
+// delta = 2^-14 (|x| + R)^2, R the largest |y| among the candidates (the
+// split and the FP32 accumulation err by less than a quarter of that).
+// The epilogue reads each accumulator from tensor memory (tcgen05.ld) and
+// keeps, per query and half of the columns, the four smallest approximate
+// distances. The window of candidates that can hold the exact winner is
+// then {d~ <= (d~_min + delta)(1 + 4e-6) + delta} (4e-6 covers the float
+// rounding of the exact distances): its members are re-ranked with the
+// exact float distance and the (d^2, caller index) keys of nn_kernel. A
+// query whose window may hold more than its four kept candidates is
+// searched exactly, alone, with nn_kernel's pruning. So the result is the
+// exact search's result; the tensor cores only choose where to look.
+//
+// Pipeline: two accumulators (256 tensor-memory columns) and two candidate
+// tiles in shared memory; the MMA of chunk c runs while the epilogue reads
+// chunk c - 1. All waits on the MMA's completion are bounded: after about
+// two seconds the kernel records NRR_E_TIMEOUT and skips the rest of its
+// work (freeing its tensor memory).
+// ---------------------------------------------------------------------------
+namespace tcs {
+constexpr int kQ = 128;                 // queries per CTA: the MMA's M
+constexpr int kN = 128;                 // candidates per chunk: the MMA's N
+constexpr int kLeaves = kN / NRR_LEAF;  // leaves per chunk
+constexpr int kCta = 256;               // warps w and w + 4 read the same tensor-memory lanes
+constexpr int kGroups = 8;              // query boxes of 16 queries for the candidate test
+constexpr int kListCap = 512;           // candidate leaves collected before they are processed
+constexpr int kTop = 4;                 // best approximate candidates kept per query and half
+constexpr unsigned kTmemCols = 2 * kN;  // two accumulators
+constexpr float kDelta = 1.0f / 16384.0f;
+// byte offset of element k of row r of a 128 x 16 BF16 operand tile in the
+// tensor cores' K-major layout without swizzle: 8-row x 16-byte core
+// matrices, the two along K 128 bytes apart, row groups 256 bytes apart
+__host__ __device__ constexpr int tile_off(int r, int kc) { return (r >> 3) * 256 + kc * 128 + (r & 7) * 16; }
+// instruction descriptor of kind::f16: D f32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr unsigned kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kN >> 3) << 17) |
+                            ((unsigned)(kQ >> 4) << 24);
+constexpr long long kSpin = 4000000000LL;   // clock64 cycles of a bounded wait
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading (K) byte offset
+// 128, stride (8-row group) byte offset 256, the fixed version bits 46-48 =
+// 1, no swizzle
+__device__ __forceinline__ unsigned long long tile_desc(const void* tile) {
+    unsigned long long dsc = (unsigned long long)((smem_addr(tile) & 0x3FFFFu) >> 4);
+    dsc |= (unsigned long long)(128u >> 4) << 16;
+    dsc |= (unsigned long long)(256u >> 4) << 32;
+    dsc |= 1ull << 46;
+    return dsc;
+}
+
+__device__ __forceinline__ unsigned bf16_bits(float x) { return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_val(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ unsigned pack2(unsigned lo, unsigned hi) { return lo | (hi << 16); }
+
+__device__ __forceinline__ bool mbar_done(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of an MMA completion barrier; false if it
+// timed out (the caller records the failure).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* b, unsigned parity) {
+    if (mbar_done(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_done(b, parity))
+        if (clock64() - t0 > kSpin) return false;
+    return true;
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(unsigned addr, float (&v)[32]) {
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(addr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// sorted insertion into a query's four best (approximate distance, slot)
+__device__ __forceinline__ void top_insert(float (&tv)[kTop], int (&ts)[kTop], float v, int slot) {
+    if (!(v < tv[kTop - 1])) return;
+    tv[kTop - 1] = v;
+    ts[kTop - 1] = slot;
+#pragma unroll
+    for (int k = kTop - 1; k > 0; --k) {
+        if (tv[k] < tv[k - 1]) {
+            const float fv = tv[k]; tv[k] = tv[k - 1]; tv[k - 1] = fv;
+            const int fs = ts[k]; ts[k] = ts[k - 1]; ts[k - 1] = fs;
+        }
+    }
+}
+}  // namespace tcs
+
+template <int MODE>
+__global__ void __launch_bounds__(tcs::kCta, 2) nn_tc_kernel(DevProblem<float> d) {
+    using namespace tcs;
+    __shared__ __align__(1024) unsigned char sA[kQ * 32];
+    __shared__ __align__(1024) unsigned char sB[2][kN * 32];
+    __shared__ int s_list[kListCap];
+    __shared__ int s_slot[3][kN];          // target slot of each candidate column (-1: none), by chunk % 3
+    __shared__ float s_gb[kGroups][8];     // query boxes and their bounds
+    __shared__ float s_tv[kQ][kTop];       // second half's best, for the merge
+    __shared__ int s_ts[kQ][kTop];
+    __shared__ float s_ext[kQ / 32][6];
+    __shared__ float s_ctr[3];
+    __shared__ int s_cnt[kCta / 32];
+    __shared__ unsigned s_Ru;              // bits of the largest candidate |y| (non-negative float)
+    __shared__ unsigned s_tslot;
+    __shared__ int s_fail;
+    __shared__ __align__(8) unsigned long long s_mbar[2];
+    __shared__ double s_disp[kCta / 32];
+    __shared__ int s_last;
+    NrrState* st = d.st;
+    if (MODE == NRR_MODE_PASS && st->done) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & (kQ - 1);
+    const bool owner = tid < kQ;           // owns query `row`; the other half helps the epilogue
+    const int half = tid >> 7;
+    const int P = d.P;
+    const int i = blockIdx.x * kQ + row;
+    const bool valid = owner && i < P;
+    const long long t_start = clock64();
+
+    // ---- queries and their initial candidate (the previous correspondence)
+    float qx = 0.f, qy = 0.f, qz = 0.f, bx = 0.f, by = 0.f, bz = 0.f, best = 0.f;
+    unsigned long long bkey = 0ull;
+    int bpos = -1;
+    if (valid) {
+        query_point<float, MODE>(d, i, qx, qy, qz);
+        bx = d.u[i]; by = d.u[P + i]; bz = d.u[2 * P + i];
+        best = sqdist(qx, qy, qz, bx, by, bz);
+        bkey = cand_key(best, d.rho[i]);
+    }
+    // ---- the CTA's centre (midpoint of its queries' box) and query boxes
+    if (owner) {
+        float e[6] = {valid ? qx : INFINITY, valid ? qy : INFINITY, valid ? qz : INFINITY,
+                      valid ? qx : -INFINITY, valid ? qy : -INFINITY, valid ? qz : -INFINITY};
+        float ub = valid ? ub_f(best) : 0.f;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) e[k] = fminf(e[k], __shfl_xor_sync(0xffffffffu, e[k], o));
+#pragma unroll
+            for (int k = 3; k < 6; ++k) e[k] = fmaxf(e[k], __shfl_xor_sync(0xffffffffu, e[k], o));
+            ub = fmaxf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
+        }
+        if ((lane & 15) == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s_gb[row >> 4][k] = e[k];
+            s_gb[row >> 4][6] = ub;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) e[k] = fminf(e[k], __shfl_xor_sync(0xffffffffu, e[k], 16));
+#pragma unroll
+        for (int k = 3; k < 6; ++k) e[k] = fmaxf(e[k], __shfl_xor_sync(0xffffffffu, e[k], 16));
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s_ext[warp][k] = e[k];
+        }
+    }
+    if (tid == 0) {
+        s_Ru = 0u;
+        s_fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid < 3) {
+        float lo = s_ext[0][tid], hi = s_ext[0][3 + tid];
+        for (int w = 1; w < kQ / 32; ++w) { lo = fminf(lo, s_ext[w][tid]); hi = fmaxf(hi, s_ext[w][3 + tid]); }
+        s_ctr[tid] = 0.5f * (lo + hi);
+    }
+    __syncthreads();
+    const unsigned taddr = s_tslot;
+    const float cx = s_ctr[0], cy = s_ctr[1], cz = s_ctr[2];
+    // ---- query rows of the A operand (zeros for rows without a query)
+    float xn = 0.f;   // |x| of this query, for its error bound
+    if (owner) {
+        unsigned w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (valid) {
+            const float x0 = qx - cx, x1 = qy - cy, x2 = qz - cz;
+            const float h0 = bf16_val(x0), h1 = bf16_val(x1), h2 = bf16_val(x2);
+            const float nq = x0 * x0 + x1 * x1 + x2 * x2;
+            const float nh = bf16_val(nq);
+            xn = sqrtf(nq);
+            const unsigned a0 = bf16_bits(-2.f * h0), a1 = bf16_bits(-2.f * h1), a2 = bf16_bits(-2.f * h2);
+            const unsigned l0 = bf16_bits(-2.f * (x0 - h0)), l1 = bf16_bits(-2.f * (x1 - h1)),
+                           l2 = bf16_bits(-2.f * (x2 - h2));
+            const unsigned one = bf16_bits(1.f);
+            // k 0..7: -2x_hi, -2x_hi(0..1); k 8..15: -2x_hi(2), -2x_lo, 1, 1, |x|^2 hi, lo, 0
+            w[0] = pack2(a0, a1); w[1] = pack2(a2, a0); w[2] = pack2(a1, a2); w[3] = pack2(l0, l1);
+            w[4] = pack2(l2, one); w[5] = pack2(one, bf16_bits(nh)); w[6] = pack2(bf16_bits(nq - nh), 0u);
+            w[7] = 0u;
+        }
+        *reinterpret_cast<uint4*>(sA + tile_off(row, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(sA + tile_off(row, 1)) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+
+    const unsigned long long descA = tile_desc(sA);
+    float tv[kTop];
+    int ts[kTop];
+#pragma unroll
+    for (int k = 0; k < kTop; ++k) { tv[k] = INFINITY; ts[k] = -1; }
+    unsigned phase[2] = {0u, 0u};
+    int chunk = 0;          // chunks issued so far
+    int n_cand = 0;         // candidate leaves (statistics)
+    bool failed = false;
+
+    // epilogue of chunk ch (accumulator ch & 1): every thread reads 64
+    // columns of its query's row and keeps the four smallest. (The column
+    // slots of a chunk sit in s_slot[ch % 3]: the chunk after next writes
+    // its own while a slow thread may still read these.)
+    auto epilogue = [&](int ch) {
+        const int b = ch & 1;
+        if (!failed) {
+            // warp-uniform outcome: tcgen05.ld needs the whole warp
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&s_mbar[b], phase[b]));
+            if (!ok) {
+                failed = true;
+                s_fail = 1;
+                atomicExch(&st->status, (int)NRR_E_TIMEOUT);
+            }
+        }
+        phase[b] ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (failed) return;
+        const unsigned base = taddr + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(b * kN + half * 64);
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            float v[32];
+            tmem_ld32(base + (unsigned)(part * 32), v);
+            if (valid || (!owner && blockIdx.x * kQ + row < P)) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int slot = s_slot[ch % 3][half * 64 + part * 32 + j];
+                    if (slot >= 0) top_insert(tv, ts, v[j], slot);
+                }
+            }
+        }
+    };
+
+    // chunks of the collected leaves: build the candidate rows, issue the
+    // MMA, and run the epilogue of the previous chunk behind it
+    auto process = [&](int nlist) {
+        const int nch = (nlist + kLeaves - 1) / kLeaves;
+        for (int c = 0; c < nch; ++c) {
+            const int b = chunk & 1;
+            {
+                const int r = tid >> 1, kc = tid & 1;
+                const int li = c * kLeaves + (r >> 5);
+                unsigned w[4] = {0u, 0u, 0u, 0u};
+                int slot = -1;
+                if (li < nlist) {
+                    const int sl = s_list[li] * NRR_LEAF + (r & 31);
+                    const TPoint<float> pt = d.tpts[sl];
+                    if (pt.idx != 0x7fffffff) {   // not a padding point
+                        slot = sl;
+                        const float y0 = pt.x - cx, y1 = pt.y - cy, y2 = pt.z - cz;
+                        const float h0 = bf16_val(y0), h1 = bf16_val(y1), h2 = bf16_val(y2);
+                        const float ny = y0 * y0 + y1 * y1 + y2 * y2;
+                        const float nh = bf16_val(ny);
+                        const unsigned a0 = bf16_bits(h0), a1 = bf16_bits(h1), a2 = bf16_bits(h2);
+                        const unsigned one = bf16_bits(1.f);
+                        if (kc == 0) {
+                            // k 0..7: y_hi, y_lo, y_hi(0..1)
+                            w[0] = pack2(a0, a1);
+                            w[1] = pack2(a2, bf16_bits(y0 - h0));
+                            w[2] = pack2(bf16_bits(y1 - h1), bf16_bits(y2 - h2));
+                            w[3] = pack2(a0, a1);
+                            atomicMax(&s_Ru, __float_as_uint(sqrtf(ny)));
+                        } else {
+                            // k 8..15: y_hi(2), |y|^2 hi, lo, 1, 1, 0, 0, 0
+                            w[0] = pack2(a2, bf16_bits(nh));
+                            w[1] = pack2(bf16_bits(ny - nh), one);
+                            w[2] = pack2(one, 0u);
+                            w[3] = 0u;
+                        }
+                    }
+                }
+                *reinterpret_cast<uint4*>(sB[b] + tile_off(r, kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+                if (kc == 0) s_slot[chunk % 3][r] = slot;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (tid == 0 && !s_fail) {
+                const unsigned long long descB = tile_desc(sB[b]);
+                const unsigned dcol = taddr + (unsigned)(b * kN);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+                    "l"(descA), "l"(descB), "r"(kIdesc), "r"(0u)
+                    : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_addr(&s_mbar[b]))
+                             : "memory");
+            }
+            if (c > 0) epilogue(chunk - 1);
+            ++chunk;
+        }
+        if (nch > 0) epilogue(chunk - 1);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    };
+
+    // ---- candidate leaves: eight super tiles per round, one per warp; a
+    // super tile (then a leaf) is a candidate if it comes within the bound
+    // of any query box; leaves are listed in super-tile, then leaf order
+    auto box_ok = [&](const float* box) {
+        bool c = false;
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g)
+            c = c || box_gap2(s_gb[g][0], s_gb[g][1], s_gb[g][2], s_gb[g][3], s_gb[g][4], s_gb[g][5], box) <= s_gb[g][6];
+        return c;
+    };
+    int nlist = 0;
+    for (int s0 = 0; s0 < d.n_supers; s0 += kCta / 32) {
+        const int S = s0 + warp;
+        bool gs = false;
+        if (S < d.n_supers && lane < kGroups) {
+            const float* sbx = d.super_box + 6 * S;
+            gs = box_gap2(s_gb[lane][0], s_gb[lane][1], s_gb[lane][2], s_gb[lane][3], s_gb[lane][4], s_gb[lane][5],
+                          sbx) <= s_gb[lane][6];
+        }
+        unsigned lmask = 0u;
+        if (__any_sync(0xffffffffu, gs)) {
+            const int L = S * 32 + lane;
+            const bool lc = L < d.n_leaves && box_ok(d.leaf_box + 6 * L);
+            lmask = __ballot_sync(0xffffffffu, lc);
+        }
+        if (lane == 0) s_cnt[warp] = __popc(lmask);
+        __syncthreads();
+        int off = nlist, total = 0;
+#pragma unroll
+        for (int w = 0; w < kCta / 32; ++w) {
+            const int cw = s_cnt[w];
+            if (w < warp) off += cw;
+            total += cw;
+        }
+        if (lmask & (1u << lane)) s_list[off + __popc(lmask & ((1u << lane) - 1u))] = S * 32 + lane;
+        __syncthreads();
+        nlist += total;
+        n_cand += total;
+        if (nlist > kListCap - 32 * (kCta / 32) || s0 + kCta / 32 >= d.n_supers) {
+            process(nlist);
+            nlist = 0;
+        }
+    }
+
+    // ---- merge the halves' best four; window; exact re-rank
+    if (!owner) {
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) { s_tv[row][k] = tv[k]; s_ts[row][k] = ts[k]; }
+    }
+    __syncthreads();
+    bool fallback = false;
+    if (valid) {
+#pragma unroll
+        for (int k = 0; k < kTop; ++k) top_insert(tv, ts, s_tv[row][k], s_ts[row][k]);
+        const float Ru = __uint_as_float(s_Ru);
+        const float r = __fadd_ru(xn, Ru);
+        const float delta = __fmul_ru(kDelta, __fmul_ru(r, r));
+        const float T = __fadd_ru(__fmul_ru(__fadd_ru(tv[0], delta), 1.000004f), delta);
+        fallback = failed || tv[kTop - 1] <= T;
+        if (!fallback) {
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) {
+                if (ts[k] >= 0 && tv[k] <= T) {
+                    const TPoint<float> c = d.tpts[ts[k]];
+                    const unsigned long long key = cand_key(sqdist(qx, qy, qz, c.x, c.y, c.z), c.idx);
+                    if (key < bkey) { bkey = key; bpos = ts[k]; }
+                }
+            }
+        } else {
+            // exact search of this query alone, pruned by its own box
+            float ub = ub_f(__uint_as_float((unsigned)(bkey >> 32)));
+            for (int S = 0; S < d.n_supers; ++S) {
+                if (box_gap2(qx, qy, qz, qx, qy, qz, d.super_box + 6 * S) > ub) continue;
+                for (int L = S * 32; L < min(d.n_leaves, S * 32 + 32); ++L) {
+                    if (box_gap2(qx, qy, qz, qx, qy, qz, d.leaf_box + 6 * L) > ub) continue;
+                    for (int j = 0; j < NRR_LEAF; ++j) {
+                        const TPoint<float> c = d.tpts[L * NRR_LEAF + j];
+                        const unsigned long long key = cand_key(sqdist(qx, qy, qz, c.x, c.y, c.z), c.idx);
+                        if (key < bkey) { bkey = key; bpos = L * NRR_LEAF + j; }
+                    }
+                    ub = ub_f(__uint_as_float((unsigned)(bkey >> 32)));
+                }
             }
         }
     }
-    if constexpr (MODE == NRR_MODE_PASS) {
-    // ---- stopping test of Algorithm 2 (max displacement) --------------------
-    for (int o = 16; o > 0; o >>= 1) dv2 = fmax(dv2, __shfl_xor_sync(0xffffffffu, dv2, o));
-    if (lane == 0) s_disp[warp] = dv2;
+    // ---- tensor memory back, statistics, outputs
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = s_disp[0];
-        for (int w = 1; w < kWarps; ++w) m = fmax(m, s_disp[w]);
-        // non-negative doubles order like their bit patterns
-        atomicMax(&st->disp_bits, (unsigned long long)__double_as_longlong(m));
-        __threadfence();
-        const unsigned t = atomicAdd(&st->cnt_nn, 1u);
-        s_last = (t == gridDim.x - 1);
+    if (warp == 0) {
+        if (s_fail) {
+            // let an MMA still in flight finish (bounded) before freeing
+            const long long t0 = clock64();
+            while (clock64() - t0 < 200000LL) {
+            }
+        }
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols) : "memory");
     }
-    __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    __threadfence();
-    st->cnt_nn = 0;
-    st->vlast = wb;
-    if (st->pending_stop) {
-        const double disp = sqrt(__longlong_as_double((long long)atomicAdd(&st->disp_bits, 0ull)));
-        st->max_disp = disp;
-        st->pending_stop = 0;
-        // with an energy test the stage ends on it (or I_max) only
-        if ((st->rel_tol <= 0 && disp < st->eps) || st->n_solves_stage >= st->max_iters_stage) nrr_end_stage(st);
+    if (d.nn_stats != nullptr) {
+        const int nfb = __syncthreads_count(fallback);
+        if (tid == 0) {
+            unsigned long long* o = d.nn_stats + 4 * (size_t)blockIdx.x;
+            o[0] = (unsigned long long)(clock64() - t_start);
+            o[1] = (unsigned long long)n_cand;
+            o[2] = (unsigned long long)chunk;
+            o[3] = (unsigned long long)nfb;
+        }
     }
-    st->disp_bits = 0ull;
+    const float bst = __uint_as_float((unsigned)(bkey >> 32));
+    const int bidx = (int)(unsigned)(bkey & 0xffffffffull);
+    if (valid && bpos >= 0) {
+        const TPoint<float> c = d.tpts[bpos];
+        bx = c.x; by = c.y; bz = c.z;
     }
+    search_outputs<float, MODE>(d, i, valid, bidx, bst, bx, by, bz, qx, qy, qz, s_disp, &s_last);
 }
 
 }  // namespace
@@ -378,6 +871,16 @@ cudaError_t nrr_launch_nn(const DevProblem<T>& d, int mode, int lanes_per_query,
         case 4: return launch_nn_lpq<T, 4>(d, mode, s);
         default: return launch_nn_lpq<T, 8>(d, mode, s);
     }
+}
+
+// The tensor-core candidate search (float path, pass or evaluation mode).
+cudaError_t nrr_launch_nn_tc(const DevProblem<float>& d, int mode, cudaStream_t s) {
+    const int g = (d.P + tcs::kQ - 1) / tcs::kQ;
+    if (g == 0) return cudaSuccess;
+    if (mode == NRR_MODE_PASS) nn_tc_kernel<NRR_MODE_PASS><<<g, tcs::kCta, 0, s>>>(d);
+    else if (mode == NRR_MODE_EVAL) nn_tc_kernel<NRR_MODE_EVAL><<<g, tcs::kCta, 0, s>>>(d);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 template cudaError_t nrr_launch_nn<float>(const DevProblem<float>&, int, int, cudaStream_t);

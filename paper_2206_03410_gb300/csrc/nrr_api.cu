@@ -70,6 +70,7 @@ struct nrr_ctx {
     bool coop = true;
     int grid_energy = 0, grid_asm = 0, grid_solve = 0, grid_aa = 0, num_sms = 0;
     int nn_lpq = 8;                    // closest points: lanes per query (1, 2, 4, 8)
+    bool nn_tc = false;                // closest points: tensor-core candidates (float path)
     int* d_order = nullptr;            // internal -> caller source index (gradients)
     double* d_grad = nullptr;          // gradient staging [N*12 + P*3]
     void* d_tune = nullptr;            // autotuner scratch: warm start and output of a solve, [2][N][12] in T
@@ -216,6 +217,19 @@ cudaError_t launch_solve_on(nrr_ctx* c, const DevProblem<T>& d) {
 template <typename T>
 cudaError_t launch_solve(nrr_ctx* c) { return launch_solve_on<T>(c, prob<T>(c)); }
 
+// The closest-point search of the context's launch shape: the exact pruned
+// search, or (float path, pass and evaluation modes) the tensor-core
+// candidate search with its exact re-rank; both give the same outputs.
+template <typename T>
+cudaError_t launch_search(nrr_ctx* c, const DevProblem<T>& d, int mode) {
+    return nrr_launch_nn<T>(d, mode, c->nn_lpq, c->stream);
+}
+template <>
+cudaError_t launch_search<float>(nrr_ctx* c, const DevProblem<float>& d, int mode) {
+    if (c->nn_tc && mode != NRR_MODE_RAW) return nrr_launch_nn_tc(d, mode, c->stream);
+    return nrr_launch_nn<float>(d, mode, c->nn_lpq, c->stream);
+}
+
 // The solve step of a pass: PCG, then the free-translation fix of singular
 // components.
 template <typename T>
@@ -345,7 +359,7 @@ cudaError_t launch_pass(nrr_ctx* c) {
     if (e == cudaSuccess) e = nrr_launch_xterm<T>(d, NRR_MODE_PASS, c->aux);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->aux);
     if (e != cudaSuccess) return e;
-    e = nrr_launch_nn<T>(d, NRR_MODE_PASS, c->nn_lpq, c->stream);
+    e = launch_search<T>(c, d, NRR_MODE_PASS);
     if (e != cudaSuccess) return e;
     e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
     if (e != cudaSuccess) return e;
@@ -886,7 +900,7 @@ template <typename T>
 nrr_status unroll_system_at(nrr_ctx* c, const T* Xk) {
     DevProblem<T>& d = prob<T>(c);
     CK(cudaMemcpyAsync(d.Xeval, Xk, sizeof(T) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
-    CK(nrr_launch_nn<T>(d, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+    CK(launch_search<T>(c, d, NRR_MODE_EVAL));
     CK(nrr_launch_xterm<T>(d, NRR_MODE_EVAL, c->stream));
     CK(nrr_launch_energy<T>(d, NRR_MODE_EVAL, c->grid_energy, c->stream));
     CK(nrr_launch_assemble<T>(d, c->grid_asm, c->stream));
@@ -952,7 +966,7 @@ nrr_status unroll_backward_t(nrr_ctx* c, const double* C, double* grad_X, double
     if (C == nullptr) {
         // L = E(X^(K)): closest points held at X^(K)
         CK(cudaMemcpyAsync(d.Xeval, ck + (size_t)K * n12, sizeof(T) * n12, cudaMemcpyDeviceToDevice, c->stream));
-        CK(nrr_launch_nn<T>(d, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+        CK(launch_search<T>(c, d, NRR_MODE_EVAL));
         CK(nrr_launch_xterm<T>(d, NRR_MODE_EVAL, c->stream));
         CK(nrr_launch_energy<T>(d, NRR_MODE_EVAL, c->grid_energy, c->stream));
         const int grid = std::max(1, (c->N + 31) / 32);
@@ -1003,18 +1017,20 @@ int half_octave(int64_t x) { return (int)std::floor(2.0 * std::log2((double)std:
 
 TuneKey tune_key(const nrr_ctx* c) { return {c->fp64 ? 1 : 0, half_octave(c->P), half_octave(c->T), half_octave(c->N)}; }
 
-// Last line of the table that matches key: "nrr-tune <fp64> <bP> <bT> <bN> <lpq> <ctas>".
-bool table_lookup(const char* path, const TuneKey& k, int* lpq, int* ctas) {
+// Last line of the table that matches key:
+// "nrr-tune <fp64> <bP> <bT> <bN> <lpq> <ctas> [<tensor cores>]".
+bool table_lookup(const char* path, const TuneKey& k, int* lpq, int* ctas, int* tc = nullptr) {
     FILE* f = path ? std::fopen(path, "r") : nullptr;
     if (!f) return false;
     char line[256];
     bool found = false;
     while (std::fgets(line, sizeof line, f)) {
-        int a[6];
-        if (std::sscanf(line, "nrr-tune %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5]) == 6 &&
-            a[0] == k.fp64 && a[1] == k.bP && a[2] == k.bT && a[3] == k.bN) {
+        int a[7] = {0, 0, 0, 0, 0, 0, 0};
+        const int n = std::sscanf(line, "nrr-tune %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6]);
+        if (n >= 6 && a[0] == k.fp64 && a[1] == k.bP && a[2] == k.bT && a[3] == k.bN) {
             *lpq = a[4];
             *ctas = a[5];
+            if (tc) *tc = n == 7 ? a[6] : 0;
             found = true;
         }
     }
@@ -1022,10 +1038,10 @@ bool table_lookup(const char* path, const TuneKey& k, int* lpq, int* ctas) {
     return found;
 }
 
-void table_append(const char* path, const TuneKey& k, int lpq, int ctas) {
+void table_append(const char* path, const TuneKey& k, int lpq, int ctas, int tc = 0) {
     FILE* f = path ? std::fopen(path, "a") : nullptr;
     if (!f) return;
-    std::fprintf(f, "nrr-tune %d %d %d %d %d %d\n", k.fp64, k.bP, k.bT, k.bN, lpq, ctas);
+    std::fprintf(f, "nrr-tune %d %d %d %d %d %d %d\n", k.fp64, k.bP, k.bT, k.bN, lpq, ctas, tc);
     std::fclose(f);
 }
 
@@ -1054,16 +1070,20 @@ bool valid_lpq(int v) { return v == 1 || v == 2 || v == 4 || v == 8; }
 
 // Applies a launch configuration (validated) and recaptures the pass graph.
 template <typename T>
-nrr_status apply_config(nrr_ctx* c, int lpq, int ctas) {
+nrr_status apply_config(nrr_ctx* c, int lpq, int ctas, int tc) {
     if (!valid_lpq(lpq)) return fail(c, NRR_E_INVALID, "lanes per query must be 1, 2, 4 or 8");
+    if (tc != 0 && tc != 1) return fail(c, NRR_E_INVALID, "nn_tensor_cores must be 0 or 1");
+    if (tc && c->fp64) return fail(c, NRR_E_INVALID, "the tensor-core search serves the mixed-precision path only");
     if (ctas < 0 || ctas > 16 || !set_solver<T>(c, ctas))
         return fail(c, NRR_E_INVALID, "the cluster solve with " + std::to_string(ctas) + " CTAs does not fit");
     c->nn_lpq = lpq;
+    c->nn_tc = tc != 0;
     return capture_graph(c);
 }
 
 template <typename T>
-nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, double* nn_ms, double* solve_ms) {
+nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, int* best_tc, double* nn_ms,
+                  double* solve_ms) {
     DevProblem<T>& d = prob<T>(c);
     const size_t n12 = (size_t)c->N * 12;
     if (!c->d_tune) CK(cudaMalloc(&c->d_tune, 2 * sizeof(T) * n12));
@@ -1085,6 +1105,14 @@ nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, double* n
         if (ms < *nn_ms) { *nn_ms = ms; *best_lpq = lpq; }
     }
     if (!std::isfinite(*nn_ms)) *best_lpq = c->nn_lpq;
+    *best_tc = 0;
+    if (!c->fp64) {
+        // the tensor-core candidate search (same results as the exact one)
+        double ms = 0;
+        st = time_launches(c, reps, [&]() { return nrr_launch_nn_tc(c->df, NRR_MODE_EVAL, c->stream); }, &ms);
+        if (st != NRR_OK) return st;
+        if (ms < *nn_ms) { *nn_ms = ms; *best_tc = 1; }
+    }
     // the solve of that system, per cluster size (0: grid-wide); the
     // solution goes to scratch, the pass state is not touched
     DevProblem<T> ds = d;
@@ -1113,7 +1141,7 @@ nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, double* n
     c->h_state->vlast = c->h_state->vk ^ 1;
     st = push_state(c);
     if (st != NRR_OK) return st;
-    st = apply_config<T>(c, *best_lpq, *best_ctas);
+    st = apply_config<T>(c, *best_lpq, *best_ctas, *best_tc);
     if (st != NRR_OK) return st;
     return nrr_reset(c);
 }
@@ -1446,7 +1474,7 @@ nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[6]) {
         for (int s = 0; s < kSteps && e == cudaSuccess; ++s) {
             if (c->fp64) {
                 DevProblem<double>& d = c->dd;
-                e = s == 0 ? nrr_launch_nn<double>(d, NRR_MODE_PASS, c->nn_lpq, c->stream)
+                e = s == 0 ? launch_search<double>(c, d, NRR_MODE_PASS)
                   : s == 1 ? nrr_launch_xterm<double>(d, NRR_MODE_PASS, c->stream)
                   : s == 2 ? nrr_launch_energy<double>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
                   : s == 3 ? nrr_launch_assemble<double>(d, c->grid_asm, c->stream)
@@ -1454,7 +1482,7 @@ nrr_status nrr_time_kernels(nrr_ctx* c, int n, double out_ms[6]) {
                            : nrr_launch_aa<double>(d, c->grid_aa, c->stream);
             } else {
                 DevProblem<float>& d = c->df;
-                e = s == 0 ? nrr_launch_nn<float>(d, NRR_MODE_PASS, c->nn_lpq, c->stream)
+                e = s == 0 ? launch_search<float>(c, d, NRR_MODE_PASS)
                   : s == 1 ? nrr_launch_xterm<float>(d, NRR_MODE_PASS, c->stream)
                   : s == 2 ? nrr_launch_energy<float>(d, NRR_MODE_PASS, c->grid_energy, c->stream)
                   : s == 3 ? nrr_launch_assemble<float>(d, c->grid_asm, c->stream)
@@ -1507,13 +1535,13 @@ nrr_status nrr_energy(nrr_ctx* c, const double* X, double out_terms[4]) {
     if (c->fp64) {
         if (X) { st = write_X<double>(c, c->dd.Xeval, X); if (st != NRR_OK) return st; }
         else CK(cudaMemcpyAsync(c->dd.Xeval, c->dd.X, sizeof(double) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
-        CK(nrr_launch_nn<double>(c->dd, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+        CK(launch_search<double>(c, c->dd, NRR_MODE_EVAL));
         CK(nrr_launch_xterm<double>(c->dd, NRR_MODE_EVAL, c->stream));
         CK(nrr_launch_energy<double>(c->dd, NRR_MODE_EVAL, c->grid_energy, c->stream));
     } else {
         if (X) { st = write_X<float>(c, c->df.Xeval, X); if (st != NRR_OK) return st; }
         else CK(cudaMemcpyAsync(c->df.Xeval, c->df.X, sizeof(float) * 12 * (size_t)c->N, cudaMemcpyDeviceToDevice, c->stream));
-        CK(nrr_launch_nn<float>(c->df, NRR_MODE_EVAL, c->nn_lpq, c->stream));
+        CK(launch_search<float>(c, c->df, NRR_MODE_EVAL));
         CK(nrr_launch_xterm<float>(c->df, NRR_MODE_EVAL, c->stream));
         CK(nrr_launch_energy<float>(c->df, NRR_MODE_EVAL, c->grid_energy, c->stream));
     }
@@ -1563,7 +1591,7 @@ nrr_status nrr_get_mm_solution(nrr_ctx* c, double* G) {
 nrr_status nrr_get_search_stats(nrr_ctx* c, unsigned long long* out, int64_t max_warps, int64_t* n_warps) {
     if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
     const unsigned long long* src = c->fp64 ? c->dd.nn_stats : c->df.nn_stats;
-    const int per_warp = 32 / c->nn_lpq;
+    const int per_warp = c->nn_tc ? 128 : 32 / c->nn_lpq;   // tensor-core search: per CTA of 128 queries
     const int64_t nw = (c->P + per_warp - 1) / per_warp;
     if (n_warps) *n_warps = src ? nw : 0;
     if (!src || !out) return NRR_OK;
@@ -1751,6 +1779,7 @@ nrr_status nrr_get_system(nrr_ctx* c, double* Kdense, double* B) {
 nrr_status nrr_get_launch_config(nrr_ctx* c, nrr_launch_config* out) {
     if (!c || !out) return fail(c, NRR_E_INVALID, "NULL argument");
     out->nn_lanes_per_query = c->nn_lpq;
+    out->nn_tensor_cores = c->nn_tc ? 1 : 0;
     out->solve_ctas = c->cl_C;
     out->nn_ms = 0.0;
     out->solve_ms = 0.0;
@@ -1762,8 +1791,8 @@ nrr_status nrr_get_launch_config(nrr_ctx* c, nrr_launch_config* out) {
 nrr_status nrr_set_launch_config(nrr_ctx* c, const nrr_launch_config* cfg) {
     if (!c || !cfg) return fail(c, NRR_E_INVALID, "NULL argument");
     if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
-    return c->fp64 ? apply_config<double>(c, cfg->nn_lanes_per_query, cfg->solve_ctas)
-                   : apply_config<float>(c, cfg->nn_lanes_per_query, cfg->solve_ctas);
+    return c->fp64 ? apply_config<double>(c, cfg->nn_lanes_per_query, cfg->solve_ctas, cfg->nn_tensor_cores)
+                   : apply_config<float>(c, cfg->nn_lanes_per_query, cfg->solve_ctas, cfg->nn_tensor_cores);
 }
 
 nrr_status nrr_tune(nrr_ctx* c, const char* table_path, int reps, nrr_launch_config* out) {
@@ -1773,18 +1802,18 @@ nrr_status nrr_tune(nrr_ctx* c, const char* table_path, int reps, nrr_launch_con
     if (reps <= 0) reps = 5;
     if (reps > 1000) return fail(c, NRR_E_INVALID, "nrr_tune: reps must be at most 1000");
     const TuneKey key = tune_key(c);
-    int lpq = 0, ctas = 0;
+    int lpq = 0, ctas = 0, tc = 0;
     double nn_ms = 0.0, solve_ms = 0.0;
     nrr_status st = NRR_E_INVALID;
-    if (table_lookup(table_path, key, &lpq, &ctas)) {
-        st = c->fp64 ? apply_config<double>(c, lpq, ctas) : apply_config<float>(c, lpq, ctas);
+    if (table_lookup(table_path, key, &lpq, &ctas, &tc)) {
+        st = c->fp64 ? apply_config<double>(c, lpq, ctas, tc) : apply_config<float>(c, lpq, ctas, tc);
         if (st == NRR_OK) st = nrr_reset(c);
     }
     if (st != NRR_OK) {   // no usable entry: measure
-        st = c->fp64 ? tune_t<double>(c, reps, &lpq, &ctas, &nn_ms, &solve_ms)
-                     : tune_t<float>(c, reps, &lpq, &ctas, &nn_ms, &solve_ms);
+        st = c->fp64 ? tune_t<double>(c, reps, &lpq, &ctas, &tc, &nn_ms, &solve_ms)
+                     : tune_t<float>(c, reps, &lpq, &ctas, &tc, &nn_ms, &solve_ms);
         if (st != NRR_OK) return st;
-        table_append(table_path, key, lpq, ctas);
+        table_append(table_path, key, lpq, ctas, tc);
     }
     if (out) {
         out->nn_lanes_per_query = lpq;
@@ -1793,6 +1822,7 @@ nrr_status nrr_tune(nrr_ctx* c, const char* table_path, int reps, nrr_launch_con
         out->solve_ms = solve_ms;
         out->pass_ms = 0.0;
         out->launches_per_pass = kNrrLaunchesPerPass;
+        out->nn_tensor_cores = tc;
     }
     return NRR_OK;
 }
@@ -2056,6 +2086,7 @@ nrr_status nrr_batch_tune(nrr_batch* b, const char* table_path, int reps, nrr_la
         out->solve_ms = 0.0;
         out->pass_ms = best_ms;
         out->launches_per_pass = 0;
+        out->nn_tensor_cores = 0;
     }
     return NRR_OK;
 }

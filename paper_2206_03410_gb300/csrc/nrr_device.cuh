@@ -130,6 +130,9 @@ enum NrrMode { NRR_MODE_PASS = 0, NRR_MODE_EVAL = 1, NRR_MODE_RAW = 2 };
 // Launch helpers (defined in the kernel translation units).
 template <typename T>
 cudaError_t nrr_launch_nn(const DevProblem<T>& d, int mode, int lanes_per_query, cudaStream_t s);
+// Tensor-core candidate search with an exact float re-rank (float path,
+// NRR_MODE_PASS or NRR_MODE_EVAL): the outputs of nrr_launch_nn, bit for bit.
+cudaError_t nrr_launch_nn_tc(const DevProblem<float>& d, int mode, cudaStream_t s);
 template <typename T>
 cudaError_t nrr_launch_energy(const DevProblem<T>& d, int mode, int grid, cudaStream_t s);
 template <typename T>

@@ -68,6 +68,7 @@ class NrrLaunchConfig(ctypes.Structure):
         ("solve_ms", ctypes.c_double),
         ("pass_ms", ctypes.c_double),
         ("launches_per_pass", ctypes.c_int),
+        ("nn_tensor_cores", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -327,8 +328,9 @@ def nrr_get_launch_config(ctx) -> NrrLaunchConfig:
     return out
 
 
-def nrr_set_launch_config(ctx, nn_lanes_per_query: int, solve_ctas: int):
-    cfg = NrrLaunchConfig(nn_lanes_per_query=int(nn_lanes_per_query), solve_ctas=int(solve_ctas))
+def nrr_set_launch_config(ctx, nn_lanes_per_query: int, solve_ctas: int, nn_tensor_cores: int = 0):
+    cfg = NrrLaunchConfig(nn_lanes_per_query=int(nn_lanes_per_query), solve_ctas=int(solve_ctas),
+                          nn_tensor_cores=int(nn_tensor_cores))
     _check(load().nrr_set_launch_config(ctx, ctypes.byref(cfg)), ctx)
 
 
@@ -574,8 +576,8 @@ class Registration:
     def launch_config(self) -> NrrLaunchConfig:
         return nrr_get_launch_config(self.ctx)
 
-    def set_launch_config(self, nn_lanes_per_query: int, solve_ctas: int):
-        nrr_set_launch_config(self.ctx, nn_lanes_per_query, solve_ctas)
+    def set_launch_config(self, nn_lanes_per_query: int, solve_ctas: int, nn_tensor_cores: int = 0):
+        nrr_set_launch_config(self.ctx, nn_lanes_per_query, solve_ctas, nn_tensor_cores)
 
     def unroll(self, K: int, X0) -> np.ndarray:
         return nrr_unroll(self.ctx, K, X0)
