@@ -14,8 +14,6 @@
 // that could win or tie; the distance itself is evaluated in T. Ties go to
 // the lowest caller index. Work per query is a few hundred distance
 // evaluations instead of T; the kernel is bound by issue slots.
-#include <cuda_bf16.h>
-
 #include "nrr_device.cuh"
 
 namespace {
@@ -388,70 +386,77 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
 //
 // A CTA serves 128 curve-consecutive source points (the M = 128 rows of a
 // tcgen05.mma). Its candidate target points are the union of the leaves
-// that any of its eight 16-query boxes may need under the queries' current
+// that any of its sixteen 8-query boxes may need under the queries' current
 // bounds (the distance to the previous correspondence), in chunks of four
-// leaves (N = 128 columns). For every chunk one MMA (kind::f16, BF16 inputs,
-// FP32 accumulator in tensor memory) forms all 128 x 128 approximate squared
-// distances at once, as one dot product of K = 16:
+// leaves (N = 128 columns). For every chunk two MMAs (kind::tf32, K = 8
+// each, FP32 accumulator in tensor memory) form all 128 x 128 approximate
+// squared distances at once, as one dot product of K = 16:
 //   query row     [-2 x_hi, -2 x_hi, -2 x_lo, 1, 1, |x|^2_hi, |x|^2_lo, 0...]
 //   candidate row [ y_hi,    y_lo,    y_hi, |y|^2_hi, |y|^2_lo, 1, 1, 0...]
 // with x, y the float coordinates minus the CTA's centre and every value
-// split into two BF16 parts (hi + lo), so that the product carries about 16
+// split into two TF32 parts (hi + lo), so that the product carries about 22
 // significant bits: |x - y|^2 = |x|^2 + |y|^2 - 2 x.y up to
-// delta = 2^-14 (|x| + R)^2, R the largest |y| among the candidates (the
+// delta = 2^-17 (|x| + R)^2, R the largest |y| among the candidates (the
 // split and the FP32 accumulation err by less than a quarter of that).
 // The epilogue reads each accumulator from tensor memory (tcgen05.ld) and
-// keeps, per query and half of the columns, the four smallest approximate
-// distances. The window of candidates that can hold the exact winner is
-// then {d~ <= (d~_min + delta)(1 + 4e-6) + delta} (4e-6 covers the float
-// rounding of the exact distances): its members are re-ranked with the
-// exact float distance and the (d^2, caller index) keys of nn_kernel. A
-// query whose window may hold more than its four kept candidates is
+// keeps, per query and half of the columns, the eight smallest approximate
+// distances; the halves are merged to eight, whose exact float distances
+// and (d^2, caller index) keys (those of nn_kernel) are formed. With D the
+// best of them, no candidate that was not kept can win when the eighth
+// approximate distance exceeds D (1 + 2e-6) + delta (2e-6 covers the float
+// rounding of the exact distances); a query for which this fails is
 // searched exactly, alone, with nn_kernel's pruning. So the result is the
-// exact search's result; the tensor cores only choose where to look.
+// exact search's; the tensor cores only choose where to look.
 //
 // Pipeline: two accumulators (256 tensor-memory columns) and two candidate
 // tiles in shared memory; the MMA of chunk c runs while the epilogue reads
-// chunk c - 1. All waits on the MMA's completion are bounded: after about
-// two seconds the kernel records NRR_E_TIMEOUT and skips the rest of its
-// work (freeing its tensor memory).
+// chunk c - 1, and the target points of chunk c + 1 are loaded meanwhile.
+// All waits on the MMA's completion are bounded: after about two seconds
+// the kernel records NRR_E_TIMEOUT and finishes every query by the exact
+// scan (freeing its tensor memory).
 // ---------------------------------------------------------------------------
 namespace tcs {
 constexpr int kQ = 128;                 // queries per CTA: the MMA's M
 constexpr int kN = 128;                 // candidates per chunk: the MMA's N
 constexpr int kLeaves = kN / NRR_LEAF;  // leaves per chunk
 constexpr int kCta = 256;               // warps w and w + 4 read the same tensor-memory lanes
-constexpr int kGroups = 8;              // query boxes of 16 queries for the candidate test
+constexpr int kGroups = 16;             // query boxes of 8 queries for the candidate test
 constexpr int kListCap = 512;           // candidate leaves collected before they are processed
-constexpr int kTop = 4;                 // best approximate candidates kept per query and half
+constexpr int kTop = 8;                 // best approximate candidates kept per query and half
 constexpr unsigned kTmemCols = 2 * kN;  // two accumulators
-constexpr float kDelta = 1.0f / 16384.0f;
-// byte offset of element k of row r of a 128 x 16 BF16 operand tile in the
-// tensor cores' K-major layout without swizzle: 8-row x 16-byte core
-// matrices, the two along K 128 bytes apart, row groups 256 bytes apart
-__host__ __device__ constexpr int tile_off(int r, int kc) { return (r >> 3) * 256 + kc * 128 + (r & 7) * 16; }
-// instruction descriptor of kind::f16: D f32 (bits 4-5 = 1), A and B bf16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-constexpr unsigned kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kN >> 3) << 17) |
+constexpr float kDelta = 1.0f / 131072.0f;   // 2^-17
+constexpr int kRowBytes = 64;           // 16 TF32 values per operand row
+constexpr int kTileBytes = 128 * kRowBytes;
+// byte offset of core matrix kc (4 TF32 values along K) of row r of a
+// 128 x 16 TF32 operand tile in the tensor cores' K-major layout without
+// swizzle: 8-row x 16-byte core matrices, those along K 128 bytes apart,
+// row groups 512 bytes apart
+__host__ __device__ constexpr int tile_off(int r, int kc) { return (r >> 3) * 512 + kc * 128 + (r & 7) * 16; }
+// instruction descriptor of kind::tf32: D f32 (bits 4-5 = 1), A and B tf32
+// (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr unsigned kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(kN >> 3) << 17) |
                             ((unsigned)(kQ >> 4) << 24);
 constexpr long long kSpin = 4000000000LL;   // clock64 cycles of a bounded wait
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: start address, leading (K) byte offset
-// 128, stride (8-row group) byte offset 256, the fixed version bits 46-48 =
-// 1, no swizzle
-__device__ __forceinline__ unsigned long long tile_desc(const void* tile) {
-    unsigned long long dsc = (unsigned long long)((smem_addr(tile) & 0x3FFFFu) >> 4);
+// shared-memory matrix descriptor of the K-slice starting at `start`:
+// leading (K) byte offset 128, stride (8-row group) byte offset 512, the
+// fixed version bits 46-48 = 1, no swizzle
+__device__ __forceinline__ unsigned long long tile_desc(const void* start) {
+    unsigned long long dsc = (unsigned long long)((smem_addr(start) & 0x3FFFFu) >> 4);
     dsc |= (unsigned long long)(128u >> 4) << 16;
-    dsc |= (unsigned long long)(256u >> 4) << 32;
+    dsc |= (unsigned long long)(512u >> 4) << 32;
     dsc |= 1ull << 46;
     return dsc;
 }
 
-__device__ __forceinline__ unsigned bf16_bits(float x) { return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x)); }
-__device__ __forceinline__ float bf16_val(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-__device__ __forceinline__ unsigned pack2(unsigned lo, unsigned hi) { return lo | (hi << 16); }
+// round to TF32 (nearest, ties away), returned as a float
+__device__ __forceinline__ float tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 
 __device__ __forceinline__ bool mbar_done(unsigned long long* b, unsigned parity) {
     unsigned ok;
@@ -475,24 +480,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* b, unsigne
     return true;
 }
 
-// 32 consecutive accumulator columns of this warp's 32 lanes
-__device__ __forceinline__ void tmem_ld32(unsigned addr, float (&v)[32]) {
-    unsigned r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(addr)
-        : "memory");
+// 8 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld8(unsigned addr, float (&v)[8]) {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr)
+                 : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// sorted insertion into a query's four best (approximate distance, slot)
+// sorted insertion into a query's kTop best (approximate distance, slot)
 __device__ __forceinline__ void top_insert(float (&tv)[kTop], int (&ts)[kTop], float v, int slot) {
     if (!(v < tv[kTop - 1])) return;
     tv[kTop - 1] = v;
@@ -505,13 +505,18 @@ __device__ __forceinline__ void top_insert(float (&tv)[kTop], int (&ts)[kTop], f
         }
     }
 }
+
+// one operand row (16 TF32 values) as four 16-byte core-matrix rows
+struct Row16 {
+    float v[16];
+};
 }  // namespace tcs
 
 template <int MODE>
 __global__ void __launch_bounds__(tcs::kCta, 2) nn_tc_kernel(DevProblem<float> d) {
     using namespace tcs;
-    __shared__ __align__(1024) unsigned char sA[kQ * 32];
-    __shared__ __align__(1024) unsigned char sB[2][kN * 32];
+    __shared__ __align__(1024) unsigned char sA[kTileBytes];
+    __shared__ __align__(1024) unsigned char sB[2][kTileBytes];
     __shared__ int s_list[kListCap];
     __shared__ int s_slot[3][kN];          // target slot of each candidate column (-1: none), by chunk % 3
     __shared__ float s_gb[kGroups][8];     // query boxes and their bounds
@@ -535,6 +540,7 @@ __global__ void __launch_bounds__(tcs::kCta, 2) nn_tc_kernel(DevProblem<float> d
     const int P = d.P;
     const int i = blockIdx.x * kQ + row;
     const bool valid = owner && i < P;
+    const bool row_valid = i < P;          // the row holds a query (either half)
     const long long t_start = clock64();
 
     // ---- queries and their initial candidate (the previous correspondence)
@@ -553,22 +559,25 @@ __global__ void __launch_bounds__(tcs::kCta, 2) nn_tc_kernel(DevProblem<float> d
                       valid ? qx : -INFINITY, valid ? qy : -INFINITY, valid ? qz : -INFINITY};
         float ub = valid ? ub_f(best) : 0.f;
 #pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {
+        for (int o = 1; o < 8; o <<= 1) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) e[k] = fminf(e[k], __shfl_xor_sync(0xffffffffu, e[k], o));
 #pragma unroll
             for (int k = 3; k < 6; ++k) e[k] = fmaxf(e[k], __shfl_xor_sync(0xffffffffu, e[k], o));
             ub = fmaxf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
         }
-        if ((lane & 15) == 0) {
+        if ((lane & 7) == 0) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) s_gb[row >> 4][k] = e[k];
-            s_gb[row >> 4][6] = ub;
+            for (int k = 0; k < 6; ++k) s_gb[row >> 3][k] = e[k];
+            s_gb[row >> 3][6] = ub;
         }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) e[k] = fminf(e[k], __shfl_xor_sync(0xffffffffu, e[k], 16));
+        for (int o = 8; o < 32; o <<= 1) {
 #pragma unroll
-        for (int k = 3; k < 6; ++k) e[k] = fmaxf(e[k], __shfl_xor_sync(0xffffffffu, e[k], 16));
+            for (int k = 0; k < 3; ++k) e[k] = fminf(e[k], __shfl_xor_sync(0xffffffffu, e[k], o));
+#pragma unroll
+            for (int k = 3; k < 6; ++k) e[k] = fmaxf(e[k], __shfl_xor_sync(0xffffffffu, e[k], o));
+        }
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) s_ext[warp][k] = e[k];
@@ -601,29 +610,31 @@ __global__ void __launch_bounds__(tcs::kCta, 2) nn_tc_kernel(DevProblem<float> d
     // ---- query rows of the A operand (zeros for rows without a query)
     float xn = 0.f;   // |x| of this query, for its error bound
     if (owner) {
-        unsigned w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        Row16 a;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a.v[k] = 0.f;
         if (valid) {
-            const float x0 = qx - cx, x1 = qy - cy, x2 = qz - cz;
-            const float h0 = bf16_val(x0), h1 = bf16_val(x1), h2 = bf16_val(x2);
-            const float nq = x0 * x0 + x1 * x1 + x2 * x2;
-            const float nh = bf16_val(nq);
+            const float x[3] = {qx - cx, qy - cy, qz - cz};
+            const float nq = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const float nh = tf32(nq);
             xn = sqrtf(nq);
-            const unsigned a0 = bf16_bits(-2.f * h0), a1 = bf16_bits(-2.f * h1), a2 = bf16_bits(-2.f * h2);
-            const unsigned l0 = bf16_bits(-2.f * (x0 - h0)), l1 = bf16_bits(-2.f * (x1 - h1)),
-                           l2 = bf16_bits(-2.f * (x2 - h2));
-            const unsigned one = bf16_bits(1.f);
-            // k 0..7: -2x_hi, -2x_hi(0..1); k 8..15: -2x_hi(2), -2x_lo, 1, 1, |x|^2 hi, lo, 0
-            w[0] = pack2(a0, a1); w[1] = pack2(a2, a0); w[2] = pack2(a1, a2); w[3] = pack2(l0, l1);
-            w[4] = pack2(l2, one); w[5] = pack2(one, bf16_bits(nh)); w[6] = pack2(bf16_bits(nq - nh), 0u);
-            w[7] = 0u;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float h = tf32(x[k]);
+                a.v[k] = -2.f * h;
+                a.v[3 + k] = -2.f * h;
+                a.v[6 + k] = -2.f * tf32(x[k] - h);
+            }
+            a.v[9] = 1.f; a.v[10] = 1.f; a.v[11] = nh; a.v[12] = tf32(nq - nh);
         }
-        *reinterpret_cast<uint4*>(sA + tile_off(row, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4*>(sA + tile_off(row, 1)) = make_uint4(w[4], w[5], w[6], w[7]);
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc)
+            *reinterpret_cast<float4*>(sA + tile_off(row, kc)) =
+                make_float4(a.v[4 * kc], a.v[4 * kc + 1], a.v[4 * kc + 2], a.v[4 * kc + 3]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
 
-    const unsigned long long descA = tile_desc(sA);
     float tv[kTop];
     int ts[kTop];
 #pragma unroll
@@ -633,100 +644,118 @@ __global__ void __launch_bounds__(tcs::kCta, 2) nn_tc_kernel(DevProblem<float> d
     int n_cand = 0;         // candidate leaves (statistics)
     bool failed = false;
 
-    // epilogue of chunk ch (accumulator ch & 1): every thread reads 64
-    // columns of its query's row and keeps the four smallest. (The column
-    // slots of a chunk sit in s_slot[ch % 3]: the chunk after next writes
-    // its own while a slow thread may still read these.)
-    auto epilogue = [&](int ch) {
-        const int b = ch & 1;
-        if (!failed) {
-            // warp-uniform outcome: tcgen05.ld needs the whole warp
-            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&s_mbar[b], phase[b]));
-            if (!ok) {
-                failed = true;
-                s_fail = 1;
-                atomicExch(&st->status, (int)NRR_E_TIMEOUT);
-            }
-        }
-        phase[b] ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (failed) return;
-        const unsigned base = taddr + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(b * kN + half * 64);
-#pragma unroll
-        for (int part = 0; part < 2; ++part) {
-            float v[32];
-            tmem_ld32(base + (unsigned)(part * 32), v);
-            if (valid || (!owner && blockIdx.x * kQ + row < P)) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int slot = s_slot[ch % 3][half * 64 + part * 32 + j];
-                    if (slot >= 0) top_insert(tv, ts, v[j], slot);
-                }
-            }
-        }
-    };
-
-    // chunks of the collected leaves: build the candidate rows, issue the
-    // MMA, and run the epilogue of the previous chunk behind it
+    // chunks of the collected leaves. Iteration c builds the candidate rows
+    // of chunk c, issues its two MMAs, loads the points of chunk c + 1 and
+    // runs the epilogue of chunk c - 1 behind the MMAs: every thread reads
+    // 64 accumulator columns of its query's row, 8 at a time, and keeps the
+    // eight smallest. (The column slots of a chunk sit in s_slot[ch % 3]:
+    // the chunk after next writes its own while a slow thread may still read
+    // these.) One call site per step keeps the kernel's code small.
     auto process = [&](int nlist) {
         const int nch = (nlist + kLeaves - 1) / kLeaves;
-        for (int c = 0; c < nch; ++c) {
-            const int b = chunk & 1;
-            {
-                const int r = tid >> 1, kc = tid & 1;
-                const int li = c * kLeaves + (r >> 5);
-                unsigned w[4] = {0u, 0u, 0u, 0u};
-                int slot = -1;
-                if (li < nlist) {
+        TPoint<float> pt{};
+        int slot = -1;
+        const int r = tid >> 1, hv = tid & 1;
+#pragma unroll 1
+        for (int c = 0; c <= nch; ++c) {
+            if (c < nch) {
+                // the target point of this thread's candidate row (two
+                // threads per row, one per half of its 16 values)
+                if (c == 0) {
+                    const int li = r >> 5;
+                    slot = -1;
+                    if (li < nlist) {
+                        const int sl = s_list[li] * NRR_LEAF + (r & 31);
+                        pt = d.tpts[sl];
+                        if (pt.idx != 0x7fffffff) slot = sl;   // not a padding point
+                    }
+                }
+                const int b = chunk & 1;
+                float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (slot >= 0) {
+                    const float y[3] = {pt.x - cx, pt.y - cy, pt.z - cz};
+                    const float ny = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+                    float h[3], l[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) { h[k] = tf32(y[k]); l[k] = tf32(y[k] - h[k]); }
+                    if (hv == 0) {
+                        // values 0..7: y_hi, y_lo, y_hi(0..1)
+                        w[0] = h[0]; w[1] = h[1]; w[2] = h[2]; w[3] = l[0];
+                        w[4] = l[1]; w[5] = l[2]; w[6] = h[0]; w[7] = h[1];
+                        atomicMax(&s_Ru, __float_as_uint(sqrtf(ny)));
+                    } else {
+                        // values 8..15: y_hi(2), |y|^2 hi, lo, 1, 1, 0, 0, 0
+                        const float nh = tf32(ny);
+                        w[0] = h[2]; w[1] = nh; w[2] = tf32(ny - nh); w[3] = 1.f; w[4] = 1.f;
+                    }
+                }
+                *reinterpret_cast<float4*>(sB[b] + tile_off(r, 2 * hv)) = make_float4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<float4*>(sB[b] + tile_off(r, 2 * hv + 1)) = make_float4(w[4], w[5], w[6], w[7]);
+                if (hv == 0) s_slot[chunk % 3][r] = slot;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (tid == 0 && !s_fail) {
+                    const unsigned dcol = taddr + (unsigned)(b * kN);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        // K values 8 ks .. 8 ks + 7: core matrices 2 ks and 2 ks + 1
+                        const unsigned long long da = tile_desc(sA + ks * 256);
+                        const unsigned long long db = tile_desc(sB[b] + ks * 256);
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+                            "l"(da), "l"(db), "r"(kIdesc), "r"((unsigned)ks)
+                            : "memory");
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            smem_addr(&s_mbar[b]))
+                        : "memory");
+                }
+                // the next chunk's point, loaded behind the MMAs
+                const int li = (c + 1) * kLeaves + (r >> 5);
+                slot = -1;
+                if (c + 1 < nch && li < nlist) {
                     const int sl = s_list[li] * NRR_LEAF + (r & 31);
-                    const TPoint<float> pt = d.tpts[sl];
-                    if (pt.idx != 0x7fffffff) {   // not a padding point
-                        slot = sl;
-                        const float y0 = pt.x - cx, y1 = pt.y - cy, y2 = pt.z - cz;
-                        const float h0 = bf16_val(y0), h1 = bf16_val(y1), h2 = bf16_val(y2);
-                        const float ny = y0 * y0 + y1 * y1 + y2 * y2;
-                        const float nh = bf16_val(ny);
-                        const unsigned a0 = bf16_bits(h0), a1 = bf16_bits(h1), a2 = bf16_bits(h2);
-                        const unsigned one = bf16_bits(1.f);
-                        if (kc == 0) {
-                            // k 0..7: y_hi, y_lo, y_hi(0..1)
-                            w[0] = pack2(a0, a1);
-                            w[1] = pack2(a2, bf16_bits(y0 - h0));
-                            w[2] = pack2(bf16_bits(y1 - h1), bf16_bits(y2 - h2));
-                            w[3] = pack2(a0, a1);
-                            atomicMax(&s_Ru, __float_as_uint(sqrtf(ny)));
-                        } else {
-                            // k 8..15: y_hi(2), |y|^2 hi, lo, 1, 1, 0, 0, 0
-                            w[0] = pack2(a2, bf16_bits(nh));
-                            w[1] = pack2(bf16_bits(ny - nh), one);
-                            w[2] = pack2(one, 0u);
-                            w[3] = 0u;
+                    pt = d.tpts[sl];
+                    if (pt.idx != 0x7fffffff) slot = sl;
+                }
+                ++chunk;
+            }
+            if (c == 0) continue;
+            // ---- epilogue of chunk ch = chunk - 1 - (c < nch)
+            const int ch = c < nch ? chunk - 2 : chunk - 1;
+            const int b = ch & 1;
+            if (!failed) {
+                // warp-uniform outcome: tcgen05.ld needs the whole warp
+                const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&s_mbar[b], phase[b]));
+                if (!ok) {
+                    failed = true;
+                    s_fail = 1;
+                    atomicExch(&st->status, (int)NRR_E_TIMEOUT);
+                }
+            }
+            phase[b] ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!failed) {
+                const unsigned base = taddr + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(b * kN + half * 64);
+                const int* slots = s_slot[ch % 3] + half * 64;
+#pragma unroll 1
+                for (int part = 0; part < 8; ++part) {
+                    float v[8];
+                    tmem_ld8(base + (unsigned)(part * 8), v);
+                    if (row_valid) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int sl = slots[part * 8 + j];
+                            if (v[j] < tv[kTop - 1] && sl >= 0) top_insert(tv, ts, v[j], sl);
                         }
                     }
                 }
-                *reinterpret_cast<uint4*>(sB[b] + tile_off(r, kc)) = make_uint4(w[0], w[1], w[2], w[3]);
-                if (kc == 0) s_slot[chunk % 3][r] = slot;
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (tid == 0 && !s_fail) {
-                const unsigned long long descB = tile_desc(sB[b]);
-                const unsigned dcol = taddr + (unsigned)(b * kN);
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
-                    "l"(descA), "l"(descB), "r"(kIdesc), "r"(0u)
-                    : "memory");
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_addr(&s_mbar[b]))
-                             : "memory");
-            }
-            if (c > 0) epilogue(chunk - 1);
-            ++chunk;
         }
-        if (nch > 0) epilogue(chunk - 1);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     };
@@ -775,7 +804,7 @@ __global__ void __launch_bounds__(tcs::kCta, 2) nn_tc_kernel(DevProblem<float> d
         }
     }
 
-    // ---- merge the halves' best four; window; exact re-rank
+    // ---- merge the halves' best eight, exact re-rank, completeness test
     if (!owner) {
 #pragma unroll
         for (int k = 0; k < kTop; ++k) { s_tv[row][k] = tv[k]; s_ts[row][k] = ts[k]; }
@@ -785,27 +814,31 @@ __global__ void __launch_bounds__(tcs::kCta, 2) nn_tc_kernel(DevProblem<float> d
     if (valid) {
 #pragma unroll
         for (int k = 0; k < kTop; ++k) top_insert(tv, ts, s_tv[row][k], s_ts[row][k]);
-        const float Ru = __uint_as_float(s_Ru);
-        const float r = __fadd_ru(xn, Ru);
-        const float delta = __fmul_ru(kDelta, __fmul_ru(r, r));
-        const float T = __fadd_ru(__fmul_ru(__fadd_ru(tv[0], delta), 1.000004f), delta);
-        fallback = failed || tv[kTop - 1] <= T;
-        if (!fallback) {
+        float D = INFINITY;   // best exact float distance among the kept candidates
+        if (!failed) {
 #pragma unroll
             for (int k = 0; k < kTop; ++k) {
-                if (ts[k] >= 0 && tv[k] <= T) {
+                if (ts[k] >= 0) {
                     const TPoint<float> c = d.tpts[ts[k]];
-                    const unsigned long long key = cand_key(sqdist(qx, qy, qz, c.x, c.y, c.z), c.idx);
+                    const float dd = sqdist(qx, qy, qz, c.x, c.y, c.z);
+                    D = fminf(D, dd);
+                    const unsigned long long key = cand_key(dd, c.idx);
                     if (key < bkey) { bkey = key; bpos = ts[k]; }
                 }
             }
-        } else {
+        }
+        const float Ru = __uint_as_float(s_Ru);
+        const float r = __fadd_ru(xn, Ru);
+        const float delta = __fmul_ru(kDelta, __fmul_ru(r, r));
+        fallback = failed || !(tv[kTop - 1] > __fadd_ru(__fmul_ru(D, 1.000002f), delta));
+        if (fallback) {
             // exact search of this query alone, pruned by its own box
             float ub = ub_f(__uint_as_float((unsigned)(bkey >> 32)));
             for (int S = 0; S < d.n_supers; ++S) {
                 if (box_gap2(qx, qy, qz, qx, qy, qz, d.super_box + 6 * S) > ub) continue;
                 for (int L = S * 32; L < min(d.n_leaves, S * 32 + 32); ++L) {
                     if (box_gap2(qx, qy, qz, qx, qy, qz, d.leaf_box + 6 * L) > ub) continue;
+#pragma unroll 8
                     for (int j = 0; j < NRR_LEAF; ++j) {
                         const TPoint<float> c = d.tpts[L * NRR_LEAF + j];
                         const unsigned long long key = cand_key(sqdist(qx, qy, qz, c.x, c.y, c.z), c.idx);
