@@ -244,6 +244,46 @@ nrr_status nrr_energy(nrr_ctx* ctx, const double* X, double out_terms[4]);
 nrr_status nrr_backward(nrr_ctx* ctx, int mode, const double* X,
                         double* grad_X, double* grad_src);
 
+/* The preliminary version's solver, a comparison solver on the same energy
+ * (Sec. 3.3.4, the Remark on the preliminary version; Sec. 4.3). Each outer
+ * iteration holds the closest points at the current iterate X^k, which
+ * turns E into a surrogate that majorises it and equals it at X^k (the
+ * Welsch functions and the rotation term are kept, so it is not quadratic),
+ * and minimises that surrogate with an inner L-BFGS: the two-loop
+ * recursion with m pairs (cleared at every outer iteration; a pair is kept
+ * only if y.s > 1e-12 |y| |s|; H0 = gamma I with gamma = s.y / y.y of the
+ * newest pair, or 1/|g| without pairs), a backtracking line search from
+ * t = 1 that halves t until E(X + t d) <= E(X) + c1 t g.d (at most
+ * max_halvings times; no acceptable step ends the inner solve), and the
+ * inner solve ends when |g| <= g_tol |g_0| or after max_inner accepted
+ * steps. The nu annealing, alpha, beta and the stopping tests (eps or
+ * rel_energy_tol, I_max counting outer iterations) are those of Algorithm 2
+ * with the context's parameters. */
+typedef struct {
+    int    m;              /* history pairs, 1..8; default 5                 */
+    double c1;             /* sufficient decrease of the line search, (0,1);
+                              default 1e-4                                  */
+    double g_tol;          /* |g| <= g_tol |g_0| ends the inner solve;
+                              default 1e-3                                  */
+    int    max_inner;      /* accepted inner steps per outer iteration;
+                              default 20                                    */
+    int    max_halvings;   /* line-search halvings per step, 0..60; default
+                              30                                            */
+} nrr_lbfgs_params;
+
+void nrr_lbfgs_params_default(nrr_lbfgs_params* params);
+
+/* Runs outer iterations of the preliminary version's solver from the
+ * context's current iterate and stage until the stage loop returns or
+ * max_outer (<= 0: the max_total_passes parameter) outer iterations ran.
+ * Each outer iteration counts as a pass and a solve in nrr_step_info
+ * (n_passes, n_solves); E is the energy at the iterate it started from.
+ * params NULL = defaults. info (host, may be NULL) receives the final
+ * state; NRR_E_NOT_CONVERGED if the cap was hit; NRR_E_INVALID for
+ * parameters out of range. nrr_step / nrr_solve may follow (they start a
+ * fresh Anderson history). */
+nrr_status nrr_solve_lbfgs(nrr_ctx* ctx, const nrr_lbfgs_params* params, int max_outer, nrr_step_info* info);
+
 /* K plain MM steps from X0 (Sec. 3.3.1-3.3.2): X^(k+1) = K(X^(k))^-1
  * B(X^(k)) of Eq. (surr_solution) at the current stage's nu_a, nu_r, alpha,
  * beta, without the Anderson mix and the safeguard (the accept/reject

@@ -23,8 +23,10 @@ Modules:
   solver     Algorithm 2 (stage loop, MM + AA passes, safeguard).
   unrolled   K plain MM steps at fixed nu and their reverse-mode derivative
              w.r.t. the initial transforms and the source positions.
+  lbfgs      the preliminary version's solver (fixed closest points + inner
+             L-BFGS with a backtracking line search), a comparison solver.
 
 Parity pins: every function is pinned by the tests in tests/test_oracle_*.py
 against closed forms, invariants, brute force and library routines.
 """
-from . import graph, model, surrogate, anderson, solver, unrolled  # noqa: F401
+from . import graph, model, surrogate, anderson, solver, unrolled, lbfgs  # noqa: F401

@@ -880,6 +880,24 @@ __global__ void __launch_bounds__(tcs::kCta, 2) nn_tc_kernel(DevProblem<float> d
     search_outputs<float, MODE>(d, i, valid, bidx, bst, bx, by, bz, qx, qy, qz, s_disp, &s_last);
 }
 
+// The alignment state at Xeval with the closest points held (the surrogate
+// of the preliminary version's solver): v_hat_i of Eq. (deformed_position)
+// into the non-kept buffer and d_i^2 = |v_hat_i - u_i|^2 to the held
+// closest point u_i; rho and u unchanged.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) fixed_corr_kernel(DevProblem<T> d) {
+    NrrState* st = d.st;
+    const int P = d.P;
+    const int wb = st->vk ^ 1;
+    T* vh = d.vhat + (size_t)wb * 3 * P;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        T qx, qy, qz;
+        query_point<T, NRR_MODE_EVAL>(d, i, qx, qy, qz);
+        vh[i] = qx; vh[P + i] = qy; vh[2 * P + i] = qz;
+        d.d2[i] = sqdist(qx, qy, qz, d.u[i], d.u[P + i], d.u[2 * P + i]);
+    }
+}
+
 }  // namespace
 
 template <typename T, int LPQ>
@@ -915,6 +933,16 @@ cudaError_t nrr_launch_nn_tc(const DevProblem<float>& d, int mode, cudaStream_t 
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t nrr_launch_fixed_corr(const DevProblem<T>& d, cudaStream_t s) {
+    const int g = (d.P + kThreads - 1) / kThreads;
+    if (g == 0) return cudaSuccess;
+    fixed_corr_kernel<T><<<g, kThreads, 0, s>>>(d);
+    return cudaGetLastError();
+}
+template cudaError_t nrr_launch_fixed_corr<float>(const DevProblem<float>&, cudaStream_t);
+template cudaError_t nrr_launch_fixed_corr<double>(const DevProblem<double>&, cudaStream_t);
 
 template cudaError_t nrr_launch_nn<float>(const DevProblem<float>&, int, int, cudaStream_t);
 template cudaError_t nrr_launch_nn<double>(const DevProblem<double>&, int, int, cudaStream_t);

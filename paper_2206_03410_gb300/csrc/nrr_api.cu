@@ -88,6 +88,13 @@ struct nrr_ctx {
     double diag = 0.0;
     double nu_a0 = 0.0, nu_r0 = 0.0;   // first-stage parameters
     uint64_t problem_hash = 0;         // inputs, graph and parameters (checkpoints)
+    // the preliminary version's solver (nrr_solve_lbfgs): history pairs
+    // S, Y [m][12N], gradients g, g_new and the direction [12N] (double),
+    // scalars [8], the inner iterate X_k [12N] and v_hat at the outer
+    // iterate [3P] (context precision)
+    double* lb_buf = nullptr;
+    void* lb_t = nullptr;
+    int lb_m = 0;
     bool failed = false;
     std::string err;
 };
@@ -1148,6 +1155,154 @@ nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, int* best
 
 
 // ---------------------------------------------------------------------------
+// The preliminary version's solver (Sec. 3.3.4, the Remark on the
+// preliminary version; Sec. 4.3), as a comparison solver on the same energy:
+// each outer iteration holds the closest points at X^k, which makes E a
+// non-quadratic surrogate (it keeps Welsch's functions and the rotation
+// term), and minimises it by an inner L-BFGS with a backtracking line search
+// (sufficient decrease c1) that ends at |g| <= g_tol |g_0| or after
+// max_inner steps. The nu annealing, alpha, beta and the stopping tests are
+// those of Algorithm 2. Every evaluation (closest points, energy terms,
+// gradient, direction, trial point) runs in the library's kernels; the host
+// takes the accept/reject decisions from the energies it reads back.
+// ---------------------------------------------------------------------------
+void host_end_stage(NrrState& s) {
+    if (s.nu_a == s.nu_a_min) {
+        s.done = 1;
+        return;
+    }
+    s.nu_a = std::max(s.nu_a * 0.5, s.nu_a_min);
+    s.nu_r = s.nu_r * 0.5;
+    s.stage += 1;
+    host_stage_weights(s);
+    s.E_prev = std::numeric_limits<double>::infinity();
+    s.n_solves_stage = 0;
+}
+
+template <typename T>
+nrr_status lbfgs_t(nrr_ctx* c, const nrr_lbfgs_params& lb, int max_outer) {
+    DevProblem<T>& d = prob<T>(c);
+    const int n = c->N * 12;
+    const size_t P = (size_t)c->P;
+    const int m = lb.m;
+    if (c->lb_m < m || !c->lb_buf) {
+        if (c->lb_buf) { CK(cudaFree(c->lb_buf)); c->lb_buf = nullptr; }
+        CK(cudaMalloc(&c->lb_buf, sizeof(double) * ((size_t)2 * m * n + 3 * (size_t)n + 8)));
+        c->lb_m = m;
+    }
+    if (!c->lb_t) CK(cudaMalloc(&c->lb_t, sizeof(T) * ((size_t)n + 3 * P)));
+    if (!c->d_order) {
+        CK(cudaMalloc(&c->d_order, sizeof(int) * P));
+        CK(cudaMemcpyAsync(c->d_order, c->src_order.data(), sizeof(int) * P, cudaMemcpyHostToDevice, c->stream));
+    }
+    double* S = c->lb_buf;
+    double* Y = S + (size_t)m * n;
+    double* g = Y + (size_t)m * n;
+    double* gn = g + n;
+    double* dv = gn + n;
+    double* scal = dv + n;
+    T* Xk = (T*)c->lb_t;
+    T* vk = Xk + n;
+    double hs[8];
+    const int grid_g = std::max(1, (c->N + 31) / 32);
+    nrr_status st = pull_state(c);
+    if (st != NRR_OK) return st;
+    NrrState& h = *c->h_state;
+    const size_t vbytes = sizeof(T) * 3 * P;
+    auto vhat_eval = [&]() { return d.vhat + (size_t)(h.vk ^ 1) * 3 * P; };
+    // energy at Xeval, with the closest points searched (true) or held
+    auto energy_at_eval = [&](bool search, double* E) -> nrr_status {
+        if (search) CK(launch_search<T>(c, d, NRR_MODE_EVAL));
+        else CK(nrr_launch_fixed_corr<T>(d, c->stream));
+        CK(nrr_launch_xterm<T>(d, NRR_MODE_EVAL, c->stream));
+        CK(nrr_launch_energy<T>(d, NRR_MODE_EVAL, c->grid_energy, c->stream));
+        CK(cudaMemcpyAsync(c->h_state->E_eval, &c->d_state->E_eval, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        *E = c->h_state->E_eval[0];
+        return NRR_OK;
+    };
+    auto read_scal = [&]() -> nrr_status {
+        CK(cudaMemcpyAsync(hs, scal, sizeof hs, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return NRR_OK;
+    };
+    for (int outer = 0; outer < max_outer && !h.done; ++outer) {
+        // the device state (stage parameters read by the kernels) follows
+        // the host's decisions of the previous iteration
+        if (outer > 0) {
+            if ((st = push_state(c)) != NRR_OK) return st;
+        }
+        if ((st = pull_state(c)) != NRR_OK) return st;
+        if (h.status != 0) break;
+        // ---- closest points and the energy at X^k (stopping tests as Algorithm 2)
+        CK(cudaMemcpyAsync(d.Xeval, d.X, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream));
+        double E = 0.0;
+        if ((st = energy_at_eval(true, &E)) != NRR_OK) return st;
+        h.E = E;
+        h.E_align = h.E_eval[1]; h.E_reg = h.E_eval[2]; h.E_rot = h.E_eval[3];
+        h.n_passes += 1;
+        h.kept = 1;
+        h.solved = 0;
+        if (h.rel_tol > 0 && std::isfinite(h.E_prev) && std::fabs(h.E_prev - E) < h.rel_tol * std::fabs(h.E_prev)) {
+            host_end_stage(h);
+            continue;
+        }
+        h.E_prev = E;
+        CK(cudaMemcpyAsync(vk, vhat_eval(), vbytes, cudaMemcpyDeviceToDevice, c->stream));
+        // ---- inner L-BFGS on the surrogate (closest points held)
+        CK(cudaMemcpyAsync(Xk, d.X, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(nrr_launch_gradient<T>(d, g, nullptr, c->d_order, grid_g, c->stream));
+        double f = E, g0 = 0.0;
+        int mk = 0, head = 0;
+        for (int it = 0; it < lb.max_inner; ++it) {
+            CK(nrr_launch_lbfgs_dir<T>(n, g, S, Y, mk, head, m, dv, scal, c->stream));
+            if ((st = read_scal()) != NRR_OK) return st;
+            if (it == 0) g0 = hs[1];
+            if (!(hs[1] > lb.g_tol * g0)) break;
+            const double gd = hs[0];
+            double t = 1.0, Et = 0.0;
+            bool accepted = false;
+            for (int k = 0; k <= lb.max_halvings; ++k) {
+                CK(nrr_launch_lbfgs_axpy<T>(n, Xk, t, dv, d.Xeval, c->stream));
+                if ((st = energy_at_eval(false, &Et)) != NRR_OK) return st;
+                if (Et <= f + lb.c1 * t * gd) { accepted = true; break; }
+                t *= 0.5;
+            }
+            if (!accepted) break;
+            CK(nrr_launch_gradient<T>(d, gn, nullptr, c->d_order, grid_g, c->stream));
+            CK(nrr_launch_lbfgs_pair<T>(n, Xk, d.Xeval, g, gn, S, Y, head, scal, c->stream));
+            if ((st = read_scal()) != NRR_OK) return st;
+            if (hs[2] > 1e-12 * hs[3] * hs[4]) {
+                head = (head + 1) % m;
+                mk = std::min(mk + 1, m);
+            }
+            f = Et;
+        }
+        // ---- the new outer iterate and its displacement
+        CK(cudaMemcpyAsync(d.X, Xk, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(d.Xeval, Xk, sizeof(T) * n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(nrr_launch_fixed_corr<T>(d, c->stream));
+        CK(nrr_launch_max_disp<T>((int)P, vhat_eval(), vk, scal, c->stream));
+        if ((st = read_scal()) != NRR_OK) return st;
+        h.max_disp = std::sqrt(hs[6]);
+        h.solved = 1;
+        h.n_solves += 1;
+        h.n_solves_stage += 1;
+        if ((h.rel_tol <= 0 && h.max_disp < h.eps) || h.n_solves_stage >= h.max_iters_stage) host_end_stage(h);
+    }
+    // later passes of Algorithm 2 start a fresh Anderson history; the
+    // evaluation buffer holds v_hat at the last iterate
+    h.aa_count = 0;
+    h.aa_head = 0;
+    h.just_reverted = 0;
+    h.pending_stop = 0;
+    h.skip = 0;
+    h.vlast = h.vk ^ 1;
+    return push_state(c);
+}
+
+// ---------------------------------------------------------------------------
 // Checkpoint / resume: the solver state that a pass reads and that later
 // passes do not rebuild - the device control block, the iterate X, the MM
 // results G, G_prev, F_prev, the Anderson rings dF, dG and both deformed-
@@ -1240,6 +1395,8 @@ void nrr_destroy(nrr_ctx* c) {
     if (c->d_ck) cudaFree(c->d_ck);
     if (c->d_adj) cudaFree(c->d_adj);
     if (c->d_adjd) cudaFree(c->d_adjd);
+    if (c->lb_buf) cudaFree(c->lb_buf);
+    if (c->lb_t) cudaFree(c->lb_t);
     if (c->d_state) cudaFree(c->d_state);
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->aux) cudaStreamDestroy(c->aux);
@@ -1907,6 +2064,38 @@ nrr_status nrr_backward(nrr_ctx* c, int mode, const double* X, double* grad_X, d
     if (grad_src) CK(cudaMemcpyAsync(grad_src, gv, sizeof(double) * (size_t)c->P * 3, cudaMemcpyDefault, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return NRR_OK;
+}
+
+void nrr_lbfgs_params_default(nrr_lbfgs_params* p) {
+    if (!p) return;
+    p->m = 5;
+    p->c1 = 1e-4;
+    p->g_tol = 1e-3;
+    p->max_inner = 20;
+    p->max_halvings = 30;
+}
+
+nrr_status nrr_solve_lbfgs(nrr_ctx* c, const nrr_lbfgs_params* params, int max_outer, nrr_step_info* info) {
+    NvtxRange nvtx_range("nrr_solve_lbfgs");
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (c->failed) return fail(c, NRR_E_STATE, "context failed earlier: " + c->err);
+    nrr_lbfgs_params lb;
+    if (params) lb = *params; else nrr_lbfgs_params_default(&lb);
+    if (lb.m < 1 || lb.m > NRR_AA_MMAX || lb.max_inner < 1 || lb.max_halvings < 0 || lb.max_halvings > 60 ||
+        !(lb.c1 > 0 && lb.c1 < 1) || !(lb.g_tol >= 0 && lb.g_tol < 1))
+        return fail(c, NRR_E_INVALID, "nrr_solve_lbfgs: m in 1..8, max_inner >= 1, max_halvings in 0..60, "
+                                      "0 < c1 < 1, 0 <= g_tol < 1");
+    const int cap = max_outer > 0 ? max_outer : c->prm.max_total_passes;
+    nrr_status st = c->fp64 ? lbfgs_t<double>(c, lb, cap) : lbfgs_t<float>(c, lb, cap);
+    if (st != NRR_OK) { c->failed = true; return st; }
+    st = pull_state(c);
+    if (st != NRR_OK) return st;
+    fill_info(*c->h_state, info);
+    if (c->h_state->status != 0) {
+        c->failed = true;
+        return fail(c, (nrr_status)c->h_state->status, "device-side check failed");
+    }
+    return c->h_state->done ? NRR_OK : NRR_E_NOT_CONVERGED;
 }
 
 nrr_status nrr_unroll(nrr_ctx* c, int K, const double* X0, double* XK) {

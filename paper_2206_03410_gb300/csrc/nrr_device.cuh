@@ -130,6 +130,26 @@ enum NrrMode { NRR_MODE_PASS = 0, NRR_MODE_EVAL = 1, NRR_MODE_RAW = 2 };
 // Launch helpers (defined in the kernel translation units).
 template <typename T>
 cudaError_t nrr_launch_nn(const DevProblem<T>& d, int mode, int lanes_per_query, cudaStream_t s);
+// v_hat at Xeval and d^2 to the held closest points u (rho, u unchanged).
+template <typename T>
+cudaError_t nrr_launch_fixed_corr(const DevProblem<T>& d, cudaStream_t s);
+// Vector kernels of the L-BFGS comparison solver (kernels_lbfgs.cu), on n =
+// 12 N values: the two-loop direction d = -H g from a ring of mk pairs
+// (S, Y [m][n], newest at slot (head - 1) mod m) with scal[0] = g.d and
+// scal[1] = |g|; Xout = Xk + t d; the new pair s = Xt - Xk, y = gn - g
+// into slot `slot` with scal[2..5] = y.s, |y|, |s|, |gn|, then Xk = Xt and
+// g = gn; and the largest |a_i - b_i| of two v_hat buffers into scal[6].
+template <typename T>
+cudaError_t nrr_launch_lbfgs_dir(int n, const double* g, const double* S, const double* Y, int mk, int head, int m,
+                                 double* dvec, double* scal, cudaStream_t s);
+template <typename T>
+cudaError_t nrr_launch_lbfgs_axpy(int n, const T* Xk, double t, const double* dvec, T* Xout, cudaStream_t s);
+template <typename T>
+cudaError_t nrr_launch_lbfgs_pair(int n, T* Xk, const T* Xt, double* g, const double* gn, double* S, double* Y,
+                                  int slot, double* scal, cudaStream_t s);
+template <typename T>
+cudaError_t nrr_launch_max_disp(int P, const T* a, const T* b, double* scal, cudaStream_t s);
+
 // Tensor-core candidate search with an exact float re-rank (float path,
 // NRR_MODE_PASS or NRR_MODE_EVAL): the outputs of nrr_launch_nn, bit for bit.
 cudaError_t nrr_launch_nn_tc(const DevProblem<float>& d, int mode, cudaStream_t s);

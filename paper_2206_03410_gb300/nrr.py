@@ -60,6 +60,16 @@ class NrrParams(ctypes.Structure):
     ]
 
 
+class NrrLbfgsParams(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int),
+        ("c1", ctypes.c_double),
+        ("g_tol", ctypes.c_double),
+        ("max_inner", ctypes.c_int),
+        ("max_halvings", ctypes.c_int),
+    ]
+
+
 class NrrLaunchConfig(ctypes.Structure):
     _fields_ = [
         ("nn_lanes_per_query", ctypes.c_int),
@@ -151,6 +161,9 @@ _SIGS = [
     ("nrr_set_launch_config", ctypes.c_int, [_VP, ctypes.POINTER(NrrLaunchConfig)]),
     ("nrr_tune", ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(NrrLaunchConfig)]),
     ("nrr_batch_tune", ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(NrrLaunchConfig)]),
+    ("nrr_lbfgs_params_default", None, [ctypes.POINTER(NrrLbfgsParams)]),
+    ("nrr_solve_lbfgs", ctypes.c_int, [_VP, ctypes.POINTER(NrrLbfgsParams), ctypes.c_int,
+                                       ctypes.POINTER(NrrStepInfo)]),
     ("nrr_last_error", ctypes.c_char_p, [_VP]),
 ]
 
@@ -256,6 +269,22 @@ def nrr_step(ctx) -> NrrStepInfo:
 def nrr_solve(ctx, max_passes: int = 0) -> NrrStepInfo:
     info = NrrStepInfo()
     _check(load().nrr_solve(ctx, int(max_passes), ctypes.byref(info)), ctx,
+           ok=(NRR_OK, NRR_E_NOT_CONVERGED))
+    return info
+
+
+def nrr_solve_lbfgs(ctx, max_outer: int = 0, **lbfgs) -> NrrStepInfo:
+    """The preliminary version's solver (fixed closest points + inner
+    L-BFGS) from the current state; keyword arguments override the fields of
+    nrr_lbfgs_params (m, c1, g_tol, max_inner, max_halvings)."""
+    p = NrrLbfgsParams()
+    load().nrr_lbfgs_params_default(ctypes.byref(p))
+    for k, v in lbfgs.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    info = NrrStepInfo()
+    _check(load().nrr_solve_lbfgs(ctx, ctypes.byref(p), int(max_outer), ctypes.byref(info)), ctx,
            ok=(NRR_OK, NRR_E_NOT_CONVERGED))
     return info
 
@@ -547,6 +576,9 @@ class Registration:
 
     def solve(self, max_passes: int = 0) -> NrrStepInfo:
         return nrr_solve(self.ctx, max_passes)
+
+    def solve_lbfgs(self, max_outer: int = 0, **lbfgs) -> NrrStepInfo:
+        return nrr_solve_lbfgs(self.ctx, max_outer, **lbfgs)
 
     def enqueue_passes(self, n: int):
         nrr_enqueue_passes(self.ctx, n)

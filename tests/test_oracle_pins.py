@@ -738,3 +738,57 @@ def test_singular_system_keeps_free_translation():
     t2 = reg2.terms()
     _, _, parts2 = S.normal_equations(reg2.V, reg2.U, reg2.graph, t2, reg2.nu_a, reg2.nu_r, a, b)
     assert S.free_components(reg2.graph, parts2["wa"]) == []
+
+
+def test_lbfgs_two_loop_satisfies_the_secant_equation():
+    """The two-loop recursion applies the L-BFGS inverse-Hessian estimate H,
+    which satisfies the secant equation of its newest pair, H y = s, and is
+    symmetric positive definite (g.d < 0 for d = -H g)."""
+    from oracle.lbfgs import two_loop
+    rng = _rng(21)
+    n = 12
+    Q = rng.standard_normal((n, n))
+    A = Q @ Q.T + n * np.eye(n)
+    S = [rng.standard_normal(n) for _ in range(5)]
+    Y = [A @ s for s in S]
+    d = two_loop(Y[-1], S, Y)
+    assert np.abs(d + S[-1]).max() < 1e-12 * np.abs(S[-1]).max()
+    for _ in range(3):
+        g = rng.standard_normal(n)
+        assert float(np.dot(g, two_loop(g, S, Y))) < 0
+    # no pairs: a unit-length steepest-descent step
+    g = rng.standard_normal(n)
+    assert np.allclose(two_loop(g, [], []), -g / np.linalg.norm(g), rtol=1e-15, atol=0)
+
+
+def test_lbfgs_reaches_the_quadratic_minimiser():
+    """With the squared-l2 robust function and beta = 0 the surrogate of the
+    preliminary version's solver (closest points held) is the quadratic
+    |F X - Q|^2 + alpha |H X - Y|^2, whose minimiser solves the normal
+    equations K X = B (Sec. 3.3.2, all weights 1): the inner L-BFGS, run to a
+    tight gradient tolerance, reaches that direct solution."""
+    from oracle.lbfgs import LbfgsParams, LbfgsRegistration
+    pair = synth.tiny_pair(500, 550, seed=41, noise=0.002)
+    reg = LbfgsRegistration(pair.src, pair.tgt, Params(radius=0.35, robust="l2", beta=0.0, alpha=0.5),
+                            LbfgsParams(max_inner=3000, g_tol=1e-11))
+    X0 = _near_identity_X(reg.graph.N, _rng(2), scale=0.02)
+    t = reg.terms(X0)
+    a, b = reg.weights()
+    K, B, _ = S.normal_equations(reg.V, reg.U, reg.graph, t, reg.nu_a, reg.nu_r, a, b, robust="l2")
+    X_direct = S.solve_normal_equations(K, B)
+    X_lb = reg.minimise_surrogate(X0, t["rho"])
+    assert np.abs(X_lb - X_direct).max() < 1e-7 * np.abs(X_direct).max()
+
+
+def test_lbfgs_outer_energies_decrease():
+    """Each outer iteration minimises a majoriser of E that touches it at X^k
+    (closest points held) with sufficient-decrease steps only, so the
+    energies of the outer iterates never increase within a stage."""
+    from oracle.lbfgs import LbfgsRegistration
+    pair = synth.tiny_pair(600, 660, seed=43, noise=0.002, outliers=0.05)
+    reg = LbfgsRegistration(pair.src, pair.tgt, Params(radius=0.3, max_iters_per_stage=6))
+    recs = [reg.step() for _ in range(6)]
+    assert all(r.stage == 0 for r in recs)
+    E = [r.E for r in recs]
+    assert all(E[k + 1] <= E[k] * (1 + 1e-12) for k in range(len(E) - 1)), E
+    assert all(steps >= 1 for steps, _ in reg.inner)
