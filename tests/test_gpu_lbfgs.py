@@ -36,13 +36,17 @@ def relmax(a, b):
 def test_fp64_outer_iterations_match_oracle():
     nrr = _nrr()
     pair = synth.tiny_pair(800, 880, seed=31, noise=0.002, outliers=0.05)
-    kw = dict(radius=0.3, aa_m=5, max_iters_per_stage=3)
+    # four stages (nu_a 0.05, 0.025, 0.0125, 0.01) of at most three outer
+    # iterations: the run below crosses a stage end
+    kw = dict(radius=0.3, aa_m=5, max_iters_per_stage=3, nu_a=0.05, nu_r=0.2, nu_a_min=0.01)
     ora = LbfgsRegistration(pair.src, pair.tgt, Params(**kw), LbfgsParams(max_inner=8))
     reg = nrr.Registration(pair.src, pair.tgt, precision="fp64", **kw)
     for k in range(5):
         rec = ora.step()
+        assert rec is not None
         info = reg.solve_lbfgs(1, max_inner=8)
-        assert info.n_passes == k + 1 and info.stage == rec.stage, k
+        # info.stage is the stage after the pass (a stage end moves it on)
+        assert info.n_passes == k + 1 and info.stage == ora.stage, k
         assert abs(info.E - rec.E) < 1e-9 * abs(rec.E), (k, info.E, rec.E)
         X = reg.transforms()
         assert relmax(X, ora.X) < 1e-8, (k, relmax(X, ora.X))
