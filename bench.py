@@ -406,6 +406,42 @@ def run_variants(nrr, stream) -> dict:
     return out
 
 
+def run_solver_comparison(nrr, stream) -> dict:
+    """Sec. 4.3's comparison of the two solvers of the same energy on the
+    partial-overlap workload (mixed precision, stages end at relative dE <
+    1e-6): Algorithm 2 (MM + Anderson) against the preliminary version's
+    solver (closest points held, inner L-BFGS; nrr_solve_lbfgs): wall time
+    to return, outer iterations, and both final energies evaluated at the
+    MM run's final nu (lower is better)."""
+    import torch
+    pair = synth.workload("sphere50k_partial")
+    kw = {k: v for k, v in pair.params.items() if k not in ("precision", "iters", "unroll")}
+    kw["rel_energy_tol"] = 1e-6
+    src = torch.from_numpy(pair.src).cuda()
+    tgt = torch.from_numpy(pair.tgt).cuda()
+    out = {"workload": "sphere50k_partial (P=%d, T=%d), mixed, stages end at relative dE < 1e-6" % (pair.P, pair.T)}
+    regs, finals = {}, {}
+    for name in ("mm_anderson", "lbfgs"):
+        r = nrr.Registration(src, tgt, stream=stream.cuda_stream, precision="mixed", **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = r.solve(20000) if name == "mm_anderson" else r.solve_lbfgs(20000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"ms": round(dt * 1e3, 2), "outer_iters": info.n_solves, "stages": info.stage + 1,
+                     "done": info.done}
+        regs[name], finals[name] = r, (r.transforms(), info)
+    ref = regs["mm_anderson"]
+    i0 = finals["mm_anderson"][1]
+    ref.set_stage(i0.nu_a, i0.nu_r)
+    for name in finals:
+        out[name]["E_final_at_mm_nu"] = float(ref.energy(finals[name][0])[0])
+    for r in regs.values():
+        r.close()
+    out["lbfgs_time_ratio"] = round(out["lbfgs"]["ms"] / out["mm_anderson"]["ms"], 2)
+    return out
+
+
 def reduce_over_ranks(total_ms: float, iters: float, device) -> tuple[float, float]:
     """Whole-job numbers over the ranks of a replica run: the slowest rank's
     timed milliseconds and the sum of every rank's iterations."""
@@ -614,6 +650,7 @@ def run_ours(args):
         # ---- robust-norm variants (Sec. 4.2) on the partial-overlap workload ----
         if not args.no_variants:
             result["variants"] = run_variants(nrr, stream)
+            result["solvers"] = run_solver_comparison(nrr, stream)
 
         # ---- end to end through the public API from pinned host buffers ----
         hs = torch.from_numpy(pair.src).pin_memory()
@@ -700,6 +737,7 @@ def main():
         "batch": res.get("batch"),
         "launch": res.get("launch"),
         "variants": res.get("variants"),
+        "solvers": res.get("solvers"),
     }
     if ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(pair, kw)

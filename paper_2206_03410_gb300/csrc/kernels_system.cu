@@ -248,8 +248,11 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
 // entries of its symmetric upper triangle. Off-diagonal blocks go four to a
 // warp, 8 lanes each. Warps with diagonal blocks come first.
 // ---------------------------------------------------------------------------
+// entries per lane loaded together (independent gather chains in flight)
+constexpr int kU = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) assemble_kernel(DevProblem<T> d) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) assemble_kernel(DevProblem<T> d) {
     NrrState* st = d.st;
     if (st->done || st->skip) return;
     const int lane = threadIdx.x & 31;
@@ -265,7 +268,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) assemble_ker
         if (wk < N) {
             // ---- diagonal block of node n and row n of B: one warp ----
             const int n = wk;
-            const int b = d.diag_blk[n];
+            const int4 desc = __ldg(d.asm_diag + n);   // {block, entries, first edge}
+            const int b = desc.x;
+            const int adj1 = __ldg(d.adj_ptr + n + 1);
             const T pnx = d.p[3 * n], pny = d.p[3 * n + 1], pnz = d.p[3 * n + 2];
             T acc[10];
             T accB[12];
@@ -273,27 +278,79 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) assemble_ker
             for (int t = 0; t < 10; ++t) acc[t] = 0;
 #pragma unroll
             for (int t = 0; t < 12; ++t) accB[t] = 0;
-            for (int e = d.ent_ptr[b] + lane, e_end = d.ent_ptr[b + 1]; e < e_end; e += 32) {
-                const int i = d.ent[e] >> 6;
-                const T wn = d.ent_w[2 * e];
-                const T wai = d.wa[i];
-                const T an[4] = {d.v[i] - pnx, d.v[P + i] - pny, d.v[2 * P + i] - pnz, (T)1};
-                // Q_i = u_rho(i) - sum_j w_ij p_j
-                const T Qx = d.u[i] - d.pbar[i];
-                const T Qy = d.u[P + i] - d.pbar[P + i];
-                const T Qz = d.u[2 * P + i] - d.pbar[2 * P + i];
-                const T cb = wai * wn;
-                const T c = cb * wn;
+            // kU entries per lane at a time (e, e + 32, ...): every gather of
+            // the batch is issued before the first is used; each lane still
+            // adds its entries in increasing order
+            const int e_end = desc.z;
+            for (int e0 = desc.y + lane; e0 < e_end; e0 += 32 * kU) {
+                int ii[kU];
+                T wq[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int e = e0 + 32 * u;
+                    ii[u] = e < e_end ? __ldg(d.ent + e) >> 6 : -1;
+                    wq[u] = e < e_end ? __ldg(d.ent_q + e) : (T)0;
+                }
+                T vx[kU], vy[kU], vz[kU], wa[kU], qx[kU], qy[kU], qz[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int i = ii[u] < 0 ? 0 : ii[u];
+                    vx[u] = d.v[i]; vy[u] = d.v[P + i]; vz[u] = d.v[2 * P + i];
+                    wa[u] = d.wa[i];
+                    // Q_i = u_rho(i) - sum_j w_ij p_j
+                    qx[u] = d.u[i] - d.pbar[i];
+                    qy[u] = d.u[P + i] - d.pbar[P + i];
+                    qz[u] = d.u[2 * P + i] - d.pbar[2 * P + i];
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    if (ii[u] < 0) break;
+                    const T an[4] = {vx[u] - pnx, vy[u] - pny, vz[u] - pnz, (T)1};
+                    const T cb = wa[u] * wq[u];
+                    const T c = cb * wq[u];
+                    int t = 0;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const T cr = c * an[r];
+#pragma unroll
+                        for (int s2 = r; s2 < 4; ++s2) acc[t++] += cr * an[s2];
+                        const T br = cb * an[r];
+                        accB[3 * r + 0] += br * qx[u];
+                        accB[3 * r + 1] += br * qy[u];
+                        accB[3 * r + 2] += br * qz[u];
+                    }
+                }
+            }
+            // the alignment part of the (t, t) entry, summed apart: 0 when no
+            // point that node n influences has alignment weight (singular K,
+            // kernels_solve.cu)
+            T a33 = acc[9];
+            // regularisation part, one edge of node n per lane (all lanes'
+            // loads in flight together). Pair (n, j): its H row is
+            // [0,0,0,-r] at X_n, so r^2 on entry (3,3) and B row 3 gets
+            // -r y with y = r (p_n - p_j); reverse pair (j, n): h = r'[(p_j -
+            // p_n)^T, 1] at X_n adds h h^T and h y'^T with y' = r'(p_j - p_n)
+            for (int e = desc.w + lane; e < adj1; e += 32) {
+                const int j = d.e_j[e];
+                const int er = d.e_rev[e];
+                const T r = d.e_r[e], w = alpha * d.wr[e];
+                const T r2 = d.e_r[er], w2 = alpha * d.wr[er];
+                const T dj[3] = {d.p[3 * j] - pnx, d.p[3 * j + 1] - pny, d.p[3 * j + 2] - pnz};
+                const T wrr = w * r * r;
+                acc[9] += wrr;
+                accB[9] += wrr * dj[0];
+                accB[10] += wrr * dj[1];
+                accB[11] += wrr * dj[2];
+                const T h[4] = {r2 * dj[0], r2 * dj[1], r2 * dj[2], r2};
                 int t = 0;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const T cr = c * an[r];
+                for (int a = 0; a < 4; ++a) {
+                    const T wh = w2 * h[a];
 #pragma unroll
-                    for (int s2 = r; s2 < 4; ++s2) acc[t++] += cr * an[s2];
-                    const T br = cb * an[r];
-                    accB[3 * r + 0] += br * Qx;
-                    accB[3 * r + 1] += br * Qy;
-                    accB[3 * r + 2] += br * Qz;
+                    for (int cc = a; cc < 4; ++cc) acc[t++] += wh * h[cc];
+                    accB[3 * a + 0] += wh * h[0];
+                    accB[3 * a + 1] += wh * h[1];
+                    accB[3 * a + 2] += wh * h[2];
                 }
             }
 #pragma unroll
@@ -302,11 +359,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) assemble_ker
                 for (int t = 0; t < 10; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
 #pragma unroll
                 for (int t = 0; t < 12; ++t) accB[t] += __shfl_xor_sync(0xffffffffu, accB[t], o);
+                a33 += __shfl_xor_sync(0xffffffffu, a33, o);
             }
             if (lane != 0) continue;
-            // alignment part of the (t, t) entry: 0 when no point that node n
-            // influences has alignment weight (singular K, kernels_solve.cu)
-            d.anode[n] = acc[9];
+            d.anode[n] = a33;
             T K16[16];
             {
                 int t = 0;
@@ -318,29 +374,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) assemble_ker
                         K16[4 * s2 + r] = acc[t];
                         ++t;
                     }
-            }
-            // edges (n, j): H row has [0,0,0,-r] at X_n -> r^2 on entry (3,3);
-            // B row 3 gets -r * y with y = r (p_n - p_j)
-            for (int e = d.adj_ptr[n]; e < d.adj_ptr[n + 1]; ++e) {
-                const int j = d.e_j[e];
-                const T r = d.e_r[e], w = alpha * d.wr[e];
-                K16[15] += w * r * r;
-                accB[9] -= w * r * r * (pnx - d.p[3 * j]);
-                accB[10] -= w * r * r * (pny - d.p[3 * j + 1]);
-                accB[11] -= w * r * r * (pnz - d.p[3 * j + 2]);
-                // reverse pair (j, n): h = r'[(p_j - p_n)^T, 1] at X_n
-                const int er = d.e_rev[e];
-                const T r2 = d.e_r[er], w2 = alpha * d.wr[er];
-                const T h[4] = {r2 * (d.p[3 * j] - pnx), r2 * (d.p[3 * j + 1] - pny),
-                                r2 * (d.p[3 * j + 2] - pnz), r2};
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-#pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) K16[4 * a + cc] += w2 * h[a] * h[cc];
-                    accB[3 * a + 0] += w2 * h[a] * h[0];
-                    accB[3 * a + 1] += w2 * h[a] * h[1];
-                    accB[3 * a + 2] += w2 * h[a] * h[2];
-                }
             }
             // rotation term: beta on A-rows, B rows 0..2 += beta R_n^T
             K16[0] += beta; K16[5] += beta; K16[10] += beta;
@@ -358,26 +391,44 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) assemble_ker
             const int q = (wk - N) * 4 + (lane >> 3);
             const bool active = q < n_off;
             const int lane8 = lane & 7;
-            const int b = d.offd_blk[active ? q : n_off - 1];
-            const int n = d.blk_row[b], k = d.bsr_col[b];
+            const int4 desc = __ldg(d.asm_off + (active ? q : n_off - 1));   // {block, entries, pair}
+            const int4 nk = __ldg(d.asm_off2 + (active ? q : n_off - 1));    // {n, k, reverse pair}
+            const int b = desc.x;
+            const int n = nk.x, k = nk.y;
             const T pnx = d.p[3 * n], pny = d.p[3 * n + 1], pnz = d.p[3 * n + 2];
             const T pkx = d.p[3 * k], pky = d.p[3 * k + 1], pkz = d.p[3 * k + 2];
             T acc[16];
 #pragma unroll
             for (int t = 0; t < 16; ++t) acc[t] = 0;
-            const int e_end = active ? d.ent_ptr[b + 1] : 0;
-            for (int e = d.ent_ptr[b] + lane8; e < e_end; e += 8) {
-                const int i = d.ent[e] >> 6;
-                const T wn = d.ent_w[2 * e], wk2 = d.ent_w[2 * e + 1];
-                const T vx = d.v[i], vy = d.v[P + i], vz = d.v[2 * P + i];
-                const T an[4] = {vx - pnx, vy - pny, vz - pnz, (T)1};
-                const T ak[4] = {vx - pkx, vy - pky, vz - pkz, (T)1};
-                const T c = d.wa[i] * wn * wk2;
+            const int e_end = active ? desc.z : 0;
+            for (int e0 = desc.y + lane8; e0 < e_end; e0 += 8 * kU) {
+                int ii[kU];
+                T wq[kU];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const T cr = c * an[r];
+                for (int u = 0; u < kU; ++u) {
+                    const int e = e0 + 8 * u;
+                    ii[u] = e < e_end ? __ldg(d.ent + e) >> 6 : -1;
+                    wq[u] = e < e_end ? __ldg(d.ent_q + e) : (T)0;
+                }
+                T vx[kU], vy[kU], vz[kU], wa[kU];
 #pragma unroll
-                    for (int s2 = 0; s2 < 4; ++s2) acc[4 * r + s2] += cr * ak[s2];
+                for (int u = 0; u < kU; ++u) {
+                    const int i = ii[u] < 0 ? 0 : ii[u];
+                    vx[u] = d.v[i]; vy[u] = d.v[P + i]; vz[u] = d.v[2 * P + i];
+                    wa[u] = d.wa[i];
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    if (ii[u] < 0) break;
+                    const T an[4] = {vx[u] - pnx, vy[u] - pny, vz[u] - pnz, (T)1};
+                    const T ak[4] = {vx[u] - pkx, vy[u] - pky, vz[u] - pkz, (T)1};
+                    const T c = wa[u] * wq[u];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const T cr = c * an[r];
+#pragma unroll
+                        for (int s2 = 0; s2 < 4; ++s2) acc[4 * r + s2] += cr * ak[s2];
+                    }
                 }
             }
 #pragma unroll
@@ -388,14 +439,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) assemble_ker
             if (lane8 != 0 || !active) continue;
             // pair (n, k): block (n, k) gets -r w h_k^T on row 3,
             // h_k = r [(p_n - p_k)^T, 1]
-            const int e = d.bsr_edge[b];
+            const int e = desc.w;
             const T r = d.e_r[e], w = alpha * d.wr[e];
             const T hk[4] = {r * (pnx - pkx), r * (pny - pky), r * (pnz - pkz), r};
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) acc[12 + cc] -= w * r * hk[cc];
             // pair (k, n): block (n, k) gets -r' w' h_n on column 3,
             // h_n = r' [(p_k - p_n)^T, 1]
-            const int er = d.e_rev[e];
+            const int er = nk.z;
             const T r2 = d.e_r[er], w2 = alpha * d.wr[er];
             const T hn[4] = {r2 * (pkx - pnx), r2 * (pky - pny), r2 * (pkz - pnz), r2};
 #pragma unroll
@@ -438,7 +489,7 @@ __global__ void __launch_bounds__(kThreads) gradient_kernel(DevProblem<T> d, dou
         const int e_end = active ? d.ent_ptr[bdg + 1] : 0;
         for (int e = d.ent_ptr[bdg] + lane8; e < e_end; e += 8) {
             const int i = d.ent[e] >> 6;
-            const T wn = d.ent_w[2 * e];
+            const T wn = d.ent_q[e];   // diagonal block: w_in
             const T c = (T)2 * d.wa[i] * wn;
             const T an[4] = {d.v[i] - pnx, d.v[P + i] - pny, d.v[2 * P + i] - pnz, (T)1};
             const T rx = vh[i] - d.u[i], ry = vh[P + i] - d.u[P + i], rz = vh[2 * P + i] - d.u[2 * P + i];

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kThreads)
         const int e_end = active ? d.ent_ptr[bdg + 1] : 0;
         for (int e = d.ent_ptr[bdg] + lane8; e < e_end; e += 8) {
             const int i = d.ent[e] >> 6;
-            const T wn = d.ent_w[2 * e];
+            const T wn = d.ent_q[e];   // diagonal block: w_in
             const T an[4] = {d.v[i] - pnx, d.v[P + i] - pny, d.v[2 * P + i] - pnz, (T)1};
             const T ex = ebuf[i], ey = ebuf[P + i], ez = ebuf[2 * P + i];
 #pragma unroll

@@ -637,11 +637,14 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         std::vector<int> fill(comp_ptr.begin(), comp_ptr.end() - 1);
         for (int j = 0; j < N; ++j) comp_nodes[(size_t)fill[(size_t)label[(size_t)j]]++] = j;
     }
-    std::vector<T> ent_w(ent.size() * 2);
+    // one weight per entry: w_in on a diagonal block (the entry's two slots
+    // are the same node), w_in w_ik (product in double, rounded once) off it
+    std::vector<T> ent_q(ent.size());
     for (size_t e = 0; e < ent.size(); ++e) {
         const int ii = ent[e] >> 6, sa = (ent[e] >> 3) & 7, sb = ent[e] & 7;
-        ent_w[2 * e] = infl_w[(size_t)infl_ptr[(size_t)ii] + sa];
-        ent_w[2 * e + 1] = infl_w[(size_t)infl_ptr[(size_t)ii] + sb];
+        const double wa_ = (double)infl_w[(size_t)infl_ptr[(size_t)ii] + sa];
+        const double wb_ = (double)infl_w[(size_t)infl_ptr[(size_t)ii] + sb];
+        ent_q[e] = (T)(sa == sb ? wa_ : wa_ * wb_);
     }
     std::vector<int> blk_row((size_t)c->nblk);
     for (int n = 0; n < N; ++n)
@@ -737,7 +740,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     {
         T *ew_, *pb_;
         int* br_;
-        CK(upload(c, &ew_, ent_w)); d.ent_w = ew_;
+        CK(upload(c, &ew_, ent_q)); d.ent_q = ew_;
         CK(upload(c, &pb_, pbar)); d.pbar = pb_;
         CK(upload(c, &br_, blk_row)); d.blk_row = br_;
         std::vector<int> diag_blk((size_t)N), offd_blk;
@@ -749,6 +752,21 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         int *db_, *ob_;
         CK(upload(c, &db_, diag_blk)); d.diag_blk = db_;
         CK(upload(c, &ob_, offd_blk)); d.offd_blk = ob_;
+        std::vector<int4> adiag((size_t)N), aoff(offd_blk.size()), aoff2(offd_blk.size());
+        for (int n = 0; n < N; ++n) {
+            const int b = diag_blk[(size_t)n];
+            adiag[(size_t)n] = make_int4(b, ent_cnt[(size_t)b], ent_cnt[(size_t)b + 1], adj_ptr[(size_t)n]);
+        }
+        for (size_t q = 0; q < offd_blk.size(); ++q) {
+            const int b = offd_blk[q];
+            const int e = be[(size_t)b];
+            aoff[q] = make_int4(b, ent_cnt[(size_t)b], ent_cnt[(size_t)b + 1], e);
+            aoff2[q] = make_int4(blk_row[(size_t)b], bc[(size_t)b], e_rev[(size_t)e], 0);
+        }
+        int4 *ad_, *ao_, *ao2_;
+        CK(upload(c, &ad_, adiag)); d.asm_diag = ad_;
+        CK(upload(c, &ao_, aoff)); d.asm_off = ao_;
+        CK(upload(c, &ao2_, aoff2)); d.asm_off2 = ao2_;
     }
     CK(upload(c, &d.X, X0));
     CK(dalloc(c, &d.Xeval, (size_t)N * 12));

@@ -14,7 +14,8 @@
 //   system: block-sparse K in BSR with 4x4 blocks on the node-graph pattern
 //     (bsr_ptr [N+1], bsr_col [nblk], bsr_edge [nblk] = directed pair (row,
 //     col) or -1 on the diagonal), Kv [nblk][16], B [N][12]; per block the
-//     list of (point, slot_row, slot_col) contributions (ent_ptr, ent).
+//     list of (point, slot_row, slot_col) contributions (ent_ptr, ent) and
+//     their skinning weights (ent_q, one value per entry).
 //   iterates: X, G, Gprev, Fprev [N][12]; Anderson rings dF, dG [m][N*12];
 //     PCG vectors r, z, p, q [N*12], block-Jacobi inverse Minv [N][16].
 #pragma once
@@ -88,10 +89,18 @@ struct DevProblem {
     const int* bsr_edge;
     const int* ent_ptr;
     const int* ent;         // packed (point << 6 | slot_row << 3 | slot_col)
-    const T* ent_w;         // [n_ent][2] (w_row, w_col) of the entry's point
+    const T* ent_q;         // [n_ent] weight of the entry: w_in on a diagonal block (n, n),
+                            // w_in w_ik (rounded once, from double) on a block (n, k)
     const int* blk_row;     // [nblk] row node of each block
     const int* diag_blk;    // [N] block (n, n) of each node
     const int* offd_blk;    // [nblk - N] the off-diagonal blocks, in BSR order
+    // assembly work descriptors (static), one load each: per node n
+    // {diagonal block, entry begin, entry end, first edge of n}; per
+    // off-diagonal block (BSR order) {block, entry begin, entry end, directed
+    // pair (n, k)} and {n, k, reverse pair, 0}
+    const int4* asm_diag;
+    const int4* asm_off;
+    const int4* asm_off2;
     const T* pbar;          // [3][P] sum_j w_ij p_j (constant part of Q_i)
     T* Kv;
     T* Bv;
