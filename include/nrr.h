@@ -128,6 +128,9 @@ typedef struct {
     int    robust;             /* nrr_robust; default NRR_WELSCH            */
     int    nu_schedule;        /* nrr_nu_schedule; default NRR_NU_ANNEAL
                                   (then `anneal` applies)                   */
+    int    graph_on_gpu;       /* 1: nrr_create builds the deformation graph
+                                  (Algorithm 1) on the GPU, the same graph
+                                  as the host construction; default 0       */
 } nrr_params;
 
 /* State after a pass (one execution of the repeat body of Algorithm 2). */
@@ -355,6 +358,20 @@ nrr_status nrr_get_graph(nrr_ctx* ctx, int32_t* node_src, int32_t* nidx,
 typedef struct nrr_graph nrr_graph;
 nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, double radius,
                            int max_influence);
+/* The same graph built on the GPU (Algorithm 1, Sec. 3.1, Euclidean
+ * reading): PCA by reductions and a 3x3 Jacobi eigen-solve, the visiting
+ * order by a radix sort of the projections, the greedy sampling as the
+ * lexicographically first maximal independent set of the radius graph in
+ * that order (rounds over a window that follows the sweep; each decision
+ * depends only on earlier final ones, so the result is the sequential
+ * one), then the influence sets, weights, edges and r_ij; every distance
+ * and projection in double without fused multiply-adds. src_xyz [P][3]
+ * float32, host or device; cuda_stream the stream to use (NULL: the legacy
+ * default stream); l-bar (and the default radius 5 l-bar) on the host.
+ * Errors as nrr_graph_build, plus NRR_E_CUDA. The handle is used with
+ * nrr_graph_sizes/get/destroy. */
+nrr_status nrr_graph_build_gpu(nrr_graph** out, const float* src_xyz, int64_t P, double radius, int max_influence,
+                               void* cuda_stream);
 nrr_status nrr_graph_sizes(const nrr_graph* g, int64_t* N, int64_t* n_edges, int32_t* max_influence,
                            double* radius);
 nrr_status nrr_graph_get(const nrr_graph* g, int32_t* node_src, int32_t* nidx, double* w,

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnrr.so")
 
 CU_SOURCES = ["kernels_nn.cu", "kernels_system.cu", "kernels_solve.cu", "kernels_aa.cu", "kernels_unroll.cu", "kernels_lbfgs.cu",
-              "nrr_api.cu", "noalloc.cu"]
+              "graph_gpu.cu", "nrr_api.cu", "noalloc.cu"]
 CPP_SOURCES = ["graph_build.cpp"]
 HEADERS = ["nrr_internal.h", "nrr_device.cuh", "nrr_rotation.cuh"]
 

@@ -1,0 +1,688 @@
+// Algorithm 1 (Sec. 3.1) on the GPU, with Euclidean distances in place of
+// geodesics (the point-cloud reading: the ball B(v_j) is {q : |v_j - q| < R},
+// strict), followed by the weights of Eq. (weight_data), the edges of the
+// capped influence sets and r_ij of Sec. 3.2. It builds the same graph as the
+// host code (graph_build.cpp) and the FP64 oracle: every distance is formed
+// in double as dx*dx + dy*dy + dz*dz with separate roundings (no fused
+// multiply-adds), and so is every projection on the PCA axis.
+//
+// Steps (all on the device; the host only sequences them and reads the
+// final arrays back):
+//  1. PCA: mean and covariance by fixed-order reductions, the 3x3 symmetric
+//     eigenproblem by cyclic Jacobi in one thread; the axis of the largest
+//     eigenvalue with its largest-magnitude entry made positive.
+//  2. The visiting order: projections sorted by a stable radix sort (ties
+//     keep the lower index).
+//  3. The greedy sampling. Visiting the points in that order, a point
+//     becomes a node iff no earlier node lies within R; this is the
+//     lexicographically first maximal independent set of the graph that
+//     joins points closer than R, ranked by the visiting order. It is
+//     computed in rounds over a window of ranks that follows the sweep: a
+//     point with an earlier node within R is covered; a point whose earlier
+//     neighbours within R are all covered is a node; any other point waits.
+//     Both decisions depend only on earlier, already final decisions, so the
+//     result is the sequential one whatever the order of the updates, and
+//     the lowest undecided rank is decided in every round.
+//  4. Influence sets (the K nearest nodes within R, ties to the lower node
+//     id), weights, the edges between the nodes of each set (sorted, unique)
+//     and r_ij.
+// Neighbours come from a uniform grid of cell size R (points sorted by cell
+// key, cells found by binary search of the sorted keys).
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "nrr_device.cuh"
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kRed = 256;   // CTAs of the fixed-order reductions
+
+__device__ __forceinline__ double sqd(double ax, double ay, double az, double bx, double by, double bz) {
+    const double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by), dz = __dsub_rn(az, bz);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// order-preserving map of a double to an unsigned key (-0 taken as +0)
+__device__ __forceinline__ unsigned long long dkey(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x + 0.0);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void to_double_kernel(const float* __restrict__ src, double* __restrict__ V, int64_t n3) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
+        V[k] = (double)src[k];
+}
+
+// per-CTA partial sums over a contiguous range of points (thread-strided,
+// then a fixed shuffle tree and the warps in order) of: mode 0 the
+// coordinates and their min/max; mode 1 the products (v - mu)(v - mu)^T
+__global__ void __launch_bounds__(kT) moments_kernel(const double* __restrict__ V, int64_t P, int mode,
+                                                     const double* __restrict__ mu, double* __restrict__ part) {
+    __shared__ double sh[kT / 32][12];
+    const int64_t per = (P + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = blockIdx.x * per, i1 = min(P, i0 + per);
+    double a[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a[k] = 0.0;
+    if (mode == 0) {
+        for (int k = 3; k < 6; ++k) a[k] = INFINITY;
+        for (int k = 6; k < 9; ++k) a[k] = -INFINITY;
+    }
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kT) {
+        const double x = V[3 * i], y = V[3 * i + 1], z = V[3 * i + 2];
+        if (mode == 0) {
+            a[0] += x; a[1] += y; a[2] += z;
+            a[3] = fmin(a[3], x); a[4] = fmin(a[4], y); a[5] = fmin(a[5], z);
+            a[6] = fmax(a[6], x); a[7] = fmax(a[7], y); a[8] = fmax(a[8], z);
+        } else {
+            const double c[3] = {x - mu[0], y - mu[1], z - mu[2]};
+            a[0] += c[0] * c[0]; a[1] += c[0] * c[1]; a[2] += c[0] * c[2];
+            a[3] += c[1] * c[1]; a[4] += c[1] * c[2]; a[5] += c[2] * c[2];
+        }
+    }
+    const int nv = mode == 0 ? 9 : 6;
+    for (int k = 0; k < nv; ++k) {
+        double v = a[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double u = __shfl_xor_sync(0xffffffffu, v, o);
+            v = (mode == 0 && k >= 3) ? (k < 6 ? fmin(v, u) : fmax(v, u)) : v + u;
+        }
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        const int k = threadIdx.x;
+        double v = sh[0][k];
+        for (int w = 1; w < kT / 32; ++w)
+            v = (mode == 0 && k >= 3) ? (k < 6 ? fmin(v, sh[w][k]) : fmax(v, sh[w][k])) : v + sh[w][k];
+        part[blockIdx.x * 12 + k] = v;
+    }
+}
+
+// cyclic Jacobi for a symmetric 3x3 matrix (Golub and Van Loan, Sec. 8.5):
+// eigenvalues in ev, eigenvectors as the columns of Q
+__device__ void jacobi3(const double Ain[9], double ev[3], double Q[9]) {
+    double A[9];
+    for (int i = 0; i < 9; ++i) { A[i] = Ain[i]; Q[i] = (i % 4 == 0) ? 1.0 : 0.0; }
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        if (A[1] * A[1] + A[2] * A[2] + A[5] * A[5] == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                const double apq = A[3 * p + q];
+                if (apq == 0.0) continue;
+                const double theta = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {
+                    const double akp = A[3 * k + p], akq = A[3 * k + q];
+                    A[3 * k + p] = c * akp - s * akq;
+                    A[3 * k + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double apk = A[3 * p + k], aqk = A[3 * q + k];
+                    A[3 * p + k] = c * apk - s * aqk;
+                    A[3 * q + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double qkp = Q[3 * k + p], qkq = Q[3 * k + q];
+                    Q[3 * k + p] = c * qkp - s * qkq;
+                    Q[3 * k + q] = s * qkp + c * qkq;
+                }
+            }
+    }
+    ev[0] = A[0]; ev[1] = A[4]; ev[2] = A[8];
+}
+
+// single thread: the CTA partials added in order; mode 0 leaves the mean
+// (sc[0..2]) and the bounding box (sc[3..8]); mode 1 the covariance, its
+// eigen-decomposition and the axis (sc[9..11])
+__global__ void finish_moments_kernel(const double* __restrict__ part, int nb, int64_t P, int mode, double* sc) {
+    if (mode == 0) {
+        double a[9] = {0, 0, 0, INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int b = 0; b < nb; ++b)
+            for (int k = 0; k < 9; ++k)
+                a[k] = k < 3 ? a[k] + part[12 * b + k] : (k < 6 ? fmin(a[k], part[12 * b + k]) : fmax(a[k], part[12 * b + k]));
+        for (int k = 0; k < 3; ++k) sc[k] = a[k] / (double)P;
+        for (int k = 3; k < 9; ++k) sc[k] = a[k];
+        return;
+    }
+    double s6[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < 6; ++k) s6[k] += part[12 * b + k];
+    double C[9] = {s6[0], s6[1], s6[2], s6[1], s6[3], s6[4], s6[2], s6[4], s6[5]};
+    for (int k = 0; k < 9; ++k) C[k] /= (double)P;
+    double ev[3], Q[9];
+    jacobi3(C, ev, Q);
+    int top = 0;
+    for (int i = 1; i < 3; ++i) if (ev[i] > ev[top]) top = i;
+    double ax[3] = {Q[top], Q[3 + top], Q[6 + top]};
+    int big = 0;
+    for (int i = 1; i < 3; ++i) if (fabs(ax[i]) > fabs(ax[big])) big = i;
+    if (ax[big] < 0) for (int i = 0; i < 3; ++i) ax[i] = -ax[i];
+    for (int i = 0; i < 3; ++i) sc[9 + i] = ax[i];
+}
+
+// projections on the axis as sort keys; grid cell keys of the points
+__global__ void keys_kernel(const double* __restrict__ V, int64_t P, const double* __restrict__ sc, double h,
+                            long long d1, long long d2, unsigned long long* __restrict__ pkey,
+                            unsigned long long* __restrict__ ckey, int* __restrict__ idx) {
+    const double a0 = sc[9], a1 = sc[10], a2 = sc[11];
+    const double lo[3] = {sc[3], sc[4], sc[5]};
+    const long long dims[3] = {0, d1, d2};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = V[3 * i], y = V[3 * i + 1], z = V[3 * i + 2];
+        pkey[i] = dkey(__dadd_rn(__dadd_rn(__dmul_rn(x, a0), __dmul_rn(y, a1)), __dmul_rn(z, a2)));
+        long long c[3];
+        const double p[3] = {x, y, z};
+        for (int d = 0; d < 3; ++d) {
+            long long v = (long long)floor((p[d] - lo[d]) / h);
+            const long long dm = d == 0 ? (long long)sc[12] : dims[d];
+            c[d] = v < 0 ? 0 : (v > dm - 1 ? dm - 1 : v);
+        }
+        ckey[i] = (unsigned long long)((c[0] * d1 + c[1]) * d2 + c[2]);
+        idx[i] = (int)i;
+    }
+}
+
+// rank of each point in the visiting order
+__global__ void rank_kernel(int64_t P, const int* __restrict__ order, int* __restrict__ rank) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P; r += (int64_t)gridDim.x * blockDim.x)
+        rank[order[r]] = (int)r;
+}
+
+// the grid's point data in cell order: coordinates and rank
+__global__ void grid_data_kernel(int64_t P, const int* __restrict__ gitem, const double* __restrict__ V,
+                                 const int* __restrict__ rank, double* __restrict__ gxyz, int* __restrict__ grank) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < P; s += (int64_t)gridDim.x * blockDim.x) {
+        const int i = gitem[s];
+        gxyz[3 * s] = V[3 * (int64_t)i];
+        gxyz[3 * s + 1] = V[3 * (int64_t)i + 1];
+        gxyz[3 * s + 2] = V[3 * (int64_t)i + 2];
+        grank[s] = rank[i];
+    }
+}
+
+// [first, last) of the sorted keys equal to k
+__device__ __forceinline__ void cell_range(const unsigned long long* keys, int n, unsigned long long k, int* s0,
+                                           int* s1) {
+    int lo = 0, hi = n;
+    while (lo < hi) { const int m = (lo + hi) >> 1; if (keys[m] < k) lo = m + 1; else hi = m; }
+    *s0 = lo;
+    hi = n;
+    while (lo < hi) { const int m = (lo + hi) >> 1; if (keys[m] <= k) lo = m + 1; else hi = m; }
+    *s1 = lo;
+}
+
+struct GridView {
+    const unsigned long long* keys;   // sorted cell keys [n]
+    const double* xyz;                // coordinates in that order [n][3]
+    int n;
+    double lo[3];
+    double h;
+    long long dims[3];
+    __device__ void cell(double x, double y, double z, long long c[3]) const {
+        const double p[3] = {x, y, z};
+        for (int d = 0; d < 3; ++d) {
+            long long v = (long long)floor((p[d] - lo[d]) / h);
+            c[d] = v < 0 ? 0 : (v > dims[d] - 1 ? dims[d] - 1 : v);
+        }
+    }
+};
+
+// One round of the greedy sampling over the ranks [win[0], win[1]):
+// state 0 undecided, 1 node, 2 covered
+__global__ void __launch_bounds__(kT) greedy_round_kernel(GridView g, const int* __restrict__ grank,
+                                                          const int* __restrict__ gitem, const int* __restrict__ order,
+                                                          const double* __restrict__ V, double R2,
+                                                          unsigned char* state, const int* __restrict__ win) {
+    const int r0 = win[0], r1 = win[1];
+    for (int r = r0 + blockIdx.x * blockDim.x + threadIdx.x; r < r1; r += gridDim.x * blockDim.x) {
+        const int v = order[r];
+        if (((volatile unsigned char*)state)[v] != 0) continue;
+        const double x = V[3 * (int64_t)v], y = V[3 * (int64_t)v + 1], z = V[3 * (int64_t)v + 2];
+        long long c[3];
+        g.cell(x, y, z, c);
+        bool covered = false, pending = false;
+        for (long long cx = c[0] - 1; cx <= c[0] + 1 && !covered; ++cx)
+            for (long long cy = c[1] - 1; cy <= c[1] + 1 && !covered; ++cy)
+                for (long long cz = c[2] - 1; cz <= c[2] + 1 && !covered; ++cz) {
+                    if (cx < 0 || cy < 0 || cz < 0 || cx >= g.dims[0] || cy >= g.dims[1] || cz >= g.dims[2]) continue;
+                    int s0, s1;
+                    cell_range(g.keys, g.n, (unsigned long long)((cx * g.dims[1] + cy) * g.dims[2] + cz), &s0, &s1);
+                    for (int s = s0; s < s1; ++s) {
+                        if (grank[s] >= r) continue;   // only earlier points
+                        if (sqd(x, y, z, g.xyz[3 * s], g.xyz[3 * s + 1], g.xyz[3 * s + 2]) < R2) {
+                            const unsigned char su = ((volatile unsigned char*)state)[gitem[s]];
+                            if (su == 1) { covered = true; break; }
+                            if (su == 0) pending = true;
+                        }
+                    }
+                }
+        if (covered) state[v] = 2;
+        else if (!pending) state[v] = 1;
+    }
+}
+
+// next window: the lowest undecided rank f (from the current one, scanning
+// forward) and the end of the ranks whose projection is within W of f's
+__global__ void __launch_bounds__(1024) window_kernel(int P, const int* __restrict__ order,
+                                                     const unsigned char* state,
+                                                     const unsigned long long* __restrict__ skey,
+                                                     const double* __restrict__ sproj, double W, int* win) {
+    __shared__ int s_f;
+    int f = win[0];
+    while (f < P) {
+        const int r = f + (int)threadIdx.x;
+        const bool und = r < P && ((volatile const unsigned char*)state)[order[r]] == 0;
+        const int any = __syncthreads_or(und);
+        if (threadIdx.x == 0) s_f = P;
+        __syncthreads();
+        if (und) atomicMin(&s_f, r);
+        __syncthreads();
+        if (any) { f = s_f; break; }
+        f += 1024;
+    }
+    if (f > P) f = P;
+    if (threadIdx.x == 0) {
+        int hi = f;
+        if (f < P) {
+            const double lim = sproj[f] + W;
+            int lo = f, up = P;
+            while (lo < up) { const int m = (lo + up) >> 1; if (sproj[m] <= lim) lo = m + 1; else up = m; }
+            hi = lo;
+        }
+        win[0] = f;
+        win[1] = hi;
+        (void)skey;
+    }
+}
+
+// projections in visiting order (for the window), recomputed as in keys_kernel
+__global__ void sorted_proj_kernel(int64_t P, const int* __restrict__ order, const double* __restrict__ V,
+                                   const double* __restrict__ sc, double* __restrict__ sproj) {
+    const double a0 = sc[9], a1 = sc[10], a2 = sc[11];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = order[r];
+        sproj[r] = __dadd_rn(__dadd_rn(__dmul_rn(V[3 * i], a0), __dmul_rn(V[3 * i + 1], a1)), __dmul_rn(V[3 * i + 2], a2));
+    }
+}
+
+__global__ void node_flags_kernel(int64_t P, const int* __restrict__ order, const unsigned char* __restrict__ state,
+                                  int* __restrict__ flag) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P; r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = state[order[r]] == 1 ? 1 : 0;
+}
+
+__global__ void nodes_kernel(int64_t P, const int* __restrict__ order, const int* __restrict__ flag,
+                             const int* __restrict__ nid, const double* __restrict__ V, const double* __restrict__ sc,
+                             double h, long long d1, long long d2, int* __restrict__ nodes, double* __restrict__ pn,
+                             unsigned long long* __restrict__ nkey, int* __restrict__ nval) {
+    const double lo[3] = {sc[3], sc[4], sc[5]};
+    const long long dims[3] = {(long long)sc[12], d1, d2};
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P; r += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[r]) continue;
+        const int j = nid[r], i = order[r];
+        nodes[j] = i;
+        long long c[3];
+        for (int d = 0; d < 3; ++d) {
+            const double x = V[3 * (int64_t)i + d];
+            pn[3 * j + d] = x;
+            long long v = (long long)floor((x - lo[d]) / h);
+            c[d] = v < 0 ? 0 : (v > dims[d] - 1 ? dims[d] - 1 : v);
+        }
+        nkey[j] = (unsigned long long)((c[0] * d1 + c[1]) * d2 + c[2]);
+        nval[j] = j;
+    }
+}
+
+__global__ void node_grid_xyz_kernel(int N, const int* __restrict__ nsorted, const double* __restrict__ pn,
+                                     double* __restrict__ nxyz) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x)
+        for (int d = 0; d < 3; ++d) nxyz[3 * s + d] = pn[3 * nsorted[s] + d];
+}
+
+// influence sets: the K nearest nodes within R by (d^2, node id), weights of
+// Eq. (weight_data) (1 - d^2/R^2)^3 normalised over the set, and the number
+// of node pairs of each set (edges)
+__global__ void __launch_bounds__(kT) influence_kernel(GridView g, const int* __restrict__ nsorted,
+                                                       const double* __restrict__ V, int64_t P, double R2, int K,
+                                                       int* __restrict__ nidx, double* __restrict__ w,
+                                                       int* __restrict__ npairs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = V[3 * i], y = V[3 * i + 1], z = V[3 * i + 2];
+        double bd[NRR_MAX_INFL];
+        int bj[NRR_MAX_INFL];
+        int n = 0;
+        long long c[3];
+        g.cell(x, y, z, c);
+        for (long long cx = c[0] - 1; cx <= c[0] + 1; ++cx)
+            for (long long cy = c[1] - 1; cy <= c[1] + 1; ++cy)
+                for (long long cz = c[2] - 1; cz <= c[2] + 1; ++cz) {
+                    if (cx < 0 || cy < 0 || cz < 0 || cx >= g.dims[0] || cy >= g.dims[1] || cz >= g.dims[2]) continue;
+                    int s0, s1;
+                    cell_range(g.keys, g.n, (unsigned long long)((cx * g.dims[1] + cy) * g.dims[2] + cz), &s0, &s1);
+                    for (int s = s0; s < s1; ++s) {
+                        const double d2 = sqd(x, y, z, g.xyz[3 * s], g.xyz[3 * s + 1], g.xyz[3 * s + 2]);
+                        if (!(d2 < R2)) continue;
+                        const int j = nsorted[s];
+                        // sorted insertion by (d^2, node id), keeping the K smallest
+                        if (n == K && !(d2 < bd[K - 1] || (d2 == bd[K - 1] && j < bj[K - 1]))) continue;
+                        int pos = n < K ? n : K - 1;
+                        while (pos > 0 && (bd[pos - 1] > d2 || (bd[pos - 1] == d2 && bj[pos - 1] > j))) {
+                            bd[pos] = bd[pos - 1];
+                            bj[pos] = bj[pos - 1];
+                            --pos;
+                        }
+                        bd[pos] = d2;
+                        bj[pos] = j;
+                        if (n < K) ++n;
+                    }
+                }
+        double raw[NRR_MAX_INFL];
+        double sum = 0.0;
+        for (int s = 0; s < n; ++s) {
+            const double a = 1.0 - bd[s] / R2;
+            raw[s] = pow(a, 3.0);
+        }
+        for (int s = 0; s < n; ++s) sum += raw[s];
+        for (int s = 0; s < K; ++s) {
+            nidx[i * K + s] = s < n ? bj[s] : -1;
+            w[i * K + s] = s < n ? raw[s] / sum : 0.0;
+        }
+        npairs[i] = n * (n - 1) / 2;
+    }
+}
+
+__global__ void pair_keys_kernel(int64_t P, int K, const int* __restrict__ nidx, const int* __restrict__ off,
+                                 unsigned long long* __restrict__ keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        int o = off[i];
+        for (int a = 0; a < K; ++a) {
+            const int u = nidx[i * K + a];
+            if (u < 0) break;
+            for (int b = a + 1; b < K; ++b) {
+                const int v = nidx[i * K + b];
+                if (v < 0) break;
+                const unsigned long long lo = (unsigned long long)min(u, v), hi = (unsigned long long)max(u, v);
+                keys[o++] = (lo << 32) | hi;
+            }
+        }
+    }
+}
+
+__global__ void unique_flags_kernel(int64_t n, const unsigned long long* __restrict__ keys, int* __restrict__ flag) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        flag[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1 : 0;
+}
+
+// unique edges (j < k) and both directed pairs of each
+__global__ void edges_kernel(int64_t n, const unsigned long long* __restrict__ keys, const int* __restrict__ flag,
+                             const int* __restrict__ pos, int* __restrict__ edges,
+                             unsigned long long* __restrict__ dkeys) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[k]) continue;
+        const int e = pos[k];
+        const unsigned long long a = keys[k] >> 32, b = keys[k] & 0xffffffffull;
+        edges[2 * e] = (int)a;
+        edges[2 * e + 1] = (int)b;
+        dkeys[2 * e] = (a << 32) | b;
+        dkeys[2 * e + 1] = (b << 32) | a;
+    }
+}
+
+// 1 / |p_i - p_j| of every directed pair and its per-CTA partial sums
+__global__ void __launch_bounds__(kT) inv_len_kernel(int E2, const unsigned long long* __restrict__ dkeys,
+                                                     const double* __restrict__ pn, double* __restrict__ inv,
+                                                     double* __restrict__ part) {
+    __shared__ double sh[kT / 32];
+    const int per = (E2 + gridDim.x - 1) / gridDim.x;
+    const int e0 = blockIdx.x * per, e1 = min(E2, e0 + per);
+    double s = 0.0;
+    for (int e = e0 + threadIdx.x; e < e1; e += kT) {
+        const int a = (int)(dkeys[e] >> 32), b = (int)(dkeys[e] & 0xffffffffull);
+        const double v = 1.0 / sqrt(sqd(pn[3 * a], pn[3 * a + 1], pn[3 * a + 2], pn[3 * b], pn[3 * b + 1], pn[3 * b + 2]));
+        inv[e] = v;
+        s += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kT / 32; ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void r_kernel(int E2, int nb, const double* __restrict__ part, double n_edges, double* __restrict__ r,
+                         int* __restrict__ dpair, const unsigned long long* __restrict__ dkeys,
+                         const double* __restrict__ inv) {
+    __shared__ double s_sum;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += part[b];
+        s_sum = t;
+    }
+    __syncthreads();
+    const double sum = s_sum;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E2; e += gridDim.x * blockDim.x) {
+        r[e] = 2.0 * n_edges * inv[e] / sum;
+        dpair[2 * e] = (int)(dkeys[e] >> 32);
+        dpair[2 * e + 1] = (int)(dkeys[e] & 0xffffffffull);
+    }
+}
+
+// device buffers of one build, freed on every exit path
+struct Scratch {
+    std::vector<void*> p;
+    ~Scratch() {
+        for (void* q : p) cudaFree(q);
+    }
+    template <typename X>
+    cudaError_t get(X** out, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(X));
+        if (e == cudaSuccess) p.push_back(q);
+        *out = (X*)q;
+        return e;
+    }
+};
+
+template <typename K, typename V>
+cudaError_t sort_pairs(Scratch& s, const K* kin, K* kout, const V* vin, V* vout, int n, int end_bit, cudaStream_t st) {
+    size_t tb = 0;
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(nullptr, tb, kin, kout, vin, vout, n, 0, end_bit, st);
+    if (e != cudaSuccess) return e;
+    void* tmp = nullptr;
+    if ((e = s.get((unsigned char**)&tmp, tb)) != cudaSuccess) return e;
+    return cub::DeviceRadixSort::SortPairs(tmp, tb, kin, kout, vin, vout, n, 0, end_bit, st);
+}
+
+template <typename K>
+cudaError_t sort_keys(Scratch& s, const K* kin, K* kout, int n, cudaStream_t st) {
+    size_t tb = 0;
+    cudaError_t e = cub::DeviceRadixSort::SortKeys(nullptr, tb, kin, kout, n, 0, 64, st);
+    if (e != cudaSuccess) return e;
+    void* tmp = nullptr;
+    if ((e = s.get((unsigned char**)&tmp, tb)) != cudaSuccess) return e;
+    return cub::DeviceRadixSort::SortKeys(tmp, tb, kin, kout, n, 0, 64, st);
+}
+
+cudaError_t exclusive_sum(Scratch& s, const int* in, int* out, int n, cudaStream_t st) {
+    size_t tb = 0;
+    cudaError_t e = cub::DeviceScan::ExclusiveSum(nullptr, tb, in, out, n, st);
+    if (e != cudaSuccess) return e;
+    void* tmp = nullptr;
+    if ((e = s.get((unsigned char**)&tmp, tb)) != cudaSuccess) return e;
+    return cub::DeviceScan::ExclusiveSum(tmp, tb, in, out, n, st);
+}
+
+int blocks_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + kT - 1) / kT, 4096)); }
+
+}  // namespace
+
+// Algorithm 1 on the GPU (see the file comment). src: [P][3] float32, host or
+// device. Fills g as nrr_build_graph does. Returns cudaSuccess or the first
+// CUDA error; *rounds receives the number of greedy rounds.
+cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, HostGraph& g, cudaStream_t st,
+                                int* rounds) {
+#define GK(call)                                \
+    do {                                        \
+        cudaError_t e_ = (call);                \
+        if (e_ != cudaSuccess) return e_;       \
+    } while (0)
+    Scratch s;
+    const int n = (int)P;
+    const double R2 = R * R;
+    g.radius = R;
+    g.K = K;
+    float* fsrc = nullptr;
+    double *V = nullptr, *part = nullptr, *sc = nullptr;
+    GK(s.get(&fsrc, (size_t)P * 3));
+    GK(cudaMemcpyAsync(fsrc, src, sizeof(float) * 3 * (size_t)P, cudaMemcpyDefault, st));
+    GK(s.get(&V, (size_t)P * 3));
+    GK(s.get(&part, (size_t)kRed * 12));
+    GK(s.get(&sc, 16));
+    to_double_kernel<<<blocks_for(3 * P), kT, 0, st>>>(fsrc, V, 3 * P);
+    // ---- 1. PCA (mean and bounding box, then the covariance and its axis)
+    moments_kernel<<<kRed, kT, 0, st>>>(V, P, 0, sc, part);
+    finish_moments_kernel<<<1, 1, 0, st>>>(part, kRed, P, 0, sc);
+    moments_kernel<<<kRed, kT, 0, st>>>(V, P, 1, sc, part);
+    finish_moments_kernel<<<1, 1, 0, st>>>(part, kRed, P, 1, sc);
+    GK(cudaGetLastError());
+    double hsc[16];
+    GK(cudaMemcpyAsync(hsc, sc, sizeof(double) * 12, cudaMemcpyDeviceToHost, st));
+    GK(cudaStreamSynchronize(st));
+    // grid of cell size R over the bounding box (the host code's grid)
+    const double h = R > 0 ? R : 1.0;
+    long long dims[3];
+    for (int d = 0; d < 3; ++d) dims[d] = std::max<long long>(1, (long long)std::floor((hsc[6 + d] - hsc[3 + d]) / h) + 1);
+    hsc[12] = (double)dims[0];
+    GK(cudaMemcpyAsync(sc + 12, hsc + 12, sizeof(double), cudaMemcpyHostToDevice, st));
+    // ---- 2. the visiting order and the grid
+    unsigned long long *pkey, *pkey_s, *ckey, *ckey_s;
+    int *idx, *order, *gitem, *rank, *grank;
+    double *gxyz, *sproj;
+    GK(s.get(&pkey, P)); GK(s.get(&pkey_s, P)); GK(s.get(&ckey, P)); GK(s.get(&ckey_s, P));
+    GK(s.get(&idx, P)); GK(s.get(&order, P)); GK(s.get(&gitem, P)); GK(s.get(&rank, P)); GK(s.get(&grank, P));
+    GK(s.get(&gxyz, (size_t)P * 3)); GK(s.get(&sproj, P));
+    keys_kernel<<<blocks_for(P), kT, 0, st>>>(V, P, sc, h, dims[1], dims[2], pkey, ckey, idx);
+    GK(cudaGetLastError());
+    GK(sort_pairs(s, pkey, pkey_s, idx, order, n, 64, st));
+    GK(sort_pairs(s, ckey, ckey_s, idx, gitem, n, 64, st));
+    rank_kernel<<<blocks_for(P), kT, 0, st>>>(P, order, rank);
+    grid_data_kernel<<<blocks_for(P), kT, 0, st>>>(P, gitem, V, rank, gxyz, grank);
+    sorted_proj_kernel<<<blocks_for(P), kT, 0, st>>>(P, order, V, sc, sproj);
+    GK(cudaGetLastError());
+    // ---- 3. greedy sampling in rounds over a window that follows the sweep
+    unsigned char* state;
+    int* win;
+    GK(s.get(&state, P));
+    GK(s.get(&win, 2));
+    GK(cudaMemsetAsync(state, 0, (size_t)P, st));
+    GK(cudaMemsetAsync(win, 0, 2 * sizeof(int), st));
+    GridView gv{ckey_s, gxyz, n, {hsc[3], hsc[4], hsc[5]}, h, {dims[0], dims[1], dims[2]}};
+    const double W = 2.0 * R;
+    window_kernel<<<1, 1024, 0, st>>>(n, order, state, pkey_s, sproj, W, win);
+    int hwin[2] = {0, 0};
+    int nr = 0;
+    const int batch = 16;
+    while (true) {
+        for (int k = 0; k < batch; ++k) {
+            greedy_round_kernel<<<304, kT, 0, st>>>(gv, grank, gitem, order, V, R2, state, win);
+            window_kernel<<<1, 1024, 0, st>>>(n, order, state, pkey_s, sproj, W, win);
+        }
+        nr += batch;
+        GK(cudaGetLastError());
+        GK(cudaMemcpyAsync(hwin, win, sizeof hwin, cudaMemcpyDeviceToHost, st));
+        GK(cudaStreamSynchronize(st));
+        if (hwin[0] >= n) break;
+        if (nr > 4 * n + 64) return cudaErrorUnknown;   // cannot happen: every round decides its lowest rank
+    }
+    if (rounds) *rounds = nr;
+    // ---- node ids (visiting order), positions and the node grid
+    int *flag, *nid;
+    GK(s.get(&flag, P)); GK(s.get(&nid, P));
+    node_flags_kernel<<<blocks_for(P), kT, 0, st>>>(P, order, state, flag);
+    GK(exclusive_sum(s, flag, nid, n, st));
+    int last[2];
+    GK(cudaMemcpyAsync(&last[0], nid + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GK(cudaMemcpyAsync(&last[1], flag + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GK(cudaStreamSynchronize(st));
+    const int N = last[0] + last[1];
+    int *nodes, *nval, *nsorted;
+    double *pn, *nxyz;
+    unsigned long long *nkey, *nkey_s;
+    GK(s.get(&nodes, N)); GK(s.get(&nval, N)); GK(s.get(&nsorted, N));
+    GK(s.get(&pn, (size_t)N * 3)); GK(s.get(&nxyz, (size_t)N * 3));
+    GK(s.get(&nkey, N)); GK(s.get(&nkey_s, N));
+    nodes_kernel<<<blocks_for(P), kT, 0, st>>>(P, order, flag, nid, V, sc, h, dims[1], dims[2], nodes, pn, nkey, nval);
+    GK(cudaGetLastError());
+    GK(sort_pairs(s, nkey, nkey_s, nval, nsorted, N, 64, st));
+    node_grid_xyz_kernel<<<blocks_for(N), kT, 0, st>>>(N, nsorted, pn, nxyz);
+    // ---- 4. influence sets, weights, edges, r_ij
+    int *nidx, *npairs, *poff;
+    double* w;
+    GK(s.get(&nidx, (size_t)P * K)); GK(s.get(&w, (size_t)P * K));
+    GK(s.get(&npairs, P)); GK(s.get(&poff, P));
+    GridView nv{nkey_s, nxyz, N, {hsc[3], hsc[4], hsc[5]}, h, {dims[0], dims[1], dims[2]}};
+    influence_kernel<<<blocks_for(P), kT, 0, st>>>(nv, nsorted, V, P, R2, K, nidx, w, npairs);
+    GK(cudaGetLastError());
+    GK(exclusive_sum(s, npairs, poff, n, st));
+    GK(cudaMemcpyAsync(&last[0], poff + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GK(cudaMemcpyAsync(&last[1], npairs + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GK(cudaStreamSynchronize(st));
+    const int n_pk = last[0] + last[1];
+    unsigned long long *pk, *pk_s;
+    int *uflag, *upos;
+    GK(s.get(&pk, n_pk)); GK(s.get(&pk_s, n_pk)); GK(s.get(&uflag, n_pk)); GK(s.get(&upos, n_pk));
+    pair_keys_kernel<<<blocks_for(P), kT, 0, st>>>(P, K, nidx, poff, pk);
+    GK(cudaGetLastError());
+    int n_edges = 0;
+    if (n_pk > 0) {
+        GK(sort_keys(s, pk, pk_s, n_pk, st));
+        unique_flags_kernel<<<blocks_for(n_pk), kT, 0, st>>>(n_pk, pk_s, uflag);
+        GK(exclusive_sum(s, uflag, upos, n_pk, st));
+        GK(cudaMemcpyAsync(&last[0], upos + n_pk - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GK(cudaMemcpyAsync(&last[1], uflag + n_pk - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GK(cudaStreamSynchronize(st));
+        n_edges = last[0] + last[1];
+    }
+    const int E2 = 2 * n_edges;
+    int *edges, *dpair;
+    unsigned long long *dk, *dk_s;
+    double *inv, *rr, *rpart;
+    GK(s.get(&edges, 2 * (size_t)n_edges)); GK(s.get(&dpair, 2 * (size_t)E2));
+    GK(s.get(&dk, E2)); GK(s.get(&dk_s, E2)); GK(s.get(&inv, E2)); GK(s.get(&rr, E2)); GK(s.get(&rpart, kRed));
+    if (n_edges > 0) {
+        edges_kernel<<<blocks_for(n_pk), kT, 0, st>>>(n_pk, pk_s, uflag, upos, edges, dk);
+        GK(cudaGetLastError());
+        GK(sort_keys(s, dk, dk_s, E2, st));
+        inv_len_kernel<<<kRed, kT, 0, st>>>(E2, dk_s, pn, inv, rpart);
+        r_kernel<<<blocks_for(E2), kT, 0, st>>>(E2, kRed, rpart, (double)n_edges, rr, dpair, dk_s, inv);
+        GK(cudaGetLastError());
+    }
+    // ---- back to the host graph
+    g.nodes.resize((size_t)N);
+    g.nidx.resize((size_t)P * K);
+    g.w.resize((size_t)P * K);
+    g.edges.resize(2 * (size_t)n_edges);
+    g.dpair.resize(2 * (size_t)E2);
+    g.r.resize((size_t)E2);
+    GK(cudaMemcpyAsync(g.nodes.data(), nodes, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, st));
+    GK(cudaMemcpyAsync(g.nidx.data(), nidx, sizeof(int) * (size_t)P * K, cudaMemcpyDeviceToHost, st));
+    GK(cudaMemcpyAsync(g.w.data(), w, sizeof(double) * (size_t)P * K, cudaMemcpyDeviceToHost, st));
+    if (n_edges > 0) {
+        GK(cudaMemcpyAsync(g.edges.data(), edges, sizeof(int) * 2 * (size_t)n_edges, cudaMemcpyDeviceToHost, st));
+        GK(cudaMemcpyAsync(g.dpair.data(), dpair, sizeof(int) * 2 * (size_t)E2, cudaMemcpyDeviceToHost, st));
+        GK(cudaMemcpyAsync(g.r.data(), rr, sizeof(double) * (size_t)E2, cudaMemcpyDeviceToHost, st));
+    }
+    GK(cudaStreamSynchronize(st));
+    return cudaSuccess;
+#undef GK
+}

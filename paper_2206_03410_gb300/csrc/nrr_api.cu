@@ -482,6 +482,31 @@ uint64_t problem_hash(const std::vector<float>& src, const std::vector<float>& t
     return ph.h;
 }
 
+// Algorithm 1 on the GPU (graph_gpu.cu) with l-bar on a host thread beside
+// it when the parameters need it (or first, when the radius defaults to
+// 5 l-bar). src: the float source points (host or device).
+nrr_status graph_on_device(const float* src, const std::vector<double>& V, int64_t P, double radius, int K,
+                           bool need_lbar, cudaStream_t st, HostGraph& g) {
+    double lbar = std::nan("");
+    double R = radius;
+    std::thread t;
+    if (R <= 0) {
+        lbar = nrr_mean_spacing(V.data(), P, 6);
+        R = 5.0 * lbar;
+        if (!(R > 0)) return nrr_set_global_error(NRR_E_INVALID, "graph radius 5 l-bar is not positive");
+    } else if (need_lbar) {
+        t = std::thread([&]() { lbar = nrr_mean_spacing(V.data(), P, 6); });
+    }
+    int rounds = 0;
+    const cudaError_t e = nrr_build_graph_gpu(src, P, R, K, g, st, &rounds);
+    if (t.joinable()) t.join();
+    if (e != cudaSuccess)
+        return nrr_set_global_error(e == cudaErrorMemoryAllocation ? NRR_E_OOM : NRR_E_CUDA,
+                                    (std::string("deformation graph on the GPU: ") + cudaGetErrorString(e)).c_str());
+    g.lbar = lbar;
+    return NRR_OK;
+}
+
 // Hilbert orders of source and target over their common bounding box; they
 // depend on the inputs only, so nrr_create computes them on a second host
 // thread while it builds the deformation graph.
@@ -1396,6 +1421,7 @@ void nrr_params_default(nrr_params* p) {
     p->solve_ctas = 0;
     p->robust = NRR_WELSCH;
     p->nu_schedule = NRR_NU_ANNEAL;
+    p->graph_on_gpu = 0;
 }
 
 const char* nrr_last_error(const nrr_ctx* ctx) {
@@ -1447,6 +1473,8 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         return fail(nullptr, NRR_E_INVALID, "solve_ctas must be in -1..16");
     if (prm.robust < NRR_WELSCH || prm.robust > NRR_L2_TRUNCATED)
         return fail(nullptr, NRR_E_INVALID, "robust must be NRR_WELSCH, NRR_L2 or NRR_L2_TRUNCATED");
+    if (prm.graph_on_gpu != 0 && prm.graph_on_gpu != 1)
+        return fail(nullptr, NRR_E_INVALID, "graph_on_gpu must be 0 or 1");
     if (prm.nu_schedule < NRR_NU_ANNEAL || prm.nu_schedule > NRR_NU_FIXED_MED)
         return fail(nullptr, NRR_E_INVALID, "nu_schedule must be one of nrr_nu_schedule");
     if (!(std::isfinite(prm.graph_radius) && std::isfinite(prm.nu_a) && std::isfinite(prm.nu_r) &&
@@ -1496,8 +1524,13 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     // l-bar, radius and the deformation graph (Algorithm 1)
     std::vector<double> V(src.begin(), src.end());
     const bool need_lbar = prm.graph_radius <= 0 || prm.nu_r <= 0 || prm.nu_a_min <= 0;
-    if (!nrr_graph_and_spacing(V.data(), P, prm.graph_radius, prm.max_influence, need_lbar, c->hg))
+    if (prm.graph_on_gpu) {
+        const nrr_status gs = graph_on_device(src.data(), V, P, prm.graph_radius, prm.max_influence, need_lbar,
+                                              c->stream, c->hg);
+        if (gs != NRR_OK) return gs;
+    } else if (!nrr_graph_and_spacing(V.data(), P, prm.graph_radius, prm.max_influence, need_lbar, c->hg)) {
         return fail(nullptr, NRR_E_INVALID, "graph radius must be positive");
+    }
     tm.lap("l-bar + graph (Algorithm 1)");
     c->N = (int)c->hg.nodes.size();
     c->E2 = (int)c->hg.r.size();
@@ -1828,6 +1861,31 @@ nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, dou
         return NRR_OK;
     } catch (const std::bad_alloc&) {
         return nrr_set_global_error(NRR_E_OOM, "nrr_graph_build: out of host memory");
+    }
+}
+
+nrr_status nrr_graph_build_gpu(nrr_graph** out, const float* src_xyz, int64_t P, double radius, int max_influence,
+                               void* cuda_stream) {
+    if (!out || !src_xyz) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_gpu: NULL argument");
+    *out = nullptr;
+    if (P < 1 || P >= (1LL << 25)) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_gpu: P must be in 1..2^25-1");
+    if (!std::isfinite(radius)) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_gpu: radius not finite");
+    const int K = max_influence <= 0 ? 8 : max_influence;
+    if (K > 8) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_gpu: max_influence > 8");
+    try {
+        std::vector<float> src;
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        if (fetch_floats(src_xyz, (size_t)P * 3, src, st) != cudaSuccess)
+            return nrr_set_global_error(NRR_E_CUDA, "nrr_graph_build_gpu: reading the points failed");
+        if (!finite3(src)) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_gpu: non-finite point");
+        std::vector<double> V(src.begin(), src.end());
+        std::unique_ptr<nrr_graph> g(new nrr_graph);
+        const nrr_status gs = graph_on_device(src.data(), V, P, radius, K, true, st, g->g);
+        if (gs != NRR_OK) return gs;
+        *out = g.release();
+        return NRR_OK;
+    } catch (const std::bad_alloc&) {
+        return nrr_set_global_error(NRR_E_OOM, "nrr_graph_build_gpu: out of host memory");
     }
 }
 

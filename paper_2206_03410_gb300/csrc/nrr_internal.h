@@ -78,6 +78,11 @@ void nrr_curve_order(const float* pts, int64_t n, const double lo[3],
                       const double hi[3], std::vector<int>& order,
                       std::vector<uint64_t>* codes_sorted);
 
+// graph_gpu.cu: Algorithm 1 on the GPU (the same graph as nrr_build_graph);
+// src [P][3] float32 host or device; *rounds = greedy rounds run.
+cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, HostGraph& g, cudaStream_t st,
+                                int* rounds);
+
 // Records msg as the global last error (nrr_last_error(NULL)); returns code.
 nrr_status nrr_set_global_error(nrr_status code, const char* msg);
 

@@ -57,6 +57,7 @@ class NrrParams(ctypes.Structure):
         ("solve_ctas", ctypes.c_int),
         ("robust", ctypes.c_int),
         ("nu_schedule", ctypes.c_int),
+        ("graph_on_gpu", ctypes.c_int),
     ]
 
 
@@ -142,6 +143,7 @@ _SIGS = [
     ("nrr_get_sizes", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     ("nrr_get_graph", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("nrr_graph_build", ctypes.c_int, [ctypes.POINTER(_VP), _VP, _I64, ctypes.c_double, ctypes.c_int]),
+    ("nrr_graph_build_gpu", ctypes.c_int, [ctypes.POINTER(_VP), _VP, _I64, ctypes.c_double, ctypes.c_int, _VP]),
     ("nrr_graph_sizes", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     ("nrr_graph_get", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("nrr_graph_destroy", None, [_VP]),
@@ -480,22 +482,32 @@ def nrr_get_graph(ctx) -> GraphView:
     return GraphView(nodes, nidx, w, edges, r, lbar.value)
 
 
-def build_graph(src, radius: float = 0.0, max_influence: int = 0) -> GraphView:
+def build_graph(src, radius: float = 0.0, max_influence: int = 0, on_gpu: bool = False,
+                stream=None) -> GraphView:
     """The deformation graph of the source points src [P,3] (Algorithm 1,
-    Sec. 3.1-3.2), built on the host by the library without a GPU: the graph
-    nrr_create would build with the same radius (<= 0: 5 lbar) and influence
-    cap (<= 0: 8)."""
-    v = np.ascontiguousarray(np.asarray(src, dtype=np.float32))
-    if v.ndim != 2 or v.shape[1] != 3:
-        raise ValueError("src must be [P, 3]")
+    Sec. 3.1-3.2): the graph nrr_create would build with the same radius
+    (<= 0: 5 lbar) and influence cap (<= 0: 8), built by the library on the
+    host (nrr_graph_build, no GPU needed) or on the GPU
+    (nrr_graph_build_gpu)."""
     lib = load()
     g = _VP()
-    _check(lib.nrr_graph_build(ctypes.byref(g), _ptr(v), v.shape[0], float(radius), int(max_influence)))
+    if on_gpu and hasattr(src, "data_ptr"):
+        v = src.contiguous()
+        P = int(v.shape[0])
+        _check(lib.nrr_graph_build_gpu(ctypes.byref(g), _ptr(v), P, float(radius), int(max_influence), stream))
+    else:
+        v = np.ascontiguousarray(np.asarray(src, dtype=np.float32))
+        if v.ndim != 2 or v.shape[1] != 3:
+            raise ValueError("src must be [P, 3]")
+        P = int(v.shape[0])
+        if on_gpu:
+            _check(lib.nrr_graph_build_gpu(ctypes.byref(g), _ptr(v), P, float(radius), int(max_influence), stream))
+        else:
+            _check(lib.nrr_graph_build(ctypes.byref(g), _ptr(v), P, float(radius), int(max_influence)))
     try:
         N, E, K = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         R = ctypes.c_double()
         _check(lib.nrr_graph_sizes(g, ctypes.byref(N), ctypes.byref(E), ctypes.byref(K), ctypes.byref(R)))
-        P = v.shape[0]
         nodes = np.zeros(N.value, dtype=np.int32)
         nidx = np.zeros((P, K.value), dtype=np.int32)
         w = np.zeros((P, K.value), dtype=np.float64)
