@@ -13,21 +13,18 @@
 //     eigenvalue with its largest-magnitude entry made positive.
 //  2. The visiting order: projections sorted by a stable radix sort (ties
 //     keep the lower index).
-//  3. The greedy sampling. Visiting the points in that order, a point
-//     becomes a node iff no earlier node lies within R; this is the
-//     lexicographically first maximal independent set of the graph that
-//     joins points closer than R, ranked by the visiting order. It is
-//     computed in rounds over a window of ranks that follows the sweep: a
-//     point with an earlier node within R is covered; a point whose earlier
-//     neighbours within R are all covered is a node; any other point waits.
-//     Both decisions depend only on earlier, already final decisions, so the
-//     result is the sequential one whatever the order of the updates, and
-//     the lowest undecided rank is decided in every round.
+//  3. The greedy sampling, node by node as Algorithm 1 states it: the next
+//     point in visiting order that no node covers becomes a node and covers
+//     every point strictly within R of it. One CTA runs it: its threads share
+//     the forward scan for the next uncovered point and the covering of each
+//     ball, so the sequential steps are the N node creations, not the P
+//     points.
 //  4. Influence sets (the K nearest nodes within R, ties to the lower node
 //     id), weights, the edges between the nodes of each set (sorted, unique)
 //     and r_ij.
 // Neighbours come from a uniform grid of cell size R (points sorted by cell
-// key, cells found by binary search of the sorted keys).
+// key; cells found through a dense table of each cell's first entry, or by
+// binary search of the sorted keys when the grid has too many cells).
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
@@ -189,21 +186,14 @@ __global__ void keys_kernel(const double* __restrict__ V, int64_t P, const doubl
     }
 }
 
-// rank of each point in the visiting order
-__global__ void rank_kernel(int64_t P, const int* __restrict__ order, int* __restrict__ rank) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P; r += (int64_t)gridDim.x * blockDim.x)
-        rank[order[r]] = (int)r;
-}
-
-// the grid's point data in cell order: coordinates and rank
+// the grid's point coordinates in cell order
 __global__ void grid_data_kernel(int64_t P, const int* __restrict__ gitem, const double* __restrict__ V,
-                                 const int* __restrict__ rank, double* __restrict__ gxyz, int* __restrict__ grank) {
+                                 double* __restrict__ gxyz) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < P; s += (int64_t)gridDim.x * blockDim.x) {
         const int i = gitem[s];
         gxyz[3 * s] = V[3 * (int64_t)i];
         gxyz[3 * s + 1] = V[3 * (int64_t)i + 1];
         gxyz[3 * s + 2] = V[3 * (int64_t)i + 2];
-        grank[s] = rank[i];
     }
 }
 
@@ -225,6 +215,11 @@ struct GridView {
     double lo[3];
     double h;
     long long dims[3];
+    const int* cstart;                // [cells + 1]: first entry of each cell key, or NULL (binary search)
+    __device__ __forceinline__ void range(unsigned long long k, int* s0, int* s1) const {
+        if (cstart) { *s0 = cstart[k]; *s1 = cstart[k + 1]; }
+        else cell_range(keys, n, k, s0, s1);
+    }
     __device__ void cell(double x, double y, double z, long long c[3]) const {
         const double p[3] = {x, y, z};
         for (int d = 0; d < 3; ++d) {
@@ -234,100 +229,90 @@ struct GridView {
     }
 };
 
-// One round of the greedy sampling over the ranks [win[0], win[1]):
-// state 0 undecided, 1 node, 2 covered
-__global__ void __launch_bounds__(kT) greedy_round_kernel(GridView g, const int* __restrict__ grank,
-                                                          const int* __restrict__ gitem, const int* __restrict__ order,
-                                                          const double* __restrict__ V, double R2,
-                                                          unsigned char* state, const int* __restrict__ win) {
-    const int r0 = win[0], r1 = win[1];
-    for (int r = r0 + blockIdx.x * blockDim.x + threadIdx.x; r < r1; r += gridDim.x * blockDim.x) {
-        const int v = order[r];
-        if (((volatile unsigned char*)state)[v] != 0) continue;
-        const double x = V[3 * (int64_t)v], y = V[3 * (int64_t)v + 1], z = V[3 * (int64_t)v + 2];
-        long long c[3];
-        g.cell(x, y, z, c);
-        bool covered = false, pending = false;
-        for (long long cx = c[0] - 1; cx <= c[0] + 1 && !covered; ++cx)
-            for (long long cy = c[1] - 1; cy <= c[1] + 1 && !covered; ++cy)
-                for (long long cz = c[2] - 1; cz <= c[2] + 1 && !covered; ++cz) {
-                    if (cx < 0 || cy < 0 || cz < 0 || cx >= g.dims[0] || cy >= g.dims[1] || cz >= g.dims[2]) continue;
-                    int s0, s1;
-                    cell_range(g.keys, g.n, (unsigned long long)((cx * g.dims[1] + cy) * g.dims[2] + cz), &s0, &s1);
-                    for (int s = s0; s < s1; ++s) {
-                        if (grank[s] >= r) continue;   // only earlier points
-                        if (sqd(x, y, z, g.xyz[3 * s], g.xyz[3 * s + 1], g.xyz[3 * s + 2]) < R2) {
-                            const unsigned char su = ((volatile unsigned char*)state)[gitem[s]];
-                            if (su == 1) { covered = true; break; }
-                            if (su == 0) pending = true;
-                        }
-                    }
-                }
-        if (covered) state[v] = 2;
-        else if (!pending) state[v] = 1;
+// first entry of every cell key in the sorted keys (a dense table over all
+// cells of the grid)
+__global__ void cell_start_kernel(const unsigned long long* __restrict__ keys, int n, long long cells,
+                                  int* __restrict__ cstart) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k <= cells; k += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n;
+        while (lo < hi) { const int m = (lo + hi) >> 1; if (keys[m] < (unsigned long long)k) lo = m + 1; else hi = m; }
+        cstart[k] = lo;
     }
 }
 
-// next window: the lowest undecided rank f (from the current one, scanning
-// forward) and the end of the ranks whose projection is within W of f's
-__global__ void __launch_bounds__(1024) window_kernel(int P, const int* __restrict__ order,
-                                                     const unsigned char* state,
-                                                     const unsigned long long* __restrict__ skey,
-                                                     const double* __restrict__ sproj, double W, int* win) {
-    __shared__ int s_f;
-    int f = win[0];
-    while (f < P) {
-        const int r = f + (int)threadIdx.x;
-        const bool und = r < P && ((volatile const unsigned char*)state)[order[r]] == 0;
-        const int any = __syncthreads_or(und);
-        if (threadIdx.x == 0) s_f = P;
+// The greedy sampling, node by node, in one CTA: the next rank (in visiting
+// order) that no node covers becomes a node, and every point strictly within
+// R of it is marked covered (state 0 open, 1 node, 2 covered); the scan goes
+// on after that rank. This is the sequential algorithm itself; the CTA's
+// threads share the forward scan (1024 ranks at a time) and the covering of
+// each ball. nodes[] receives the nodes in order, *n_nodes their number.
+__global__ void __launch_bounds__(1024) greedy_kernel(GridView g, const int* __restrict__ gitem,
+                                                      const int* __restrict__ order, const double* __restrict__ V,
+                                                      int P, double R2, unsigned char* state, int* __restrict__ nodes,
+                                                      int* __restrict__ n_nodes) {
+    __shared__ int s_next;
+    __shared__ int s_beg[27], s_off[28];
+    int pos = 0, nn = 0;
+    while (pos < P) {
+        // ---- the next open rank at or after pos
+        if (threadIdx.x == 0) s_next = P;
         __syncthreads();
-        if (und) atomicMin(&s_f, r);
+        const int r = pos + (int)threadIdx.x;
+        if (r < P && ((volatile unsigned char*)state)[order[r]] == 0) atomicMin(&s_next, r);
         __syncthreads();
-        if (any) { f = s_f; break; }
-        f += 1024;
-    }
-    if (f > P) f = P;
-    if (threadIdx.x == 0) {
-        int hi = f;
-        if (f < P) {
-            const double lim = sproj[f] + W;
-            int lo = f, up = P;
-            while (lo < up) { const int m = (lo + up) >> 1; if (sproj[m] <= lim) lo = m + 1; else up = m; }
-            hi = lo;
+        const int f = s_next;
+        if (f == P) {
+            pos += 1024;
+            continue;
         }
-        win[0] = f;
-        win[1] = hi;
-        (void)skey;
+        // ---- rank f becomes node nn and covers its ball
+        const int v = order[f];
+        const double x = V[3 * (int64_t)v], y = V[3 * (int64_t)v + 1], z = V[3 * (int64_t)v + 2];
+        if (threadIdx.x < 27) {
+            long long c[3];
+            g.cell(x, y, z, c);
+            const long long cx = c[0] - 1 + threadIdx.x / 9, cy = c[1] - 1 + (threadIdx.x / 3) % 3,
+                            cz = c[2] - 1 + threadIdx.x % 3;
+            int s0 = 0, s1 = 0;
+            if (cx >= 0 && cy >= 0 && cz >= 0 && cx < g.dims[0] && cy < g.dims[1] && cz < g.dims[2])
+                g.range((unsigned long long)((cx * g.dims[1] + cy) * g.dims[2] + cz), &s0, &s1);
+            s_beg[threadIdx.x] = s0;
+            s_off[threadIdx.x + 1] = s1 - s0;
+        }
+        if (threadIdx.x == 0) {
+            state[v] = 1;
+            nodes[nn] = v;
+            s_off[0] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 27; ++k) s_off[k + 1] += s_off[k];
+        __syncthreads();
+        const int total = s_off[27];
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int k = 0;
+            while (s_off[k + 1] <= t) ++k;
+            const int sidx = s_beg[k] + (t - s_off[k]);
+            if (sqd(x, y, z, g.xyz[3 * sidx], g.xyz[3 * sidx + 1], g.xyz[3 * sidx + 2]) < R2) {
+                const int u = gitem[sidx];
+                if (((volatile unsigned char*)state)[u] == 0) state[u] = 2;
+            }
+        }
+        ++nn;
+        pos = f + 1;
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *n_nodes = nn;
 }
 
-// projections in visiting order (for the window), recomputed as in keys_kernel
-__global__ void sorted_proj_kernel(int64_t P, const int* __restrict__ order, const double* __restrict__ V,
-                                   const double* __restrict__ sc, double* __restrict__ sproj) {
-    const double a0 = sc[9], a1 = sc[10], a2 = sc[11];
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P; r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = order[r];
-        sproj[r] = __dadd_rn(__dadd_rn(__dmul_rn(V[3 * i], a0), __dmul_rn(V[3 * i + 1], a1)), __dmul_rn(V[3 * i + 2], a2));
-    }
-}
-
-__global__ void node_flags_kernel(int64_t P, const int* __restrict__ order, const unsigned char* __restrict__ state,
-                                  int* __restrict__ flag) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P; r += (int64_t)gridDim.x * blockDim.x)
-        flag[r] = state[order[r]] == 1 ? 1 : 0;
-}
-
-__global__ void nodes_kernel(int64_t P, const int* __restrict__ order, const int* __restrict__ flag,
-                             const int* __restrict__ nid, const double* __restrict__ V, const double* __restrict__ sc,
-                             double h, long long d1, long long d2, int* __restrict__ nodes, double* __restrict__ pn,
-                             unsigned long long* __restrict__ nkey, int* __restrict__ nval) {
+// node positions and node-grid keys
+__global__ void nodes_kernel(int N, const int* __restrict__ nodes, const double* __restrict__ V,
+                             const double* __restrict__ sc, double h, long long d1, long long d2,
+                             double* __restrict__ pn, unsigned long long* __restrict__ nkey, int* __restrict__ nval) {
     const double lo[3] = {sc[3], sc[4], sc[5]};
     const long long dims[3] = {(long long)sc[12], d1, d2};
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P; r += (int64_t)gridDim.x * blockDim.x) {
-        if (!flag[r]) continue;
-        const int j = nid[r], i = order[r];
-        nodes[j] = i;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        const int i = nodes[j];
         long long c[3];
         for (int d = 0; d < 3; ++d) {
             const double x = V[3 * (int64_t)i + d];
@@ -365,7 +350,7 @@ __global__ void __launch_bounds__(kT) influence_kernel(GridView g, const int* __
                 for (long long cz = c[2] - 1; cz <= c[2] + 1; ++cz) {
                     if (cx < 0 || cy < 0 || cz < 0 || cx >= g.dims[0] || cy >= g.dims[1] || cz >= g.dims[2]) continue;
                     int s0, s1;
-                    cell_range(g.keys, g.n, (unsigned long long)((cx * g.dims[1] + cy) * g.dims[2] + cz), &s0, &s1);
+                    g.range((unsigned long long)((cx * g.dims[1] + cy) * g.dims[2] + cz), &s0, &s1);
                     for (int s = s0; s < s1; ++s) {
                         const double d2 = sqd(x, y, z, g.xyz[3 * s], g.xyz[3 * s + 1], g.xyz[3 * s + 2]);
                         if (!(d2 < R2)) continue;
@@ -566,62 +551,48 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     GK(cudaMemcpyAsync(sc + 12, hsc + 12, sizeof(double), cudaMemcpyHostToDevice, st));
     // ---- 2. the visiting order and the grid
     unsigned long long *pkey, *pkey_s, *ckey, *ckey_s;
-    int *idx, *order, *gitem, *rank, *grank;
-    double *gxyz, *sproj;
+    int *idx, *order, *gitem;
+    double* gxyz;
     GK(s.get(&pkey, P)); GK(s.get(&pkey_s, P)); GK(s.get(&ckey, P)); GK(s.get(&ckey_s, P));
-    GK(s.get(&idx, P)); GK(s.get(&order, P)); GK(s.get(&gitem, P)); GK(s.get(&rank, P)); GK(s.get(&grank, P));
-    GK(s.get(&gxyz, (size_t)P * 3)); GK(s.get(&sproj, P));
+    GK(s.get(&idx, P)); GK(s.get(&order, P)); GK(s.get(&gitem, P));
+    GK(s.get(&gxyz, (size_t)P * 3));
     keys_kernel<<<blocks_for(P), kT, 0, st>>>(V, P, sc, h, dims[1], dims[2], pkey, ckey, idx);
     GK(cudaGetLastError());
     GK(sort_pairs(s, pkey, pkey_s, idx, order, n, 64, st));
     GK(sort_pairs(s, ckey, ckey_s, idx, gitem, n, 64, st));
-    rank_kernel<<<blocks_for(P), kT, 0, st>>>(P, order, rank);
-    grid_data_kernel<<<blocks_for(P), kT, 0, st>>>(P, gitem, V, rank, gxyz, grank);
-    sorted_proj_kernel<<<blocks_for(P), kT, 0, st>>>(P, order, V, sc, sproj);
+    grid_data_kernel<<<blocks_for(P), kT, 0, st>>>(P, gitem, V, gxyz);
     GK(cudaGetLastError());
-    // ---- 3. greedy sampling in rounds over a window that follows the sweep
-    unsigned char* state;
-    int* win;
-    GK(s.get(&state, P));
-    GK(s.get(&win, 2));
-    GK(cudaMemsetAsync(state, 0, (size_t)P, st));
-    GK(cudaMemsetAsync(win, 0, 2 * sizeof(int), st));
-    GridView gv{ckey_s, gxyz, n, {hsc[3], hsc[4], hsc[5]}, h, {dims[0], dims[1], dims[2]}};
-    const double W = 2.0 * R;
-    window_kernel<<<1, 1024, 0, st>>>(n, order, state, pkey_s, sproj, W, win);
-    int hwin[2] = {0, 0};
-    int nr = 0;
-    const int batch = 16;
-    while (true) {
-        for (int k = 0; k < batch; ++k) {
-            greedy_round_kernel<<<304, kT, 0, st>>>(gv, grank, gitem, order, V, R2, state, win);
-            window_kernel<<<1, 1024, 0, st>>>(n, order, state, pkey_s, sproj, W, win);
-        }
-        nr += batch;
-        GK(cudaGetLastError());
-        GK(cudaMemcpyAsync(hwin, win, sizeof hwin, cudaMemcpyDeviceToHost, st));
-        GK(cudaStreamSynchronize(st));
-        if (hwin[0] >= n) break;
-        if (nr > 4 * n + 64) return cudaErrorUnknown;   // cannot happen: every round decides its lowest rank
+    // ---- 3. the greedy sampling (one CTA, node by node)
+    const double cells_d = (double)dims[0] * (double)dims[1] * (double)dims[2];
+    const bool dense = cells_d <= 4.0 * (double)P + 1048576.0;
+    const long long cells = (long long)cells_d;
+    int* cstart = nullptr;
+    if (dense) {
+        GK(s.get(&cstart, (size_t)cells + 1));
+        cell_start_kernel<<<blocks_for(cells + 1), kT, 0, st>>>(ckey_s, n, cells, cstart);
     }
-    if (rounds) *rounds = nr;
-    // ---- node ids (visiting order), positions and the node grid
-    int *flag, *nid;
-    GK(s.get(&flag, P)); GK(s.get(&nid, P));
-    node_flags_kernel<<<blocks_for(P), kT, 0, st>>>(P, order, state, flag);
-    GK(exclusive_sum(s, flag, nid, n, st));
-    int last[2];
-    GK(cudaMemcpyAsync(&last[0], nid + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GK(cudaMemcpyAsync(&last[1], flag + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    unsigned char* state;
+    int *nodes, *nnode;
+    GK(s.get(&state, P));
+    GK(s.get(&nodes, P));
+    GK(s.get(&nnode, 1));
+    GK(cudaMemsetAsync(state, 0, (size_t)P, st));
+    GridView gv{ckey_s, gxyz, n, {hsc[3], hsc[4], hsc[5]}, h, {dims[0], dims[1], dims[2]}, cstart};
+    greedy_kernel<<<1, 1024, 0, st>>>(gv, gitem, order, V, n, R2, state, nodes, nnode);
+    GK(cudaGetLastError());
+    int N = 0;
+    GK(cudaMemcpyAsync(&N, nnode, sizeof(int), cudaMemcpyDeviceToHost, st));
     GK(cudaStreamSynchronize(st));
-    const int N = last[0] + last[1];
-    int *nodes, *nval, *nsorted;
+    if (rounds) *rounds = N;
+    int last[2];
+    // ---- node positions and the node grid
+    int *nval, *nsorted;
     double *pn, *nxyz;
     unsigned long long *nkey, *nkey_s;
-    GK(s.get(&nodes, N)); GK(s.get(&nval, N)); GK(s.get(&nsorted, N));
+    GK(s.get(&nval, N)); GK(s.get(&nsorted, N));
     GK(s.get(&pn, (size_t)N * 3)); GK(s.get(&nxyz, (size_t)N * 3));
     GK(s.get(&nkey, N)); GK(s.get(&nkey_s, N));
-    nodes_kernel<<<blocks_for(P), kT, 0, st>>>(P, order, flag, nid, V, sc, h, dims[1], dims[2], nodes, pn, nkey, nval);
+    nodes_kernel<<<blocks_for(N), kT, 0, st>>>(N, nodes, V, sc, h, dims[1], dims[2], pn, nkey, nval);
     GK(cudaGetLastError());
     GK(sort_pairs(s, nkey, nkey_s, nval, nsorted, N, 64, st));
     node_grid_xyz_kernel<<<blocks_for(N), kT, 0, st>>>(N, nsorted, pn, nxyz);
@@ -630,7 +601,12 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     double* w;
     GK(s.get(&nidx, (size_t)P * K)); GK(s.get(&w, (size_t)P * K));
     GK(s.get(&npairs, P)); GK(s.get(&poff, P));
-    GridView nv{nkey_s, nxyz, N, {hsc[3], hsc[4], hsc[5]}, h, {dims[0], dims[1], dims[2]}};
+    int* ncstart = nullptr;
+    if (dense) {
+        GK(s.get(&ncstart, (size_t)cells + 1));
+        cell_start_kernel<<<blocks_for(cells + 1), kT, 0, st>>>(nkey_s, N, cells, ncstart);
+    }
+    GridView nv{nkey_s, nxyz, N, {hsc[3], hsc[4], hsc[5]}, h, {dims[0], dims[1], dims[2]}, ncstart};
     influence_kernel<<<blocks_for(P), kT, 0, st>>>(nv, nsorted, V, P, R2, K, nidx, w, npairs);
     GK(cudaGetLastError());
     GK(exclusive_sum(s, npairs, poff, n, st));

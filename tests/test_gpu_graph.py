@@ -78,15 +78,17 @@ def test_gpu_graph_equals_oracle():
 
 def test_create_with_graph_on_gpu():
     """nrr_create builds the same context with either construction: the same
-    graph and the same first pass."""
+    graph and the same first pass (to rounding)."""
     nrr = _nrr()
     pair = synth.workload("sphere5k")
     kw = dict(radius=0.15, aa_m=5, precision="fp64")
     a = nrr.Registration(pair.src, pair.tgt, **kw)
     b = nrr.Registration(pair.src, pair.tgt, graph_on_gpu=1, **kw)
     _same(b.graph(), a.graph())
+    # the weights and r_ij agree to rounding (pow and the r_ij sum order
+    # differ between the constructions), so the first pass agrees to rounding
     ia, ib = a.step(), b.step()
-    assert ia.E == ib.E
-    assert np.array_equal(a.transforms(), b.transforms())
+    assert abs(ia.E - ib.E) < 1e-12 * abs(ia.E)
+    assert relmax(b.transforms(), a.transforms()) < 1e-11
     a.close()
     b.close()
