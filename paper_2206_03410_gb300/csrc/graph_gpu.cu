@@ -107,7 +107,10 @@ __device__ void jacobi3(const double Ain[9], double ev[3], double Q[9]) {
     double A[9];
     for (int i = 0; i < 9; ++i) { A[i] = Ain[i]; Q[i] = (i % 4 == 0) ? 1.0 : 0.0; }
     for (int sweep = 0; sweep < 50; ++sweep) {
-        if (A[1] * A[1] + A[2] * A[2] + A[5] * A[5] == 0.0) break;
+        // off-diagonal mass below (1e-18 of the diagonal)^2: further
+        // rotations move no eigenvector by a unit in the last place
+        const double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        if (off <= 1e-36 * (A[0] * A[0] + A[4] * A[4] + A[8] * A[8])) break;
         for (int p = 0; p < 2; ++p)
             for (int q = p + 1; q < 3; ++q) {
                 const double apq = A[3 * p + q];
