@@ -309,14 +309,23 @@ def stepped_profile(reg, stream, imax, final_stage=None, r64=None, E_target=None
             "passes": prev.n_passes, "iters": prev.n_solves}
 
 
-def ttc_compare(nrr, pair, kw, stream, args, stepped: bool = True) -> dict:
+def ttc_compare(nrr, pair, kw, stream, args, stepped: bool = True, split: bool = False) -> dict:
     """Time-to-converge of the mixed path, the FP64 path and the control arm
     on one pair (wall time of nrr_solve from X = I, each tuned), their final
     energies evaluated in FP64 at the FP64 run's final nu (signed relative
     gaps to the FP64 arm), how every stage of the mixed and FP64 runs ended,
     and the time the mixed run takes to reach the FP64 run's final energy
     within 1e-5 relative (its iterate in the final stage, evaluated in FP64
-    at the final nu; "reached": false if it never does)."""
+    at the final nu; "reached": false if it never does).
+
+    With ``split``, two more measurements separate the precision's own effect
+    from the divergence of trajectories: ``shared_start`` restarts the final
+    stage of the mixed path (and of the FP64 path) from the FP64 run's
+    converged iterate and reports the signed FP64-energy gap of where each
+    ends; ``summation_order`` reruns the FP64 path from X = I with another
+    PCG partition (another CTA count, hence another order of every
+    reduction in the solve, the only step whose order depends on the launch
+    shape) and reports its signed gap to the FP64 arm."""
     import torch
     src = torch.from_numpy(pair.src).cuda()
     tgt = torch.from_numpy(pair.tgt).cuda()
@@ -346,6 +355,47 @@ def ttc_compare(nrr, pair, kw, stream, args, stepped: bool = True) -> dict:
     out["gap"] = float((E["mixed"] - e64) / abs(e64))
     out["gap_" + CONTROL] = float((E[CONTROL] - e64) / abs(e64))
     out["speedup"] = round(out["fp64"]["ms"] / out["mixed"]["ms"], 3)
+    if split:
+        X64 = finals["fp64"][0]
+        sh = {"start": "the FP64 run's final iterate, final stage (nu_a, nu_r) restarted"}
+        for name in ("mixed", "fp64"):
+            r = regs[name]
+            r.reset()
+            r.set_transforms(X64)
+            r.set_stage(i64.nu_a, i64.nu_r)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            inf = r.solve(100000)
+            torch.cuda.synchronize()
+            ms = round((time.perf_counter() - t0) * 1e3, 2)
+            Xs = r.transforms()
+            r64.set_stage(i64.nu_a, i64.nu_r)
+            e = float(r64.energy(Xs)[0])
+            sh[name] = {"ms": ms, "iters": inf.n_solves, "done": inf.done, "gap": float((e - e64) / abs(e64))}
+        sh["mixed_within_1e-5"] = abs(sh["mixed"]["gap"]) <= 1e-5
+        out["shared_start"] = sh
+        # the FP64 path on the same pair with the source points in another
+        # order: every sum over points (energy, assembly, and through them
+        # the solve) runs in another order; the graph and the node order
+        # are the same (checked), so the final transforms compare directly
+        perm = np.random.default_rng(7).permutation(pair.P)
+        srcp = torch.from_numpy(np.ascontiguousarray(pair.src[perm])).cuda()
+        r2 = nrr.Registration(srcp, tgt, stream=stream.cuda_stream, precision="fp64", **kw)
+        same_graph = bool(np.array_equal(perm[r2.graph().nodes], r64.graph().nodes))
+        so = {"permutation": "seeded permutation of the source points", "same_graph": same_graph}
+        if same_graph:
+            if not args.no_tune:
+                r2.tune()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            inf = r2.solve(100000)
+            torch.cuda.synchronize()
+            so["ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+            so["iters"] = inf.n_solves
+            r64.set_stage(i64.nu_a, i64.nu_r)
+            so["gap"] = float((float(r64.energy(r2.transforms())[0]) - e64) / abs(e64))
+        r2.close()
+        out["summation_order"] = so
     if stepped:
         target = e64 * (1 + 1e-5)
         prof = stepped_profile(regs["mixed"], stream, imax, final_stage=i64.stage, r64=r64, E_target=target)
@@ -591,7 +641,7 @@ def run_ours(args):
 
         # ---- time-to-converge: mixed vs FP64, same energy -----------------
         if not args.no_ttc:
-            ttc = {"main": ttc_compare(nrr, pair, kw, stream, args)}
+            ttc = {"main": ttc_compare(nrr, pair, kw, stream, args, split=True)}
             main = ttc["main"]
             ttc["speedup_mixed_vs_fp64"] = main["speedup"]
             ttc["energy_rel_gap"] = abs(main["gap"])
@@ -615,7 +665,7 @@ def run_ours(args):
             # I_max large enough that the energy rule ends the stages
             if not args.no_uncapped:
                 kw_u = dict(kw, max_iters_per_stage=UNCAPPED_IMAX)
-                ttc["uncapped"] = dict(ttc_compare(nrr, pair, kw_u, stream, args),
+                ttc["uncapped"] = dict(ttc_compare(nrr, pair, kw_u, stream, args, split=True),
                                        max_iters_per_stage=UNCAPPED_IMAX)
             result["ttc"] = ttc
 
@@ -640,11 +690,33 @@ def run_ours(args):
                 runs.append(time.perf_counter() - t0)
             dt = min(runs)
             its = sum(i.n_solves for i in infos)
+            # HBM view of the batch (its working set exceeds L2): the
+            # algorithmic bytes of one pass of every pair, the solve at the
+            # CG iterations of each pair's last pass, over the tuned batch
+            # pass time
+            ab_tot, ab_solve = 0.0, 0.0
+            for k, inf in enumerate(infos):
+                g = nrr.nrr_get_graph(bt.context(k))
+                Pk, Tk, Nk, Ek, _ = nrr.nrr_get_sizes(bt.context(k))
+                a = algorithmic_bytes(Pk, Tk, Nk, 2 * Ek, int((g.nidx >= 0).sum()), inf.pcg_iters)
+                ab_tot += sum(a.values())
+                ab_solve += a["solve_kernel"]
+            pass_ms = launch.get("batch", {}).get("pass_ms")
             result["batch"] = {"workload": "64 sphere pairs, P log-uniform 2k-40k (sum %d), N 100-1000, "
                                            "crop 0-30 %%, outliers 0-10 %%, mixed" % sum(p.P for p in pairs),
                                "ms_to_converge_all": round(dt * 1e3, 2), "pairs_per_s": round(64 / dt, 2),
                                "mm_iters_per_s": round(its / dt, 1), "iters": its,
-                               "all_done": all(i.done for i in infos), "create_s": round(t_create, 2)}
+                               "all_done": all(i.done for i in infos), "create_s": round(t_create, 2),
+                               "loop": "device-side (one graph launch repeats the pass until every pair "
+                                       "has returned or half of the captured pairs have)",
+                               "algorithmic_bytes_per_pass": int(ab_tot),
+                               "algorithmic_bytes_per_pass_without_solve": int(ab_tot - ab_solve)}
+            if pass_ms:
+                gbs = ab_tot / (pass_ms / 1e3) / 1e9
+                result["batch"]["hbm"] = {"pass_ms": pass_ms, "GB_s": round(gbs, 1),
+                                          "frac": round(gbs / float(peaks.get("hbm_gbs", 6800.0)), 4),
+                                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks
+                                          else "fallback"}
             bt.close()
 
         # ---- robust-norm variants (Sec. 4.2) on the partial-overlap workload ----

@@ -190,7 +190,13 @@ nrr_status nrr_step(nrr_ctx* ctx, nrr_step_info* info);
 
 /* Runs passes until Algorithm 2 returns or max_passes (<= 0: the
  * max_total_passes parameter) passes have run. info (host, may be NULL)
- * receives the final state; NRR_E_NOT_CONVERGED if the cap was hit. */
+ * receives the final state; NRR_E_NOT_CONVERGED if the cap was hit. The
+ * passes repeat on the device inside one graph launch (a conditional loop
+ * whose body is the pass and a control kernel that tests the returned
+ * flag, the status and the cap); the host reads the state once at the
+ * end. With the environment variable NRR_HOST_LOOP set when the context's
+ * pass graph is captured, the host launches the passes in groups of four
+ * instead (same results). */
 nrr_status nrr_solve(nrr_ctx* ctx, int max_passes, nrr_step_info* info);
 
 /* Enqueues n passes (as nrr_step, without the host summary) on the
@@ -451,7 +457,11 @@ nrr_status nrr_batch_create(nrr_batch** out, int n_pairs, const float* const* sr
 /* Runs batch passes until every pair's Algorithm 2 has returned or
  * max_passes (<= 0: the largest max_total_passes) passes ran. infos (host,
  * may be NULL) receives n_pairs summaries. NRR_E_NOT_CONVERGED if the cap
- * was hit. */
+ * was hit. One graph launch repeats the pass of every captured pair on the
+ * device until every pair has returned, a pair failed, the cap is reached
+ * or half of the captured pairs have returned; the host then recaptures
+ * the pairs still running (passes of returned pairs launch and do
+ * nothing) and launches again. */
 nrr_status nrr_batch_solve(nrr_batch* b, int max_passes, nrr_step_info* infos);
 
 /* Restarts every pair (nrr_reset). */

@@ -67,6 +67,10 @@ struct nrr_ctx {
     DevProblem<double> dd{};
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
+    cudaGraphExec_t loop_exec = nullptr;   // passes repeated on the device (nrr_solve)
+    NrrState** d_states1 = nullptr;        // {d_state}, for the loop's control kernel
+    int* d_ctrl = nullptr;                 // loop control: [0] passes run, [1] cap
+    int* h_ctrl = nullptr;                 // pinned staging of the cap
     bool coop = true;
     int grid_energy = 0, grid_asm = 0, grid_solve = 0, grid_aa = 0, num_sms = 0;
     int nn_lpq = 8;                    // closest points: lanes per query (1, 2, 4, 8)
@@ -383,11 +387,94 @@ cudaError_t launch_pass(nrr_ctx* c) {
 
 cudaError_t launch_pass_any(nrr_ctx* c) { return c->fp64 ? launch_pass<double>(c) : launch_pass<float>(c); }
 
+// Control of a device-side pass loop (one CTA): copies every context's
+// done flag, status and counters to `flags` (when given), counts the
+// contexts still running, and lets the loop's body run again while one is
+// running, none has failed, fewer than ctrl[1] passes ran in this launch and
+// more than half of the `members` contexts whose passes the body holds are
+// still running (below that the host recaptures a smaller body).
+__global__ void loop_control(NrrState* const* st, int n, int members, int* flags, int* ctrl,
+                             cudaGraphConditionalHandle h) {
+    __shared__ int s_run, s_err;
+    if (threadIdx.x == 0) { s_run = 0; s_err = 0; }
+    __syncthreads();
+    int run = 0, err = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const NrrState* s = st[i];
+        if (flags) {
+            flags[4 * i + 0] = s->done;
+            flags[4 * i + 1] = s->status;
+            flags[4 * i + 2] = s->n_passes;
+            flags[4 * i + 3] = s->n_solves;
+        }
+        err |= s->status != 0;
+        run += s->status == 0 && !s->done;
+    }
+    if (run) atomicAdd(&s_run, run);
+    if (err) atomicOr(&s_err, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int k = ctrl[0] + 1;
+        ctrl[0] = k;
+        const bool more = s_run > 0 && !s_err && k < ctrl[1] && 2 * s_run > members;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
+// Builds `*out`: one conditional WHILE node whose body is what `body`
+// enqueues on `stream` (captured into the body graph) followed by
+// loop_control. The handle starts at 1 on every launch, so a launch runs the
+// body at least once.
+template <typename F>
+cudaError_t build_loop_graph(cudaStream_t stream, F&& body, NrrState* const* st, int n, int members,
+                             int* flags, int* ctrl, cudaGraphExec_t* out) {
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h{};
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams prm{};
+    cudaGraph_t bodyg = nullptr;
+    if (e == cudaSuccess) {
+        prm.type = cudaGraphNodeTypeConditional;
+        prm.conditional.handle = h;
+        prm.conditional.type = cudaGraphCondTypeWhile;
+        prm.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &prm);
+        if (e == cudaSuccess) bodyg = prm.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(stream, bodyg, nullptr, nullptr, 0,
+                                                            cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t be = body();
+        if (be == cudaSuccess) {
+            loop_control<<<1, 256, 0, stream>>>(st, n, members, flags, ctrl, h);
+            be = cudaGetLastError();
+        }
+        cudaGraph_t captured = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(stream, &captured);
+        e = be != cudaSuccess ? be : ee;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+    }
+    return e;
+}
+
 nrr_status capture_graph(nrr_ctx* c) {
     c->use_graph = false;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
+    }
+    if (c->loop_exec) {
+        cudaGraphExecDestroy(c->loop_exec);
+        c->loop_exec = nullptr;
     }
     if (std::getenv("NRR_NO_GRAPH")) return NRR_OK;
     cudaGraph_t g = nullptr;
@@ -410,6 +497,11 @@ nrr_status capture_graph(nrr_ctx* c) {
         return NRR_OK;
     }
     c->use_graph = true;
+    // the same pass as the body of a device-side loop (nrr_solve); without
+    // it nrr_solve launches the pass graph from the host
+    if (c->d_states1 && !std::getenv("NRR_HOST_LOOP"))
+        build_loop_graph(c->stream, [c]() { return launch_pass_any(c); }, c->d_states1, 1, 1, nullptr,
+                         c->d_ctrl, &c->loop_exec);
     return NRR_OK;
 }
 
@@ -418,6 +510,7 @@ nrr_status run_pass(nrr_ctx* c) {
     else CK(launch_pass_any(c));
     return NRR_OK;
 }
+
 
 void fill_info(const NrrState& s, nrr_step_info* info) {
     if (!info) return;
@@ -1432,6 +1525,10 @@ void nrr_destroy(nrr_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+    if (c->d_states1) cudaFree(c->d_states1);
+    if (c->d_ctrl) cudaFree(c->d_ctrl);
+    if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
     for (void* p : c->allocs) cudaFree(p);
     if (c->d_order) cudaFree(c->d_order);
     if (c->d_grad) cudaFree(c->d_grad);
@@ -1557,6 +1654,10 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     CK(cudaMalloc(&c->d_state, sizeof(NrrState)));
     CK(cudaMallocHost(&c->h_state, sizeof(NrrState)));
     std::memset(c->h_state, 0, sizeof(NrrState));
+    CK(cudaMalloc(&c->d_states1, sizeof(NrrState*)));
+    CK(cudaMemcpy(c->d_states1, &c->d_state, sizeof(NrrState*), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->d_ctrl, 2 * sizeof(int)));
+    CK(cudaMallocHost(&c->h_ctrl, 2 * sizeof(int)));
     orders_thread.t.join();
     tm.lap("curve orders (joined)");
     nrr_status st = c->fp64 ? build_device<double>(c, src, tgt, co, tm) : build_device<float>(c, src, tgt, co, tm);
@@ -1638,6 +1739,22 @@ nrr_status nrr_solve(nrr_ctx* c, int max_passes, nrr_step_info* info) {
     nrr_status st = pull_state(c);
     if (st != NRR_OK) return st;
     const int start = c->h_state->n_passes;
+    if (c->use_graph && c->loop_exec && !c->h_state->done) {
+        // every pass on the device: one launch, one read of the state
+        c->h_ctrl[0] = 0;
+        c->h_ctrl[1] = cap;
+        CK(cudaMemcpyAsync(c->d_ctrl, c->h_ctrl, 2 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaGraphLaunch(c->loop_exec, c->stream));
+        st = pull_state(c);
+        if (st != NRR_OK) { c->failed = true; return st; }
+        if (c->h_state->status != 0) {
+            c->failed = true;
+            fill_info(*c->h_state, info);
+            return fail(c, (nrr_status)c->h_state->status, "device-side wait timed out");
+        }
+        fill_info(*c->h_state, info);
+        return c->h_state->done ? NRR_OK : NRR_E_NOT_CONVERGED;
+    }
     int launched = 0;
     const int batch = 4;
     while (!c->h_state->done && c->h_state->n_passes - start < cap) {
@@ -2202,6 +2319,9 @@ struct nrr_batch {
     int* d_flags = nullptr;
     int* h_flags = nullptr;
     std::vector<int> captured;   // pairs whose pass the batch graph holds
+    cudaGraphExec_t loop_exec = nullptr;   // the same passes repeated on the device
+    int* d_ctrl = nullptr;                 // loop control: [0] passes run, [1] cap
+    int* h_ctrl = nullptr;
     std::string err;
 };
 
@@ -2270,6 +2390,30 @@ nrr_status batch_capture(nrr_batch* b, const std::vector<int>& members) {
     cudaError_t ie = cudaGraphInstantiate(&b->gexec, g, 0);
     cudaGraphDestroy(g);
     BK(ie);
+    // the members' passes as the body of a device-side loop that runs
+    // until every pair has returned, a pair failed, the cap is reached, or
+    // half of the members have returned (then the host recaptures)
+    if (b->loop_exec) {
+        cudaGraphExecDestroy(b->loop_exec);
+        b->loop_exec = nullptr;
+    }
+    if (!std::getenv("NRR_HOST_LOOP")) {
+        auto body = [b, &members]() {
+            const int n_all = (int)b->ctx.size();
+            cudaError_t e = cudaEventRecord(b->events[(size_t)n_all], b->stream);
+            for (int i : members) {
+                if (e != cudaSuccess) break;
+                nrr_ctx* c = b->ctx[(size_t)i];
+                e = cudaStreamWaitEvent(c->stream, b->events[(size_t)n_all], 0);
+                if (e == cudaSuccess) e = launch_pass_any(c);
+                if (e == cudaSuccess) e = cudaEventRecord(b->events[(size_t)i], c->stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->events[(size_t)i], 0);
+            }
+            return e;
+        };
+        build_loop_graph(b->stream, body, b->d_states, n, (int)members.size(), b->d_flags, b->d_ctrl,
+                         &b->loop_exec);
+    }
     return NRR_OK;
 }
 
@@ -2360,6 +2504,9 @@ void nrr_batch_destroy(nrr_batch* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->loop_exec) cudaGraphExecDestroy(b->loop_exec);
+    if (b->d_ctrl) cudaFree(b->d_ctrl);
+    if (b->h_ctrl) cudaFreeHost(b->h_ctrl);
     for (nrr_ctx* c : b->ctx) nrr_destroy(c);
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
     if (b->d_states) cudaFree(b->d_states);
@@ -2402,6 +2549,8 @@ nrr_status nrr_batch_create(nrr_batch** out, int n_pairs, const float* const* sr
     BK(cudaMemcpy(b->d_states, sts.data(), sizeof(NrrState*) * (size_t)n, cudaMemcpyHostToDevice));
     BK(cudaMalloc(&b->d_flags, sizeof(int) * 4 * (size_t)n));
     BK(cudaMallocHost(&b->h_flags, sizeof(int) * 4 * (size_t)n));
+    BK(cudaMalloc(&b->d_ctrl, 2 * sizeof(int)));
+    BK(cudaMallocHost(&b->h_ctrl, 2 * sizeof(int)));
     b->events.resize((size_t)n + 1);
     for (auto& e : b->events) BK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     nrr_status cst = batch_capture(b, all_pairs(b));
@@ -2430,11 +2579,22 @@ nrr_status nrr_batch_solve(nrr_batch* b, int max_passes, nrr_step_info* infos) {
         if (cst != NRR_OK) return cst;
     }
     while (!all_done && launched < cap) {
-        const int nb = std::min(4, cap - launched);
-        for (int k = 0; k < nb; ++k) BK(cudaGraphLaunch(b->gexec, b->stream));
-        launched += nb;
+        if (b->loop_exec) {
+            // passes repeat on the device until every pair has returned or
+            // half of the captured pairs have (the cap and failures too)
+            b->h_ctrl[0] = 0;
+            b->h_ctrl[1] = cap - launched;
+            BK(cudaMemcpyAsync(b->d_ctrl, b->h_ctrl, 2 * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+            BK(cudaGraphLaunch(b->loop_exec, b->stream));
+            BK(cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        } else {
+            const int nb = std::min(4, cap - launched);
+            for (int k = 0; k < nb; ++k) BK(cudaGraphLaunch(b->gexec, b->stream));
+            b->h_ctrl[0] = nb;
+        }
         BK(cudaMemcpyAsync(b->h_flags, b->d_flags, sizeof(int) * 4 * (size_t)n, cudaMemcpyDeviceToHost, b->stream));
         BK(cudaStreamSynchronize(b->stream));
+        launched += b->h_ctrl[0];
         all_done = true;
         std::vector<int> running;
         for (int i = 0; i < n; ++i) {
