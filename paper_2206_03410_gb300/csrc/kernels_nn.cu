@@ -281,8 +281,17 @@ __global__ void __launch_bounds__(kThreads) nn_kernel(DevProblem<T> d) {
     };
     refresh_bounds();
 
-    if (any_valid) {
-        for (int s0 = 0; s0 < d.n_supers; s0 += 32) {
+    // mega tiles (32 super tiles each) first, then the super tiles of each
+    // candidate mega tile: super tiles are visited in the same order as by
+    // a flat scan, the tests of those whose mega tile is out of reach are
+    // skipped (a mega tile's box holds its super tiles' boxes, and bounds
+    // only shrink)
+    for (int m0 = 0; any_valid && m0 < d.n_megas; m0 += 32) {
+        const int m = m0 + lane;
+        unsigned mmask = __ballot_sync(0xffffffffu, m < d.n_megas && candidate(d.mega_box + 6 * m));
+        while (mmask) {
+            const int s0 = (m0 + __ffs(mmask) - 1) * 32;
+            mmask &= mmask - 1;
             const int s = s0 + lane;
             bool sc = s < d.n_supers && candidate(d.super_box + 6 * s);
             unsigned smask = __ballot_sync(0xffffffffu, sc);

@@ -814,6 +814,17 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
             }
         std::memcpy(&sbox[(size_t)S * 6], b, sizeof(b));
     }
+    const int nm = (ns + 31) / 32;
+    std::vector<float> mbox((size_t)nm * 6);
+    for (int M = 0; M < nm; ++M) {
+        float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int S = M * 32; S < std::min(ns, (M + 1) * 32); ++S)
+            for (int a = 0; a < 3; ++a) {
+                b[a] = std::min(b[a], sbox[(size_t)S * 6 + a]);
+                b[3 + a] = std::max(b[3 + a], sbox[(size_t)S * 6 + 3 + a]);
+            }
+        std::memcpy(&mbox[(size_t)M * 6], b, sizeof(b));
+    }
     // initial correspondence guess: the target point next along the curve
     std::vector<T> u0((size_t)(3 * P));
     std::vector<int> rho0((size_t)P);
@@ -828,7 +839,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     for (int j = 0; j < N; ++j) { X0[(size_t)12 * j + 0] = 1; X0[(size_t)12 * j + 4] = 1; X0[(size_t)12 * j + 8] = 1; }
 
     tm.lap("leaves + initial bound");
-    d.P = (int)P; d.N = N; d.E2 = E2; d.n_leaves = nl; d.n_supers = ns; d.nblk = c->nblk;
+    d.P = (int)P; d.N = N; d.E2 = E2; d.n_leaves = nl; d.n_supers = ns; d.n_megas = nm; d.nblk = c->nblk;
     d.aa_m = c->prm.aa_m;
     d.robust = c->prm.robust;
     d.pcg_max = c->prm.pcg_max_iters;
@@ -836,7 +847,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     T *pv_, *pw_, *pp_, *er_;
     int *ip_, *in_, *ei_, *ej_, *ap_, *rv_, *bp_, *bc_, *be_, *ep_, *en_, *rho_;
     TPoint<T>* tp_;
-    float *lb_, *sb_;
+    float *lb_, *sb_, *mb_;
     CK(upload(c, &pv_, v)); d.v = pv_;
     CK(upload(c, &ip_, infl_ptr)); d.infl_ptr = ip_;
     CK(upload(c, &in_, infl_node)); d.infl_node = in_;
@@ -845,6 +856,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     CK(upload(c, &tp_, tp)); d.tpts = tp_;
     CK(upload(c, &lb_, lbox)); d.leaf_box = lb_;
     CK(upload(c, &sb_, sbox)); d.super_box = sb_;
+    CK(upload(c, &mb_, mbox)); d.mega_box = mb_;
     CK(upload(c, &ei_, e_i)); d.e_i = ei_;
     CK(upload(c, &ej_, e_j)); d.e_j = ej_;
     CK(upload(c, &er_, e_r)); d.e_r = er_;

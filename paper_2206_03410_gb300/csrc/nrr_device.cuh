@@ -46,7 +46,7 @@ struct __align__(16) TPoint {
 
 template <typename T>
 struct DevProblem {
-    int P, N, E2, n_leaves, n_supers, nblk;
+    int P, N, E2, n_leaves, n_supers, n_megas, nblk;
     int aa_m;
     int robust;         // nrr_robust: Welsch's function or an l2 variant
     int pcg_max;
@@ -61,6 +61,7 @@ struct DevProblem {
     const TPoint<T>* tpts;
     const float* leaf_box;
     const float* super_box;
+    const float* mega_box;   // boxes of 32 consecutive super tiles
     // iterates
     T* X;
     T* Xeval;
