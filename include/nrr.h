@@ -131,6 +131,18 @@ typedef struct {
     int    graph_on_gpu;       /* 1: nrr_create builds the deformation graph
                                   (Algorithm 1) on the GPU, the same graph
                                   as the host construction; default 0       */
+    const int32_t* src_faces;  /* NULL (default): the source is a point
+                                  cloud and D of Eq. (InfluenceNodes) is the
+                                  Euclidean distance. Else the source is a
+                                  triangle mesh with these n_src_faces faces
+                                  [n][3] (vertex indices into src_xyz, host
+                                  or device memory, read during nrr_create):
+                                  Algorithm 1 uses exact geodesic distances
+                                  on the sub-mesh of each node's ball, and
+                                  l-bar is the mean mesh edge length (see
+                                  nrr_graph_build_mesh); graph_on_gpu must
+                                  then be 0                                 */
+    int64_t n_src_faces;
 } nrr_params;
 
 /* State after a pass (one execution of the repeat body of Algorithm 2). */
@@ -366,11 +378,11 @@ nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, dou
                            int max_influence);
 /* The same graph built on the GPU (Algorithm 1, Sec. 3.1, Euclidean
  * reading): PCA by reductions and a 3x3 Jacobi eigen-solve, the visiting
- * order by a radix sort of the projections, the greedy sampling as the
- * lexicographically first maximal independent set of the radius graph in
- * that order (rounds over a window that follows the sweep; each decision
- * depends only on earlier final ones, so the result is the sequential
- * one), then the influence sets, weights, edges and r_ij; every distance
+ * order by a radix sort of the projections, the greedy sampling node by
+ * node in that order in one CTA (its threads share the scan for the next
+ * uncovered point and the covering of each new node's ball, found through
+ * a uniform grid of cells of size R: the sequential decisions exactly),
+ * then the influence sets, weights, edges and r_ij; every distance
  * and projection in double without fused multiply-adds. src_xyz [P][3]
  * float32, host or device; cuda_stream the stream to use (NULL: the legacy
  * default stream); l-bar (and the default radius 5 l-bar) on the host.
@@ -378,6 +390,26 @@ nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, dou
  * nrr_graph_sizes/get/destroy. */
 nrr_status nrr_graph_build_gpu(nrr_graph** out, const float* src_xyz, int64_t P, double radius, int max_influence,
                                void* cuda_stream);
+/* The deformation graph of a triangle-mesh source (Sec. 3.1, Algorithm 1
+ * with the geodesic distance D of Eq. InfluenceNodes). Points are visited in
+ * the PCA order of the point-cloud construction; a point with no influencing
+ * node becomes a node v, its ball B(v) is found by a breadth-first search
+ * along mesh edges through the vertices q with |v - q| < R, and D(v, q) is
+ * the exact geodesic distance on the sub-mesh of the faces incident to
+ * B(v) (window propagation: straight paths across unfolded faces that bend
+ * only at vertices of total angle >= 2 pi or on a boundary; the paper uses
+ * the VTP algorithm for the same distances); v influences q when D < R, with
+ * the weight of Eq. (weight_data) from D. Influence caps, edges and r_ij as
+ * nrr_graph_build. src_xyz [P][3] host float32; faces [n_faces][3] host
+ * int32 vertex indices (every edge in at most two faces); radius R (> 0;
+ * <= 0: 5 l-bar with l-bar the mean mesh edge length, Sec. 4.1);
+ * max_influence 1..8 (<= 0: 8). lbar of nrr_graph_get is the mean edge
+ * length. Errors: NRR_E_INVALID (NULL pointer, P < 1, n_faces < 1,
+ * non-finite coordinate or radius, max_influence > 8, an index out of
+ * range, a face that repeats a vertex or has a zero-length edge, an edge
+ * of three or more faces), NRR_E_OOM. Host only; no GPU is used. */
+nrr_status nrr_graph_build_mesh(nrr_graph** out, const float* src_xyz, int64_t P, const int32_t* faces,
+                                int64_t n_faces, double radius, int max_influence);
 nrr_status nrr_graph_sizes(const nrr_graph* g, int64_t* N, int64_t* n_edges, int32_t* max_influence,
                            double* radius);
 nrr_status nrr_graph_get(const nrr_graph* g, int32_t* node_src, int32_t* nidx, double* w,

@@ -15,6 +15,9 @@ arithmetic).
 Modules:
   graph      Sec. 3.1 and Algorithm 1 (Euclidean reading), the edge-length
              normalisation r_ij of Sec. 3.2, mean spacing l-bar.
+  geodesic   exact geodesic distances on triangle meshes and Algorithm 1 for
+             a mesh source (geodesic D, ball by breadth-first search,
+             sub-mesh per node), l-bar as the mean mesh edge length.
   model      Eq. (deformed_position), closest points, Welsch function,
              regularisation residual D_ij, rotation projection, energy Eq. (2).
   surrogate  Sec. 3.3.2 matrix form (W_a, F, Q, W_r, H, Y, J, Z) and the
@@ -29,4 +32,4 @@ Modules:
 Parity pins: every function is pinned by the tests in tests/test_oracle_*.py
 against closed forms, invariants, brute force and library routines.
 """
-from . import graph, model, surrogate, anderson, solver, unrolled, lbfgs  # noqa: F401
+from . import graph, geodesic, model, surrogate, anderson, solver, unrolled, lbfgs  # noqa: F401

@@ -55,7 +55,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import graph as graph_mod
-from . import model, surrogate
+from . import geodesic, model, surrogate
 from .anderson import Anderson
 
 
@@ -95,14 +95,22 @@ class PassRecord:
 
 
 class Registration:
-    def __init__(self, src, tgt, params: Params | None = None, graph=None):
+    def __init__(self, src, tgt, params: Params | None = None, graph=None, faces=None):
+        """``faces`` [F,3]: the source is a triangle mesh; the graph then uses
+        geodesic distances and l-bar is the mean mesh edge length
+        (``oracle.geodesic``)."""
         self.V = np.asarray(src, dtype=np.float64)
         self.U = np.asarray(tgt, dtype=np.float64)
         self.p = params or Params()
         need_lbar = (self.p.radius <= 0 or self.p.nu_r <= 0
                      or self.p.nu_a_min <= 0)
-        self.lbar = graph_mod.mean_spacing(self.V) if need_lbar else float("nan")
+        if faces is not None:
+            self.lbar = geodesic.mean_edge_length(self.V, faces)
+        else:
+            self.lbar = graph_mod.mean_spacing(self.V) if need_lbar else float("nan")
         R = self.p.radius if self.p.radius > 0 else 5.0 * self.lbar
+        if graph is None and faces is not None:
+            graph = geodesic.build_graph_mesh(self.V, faces, R, self.p.max_influence)
         self.graph = graph if graph is not None else graph_mod.build_graph(
             self.V, R, self.p.max_influence)
         both = np.concatenate([self.V, self.U])

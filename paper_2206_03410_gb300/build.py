@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libnrr.so")
 
 CU_SOURCES = ["kernels_nn.cu", "kernels_system.cu", "kernels_solve.cu", "kernels_aa.cu", "kernels_unroll.cu", "kernels_lbfgs.cu",
               "graph_gpu.cu", "nrr_api.cu", "noalloc.cu"]
-CPP_SOURCES = ["graph_build.cpp"]
+CPP_SOURCES = ["graph_build.cpp", "geodesic.cpp"]
 HEADERS = ["nrr_internal.h", "nrr_device.cuh", "nrr_rotation.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -327,10 +327,7 @@ double nrr_mean_spacing(const double* V, int64_t P, int k) {
     return total / ((double)P * kk);
 }
 
-void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) {
-    g.radius = R;
-    g.K = K;
-    const double R2 = R * R;
+std::vector<int> nrr_pca_order(const double* V, int64_t P) {
     // PCA axis of the largest covariance eigenvalue
     double mu[3] = {0, 0, 0};
     for (int64_t i = 0; i < P; ++i)
@@ -361,15 +358,19 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
     parallel_sort(pk);
     std::vector<int> order((size_t)P);
     for (int64_t i = 0; i < P; ++i) order[(size_t)i] = pk[(size_t)i].second;
+    return order;
+}
 
+void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) {
+    const double R2 = R * R;
+    const std::vector<int> order = nrr_pca_order(V, P);
     // Greedy radius sampling: a point becomes a node if it has no influencing
     // node yet; the new node influences every point strictly within R.
     Grid grid;
     grid.build(V, P, R);
-    // (point, squared distance, node) of every influence, appended in node
+    // (point, node, squared distance) of every influence, appended in node
     // order; a point is covered once some node influences it
-    struct Infl { int pt; int node; double d2; };
-    std::vector<Infl> trip;
+    std::vector<NrrInfl> trip;
     trip.reserve((size_t)P * 4);
     std::vector<unsigned char> covered((size_t)P, 0);
     g.nodes.clear();
@@ -391,6 +392,14 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
                         }
                     });
     }
+    nrr_finish_graph(V, P, R, K, trip, g);
+}
+
+void nrr_finish_graph(const double* V, int64_t P, double R, int K, const std::vector<NrrInfl>& trip,
+                      HostGraph& g) {
+    g.radius = R;
+    g.K = K;
+    const double R2 = R * R;
     // grouped by point (counting sort, node order kept within a point): per
     // chunk of the triples a histogram over the points, then every chunk
     // scatters its triples after those of the earlier chunks
@@ -421,7 +430,7 @@ void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g) 
         parallel_chunks_idx(nT, nc, [&](int64_t t, int64_t a, int64_t b) {
             std::vector<int>& h = cnt[(size_t)t];
             for (int64_t e = a; e < b; ++e) {
-                const Infl& x = trip[(size_t)e];
+                const NrrInfl& x = trip[(size_t)e];
                 iv[(size_t)(iptr[(size_t)x.pt] + h[(size_t)x.pt]++)] = {x.d2, x.node};
             }
         });

@@ -600,6 +600,24 @@ nrr_status graph_on_device(const float* src, const std::vector<double>& V, int64
     return NRR_OK;
 }
 
+// Algorithm 1 on a triangle-mesh source (faces already on the host): l-bar
+// is the mean mesh edge length, the radius 5 l-bar unless given.
+nrr_status graph_from_mesh(const std::vector<double>& V, int64_t P, const std::vector<int>& F, double radius,
+                           int K, HostGraph& g, const char* who) {
+    const int64_t nF = (int64_t)(F.size() / 3);
+    for (int x : F)
+        if (x < 0 || x >= P) return nrr_set_global_error(NRR_E_INVALID, (std::string(who) + ": face index out of range").c_str());
+    const double lbar = nrr_mesh_mean_edge(V.data(), F.data(), nF);
+    const double R = radius > 0 ? radius : 5.0 * lbar;
+    if (!(R > 0) || !std::isfinite(R))
+        return nrr_set_global_error(NRR_E_INVALID, (std::string(who) + ": radius 5 l-bar is not positive").c_str());
+    std::string err;
+    if (!nrr_build_graph_mesh(V.data(), P, F.data(), nF, R, K, g, err))
+        return nrr_set_global_error(NRR_E_INVALID, (std::string(who) + ": " + err).c_str());
+    g.lbar = lbar;
+    return NRR_OK;
+}
+
 // Hilbert orders of source and target over their common bounding box; they
 // depend on the inputs only, so nrr_create computes them on a second host
 // thread while it builds the deformation graph.
@@ -1578,6 +1596,10 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         return fail(nullptr, NRR_E_INVALID, "precision must be NRR_FP64 or NRR_MIXED");
     if (prm.max_iters_per_stage < 1 || prm.pcg_max_iters < 1 || prm.max_total_passes < 1)
         return fail(nullptr, NRR_E_INVALID, "iteration caps must be >= 1");
+    if (prm.src_faces && (prm.n_src_faces < 1 || prm.n_src_faces > (1LL << 28)))
+        return fail(nullptr, NRR_E_INVALID, "n_src_faces must be in 1..2^28 when src_faces is given");
+    if (prm.src_faces && prm.graph_on_gpu)
+        return fail(nullptr, NRR_E_INVALID, "graph_on_gpu is not available for a mesh source (src_faces)");
     if (prm.solve_ctas < -1 || prm.solve_ctas > 16)
         return fail(nullptr, NRR_E_INVALID, "solve_ctas must be in -1..16");
     if (prm.robust < NRR_WELSCH || prm.robust > NRR_L2_TRUNCATED)
@@ -1633,7 +1655,13 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     // l-bar, radius and the deformation graph (Algorithm 1)
     std::vector<double> V(src.begin(), src.end());
     const bool need_lbar = prm.graph_radius <= 0 || prm.nu_r <= 0 || prm.nu_a_min <= 0;
-    if (prm.graph_on_gpu) {
+    if (prm.src_faces) {
+        std::vector<int> F((size_t)prm.n_src_faces * 3);
+        CK(cudaMemcpyAsync(F.data(), prm.src_faces, sizeof(int) * F.size(), cudaMemcpyDefault, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const nrr_status gs = graph_from_mesh(V, P, F, prm.graph_radius, prm.max_influence, c->hg, "nrr_create");
+        if (gs != NRR_OK) return gs;
+    } else if (prm.graph_on_gpu) {
         const nrr_status gs = graph_on_device(src.data(), V, P, prm.graph_radius, prm.max_influence, need_lbar,
                                               c->stream, c->hg);
         if (gs != NRR_OK) return gs;
@@ -1990,6 +2018,33 @@ nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, dou
         return NRR_OK;
     } catch (const std::bad_alloc&) {
         return nrr_set_global_error(NRR_E_OOM, "nrr_graph_build: out of host memory");
+    }
+}
+
+nrr_status nrr_graph_build_mesh(nrr_graph** out, const float* src_xyz, int64_t P, const int32_t* faces,
+                                int64_t n_faces, double radius, int max_influence) {
+    if (!out || !src_xyz || !faces) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_mesh: NULL argument");
+    *out = nullptr;
+    if (P < 1 || P >= (1LL << 31)) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_mesh: P must be in 1..2^31-1");
+    if (n_faces < 1 || n_faces > (1LL << 28))
+        return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_mesh: n_faces must be in 1..2^28");
+    if (!std::isfinite(radius)) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_mesh: radius not finite");
+    const int K = max_influence <= 0 ? 8 : max_influence;
+    if (K > 8) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_mesh: max_influence > 8");
+    try {
+        std::vector<double> V((size_t)P * 3);
+        for (size_t k = 0; k < V.size(); ++k) {
+            V[k] = (double)src_xyz[k];
+            if (!std::isfinite(V[k])) return nrr_set_global_error(NRR_E_INVALID, "nrr_graph_build_mesh: non-finite point");
+        }
+        std::vector<int> F(faces, faces + 3 * n_faces);
+        std::unique_ptr<nrr_graph> g(new nrr_graph);
+        const nrr_status gs = graph_from_mesh(V, P, F, radius, K, g->g, "nrr_graph_build_mesh");
+        if (gs != NRR_OK) return gs;
+        *out = g.release();
+        return NRR_OK;
+    } catch (const std::bad_alloc&) {
+        return nrr_set_global_error(NRR_E_OOM, "nrr_graph_build_mesh: out of host memory");
     }
 }
 

@@ -69,6 +69,29 @@ struct HostGraph {
 void nrr_parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f);
 double nrr_mean_spacing(const double* V, int64_t P, int k);
 void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g);
+// Pieces of Algorithm 1 shared by the point-cloud and mesh constructions:
+// the visiting order (ascending projection on the PCA axis of the largest
+// covariance eigenvalue, ties to the lower index), and the influence sets
+// (the K nearest nodes of each point, ties to the lower node id), weights of
+// Eq. (weight_data), edges and r_ij from the (point, node, D^2) influences
+// of the greedy pass, appended in node order; g.nodes must hold the nodes.
+struct NrrInfl {
+    int pt;
+    int node;
+    double d2;
+};
+std::vector<int> nrr_pca_order(const double* V, int64_t P);
+void nrr_finish_graph(const double* V, int64_t P, double R, int K, const std::vector<NrrInfl>& trip,
+                      HostGraph& g);
+// geodesic.cpp: Algorithm 1 on a triangle-mesh source (faces F [nF][3]
+// vertex indices): the ball B(v) by breadth-first search along mesh edges,
+// exact geodesic distances on its sub-mesh, influence where D < R. Returns
+// false with a message for a non-manifold edge (three or more faces), a bad
+// index or a degenerate face.
+bool nrr_build_graph_mesh(const double* V, int64_t P, const int* F, int64_t nF, double R, int K, HostGraph& g,
+                          std::string& err);
+// l-bar of a mesh: the mean length of its (undirected) edges.
+double nrr_mesh_mean_edge(const double* V, const int* F, int64_t nF);
 // Algorithm 1 with radius R (> 0), or with 5 l-bar (radius <= 0), and l-bar
 // (the mean 6-NN spacing) into g.lbar if need_lbar or radius <= 0 (else
 // NaN); with a given radius the two run concurrently. Returns false (and

@@ -58,6 +58,8 @@ class NrrParams(ctypes.Structure):
         ("robust", ctypes.c_int),
         ("nu_schedule", ctypes.c_int),
         ("graph_on_gpu", ctypes.c_int),
+        ("src_faces", ctypes.c_void_p),
+        ("n_src_faces", ctypes.c_int64),
     ]
 
 
@@ -144,6 +146,8 @@ _SIGS = [
     ("nrr_get_graph", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("nrr_graph_build", ctypes.c_int, [ctypes.POINTER(_VP), _VP, _I64, ctypes.c_double, ctypes.c_int]),
     ("nrr_graph_build_gpu", ctypes.c_int, [ctypes.POINTER(_VP), _VP, _I64, ctypes.c_double, ctypes.c_int, _VP]),
+    ("nrr_graph_build_mesh", ctypes.c_int, [ctypes.POINTER(_VP), _VP, _I64, _VP, _I64, ctypes.c_double,
+                                             ctypes.c_int]),
     ("nrr_graph_sizes", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     ("nrr_graph_get", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("nrr_graph_destroy", None, [_VP]),
@@ -482,16 +486,34 @@ def nrr_get_graph(ctx) -> GraphView:
     return GraphView(nodes, nidx, w, edges, r, lbar.value)
 
 
+def _faces_array(faces) -> np.ndarray:
+    F = np.ascontiguousarray(np.asarray(faces, dtype=np.int32))
+    if F.ndim != 2 or F.shape[1] != 3 or F.shape[0] < 1:
+        raise ValueError("faces must be [n_faces, 3] with n_faces >= 1")
+    return F
+
+
 def build_graph(src, radius: float = 0.0, max_influence: int = 0, on_gpu: bool = False,
-                stream=None) -> GraphView:
+                stream=None, faces=None) -> GraphView:
     """The deformation graph of the source points src [P,3] (Algorithm 1,
     Sec. 3.1-3.2): the graph nrr_create would build with the same radius
     (<= 0: 5 lbar) and influence cap (<= 0: 8), built by the library on the
     host (nrr_graph_build, no GPU needed) or on the GPU
-    (nrr_graph_build_gpu)."""
+    (nrr_graph_build_gpu); with ``faces`` [n,3] the source is a triangle
+    mesh and D is the exact geodesic distance (nrr_graph_build_mesh, host)."""
     lib = load()
     g = _VP()
-    if on_gpu and hasattr(src, "data_ptr"):
+    if faces is not None:
+        if on_gpu:
+            raise ValueError("a mesh graph is built on the host (on_gpu must be False)")
+        v = np.ascontiguousarray(np.asarray(src, dtype=np.float32))
+        if v.ndim != 2 or v.shape[1] != 3:
+            raise ValueError("src must be [P, 3]")
+        P = int(v.shape[0])
+        F = _faces_array(faces)
+        _check(lib.nrr_graph_build_mesh(ctypes.byref(g), _ptr(v), P, _ptr(F), int(F.shape[0]), float(radius),
+                                        int(max_influence)))
+    elif on_gpu and hasattr(src, "data_ptr"):
         v = src.contiguous()
         P = int(v.shape[0])
         _check(lib.nrr_graph_build_gpu(ctypes.byref(g), _ptr(v), P, float(radius), int(max_influence), stream))
@@ -560,9 +582,15 @@ class Registration:
     >>> X = reg.transforms()
     """
 
-    def __init__(self, src, tgt, src_nrm=None, tgt_nrm=None, stream=None, **params):
+    def __init__(self, src, tgt, src_nrm=None, tgt_nrm=None, stream=None, faces=None, **params):
         self._p = make_params(**params)
-        self._keep = (src, tgt, src_nrm, tgt_nrm)
+        F = None
+        if faces is not None:
+            # a triangle-mesh source: geodesic influence (host int32 faces)
+            F = _faces_array(faces)
+            self._p.src_faces = F.ctypes.data
+            self._p.n_src_faces = int(F.shape[0])
+        self._keep = (src, tgt, src_nrm, tgt_nrm, F)
         self.ctx = nrr_create(src, tgt, self._p, src_nrm, tgt_nrm, stream)
         self.P, self.T, self.N, self.n_edges, self.K = nrr_get_sizes(self.ctx)
 

@@ -47,6 +47,7 @@ class Pair:
     gt: np.ndarray                       # [P,3] float32, true match of src
     params: dict = field(default_factory=dict)
     name: str = ""
+    faces: np.ndarray | None = None      # [F,3] int32 when the source is a mesh
 
     @property
     def P(self) -> int:
@@ -145,6 +146,155 @@ def _bbox_diag(*arrs) -> float:
 
 def _f32(*arrs):
     return tuple(np.ascontiguousarray(a, dtype=np.float32) for a in arrs)
+
+
+def icosphere(subdiv: int):
+    """Unit icosphere: the icosahedron with every face split into four,
+    ``subdiv`` times, vertices pushed onto the sphere. Returns (V [n,3]
+    float64, F [m,3] int64); consistent outward orientation."""
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    V = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
+         (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    V = [np.array(v, dtype=np.float64) / math.sqrt(1 + t * t) for v in V]
+    F = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+         (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+         (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(subdiv):
+        mid = {}
+
+        def midpoint(a, b):
+            k = (min(a, b), max(a, b))
+            if k not in mid:
+                m = V[a] + V[b]
+                V.append(m / np.linalg.norm(m))
+                mid[k] = len(V) - 1
+            return mid[k]
+
+        nf = []
+        for a, b, c in F:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        F = nf
+    return np.array(V), np.array(F, dtype=np.int64)
+
+
+def bumpy_sphere_mesh(subdiv: int, n_bumps: int, amp: float, width: float,
+                      rng: np.random.Generator, bumps=None):
+    """The bumped sphere of ``bumpy_sphere`` as a triangle mesh: the
+    icosphere's vertices moved radially. Returns (xyz, normals, faces,
+    bumps)."""
+    n, F = icosphere(subdiv)
+    if bumps is None:
+        c = _unit_sphere(n_bumps, rng)
+        a = amp * np.where(rng.random(n_bumps) < 0.5, -1.0, 1.0)
+        bumps = (c, a)
+    c, a = bumps
+    diff = n[:, None, :] - c[None, :, :]
+    g = np.exp(-np.sum(diff * diff, axis=2) / (2.0 * width * width))
+    r = 1.0 + g @ a
+    grad = -np.einsum("nk,nkd->nd", g * a[None, :], diff) / (width * width)
+    grad -= np.sum(grad * n, axis=1, keepdims=True) * n
+    normal = r[:, None] * n - grad
+    normal /= np.linalg.norm(normal, axis=1, keepdims=True)
+    return r[:, None] * n, normal, F, bumps
+
+
+def grid_mesh(nx: int, ny: int, h: float = 1.0, keep=None):
+    """Flat triangulated grid of nx x ny vertices (spacing h, z = 0), each
+    cell split along alternating diagonals; ``keep(i, j)`` selects cells (an
+    L-shaped or holed domain). Returns (V [n,3] float64, F [m,3] int64,
+    index dict (i, j) -> vertex); vertices of dropped cells stay unused."""
+    V, idx = [], {}
+    for j in range(ny):
+        for i in range(nx):
+            idx[(i, j)] = len(V)
+            V.append((i * h, j * h, 0.0))
+    F = []
+    for j in range(ny - 1):
+        for i in range(nx - 1):
+            if keep is not None and not keep(i, j):
+                continue
+            a, b, c, d = idx[(i, j)], idx[(i + 1, j)], idx[(i + 1, j + 1)], idx[(i, j + 1)]
+            F += [(a, b, c), (a, c, d)] if (i + j) % 2 == 0 else [(a, b, d), (b, c, d)]
+    return np.array(V, dtype=np.float64), np.array(F, dtype=np.int64), idx
+
+
+def cylinder_mesh(n: int, rings: int, radius: float, dz: float):
+    """Open triangulated cylinder: ``rings`` rings of n vertices around the
+    z axis, ring spacing dz. Vertex (ring j, k) has index j * n + k."""
+    V = [(radius * math.cos(2 * math.pi * k / n), radius * math.sin(2 * math.pi * k / n), j * dz)
+         for j in range(rings) for k in range(n)]
+    F = []
+    for j in range(rings - 1):
+        for k in range(n):
+            a, b = j * n + k, j * n + (k + 1) % n
+            c, d = (j + 1) * n + (k + 1) % n, (j + 1) * n + k
+            F += [(a, b, c), (a, c, d)]
+    return np.array(V, dtype=np.float64), np.array(F, dtype=np.int64)
+
+
+def cube_mesh(nd: int):
+    """Surface of the unit cube [0, 1]^3, each face an nd x nd grid of
+    squares split into two triangles. Returns (V, F)."""
+    key, V, F = {}, [], []
+
+    def vid(p):
+        k = tuple(int(round(x * nd)) for x in p)
+        if k not in key:
+            key[k] = len(V)
+            V.append(p)
+        return key[k]
+
+    for axis in range(3):
+        for side in (0.0, 1.0):
+            for a in range(nd):
+                for b in range(nd):
+                    def at(u, v):
+                        p = [0.0, 0.0, 0.0]
+                        p[axis], p[(axis + 1) % 3], p[(axis + 2) % 3] = side, u / nd, v / nd
+                        return tuple(p)
+                    q = [vid(at(a, b)), vid(at(a + 1, b)), vid(at(a + 1, b + 1)), vid(at(a, b + 1))]
+                    F += [(q[0], q[1], q[2]), (q[0], q[2], q[3])]
+    return np.array(V, dtype=np.float64), np.array(F, dtype=np.int64)
+
+
+def crown_mesh(n: int, apex_angle_deg: float):
+    """A fan of n triangles around an apex (vertex 0) with ring vertices
+    1..n at distance 1 from it and apex angle ``apex_angle_deg`` per
+    triangle, the ring zig-zagging in z so that the angles fit in 3-D (n
+    even). With n * angle > 360 degrees the apex is a saddle vertex."""
+    alpha = math.radians(apex_angle_deg)
+    rho = math.cos(alpha / 2) / math.cos(math.pi / n)
+    h = math.sqrt(max(1.0 - rho * rho, 0.0))
+    V = [(0.0, 0.0, 0.0)] + [(rho * math.cos(2 * math.pi * i / n), rho * math.sin(2 * math.pi * i / n),
+                              h if i % 2 else -h) for i in range(n)]
+    F = [(0, 1 + i, 1 + (i + 1) % n) for i in range(n)]
+    return np.array(V, dtype=np.float64), np.array(F, dtype=np.int64)
+
+
+def mesh_pair(subdiv: int, T: int, n_bumps: int, amp: float, width: float, warp_cap: float,
+              noise: float, outliers: float, crop: float, seed: int) -> Pair:
+    """A triangle-mesh source (the bumped icosphere) and a target sampled
+    independently from the same surface, warped, with noise, outliers and a
+    crop as ``sphere_pair``; ``faces`` holds the source triangles."""
+    rng = np.random.default_rng(seed)
+    src, src_n, F, bumps = bumpy_sphere_mesh(subdiv, n_bumps, amp, width, rng)
+    base, base_n, _ = bumpy_sphere(T, n_bumps, amp, width, rng, bumps)
+    lo, hi = src.min(axis=0), src.max(axis=0)
+    _, phi = smooth_warp(base, 1.0, rng, lo, hi, return_field=True)
+    both = np.concatenate([src, base])
+    disp = phi(both) - both
+    s = warp_cap / float(np.linalg.norm(disp, axis=1).max())
+    warp = lambda p: p + s * (phi(p) - p)
+    tgt, tgt_n, gt = warp(base), base_n, warp(src)
+    diag = _bbox_diag(src, tgt)
+    keep = crop_halfspace(tgt, crop, rng)
+    tgt, tgt_n = tgt[keep], tgt_n[keep]
+    tgt = add_noise(tgt, noise, diag, rng) if noise > 0 else tgt
+    if outliers > 0:
+        tgt, tgt_n = add_outliers(tgt, tgt_n, outliers, rng)
+    src, src_n, tgt, tgt_n, gt = _f32(src, src_n, tgt, tgt_n, gt)
+    return Pair(src, src_n, tgt, tgt_n, gt, faces=F.astype(np.int32))
 
 
 def sphere_pair(P: int, T: int | None, n_bumps: int, amp: float, width: float,

@@ -69,3 +69,76 @@ def test_host_graph_default_radius_needs_spread_points():
     assert e.value.code == nrr.NRR_E_INVALID
     g = nrr.build_graph(pts, radius=0.1)      # an explicit radius works
     assert len(g.nodes) == 1 and g.lbar == 0.0
+
+
+# ---- triangle-mesh source: geodesic D (nrr_graph_build_mesh) ----------------
+
+def _mesh_cases():
+    rng = np.random.default_rng(3)
+    V3, _, F3, _ = synth.bumpy_sphere_mesh(3, 6, 0.15, 0.4, rng)
+    V2, _, F2, _ = synth.bumpy_sphere_mesh(2, 4, 0.2, 0.5, rng)
+    Vg, Fg, idx = synth.grid_mesh(14, 12, h=0.1, keep=lambda i, j: not (4 <= i < 8 and 3 <= j < 7))
+    rg = np.random.default_rng(4)
+    for v in range(len(Vg)):
+        Vg[v] += rg.uniform(-0.01, 0.01, 3) * np.array([1.0, 1.0, 2.0])
+    # symmetric meshes are jittered: a tie in the PCA axis or in the
+    # projections would make the visiting order depend on rounding
+    Vc, Fc = synth.cylinder_mesh(16, 6, 0.5, 0.2)
+    Vk, Fk = synth.crown_mesh(8, 50.0)
+    Vq, Fq = synth.cube_mesh(3)
+    for Vx in (Vc, Vk, Vq):
+        Vx += rg.uniform(-2e-3, 2e-3, Vx.shape)
+    return {
+        "icosphere3_5lbar": (V3, F3, 0.0, 8),
+        "icosphere3_3lbar": (V3, F3, 3.0, 8),
+        "icosphere2_K4": (V2, F2, 0.5, 4),
+        "holed_grid": (Vg, Fg, 0.33, 8),        # boundary around a hole: paths bend there
+        "cylinder": (Vc, Fc, 0.55, 8),
+        "saddle_crown": (Vk, Fk, 1.3, 8),
+        "cube": (Vq, Fq, 0.9, 8),
+    }
+
+
+@pytest.mark.parametrize("name", list(_mesh_cases().keys()))
+def test_host_mesh_graph_matches_oracle(name):
+    from oracle import geodesic as GD
+    V, F, R, K = _mesh_cases()[name]
+    V32 = V.astype(np.float32)
+    V64 = V32.astype(np.float64)
+    lbar = GD.mean_edge_length(V64, F)
+    if name == "icosphere3_3lbar":
+        R = 3.0 * lbar
+    g = nrr.build_graph(V32, radius=R, max_influence=K, faces=F)
+    assert abs(g.lbar - lbar) < 1e-13 * lbar
+    og = GD.build_graph_mesh(V64, F, R if R > 0 else 5.0 * lbar, K)
+    assert np.array_equal(g.nodes, og.nodes)
+    assert np.array_equal(g.nidx, og.nidx)
+    assert np.array_equal(g.edges, og.edges)
+    assert relmax(g.w, og.w) < 1e-12
+    assert relmax(g.r, og.r) < 1e-12
+
+
+def test_host_mesh_graph_rejects_bad_meshes():
+    V, F, _ = synth.grid_mesh(4, 4)
+    V32 = V.astype(np.float32)
+    bad = {
+        "index out of range": np.vstack([F, [[0, 1, 99]]]),
+        "repeated vertex": np.vstack([F, [[0, 0, 1]]]),
+        "non-manifold edge": np.vstack([F, [[0, 5, 15]]]),   # (0, 5) is the diagonal of cell (0, 0)
+    }
+    for why, Fb in bad.items():
+        with pytest.raises(nrr.NrrError) as e:
+            nrr.build_graph(V32, radius=1.5, faces=Fb)
+        assert e.value.code == nrr.NRR_E_INVALID, why
+    # a zero-length edge (two vertices at one position)
+    Vz = V32.copy()
+    Vz[1] = Vz[0]
+    with pytest.raises(nrr.NrrError):
+        nrr.build_graph(Vz, radius=1.5, faces=F)
+    lib = nrr.load()
+    g = nrr._VP()
+    assert lib.nrr_graph_build_mesh(None, nrr._ptr(V32), 16, nrr._ptr(F.astype(np.int32)), len(F), 1.0, 8) \
+        == nrr.NRR_E_INVALID
+    assert lib.nrr_graph_build_mesh(g, nrr._ptr(V32), 16, None, len(F), 1.0, 8) == nrr.NRR_E_INVALID
+    assert lib.nrr_graph_build_mesh(g, nrr._ptr(V32), 16, nrr._ptr(F.astype(np.int32)), 0, 1.0, 8) \
+        == nrr.NRR_E_INVALID
