@@ -241,7 +241,9 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
     }
     __syncthreads();
 
-    // initial residual with the warm start X^(k)
+    // initial residual with the warm start x = X^(k) (+ the previous MM
+    // step once the stage has solved: K x = K X^(k) + K dx)
+    const T* wdx = (d.warm_dx != nullptr && st->n_solves_stage > 0) ? d.warm_dx : nullptr;
     double acc[9];
     double sums[9];
 #pragma unroll
@@ -250,12 +252,17 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(DevProblem<T> d) {
         const int n = n0 + idx / 3, c = idx % 3;
         T y[4];
         spmv_pair<T, false>(d, d.X, n, c, y);
+        if (wdx) {
+            T y2[4];
+            spmv_pair<T, false>(d, wdx, n, c, y2);
+            for (int a = 0; a < 4; ++a) y[a] += y2[a];
+        }
         T rr[4];
         for (int a = 0; a < 4; ++a) {
             const T b = d.Bv[12 * n + 3 * a + c];
             rr[a] = b - y[a];
             d.r[12 * n + 3 * a + c] = rr[a];
-            d.G[12 * n + 3 * a + c] = d.X[12 * n + 3 * a + c];
+            d.G[12 * n + 3 * a + c] = d.X[12 * n + 3 * a + c] + (wdx ? wdx[12 * n + 3 * a + c] : T(0));
             acc[6 + c] += (double)b * (double)b;
         }
         const T* Mi = d.Minv + 16 * n;
@@ -723,7 +730,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         _Pragma("unroll") for (int a = 0; a < 4; ++a) w[a] = wv[3 * a + c];            \
     }
 
-    // start: r = B - K X^(k), u = M^-1 r, w = K u
+    // start: x = X^(k) (+ the previous MM step), r = B - K x, u = M^-1 r,
+    // w = K u
+    const T* wdx = (d.warm_dx != nullptr && d.st->n_solves_stage > 0) ? d.warm_dx : nullptr;
     T bb = 0;
     if (has) {
         T y[4] = {0, 0, 0, 0};
@@ -731,7 +740,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
             const int k = d.bsr_col[b0 + b];
             T v[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) v[t] = d.X[12 * k + 3 * t + c];
+            for (int t = 0; t < 4; ++t) v[t] = d.X[12 * k + 3 * t + c] + (wdx ? wdx[12 * k + 3 * t + c] : T(0));
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 T k4[4];
@@ -742,7 +751,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const T bv = d.Bv[12 * n + 3 * a + c];
-            x[a] = d.X[12 * n + 3 * a + c];
+            x[a] = d.X[12 * n + 3 * a + c] + (wdx ? wdx[12 * n + 3 * a + c] : T(0));
             r[a] = bv - y[a];
             bb += bv * bv;
         }

@@ -921,6 +921,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     CK(dalloc(c, &d.G, (size_t)N * 12));
     CK(upload(c, &d.Gprev, X0));
     CK(dalloc(c, &d.Fprev, (size_t)N * 12));
+    d.warm_dx = d.Fprev;
     const int mm = std::max(1, c->prm.aa_m);
     CK(dalloc(c, &d.dF, (size_t)mm * N * 12));
     CK(dalloc(c, &d.dG, (size_t)mm * N * 12));
@@ -1100,6 +1101,7 @@ nrr_status unroll_t(nrr_ctx* c, int K, const double* X0, double* XK) {
         if (st != NRR_OK) return st;
         DevProblem<T> ds = prob<T>(c);
         ds.X = ck + (size_t)k * n12;          // warm start X^(k)
+        ds.warm_dx = nullptr;
         ds.G = ck + (size_t)(k + 1) * n12;    // X^(k+1) = K^-1 B
         CK(launch_solve_on<T>(c, ds));
     }
@@ -1157,6 +1159,7 @@ nrr_status unroll_backward_t(nrr_ctx* c, const double* C, double* grad_X, double
         if (st != NRR_OK) return st;
         DevProblem<T> ds = d;
         ds.X = zero;     // warm start 0
+        ds.warm_dx = nullptr;
         ds.Bv = gt;      // K lambda = g_bar
         ds.G = lam;
         CK(launch_solve_on<T>(c, ds));
@@ -1290,6 +1293,7 @@ nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, int* best
     // solution goes to scratch, the pass state is not touched
     DevProblem<T> ds = d;
     ds.X = x0;
+    ds.warm_dx = nullptr;
     ds.G = x0 + n12;
     *solve_ms = INFINITY;
     const int keep_C = c->cl_C;

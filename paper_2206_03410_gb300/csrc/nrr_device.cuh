@@ -68,6 +68,10 @@ struct DevProblem {
     T* G;
     T* Gprev;
     T* Fprev;
+    // PCG warm start of a pass's solve: X^(k) + warm_dx once the stage has
+    // solved before (the previous MM step F^(k-1) = G^(k-1) - X^(k-1));
+    // NULL: X^(k) alone (solves outside a pass)
+    const T* warm_dx;
     T* dF;
     T* dG;
     // per point
