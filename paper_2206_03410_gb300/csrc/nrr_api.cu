@@ -655,6 +655,87 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     c->src_rank.assign((size_t)P, 0);
     for (int64_t ii = 0; ii < P; ++ii) c->src_rank[(size_t)c->src_order[(size_t)ii]] = (int)ii;
 
+    // the target's leaves, tiles and the initial correspondence guess depend
+    // on the curve orders only: built on another thread beside the
+    // graph-dependent structures below
+    struct Leaves {
+        int nl = 0, ns = 0, nm = 0;
+        std::vector<TPoint<T>> tp;
+        std::vector<float> lbox, sbox, mbox;
+        std::vector<T> u0;
+        std::vector<int> rho0;
+    } lv;
+    struct Joiner {
+        std::thread t;
+        ~Joiner() { if (t.joinable()) t.join(); }
+    } leaves_thread{std::thread([&]() {
+        // target leaves (32 curve-consecutive points) and super tiles
+        const int nl = (int)((Tn + NRR_LEAF - 1) / NRR_LEAF);
+        const int ns = (nl + 31) / 32;
+        lv.nl = nl;
+        lv.ns = ns;
+        std::vector<TPoint<T>>& tp = lv.tp;
+        tp.resize((size_t)nl * NRR_LEAF);
+        std::vector<float>& lbox = lv.lbox;
+        std::vector<float>& sbox = lv.sbox;
+        lbox.resize((size_t)nl * 6);
+        sbox.resize((size_t)ns * 6);
+        for (size_t k = 0; k < tp.size(); ++k) {
+            if ((int64_t)k < Tn) {
+                const int t = tgt_order[k];
+                tp[k].x = (T)tgt[3 * (size_t)t]; tp[k].y = (T)tgt[3 * (size_t)t + 1]; tp[k].z = (T)tgt[3 * (size_t)t + 2];
+                tp[k].idx = t;
+            } else {
+                tp[k].x = tp[k].y = tp[k].z = std::numeric_limits<T>::infinity();
+                tp[k].idx = 0x7fffffff;
+            }
+        }
+        for (int L = 0; L < nl; ++L) {
+            float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+            for (int k = L * NRR_LEAF; k < std::min<int64_t>(Tn, (int64_t)(L + 1) * NRR_LEAF); ++k) {
+                const int t = tgt_order[(size_t)k];
+                for (int a = 0; a < 3; ++a) {
+                    b[a] = std::min(b[a], tgt[3 * (size_t)t + a]);
+                    b[3 + a] = std::max(b[3 + a], tgt[3 * (size_t)t + a]);
+                }
+            }
+            std::memcpy(&lbox[(size_t)L * 6], b, sizeof(b));
+        }
+        for (int S = 0; S < ns; ++S) {
+            float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+            for (int L = S * 32; L < std::min(nl, (S + 1) * 32); ++L)
+                for (int a = 0; a < 3; ++a) {
+                    b[a] = std::min(b[a], lbox[(size_t)L * 6 + a]);
+                    b[3 + a] = std::max(b[3 + a], lbox[(size_t)L * 6 + 3 + a]);
+                }
+            std::memcpy(&sbox[(size_t)S * 6], b, sizeof(b));
+        }
+        const int nm = (ns + 31) / 32;
+        lv.nm = nm;
+        std::vector<float>& mbox = lv.mbox;
+        mbox.resize((size_t)nm * 6);
+        for (int M = 0; M < nm; ++M) {
+            float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+            for (int S = M * 32; S < std::min(ns, (M + 1) * 32); ++S)
+                for (int a = 0; a < 3; ++a) {
+                    b[a] = std::min(b[a], sbox[(size_t)S * 6 + a]);
+                    b[3 + a] = std::max(b[3 + a], sbox[(size_t)S * 6 + 3 + a]);
+                }
+            std::memcpy(&mbox[(size_t)M * 6], b, sizeof(b));
+        }
+        // initial correspondence guess: the target point next along the curve
+        std::vector<T>& u0 = lv.u0;
+        std::vector<int>& rho0 = lv.rho0;
+        u0.resize((size_t)(3 * P));
+        rho0.resize((size_t)P);
+        for (int64_t ii = 0; ii < P; ++ii) {
+            size_t pos = (size_t)(std::lower_bound(tgt_codes.begin(), tgt_codes.end(), src_codes[(size_t)ii]) - tgt_codes.begin());
+            if (pos >= (size_t)Tn) pos = (size_t)Tn - 1;
+            for (int a = 0; a < 3; ++a) u0[(size_t)(a * P + ii)] = a == 0 ? tp[pos].x : (a == 1 ? tp[pos].y : tp[pos].z);
+            rho0[(size_t)ii] = tp[pos].idx;
+        }
+    })};
+
     // source SoA and influence CSR in internal order
     std::vector<T> v((size_t)(3 * P));
     std::vector<int> infl_ptr((size_t)P + 1, 0), infl_node;
@@ -795,63 +876,16 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         }
         for (int a = 0; a < 3; ++a) pbar[(size_t)(a * P + ii)] = (T)acc[a];
     }
-    // target leaves (32 curve-consecutive points) and super tiles
-    const int nl = (int)((Tn + NRR_LEAF - 1) / NRR_LEAF);
-    const int ns = (nl + 31) / 32;
+    leaves_thread.t.join();
+    const int nl = lv.nl, ns = lv.ns, nm = lv.nm;
     c->n_leaves = nl;
     c->n_supers = ns;
-    std::vector<TPoint<T>> tp((size_t)nl * NRR_LEAF);
-    std::vector<float> lbox((size_t)nl * 6), sbox((size_t)ns * 6);
-    for (size_t k = 0; k < tp.size(); ++k) {
-        if ((int64_t)k < Tn) {
-            const int t = tgt_order[k];
-            tp[k].x = (T)tgt[3 * (size_t)t]; tp[k].y = (T)tgt[3 * (size_t)t + 1]; tp[k].z = (T)tgt[3 * (size_t)t + 2];
-            tp[k].idx = t;
-        } else {
-            tp[k].x = tp[k].y = tp[k].z = std::numeric_limits<T>::infinity();
-            tp[k].idx = 0x7fffffff;
-        }
-    }
-    for (int L = 0; L < nl; ++L) {
-        float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-        for (int k = L * NRR_LEAF; k < std::min<int64_t>(Tn, (int64_t)(L + 1) * NRR_LEAF); ++k) {
-            const int t = tgt_order[(size_t)k];
-            for (int a = 0; a < 3; ++a) {
-                b[a] = std::min(b[a], tgt[3 * (size_t)t + a]);
-                b[3 + a] = std::max(b[3 + a], tgt[3 * (size_t)t + a]);
-            }
-        }
-        std::memcpy(&lbox[(size_t)L * 6], b, sizeof(b));
-    }
-    for (int S = 0; S < ns; ++S) {
-        float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-        for (int L = S * 32; L < std::min(nl, (S + 1) * 32); ++L)
-            for (int a = 0; a < 3; ++a) {
-                b[a] = std::min(b[a], lbox[(size_t)L * 6 + a]);
-                b[3 + a] = std::max(b[3 + a], lbox[(size_t)L * 6 + 3 + a]);
-            }
-        std::memcpy(&sbox[(size_t)S * 6], b, sizeof(b));
-    }
-    const int nm = (ns + 31) / 32;
-    std::vector<float> mbox((size_t)nm * 6);
-    for (int M = 0; M < nm; ++M) {
-        float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-        for (int S = M * 32; S < std::min(ns, (M + 1) * 32); ++S)
-            for (int a = 0; a < 3; ++a) {
-                b[a] = std::min(b[a], sbox[(size_t)S * 6 + a]);
-                b[3 + a] = std::max(b[3 + a], sbox[(size_t)S * 6 + 3 + a]);
-            }
-        std::memcpy(&mbox[(size_t)M * 6], b, sizeof(b));
-    }
-    // initial correspondence guess: the target point next along the curve
-    std::vector<T> u0((size_t)(3 * P));
-    std::vector<int> rho0((size_t)P);
-    for (int64_t ii = 0; ii < P; ++ii) {
-        size_t pos = (size_t)(std::lower_bound(tgt_codes.begin(), tgt_codes.end(), src_codes[(size_t)ii]) - tgt_codes.begin());
-        if (pos >= (size_t)Tn) pos = (size_t)Tn - 1;
-        for (int a = 0; a < 3; ++a) u0[(size_t)(a * P + ii)] = a == 0 ? tp[pos].x : (a == 1 ? tp[pos].y : tp[pos].z);
-        rho0[(size_t)ii] = tp[pos].idx;
-    }
+    std::vector<TPoint<T>>& tp = lv.tp;
+    std::vector<float>& lbox = lv.lbox;
+    std::vector<float>& sbox = lv.sbox;
+    std::vector<float>& mbox = lv.mbox;
+    std::vector<T>& u0 = lv.u0;
+    std::vector<int>& rho0 = lv.rho0;
     // identity transforms
     std::vector<T> X0((size_t)N * 12, (T)0);
     for (int j = 0; j < N; ++j) { X0[(size_t)12 * j + 0] = 1; X0[(size_t)12 * j + 4] = 1; X0[(size_t)12 * j + 8] = 1; }
@@ -984,9 +1018,16 @@ nrr_status median_distance(nrr_ctx* c, double* out) {
     CK(cudaStreamSynchronize(c->stream));
     std::vector<double> dist((size_t)c->P);
     for (size_t i = 0; i < dist.size(); ++i) dist[i] = std::sqrt((double)d2[i]);
-    std::sort(dist.begin(), dist.end());
+    // the middle element(s) by selection, not a full sort
     const size_t n = dist.size();
-    *out = (n % 2) ? dist[n / 2] : (dist[n / 2 - 1] + dist[n / 2]) / 2.0;
+    std::nth_element(dist.begin(), dist.begin() + n / 2, dist.end());
+    const double hi = dist[n / 2];
+    if (n % 2) {
+        *out = hi;
+    } else {
+        const double lo = *std::max_element(dist.begin(), dist.begin() + n / 2);
+        *out = (lo + hi) / 2.0;
+    }
     return NRR_OK;
 }
 
