@@ -385,7 +385,9 @@ nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, dou
  * then the influence sets, weights, edges and r_ij; every distance
  * and projection in double without fused multiply-adds. src_xyz [P][3]
  * float32, host or device; cuda_stream the stream to use (NULL: the legacy
- * default stream); l-bar (and the default radius 5 l-bar) on the host.
+ * default stream); l-bar on the GPU on the graph's grid when the radius is
+ * given (on the host when it defaults to 5 l-bar, or when some point's six
+ * nearest others are not all within R).
  * Errors as nrr_graph_build, plus NRR_E_CUDA. The handle is used with
  * nrr_graph_sizes/get/destroy. */
 nrr_status nrr_graph_build_gpu(nrr_graph** out, const float* src_xyz, int64_t P, double radius, int max_influence,

@@ -243,6 +243,70 @@ __global__ void cell_start_kernel(const unsigned long long* __restrict__ keys, i
     }
 }
 
+// l-bar (the mean distance of every point to its kk = 6 nearest others) on
+// the grid of cell size h = R: per point the kk smallest squared distances
+// among the points of its 27 cells (ascending), certified when the kk-th is
+// at most h^2 (every point outside the 27 cells is at least h away); the
+// sum of their square roots in ascending order, as the host computes it.
+// Uncertified points are counted (the host then computes l-bar itself).
+__global__ void spacing_kernel(GridView g, const int* __restrict__ gitem, const double* __restrict__ V, int P, int kk,
+                               double* __restrict__ per_point, int* __restrict__ n_bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        const double x = V[3 * (int64_t)i], y = V[3 * (int64_t)i + 1], z = V[3 * (int64_t)i + 2];
+        double best[8];
+        for (int t = 0; t < 8; ++t) best[t] = INFINITY;
+        long long c[3];
+        g.cell(x, y, z, c);
+        for (long long a = c[0] - 1; a <= c[0] + 1; ++a) {
+            if (a < 0 || a >= g.dims[0]) continue;
+            for (long long b = c[1] - 1; b <= c[1] + 1; ++b) {
+                if (b < 0 || b >= g.dims[1]) continue;
+                for (long long d = c[2] - 1; d <= c[2] + 1; ++d) {
+                    if (d < 0 || d >= g.dims[2]) continue;
+                    int s0, s1;
+                    g.range((unsigned long long)((a * g.dims[1] + b) * g.dims[2] + d), &s0, &s1);
+                    for (int s = s0; s < s1; ++s) {
+                        const double dx = __dsub_rn(x, g.xyz[3 * s]), dy = __dsub_rn(y, g.xyz[3 * s + 1]),
+                                     dz = __dsub_rn(z, g.xyz[3 * s + 2]);
+                        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                        if (d2 < best[kk - 1] && gitem[s] != i) {
+                            int pos = kk - 1;
+                            while (pos > 0 && best[pos - 1] > d2) { best[pos] = best[pos - 1]; --pos; }
+                            best[pos] = d2;
+                        }
+                    }
+                }
+            }
+        }
+        if (!(best[kk - 1] <= g.h * g.h)) atomicAdd(n_bad, 1);
+        double sp = 0.0;
+        for (int t = 0; t < kk; ++t) sp += sqrt(best[t]);
+        per_point[i] = sp;
+    }
+}
+
+// Fixed-order sum of x[0..n): per CTA a contiguous share reduced by a
+// shared-memory tree, then the CTAs' partials in order by one thread.
+__global__ void sum_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+    __shared__ double sh[kT];
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b = blockIdx.x * per, e = b + per < n ? b + per : n;
+    double acc = 0.0;
+    for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) acc += x[k];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+__global__ void finish_sum_kernel(const double* __restrict__ part, int n, double scale, double* __restrict__ out) {
+    double t = 0.0;
+    for (int k = 0; k < n; ++k) t += part[k];
+    *out = t * scale;
+}
+
 // The greedy sampling, node by node, in one CTA: the next rank (in visiting
 // order) that no node covers becomes a node, and every point strictly within
 // R of it is marked covered (state 0 open, 1 node, 2 covered); the scan goes
@@ -518,7 +582,7 @@ int blocks_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((
 // device. Fills g as nrr_build_graph does. Returns cudaSuccess or the first
 // CUDA error; *rounds receives the number of greedy rounds.
 cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, HostGraph& g, cudaStream_t st,
-                                int* rounds) {
+                                int* rounds, double* lbar) {
 #define GK(call)                                \
     do {                                        \
         cudaError_t e_ = (call);                \
@@ -581,12 +645,54 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     GK(s.get(&nnode, 1));
     GK(cudaMemsetAsync(state, 0, (size_t)P, st));
     GridView gv{ckey_s, gxyz, n, {hsc[3], hsc[4], hsc[5]}, h, {dims[0], dims[1], dims[2]}, cstart};
+    // l-bar on the same grid (cell R) when asked for; read back with the
+    // node count below
+    double* d_lbar = nullptr;
+    int* d_bad = nullptr;
+    const int kk = (int)std::min<int64_t>(6, P - 1);
+    // on a second stream: the greedy sampling below runs in one CTA and
+    // leaves the other SMs to it
+    struct SideStream {
+        cudaStream_t s = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
+        ~SideStream() {
+            if (s) cudaStreamDestroy(s);
+            if (fork) cudaEventDestroy(fork);
+            if (join) cudaEventDestroy(join);
+        }
+    } side;
+    if (lbar) {
+        *lbar = std::nan("");
+        if (kk >= 1) {
+            double *pp, *lpart;
+            GK(s.get(&pp, P)); GK(s.get(&lpart, kRed)); GK(s.get(&d_lbar, 1)); GK(s.get(&d_bad, 1));
+            GK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+            GK(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+            GK(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming));
+            GK(cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming));
+            GK(cudaEventRecord(side.fork, st));
+            GK(cudaStreamWaitEvent(side.s, side.fork, 0));
+            spacing_kernel<<<blocks_for(P), kT, 0, side.s>>>(gv, gitem, V, n, kk, pp, d_bad);
+            sum_kernel<<<kRed, kT, 0, side.s>>>(pp, P, lpart);
+            finish_sum_kernel<<<1, 1, 0, side.s>>>(lpart, kRed, 1.0 / ((double)P * kk), d_lbar);
+            GK(cudaGetLastError());
+            GK(cudaEventRecord(side.join, side.s));
+        }
+    }
     greedy_kernel<<<1, 1024, 0, st>>>(gv, gitem, order, V, n, R2, state, nodes, nnode);
     GK(cudaGetLastError());
     int N = 0;
     GK(cudaMemcpyAsync(&N, nnode, sizeof(int), cudaMemcpyDeviceToHost, st));
+    double lb = std::nan("");
+    int bad = 0;
+    if (d_lbar) {
+        GK(cudaStreamWaitEvent(st, side.join, 0));
+        GK(cudaMemcpyAsync(&lb, d_lbar, sizeof(double), cudaMemcpyDeviceToHost, st));
+        GK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
     GK(cudaStreamSynchronize(st));
     if (rounds) *rounds = N;
+    if (d_lbar && bad == 0) *lbar = lb;
     int last[2];
     // ---- node positions and the node grid
     int *nval, *nsorted;

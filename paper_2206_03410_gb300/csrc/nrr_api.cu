@@ -582,20 +582,22 @@ nrr_status graph_on_device(const float* src, const std::vector<double>& V, int64
                            bool need_lbar, cudaStream_t st, HostGraph& g) {
     double lbar = std::nan("");
     double R = radius;
-    std::thread t;
-    if (R <= 0) {
+    const bool lbar_first = R <= 0;
+    if (lbar_first) {
         lbar = nrr_mean_spacing(V.data(), P, 6);
         R = 5.0 * lbar;
         if (!(R > 0)) return nrr_set_global_error(NRR_E_INVALID, "graph radius 5 l-bar is not positive");
-    } else if (need_lbar) {
-        t = std::thread([&]() { lbar = nrr_mean_spacing(V.data(), P, 6); });
     }
+    // with a given radius, l-bar comes from the GPU beside the graph (on the
+    // graph's grid); the host computes it only if a point's 6 nearest
+    // others are not all within R
     int rounds = 0;
-    const cudaError_t e = nrr_build_graph_gpu(src, P, R, K, g, st, &rounds);
-    if (t.joinable()) t.join();
+    double lb_gpu = std::nan("");
+    const cudaError_t e = nrr_build_graph_gpu(src, P, R, K, g, st, &rounds, (!lbar_first && need_lbar) ? &lb_gpu : nullptr);
     if (e != cudaSuccess)
         return nrr_set_global_error(e == cudaErrorMemoryAllocation ? NRR_E_OOM : NRR_E_CUDA,
                                     (std::string("deformation graph on the GPU: ") + cudaGetErrorString(e)).c_str());
+    if (!lbar_first && need_lbar) lbar = std::isnan(lb_gpu) ? nrr_mean_spacing(V.data(), P, 6) : lb_gpu;
     g.lbar = lbar;
     return NRR_OK;
 }

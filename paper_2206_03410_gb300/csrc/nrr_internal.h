@@ -102,9 +102,12 @@ void nrr_curve_order(const float* pts, int64_t n, const double lo[3],
                       std::vector<uint64_t>* codes_sorted);
 
 // graph_gpu.cu: Algorithm 1 on the GPU (the same graph as nrr_build_graph);
-// src [P][3] float32 host or device; *rounds = greedy rounds run.
+// src [P][3] float32 host or device; *rounds = greedy rounds run; with lbar
+// non-NULL also l-bar (the mean 6-NN spacing, nrr_mean_spacing's per-point
+// values, summed in another order) on the graph's grid, or NaN when a
+// point's 6 nearest others are not all within R (then the host computes it).
 cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, HostGraph& g, cudaStream_t st,
-                                int* rounds);
+                                int* rounds, double* lbar = nullptr);
 
 // Records msg as the global last error (nrr_last_error(NULL)); returns code.
 nrr_status nrr_set_global_error(nrr_status code, const char* msg);

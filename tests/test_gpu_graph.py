@@ -60,8 +60,25 @@ def test_gpu_graph_equals_host_graph(case):
     gh = nrr.build_graph(src, radius=R, max_influence=K)
     gg = nrr.build_graph(torch.from_numpy(src).cuda(), radius=R, max_influence=K, on_gpu=True)
     _same(gg, gh)
-    if R <= 0:
-        assert abs(gg.lbar - gh.lbar) < 1e-12 * gh.lbar
+    # l-bar: with a given radius computed on the GPU on the graph's grid (the
+    # host's per-point values, summed in another order)
+    assert abs(gg.lbar - gh.lbar) < 1e-12 * gh.lbar
+
+
+def test_gpu_lbar_matches_oracle_and_falls_back():
+    """l-bar on the GPU against the oracle's brute-force mean 6-NN spacing;
+    with a far outlier whose six nearest others are not within R the GPU's
+    value is not certified and the host computes l-bar (same result)."""
+    nrr = _nrr()
+    src = synth.tiny_pair(700, 720, seed=5).src
+    gg = nrr.build_graph(torch.from_numpy(src).cuda(), radius=0.3, on_gpu=True)
+    lo = OG.mean_spacing(src.astype(np.float64))
+    assert abs(gg.lbar - lo) < 1e-12 * lo
+    far = np.concatenate([src, np.array([[40.0, 40.0, 40.0]], dtype=np.float32)])
+    gg = nrr.build_graph(torch.from_numpy(far).cuda(), radius=0.3, on_gpu=True)
+    gh = nrr.build_graph(far, radius=0.3)
+    lo = OG.mean_spacing(far.astype(np.float64))
+    assert abs(gg.lbar - lo) < 1e-12 * lo and abs(gh.lbar - lo) < 1e-12 * lo
 
 
 def test_gpu_graph_equals_oracle():
