@@ -517,7 +517,9 @@ typedef struct {
                                   K in shared memory (1..16), or 0 for the
                                   grid-wide solve. For a batch: -1 = each
                                   pair's smallest fitting cluster, 0 = its
-                                  largest                                   */
+                                  largest, -2 = balanced: the smallest
+                                  cluster whose CTAs hold at most (all
+                                  pairs' nodes / SMs) nodes each            */
     double nn_ms, solve_ms;    /* measured mean kernel durations of the
                                   chosen shapes (nrr_tune; 0 otherwise)     */
     double pass_ms;            /* measured mean batch pass (nrr_batch_tune) */

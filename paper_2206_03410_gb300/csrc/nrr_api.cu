@@ -87,6 +87,7 @@ struct nrr_ctx {
     double* d_adjd = nullptr;          // g_bar [N][12] and dL/dv [P][3] in double
     size_t nn_stats_n = 0;             // per-warp search counters (debug, opt-in)
     int cl_C = 0, cl_cap = 0;          // cluster solve: CTAs per cluster, K blocks per CTA
+    int bal_nodes = 0;                 // batch policy -2: most nodes per CTA (0: unset)
     size_t cl_smem = 0;
     NrrHaloWin cl_win{};               // cluster solve: halo windows
     double diag = 0.0;
@@ -353,6 +354,16 @@ void choose_solver(nrr_ctx* c) {
     if (const char* e = std::getenv("NRR_CLUSTER_CTAS")) forced = std::atoi(e);
     const bool smallest = c->prm.solve_ctas < 0;
     const int order_small[5] = {1, 2, 4, 8, 16}, order_large[5] = {16, 8, 4, 2, 1};
+    // balanced (batches): the smallest cluster whose CTAs hold at most
+    // bal_nodes nodes each, so that the pairs' clusters share the SMs in
+    // proportion to their systems
+    if (c->prm.solve_ctas == -2 && c->bal_nodes > 0 && forced == 0) {
+        for (int C : order_small)
+            if ((c->N + C - 1) / C <= c->bal_nodes && set_solver<T>(c, C)) return;
+        for (int C : order_large)
+            if (set_solver<T>(c, C)) return;
+        return;
+    }
     for (int C : (smallest ? order_small : order_large)) {
         if (forced > 0 && C != forced) continue;
         if (set_solver<T>(c, C)) return;
@@ -2540,7 +2551,13 @@ std::vector<int> all_pairs(const nrr_batch* b) {
 // Applies one launch policy to every pair of a batch: lanes per query and
 // each pair's smallest (policy -1) or largest (policy 0) fitting cluster.
 nrr_status batch_apply(nrr_batch* b, int lpq, int policy) {
+    // policy -2: all pairs' nodes spread over the SMs
+    int64_t sum_n = 0;
+    for (nrr_ctx* c : b->ctx) sum_n += c->N;
+    const int sms = std::max(1, b->ctx.empty() ? 1 : b->ctx[0]->num_sms);
+    const int bal = (int)std::max<int64_t>(64, (sum_n + sms - 1) / sms);
     for (nrr_ctx* c : b->ctx) {
+        c->bal_nodes = bal;
         c->nn_lpq = lpq;
         c->prm.solve_ctas = policy;
         if (c->fp64) choose_solver<double>(c); else choose_solver<float>(c);
@@ -2567,7 +2584,7 @@ nrr_status nrr_batch_tune(nrr_batch* b, const char* table_path, int reps, nrr_la
     int lpq = 0, policy = 0;
     double best_ms = 0.0;
     nrr_status st = NRR_E_INVALID;
-    if (table_lookup(table_path, key, &lpq, &policy) && valid_lpq(lpq) && (policy == -1 || policy == 0)) {
+    if (table_lookup(table_path, key, &lpq, &policy) && valid_lpq(lpq) && (policy >= -2 && policy <= 0)) {
         st = batch_apply(b, lpq, policy);
     }
     if (st != NRR_OK) {
@@ -2576,7 +2593,7 @@ nrr_status nrr_batch_tune(nrr_batch* b, const char* table_path, int reps, nrr_la
         BK(cudaEventCreate(&e0));
         BK(cudaEventCreate(&e1));
         for (int cl : {4, 8, 2})
-            for (int pol : {-1, 0}) {
+            for (int pol : {-1, 0, -2}) {
                 st = batch_apply(b, cl, pol);
                 if (st == NRR_OK) st = nrr_batch_reset(b);
                 if (st != NRR_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
@@ -2692,7 +2709,12 @@ nrr_status nrr_batch_solve(nrr_batch* b, int max_passes, nrr_step_info* infos) {
         nrr_status cst = batch_capture(b, all_pairs(b));
         if (cst != NRR_OK) return cst;
     }
+    // NRR_BATCH_TIMES: each launch's captured pairs, passes and wall time
+    // on stderr (profiling of the batch's phases)
+    const bool times = std::getenv("NRR_BATCH_TIMES") != nullptr;
     while (!all_done && launched < cap) {
+        const auto t_launch = std::chrono::steady_clock::now();
+        const int launched_before = launched;
         if (b->loop_exec) {
             // passes repeat on the device until every pair has returned or
             // half of the captured pairs have (the cap and failures too)
@@ -2709,6 +2731,10 @@ nrr_status nrr_batch_solve(nrr_batch* b, int max_passes, nrr_step_info* infos) {
         BK(cudaMemcpyAsync(b->h_flags, b->d_flags, sizeof(int) * 4 * (size_t)n, cudaMemcpyDeviceToHost, b->stream));
         BK(cudaStreamSynchronize(b->stream));
         launched += b->h_ctrl[0];
+        if (times)
+            std::fprintf(stderr, "nrr_batch_solve: %3d pairs captured, %5d passes, %9.2f ms\n",
+                         (int)b->captured.size(), launched - launched_before,
+                         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_launch).count());
         all_done = true;
         std::vector<int> running;
         for (int i = 0; i < n; ++i) {

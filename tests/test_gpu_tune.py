@@ -96,10 +96,21 @@ def test_batch_tune():
              for k, (P, T) in enumerate([(900, 1000), (2500, 2400), (400, 450)])]
     batch = nrr.BatchRegistration([(p.src, p.tgt) for p in pairs], params=KW)
     cfg = batch.tune(reps=2)
-    assert cfg.nn_lanes_per_query in (2, 4, 8) and cfg.solve_ctas in (-1, 0)
+    assert cfg.nn_lanes_per_query in (2, 4, 8) and cfg.solve_ctas in (-2, -1, 0)
     assert cfg.pass_ms > 0
     infos = batch.solve(3000)
     assert all(i.done == 1 and i.status == 0 for i in infos)
+    # whatever policy the tuner chose (smallest, largest or balanced
+    # clusters), each pair ends bitwise where a single context with the same
+    # lanes per query and cluster size ends
+    for k, p in enumerate(pairs):
+        c = nrr.nrr_get_launch_config(batch.context(k))
+        single = nrr.Registration(p.src, p.tgt, **KW)
+        single.set_launch_config(c.nn_lanes_per_query, c.solve_ctas)
+        si = single.solve(3000)
+        assert (si.n_passes, si.n_solves) == (infos[k].n_passes, infos[k].n_solves)
+        assert np.array_equal(single.transforms(), nrr.nrr_get_transforms(batch.context(k)))
+        single.close()
     batch.close()
 
 
