@@ -125,6 +125,55 @@ __global__ void __launch_bounds__(kThreads) xterm_kernel(DevProblem<T> d) {
 // from the closest-point distances, the sum of all terms (FP64, fixed
 // order: the last CTA adds every CTA's partial sums and xterm_kernel's), and
 // in a pass the safeguard test of Algorithm 2.
+// The assembly's row of point i (pts, 8 values of T): v_i, w^a_i, and
+// Q_i = u_rho(i) - pbar_i (the same float operations the assembly did on its
+// gathers), stored as two 16-byte vectors (float) or four (double).
+template <typename T>
+__device__ __forceinline__ void store_pt(T* pts, int i, T vx, T vy, T vz, T wa, T qx, T qy, T qz);
+template <>
+__device__ __forceinline__ void store_pt<float>(float* pts, int i, float vx, float vy, float vz, float wa, float qx,
+                                                float qy, float qz) {
+    float4* p = reinterpret_cast<float4*>(pts) + 2 * (size_t)i;
+    p[0] = make_float4(vx, vy, vz, wa);
+    p[1] = make_float4(qx, qy, qz, 0.f);
+}
+template <>
+__device__ __forceinline__ void store_pt<double>(double* pts, int i, double vx, double vy, double vz, double wa,
+                                                 double qx, double qy, double qz) {
+    double2* p = reinterpret_cast<double2*>(pts) + 4 * (size_t)i;
+    p[0] = make_double2(vx, vy);
+    p[1] = make_double2(vz, wa);
+    p[2] = make_double2(qx, qy);
+    p[3] = make_double2(qz, 0.0);
+}
+template <typename T>
+__device__ __forceinline__ void load_pt_v(const T* pts, int i, T& vx, T& vy, T& vz, T& wa);
+template <>
+__device__ __forceinline__ void load_pt_v<float>(const float* pts, int i, float& vx, float& vy, float& vz, float& wa) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(pts) + 2 * (size_t)i);
+    vx = a.x; vy = a.y; vz = a.z; wa = a.w;
+}
+template <>
+__device__ __forceinline__ void load_pt_v<double>(const double* pts, int i, double& vx, double& vy, double& vz,
+                                                  double& wa) {
+    const double2* p = reinterpret_cast<const double2*>(pts) + 4 * (size_t)i;
+    const double2 a = __ldg(p), b = __ldg(p + 1);
+    vx = a.x; vy = a.y; vz = b.x; wa = b.y;
+}
+template <typename T>
+__device__ __forceinline__ void load_pt_q(const T* pts, int i, T& qx, T& qy, T& qz);
+template <>
+__device__ __forceinline__ void load_pt_q<float>(const float* pts, int i, float& qx, float& qy, float& qz) {
+    const float4 b = __ldg(reinterpret_cast<const float4*>(pts) + 2 * (size_t)i + 1);
+    qx = b.x; qy = b.y; qz = b.z;
+}
+template <>
+__device__ __forceinline__ void load_pt_q<double>(const double* pts, int i, double& qx, double& qy, double& qz) {
+    const double2* p = reinterpret_cast<const double2*>(pts) + 4 * (size_t)i + 2;
+    const double2 a = __ldg(p), b = __ldg(p + 1);
+    qx = a.x; qy = a.y; qz = b.x;
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
     __shared__ double sh[kThreads / 32];
@@ -151,20 +200,26 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(DevProblem<T> d) {
     // alignment term (Eq. AlignmentTerm) and its surrogate weights w^a_i;
     // the l2 variants: d^2 with weight 1, or min(d^2, 9 nu_a^2) with weight
     // 1 below 3 nu_a and 0 from there on
+    const int P = d.P;
+    auto put_row = [&](int i, T w) {
+        d.wa[i] = w;
+        store_pt<T>(d.pts, i, d.v[i], d.v[P + i], d.v[2 * P + i], w, d.u[i] - d.pbar[i],
+                    d.u[P + i] - d.pbar[P + i], d.u[2 * P + i] - d.pbar[2 * P + i]);
+    };
     if (d.robust == NRR_WELSCH) {
-        for (int i = gtid; i < d.P; i += gstride) {
+        for (int i = gtid; i < P; i += gstride) {
             const T x = d.d2[i] * ia;
             ea += (double)(-t_expm1<T>(-x));
-            d.wa[i] = t_exp<T>(-x) * ia;
+            put_row(i, t_exp<T>(-x) * ia);
         }
     } else {
         const T cut = (T)(9.0 * nua * nua);
         const bool trunc = d.robust == NRR_L2_TRUNCATED;
-        for (int i = gtid; i < d.P; i += gstride) {
+        for (int i = gtid; i < P; i += gstride) {
             const T d2 = d.d2[i];
             const bool in = !trunc || d2 < cut;
             ea += (double)(in ? d2 : cut);
-            d.wa[i] = in ? (T)1 : (T)0;
+            put_row(i, in ? (T)1 : (T)0);
         }
     }
     const double sa = block_sum(ea, sh);
@@ -294,13 +349,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) assemble_ker
                 T vx[kU], vy[kU], vz[kU], wa[kU], qx[kU], qy[kU], qz[kU];
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
+                    // v_i, w^a_i and Q_i = u_rho(i) - sum_j w_ij p_j, one row
                     const int i = ii[u] < 0 ? 0 : ii[u];
-                    vx[u] = d.v[i]; vy[u] = d.v[P + i]; vz[u] = d.v[2 * P + i];
-                    wa[u] = d.wa[i];
-                    // Q_i = u_rho(i) - sum_j w_ij p_j
-                    qx[u] = d.u[i] - d.pbar[i];
-                    qy[u] = d.u[P + i] - d.pbar[P + i];
-                    qz[u] = d.u[2 * P + i] - d.pbar[2 * P + i];
+                    load_pt_v<T>(d.pts, i, vx[u], vy[u], vz[u], wa[u]);
+                    load_pt_q<T>(d.pts, i, qx[u], qy[u], qz[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
@@ -414,8 +466,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) assemble_ker
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     const int i = ii[u] < 0 ? 0 : ii[u];
-                    vx[u] = d.v[i]; vy[u] = d.v[P + i]; vz[u] = d.v[2 * P + i];
-                    wa[u] = d.wa[i];
+                    load_pt_v<T>(d.pts, i, vx[u], vy[u], vz[u], wa[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {

@@ -977,6 +977,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     CK(upload(c, &rho_, rho0)); d.rho = rho_;
     CK(dalloc(c, &d.d2, (size_t)P));
     CK(dalloc(c, &d.wa, (size_t)P));
+    CK(dalloc(c, &d.pts, (size_t)P * 8));
     CK(dalloc(c, &d.wr, (size_t)E2));
     CK(dalloc(c, &d.Rm, (size_t)N * 9));
     CK(dalloc(c, &d.Kv, (size_t)c->nblk * 16));

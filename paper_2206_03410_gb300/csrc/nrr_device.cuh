@@ -80,6 +80,8 @@ struct DevProblem {
     int* rho;       // [P] caller target index
     T* d2;          // [P]
     T* wa;          // [P]
+    T* pts;         // [P][8] per pass: v_i, w^a_i, Q_i = u_rho(i) - pbar_i, 0
+                    // (energy_kernel; the assembly gathers one row per entry)
     // graph edges
     const int* e_i;
     const int* e_j;
