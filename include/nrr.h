@@ -448,6 +448,19 @@ nrr_status nrr_get_solve_stats(nrr_ctx* ctx, long long out[64]);
 /* State of the last pass without running one (host info). */
 nrr_status nrr_get_info(nrr_ctx* ctx, nrr_step_info* info);
 
+/* The pass-by-pass record of the last nrr_solve call: the state after each
+ * pass of Algorithm 2 (energy terms, nu, kept/rejected, stage, PCG
+ * iterations and residual, counters), in pass order, as nrr_step would have
+ * reported it; when the call returned, the last record is that of the pass
+ * whose stopping test ended Algorithm 2 (done = 1; it is not counted in
+ * n_passes). Recorded on the device by the solve's device-side loop (no
+ * host round trip per pass), for at most the first 8192 passes of the call;
+ * empty when the passes were launched from the host (NRR_HOST_LOOP) or the
+ * call ran no pass. out: host array of max_records entries, or NULL to query
+ * the count; *n_records (may be NULL): records copied (or available when out
+ * is NULL). NRR_E_INVALID for a NULL context or max_records < 0. */
+nrr_status nrr_get_history(nrr_ctx* ctx, nrr_step_info* out, int max_records, int* n_records);
+
 /* The alignment term of the energy (the sum of Welsch's function psi_nu_a
  * over the closest-point distances) and the weights of its quadratic
  * surrogate, computed from those distances without allocating any memory.

@@ -71,6 +71,8 @@ struct nrr_ctx {
     NrrState** d_states1 = nullptr;        // {d_state}, for the loop's control kernel
     int* d_ctrl = nullptr;                 // loop control: [0] passes run, [1] cap
     int* h_ctrl = nullptr;                 // pinned staging of the cap
+    nrr_step_info* d_hist = nullptr;       // records of the last device-side loop's passes
+    int hist_n = 0;                        // records of the last nrr_solve
     bool coop = true;
     int grid_energy = 0, grid_asm = 0, grid_solve = 0, grid_aa = 0, num_sms = 0;
     int nn_lpq = 8;                    // closest points: lanes per query (1, 2, 4, 8)
@@ -398,14 +400,34 @@ cudaError_t launch_pass(nrr_ctx* c) {
 
 cudaError_t launch_pass_any(nrr_ctx* c) { return c->fp64 ? launch_pass<double>(c) : launch_pass<float>(c); }
 
+// Passes of one nrr_solve whose summaries the device-side loop records.
+constexpr int kHistCap = 8192;
+
+// The summary of a context state after a pass (host and device).
+__host__ __device__ void fill_info(const NrrState& s, nrr_step_info* info) {
+    if (!info) return;
+    info->E = s.E; info->E_align = s.E_align; info->E_reg = s.E_reg; info->E_rot = s.E_rot;
+    info->nu_a = s.nu_a; info->nu_r = s.nu_r; info->alpha = s.alpha; info->beta = s.beta;
+    info->max_disp = s.max_disp;
+    info->pcg_rel_residual = s.pcg_res;
+    info->kept = s.kept; info->solved = s.solved; info->stage = s.stage; info->done = s.done;
+    info->pcg_iters = s.pcg_iters; info->aa_mk = s.aa_mk;
+    info->n_passes = s.n_passes; info->n_solves = s.n_solves; info->n_rejected = s.n_rejected;
+    info->status = s.status;
+    info->n_singular = s.n_singular;
+    info->warning = s.n_singular > 0 ? NRR_E_SINGULAR : NRR_OK;
+}
+
 // Control of a device-side pass loop (one CTA): copies every context's
-// done flag, status and counters to `flags` (when given), counts the
-// contexts still running, and lets the loop's body run again while one is
-// running, none has failed, fewer than ctrl[1] passes ran in this launch and
-// more than half of the `members` contexts whose passes the body holds are
-// still running (below that the host recaptures a smaller body).
+// done flag, status and counters to `flags` (when given), records the state
+// of a single context after each pass in `hist` (when given, up to hist_cap
+// passes), counts the contexts still running, and lets the loop's body run
+// again while one is running, none has failed, fewer than ctrl[1] passes ran
+// in this launch and more than half of the `members` contexts whose passes
+// the body holds are still running (below that the host recaptures a
+// smaller body).
 __global__ void loop_control(NrrState* const* st, int n, int members, int* flags, int* ctrl,
-                             cudaGraphConditionalHandle h) {
+                             nrr_step_info* hist, int hist_cap, cudaGraphConditionalHandle h) {
     __shared__ int s_run, s_err;
     if (threadIdx.x == 0) { s_run = 0; s_err = 0; }
     __syncthreads();
@@ -427,6 +449,8 @@ __global__ void loop_control(NrrState* const* st, int n, int members, int* flags
     if (threadIdx.x == 0) {
         const int k = ctrl[0] + 1;
         ctrl[0] = k;
+        // a single context's pass record (the loop's history)
+        if (hist && k <= hist_cap) fill_info(*st[0], hist + (k - 1));
         const bool more = s_run > 0 && !s_err && k < ctrl[1] && 2 * s_run > members;
         cudaGraphSetConditional(h, more ? 1u : 0u);
     }
@@ -438,7 +462,7 @@ __global__ void loop_control(NrrState* const* st, int n, int members, int* flags
 // body at least once.
 template <typename F>
 cudaError_t build_loop_graph(cudaStream_t stream, F&& body, NrrState* const* st, int n, int members,
-                             int* flags, int* ctrl, cudaGraphExec_t* out) {
+                             int* flags, int* ctrl, nrr_step_info* hist, int hist_cap, cudaGraphExec_t* out) {
     *out = nullptr;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
@@ -461,7 +485,7 @@ cudaError_t build_loop_graph(cudaStream_t stream, F&& body, NrrState* const* st,
     if (e == cudaSuccess) {
         cudaError_t be = body();
         if (be == cudaSuccess) {
-            loop_control<<<1, 256, 0, stream>>>(st, n, members, flags, ctrl, h);
+            loop_control<<<1, 256, 0, stream>>>(st, n, members, flags, ctrl, hist, hist_cap, h);
             be = cudaGetLastError();
         }
         cudaGraph_t captured = nullptr;
@@ -512,7 +536,7 @@ nrr_status capture_graph(nrr_ctx* c) {
     // it nrr_solve launches the pass graph from the host
     if (c->d_states1 && !std::getenv("NRR_HOST_LOOP"))
         build_loop_graph(c->stream, [c]() { return launch_pass_any(c); }, c->d_states1, 1, 1, nullptr,
-                         c->d_ctrl, &c->loop_exec);
+                         c->d_ctrl, c->d_hist, kHistCap, &c->loop_exec);
     return NRR_OK;
 }
 
@@ -523,19 +547,6 @@ nrr_status run_pass(nrr_ctx* c) {
 }
 
 
-void fill_info(const NrrState& s, nrr_step_info* info) {
-    if (!info) return;
-    info->E = s.E; info->E_align = s.E_align; info->E_reg = s.E_reg; info->E_rot = s.E_rot;
-    info->nu_a = s.nu_a; info->nu_r = s.nu_r; info->alpha = s.alpha; info->beta = s.beta;
-    info->max_disp = s.max_disp;
-    info->pcg_rel_residual = s.pcg_res;
-    info->kept = s.kept; info->solved = s.solved; info->stage = s.stage; info->done = s.done;
-    info->pcg_iters = s.pcg_iters; info->aa_mk = s.aa_mk;
-    info->n_passes = s.n_passes; info->n_solves = s.n_solves; info->n_rejected = s.n_rejected;
-    info->status = s.status;
-    info->n_singular = s.n_singular;
-    info->warning = s.n_singular > 0 ? NRR_E_SINGULAR : NRR_OK;
-}
 
 // ---------------------------------------------------------------------------
 // Creation
@@ -1616,6 +1627,7 @@ void nrr_destroy(nrr_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
     if (c->d_states1) cudaFree(c->d_states1);
+    if (c->d_hist) cudaFree(c->d_hist);
     if (c->d_ctrl) cudaFree(c->d_ctrl);
     if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
     for (void* p : c->allocs) cudaFree(p);
@@ -1753,6 +1765,7 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     CK(cudaMalloc(&c->d_state, sizeof(NrrState)));
     CK(cudaMallocHost(&c->h_state, sizeof(NrrState)));
     std::memset(c->h_state, 0, sizeof(NrrState));
+    CK(cudaMalloc(&c->d_hist, sizeof(nrr_step_info) * kHistCap));
     CK(cudaMalloc(&c->d_states1, sizeof(NrrState*)));
     CK(cudaMemcpy(c->d_states1, &c->d_state, sizeof(NrrState*), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&c->d_ctrl, 2 * sizeof(int)));
@@ -1844,7 +1857,9 @@ nrr_status nrr_solve(nrr_ctx* c, int max_passes, nrr_step_info* info) {
         c->h_ctrl[1] = cap;
         CK(cudaMemcpyAsync(c->d_ctrl, c->h_ctrl, 2 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
         CK(cudaGraphLaunch(c->loop_exec, c->stream));
+        CK(cudaMemcpyAsync(c->h_ctrl, c->d_ctrl, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         st = pull_state(c);
+        c->hist_n = std::min(c->h_ctrl[0], kHistCap);
         if (st != NRR_OK) { c->failed = true; return st; }
         if (c->h_state->status != 0) {
             c->failed = true;
@@ -1854,6 +1869,7 @@ nrr_status nrr_solve(nrr_ctx* c, int max_passes, nrr_step_info* info) {
         fill_info(*c->h_state, info);
         return c->h_state->done ? NRR_OK : NRR_E_NOT_CONVERGED;
     }
+    c->hist_n = 0;   // the host-launched loop records no history
     int launched = 0;
     const int batch = 4;
     while (!c->h_state->done && c->h_state->n_passes - start < cap) {
@@ -2039,6 +2055,18 @@ nrr_status nrr_get_info(nrr_ctx* c, nrr_step_info* info) {
     nrr_status st = pull_state(c);
     if (st != NRR_OK) return st;
     fill_info(*c->h_state, info);
+    return NRR_OK;
+}
+
+nrr_status nrr_get_history(nrr_ctx* c, nrr_step_info* out, int max_records, int* n_records) {
+    if (!c) return fail(nullptr, NRR_E_INVALID, "ctx is NULL");
+    if (max_records < 0) return fail(c, NRR_E_INVALID, "max_records must be >= 0");
+    const int n = out ? std::min(max_records, c->hist_n) : 0;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(out, c->d_hist, sizeof(nrr_step_info) * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (n_records) *n_records = out ? n : c->hist_n;
     return NRR_OK;
 }
 
@@ -2537,7 +2565,7 @@ nrr_status batch_capture(nrr_batch* b, const std::vector<int>& members) {
             }
             return e;
         };
-        build_loop_graph(b->stream, body, b->d_states, n, (int)members.size(), b->d_flags, b->d_ctrl,
+        build_loop_graph(b->stream, body, b->d_states, n, (int)members.size(), b->d_flags, b->d_ctrl, nullptr, 0,
                          &b->loop_exec);
     }
     return NRR_OK;

@@ -154,6 +154,7 @@ _SIGS = [
     ("nrr_get_system", ctypes.c_int, [_VP, _VP, _VP]),
     ("nrr_get_mm_solution", ctypes.c_int, [_VP, _VP]),
     ("nrr_get_info", ctypes.c_int, [_VP, ctypes.POINTER(NrrStepInfo)]),
+    ("nrr_get_history", ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
     ("nrr_get_search_stats", ctypes.c_int, [_VP, _VP, _I64, _VP]),
     ("nrr_get_solve_stats", ctypes.c_int, [_VP, _VP]),
     ("nrr_align_energy_noalloc", ctypes.c_int, [_VP, _I64, ctypes.c_double, _VP, _VP, _VP]),
@@ -574,6 +575,17 @@ def nrr_get_info(ctx) -> NrrStepInfo:
     return info
 
 
+def nrr_get_history(ctx) -> list:
+    """Per-pass records (NrrStepInfo) of the last nrr_solve call."""
+    lib = load()
+    n = ctypes.c_int()
+    _check(lib.nrr_get_history(ctx, None, 0, ctypes.byref(n)), ctx)
+    recs = (NrrStepInfo * max(n.value, 1))()
+    got = ctypes.c_int()
+    _check(lib.nrr_get_history(ctx, ctypes.cast(recs, ctypes.c_void_p), n.value, ctypes.byref(got)), ctx)
+    return list(recs)[:got.value]
+
+
 class Registration:
     """Owner of one nrr context.
 
@@ -685,6 +697,10 @@ class Registration:
 
     def info(self) -> NrrStepInfo:
         return nrr_get_info(self.ctx)
+
+    def history(self) -> list:
+        """Per-pass records of the last solve() (device-side loop)."""
+        return nrr_get_history(self.ctx)
 
 
 def energy_function():

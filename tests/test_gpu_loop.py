@@ -99,3 +99,36 @@ def test_device_loop_batch_cap():
     for k in range(len(pairs)):
         assert infos[k].n_passes == 4 and not infos[k].done
     b.close()
+
+
+def test_device_loop_history_matches_steps():
+    """nrr_get_history returns, pass by pass, the state nrr_step reports for
+    the same passes (recorded on the device by the loop's control kernel);
+    a capped call records only its own passes, the host-launched loop none."""
+    nrr = _nrr()
+    p = synth.workload("sphere5k")
+    kw = {k: v for k, v in p.params.items() if k not in ("precision", "iters")}
+    kw.update(precision="mixed", max_iters_per_stage=30)
+    a = nrr.Registration(p.src, p.tgt, **kw)
+    info = a.solve(100000)
+    hist = a.history()
+    # one record per pass the loop ran: the counted passes, then the pass
+    # whose stopping test returns (done, not counted)
+    assert info.done == 1 and len(hist) == info.n_passes + 1
+    assert hist[-1].done == 1 and all(h.done == 0 for h in hist[:-1])
+    b = nrr.Registration(p.src, p.tgt, **kw)
+    for k, h in enumerate(hist):
+        s = b.step()
+        assert h.as_dict() == s.as_dict(), k
+    assert hist[-1].as_dict() == info.as_dict()
+    a.reset()
+    a.solve(5)
+    h5 = a.history()
+    assert [h.n_passes for h in h5] == [1, 2, 3, 4, 5]
+    with _host_loop():
+        c = nrr.Registration(p.src, p.tgt, **kw)
+        c.solve(5)
+    assert c.history() == []
+    a.close()
+    b.close()
+    c.close()
