@@ -504,6 +504,37 @@ __device__ __forceinline__ bool halo_wait(unsigned long long* bar, unsigned pari
     return true;
 }
 
+// One connected component of the node graph (warp-wide, all 32 lanes): if
+// no node of it has alignment weight (anode == 0 for all), shift its nodes'
+// translations in G so that their sum is that of X^(k), and count it.
+template <typename T>
+__device__ __forceinline__ void free_component(const DevProblem<T>& d, int comp, int lane) {
+    const int c0 = d.comp_ptr[comp], c1 = d.comp_ptr[comp + 1];
+    // weighted as soon as one node is (almost always in the first chunk)
+    for (int k0 = c0; k0 < c1; k0 += 32) {
+        const int k = k0 + lane;
+        if (__any_sync(0xffffffffu, k < c1 && d.anode[d.comp_nodes[k]] != T(0))) return;
+    }
+    double sh[3] = {0.0, 0.0, 0.0};
+    for (int k = c0 + lane; k < c1; k += 32) {
+        const int j = d.comp_nodes[k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sh[a] += (double)d.G[12 * j + 9 + a] - (double)d.X[12 * j + 9 + a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sh[a] += __shfl_xor_sync(0xffffffffu, sh[a], o);
+        sh[a] /= (double)(c1 - c0);
+    }
+    for (int k = c0 + lane; k < c1; k += 32) {
+        const int j = d.comp_nodes[k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d.G[12 * j + 9 + a] = (T)((double)d.G[12 * j + 9 + a] - sh[a]);
+    }
+    if (lane == 0) atomicAdd(&d.st->n_singular, 1);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kClusterThreads, 1)
     solve_cluster_kernel(DevProblem<T> d, int cap, NrrHaloWin win) {
@@ -841,8 +872,15 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     }
     stamp();
     if (ts) ts[63] = tsn;
-    // no CTA may leave while another can still read its shared memory
+    // no CTA may leave while another can still read its shared memory; the
+    // barrier also publishes every CTA's G to the others
     cl.sync();
+    // singular K (the free-translation fix of free_translation_kernel,
+    // here for the passes' solves): one warp of the cluster per component
+    if (d.fix_free && st->status == 0) {
+        const int nwc = bd >> 5;
+        for (int comp = rank * nwc + (tid >> 5); comp < d.n_comp; comp += C * nwc) free_component(d, comp, tid & 31);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -866,30 +904,7 @@ __global__ void __launch_bounds__(256) free_translation_kernel(DevProblem<T> d) 
     const int lane = threadIdx.x & 31;
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int comp = gwarp; comp < d.n_comp; comp += nwarps) {
-        const int c0 = d.comp_ptr[comp], c1 = d.comp_ptr[comp + 1];
-        bool weighted = false;
-        for (int k = c0 + lane; k < c1; k += 32) weighted = weighted || d.anode[d.comp_nodes[k]] != T(0);
-        if (__any_sync(0xffffffffu, weighted)) continue;
-        double sh[3] = {0.0, 0.0, 0.0};
-        for (int k = c0 + lane; k < c1; k += 32) {
-            const int j = d.comp_nodes[k];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) sh[a] += (double)d.G[12 * j + 9 + a] - (double)d.X[12 * j + 9 + a];
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sh[a] += __shfl_xor_sync(0xffffffffu, sh[a], o);
-            sh[a] /= (double)(c1 - c0);
-        }
-        for (int k = c0 + lane; k < c1; k += 32) {
-            const int j = d.comp_nodes[k];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) d.G[12 * j + 9 + a] = (T)((double)d.G[12 * j + 9 + a] - sh[a]);
-        }
-        if (lane == 0) atomicAdd(&st->n_singular, 1);
-    }
+    for (int comp = gwarp; comp < d.n_comp; comp += nwarps) free_component(d, comp, lane);
 }
 
 }  // namespace

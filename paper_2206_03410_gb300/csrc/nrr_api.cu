@@ -245,11 +245,13 @@ cudaError_t launch_search<float>(nrr_ctx* c, const DevProblem<float>& d, int mod
 }
 
 // The solve step of a pass: PCG, then the free-translation fix of singular
-// components.
+// components (a kernel of its own after the grid-wide solve; the cluster
+// solve applies it in its last phase).
 template <typename T>
 cudaError_t launch_solve_step(nrr_ctx* c) {
     cudaError_t e = launch_solve<T>(c);
     if (e != cudaSuccess) return e;
+    if (c->cl_C > 0) return cudaSuccess;
     return nrr_launch_free_translation<T>(prob<T>(c), c->stream);
 }
 
@@ -391,9 +393,7 @@ cudaError_t launch_pass(nrr_ctx* c) {
     if (e != cudaSuccess) return e;
     e = nrr_launch_assemble<T>(d, c->grid_asm, c->stream);
     if (e != cudaSuccess) return e;
-    e = launch_solve<T>(c);
-    if (e != cudaSuccess) return e;
-    e = nrr_launch_free_translation<T>(d, c->stream);
+    e = launch_solve_step<T>(c);
     if (e != cudaSuccess) return e;
     return nrr_launch_aa<T>(d, c->grid_aa, c->stream);
 }
@@ -980,6 +980,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     CK(upload(c, &d.Gprev, X0));
     CK(dalloc(c, &d.Fprev, (size_t)N * 12));
     d.warm_dx = d.Fprev;
+    d.fix_free = 1;
     const int mm = std::max(1, c->prm.aa_m);
     CK(dalloc(c, &d.dF, (size_t)mm * N * 12));
     CK(dalloc(c, &d.dG, (size_t)mm * N * 12));
@@ -1168,6 +1169,7 @@ nrr_status unroll_t(nrr_ctx* c, int K, const double* X0, double* XK) {
         DevProblem<T> ds = prob<T>(c);
         ds.X = ck + (size_t)k * n12;          // warm start X^(k)
         ds.warm_dx = nullptr;
+        ds.fix_free = 0;
         ds.G = ck + (size_t)(k + 1) * n12;    // X^(k+1) = K^-1 B
         CK(launch_solve_on<T>(c, ds));
     }
@@ -1226,6 +1228,7 @@ nrr_status unroll_backward_t(nrr_ctx* c, const double* C, double* grad_X, double
         DevProblem<T> ds = d;
         ds.X = zero;     // warm start 0
         ds.warm_dx = nullptr;
+        ds.fix_free = 0;
         ds.Bv = gt;      // K lambda = g_bar
         ds.G = lam;
         CK(launch_solve_on<T>(c, ds));
@@ -1360,6 +1363,7 @@ nrr_status tune_t(nrr_ctx* c, int reps, int* best_lpq, int* best_ctas, int* best
     DevProblem<T> ds = d;
     ds.X = x0;
     ds.warm_dx = nullptr;
+    ds.fix_free = 0;
     ds.G = x0 + n12;
     *solve_ms = INFINITY;
     const int keep_C = c->cl_C;
@@ -2288,7 +2292,7 @@ nrr_status nrr_get_launch_config(nrr_ctx* c, nrr_launch_config* out) {
     out->nn_ms = 0.0;
     out->solve_ms = 0.0;
     out->pass_ms = 0.0;
-    out->launches_per_pass = kNrrLaunchesPerPass;
+    out->launches_per_pass = nrr_launches_per_pass(c->cl_C > 0);
     return NRR_OK;
 }
 
@@ -2325,7 +2329,7 @@ nrr_status nrr_tune(nrr_ctx* c, const char* table_path, int reps, nrr_launch_con
         out->nn_ms = nn_ms;
         out->solve_ms = solve_ms;
         out->pass_ms = 0.0;
-        out->launches_per_pass = kNrrLaunchesPerPass;
+        out->launches_per_pass = nrr_launches_per_pass(c->cl_C > 0);
         out->nn_tensor_cores = tc;
     }
     return NRR_OK;

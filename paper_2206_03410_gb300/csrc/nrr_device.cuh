@@ -72,6 +72,9 @@ struct DevProblem {
     // solved before (the previous MM step F^(k-1) = G^(k-1) - X^(k-1));
     // NULL: X^(k) alone (solves outside a pass)
     const T* warm_dx;
+    // 1: the cluster solve applies the singular-K fix itself (a pass's
+    // solve); 0: solves outside a pass
+    int fix_free;
     T* dF;
     T* dG;
     // per point
@@ -186,8 +189,12 @@ cudaError_t nrr_launch_aa(const DevProblem<T>& d, int grid, cudaStream_t s);
 template <typename T>
 cudaError_t nrr_launch_free_translation(const DevProblem<T>& d, cudaStream_t s);
 // kernels one pass launches: closest points, X-only terms, energy, assembly,
-// solve, free translations, Anderson differences/Gram solve, Anderson mix
+// solve, free translations (a kernel of its own after the grid-wide solve
+// only), Anderson differences/Gram solve, Anderson mix
 constexpr int kNrrLaunchesPerPass = 8;
+__host__ __device__ constexpr int nrr_launches_per_pass(bool cluster_solve) {
+    return cluster_solve ? kNrrLaunchesPerPass - 1 : kNrrLaunchesPerPass;
+}
 template <typename T>
 cudaError_t nrr_launch_gradient(const DevProblem<T>& d, double* grad_X, double* grad_v, const int* order,
                                 int grid, cudaStream_t s);
