@@ -29,6 +29,9 @@
 #include <cub/device/device_scan.cuh>
 
 #include <cmath>
+#include <cstdlib>
+#include <cstdio>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -37,6 +40,7 @@
 namespace {
 
 constexpr int kT = 256;
+constexpr int kBadCap = 4096;   // l-bar: points searched by brute force at most
 constexpr int kRed = 256;   // CTAs of the fixed-order reductions
 
 __device__ __forceinline__ double sqd(double ax, double ay, double az, double bx, double by, double bz) {
@@ -248,9 +252,11 @@ __global__ void cell_start_kernel(const unsigned long long* __restrict__ keys, i
 // among the points of its 27 cells (ascending), certified when the kk-th is
 // at most h^2 (every point outside the 27 cells is at least h away); the
 // sum of their square roots in ascending order, as the host computes it.
-// Uncertified points are counted (the host then computes l-bar itself).
+// Uncertified points are listed (at most bad_cap; beyond that the host
+// computes l-bar itself) for spacing_fallback_kernel.
 __global__ void spacing_kernel(GridView g, const int* __restrict__ gitem, const double* __restrict__ V, int P, int kk,
-                               double* __restrict__ per_point, int* __restrict__ n_bad) {
+                               double* __restrict__ per_point, int* __restrict__ n_bad, int* __restrict__ bad,
+                               int bad_cap) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
         const double x = V[3 * (int64_t)i], y = V[3 * (int64_t)i + 1], z = V[3 * (int64_t)i + 2];
         double best[8];
@@ -278,10 +284,60 @@ __global__ void spacing_kernel(GridView g, const int* __restrict__ gitem, const 
                 }
             }
         }
-        if (!(best[kk - 1] <= g.h * g.h)) atomicAdd(n_bad, 1);
+        if (!(best[kk - 1] <= g.h * g.h)) {
+            const int k = atomicAdd(n_bad, 1);
+            if (k < bad_cap) bad[k] = i;
+        }
         double sp = 0.0;
         for (int t = 0; t < kk; ++t) sp += sqrt(best[t]);
         per_point[i] = sp;
+    }
+}
+
+// The points whose kk nearest others are not all within R: brute force
+// over every point, one CTA per listed point (its threads keep the kk
+// smallest of their share, then thread 0 merges them), the same sum.
+__global__ void __launch_bounds__(256) spacing_fallback_kernel(const double* __restrict__ V, int P, int kk,
+                                                               const int* __restrict__ n_bad,
+                                                               const int* __restrict__ bad, int bad_cap,
+                                                               double* __restrict__ per_point) {
+    __shared__ double cand[256 * 8];
+    const int nb = min(*n_bad, bad_cap);
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int i = bad[b];
+        const double x = V[3 * (int64_t)i], y = V[3 * (int64_t)i + 1], z = V[3 * (int64_t)i + 2];
+        double best[8];
+        for (int t = 0; t < 8; ++t) best[t] = INFINITY;
+        for (int j = threadIdx.x; j < P; j += blockDim.x) {
+            if (j == i) continue;
+            const double dx = __dsub_rn(x, V[3 * (int64_t)j]), dy = __dsub_rn(y, V[3 * (int64_t)j + 1]),
+                         dz = __dsub_rn(z, V[3 * (int64_t)j + 2]);
+            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            if (d2 < best[kk - 1]) {
+                int pos = kk - 1;
+                while (pos > 0 && best[pos - 1] > d2) { best[pos] = best[pos - 1]; --pos; }
+                best[pos] = d2;
+            }
+        }
+        for (int t = 0; t < kk; ++t) cand[threadIdx.x * 8 + t] = best[t];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m[8];
+            for (int t = 0; t < 8; ++t) m[t] = INFINITY;
+            for (int q = 0; q < (int)blockDim.x * 8; ++q) {
+                if ((q & 7) >= kk) continue;
+                const double d2 = cand[q];
+                if (d2 < m[kk - 1]) {
+                    int pos = kk - 1;
+                    while (pos > 0 && m[pos - 1] > d2) { m[pos] = m[pos - 1]; --pos; }
+                    m[pos] = d2;
+                }
+            }
+            double sp = 0.0;
+            for (int t = 0; t < kk; ++t) sp += sqrt(m[t]);
+            per_point[i] = sp;
+        }
+        __syncthreads();
     }
 }
 
@@ -309,51 +365,59 @@ __global__ void finish_sum_kernel(const double* __restrict__ part, int n, double
 
 // The greedy sampling, node by node, in one CTA: the next rank (in visiting
 // order) that no node covers becomes a node, and every point strictly within
-// R of it is marked covered (state 0 open, 1 node, 2 covered); the scan goes
+// R of it is marked covered (state by visiting rank: 0 open, 1 node, 2 covered); the scan goes
 // on after that rank. This is the sequential algorithm itself; the CTA's
 // threads share the forward scan (1024 ranks at a time) and the covering of
 // each ball. nodes[] receives the nodes in order, *n_nodes their number.
-__global__ void __launch_bounds__(1024) greedy_kernel(GridView g, const int* __restrict__ gitem,
+__global__ void __launch_bounds__(1024) greedy_kernel(GridView g, const int* __restrict__ slot_rank,
                                                       const int* __restrict__ order, const double* __restrict__ V,
-                                                      int P, double R2, unsigned char* state, int* __restrict__ nodes,
+                                                      int P, double R2, unsigned char* rstate, int* __restrict__ nodes,
                                                       int* __restrict__ n_nodes) {
     __shared__ int s_next;
     __shared__ int s_beg[27], s_off[28];
+    const int lane = threadIdx.x & 31;
     int pos = 0, nn = 0;
     while (pos < P) {
-        // ---- the next open rank at or after pos
+        // ---- the next open rank at or after pos (states are kept by rank)
         if (threadIdx.x == 0) s_next = P;
         __syncthreads();
         const int r = pos + (int)threadIdx.x;
-        if (r < P && ((volatile unsigned char*)state)[order[r]] == 0) atomicMin(&s_next, r);
+        if (r < P && ((volatile unsigned char*)rstate)[r] == 0) atomicMin(&s_next, r);
         __syncthreads();
         const int f = s_next;
         if (f == P) {
             pos += 1024;
             continue;
         }
-        // ---- rank f becomes node nn and covers its ball
+        // ---- rank f becomes node nn and covers its ball: warp 0 finds the
+        // 27 cells' runs and their offsets (a shuffle scan)
         const int v = order[f];
         const double x = V[3 * (int64_t)v], y = V[3 * (int64_t)v + 1], z = V[3 * (int64_t)v + 2];
-        if (threadIdx.x < 27) {
-            long long c[3];
-            g.cell(x, y, z, c);
-            const long long cx = c[0] - 1 + threadIdx.x / 9, cy = c[1] - 1 + (threadIdx.x / 3) % 3,
-                            cz = c[2] - 1 + threadIdx.x % 3;
+        if (threadIdx.x < 32) {
             int s0 = 0, s1 = 0;
-            if (cx >= 0 && cy >= 0 && cz >= 0 && cx < g.dims[0] && cy < g.dims[1] && cz < g.dims[2])
-                g.range((unsigned long long)((cx * g.dims[1] + cy) * g.dims[2] + cz), &s0, &s1);
-            s_beg[threadIdx.x] = s0;
-            s_off[threadIdx.x + 1] = s1 - s0;
+            if (lane < 27) {
+                long long c[3];
+                g.cell(x, y, z, c);
+                const long long cx = c[0] - 1 + lane / 9, cy = c[1] - 1 + (lane / 3) % 3, cz = c[2] - 1 + lane % 3;
+                if (cx >= 0 && cy >= 0 && cz >= 0 && cx < g.dims[0] && cy < g.dims[1] && cz < g.dims[2])
+                    g.range((unsigned long long)((cx * g.dims[1] + cy) * g.dims[2] + cz), &s0, &s1);
+            }
+            int incl = s1 - s0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane < 27) {
+                s_beg[lane] = s0;
+                s_off[lane + 1] = incl;
+            }
+            if (lane == 0) {
+                s_off[0] = 0;
+                rstate[f] = 1;
+                nodes[nn] = v;
+            }
         }
-        if (threadIdx.x == 0) {
-            state[v] = 1;
-            nodes[nn] = v;
-            s_off[0] = 0;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0)
-            for (int k = 0; k < 27; ++k) s_off[k + 1] += s_off[k];
         __syncthreads();
         const int total = s_off[27];
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
@@ -361,8 +425,8 @@ __global__ void __launch_bounds__(1024) greedy_kernel(GridView g, const int* __r
             while (s_off[k + 1] <= t) ++k;
             const int sidx = s_beg[k] + (t - s_off[k]);
             if (sqd(x, y, z, g.xyz[3 * sidx], g.xyz[3 * sidx + 1], g.xyz[3 * sidx + 2]) < R2) {
-                const int u = gitem[sidx];
-                if (((volatile unsigned char*)state)[u] == 0) state[u] = 2;
+                const int ru = slot_rank[sidx];
+                if (((volatile unsigned char*)rstate)[ru] == 0) rstate[ru] = 2;
             }
         }
         ++nn;
@@ -370,6 +434,15 @@ __global__ void __launch_bounds__(1024) greedy_kernel(GridView g, const int* __r
         __syncthreads();
     }
     if (threadIdx.x == 0) *n_nodes = nn;
+}
+
+// rank of each point in the visiting order, then of each grid slot's point
+__global__ void rank_of_kernel(int P, const int* __restrict__ order, int* __restrict__ rank_of) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P; r += gridDim.x * blockDim.x) rank_of[order[r]] = r;
+}
+__global__ void slot_rank_kernel(int P, const int* __restrict__ gitem, const int* __restrict__ rank_of,
+                                 int* __restrict__ slot_rank) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P; s += gridDim.x * blockDim.x) slot_rank[s] = rank_of[gitem[s]];
 }
 
 // node positions and node-grid keys
@@ -591,6 +664,18 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     Scratch s;
     const int n = (int)P;
     const double R2 = R * R;
+    // NRR_SETUP_TIMES: the phases on stderr (each timed to the end of its
+    // GPU work)
+    const bool times = std::getenv("NRR_SETUP_TIMES") != nullptr;
+    auto t_last = std::chrono::steady_clock::now();
+    auto lap = [&](const char* what) {
+        if (!times) return;
+        cudaStreamSynchronize(st);
+        const auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "  graph on the GPU: %-28s %8.2f ms\n", what,
+                     std::chrono::duration<double, std::milli>(now - t_last).count());
+        t_last = now;
+    };
     g.radius = R;
     g.K = K;
     float* fsrc = nullptr;
@@ -616,6 +701,7 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     for (int d = 0; d < 3; ++d) dims[d] = std::max<long long>(1, (long long)std::floor((hsc[6 + d] - hsc[3 + d]) / h) + 1);
     hsc[12] = (double)dims[0];
     GK(cudaMemcpyAsync(sc + 12, hsc + 12, sizeof(double), cudaMemcpyHostToDevice, st));
+    lap("PCA");
     // ---- 2. the visiting order and the grid
     unsigned long long *pkey, *pkey_s, *ckey, *ckey_s;
     int *idx, *order, *gitem;
@@ -629,6 +715,7 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     GK(sort_pairs(s, ckey, ckey_s, idx, gitem, n, 64, st));
     grid_data_kernel<<<blocks_for(P), kT, 0, st>>>(P, gitem, V, gxyz);
     GK(cudaGetLastError());
+    lap("visiting order and grid");
     // ---- 3. the greedy sampling (one CTA, node by node)
     const double cells_d = (double)dims[0] * (double)dims[1] * (double)dims[2];
     const bool dense = cells_d <= 4.0 * (double)P + 1048576.0;
@@ -672,15 +759,23 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
             GK(cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming));
             GK(cudaEventRecord(side.fork, st));
             GK(cudaStreamWaitEvent(side.s, side.fork, 0));
-            spacing_kernel<<<blocks_for(P), kT, 0, side.s>>>(gv, gitem, V, n, kk, pp, d_bad);
+            int* d_badlist;
+            GK(s.get(&d_badlist, kBadCap));
+            spacing_kernel<<<blocks_for(P), kT, 0, side.s>>>(gv, gitem, V, n, kk, pp, d_bad, d_badlist, kBadCap);
+            spacing_fallback_kernel<<<256, 256, 0, side.s>>>(V, n, kk, d_bad, d_badlist, kBadCap, pp);
             sum_kernel<<<kRed, kT, 0, side.s>>>(pp, P, lpart);
             finish_sum_kernel<<<1, 1, 0, side.s>>>(lpart, kRed, 1.0 / ((double)P * kk), d_lbar);
             GK(cudaGetLastError());
             GK(cudaEventRecord(side.join, side.s));
         }
     }
-    greedy_kernel<<<1, 1024, 0, st>>>(gv, gitem, order, V, n, R2, state, nodes, nnode);
+    int *rank_of, *slot_rank;
+    GK(s.get(&rank_of, P)); GK(s.get(&slot_rank, P));
+    rank_of_kernel<<<blocks_for(P), kT, 0, st>>>(n, order, rank_of);
+    slot_rank_kernel<<<blocks_for(P), kT, 0, st>>>(n, gitem, rank_of, slot_rank);
+    greedy_kernel<<<1, 1024, 0, st>>>(gv, slot_rank, order, V, n, R2, state, nodes, nnode);
     GK(cudaGetLastError());
+    lap("greedy sampling (+ l-bar)");
     int N = 0;
     GK(cudaMemcpyAsync(&N, nnode, sizeof(int), cudaMemcpyDeviceToHost, st));
     double lb = std::nan("");
@@ -692,7 +787,8 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     }
     GK(cudaStreamSynchronize(st));
     if (rounds) *rounds = N;
-    if (d_lbar && bad == 0) *lbar = lb;
+    if (d_lbar && bad <= kBadCap) *lbar = lb;
+    if (times && d_lbar) std::fprintf(stderr, "  graph on the GPU: l-bar points searched beyond R: %d\n", bad);
     int last[2];
     // ---- node positions and the node grid
     int *nval, *nsorted;
@@ -705,6 +801,7 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     GK(cudaGetLastError());
     GK(sort_pairs(s, nkey, nkey_s, nval, nsorted, N, 64, st));
     node_grid_xyz_kernel<<<blocks_for(N), kT, 0, st>>>(N, nsorted, pn, nxyz);
+    lap("node grid");
     // ---- 4. influence sets, weights, edges, r_ij
     int *nidx, *npairs, *poff;
     double* w;
@@ -752,6 +849,7 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
         r_kernel<<<blocks_for(E2), kT, 0, st>>>(E2, kRed, rpart, (double)n_edges, rr, dpair, dk_s, inv);
         GK(cudaGetLastError());
     }
+    lap("influence, edges, r_ij");
     // ---- back to the host graph
     g.nodes.resize((size_t)N);
     g.nidx.resize((size_t)P * K);
@@ -768,6 +866,7 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
         GK(cudaMemcpyAsync(g.r.data(), rr, sizeof(double) * (size_t)E2, cudaMemcpyDeviceToHost, st));
     }
     GK(cudaStreamSynchronize(st));
+    lap("copies to the host");
     return cudaSuccess;
 #undef GK
 }

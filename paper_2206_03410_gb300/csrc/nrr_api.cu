@@ -611,8 +611,8 @@ nrr_status graph_on_device(const float* src, const std::vector<double>& V, int64
         if (!(R > 0)) return nrr_set_global_error(NRR_E_INVALID, "graph radius 5 l-bar is not positive");
     }
     // with a given radius, l-bar comes from the GPU beside the graph (on the
-    // graph's grid); the host computes it only if a point's 6 nearest
-    // others are not all within R
+    // graph's grid, points whose 6 nearest others are not all within R by
+    // brute force); the host computes it only if there are too many of them
     int rounds = 0;
     double lb_gpu = std::nan("");
     const cudaError_t e = nrr_build_graph_gpu(src, P, R, K, g, st, &rounds, (!lbar_first && need_lbar) ? &lb_gpu : nullptr);

@@ -67,8 +67,9 @@ def test_gpu_graph_equals_host_graph(case):
 
 def test_gpu_lbar_matches_oracle_and_falls_back():
     """l-bar on the GPU against the oracle's brute-force mean 6-NN spacing;
-    with a far outlier whose six nearest others are not within R the GPU's
-    value is not certified and the host computes l-bar (same result)."""
+    points whose six nearest others are not within R (far outliers) are
+    searched by brute force on the GPU, and with more of them than the GPU
+    lists (4,096) the host computes l-bar: the same result each way."""
     nrr = _nrr()
     src = synth.tiny_pair(700, 720, seed=5).src
     gg = nrr.build_graph(torch.from_numpy(src).cuda(), radius=0.3, on_gpu=True)
@@ -79,6 +80,14 @@ def test_gpu_lbar_matches_oracle_and_falls_back():
     gh = nrr.build_graph(far, radius=0.3)
     lo = OG.mean_spacing(far.astype(np.float64))
     assert abs(gg.lbar - lo) < 1e-12 * lo and abs(gh.lbar - lo) < 1e-12 * lo
+    # a sparse cloud: every point uncertified, some 60 or all 5,000 of them
+    rng = np.random.default_rng(8)
+    for n_far in (60, 5000):
+        pts = np.concatenate([src, rng.uniform(-50, 50, (n_far, 3)).astype(np.float32)])
+        gg = nrr.build_graph(torch.from_numpy(pts).cuda(), radius=0.3, on_gpu=True)
+        gh = nrr.build_graph(pts, radius=0.3)
+        lo = OG.mean_spacing(pts.astype(np.float64))
+        assert abs(gg.lbar - lo) < 1e-12 * lo and abs(gh.lbar - lo) < 1e-12 * lo, n_far
 
 
 def test_gpu_graph_equals_oracle():
