@@ -43,6 +43,8 @@ constexpr int kT = 256;
 constexpr int kBadCap = 4096;   // l-bar: points searched by brute force at most
 constexpr int kRed = 256;   // CTAs of the fixed-order reductions
 
+int blocks_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + kT - 1) / kT, 4096)); }
+
 __device__ __forceinline__ double sqd(double ax, double ay, double az, double bx, double by, double bz) {
     const double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by), dz = __dsub_rn(az, bz);
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
@@ -52,6 +54,34 @@ __device__ __forceinline__ double sqd(double ax, double ay, double az, double bx
 __device__ __forceinline__ unsigned long long dkey(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x + 0.0);
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// Float prefilter of the nearest-neighbour searches. The source
+// points are floats, so the float copies of the coordinates are exact, and
+// a squared distance formed in float (round to nearest, no contraction)
+// is within a relative 4e-7 of the exact one, except below 1e-36 where
+// subnormal rounding adds an absolute error. So if t is the kk-th smallest
+// float squared distance of a point's candidates, each of its kk nearest
+// (by the double distance) has a float squared distance of at most
+// t (1 + 1e-5) + 1e-36: only those candidates are measured in double.
+__device__ __forceinline__ float sqdf(float4 a, float4 b) {
+    const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+__device__ __forceinline__ float knn_filter(float t) { return __fadd_ru(__fmul_ru(t, 1.00001f), 1e-36f); }
+// the K smallest values seen, ascending (registers: compile-time indices)
+template <int K, typename V>
+__device__ __forceinline__ void topk_insert(V (&best)[K], V d2) {
+    if (d2 < best[K - 1]) {
+        best[K - 1] = d2;
+#pragma unroll
+        for (int p = K - 1; p > 0; --p)
+            if (best[p] < best[p - 1]) {
+                const V t = best[p];
+                best[p] = best[p - 1];
+                best[p - 1] = t;
+            }
+    }
 }
 
 __global__ void to_double_kernel(const float* __restrict__ src, double* __restrict__ V, int64_t n3) {
@@ -195,12 +225,13 @@ __global__ void keys_kernel(const double* __restrict__ V, int64_t P, const doubl
 
 // the grid's point coordinates in cell order
 __global__ void grid_data_kernel(int64_t P, const int* __restrict__ gitem, const double* __restrict__ V,
-                                 double* __restrict__ gxyz) {
+                                 double* __restrict__ gxyz, float4* __restrict__ gf) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < P; s += (int64_t)gridDim.x * blockDim.x) {
         const int i = gitem[s];
         gxyz[3 * s] = V[3 * (int64_t)i];
         gxyz[3 * s + 1] = V[3 * (int64_t)i + 1];
         gxyz[3 * s + 2] = V[3 * (int64_t)i + 2];
+        gf[s] = make_float4((float)V[3 * (int64_t)i], (float)V[3 * (int64_t)i + 1], (float)V[3 * (int64_t)i + 2], 0.f);
     }
 }
 
@@ -249,96 +280,127 @@ __global__ void cell_start_kernel(const unsigned long long* __restrict__ keys, i
 
 // l-bar (the mean distance of every point to its kk = 6 nearest others) on
 // the grid of cell size h = R: per point the kk smallest squared distances
-// among the points of its 27 cells (ascending), certified when the kk-th is
-// at most h^2 (every point outside the 27 cells is at least h away); the
-// sum of their square roots in ascending order, as the host computes it.
-// Uncertified points are listed (at most bad_cap; beyond that the host
-// computes l-bar itself) for spacing_fallback_kernel.
-__global__ void spacing_kernel(GridView g, const int* __restrict__ gitem, const double* __restrict__ V, int P, int kk,
-                               double* __restrict__ per_point, int* __restrict__ n_bad, int* __restrict__ bad,
-                               int bad_cap) {
+// among the points of its 27 cells (ascending; a float pass, then the
+// double distances of the candidates the filter keeps), certified when the
+// kk-th is at most h^2 (every point outside the 27 cells is at least h
+// away); the sum of their square roots in ascending order, as the host
+// computes it. Uncertified points are listed (at most bad_cap; beyond that
+// the host computes l-bar itself) for spacing_fallback_kernel.
+template <int KK>
+__global__ void spacing_kernel(GridView g, const float4* __restrict__ gf, const int* __restrict__ gitem,
+                               const double* __restrict__ V, int P, double* __restrict__ per_point,
+                               int* __restrict__ n_bad, int* __restrict__ bad, int bad_cap) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
         const double x = V[3 * (int64_t)i], y = V[3 * (int64_t)i + 1], z = V[3 * (int64_t)i + 2];
-        double best[8];
-        for (int t = 0; t < 8; ++t) best[t] = INFINITY;
+        const float4 pf = make_float4((float)x, (float)y, (float)z, 0.f);
         long long c[3];
         g.cell(x, y, z, c);
+        int rs0[27], rs1[27];
+        int nc = 0;
         for (long long a = c[0] - 1; a <= c[0] + 1; ++a) {
-            if (a < 0 || a >= g.dims[0]) continue;
             for (long long b = c[1] - 1; b <= c[1] + 1; ++b) {
-                if (b < 0 || b >= g.dims[1]) continue;
                 for (long long d = c[2] - 1; d <= c[2] + 1; ++d) {
-                    if (d < 0 || d >= g.dims[2]) continue;
-                    int s0, s1;
-                    g.range((unsigned long long)((a * g.dims[1] + b) * g.dims[2] + d), &s0, &s1);
-                    for (int s = s0; s < s1; ++s) {
-                        const double dx = __dsub_rn(x, g.xyz[3 * s]), dy = __dsub_rn(y, g.xyz[3 * s + 1]),
-                                     dz = __dsub_rn(z, g.xyz[3 * s + 2]);
-                        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                        if (d2 < best[kk - 1] && gitem[s] != i) {
-                            int pos = kk - 1;
-                            while (pos > 0 && best[pos - 1] > d2) { best[pos] = best[pos - 1]; --pos; }
-                            best[pos] = d2;
-                        }
-                    }
+                    if (a < 0 || a >= g.dims[0] || b < 0 || b >= g.dims[1] || d < 0 || d >= g.dims[2]) continue;
+                    g.range((unsigned long long)((a * g.dims[1] + b) * g.dims[2] + d), &rs0[nc], &rs1[nc]);
+                    ++nc;
                 }
             }
         }
-        if (!(best[kk - 1] <= g.h * g.h)) {
+        float bf[KK];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) bf[t] = INFINITY;
+        for (int k = 0; k < nc; ++k)
+            for (int s = rs0[k]; s < rs1[k]; ++s)
+                if (gitem[s] != i) topk_insert(bf, sqdf(pf, gf[s]));
+        const float thr = knn_filter(bf[KK - 1]);
+        double best[KK];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) best[t] = INFINITY;
+        for (int k = 0; k < nc; ++k)
+            for (int s = rs0[k]; s < rs1[k]; ++s)
+                if (sqdf(pf, gf[s]) <= thr && gitem[s] != i)
+                    topk_insert(best, sqd(x, y, z, g.xyz[3 * s], g.xyz[3 * s + 1], g.xyz[3 * s + 2]));
+        if (!(best[KK - 1] <= g.h * g.h)) {
             const int k = atomicAdd(n_bad, 1);
             if (k < bad_cap) bad[k] = i;
         }
         double sp = 0.0;
-        for (int t = 0; t < kk; ++t) sp += sqrt(best[t]);
+#pragma unroll
+        for (int t = 0; t < KK; ++t) sp += sqrt(best[t]);
         per_point[i] = sp;
     }
 }
 
 // The points whose kk nearest others are not all within R: brute force
-// over every point, one CTA per listed point (its threads keep the kk
-// smallest of their share, then thread 0 merges them), the same sum.
-__global__ void __launch_bounds__(256) spacing_fallback_kernel(const double* __restrict__ V, int P, int kk,
+// over every point, one CTA per listed point: the kk smallest float squared
+// distances of each thread's share, merged by thread 0 into the filter
+// bound, then the same for the double distances of the candidates the
+// filter keeps; the same sum.
+template <int KK>
+__global__ void __launch_bounds__(256) spacing_fallback_kernel(const double* __restrict__ V,
+                                                               const float* __restrict__ fsrc, int P,
                                                                const int* __restrict__ n_bad,
                                                                const int* __restrict__ bad, int bad_cap,
                                                                double* __restrict__ per_point) {
-    __shared__ double cand[256 * 8];
+    __shared__ double cand[256 * KK];
+    __shared__ float s_thr;
     const int nb = min(*n_bad, bad_cap);
     for (int b = blockIdx.x; b < nb; b += gridDim.x) {
         const int i = bad[b];
         const double x = V[3 * (int64_t)i], y = V[3 * (int64_t)i + 1], z = V[3 * (int64_t)i + 2];
-        double best[8];
-        for (int t = 0; t < 8; ++t) best[t] = INFINITY;
+        const float4 pf = make_float4(fsrc[3 * (int64_t)i], fsrc[3 * (int64_t)i + 1], fsrc[3 * (int64_t)i + 2], 0.f);
+        float bf[KK];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) bf[t] = INFINITY;
         for (int j = threadIdx.x; j < P; j += blockDim.x) {
             if (j == i) continue;
-            const double dx = __dsub_rn(x, V[3 * (int64_t)j]), dy = __dsub_rn(y, V[3 * (int64_t)j + 1]),
-                         dz = __dsub_rn(z, V[3 * (int64_t)j + 2]);
-            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            if (d2 < best[kk - 1]) {
-                int pos = kk - 1;
-                while (pos > 0 && best[pos - 1] > d2) { best[pos] = best[pos - 1]; --pos; }
-                best[pos] = d2;
-            }
+            topk_insert(bf, sqdf(pf, make_float4(fsrc[3 * (int64_t)j], fsrc[3 * (int64_t)j + 1],
+                                                 fsrc[3 * (int64_t)j + 2], 0.f)));
         }
-        for (int t = 0; t < kk; ++t) cand[threadIdx.x * 8 + t] = best[t];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) cand[threadIdx.x * KK + t] = (double)bf[t];
         __syncthreads();
         if (threadIdx.x == 0) {
-            double m[8];
-            for (int t = 0; t < 8; ++t) m[t] = INFINITY;
-            for (int q = 0; q < (int)blockDim.x * 8; ++q) {
-                if ((q & 7) >= kk) continue;
-                const double d2 = cand[q];
-                if (d2 < m[kk - 1]) {
-                    int pos = kk - 1;
-                    while (pos > 0 && m[pos - 1] > d2) { m[pos] = m[pos - 1]; --pos; }
-                    m[pos] = d2;
-                }
-            }
+            float m[KK];
+#pragma unroll
+            for (int t = 0; t < KK; ++t) m[t] = INFINITY;
+            for (int q = 0; q < (int)blockDim.x * KK; ++q) topk_insert(m, (float)cand[q]);
+            s_thr = knn_filter(m[KK - 1]);
+        }
+        __syncthreads();
+        const float thr = s_thr;
+        double best[KK];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) best[t] = INFINITY;
+        for (int j = threadIdx.x; j < P; j += blockDim.x) {
+            if (j == i) continue;
+            const float4 qf = make_float4(fsrc[3 * (int64_t)j], fsrc[3 * (int64_t)j + 1], fsrc[3 * (int64_t)j + 2], 0.f);
+            if (sqdf(pf, qf) <= thr)
+                topk_insert(best, sqd(x, y, z, V[3 * (int64_t)j], V[3 * (int64_t)j + 1], V[3 * (int64_t)j + 2]));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < KK; ++t) cand[threadIdx.x * KK + t] = best[t];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m[KK];
+#pragma unroll
+            for (int t = 0; t < KK; ++t) m[t] = INFINITY;
+            for (int q = 0; q < (int)blockDim.x * KK; ++q) topk_insert(m, cand[q]);
             double sp = 0.0;
-            for (int t = 0; t < kk; ++t) sp += sqrt(m[t]);
+#pragma unroll
+            for (int t = 0; t < KK; ++t) sp += sqrt(m[t]);
             per_point[i] = sp;
         }
         __syncthreads();
     }
+}
+
+template <int KK>
+void launch_spacing(const GridView& gv, const float4* gf, const int* gitem, const double* V, const float* fsrc,
+                    int n, double* pp, int* d_bad, int* d_badlist, cudaStream_t s) {
+    spacing_kernel<KK><<<blocks_for(n), kT, 0, s>>>(gv, gf, gitem, V, n, pp, d_bad, d_badlist, kBadCap);
+    spacing_fallback_kernel<KK><<<256, 256, 0, s>>>(V, fsrc, n, d_bad, d_badlist, kBadCap, pp);
 }
 
 // Fixed-order sum of x[0..n): per CTA a contiguous share reduced by a
@@ -369,10 +431,14 @@ __global__ void finish_sum_kernel(const double* __restrict__ part, int n, double
 // on after that rank. This is the sequential algorithm itself; the CTA's
 // threads share the forward scan (1024 ranks at a time) and the covering of
 // each ball. nodes[] receives the nodes in order, *n_nodes their number.
+// Runs only when some rank's forward R-slab exceeds the window of
+// greedy_window_kernel (*span > window); returns at once otherwise.
 __global__ void __launch_bounds__(1024) greedy_kernel(GridView g, const int* __restrict__ slot_rank,
                                                       const int* __restrict__ order, const double* __restrict__ V,
                                                       int P, double R2, unsigned char* rstate, int* __restrict__ nodes,
-                                                      int* __restrict__ n_nodes) {
+                                                      int* __restrict__ n_nodes, const int* __restrict__ span,
+                                                      int window) {
+    if (*span <= window) return;   // greedy_window_kernel has run
     __shared__ int s_next;
     __shared__ int s_beg[27], s_off[28];
     const int lane = threadIdx.x & 31;
@@ -434,6 +500,186 @@ __global__ void __launch_bounds__(1024) greedy_kernel(GridView g, const int* __r
         __syncthreads();
     }
     if (threadIdx.x == 0) *n_nodes = nn;
+}
+
+// Greedy sampling in a window of the visiting order (the source points are
+// floats, so their float copies are exact). Per rank r: rend[r] = the first
+// rank whose projection on the visiting axis exceeds r's by more than R
+// (with a margin far above the projections' rounding), so every point
+// strictly within R of rank r's point that comes after it in the order has
+// a rank in (r, rend[r]). The CTA holds the ranks [lo, hi) (at most
+// kGreedyWin, slot r mod kGreedyWin) with their coordinates (float and
+// double), rend and state (0 open, 1 node, 2 covered) in shared memory.
+// Per node f: warp 0 finds the next open rank (4 ranks per lane, a
+// ballot); the window moves to [f, f + kGreedyWin) if it does not reach
+// rend[f]; every thread tests ranks of (f, rend[f]): a float distance
+// test with a margin (a float squared distance exceeds the exact one by
+// less than a relative 4e-7) selects the candidates, the double distance
+// decides as everywhere else. Used when every rend[r] - r fits the window
+// (*span); greedy_kernel runs otherwise.
+constexpr int kGreedyWin = 4096;
+
+// projection of a point on the visiting axis, as keys_kernel forms it
+__device__ __forceinline__ double axis_proj(double x, double y, double z, const double* sc) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(x, sc[9]), __dmul_rn(y, sc[10])), __dmul_rn(z, sc[11]));
+}
+
+// per rank: double and float coordinates, projection
+__global__ void greedy_coords_kernel(const int* __restrict__ order, const double* __restrict__ V, int P,
+                                     const double* __restrict__ sc, double* __restrict__ Vr,
+                                     float4* __restrict__ Vf, double* __restrict__ proj) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P; r += gridDim.x * blockDim.x) {
+        const int v = order[r];
+        const double x = V[3 * (int64_t)v], y = V[3 * (int64_t)v + 1], z = V[3 * (int64_t)v + 2];
+        Vr[3 * (int64_t)r] = x;
+        Vr[3 * (int64_t)r + 1] = y;
+        Vr[3 * (int64_t)r + 2] = z;
+        Vf[r] = make_float4((float)x, (float)y, (float)z, 0.f);
+        proj[r] = axis_proj(x, y, z, sc);
+    }
+}
+
+// rend[r] by binary search of the (ascending) projections; the largest
+// rend[r] - r into *span. Margin: |a.(p - q)| <= |a| |p - q|, and each
+// computed projection is within 3.1 * 2^-53 * (|x| + |y| + |z|) of the
+// exact one (the axis entries are at most 1); the bound adds R |a| 1e-9
+// and 1e-9 (|x| + |y| + |z| + 3R), far above both.
+__global__ void greedy_rend_kernel(const double* __restrict__ Vr, const double* __restrict__ proj, int P,
+                                   const double* __restrict__ sc, double R, int* __restrict__ rend,
+                                   int* __restrict__ span) {
+    const double na = sqrt(sc[9] * sc[9] + sc[10] * sc[10] + sc[11] * sc[11]);
+    int worst = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P; r += gridDim.x * blockDim.x) {
+        const double S = fabs(Vr[3 * (int64_t)r]) + fabs(Vr[3 * (int64_t)r + 1]) + fabs(Vr[3 * (int64_t)r + 2]);
+        const double bound = proj[r] + R * na * (1.0 + 1e-9) + 1e-9 * (S + 3.0 * R);
+        int lo = r + 1, hi = P;   // first rank in [r + 1, P] with proj > bound
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (proj[m] > bound) hi = m; else lo = m + 1;
+        }
+        rend[r] = lo;
+        worst = max(worst, lo - r);
+    }
+    atomicMax(span, worst);
+}
+
+__global__ void __launch_bounds__(1024) greedy_window_kernel(const double* __restrict__ Vr,
+                                                             const float4* __restrict__ Vf,
+                                                             const int* __restrict__ rend,
+                                                             const int* __restrict__ span, int P, double R2,
+                                                             int* __restrict__ node_rank, int* __restrict__ n_nodes) {
+    if (*span > kGreedyWin) return;   // greedy_kernel runs instead
+    constexpr int W = kGreedyWin, M = kGreedyWin - 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4* wf = reinterpret_cast<float4*>(smem);            // [W]
+    double* wx = reinterpret_cast<double*>(wf + W);          // [3][W]
+    int* wr = reinterpret_cast<int*>(wx + 3 * W);            // [W]
+    int* s_hit = wr + W;                                     // [W] candidates of the double test
+    unsigned char* ws = reinterpret_cast<unsigned char*>(s_hit + W);   // [W]
+    __shared__ int s_f, s_nhit;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // float squared distances below this are decided in double (R2 < 1e30:
+    // no float overflow for candidates near R)
+    const bool all = !(R2 < 1e30);
+    const float thr = all ? 0.f : (float)(R2 * (1.0 + 1e-5) + 1e-36);
+    int lo = 0, hi = 0;
+    // the window becomes [nlo, min(P, nlo + W)): ranks from max(hi, nlo)
+    // are loaded into slots of ranks below nlo (decided, never read again)
+    auto refill = [&](int nlo) {
+        const int nhi = min(P, nlo + W);
+        for (int r = max(hi, nlo) + (int)threadIdx.x; r < nhi; r += blockDim.x) {
+            const int q = r & M;
+            wf[q] = Vf[r];
+            wx[q] = Vr[3 * (int64_t)r];
+            wx[W + q] = Vr[3 * (int64_t)r + 1];
+            wx[2 * W + q] = Vr[3 * (int64_t)r + 2];
+            wr[q] = rend[r];
+            ws[q] = 0;
+        }
+        lo = nlo;
+        hi = nhi;
+        __syncthreads();
+    };
+    refill(0);
+    int pos = 0, nn = 0;
+    for (;;) {
+        if (wid == 0) {
+            int f = -1;   // -1: no open rank in [pos, hi)
+            for (int base = pos & ~3; base < hi; base += 128) {
+                const int r0 = base + 4 * lane;
+                unsigned m = 0;   // bit k: rank r0 + k is open, in [pos, hi)
+                if (r0 < hi) {
+                    const unsigned wv = *reinterpret_cast<const unsigned*>(ws + (r0 & M));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (((wv >> (8 * k)) & 0xffu) == 0 && r0 + k >= pos && r0 + k < hi) m |= 1u << k;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
+                if (bal) {
+                    const int src = __ffs(bal) - 1;
+                    const unsigned mm = __shfl_sync(0xffffffffu, m, src);
+                    f = base + 4 * src + __ffs(mm) - 1;
+                    break;
+                }
+            }
+            if (lane == 0) {
+                s_f = f;
+                if (f >= 0) {
+                    ws[f & M] = 1;
+                    node_rank[nn] = f;
+                }
+            }
+        }
+        __syncthreads();
+        const int f = s_f;
+        if (f < 0) {   // every rank of [pos, hi) is decided
+            if (hi >= P) break;
+            const int h = hi;
+            refill(h);
+            pos = h;
+            continue;
+        }
+        const int re = wr[f & M];
+        if (re > hi) refill(f);   // re - f <= span <= W
+        // float pass: the open candidates the filter keeps, compacted (a
+        // warp-wide append), so that the double distances run on full warps
+        const int sf = f & M;
+        const float4 pf = wf[sf];
+        if (threadIdx.x == 0) s_nhit = 0;
+        __syncthreads();
+        for (int r0 = f + 1; r0 < re; r0 += blockDim.x) {
+            const int r = r0 + (int)threadIdx.x;
+            bool keep = false;
+            if (r < re) {
+                const int q = r & M;
+                keep = (all || sqdf(pf, wf[q]) < thr) && ws[q] == 0;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (bal) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s_nhit, __popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (keep) s_hit[base + __popc(bal & ((1u << lane) - 1u))] = r & M;
+            }
+        }
+        __syncthreads();
+        const int nh = s_nhit;
+        const double x = wx[sf], y = wx[W + sf], z = wx[2 * W + sf];
+        for (int k = threadIdx.x; k < nh; k += blockDim.x) {
+            const int q = s_hit[k];
+            if (sqd(x, y, z, wx[q], wx[W + q], wx[2 * W + q]) < R2) ws[q] = 2;
+        }
+        ++nn;
+        pos = f + 1;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_nodes = nn;
+}
+
+__global__ void rank_to_point_kernel(const int* __restrict__ n_nodes, const int* __restrict__ order,
+                                     int* __restrict__ nodes) {
+    const int N = *n_nodes;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) nodes[j] = order[nodes[j]];
 }
 
 // rank of each point in the visiting order, then of each grid slot's point
@@ -647,7 +893,6 @@ cudaError_t exclusive_sum(Scratch& s, const int* in, int* out, int n, cudaStream
     return cub::DeviceScan::ExclusiveSum(tmp, tb, in, out, n, st);
 }
 
-int blocks_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + kT - 1) / kT, 4096)); }
 
 }  // namespace
 
@@ -713,7 +958,9 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     GK(cudaGetLastError());
     GK(sort_pairs(s, pkey, pkey_s, idx, order, n, 64, st));
     GK(sort_pairs(s, ckey, ckey_s, idx, gitem, n, 64, st));
-    grid_data_kernel<<<blocks_for(P), kT, 0, st>>>(P, gitem, V, gxyz);
+    float4* gf;
+    GK(s.get(&gf, P));
+    grid_data_kernel<<<blocks_for(P), kT, 0, st>>>(P, gitem, V, gxyz, gf);
     GK(cudaGetLastError());
     lap("visiting order and grid");
     // ---- 3. the greedy sampling (one CTA, node by node)
@@ -761,8 +1008,14 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
             GK(cudaStreamWaitEvent(side.s, side.fork, 0));
             int* d_badlist;
             GK(s.get(&d_badlist, kBadCap));
-            spacing_kernel<<<blocks_for(P), kT, 0, side.s>>>(gv, gitem, V, n, kk, pp, d_bad, d_badlist, kBadCap);
-            spacing_fallback_kernel<<<256, 256, 0, side.s>>>(V, n, kk, d_bad, d_badlist, kBadCap, pp);
+            switch (kk) {
+                case 1: launch_spacing<1>(gv, gf, gitem, V, fsrc, n, pp, d_bad, d_badlist, side.s); break;
+                case 2: launch_spacing<2>(gv, gf, gitem, V, fsrc, n, pp, d_bad, d_badlist, side.s); break;
+                case 3: launch_spacing<3>(gv, gf, gitem, V, fsrc, n, pp, d_bad, d_badlist, side.s); break;
+                case 4: launch_spacing<4>(gv, gf, gitem, V, fsrc, n, pp, d_bad, d_badlist, side.s); break;
+                case 5: launch_spacing<5>(gv, gf, gitem, V, fsrc, n, pp, d_bad, d_badlist, side.s); break;
+                default: launch_spacing<6>(gv, gf, gitem, V, fsrc, n, pp, d_bad, d_badlist, side.s); break;
+            }
             sum_kernel<<<kRed, kT, 0, side.s>>>(pp, P, lpart);
             finish_sum_kernel<<<1, 1, 0, side.s>>>(lpart, kRed, 1.0 / ((double)P * kk), d_lbar);
             GK(cudaGetLastError());
@@ -773,7 +1026,24 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     GK(s.get(&rank_of, P)); GK(s.get(&slot_rank, P));
     rank_of_kernel<<<blocks_for(P), kT, 0, st>>>(n, order, rank_of);
     slot_rank_kernel<<<blocks_for(P), kT, 0, st>>>(n, gitem, rank_of, slot_rank);
-    greedy_kernel<<<1, 1024, 0, st>>>(gv, slot_rank, order, V, n, R2, state, nodes, nnode);
+    // the window kernel when every rank's forward R-slab fits its window
+    // (decided on the device), else the global-state kernel
+    const size_t win_smem = (size_t)kGreedyWin * (16 + 24 + 4 + 4 + 1);
+    {
+        double *Vr, *proj;
+        float4* Vf;
+        int *rend, *span;
+        GK(s.get(&Vr, (size_t)P * 3)); GK(s.get(&proj, P)); GK(s.get(&Vf, P));
+        GK(s.get(&rend, P)); GK(s.get(&span, 1));
+        GK(cudaMemsetAsync(span, 0, sizeof(int), st));
+        GK(cudaMemsetAsync(nnode, 0, sizeof(int), st));
+        GK(cudaFuncSetAttribute(greedy_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
+        greedy_coords_kernel<<<blocks_for(P), kT, 0, st>>>(order, V, n, sc, Vr, Vf, proj);
+        greedy_rend_kernel<<<blocks_for(P), kT, 0, st>>>(Vr, proj, n, sc, R, rend, span);
+        greedy_window_kernel<<<1, 1024, win_smem, st>>>(Vr, Vf, rend, span, n, R2, nodes, nnode);
+        rank_to_point_kernel<<<blocks_for(P), kT, 0, st>>>(nnode, order, nodes);
+        greedy_kernel<<<1, 1024, 0, st>>>(gv, slot_rank, order, V, n, R2, state, nodes, nnode, span, kGreedyWin);
+    }
     GK(cudaGetLastError());
     lap("greedy sampling (+ l-bar)");
     int N = 0;

@@ -4,7 +4,8 @@ same nodes (the greedy sampling's lexicographically first maximal
 independent set in PCA order), the same influence sets and edges, and the
 weights and r_ij to rounding; on the 5,000-point sphere (also against the
 oracle), a small pair with a capped influence width and with the default
-radius 5 l-bar, the full-size depth workload and pairs of the batched
+radius 5 l-bar, the full-size depth workload, a 250,000-point sphere (the
+greedy sampling with its states in global memory) and pairs of the batched
 workload."""
 import numpy as np
 import pytest
@@ -47,7 +48,9 @@ def _cases():
     out = [("sphere5k", synth.workload("sphere5k").src, 0.15, 8),
            ("tiny_k4", synth.tiny_pair(700, 720, seed=5).src, 0.3, 4),
            ("tiny_default_radius", synth.tiny_pair(700, 720, seed=5).src, 0.0, 8),
-           ("depth100k", synth.workload("depth100k").src, 0.062, 8)]
+           ("depth100k", synth.workload("depth100k").src, 0.062, 8),
+           # beyond the shared-memory greedy sampling's 200,000 points
+           ("sphere250k", synth.tiny_pair(250000, 1000, seed=3).src, 0.08, 8)]
     for p in synth.batch_pairs(64)[:6]:
         out.append((p.name, p.src, p.params["radius"], 8))
     return out
