@@ -7,7 +7,11 @@
 // path). Compiled with -ffp-contract=off so that every squared distance is
 // evaluated as dx*dx + dy*dy + dz*dz with separate roundings on every host.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <cstring>
 #include <functional>
 #include <iterator>
@@ -24,19 +28,91 @@ int64_t setup_threads(int64_t n, int64_t grain = 4096) {
     return std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw, 64), n / grain));
 }
 
+// A pool of host worker threads (one fewer than the cores), started on
+// first use: a parallel call queues a job of nt tasks, the workers and the
+// calling thread claim tasks from it, and the call returns once every task
+// has run and no worker still holds the job. Calls may come from several
+// threads at once and from inside tasks (the caller can always finish its
+// own job alone), so setup work pays no thread creation per call.
+class SetupPool {
+    struct Job {
+        const std::function<void(int64_t)>* f;
+        int64_t n;
+        std::atomic<int64_t> next{0};
+        int users = 0;   // workers inside run() (under the mutex)
+    };
+    std::mutex m_;
+    std::condition_variable work_, idle_;
+    std::deque<Job*> q_;
+    std::vector<std::thread> th_;
+    bool stop_ = false;
+
+    static void run(Job* j) {
+        for (int64_t k = j->next.fetch_add(1); k < j->n; k = j->next.fetch_add(1)) (*j->f)(k);
+    }
+    void loop() {
+        std::unique_lock<std::mutex> lk(m_);
+        for (;;) {
+            work_.wait(lk, [&] { return stop_ || !q_.empty(); });
+            if (stop_) return;
+            Job* j = q_.front();
+            if (j->next.load() >= j->n) {   // exhausted: off the queue
+                q_.pop_front();
+                continue;
+            }
+            ++j->users;
+            lk.unlock();
+            run(j);
+            lk.lock();
+            if (--j->users == 0) idle_.notify_all();
+        }
+    }
+
+public:
+    explicit SetupPool(int workers) {
+        for (int k = 0; k < workers; ++k) th_.emplace_back([this] { loop(); });
+    }
+    ~SetupPool() {
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            stop_ = true;
+        }
+        work_.notify_all();
+        for (auto& t : th_) t.join();
+    }
+    void parallel(int64_t n, const std::function<void(int64_t)>& f) {
+        Job j;
+        j.f = &f;
+        j.n = n;
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            q_.push_back(&j);
+        }
+        work_.notify_all();
+        run(&j);
+        std::unique_lock<std::mutex> lk(m_);
+        for (auto it = q_.begin(); it != q_.end(); ++it)
+            if (*it == &j) { q_.erase(it); break; }
+        idle_.wait(lk, [&] { return j.users == 0; });
+    }
+    static SetupPool& get() {
+        static SetupPool pool((int)std::max(1u, std::thread::hardware_concurrency()) - 1);
+        return pool;
+    }
+};
+
 // Runs f(chunk, begin, end) over [0, n) split into nt contiguous chunks on
 // the host's cores (setup work; each chunk writes only its own outputs, so
 // results do not depend on the number of threads).
 template <class F>
 void parallel_chunks_idx(int64_t n, int64_t nt, F&& f) {
     if (nt <= 1) { f((int64_t)0, (int64_t)0, n); return; }
-    std::vector<std::thread> th;
     const int64_t per = (n + nt - 1) / nt;
-    for (int64_t t = 0; t < nt; ++t) {
+    const std::function<void(int64_t)> task = [&](int64_t t) {
         const int64_t b = std::min(n, t * per), e = std::min(n, b + per);
-        th.emplace_back([&f, t, b, e]() { f(t, b, e); });
-    }
-    for (auto& x : th) x.join();
+        f(t, b, e);
+    };
+    SetupPool::get().parallel(nt, task);
 }
 
 template <class F>
@@ -226,6 +302,10 @@ void jacobi_eig3(const double Ain[9], double ev[3], double Q[9]) {
 }  // namespace
 
 void nrr_parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f) { parallel_chunks(n, f); }
+int nrr_setup_chunks(int64_t n) { return (int)setup_threads(n); }
+void nrr_parallel_chunks(int64_t n, int nchunks, const std::function<void(int64_t, int64_t, int64_t)>& f) {
+    parallel_chunks_idx(n, nchunks, f);
+}
 
 double nrr_mean_spacing(const double* V, int64_t P, int k) {
     if (P < 2) return 0.0;
@@ -525,60 +605,3 @@ bool nrr_graph_and_spacing(const double* V, int64_t P, double radius, int K, boo
     return true;
 }
 
-// Hilbert index of a 3-D point with 21 bits per axis, after J. Skilling,
-// "Programming the Hilbert curve", AIP Conf. Proc. 707 (2004): the axes are
-// converted in place to the "transposed" Hilbert index, whose bits are then
-// interleaved most significant first.
-static uint64_t hilbert3(uint32_t x, uint32_t y, uint32_t z) {
-    const int bits = 21;
-    uint32_t X[3] = {x, y, z};
-    const uint32_t M = 1u << (bits - 1);
-    for (uint32_t Q = M; Q > 1; Q >>= 1) {
-        const uint32_t Pm = Q - 1;
-        for (int i = 0; i < 3; ++i) {
-            if (X[i] & Q) {
-                X[0] ^= Pm;
-            } else {
-                const uint32_t t = (X[0] ^ X[i]) & Pm;
-                X[0] ^= t;
-                X[i] ^= t;
-            }
-        }
-    }
-    for (int i = 1; i < 3; ++i) X[i] ^= X[i - 1];
-    uint32_t t = 0;
-    for (uint32_t Q = M; Q > 1; Q >>= 1)
-        if (X[2] & Q) t ^= Q - 1;
-    for (int i = 0; i < 3; ++i) X[i] ^= t;
-    uint64_t h = 0;
-    for (int b = bits - 1; b >= 0; --b)
-        for (int i = 0; i < 3; ++i) h = (h << 1) | ((X[i] >> b) & 1u);
-    return h;
-}
-
-void nrr_curve_order(const float* pts, int64_t n, const double lo[3], const double hi[3],
-                      std::vector<int>& order, std::vector<uint64_t>* codes_sorted) {
-    // points ordered along a 3-D Hilbert curve over the common bounding box:
-    // consecutive points are always spatially adjacent (no jumps between
-    // distant regions), so runs of 32 points have compact bounding boxes
-    std::vector<std::pair<uint64_t, int>> kv((size_t)n);
-    parallel_chunks(n, [&](int64_t i0, int64_t i1) {
-        for (int64_t i = i0; i < i1; ++i) {
-            uint32_t c[3];
-            for (int d = 0; d < 3; ++d) {
-                double ext = hi[d] - lo[d];
-                double f = ext > 0 ? ((double)pts[3 * i + d] - lo[d]) / ext : 0.0;
-                f = std::min(std::max(f, 0.0), 1.0);
-                c[d] = (uint32_t)std::llround(f * 2097151.0);
-            }
-            kv[(size_t)i] = {hilbert3(c[0], c[1], c[2]), (int)i};
-        }
-    });
-    parallel_sort(kv);   // (code, index) pairs are distinct
-    order.resize((size_t)n);
-    if (codes_sorted) codes_sorted->resize((size_t)n);
-    for (size_t i = 0; i < kv.size(); ++i) {
-        order[i] = kv[i].second;
-        if (codes_sorted) (*codes_sorted)[i] = kv[i].first;
-    }
-}

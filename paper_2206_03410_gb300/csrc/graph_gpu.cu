@@ -896,6 +896,24 @@ cudaError_t exclusive_sum(Scratch& s, const int* in, int* out, int n, cudaStream
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Hilbert orders of the source and target points (setup of the target leaves
+// and of the source's internal order): one thread per point forms the code
+// (nrr_curve_coord, nrr_hilbert3: the host's functions), then a stable radix
+// sort of (code, index) pairs, whose ties keep the lower index as the host's
+// sort of distinct (code, index) pairs does.
+// ---------------------------------------------------------------------------
+__global__ void curve_codes_kernel(const float* __restrict__ pts, int64_t n, double lo0, double lo1, double lo2,
+                                   double e0, double e1, double e2, unsigned long long* __restrict__ code,
+                                   int* __restrict__ idx) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t cx = nrr_curve_coord(pts[3 * i], lo0, e0), cy = nrr_curve_coord(pts[3 * i + 1], lo1, e1),
+                       cz = nrr_curve_coord(pts[3 * i + 2], lo2, e2);
+        code[i] = nrr_hilbert3(cx, cy, cz);
+        idx[i] = (int)i;
+    }
+}
+
 // Algorithm 1 on the GPU (see the file comment). src: [P][3] float32, host or
 // device. Fills g as nrr_build_graph does. Returns cudaSuccess or the first
 // CUDA error; *rounds receives the number of greedy rounds.
@@ -1139,4 +1157,40 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     lap("copies to the host");
     return cudaSuccess;
 #undef GK
+}
+
+cudaError_t nrr_curve_orders_gpu(const float* src, int64_t P, const float* tgt, int64_t T, const double lo[3],
+                                 const double hi[3], cudaStream_t st, std::vector<int>& src_order,
+                                 std::vector<uint64_t>& src_codes, std::vector<int>& tgt_order,
+                                 std::vector<uint64_t>& tgt_codes) {
+#define CK_(call)                               \
+    do {                                        \
+        cudaError_t e_ = (call);                \
+        if (e_ != cudaSuccess) return e_;       \
+    } while (0)
+    Scratch s;
+    const double e[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    const float* in[2] = {src, tgt};
+    const int64_t n[2] = {P, T};
+    std::vector<int>* ord[2] = {&src_order, &tgt_order};
+    std::vector<uint64_t>* cod[2] = {&src_codes, &tgt_codes};
+    for (int k = 0; k < 2; ++k) {
+        const int64_t m = n[k];
+        float* d_pts;
+        unsigned long long *key, *key_s;
+        int *idx, *idx_s;
+        CK_(s.get(&d_pts, (size_t)m * 3)); CK_(s.get(&key, m)); CK_(s.get(&key_s, m));
+        CK_(s.get(&idx, m)); CK_(s.get(&idx_s, m));
+        CK_(cudaMemcpyAsync(d_pts, in[k], sizeof(float) * 3 * (size_t)m, cudaMemcpyDefault, st));
+        curve_codes_kernel<<<blocks_for(m), kT, 0, st>>>(d_pts, m, lo[0], lo[1], lo[2], e[0], e[1], e[2], key, idx);
+        CK_(cudaGetLastError());
+        CK_(sort_pairs(s, key, key_s, idx, idx_s, (int)m, 63, st));
+        ord[k]->resize((size_t)m);
+        cod[k]->resize((size_t)m);
+        CK_(cudaMemcpyAsync(ord[k]->data(), idx_s, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost, st));
+        CK_(cudaMemcpyAsync(cod[k]->data(), key_s, sizeof(uint64_t) * (size_t)m, cudaMemcpyDeviceToHost, st));
+    }
+    CK_(cudaStreamSynchronize(st));
+    return cudaSuccess;
+#undef CK_
 }

@@ -562,7 +562,28 @@ struct ProblemHash {
         h *= 0xff51afd7ed558ccdull;
         h ^= h >> 33;
     }
+    // arrays of 1 MiB and more: fixed 256 KiB blocks hashed on the host's
+    // cores, their hashes then taken in order (independent of the threads)
     void bytes(const void* p, size_t n) {
+        constexpr size_t kBlock = (size_t)1 << 18;
+        if (n >= ((size_t)1 << 20)) {
+            const unsigned char* b = static_cast<const unsigned char*>(p);
+            const int64_t nb = (int64_t)((n + kBlock - 1) / kBlock);
+            std::vector<uint64_t> sub((size_t)nb);
+            nrr_parallel_chunks(nb, (int)std::min<int64_t>(nb, 16), [&](int64_t, int64_t k0, int64_t k1) {
+                for (int64_t k = k0; k < k1; ++k) {
+                    ProblemHash ph;
+                    ph.bytes_serial(b + (size_t)k * kBlock, std::min(kBlock, n - (size_t)k * kBlock));
+                    sub[(size_t)k] = ph.h;
+                }
+            });
+            for (uint64_t w : sub) word(w);
+            word((uint64_t)n);
+            return;
+        }
+        bytes_serial(p, n);
+    }
+    void bytes_serial(const void* p, size_t n) {
         const unsigned char* b = static_cast<const unsigned char*>(p);
         size_t k = 0;
         for (; k + 8 <= n; k += 8) {
@@ -642,14 +663,14 @@ nrr_status graph_from_mesh(const std::vector<double>& V, int64_t P, const std::v
     return NRR_OK;
 }
 
-// Hilbert orders of source and target over their common bounding box; they
-// depend on the inputs only, so nrr_create computes them on a second host
-// thread while it builds the deformation graph.
+// Hilbert orders of source and target over their common bounding box (on
+// the GPU: nrr_curve_orders_gpu).
 struct CurveOrders {
     double diag = 0.0;
     std::vector<int> src_order, tgt_order;
     std::vector<uint64_t> src_codes, tgt_codes;
-    void compute(const std::vector<float>& src, int64_t P, const std::vector<float>& tgt, int64_t Tn) {
+    cudaError_t compute(const std::vector<float>& src, int64_t P, const std::vector<float>& tgt, int64_t Tn,
+                        cudaStream_t st) {
         double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int64_t i = 0; i < P; ++i)
             for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], (double)src[3 * i + a]); hi[a] = std::max(hi[a], (double)src[3 * i + a]); }
@@ -657,10 +678,8 @@ struct CurveOrders {
             for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], (double)tgt[3 * i + a]); hi[a] = std::max(hi[a], (double)tgt[3 * i + a]); }
         const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
         diag = std::sqrt(dx * dx + dy * dy + dz * dz);
-        // the two orders are independent: the target's on a further thread
-        std::thread tt([&]() { nrr_curve_order(tgt.data(), Tn, lo, hi, tgt_order, &tgt_codes); });
-        nrr_curve_order(src.data(), P, lo, hi, src_order, &src_codes);
-        tt.join();
+        return nrr_curve_orders_gpu(src.data(), P, tgt.data(), Tn, lo, hi, st, src_order, src_codes, tgt_order,
+                                    tgt_codes);
     }
 };
 
@@ -677,7 +696,9 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
     std::vector<uint64_t>& tgt_codes = co.tgt_codes;
     std::vector<int>& tgt_order = co.tgt_order;
     c->src_rank.assign((size_t)P, 0);
-    for (int64_t ii = 0; ii < P; ++ii) c->src_rank[(size_t)c->src_order[(size_t)ii]] = (int)ii;
+    nrr_parallel_for(P, [&](int64_t i0, int64_t i1) {
+        for (int64_t ii = i0; ii < i1; ++ii) c->src_rank[(size_t)c->src_order[(size_t)ii]] = (int)ii;
+    });
 
     // the target's leaves, tiles and the initial correspondence guess depend
     // on the curve orders only: built on another thread beside the
@@ -704,27 +725,33 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         std::vector<float>& sbox = lv.sbox;
         lbox.resize((size_t)nl * 6);
         sbox.resize((size_t)ns * 6);
-        for (size_t k = 0; k < tp.size(); ++k) {
-            if ((int64_t)k < Tn) {
-                const int t = tgt_order[k];
-                tp[k].x = (T)tgt[3 * (size_t)t]; tp[k].y = (T)tgt[3 * (size_t)t + 1]; tp[k].z = (T)tgt[3 * (size_t)t + 2];
-                tp[k].idx = t;
-            } else {
-                tp[k].x = tp[k].y = tp[k].z = std::numeric_limits<T>::infinity();
-                tp[k].idx = 0x7fffffff;
-            }
-        }
-        for (int L = 0; L < nl; ++L) {
-            float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-            for (int k = L * NRR_LEAF; k < std::min<int64_t>(Tn, (int64_t)(L + 1) * NRR_LEAF); ++k) {
-                const int t = tgt_order[(size_t)k];
-                for (int a = 0; a < 3; ++a) {
-                    b[a] = std::min(b[a], tgt[3 * (size_t)t + a]);
-                    b[3 + a] = std::max(b[3 + a], tgt[3 * (size_t)t + a]);
+        nrr_parallel_for((int64_t)tp.size(), [&](int64_t k0, int64_t k1) {
+            for (int64_t k = k0; k < k1; ++k) {
+                if (k < Tn) {
+                    const int t = tgt_order[(size_t)k];
+                    tp[(size_t)k].x = (T)tgt[3 * (size_t)t];
+                    tp[(size_t)k].y = (T)tgt[3 * (size_t)t + 1];
+                    tp[(size_t)k].z = (T)tgt[3 * (size_t)t + 2];
+                    tp[(size_t)k].idx = t;
+                } else {
+                    tp[(size_t)k].x = tp[(size_t)k].y = tp[(size_t)k].z = std::numeric_limits<T>::infinity();
+                    tp[(size_t)k].idx = 0x7fffffff;
                 }
             }
-            std::memcpy(&lbox[(size_t)L * 6], b, sizeof(b));
-        }
+        });
+        nrr_parallel_for(nl, [&](int64_t L0, int64_t L1) {
+            for (int64_t L = L0; L < L1; ++L) {
+                float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+                for (int64_t k = L * NRR_LEAF; k < std::min<int64_t>(Tn, (L + 1) * NRR_LEAF); ++k) {
+                    const int t = tgt_order[(size_t)k];
+                    for (int a = 0; a < 3; ++a) {
+                        b[a] = std::min(b[a], tgt[3 * (size_t)t + a]);
+                        b[3 + a] = std::max(b[3 + a], tgt[3 * (size_t)t + a]);
+                    }
+                }
+                std::memcpy(&lbox[(size_t)L * 6], b, sizeof(b));
+            }
+        });
         for (int S = 0; S < ns; ++S) {
             float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
             for (int L = S * 32; L < std::min(nl, (S + 1) * 32); ++L)
@@ -752,29 +779,45 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         std::vector<int>& rho0 = lv.rho0;
         u0.resize((size_t)(3 * P));
         rho0.resize((size_t)P);
-        for (int64_t ii = 0; ii < P; ++ii) {
-            size_t pos = (size_t)(std::lower_bound(tgt_codes.begin(), tgt_codes.end(), src_codes[(size_t)ii]) - tgt_codes.begin());
-            if (pos >= (size_t)Tn) pos = (size_t)Tn - 1;
-            for (int a = 0; a < 3; ++a) u0[(size_t)(a * P + ii)] = a == 0 ? tp[pos].x : (a == 1 ? tp[pos].y : tp[pos].z);
-            rho0[(size_t)ii] = tp[pos].idx;
-        }
+        nrr_parallel_for(P, [&](int64_t i0, int64_t i1) {
+            for (int64_t ii = i0; ii < i1; ++ii) {
+                size_t pos = (size_t)(std::lower_bound(tgt_codes.begin(), tgt_codes.end(), src_codes[(size_t)ii]) -
+                                      tgt_codes.begin());
+                if (pos >= (size_t)Tn) pos = (size_t)Tn - 1;
+                for (int a = 0; a < 3; ++a)
+                    u0[(size_t)(a * P + ii)] = a == 0 ? tp[pos].x : (a == 1 ? tp[pos].y : tp[pos].z);
+                rho0[(size_t)ii] = tp[pos].idx;
+            }
+        });
     })};
 
-    // source SoA and influence CSR in internal order
+    // source SoA and influence CSR in internal order (per point the count,
+    // then the rows, on the host's cores)
     std::vector<T> v((size_t)(3 * P));
     std::vector<int> infl_ptr((size_t)P + 1, 0), infl_node;
     std::vector<T> infl_w;
-    for (int64_t ii = 0; ii < P; ++ii) {
-        const int i = c->src_order[(size_t)ii];
-        for (int a = 0; a < 3; ++a) v[(size_t)(a * P + ii)] = (T)src[3 * (size_t)i + a];
-        for (int s = 0; s < K; ++s) {
-            const int j = g.nidx[(size_t)i * K + s];
-            if (j < 0) break;
-            infl_node.push_back(j);
-            infl_w.push_back((T)g.w[(size_t)i * K + s]);
+    nrr_parallel_for(P, [&](int64_t i0, int64_t i1) {
+        for (int64_t ii = i0; ii < i1; ++ii) {
+            const int i = c->src_order[(size_t)ii];
+            for (int a = 0; a < 3; ++a) v[(size_t)(a * P + ii)] = (T)src[3 * (size_t)i + a];
+            int k = 0;
+            while (k < K && g.nidx[(size_t)i * K + k] >= 0) ++k;
+            infl_ptr[(size_t)ii + 1] = k;
         }
-        infl_ptr[(size_t)ii + 1] = (int)infl_node.size();
-    }
+    });
+    for (int64_t ii = 0; ii < P; ++ii) infl_ptr[(size_t)ii + 1] += infl_ptr[(size_t)ii];
+    infl_node.resize((size_t)infl_ptr[(size_t)P]);
+    infl_w.resize((size_t)infl_ptr[(size_t)P]);
+    nrr_parallel_for(P, [&](int64_t i0, int64_t i1) {
+        for (int64_t ii = i0; ii < i1; ++ii) {
+            const int i = c->src_order[(size_t)ii];
+            for (int k = 0, o = infl_ptr[(size_t)ii]; o < infl_ptr[(size_t)ii + 1]; ++k, ++o) {
+                infl_node[(size_t)o] = g.nidx[(size_t)i * K + k];
+                infl_w[(size_t)o] = (T)g.w[(size_t)i * K + k];
+            }
+        }
+    });
+    tm.lap("  source SoA + influence CSR");
     std::vector<T> p((size_t)N * 3);
     for (int j = 0; j < N; ++j)
         for (int a = 0; a < 3; ++a) p[(size_t)3 * j + a] = (T)src[3 * (size_t)g.nodes[(size_t)j] + a];
@@ -816,6 +859,7 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         auto first = bc.begin() + bp[(size_t)a], last = bc.begin() + bp[(size_t)a + 1];
         return (int)(std::lower_bound(first, last, b) - bc.begin());
     };
+    tm.lap("  edges + BSR pattern");
     // per-block contribution lists (point, slot_row, slot_col), by point:
     // the block of every (point, slot, slot) in parallel, then a counting
     // sort by block that keeps point order
@@ -833,20 +877,46 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
                     eblk[(size_t)o++] = block_of(infl_node[(size_t)sa], infl_node[(size_t)sb]);
         }
     });
-    std::vector<int> ent_cnt((size_t)c->nblk + 1, 0);
-    for (int b : eblk) ent_cnt[(size_t)b + 1]++;
-    for (int b = 0; b < c->nblk; ++b) ent_cnt[(size_t)b + 1] += ent_cnt[(size_t)b];
-    std::vector<int> ent((size_t)ent_cnt[(size_t)c->nblk]);
-    std::vector<int> fillp(ent_cnt.begin(), ent_cnt.end() - 1);
-    for (int64_t ii = 0; ii < P; ++ii) {
-        const int b0 = infl_ptr[(size_t)ii];
-        int64_t o = pent[(size_t)ii];
-        for (int sa = b0; sa < infl_ptr[(size_t)ii + 1]; ++sa)
-            for (int sb = b0; sb < infl_ptr[(size_t)ii + 1]; ++sb) {
-                const int blk = eblk[(size_t)o++];
-                ent[(size_t)fillp[(size_t)blk]++] = (int)((ii << 6) | ((sa - b0) << 3) | (sb - b0));
+    tm.lap("  entry blocks");
+    // stable counting sort by block: per chunk of points a histogram, then
+    // each chunk's start in every block (chunks in point order), then the
+    // chunks fill their entries in parallel
+    const int nblk = c->nblk;
+    const int nch = (int)std::max<int64_t>(
+        1, std::min<int64_t>(nrr_setup_chunks(P), ((int64_t)1 << 24) / std::max(1, nblk)));
+    std::vector<int> hist((size_t)nch * nblk, 0);
+    nrr_parallel_chunks(P, nch, [&](int64_t t, int64_t i0, int64_t i1) {
+        int* h = hist.data() + (size_t)t * nblk;
+        for (int64_t o = pent[(size_t)i0]; o < pent[(size_t)i1]; ++o) h[eblk[(size_t)o]]++;
+    });
+    std::vector<int> ent_cnt((size_t)nblk + 1, 0), run((size_t)nblk, 0);
+    nrr_parallel_for(nblk, [&](int64_t b0, int64_t b1) {
+        for (int t = 0; t < nch; ++t)
+            for (int64_t b = b0; b < b1; ++b) run[(size_t)b] += hist[(size_t)t * nblk + b];
+    });
+    for (int b = 0; b < nblk; ++b) ent_cnt[(size_t)b + 1] = ent_cnt[(size_t)b] + run[(size_t)b];
+    nrr_parallel_for(nblk, [&](int64_t b0, int64_t b1) {
+        for (int64_t b = b0; b < b1; ++b) run[(size_t)b] = ent_cnt[(size_t)b];
+        for (int t = 0; t < nch; ++t)
+            for (int64_t b = b0; b < b1; ++b) {
+                const int k = hist[(size_t)t * nblk + b];
+                hist[(size_t)t * nblk + b] = run[(size_t)b];
+                run[(size_t)b] += k;
             }
-    }
+    });
+    std::vector<int> ent((size_t)ent_cnt[(size_t)nblk]);
+    nrr_parallel_chunks(P, nch, [&](int64_t t, int64_t i0, int64_t i1) {
+        int* fillp = hist.data() + (size_t)t * nblk;
+        for (int64_t ii = i0; ii < i1; ++ii) {
+            const int b0 = infl_ptr[(size_t)ii];
+            int64_t o = pent[(size_t)ii];
+            for (int sa = b0; sa < infl_ptr[(size_t)ii + 1]; ++sa)
+                for (int sb = b0; sb < infl_ptr[(size_t)ii + 1]; ++sb) {
+                    const int blk = eblk[(size_t)o++];
+                    ent[(size_t)fillp[blk]++] = (int)((ii << 6) | ((sa - b0) << 3) | (sb - b0));
+                }
+        }
+    });
     tm.lap("BSR + contribution lists");
     // connected components of the node graph (union-find over the edges),
     // nodes listed by component in increasing order
@@ -878,28 +948,34 @@ nrr_status build_device(nrr_ctx* c, const std::vector<float>& src, const std::ve
         std::vector<int> fill(comp_ptr.begin(), comp_ptr.end() - 1);
         for (int j = 0; j < N; ++j) comp_nodes[(size_t)fill[(size_t)label[(size_t)j]]++] = j;
     }
+    tm.lap("  components");
     // one weight per entry: w_in on a diagonal block (the entry's two slots
     // are the same node), w_in w_ik (product in double, rounded once) off it
     std::vector<T> ent_q(ent.size());
-    for (size_t e = 0; e < ent.size(); ++e) {
-        const int ii = ent[e] >> 6, sa = (ent[e] >> 3) & 7, sb = ent[e] & 7;
-        const double wa_ = (double)infl_w[(size_t)infl_ptr[(size_t)ii] + sa];
-        const double wb_ = (double)infl_w[(size_t)infl_ptr[(size_t)ii] + sb];
-        ent_q[e] = (T)(sa == sb ? wa_ : wa_ * wb_);
-    }
+    nrr_parallel_for((int64_t)ent.size(), [&](int64_t e0, int64_t e1) {
+        for (int64_t e = e0; e < e1; ++e) {
+            const int ii = ent[(size_t)e] >> 6, sa = (ent[(size_t)e] >> 3) & 7, sb = ent[(size_t)e] & 7;
+            const double wa_ = (double)infl_w[(size_t)infl_ptr[(size_t)ii] + sa];
+            const double wb_ = (double)infl_w[(size_t)infl_ptr[(size_t)ii] + sb];
+            ent_q[(size_t)e] = (T)(sa == sb ? wa_ : wa_ * wb_);
+        }
+    });
     std::vector<int> blk_row((size_t)c->nblk);
     for (int n = 0; n < N; ++n)
         for (int b = bp[(size_t)n]; b < bp[(size_t)n + 1]; ++b) blk_row[(size_t)b] = n;
     std::vector<T> pbar((size_t)(3 * P), (T)0);
-    for (int64_t ii = 0; ii < P; ++ii) {
-        double acc[3] = {0, 0, 0};
-        for (int s = infl_ptr[(size_t)ii]; s < infl_ptr[(size_t)ii + 1]; ++s) {
-            const int j = infl_node[(size_t)s];
-            for (int a = 0; a < 3; ++a)
-                acc[a] += (double)infl_w[(size_t)s] * (double)src[3 * (size_t)g.nodes[(size_t)j] + a];
+    nrr_parallel_for(P, [&](int64_t i0, int64_t i1) {
+        for (int64_t ii = i0; ii < i1; ++ii) {
+            double acc[3] = {0, 0, 0};
+            for (int s = infl_ptr[(size_t)ii]; s < infl_ptr[(size_t)ii + 1]; ++s) {
+                const int j = infl_node[(size_t)s];
+                for (int a = 0; a < 3; ++a)
+                    acc[a] += (double)infl_w[(size_t)s] * (double)src[3 * (size_t)g.nodes[(size_t)j] + a];
+            }
+            for (int a = 0; a < 3; ++a) pbar[(size_t)(a * P + ii)] = (T)acc[a];
         }
-        for (int a = 0; a < 3; ++a) pbar[(size_t)(a * P + ii)] = (T)acc[a];
-    }
+    });
+    tm.lap("  entry weights, pbar");
     leaves_thread.t.join();
     const int nl = lv.nl, ns = lv.ns, nm = lv.nm;
     c->n_leaves = nl;
@@ -1721,12 +1797,9 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
         if (!finite3(tmp)) return fail(nullptr, NRR_E_INVALID, "non-finite target normals");
     }
     tm.lap("inputs");
-    // the curve orders on a second thread, beside l-bar and Algorithm 1
     CurveOrders co;
-    struct Joiner {
-        std::thread t;
-        ~Joiner() { if (t.joinable()) t.join(); }
-    } orders_thread{std::thread([&]() { co.compute(src, P, tgt, T); })};
+    CK(co.compute(src, P, tgt, T, c->stream));
+    tm.lap("curve orders");
     // l-bar, radius and the deformation graph (Algorithm 1)
     std::vector<double> V(src.begin(), src.end());
     const bool need_lbar = prm.graph_radius <= 0 || prm.nu_r <= 0 || prm.nu_a_min <= 0;
@@ -1774,8 +1847,7 @@ nrr_status nrr_create(nrr_ctx** out, const float* src_xyz, const float* src_nrm,
     CK(cudaMemcpy(c->d_states1, &c->d_state, sizeof(NrrState*), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&c->d_ctrl, 2 * sizeof(int)));
     CK(cudaMallocHost(&c->h_ctrl, 2 * sizeof(int)));
-    orders_thread.t.join();
-    tm.lap("curve orders (joined)");
+    tm.lap("hash + state buffers");
     nrr_status st = c->fp64 ? build_device<double>(c, src, tgt, co, tm) : build_device<float>(c, src, tgt, co, tm);
     if (st != NRR_OK) return st;
     if (c->fp64) choose_solver<double>(c); else choose_solver<float>(c);

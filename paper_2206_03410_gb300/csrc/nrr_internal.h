@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <functional>
 #include <string>
 #include <vector>
@@ -67,6 +68,11 @@ struct HostGraph {
 // Runs f(begin, end) over [0, n) in contiguous chunks on the host's cores
 // (setup work; f writes only the outputs of its own range).
 void nrr_parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f);
+// The number of chunks nrr_parallel_for would use for n items, and f(chunk,
+// begin, end) over [0, n) split into nchunks contiguous chunks, each on its
+// own host thread (chunk boundaries depend on n and nchunks only).
+int nrr_setup_chunks(int64_t n);
+void nrr_parallel_chunks(int64_t n, int nchunks, const std::function<void(int64_t, int64_t, int64_t)>& f);
 double nrr_mean_spacing(const double* V, int64_t P, int k);
 void nrr_build_graph(const double* V, int64_t P, double R, int K, HostGraph& g);
 // Pieces of Algorithm 1 shared by the point-cloud and mesh constructions:
@@ -97,9 +103,57 @@ double nrr_mesh_mean_edge(const double* V, const int* F, int64_t nF);
 // NaN); with a given radius the two run concurrently. Returns false (and
 // builds nothing) if the radius would be 5 l-bar = 0.
 bool nrr_graph_and_spacing(const double* V, int64_t P, double radius, int K, bool need_lbar, HostGraph& g);
-void nrr_curve_order(const float* pts, int64_t n, const double lo[3],
-                      const double hi[3], std::vector<int>& order,
-                      std::vector<uint64_t>* codes_sorted);
+
+#ifdef __CUDACC__
+#define NRR_HD __host__ __device__
+#else
+#define NRR_HD
+#endif
+// Hilbert index of a 3-D point with 21 bits per axis, after J. Skilling,
+// "Programming the Hilbert curve", AIP Conf. Proc. 707 (2004): the axes are
+// converted in place to the "transposed" Hilbert index, whose bits are then
+// interleaved most significant first. (Host and device: one definition.)
+NRR_HD inline uint64_t nrr_hilbert3(uint32_t x, uint32_t y, uint32_t z) {
+    const int bits = 21;
+    uint32_t X[3] = {x, y, z};
+    const uint32_t M = 1u << (bits - 1);
+    for (uint32_t Q = M; Q > 1; Q >>= 1) {
+        const uint32_t Pm = Q - 1;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= Pm;
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & Pm;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    for (int i = 1; i < 3; ++i) X[i] ^= X[i - 1];
+    uint32_t t = 0;
+    for (uint32_t Q = M; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    for (int i = 0; i < 3; ++i) X[i] ^= t;
+    uint64_t h = 0;
+    for (int b = bits - 1; b >= 0; --b)
+        for (int i = 0; i < 3; ++i) h = (h << 1) | ((X[i] >> b) & 1u);
+    return h;
+}
+// the 21-bit grid coordinate of p on an axis of the bounding box [lo, lo + ext]
+// (IEEE double subtraction, division and product: the same on host and device)
+NRR_HD inline uint32_t nrr_curve_coord(float p, double lo, double ext) {
+    double f = ext > 0 ? ((double)p - lo) / ext : 0.0;
+    f = fmin(fmax(f, 0.0), 1.0);
+    return (uint32_t)llround(f * 2097151.0);
+}
+// graph_gpu.cu: the Hilbert orders of the source and the target (host
+// arrays [n][3]) over the box [lo, hi], on the GPU: per point its code
+// (nrr_curve_coord per axis, nrr_hilbert3), then a stable radix sort of
+// (code, index); the orders and the sorted codes come back to the host.
+cudaError_t nrr_curve_orders_gpu(const float* src, int64_t P, const float* tgt, int64_t T, const double lo[3],
+                                 const double hi[3], cudaStream_t st, std::vector<int>& src_order,
+                                 std::vector<uint64_t>& src_codes, std::vector<int>& tgt_order,
+                                 std::vector<uint64_t>& tgt_codes);
 
 // graph_gpu.cu: Algorithm 1 on the GPU (the same graph as nrr_build_graph);
 // src [P][3] float32 host or device; *rounds = greedy rounds run; with lbar

@@ -31,7 +31,7 @@ def _worker(rank, world, port, out):
 
 def test_reduce_over_ranks_gloo_world2():
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     assert out[0] == (12.5, 12.0) and out[1] == (12.5, 12.0)
