@@ -1,6 +1,7 @@
 // C ABI of the registration library (include/nrr.h): context creation,
 // per-pass launch sequence captured in a CUDA graph, and accessors.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -401,6 +402,7 @@ cudaError_t launch_pass(nrr_ctx* c) {
 cudaError_t launch_pass_any(nrr_ctx* c) { return c->fp64 ? launch_pass<double>(c) : launch_pass<float>(c); }
 
 // Passes of one nrr_solve whose summaries the device-side loop records.
+constexpr int kBatchCreateThreads = 8;   // host threads of nrr_batch_create
 constexpr int kHistCap = 8192;
 
 // The summary of a context state after a pass (host and device).
@@ -2768,15 +2770,38 @@ nrr_status nrr_batch_create(nrr_batch** out, int n_pairs, const float* const* sr
         BK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
         b->own_stream = true;
     }
-    for (int i = 0; i < n_pairs; ++i) {
-        nrr_ctx* c = nullptr;
-        const nrr_params* pp = params ? (params_per_pair ? &params[i] : params) : nullptr;
-        nrr_params q;
-        if (pp) q = *pp; else nrr_params_default(&q);
-        if (q.solve_ctas == 0) q.solve_ctas = -1;   // smallest cluster inside a batch
-        nrr_status st = nrr_create(&c, src_xyz[i], nullptr, P[i], tgt_xyz[i], nullptr, T[i], &q, nullptr);
-        if (st != NRR_OK) return batch_fail(b, st, "pair " + std::to_string(i) + ": " + g_last_error);
-        b->ctx.push_back(c);
+    // the pairs' contexts are independent: created by a few host threads at
+    // once (each on its own stream, on the caller's device), kept in pair
+    // order; the first failing pair (lowest index) is reported
+    {
+        int device = 0;
+        BK(cudaGetDevice(&device));
+        std::vector<nrr_ctx*> made((size_t)n_pairs, nullptr);
+        std::vector<nrr_status> stat((size_t)n_pairs, NRR_OK);
+        std::vector<std::string> msg((size_t)n_pairs);
+        std::atomic<int> next{0};
+        auto work = [&]() {
+            if (cudaSetDevice(device) != cudaSuccess) return;
+            for (int i = next.fetch_add(1); i < n_pairs; i = next.fetch_add(1)) {
+                const nrr_params* pp = params ? (params_per_pair ? &params[i] : params) : nullptr;
+                nrr_params q;
+                if (pp) q = *pp; else nrr_params_default(&q);
+                if (q.solve_ctas == 0) q.solve_ctas = -1;   // smallest cluster inside a batch
+                stat[(size_t)i] = nrr_create(&made[(size_t)i], src_xyz[i], nullptr, P[i], tgt_xyz[i], nullptr, T[i],
+                                             &q, nullptr);
+                if (stat[(size_t)i] != NRR_OK) msg[(size_t)i] = g_last_error;
+            }
+        };
+        const int nth = std::max(1, std::min(n_pairs, kBatchCreateThreads));
+        std::vector<std::thread> th;
+        for (int k = 1; k < nth; ++k) th.emplace_back(work);
+        work();
+        for (auto& t : th) t.join();
+        for (int i = 0; i < n_pairs; ++i) b->ctx.push_back(made[(size_t)i]);   // destroyed with the batch
+        for (int i = 0; i < n_pairs; ++i)
+            if (stat[(size_t)i] != NRR_OK || !made[(size_t)i])
+                return batch_fail(b, stat[(size_t)i] != NRR_OK ? stat[(size_t)i] : NRR_E_CUDA,
+                                  "pair " + std::to_string(i) + ": " + msg[(size_t)i]);
     }
     const int n = n_pairs;
     std::vector<NrrState*> sts((size_t)n);
