@@ -15,41 +15,6 @@ constexpr int kM = NRR_AA_MMAX;
 constexpr int kGroups = kThreads / (2 * kM);
 static_assert(2 * kM == 16 && kThreads >= kM * kM, "thread mapping of the grid sums");
 
-// Solves (Gm + lam I) theta = rhs for the m x m Gram matrix (row-major,
-// leading dimension kM) by an LDL^T factorisation in FP64: one division per
-// column on the serial path and no square roots. Returns false if a pivot is
-// not positive (the Gram matrix plus ridge is not numerically positive
-// definite). Gm is overwritten with L (strictly lower part) and D^-1.
-__device__ bool gram_solve(double* Gm, const double* rhs, int m, double* th) {
-    double dinv[kM];
-    for (int j = 0; j < m; ++j) {
-        // column j of L and pivot d_j, with L_jk d_k held in Gm[k][j] (k < j)
-        double dj = Gm[j * kM + j];
-        for (int k = 0; k < j; ++k) dj -= Gm[j * kM + k] * Gm[k * kM + j];
-        if (!(dj > 0)) return false;
-        dinv[j] = 1.0 / dj;
-        for (int i = j + 1; i < m; ++i) {
-            double t = Gm[i * kM + j];
-            for (int k = 0; k < j; ++k) t -= Gm[i * kM + k] * Gm[k * kM + j];
-            Gm[j * kM + i] = t;                 // L_ij d_j (upper part, scratch)
-            Gm[i * kM + j] = t * dinv[j];       // L_ij
-        }
-    }
-    // L y = rhs, theta = D^-1 y, L^T theta = theta
-    for (int i = 0; i < m; ++i) {
-        double t = rhs[i];
-        for (int k = 0; k < i; ++k) t -= Gm[i * kM + k] * th[k];
-        th[i] = t;
-    }
-    for (int i = 0; i < m; ++i) th[i] *= dinv[i];
-    for (int i = m - 1; i >= 0; --i) {
-        double t = th[i];
-        for (int k = i + 1; k < m; ++k) t -= Gm[k * kM + i] * th[k];
-        th[i] = t;
-    }
-    return true;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads) aa_dots_kernel(DevProblem<T> d) {
     __shared__ double sh[kThreads / 32][2 * kM];
@@ -130,44 +95,7 @@ __global__ void __launch_bounds__(kThreads) aa_dots_kernel(DevProblem<T> d) {
     if (threadIdx.x != 0) return;
     st->cnt_energy = 0;
     double th[kM];
-    bool ok = false;
-    if (mk > 0) {
-        double Gm[kM * kM], rhs[kM];
-        double tr = 0.0;
-        for (int a = 0; a < mk; ++a) {
-            for (int b = 0; b < mk; ++b) {
-                double v;
-                if (a == slot) v = tot[b];
-                else if (b == slot) v = tot[a];
-                else v = s_gram[a * kM + b];
-                Gm[a * kM + b] = v;
-            }
-            rhs[a] = tot[kM + a];
-            tr += Gm[a * kM + a];
-        }
-        // the new Gram row is kept for the next passes
-        for (int b = 0; b < mk; ++b) {
-            st->gram[slot * kM + b] = tot[b];
-            st->gram[b * kM + slot] = tot[b];
-        }
-        // ridge relative to the mean diagonal entry
-        const double lam = 1e-10 * tr / mk;
-        for (int a = 0; a < mk; ++a) Gm[a * kM + a] += lam;
-        ok = gram_solve(Gm, rhs, mk, th);
-        if (ok) {
-            double nrm = 0.0;
-            for (int i = 0; i < mk; ++i) nrm += th[i] * th[i];
-            ok = isfinite(nrm) && nrm <= 1e8;   // |theta| <= 1e4
-        }
-    }
-    for (int i = 0; i < kM; ++i) st->theta[i] = (ok && i < mk) ? th[i] : 0.0;
-    st->aa_mk = ok ? mk : 0;
-    st->aa_count = mk;
-    st->aa_head = insert ? (slot + 1) % aa_m : slot;
-    st->n_solves_stage += 1;
-    st->n_solves += 1;
-    st->pending_stop = 1;
-    st->solved = 1;
+    nrr_aa_finish(st, s_gram, tot, mk, slot, insert, aa_m, th, true);
 }
 
 // X^(k+1) = G - sum_b theta_b dG_b; F and G kept for the next differences.

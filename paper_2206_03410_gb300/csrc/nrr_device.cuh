@@ -207,6 +207,128 @@ cudaError_t nrr_launch_adjoint(const DevProblem<T>& d, const T* lam, const T* Xn
 template <typename T>
 cudaError_t nrr_launch_to_t(const double* in, T* out, int n, cudaStream_t s);
 
+// 1/x for x > 0: a float reciprocal refined by two Newton steps in double
+// (relative error about 2^-52; a double division costs several times more
+// on this GPU's FP64 units), or the division when x lies outside the float
+// range.
+__device__ __forceinline__ double nrr_recip(double x) {
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / x;
+    double r = (double)__frcp_rn((float)x);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
+// The m x m Anderson system for a compile-time m (every array in
+// registers: one thread runs it, and local-memory round trips would
+// dominate): the Gram matrix of the ring with the new slot's row tot[0..M)
+// (gram_old: the kept entries, by ring slot), a ridge of 1e-10 times the
+// mean diagonal entry, right-hand side tot[kM..kM+M), solved by an LDL^T
+// factorisation in FP64 (one reciprocal per column on the serial path, no
+// square roots; L_ij d_j kept in the upper part as scratch). Returns false
+// if a pivot is not positive (the Gram matrix plus ridge is not numerically
+// positive definite).
+template <int M>
+__device__ __forceinline__ bool nrr_aa_solve(const double* gram_old, const double (&tot)[2 * NRR_AA_MMAX], int slot,
+                                             double (&th)[NRR_AA_MMAX]) {
+    constexpr int kM = NRR_AA_MMAX;
+    double Gm[M][M], rhs[M], dinv[M];
+    double tr = 0.0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+#pragma unroll
+        for (int b = 0; b < M; ++b) Gm[a][b] = a == slot ? tot[b] : (b == slot ? tot[a] : gram_old[a * kM + b]);
+        rhs[a] = tot[kM + a];
+        tr += Gm[a][a];
+    }
+    const double lam = 1e-10 * tr / M;
+#pragma unroll
+    for (int a = 0; a < M; ++a) Gm[a][a] += lam;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        double dj = Gm[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) dj -= Gm[j][k] * Gm[k][j];
+        if (!(dj > 0)) return false;
+        dinv[j] = nrr_recip(dj);
+#pragma unroll
+        for (int i = j + 1; i < M; ++i) {
+            double t = Gm[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= Gm[i][k] * Gm[k][j];
+            Gm[j][i] = t;
+            Gm[i][j] = t * dinv[j];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        double t = rhs[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t -= Gm[i][k] * th[k];
+        th[i] = t;
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) th[i] *= dinv[i];
+#pragma unroll
+    for (int i = M - 1; i >= 0; --i) {
+        double t = th[i];
+#pragma unroll
+        for (int k = i + 1; k < M; ++k) t -= Gm[k][i] * th[k];
+        th[i] = t;
+    }
+    return true;
+}
+
+// The Anderson step after its sums (one thread): the system of
+// nrr_aa_solve for the ring's mk entries, theta set to 0 if the solve
+// fails or |theta| > 1e4. th receives theta (kM entries). With `write` the
+// state is updated: the kept Gram row, theta, the ring counters and the
+// solve counters. Returns the number of coefficients used (mk, or 0).
+__device__ inline int nrr_aa_finish(NrrState* st, const double* gram_old, const double (&tot)[2 * NRR_AA_MMAX],
+                                    int mk, int slot, bool insert, int aa_m, double (&th)[NRR_AA_MMAX], bool write) {
+    constexpr int kM = NRR_AA_MMAX;
+    static_assert(kM == 8, "one case per ring size");
+    bool ok = false;
+    switch (mk) {
+        case 1: ok = nrr_aa_solve<1>(gram_old, tot, slot, th); break;
+        case 2: ok = nrr_aa_solve<2>(gram_old, tot, slot, th); break;
+        case 3: ok = nrr_aa_solve<3>(gram_old, tot, slot, th); break;
+        case 4: ok = nrr_aa_solve<4>(gram_old, tot, slot, th); break;
+        case 5: ok = nrr_aa_solve<5>(gram_old, tot, slot, th); break;
+        case 6: ok = nrr_aa_solve<6>(gram_old, tot, slot, th); break;
+        case 7: ok = nrr_aa_solve<7>(gram_old, tot, slot, th); break;
+        case 8: ok = nrr_aa_solve<8>(gram_old, tot, slot, th); break;
+        default: break;
+    }
+    if (ok) {
+        double nrm = 0.0;
+#pragma unroll
+        for (int i = 0; i < kM; ++i)
+            if (i < mk) nrm += th[i] * th[i];
+        ok = isfinite(nrm) && nrm <= 1e8;   // |theta| <= 1e4
+    }
+#pragma unroll
+    for (int i = 0; i < kM; ++i) th[i] = (ok && i < mk) ? th[i] : 0.0;
+    if (write) {
+        // the new Gram row is kept for the next passes
+#pragma unroll
+        for (int b = 0; b < kM; ++b)
+            if (b < mk) {
+                st->gram[slot * kM + b] = tot[b];
+                st->gram[b * kM + slot] = tot[b];
+            }
+#pragma unroll
+        for (int i = 0; i < kM; ++i) st->theta[i] = th[i];
+        st->aa_mk = ok ? mk : 0;
+        st->aa_count = mk;
+        st->aa_head = insert ? (slot + 1) % aa_m : slot;
+        st->n_solves_stage += 1;
+        st->n_solves += 1;
+        st->pending_stop = 1;
+        st->solved = 1;
+    }
+    return ok ? mk : 0;
+}
+
 // Stage transition of Algorithm 2 (halve nu_a and nu_r, recompute alpha and
 // beta with Eq. WeightSettings, restart the stage). Single device thread.
 __device__ __forceinline__ void nrr_stage_weights(NrrState* st) {
