@@ -532,7 +532,7 @@ void nrr_finish_graph(const double* V, int64_t P, double R, int K, const std::ve
         double sum = 0.0;
         for (int s = 0; s < n; ++s) {
             double a = 1.0 - L[(size_t)s].first / R2;
-            raw[s] = std::pow(a, 3.0);
+            raw[s] = a * a * a;
         }
         for (int s = 0; s < n; ++s) sum += raw[s];
         for (int s = 0; s < n; ++s) {

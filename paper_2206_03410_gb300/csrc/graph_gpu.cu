@@ -290,9 +290,12 @@ template <int KK>
 __global__ void spacing_kernel(GridView g, const float4* __restrict__ gf, const int* __restrict__ gitem,
                                const double* __restrict__ V, int P, double* __restrict__ per_point,
                                int* __restrict__ n_bad, int* __restrict__ bad, int bad_cap) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-        const double x = V[3 * (int64_t)i], y = V[3 * (int64_t)i + 1], z = V[3 * (int64_t)i + 2];
-        const float4 pf = make_float4((float)x, (float)y, (float)z, 0.f);
+    // points in grid-cell order (slot sl holds point gitem[sl]): the lanes
+    // of a warp share their cells, so their candidate loads coincide
+    for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl < P; sl += gridDim.x * blockDim.x) {
+        const int i = gitem[sl];
+        const double x = g.xyz[3 * (int64_t)sl], y = g.xyz[3 * (int64_t)sl + 1], z = g.xyz[3 * (int64_t)sl + 2];
+        const float4 pf = gf[sl];
         long long c[3];
         g.cell(x, y, z, c);
         int rs0[27], rs1[27];
@@ -311,14 +314,14 @@ __global__ void spacing_kernel(GridView g, const float4* __restrict__ gf, const 
         for (int t = 0; t < KK; ++t) bf[t] = INFINITY;
         for (int k = 0; k < nc; ++k)
             for (int s = rs0[k]; s < rs1[k]; ++s)
-                if (gitem[s] != i) topk_insert(bf, sqdf(pf, gf[s]));
+                if (s != sl) topk_insert(bf, sqdf(pf, gf[s]));
         const float thr = knn_filter(bf[KK - 1]);
         double best[KK];
 #pragma unroll
         for (int t = 0; t < KK; ++t) best[t] = INFINITY;
         for (int k = 0; k < nc; ++k)
             for (int s = rs0[k]; s < rs1[k]; ++s)
-                if (sqdf(pf, gf[s]) <= thr && gitem[s] != i)
+                if (sqdf(pf, gf[s]) <= thr && s != sl)
                     topk_insert(best, sqd(x, y, z, g.xyz[3 * s], g.xyz[3 * s + 1], g.xyz[3 * s + 2]));
         if (!(best[KK - 1] <= g.h * g.h)) {
             const int k = atomicAdd(n_bad, 1);
@@ -509,14 +512,16 @@ __global__ void __launch_bounds__(1024) greedy_kernel(GridView g, const int* __r
 // strictly within R of rank r's point that comes after it in the order has
 // a rank in (r, rend[r]). The CTA holds the ranks [lo, hi) (at most
 // kGreedyWin, slot r mod kGreedyWin) with their coordinates (float and
-// double), rend and state (0 open, 1 node, 2 covered) in shared memory.
-// Per node f: warp 0 finds the next open rank (4 ranks per lane, a
-// ballot); the window moves to [f, f + kGreedyWin) if it does not reach
-// rend[f]; every thread tests ranks of (f, rend[f]): a float distance
-// test with a margin (a float squared distance exceeds the exact one by
-// less than a relative 4e-7) selects the candidates, the double distance
-// decides as everywhere else. Used when every rend[r] - r fits the window
-// (*span); greedy_kernel runs otherwise.
+// double), rend and state (0 open, 2 covered) in shared memory. Per node f:
+// every warp finds the next open rank itself (4 ranks per lane, a ballot;
+// the same rank in every warp); the window moves to [f, f + kGreedyWin) if
+// it does not reach rend[f]; every thread tests the open ranks of
+// (f, rend[f]) in float: a float squared distance is within a relative
+// 4e-7 of the exact one, so below R^2 (1 - 1e-5) the point is covered,
+// above R^2 (1 + 1e-5) it is not, and the thin shell between is decided by
+// the double distance, as everywhere else; one CTA barrier per node. Used
+// when every rend[r] - r fits the window (*span); greedy_kernel runs
+// otherwise.
 constexpr int kGreedyWin = 4096;
 
 // projection of a point on the visiting axis, as keys_kernel forms it
@@ -574,18 +579,21 @@ __global__ void __launch_bounds__(1024) greedy_window_kernel(const double* __res
     float4* wf = reinterpret_cast<float4*>(smem);            // [W]
     double* wx = reinterpret_cast<double*>(wf + W);          // [3][W]
     int* wr = reinterpret_cast<int*>(wx + 3 * W);            // [W]
-    int* s_hit = wr + W;                                     // [W] candidates of the double test
-    unsigned char* ws = reinterpret_cast<unsigned char*>(s_hit + W);   // [W]
-    __shared__ int s_f, s_nhit;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // float squared distances below this are decided in double (R2 < 1e30:
-    // no float overflow for candidates near R)
+    unsigned char* ws = reinterpret_cast<unsigned char*>(wr + W);   // [W]
+    const int lane = threadIdx.x & 31;
+    // below thr_in a float squared distance is inside R for certain (its
+    // relative error is below 4e-7; with R2 >= 1e-30 no subnormal term
+    // matters); from thr_in to thr the double distance decides; at or above
+    // thr the point is outside (R2 < 1e30: no float overflow near R)
     const bool all = !(R2 < 1e30);
     const float thr = all ? 0.f : (float)(R2 * (1.0 + 1e-5) + 1e-36);
+    const float thr_in = (!all && R2 >= 1e-30) ? (float)(R2 * (1.0 - 1e-5)) : -1.f;
     int lo = 0, hi = 0;
     // the window becomes [nlo, min(P, nlo + W)): ranks from max(hi, nlo)
-    // are loaded into slots of ranks below nlo (decided, never read again)
+    // are loaded into slots of ranks below nlo (decided; the barrier first
+    // lets every warp finish reading them)
     auto refill = [&](int nlo) {
+        __syncthreads();
         const int nhi = min(P, nlo + W);
         for (int r = max(hi, nlo) + (int)threadIdx.x; r < nhi; r += blockDim.x) {
             const int q = r & M;
@@ -603,35 +611,28 @@ __global__ void __launch_bounds__(1024) greedy_window_kernel(const double* __res
     refill(0);
     int pos = 0, nn = 0;
     for (;;) {
-        if (wid == 0) {
-            int f = -1;   // -1: no open rank in [pos, hi)
-            for (int base = pos & ~3; base < hi; base += 128) {
-                const int r0 = base + 4 * lane;
-                unsigned m = 0;   // bit k: rank r0 + k is open, in [pos, hi)
-                if (r0 < hi) {
-                    const unsigned wv = *reinterpret_cast<const unsigned*>(ws + (r0 & M));
+        // every warp finds the next open rank f in [pos, hi) itself (4 ranks
+        // per lane, a ballot): the states were written before the last
+        // barrier and are not written again before the next, so every warp
+        // finds the same f (-1: none)
+        int f = -1;
+        for (int base = pos & ~3; base < hi; base += 128) {
+            const int r0 = base + 4 * lane;
+            unsigned m = 0;   // bit k: rank r0 + k is open, in [pos, hi)
+            if (r0 < hi) {
+                const unsigned wv = *reinterpret_cast<const unsigned*>(ws + (r0 & M));
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (((wv >> (8 * k)) & 0xffu) == 0 && r0 + k >= pos && r0 + k < hi) m |= 1u << k;
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
-                if (bal) {
-                    const int src = __ffs(bal) - 1;
-                    const unsigned mm = __shfl_sync(0xffffffffu, m, src);
-                    f = base + 4 * src + __ffs(mm) - 1;
-                    break;
-                }
+                for (int k = 0; k < 4; ++k)
+                    if (((wv >> (8 * k)) & 0xffu) == 0 && r0 + k >= pos && r0 + k < hi) m |= 1u << k;
             }
-            if (lane == 0) {
-                s_f = f;
-                if (f >= 0) {
-                    ws[f & M] = 1;
-                    node_rank[nn] = f;
-                }
+            const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
+            if (bal) {
+                const int src = __ffs(bal) - 1;
+                const unsigned mm = __shfl_sync(0xffffffffu, m, src);
+                f = base + 4 * src + __ffs(mm) - 1;
+                break;
             }
         }
-        __syncthreads();
-        const int f = s_f;
         if (f < 0) {   // every rank of [pos, hi) is decided
             if (hi >= P) break;
             const int h = hi;
@@ -639,35 +640,18 @@ __global__ void __launch_bounds__(1024) greedy_window_kernel(const double* __res
             pos = h;
             continue;
         }
+        if (threadIdx.x == 0) node_rank[nn] = f;
         const int re = wr[f & M];
         if (re > hi) refill(f);   // re - f <= span <= W
-        // float pass: the open candidates the filter keeps, compacted (a
-        // warp-wide append), so that the double distances run on full warps
         const int sf = f & M;
         const float4 pf = wf[sf];
-        if (threadIdx.x == 0) s_nhit = 0;
-        __syncthreads();
-        for (int r0 = f + 1; r0 < re; r0 += blockDim.x) {
-            const int r = r0 + (int)threadIdx.x;
-            bool keep = false;
-            if (r < re) {
-                const int q = r & M;
-                keep = (all || sqdf(pf, wf[q]) < thr) && ws[q] == 0;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (bal) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&s_nhit, __popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (keep) s_hit[base + __popc(bal & ((1u << lane) - 1u))] = r & M;
-            }
-        }
-        __syncthreads();
-        const int nh = s_nhit;
         const double x = wx[sf], y = wx[W + sf], z = wx[2 * W + sf];
-        for (int k = threadIdx.x; k < nh; k += blockDim.x) {
-            const int q = s_hit[k];
-            if (sqd(x, y, z, wx[q], wx[W + q], wx[2 * W + q]) < R2) ws[q] = 2;
+        // rank f itself is never read again (scans start after it)
+        for (int r = f + 1 + (int)threadIdx.x; r < re; r += blockDim.x) {
+            const int q = r & M;
+            if (ws[q] != 0) continue;
+            const float d2f = sqdf(pf, wf[q]);
+            if (d2f < thr_in || ((all || d2f < thr) && sqd(x, y, z, wx[q], wx[W + q], wx[2 * W + q]) < R2)) ws[q] = 2;
         }
         ++nn;
         pos = f + 1;
@@ -721,11 +705,15 @@ __global__ void node_grid_xyz_kernel(int N, const int* __restrict__ nsorted, con
 // Eq. (weight_data) (1 - d^2/R^2)^3 normalised over the set, and the number
 // of node pairs of each set (edges)
 __global__ void __launch_bounds__(kT) influence_kernel(GridView g, const int* __restrict__ nsorted,
-                                                       const double* __restrict__ V, int64_t P, double R2, int K,
+                                                       const int* __restrict__ pitem,
+                                                       const double* __restrict__ pxyz, int64_t P, double R2, int K,
                                                        int* __restrict__ nidx, double* __restrict__ w,
                                                        int* __restrict__ npairs) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
-        const double x = V[3 * i], y = V[3 * i + 1], z = V[3 * i + 2];
+    // points in the point grid's cell order (slot sl holds point pitem[sl],
+    // coordinates pxyz): the lanes of a warp read the same node cells
+    for (int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sl < P; sl += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = pitem[sl];
+        const double x = pxyz[3 * sl], y = pxyz[3 * sl + 1], z = pxyz[3 * sl + 2];
         double bd[NRR_MAX_INFL];
         int bj[NRR_MAX_INFL];
         int n = 0;
@@ -758,7 +746,7 @@ __global__ void __launch_bounds__(kT) influence_kernel(GridView g, const int* __
         double sum = 0.0;
         for (int s = 0; s < n; ++s) {
             const double a = 1.0 - bd[s] / R2;
-            raw[s] = pow(a, 3.0);
+            raw[s] = a * a * a;
         }
         for (int s = 0; s < n; ++s) sum += raw[s];
         for (int s = 0; s < K; ++s) {
@@ -1046,7 +1034,7 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
     slot_rank_kernel<<<blocks_for(P), kT, 0, st>>>(n, gitem, rank_of, slot_rank);
     // the window kernel when every rank's forward R-slab fits its window
     // (decided on the device), else the global-state kernel
-    const size_t win_smem = (size_t)kGreedyWin * (16 + 24 + 4 + 4 + 1);
+    const size_t win_smem = (size_t)kGreedyWin * (16 + 24 + 4 + 1);
     {
         double *Vr, *proj;
         float4* Vf;
@@ -1101,7 +1089,7 @@ cudaError_t nrr_build_graph_gpu(const float* src, int64_t P, double R, int K, Ho
         cell_start_kernel<<<blocks_for(cells + 1), kT, 0, st>>>(nkey_s, N, cells, ncstart);
     }
     GridView nv{nkey_s, nxyz, N, {hsc[3], hsc[4], hsc[5]}, h, {dims[0], dims[1], dims[2]}, ncstart};
-    influence_kernel<<<blocks_for(P), kT, 0, st>>>(nv, nsorted, V, P, R2, K, nidx, w, npairs);
+    influence_kernel<<<blocks_for(P), kT, 0, st>>>(nv, nsorted, gitem, gxyz, P, R2, K, nidx, w, npairs);
     GK(cudaGetLastError());
     GK(exclusive_sum(s, npairs, poff, n, st));
     GK(cudaMemcpyAsync(&last[0], poff + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
