@@ -142,3 +142,23 @@ def test_host_mesh_graph_rejects_bad_meshes():
     assert lib.nrr_graph_build_mesh(g, nrr._ptr(V32), 16, None, len(F), 1.0, 8) == nrr.NRR_E_INVALID
     assert lib.nrr_graph_build_mesh(g, nrr._ptr(V32), 16, nrr._ptr(F.astype(np.int32)), 0, 1.0, 8) \
         == nrr.NRR_E_INVALID
+
+
+def test_host_graph_from_concurrent_threads():
+    """The host construction runs its parallel loops on one pool of worker
+    threads shared by every caller: graphs built from several Python
+    threads at once (ctypes releases the GIL during the call) are those
+    built one after another, bit for bit."""
+    import concurrent.futures
+    srcs = [synth.tiny_pair(6000 + 500 * k, 100, seed=30 + k).src for k in range(6)]
+    radii = [0.12, 0.15, 0.1, 0.13, 0.11, 0.14]
+    ref = [nrr.build_graph(s, radius=r) for s, r in zip(srcs, radii)]
+    with concurrent.futures.ThreadPoolExecutor(max_workers=6) as ex:
+        got = list(ex.map(lambda a: nrr.build_graph(a[0], radius=a[1]), zip(srcs, radii)))
+    for a, b in zip(got, ref):
+        assert np.array_equal(a.nodes, b.nodes)
+        assert np.array_equal(a.nidx, b.nidx)
+        assert np.array_equal(a.w, b.w)
+        assert np.array_equal(a.edges, b.edges)
+        assert np.array_equal(a.r, b.r)
+        assert a.lbar == b.lbar
