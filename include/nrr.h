@@ -380,14 +380,17 @@ nrr_status nrr_graph_build(nrr_graph** out, const float* src_xyz, int64_t P, dou
  * reading): PCA by reductions and a 3x3 Jacobi eigen-solve, the visiting
  * order by a radix sort of the projections, the greedy sampling node by
  * node in that order in one CTA (its threads share the scan for the next
- * uncovered point and the covering of each new node's ball, found through
- * a uniform grid of cells of size R: the sequential decisions exactly),
- * then the influence sets, weights, edges and r_ij; every distance
- * and projection in double without fused multiply-adds. src_xyz [P][3]
- * float32, host or device; cuda_stream the stream to use (NULL: the legacy
- * default stream); l-bar on the GPU on the graph's grid when the radius is
- * given (on the host when it defaults to 5 l-bar, or when some point's six
- * nearest others are not all within R).
+ * uncovered point and the covering of each new node's ball, over a window
+ * of the visiting order held in shared memory, or through a uniform grid
+ * of cells of size R when a node's R-slab exceeds that window: the
+ * sequential decisions exactly), then the influence sets, weights, edges
+ * and r_ij; every decision on a distance or projection is taken in double
+ * without fused multiply-adds (float tests with proven margins only select
+ * the candidates). src_xyz [P][3] float32, host or device; cuda_stream the
+ * stream to use (NULL: the legacy default stream); l-bar on the GPU on the
+ * graph's grid when the radius is given (points whose six nearest others
+ * are not all within R by brute force on the GPU; on the host when the
+ * radius defaults to 5 l-bar, or when more than 4,096 points are such).
  * Errors as nrr_graph_build, plus NRR_E_CUDA. The handle is used with
  * nrr_graph_sizes/get/destroy. */
 nrr_status nrr_graph_build_gpu(nrr_graph** out, const float* src_xyz, int64_t P, double radius, int max_influence,
