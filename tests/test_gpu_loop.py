@@ -132,3 +132,33 @@ def test_device_loop_history_matches_steps():
     a.close()
     b.close()
     c.close()
+
+
+def test_batch_create_parallel_contexts():
+    """nrr_batch_create builds the pairs' contexts on several host threads:
+    each pair's graph is the one a single context builds (also with the
+    graph on the GPU, several constructions then sharing the device), and
+    a bad pair is reported with the lowest failing index."""
+    nrr = _nrr()
+    pairs = [synth.tiny_pair(P, T, seed=110 + k, noise=0.002, outliers=0.03)
+             for k, (P, T) in enumerate([(800, 900), (1600, 1500), (500, 520), (1200, 1250),
+                                         (2000, 2100), (700, 760), (1000, 980), (1400, 1450),
+                                         (600, 640)])]
+    for on_gpu in (0, 1):
+        kw = dict(radius=0.3, aa_m=5, precision="mixed", graph_on_gpu=on_gpu)
+        b = nrr.BatchRegistration([(q.src, q.tgt) for q in pairs], params=kw)
+        for k, q in enumerate(pairs):
+            single = nrr.Registration(q.src, q.tgt, **kw)
+            gb, gs = nrr.nrr_get_graph(b.context(k)), single.graph()
+            assert np.array_equal(gb.nodes, gs.nodes) and np.array_equal(gb.edges, gs.edges)
+            assert np.array_equal(gb.nidx, gs.nidx) and np.array_equal(gb.w, gs.w)
+            assert np.array_equal(gb.r, gs.r)
+            single.close()
+        b.close()
+    bad = [(q.src.copy(), q.tgt) for q in pairs]
+    bad[5][0][3, 1] = np.nan
+    bad[7][0][0, 0] = np.inf
+    with pytest.raises(nrr.NrrError) as e:
+        nrr.BatchRegistration(bad, params=dict(radius=0.3, aa_m=5, precision="mixed"))
+    assert e.value.code == nrr.NRR_E_INVALID
+    assert "pair 5" in str(e.value)
